@@ -1,0 +1,231 @@
+"""Block LU of the sparse S and the solve S y = U^T b, x = V y (§1, Eq. sp0).
+
+The paper factors S with a sparse direct package (§5.3-5.4) and says nothing
+about the order of elimination or about pivoting.  The readings taken:
+
+* Ordering -- nested dissection along the cluster tree.  Every S node
+  v = (l, t) below the top gets the *closure* cluster
+      closure(v) = LCA of t and every level-l close neighbour e of t with
+                   e > t (cluster number),
+  and every top node gets the root.  Two nodes whose closures lie in
+  disjoint subtrees are never coupled in S (and never become coupled by
+  fill), so the nodes are eliminated by closure depth, deepest first; the
+  nodes that share a closure form one supernode; supernodes of one closure
+  depth are independent.  Order key: (-depth(closure), closure, node id).
+* Pivoting -- partial pivoting restricted to the rows of the supernode's own
+  diagonal block (LAPACK getrf semantics: the first row of largest modulus).
+* Symbolic factorization -- plain graph elimination on the node graph of S
+  (made structurally symmetric): eliminating a supernode joins its remaining
+  neighbours (its *boundary*) into a clique.
+
+The numeric factorization is the right-looking block elimination written on
+a dictionary of dense node-by-node blocks:
+      F11 = P L11 U11          (dense LU of the supernode block, getrf)
+      U12 = L11^-1 P^T F12,    L21 = F21 U11^-1
+      M[w1, w2] -= L21[w1] U12[w2]   for all boundary pairs (w1, w2).
+The dense LU of the pivot block is the LAPACK routine (scipy) used as one
+step; everything else is written out.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import scipy.linalg as sla
+
+from .sparsify import Sparsified
+
+
+def _depths(h) -> np.ndarray:
+    dep = np.zeros(h.ncl, dtype=np.int64)
+    for d in range(h.depth + 1):
+        dep[h.level_ptr[d]:h.level_ptr[d + 1]] = d
+    return dep
+
+
+def lca(h, dep, a: int, b: int) -> int:
+    while dep[a] > dep[b]:
+        a = int(h.parent[a])
+    while dep[b] > dep[a]:
+        b = int(h.parent[b])
+    while a != b:
+        a, b = int(h.parent[a]), int(h.parent[b])
+    return a
+
+
+@dataclasses.dataclass
+class Symbolic:
+    closure: np.ndarray       # int64[nnodes]
+    order: np.ndarray         # elimination order of the nodes
+    sn_ptr: np.ndarray        # supernodes as ranges of ``order``
+    sn_closure: np.ndarray    # closure cluster of each supernode
+    sn_depth: np.ndarray      # depth of that closure
+    boundary: list            # per supernode: node ids (ascending elimination position)
+    flops: float              # (2/3)s^3 + 2 s^2 b + 2 s b^2 summed over supernodes (scalar sizes)
+
+
+def node_graph(sp: Sparsified) -> list:
+    nn = sp.sch.node_size.shape[0]
+    adj = [set() for _ in range(nn)]
+    for (i, j) in sp.blocks.keys():
+        if i != j:
+            adj[i].add(j)
+            adj[j].add(i)
+    return adj
+
+
+def symbolic(h, sp: Sparsified) -> Symbolic:
+    sch = sp.sch
+    nn = sch.node_size.shape[0]
+    dep = _depths(h)
+    close = [dict() for _ in range(sch.lstop + 1)]
+    for l in range(sch.lstop):
+        for (t, e) in sch.near[l]:
+            close[l].setdefault(int(t), []).append(int(e))
+    clo = np.zeros(nn, dtype=np.int64)
+    for v in range(nn):
+        l, t = int(sch.node_level[v]), int(sch.node_cluster[v])
+        if l == sch.lstop:
+            clo[v] = 0
+            continue
+        c = t
+        for e in close[l].get(t, []):
+            if e > t:
+                c = lca(h, dep, c, e)
+        clo[v] = c
+    order = np.array(sorted(range(nn), key=lambda v: (-dep[clo[v]], clo[v], v)), dtype=np.int64)
+    sn_ptr = [0]
+    for i in range(1, nn):
+        if clo[order[i]] != clo[order[i - 1]]:
+            sn_ptr.append(i)
+    sn_ptr.append(nn)
+    sn_ptr = np.array(sn_ptr, dtype=np.int64)
+    pos = np.empty(nn, dtype=np.int64)
+    pos[order] = np.arange(nn)
+    adj = node_graph(sp)
+    boundary = []
+    size = sch.node_size
+    flops = 0.0
+    for k in range(sn_ptr.size - 1):
+        sn = [int(v) for v in order[sn_ptr[k]:sn_ptr[k + 1]]]
+        sset = set(sn)
+        bnd = set()
+        for v in sn:
+            bnd |= adj[v]
+        bnd -= sset
+        bl = sorted(bnd, key=lambda w: pos[w])
+        assert all(pos[w] >= sn_ptr[k + 1] for w in bl)
+        boundary.append(np.array(bl, dtype=np.int64))
+        for w in bl:
+            adj[w] |= bnd
+            adj[w].discard(w)
+            adj[w] -= sset
+        s = float(sum(size[v] for v in sn))
+        b = float(sum(size[w] for w in bl))
+        flops += (2.0 / 3.0) * s ** 3 + 2.0 * s * s * b + 2.0 * s * b * b
+    sn_closure = np.array([clo[order[sn_ptr[k]]] for k in range(sn_ptr.size - 1)], dtype=np.int64)
+    return Symbolic(clo, order, sn_ptr, sn_closure, dep[sn_closure], boundary, flops)
+
+
+@dataclasses.dataclass
+class Factors:
+    sym: Symbolic
+    node_off: np.ndarray
+    lu: list       # per supernode: (lu, piv) from getrf
+    L21: list
+    U12: list
+
+
+def _rows(node_off, nodes):
+    if len(nodes) == 0:
+        return np.zeros(0, dtype=np.int64)
+    return np.concatenate([np.arange(node_off[v], node_off[v + 1]) for v in nodes])
+
+
+def _gather(M: dict, rows: list, cols: list, size) -> np.ndarray:
+    ro = np.concatenate([[0], np.cumsum([size[v] for v in rows])]).astype(np.int64)
+    co = np.concatenate([[0], np.cumsum([size[v] for v in cols])]).astype(np.int64)
+    out = np.zeros((ro[-1], co[-1]))
+    for a, v in enumerate(rows):
+        for b, w in enumerate(cols):
+            blk = M.get((v, w))
+            if blk is not None:
+                out[ro[a]:ro[a + 1], co[b]:co[b + 1]] = blk
+    return out
+
+
+def factor(h, sp: Sparsified, sym: Symbolic | None = None) -> Factors:
+    if sym is None:
+        sym = symbolic(h, sp)
+    size = sp.sch.node_size
+    M = {k: v.copy() for k, v in sp.blocks.items()}
+    LU, L21s, U12s = [], [], []
+    for k in range(sym.sn_ptr.size - 1):
+        sn = [int(v) for v in sym.order[sym.sn_ptr[k]:sym.sn_ptr[k + 1]]]
+        bd = [int(w) for w in sym.boundary[k]]
+        F11 = _gather(M, sn, sn, size)
+        F12 = _gather(M, sn, bd, size)
+        F21 = _gather(M, bd, sn, size)
+        lu, piv = sla.lu_factor(F11, check_finite=True)
+        if np.any(np.diag(lu) == 0.0):
+            raise np.linalg.LinAlgError("zero pivot in supernode %d" % k)
+        F12p = F12.copy()
+        for i, p in enumerate(piv):
+            if p != i:
+                F12p[[i, p]] = F12p[[p, i]]
+        U12 = sla.solve_triangular(lu, F12p, lower=True, unit_diagonal=True) if F12p.size else F12p
+        L21 = sla.solve_triangular(lu, F21.T, trans="T", lower=False).T if F21.size else F21
+        LU.append((lu, piv))
+        L21s.append(L21)
+        U12s.append(U12)
+        if bd:
+            upd = L21 @ U12
+            bo = np.concatenate([[0], np.cumsum([size[w] for w in bd])]).astype(np.int64)
+            for a, w1 in enumerate(bd):
+                for b, w2 in enumerate(bd):
+                    blk = upd[bo[a]:bo[a + 1], bo[b]:bo[b + 1]]
+                    if (w1, w2) in M:
+                        M[(w1, w2)] = M[(w1, w2)] - blk
+                    else:
+                        M[(w1, w2)] = -blk
+        for v in sn:
+            for w in list(bd) + sn:
+                M.pop((v, w), None)
+                M.pop((w, v), None)
+    return Factors(sym, sp.sch.node_off, LU, L21s, U12s)
+
+
+def solve_S(fa: Factors, c: np.ndarray) -> np.ndarray:
+    """y = S^{-1} c by the stored block factors (forward then backward sweep)."""
+    sym = fa.sym
+    y = np.array(c, dtype=np.float64, copy=True).reshape(c.shape[0], -1)
+    rows = [_rows(fa.node_off, [int(v) for v in sym.order[sym.sn_ptr[k]:sym.sn_ptr[k + 1]]])
+            for k in range(sym.sn_ptr.size - 1)]
+    brows = [_rows(fa.node_off, [int(w) for w in sym.boundary[k]]) for k in range(sym.sn_ptr.size - 1)]
+    for k in range(len(rows)):
+        lu, piv = fa.lu[k]
+        ys = y[rows[k]]
+        for i, p in enumerate(piv):
+            if p != i:
+                ys[[i, p]] = ys[[p, i]]
+        ys = sla.solve_triangular(lu, ys, lower=True, unit_diagonal=True)
+        y[rows[k]] = ys
+        if brows[k].size:
+            y[brows[k]] -= fa.L21[k] @ ys
+    for k in range(len(rows) - 1, -1, -1):
+        lu, _ = fa.lu[k]
+        ys = y[rows[k]]
+        if brows[k].size:
+            ys = ys - fa.U12[k] @ y[brows[k]]
+        y[rows[k]] = sla.solve_triangular(lu, ys, lower=False)
+    return y.reshape(np.shape(c))
+
+
+def solve(h, sp: Sparsified, fa: Factors, b: np.ndarray) -> np.ndarray:
+    """x = V S^{-1} U^T b (Eq. sp0: S y = U^T b, x = V y)."""
+    from .sparsify import apply_N, apply_T
+    c = apply_T(sp, h, b, col=False)
+    y = solve_S(fa, c)
+    return apply_N(sp, h, y, col=True)
