@@ -1,0 +1,249 @@
+/*
+ * h2sp -- non-extensive sparsification of H^2 matrices on one GB300 GPU.
+ *
+ * The library builds, for an H^2 matrix A given by its parameters
+ * (Definition 4.9, §4.1), the factorization  A = U S V^T  of §2 (Eq.
+ * main_fact): U and V are orthogonal products of block-diagonal and
+ * permutation matrices (Eq. main_uv), S is a sparse N x N matrix of the same
+ * size as A.  It then factors S by a block LU and solves  A x = b  as
+ * S y = U^T b,  x = V y  (§1, Eq. sp0), directly or as the preconditioner of
+ * iterative refinement / GMRES driven by the H^2 matrix-vector product (§5.5).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Index space.  Vectors are indexed in cluster-tree order: the points are
+ *   ordered so that every cluster owns the contiguous range
+ *   [begin[t], begin[t] + size[t]).  Vectors are FP64, column-major, with a
+ *   leading dimension >= n; nrhs columns.
+ * - Memory.  Pointers documented as "host" must be host memory; pointers
+ *   documented as "device" must be device memory of the current device.  The
+ *   H^2 numeric arrays are BORROWED: the handle keeps pointers to them and
+ *   reads them again in h2sp_apply(H2SP_OP_H2) and in iterative solves, so
+ *   they must stay valid and unchanged until h2sp_destroy.  Everything else
+ *   the library needs (the blocks of U and V, S, the factors, workspaces) is
+ *   allocated by the library with cudaMallocAsync on the call's stream and
+ *   owned by the handle.
+ * - Asynchrony.  Work is enqueued on the stream passed to each call.  Calls
+ *   that must look at device results (h2sp_factor's pivot check, h2sp_solve's
+ *   residual checks, exports) synchronise that stream before returning.
+ * - Errors.  Every entry point returns an h2sp_status; nothing aborts or
+ *   throws.  On error the handle is left in a state where h2sp_destroy is
+ *   the only guaranteed-safe call.  h2sp_status_string names each code.
+ * - Threading.  A handle must not be used by two host threads at once.
+ */
+#ifndef H2SP_H
+#define H2SP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *h2sp_stream; /* a cudaStream_t; NULL = legacy default stream */
+typedef struct h2sp_handle h2sp_handle;
+
+typedef enum {
+  H2SP_OK = 0,
+  H2SP_EINVAL = -1,     /* malformed descriptor or argument; nothing was launched */
+  H2SP_ENOMEM = -2,     /* device allocation failed */
+  H2SP_ECUDA = -3,      /* a CUDA runtime call failed (see h2sp_last_cuda_error) */
+  H2SP_ESINGULAR = -4,  /* a pivot block of S is singular (zero pivot) */
+  H2SP_ESTATE = -5,     /* calls in the wrong order (e.g. solve before factor) */
+  H2SP_ENOCONV = -6,    /* the iteration did not reach the tolerance in maxit */
+  H2SP_ETIMEOUT = -7,   /* a bounded device wait gave up */
+  H2SP_EUNSUPPORTED = -8 /* a valid input outside what this build supports (block too large) */
+} h2sp_status;
+
+/* Precision of the factorization of S (h2sp_factor). */
+typedef enum {
+  H2SP_FP64 = 0, /* FP64 fronts, FP64 arithmetic */
+  H2SP_FP32 = 1  /* FP32 fronts, FP32 arithmetic (a preconditioner for FP64 IR/GMRES) */
+} h2sp_prec;
+
+/* Operators for h2sp_apply. */
+typedef enum {
+  H2SP_OP_UT = 0,   /* out = U^T in   (point space -> S space)         Eq. sp0 */
+  H2SP_OP_V = 1,    /* out = V in     (S space -> point space)         Eq. sp0 */
+  H2SP_OP_U = 2,    /* out = U in                                      Eq. main_uv */
+  H2SP_OP_VT = 3,   /* out = V^T in                                    Eq. main_uv */
+  H2SP_OP_S = 4,    /* out = S in     (S space -> S space)             Eq. main_fact */
+  H2SP_OP_H2 = 5,   /* out = A in, the FP64 H^2 product of Definition 4.9 */
+  H2SP_OP_SINV = 6  /* out = S^{-1} in with the current factors (needs h2sp_factor) */
+} h2sp_op;
+
+/* Solve modes for h2sp_solve. */
+typedef enum {
+  H2SP_DIRECT = 0, /* x = V S^{-1} U^T b once (Eq. sp0) */
+  H2SP_IR = 1,     /* iterative refinement on the FP64 H^2 residual, preconditioned by the factors */
+  H2SP_GMRES = 2   /* restarted right-preconditioned GMRES on the FP64 H^2 product (§5.5) */
+} h2sp_mode;
+
+/*
+ * One H^2 matrix (Definition 4.9, §4.1).
+ *
+ * The cluster tree is level-uniform (every leaf at depth `depth`); clusters
+ * are numbered depth by depth, and inside one depth in the order of their
+ * parents, so the children of a cluster have consecutive numbers and a
+ * cluster's children come in increasing number.  Row and column cluster
+ * trees are the same tree.  Column ranks equal row ranks.
+ *
+ * Blocks are column-major and packed; *_off arrays give each block's first
+ * element in the packed array.
+ */
+typedef struct {
+  int64_t n;                         /* number of points / rows of A */
+  int32_t depth;                     /* leaf depth D >= 0 */
+  /* ---- structure: HOST arrays ---- */
+  const int32_t *level_ptr;          /* [D+2]; clusters of depth d: [level_ptr[d], level_ptr[d+1]) */
+  const int32_t *parent;             /* [ncl]; -1 for cluster 0 (the root) */
+  const int64_t *begin, *size;       /* [ncl]; contiguous index range of each cluster */
+  const int32_t *rank;               /* [ncl]; k_t, the cluster-basis rank (Definition 4.7) */
+  const int64_t *far_ptr;            /* [ncl+1]; CSR of the interaction list by row cluster */
+  const int32_t *far_col;            /* [nfar];  same-depth column cluster of each admissible pair, ascending per row */
+  const int64_t *near_ptr;           /* [nleaf+1]; CSR of the close blocks by leaf (leaf = cluster - level_ptr[D]) */
+  const int32_t *near_col;           /* [nnear]; column leaf cluster ids, ascending per row */
+  const int64_t *leaf_basis_off;     /* [nleaf]; R_t, |t| x k_t */
+  const int64_t *transfer_off;       /* [ncl];   T_c, k_c x k_parent (entry 0 unused) */
+  const int64_t *coupling_off;       /* [nfar];  D_ts, k_t x k_s */
+  const int64_t *near_off;           /* [nnear]; C_ts, |t| x |s| */
+  const int64_t *col_leaf_basis_off; /* [nleaf] or NULL */
+  const int64_t *col_transfer_off;   /* [ncl] or NULL */
+  /* ---- numbers: DEVICE arrays (borrowed, see above) ---- */
+  const double *leaf_basis;          /* row cluster basis of the leaves */
+  const double *transfer;            /* row transfer matrices */
+  const double *coupling;            /* coupling matrices of the interaction list */
+  const double *near_block;          /* close matrix blocks (Definition 4.8) */
+  const double *col_leaf_basis;      /* column basis E of the leaves; NULL => E = R (symmetric bases) */
+  const double *col_transfer;        /* column transfer matrices; NULL iff col_leaf_basis is NULL */
+} h2sp_h2_desc;
+
+typedef struct {
+  int32_t flags;       /* reserved, pass 0 */
+} h2sp_opts;
+
+typedef struct {
+  int32_t mode;        /* h2sp_mode */
+  double tol;          /* target max_k ||b_k - A x_k|| / ||b_k|| for IR / GMRES (e.g. 1e-10) */
+  int32_t maxit;       /* iteration cap (IR: refinement steps; GMRES: total inner steps) */
+  int32_t restart;     /* GMRES restart length (ignored by IR / DIRECT) */
+} h2sp_solve_opts;
+
+typedef struct {
+  int32_t iters;       /* refinement steps / GMRES inner steps taken */
+  double rel_residual; /* final max_k ||b_k - A x_k|| / ||b_k|| (FP64 H^2 product); -1 for DIRECT */
+  int32_t status;      /* h2sp_status of the solve */
+} h2sp_solve_info;
+
+/* Sizes and counters of a handle (filled by h2sp_query). */
+typedef struct {
+  int64_t n;
+  int32_t depth, lstop;           /* leaf depth; first uncompressed level (levels count from the leaves) */
+  int32_t nnodes;                 /* S nodes (non-basis blocks + top clusters) */
+  int64_t nnzb, nnz;              /* blocks and scalar nonzeros of S */
+  int32_t nsupernodes, nfront_levels;
+  int64_t max_front;              /* largest front (s + b) */
+  int64_t front_elems;            /* sum of (s+b)^2 over the fronts */
+  double factor_flops;            /* sum over supernodes of (2/3)s^3 + 2 s^2 b + 2 s b^2 */
+  double sparsify_flops;          /* algorithmic flops of the sparsification */
+  int32_t factor_prec;            /* h2sp_prec of the current factors, -1 if none */
+  double plan_seconds;            /* host time spent planning in the last h2sp_sparsify */
+} h2sp_stats;
+
+/*
+ * h2sp_sparsify -- build A = U S V^T from the H^2 parameters (§2.1-2.3 with
+ * the factors of §4.2-4.3).  Validates the descriptor on the host (returns
+ * H2SP_EINVAL without launching anything if it is malformed: unsorted lists,
+ * inconsistent tree, ranks that do not fit, a missing column array), plans
+ * the level recursion and the symbolic factorization of S on the host, and
+ * enqueues the FP64 kernels on `stream`: the Householder completions of the
+ * cluster bases per level, the coupling projections, the transforms of the
+ * close blocks and of the cross-level panels, and the scatter into S.
+ * On success *out owns a new handle.
+ */
+int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream stream, h2sp_handle **out);
+
+/*
+ * h2sp_analyze -- the host-only part of h2sp_sparsify: validate the
+ * descriptor and plan the level recursion, the block pattern of S (§3) and
+ * the symbolic factorization of S.  Makes no CUDA call and does not read the
+ * numeric arrays of the descriptor (they may be NULL).  The resulting handle
+ * supports h2sp_query, h2sp_export_structure, h2sp_export_S with vals == NULL
+ * and h2sp_destroy; every other call returns H2SP_ESTATE.
+ */
+int h2sp_analyze(const h2sp_h2_desc *desc, h2sp_handle **out);
+
+/*
+ * h2sp_factor -- block LU of S (the paper factors S with a sparse direct
+ * method, §5.3-5.4): nested-dissection order along the cluster tree,
+ * multifrontal elimination level by level, partial pivoting inside each
+ * supernode's diagonal block.  `prec` selects FP64 or FP32 fronts.
+ * Synchronises the stream; returns H2SP_ESINGULAR on a zero pivot.
+ */
+int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream);
+
+/*
+ * h2sp_solve -- x = A^{-1} b through S y = U^T b, x = V y (Eq. sp0), either
+ * once (DIRECT, needs h2sp_factor) or iterated on the FP64 H^2 residual.
+ * b (ldb >= n) and x (ldx >= n) are device arrays of nrhs columns; x may not
+ * alias b.  `info` (host, may be NULL) receives iterations and the final
+ * relative residual.  Synchronises the stream for IR / GMRES.
+ */
+int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *opts, int32_t nrhs, const double *b, int64_t ldb,
+               double *x, int64_t ldx, h2sp_solve_info *info, h2sp_stream stream);
+
+/*
+ * h2sp_apply -- out = op(in) for one of the operators above; device arrays,
+ * nrhs columns, leading dimensions >= n.  `in` and `out` must not alias.
+ */
+int h2sp_apply(h2sp_handle *h, int32_t op, int32_t nrhs, const double *in, int64_t ldin, double *out,
+               int64_t ldout, h2sp_stream stream);
+
+/*
+ * h2sp_export_S -- copy S to host arrays in its variable-block (VBR) layout:
+ * node_size[nnodes], brow_ptr[nnodes+1] (int64), bcol_idx[nnzb] (int32,
+ * ascending per block row), val_off[nnzb] (int64), vals[nnz] (each block
+ * column-major).  Pass NULL for any array to skip it; call h2sp_query first
+ * for the sizes.  Synchronises the stream.
+ */
+int h2sp_export_S(h2sp_handle *h, int64_t *node_size, int64_t *brow_ptr, int32_t *bcol_idx, int64_t *val_off,
+                  double *vals, h2sp_stream stream);
+
+/*
+ * h2sp_export_Q -- copy the square orthogonal block Q_t of cluster t (the
+ * diagonal block of U_l at t's level, §4.2; columns [0, k') span the basis,
+ * columns [k', m) the non-basis part) to host memory `q` (m x m, column
+ * major), and its local size to *m.  col != 0 selects the column side (V).
+ * q may be NULL to query m.  Clusters at or above the top level have m = 0.
+ */
+int h2sp_export_Q(h2sp_handle *h, int32_t cluster, int32_t col, int64_t *m, double *q, h2sp_stream stream);
+
+/*
+ * h2sp_export_structure -- integer structure for verification, host arrays:
+ * node_level[nnodes], node_cluster[nnodes], closure[nnodes] (closure cluster
+ * of each node), order[nnodes] (elimination order), sn_ptr[nsupernodes+1]
+ * (supernodes as ranges of `order`), bnd_ptr[nsupernodes+1] and
+ * bnd[bnd_ptr[nsupernodes]] (boundary nodes of each supernode, in
+ * elimination order).  Any pointer may be NULL.  *nbnd receives the total
+ * boundary length when not NULL.
+ */
+int h2sp_export_structure(h2sp_handle *h, int32_t *node_level, int32_t *node_cluster, int32_t *closure,
+                          int32_t *order, int32_t *sn_ptr, int32_t *bnd_ptr, int32_t *bnd, int64_t *nbnd);
+
+/* h2sp_query -- fill *st with the handle's sizes and counters. */
+int h2sp_query(const h2sp_handle *h, h2sp_stats *st);
+
+/* h2sp_destroy -- free everything the handle owns (synchronises its last stream). NULL is a no-op. */
+void h2sp_destroy(h2sp_handle *h);
+
+/* Human-readable name of a status code. */
+const char *h2sp_status_string(int32_t status);
+
+/* Text of the last CUDA error seen by the library on this thread ("" if none). */
+const char *h2sp_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* H2SP_H */

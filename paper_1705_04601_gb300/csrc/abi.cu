@@ -1,0 +1,739 @@
+// The C ABI of h2sp (include/h2sp.h): handle management and the host-side
+// orchestration of the kernels for h2sp_sparsify, h2sp_factor, h2sp_solve and
+// h2sp_apply.  All device memory the handle owns comes from cudaMallocAsync on
+// the call's stream; the numeric arrays of the H^2 descriptor are borrowed.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.h"
+
+using namespace h2sp;
+
+namespace {
+
+thread_local std::string g_cuda_err;
+
+struct CudaFail {
+  cudaError_t e;
+};
+
+inline void ck(cudaError_t e) {
+  if (e != cudaSuccess) {
+    g_cuda_err = cudaGetErrorString(e);
+    throw CudaFail{e};
+  }
+}
+
+int status_of(cudaError_t e) { return e == cudaErrorMemoryAllocation ? H2SP_ENOMEM : H2SP_ECUDA; }
+
+struct LevelDev {
+  QItem *q = nullptr, *qc = nullptr;
+  WItem *w = nullptr, *wc = nullptr;
+  CItem *c = nullptr;
+  XItem *x = nullptr;
+  int nq = 0, nw = 0, nc = 0, nx = 0;
+  double **src_base = nullptr, **dst_base = nullptr;  // device arrays of 4 pointers
+  double *W = nullptr, *Wc = nullptr;
+  ApItem *ap = nullptr;  // applies of this level's Q blocks
+  int nap = 0;
+};
+
+struct FrontLevel {
+  int lo, hi, max_s, max_f, max_b;
+};
+
+}  // namespace
+
+struct h2sp_handle {
+  Plan plan;
+  cudaStream_t stream = nullptr;
+  std::vector<void *> allocs;
+  // borrowed H^2 numbers
+  const double *leaf_basis = nullptr, *transfer = nullptr, *coupling = nullptr, *near_block = nullptr;
+  const double *col_leaf_basis = nullptr, *col_transfer = nullptr;
+  // sparsification
+  double *Q = nullptr, *Qc = nullptr, *Rr = nullptr, *Rrc = nullptr, *S = nullptr;
+  std::vector<double *> Cbuf, RPbuf, CPbuf;
+  std::vector<LevelDev> lv;
+  // applies
+  int64_t *top_src = nullptr, *top_dst = nullptr;
+  int32_t *top_len = nullptr;
+  int ntop = 0;
+  int64_t max_width = 0;
+  double *vecA = nullptr, *vecB = nullptr, *vecS = nullptr, *vecT = nullptr, *vecR = nullptr;
+  int vec_rhs = 0;
+  // S structure for products
+  int64_t *brow_ptr = nullptr, *val_off = nullptr, *node_off = nullptr;
+  int32_t *bcol = nullptr;
+  // factor
+  int prec = -1;
+  void *fronts = nullptr;
+  FrontDev *fr = nullptr;
+  int32_t *piv = nullptr, *perm = nullptr, *swaps = nullptr, *fidx = nullptr, *fmap = nullptr;
+  AItem *asm_items = nullptr;
+  int *err = nullptr;
+  std::vector<FrontLevel> flev;
+  int max_s_all = 0;
+  int64_t *work_off = nullptr;
+  void *work = nullptr;
+  float *yf = nullptr;
+  int work_rhs = 0;
+  // H^2 product
+  H2Dev h2{};
+  int32_t *child_start = nullptr, *child_cnt = nullptr;
+  double *xh = nullptr, *yh = nullptr;
+  double *norms = nullptr;
+  double plan_seconds = 0.0;
+  bool device_ready = false;  // false for handles made by h2sp_analyze
+
+  template <class T>
+  T *alloc(size_t n) {
+    if (n == 0) n = 1;
+    void *p = nullptr;
+    ck(cudaMallocAsync(&p, n * sizeof(T), stream));
+    allocs.push_back(p);
+    return static_cast<T *>(p);
+  }
+  template <class T>
+  T *upload(const std::vector<T> &v) {
+    T *d = alloc<T>(v.size());
+    if (!v.empty()) ck(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, stream));
+    return d;
+  }
+  void release() {
+    if (allocs.empty()) return;
+    for (void *p : allocs) cudaFreeAsync(p, stream);
+    allocs.clear();
+    cudaStreamSynchronize(stream);
+  }
+};
+
+namespace {
+
+void init_pool_once() {
+  static bool done = false;
+  if (done) return;
+  done = true;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;  // keep freed memory in the pool between calls of this process
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+}
+
+// ---------------- vectors of the applies ----------------
+void ensure_vectors(h2sp_handle *h, int nrhs) {
+  if (h->vec_rhs >= nrhs) return;
+  const int64_t n = h->plan.n;
+  const int64_t w = std::max<int64_t>(h->max_width, n);
+  h->vecA = h->alloc<double>(size_t(w) * nrhs);
+  h->vecB = h->alloc<double>(size_t(w) * nrhs);
+  h->vecS = h->alloc<double>(size_t(n) * nrhs);
+  h->vecT = h->alloc<double>(size_t(n) * nrhs);
+  h->vecR = h->alloc<double>(size_t(n) * nrhs);
+  h->vec_rhs = nrhs;
+}
+
+// out (S space, ld n) = Qside^T in (point space)
+void apply_T(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *out, int64_t ldout, int nrhs) {
+  const Plan &p = h->plan;
+  cudaStream_t s = h->stream;
+  const double *Qb = col ? h->Qc : h->Q;
+  if (p.lstop == 0) {
+    ck(launch_copy_rows(h->top_src, h->top_dst, h->top_len, h->ntop, in, ldin, out, ldout, nrhs, s));
+    return;
+  }
+  const int64_t ldw = std::max<int64_t>(h->max_width, p.n);
+  const double *x = in;
+  int64_t ldx = ldin;
+  double *bufs[2] = {h->vecA, h->vecB};
+  for (int l = 0; l < p.lstop; ++l) {
+    double *xn = bufs[l & 1];
+    ck(launch_apply_qt(h->lv[l].ap, h->lv[l].nap, Qb, x, ldx, out, ldout, xn, ldw, nrhs, s));
+    x = xn;
+    ldx = ldw;
+  }
+  ck(launch_copy_rows(h->top_src, h->top_dst, h->top_len, h->ntop, x, ldx, out, ldout, nrhs, s));
+}
+
+// out (point space) = Qside in (S space)
+void apply_N(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *out, int64_t ldout, int nrhs) {
+  const Plan &p = h->plan;
+  cudaStream_t s = h->stream;
+  const double *Qb = col ? h->Qc : h->Q;
+  if (p.lstop == 0) {
+    ck(launch_copy_rows(h->top_dst, h->top_src, h->top_len, h->ntop, in, ldin, out, ldout, nrhs, s));
+    return;
+  }
+  const int64_t ldw = std::max<int64_t>(h->max_width, p.n);
+  double *bufs[2] = {h->vecA, h->vecB};
+  double *xn = bufs[p.lstop & 1];
+  ck(launch_copy_rows(h->top_dst, h->top_src, h->top_len, h->ntop, in, ldin, xn, ldw, nrhs, s));
+  for (int l = p.lstop - 1; l >= 0; --l) {
+    double *x = (l == 0) ? out : bufs[l & 1];
+    const int64_t ldx = (l == 0) ? ldout : ldw;
+    ck(launch_apply_q(h->lv[l].ap, h->lv[l].nap, Qb, xn, ldw, in, ldin, x, ldx, nrhs, s));
+    xn = x;
+  }
+}
+
+void h2_matvec(h2sp_handle *h, const double *x, int64_t ldx, double *y, int64_t ldy, int nrhs) {
+  const Plan &p = h->plan;
+  ck(launch_h2_matvec(h->h2, p.level_ptr.data(), h->child_start, h->child_cnt, p.D, x, ldx, y, ldy, nrhs, h->xh,
+                      h->yh, std::max<int64_t>(p.xh_elems, 1), h->stream));
+}
+
+// per-front work vectors of the triangular solves, for 16 right-hand sides at a time
+constexpr int kSolveRhs = 16;
+void ensure_work(h2sp_handle *h, int nrhs) {
+  if (h->work_off == nullptr) {
+    const Plan &p = h->plan;
+    std::vector<int64_t> off(p.fronts.size());
+    int64_t acc = 0;
+    for (size_t k = 0; k < p.fronts.size(); ++k) {
+      off[k] = acc;
+      acc += int64_t(p.fronts[k].f) * kSolveRhs;
+    }
+    h->work_off = h->upload(off);
+    h->work = h->alloc<double>(size_t(std::max<int64_t>(acc, 1)));
+  }
+  if (h->work_rhs < nrhs) {
+    h->yf = h->alloc<float>(size_t(h->plan.n) * nrhs);
+    h->work_rhs = nrhs;
+  }
+}
+
+// y (S space, type T, ld n) <- S^{-1} y with the current factors
+template <typename T>
+void solve_S_T(h2sp_handle *h, T *y, int nrhs) {
+  const Plan &p = h->plan;
+  T *fronts = static_cast<T *>(h->fronts);
+  T *work = static_cast<T *>(h->work);
+  for (int r0 = 0; r0 < nrhs; r0 += kSolveRhs) {
+    const int nr = std::min(kSolveRhs, nrhs - r0);
+    T *yr = y + int64_t(r0) * p.n;
+    for (const FrontLevel &L : h->flev)
+      ck(launch_solve_fwd_level_impl<T>(h->fr, L.lo, L.hi - L.lo, L.max_s, L.max_f, fronts, h->perm, h->fidx, yr,
+                                        p.n, nr, work, h->work_off, h->stream));
+    for (int i = int(h->flev.size()) - 1; i >= 0; --i) {
+      const FrontLevel &L = h->flev[i];
+      ck(launch_solve_bwd_level_impl<T>(h->fr, L.lo, L.hi - L.lo, L.max_s, L.max_f, fronts, h->fidx, yr, p.n, nr,
+                                        work, h->work_off, h->stream));
+    }
+  }
+}
+
+// in-place S^{-1} on an FP64 S-space vector (ld n)
+void solve_S(h2sp_handle *h, double *y, int nrhs) {
+  ensure_work(h, nrhs);
+  const int64_t n = h->plan.n;
+  if (h->prec == H2SP_FP64) {
+    solve_S_T<double>(h, y, nrhs);
+  } else {
+    ck(launch_cast_d2f(y, n, h->yf, n, n, nrhs, h->stream));
+    solve_S_T<float>(h, h->yf, nrhs);
+    ck(launch_cast_f2d(h->yf, n, y, n, n, nrhs, h->stream));
+  }
+}
+
+// d = V S^{-1} U^T r   (the direct solve of Eq. sp0)
+void precond(h2sp_handle *h, const double *r, int64_t ldr, double *d, int64_t ldd, int nrhs) {
+  const int64_t n = h->plan.n;
+  apply_T(h, false, r, ldr, h->vecS, n, nrhs);
+  solve_S(h, h->vecS, nrhs);
+  apply_N(h, true, h->vecS, n, d, ldd, nrhs);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *h2sp_status_string(int32_t st) {
+  switch (st) {
+    case H2SP_OK: return "ok";
+    case H2SP_EINVAL: return "invalid argument or descriptor";
+    case H2SP_ENOMEM: return "out of device memory";
+    case H2SP_ECUDA: return "CUDA error";
+    case H2SP_ESINGULAR: return "singular pivot block";
+    case H2SP_ESTATE: return "call out of order";
+    case H2SP_ENOCONV: return "no convergence";
+    case H2SP_ETIMEOUT: return "device wait timed out";
+    case H2SP_EUNSUPPORTED: return "unsupported size";
+    default: return "unknown status";
+  }
+}
+
+const char *h2sp_last_cuda_error(void) { return g_cuda_err.c_str(); }
+
+int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream stream, h2sp_handle **out) {
+  (void)opts;
+  if (!out) return H2SP_EINVAL;
+  *out = nullptr;
+  h2sp_handle *h = new (std::nothrow) h2sp_handle();
+  if (!h) return H2SP_ENOMEM;
+  std::string err;
+  auto t0 = std::chrono::steady_clock::now();
+  int st = build_plan(desc, h->plan, err);
+  h->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (st != H2SP_OK) {
+    g_cuda_err = err;
+    delete h;
+    return st;
+  }
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->leaf_basis = desc->leaf_basis;
+  h->transfer = desc->transfer;
+  h->coupling = desc->coupling;
+  h->near_block = desc->near_block;
+  h->col_leaf_basis = desc->col_leaf_basis;
+  h->col_transfer = desc->col_transfer;
+  const Plan &p = h->plan;
+  cudaStream_t s = h->stream;
+  try {
+    init_pool_once();
+    // ---- owned buffers ----
+    h->Q = h->alloc<double>(size_t(p.q_elems));
+    h->Rr = h->alloc<double>(size_t(p.rr_elems));
+    if (p.sym) {
+      h->Qc = h->Q;
+      h->Rrc = h->Rr;
+    } else {
+      h->Qc = h->alloc<double>(size_t(p.q_elems));
+      h->Rrc = h->alloc<double>(size_t(p.rr_elems));
+    }
+    h->S = h->alloc<double>(size_t(p.s_elems));
+    ck(cudaMemsetAsync(h->S, 0, sizeof(double) * size_t(std::max<int64_t>(p.s_elems, 1)), s));
+    const int L = p.lstop;
+    h->Cbuf.assign(L + 1, nullptr);
+    h->RPbuf.assign(L + 1, nullptr);
+    h->CPbuf.assign(L + 1, nullptr);
+    for (int l = 1; l < L; ++l) {
+      h->Cbuf[l] = h->alloc<double>(size_t(p.c_elems[l]));
+      h->RPbuf[l] = h->alloc<double>(size_t(p.rp_elems[l]));
+      h->CPbuf[l] = h->alloc<double>(size_t(p.cp_elems[l]));
+      ck(cudaMemsetAsync(h->Cbuf[l], 0, sizeof(double) * size_t(std::max<int64_t>(p.c_elems[l], 1)), s));
+      ck(cudaMemsetAsync(h->RPbuf[l], 0, sizeof(double) * size_t(std::max<int64_t>(p.rp_elems[l], 1)), s));
+      ck(cudaMemsetAsync(h->CPbuf[l], 0, sizeof(double) * size_t(std::max<int64_t>(p.cp_elems[l], 1)), s));
+    }
+    // ---- per-level work items ----
+    const int nlw = int(p.lw.size());
+    h->lv.assign(std::max(nlw, 1), LevelDev());
+    int max_rank = 1;
+    for (int t = 0; t < p.ncl; ++t) max_rank = std::max(max_rank, p.rank[t]);
+    for (int l = 0; l < nlw; ++l) {
+      const LevelWork &w = p.lw[l];
+      LevelDev &d = h->lv[l];
+      d.q = h->upload(w.q);
+      d.nq = int(w.q.size());
+      d.w = h->upload(w.w);
+      d.nw = int(w.w.size());
+      d.c = h->upload(w.c);
+      d.nc = int(w.c.size());
+      d.x = h->upload(w.x);
+      d.nx = int(w.x.size());
+      if (!p.sym) {
+        d.qc = h->upload(w.qc);
+        d.wc = h->upload(w.wc);
+      }
+      if (l >= 1) {
+        d.W = h->alloc<double>(size_t(w.w_elems));
+        if (!p.sym) d.Wc = h->alloc<double>(size_t(w.wc_elems));
+      }
+      std::vector<double *> sb = {const_cast<double *>(h->near_block), l < L ? h->Cbuf[l] : nullptr,
+                                  l < L ? h->RPbuf[l] : nullptr, l < L ? h->CPbuf[l] : nullptr};
+      std::vector<double *> db = {h->S, l + 1 < L ? h->Cbuf[l + 1] : nullptr, l + 1 < L ? h->RPbuf[l + 1] : nullptr,
+                                  l + 1 < L ? h->CPbuf[l + 1] : nullptr};
+      d.src_base = h->upload(sb);
+      d.dst_base = h->upload(db);
+    }
+    // ---- sparsification kernels, level by level ----
+    for (int l = 0; l < nlw; ++l) {
+      const LevelWork &w = p.lw[l];
+      LevelDev &d = h->lv[l];
+      if (l < L) {
+        if (l >= 1) {
+          ck(launch_stack_w(d.w, d.nw, h->Rr, h->transfer, d.W, s));
+          if (!p.sym) ck(launch_stack_w(d.wc, d.nw, h->Rrc, h->col_transfer, d.Wc, s));
+        }
+        ck(launch_householder(d.q, d.nq, h->leaf_basis, d.W, h->Q, h->Rr, std::max(w.max_m, 1), std::max(w.max_k, 1),
+                              s));
+        if (!p.sym)
+          ck(launch_householder(d.qc, d.nq, h->col_leaf_basis, d.Wc, h->Qc, h->Rrc, std::max(w.max_m, 1),
+                                std::max(w.max_k, 1), s));
+        ck(launch_coupling(d.c, d.nc, h->Rr, h->Rrc, h->coupling, d.dst_base, max_rank, s));
+      }
+      ck(launch_transform(d.x, d.nx, const_cast<const double *const *>(d.src_base), h->Q, h->Qc, d.dst_base, s));
+    }
+    // ---- apply items ----
+    {
+      int64_t width = 0;
+      for (int l = 0; l <= L; ++l) {
+        int64_t wl = 0;
+        for (int t = p.level_ptr[p.D - l]; t < p.level_ptr[p.D - l + 1]; ++t) wl += p.m[t];
+        width = std::max(width, wl);
+      }
+      h->max_width = width;
+      for (int l = 0; l < L; ++l) {
+        std::vector<ApItem> ap;
+        for (int t = p.level_ptr[p.D - l]; t < p.level_ptr[p.D - l + 1]; ++t) {
+          if (p.m[t] == 0) continue;
+          ApItem a{};
+          a.q = p.q_off[t];
+          a.m = int32_t(p.m[t]);
+          a.kp = int32_t(p.kp[t]);
+          a.xin = p.xoff[t];
+          a.yout = p.d[t] > 0 ? p.node_off[p.node_of[t]] : -1;
+          a.xout = p.kp[t] > 0 ? p.xoff[p.parent[t]] + p.off[t] : -1;
+          ap.push_back(a);
+        }
+        h->lv[l].ap = h->upload(ap);
+        h->lv[l].nap = int(ap.size());
+      }
+      std::vector<int64_t> ts, td;
+      std::vector<int32_t> tl;
+      for (int t = p.level_ptr[p.D - L]; t < p.level_ptr[p.D - L + 1]; ++t)
+        if (p.m[t] > 0) {
+          ts.push_back(L == 0 ? p.h_begin[t] : p.xoff[t]);
+          td.push_back(p.node_off[p.node_of[t]]);
+          tl.push_back(int32_t(p.m[t]));
+        }
+      h->top_src = h->upload(ts);
+      h->top_dst = h->upload(td);
+      h->top_len = h->upload(tl);
+      h->ntop = int(ts.size());
+    }
+    // ---- S structure, H^2 structure ----
+    h->brow_ptr = h->upload(p.brow_ptr);
+    h->bcol = h->upload(p.bcol);
+    h->val_off = h->upload(p.val_off);
+    h->node_off = h->upload(p.node_off);
+    {
+      H2Dev &g = h->h2;
+      g.begin = h->upload(p.h_begin);
+      g.size = h->upload(p.h_size);
+      g.rank = h->upload(p.rank);
+      g.parent = h->upload(p.parent);
+      g.leaf_basis_off = h->upload(p.leaf_basis_off);
+      g.transfer_off = h->upload(p.transfer_off);
+      g.coupling_off = h->upload(p.coupling_off);
+      g.near_off = h->upload(p.near_off);
+      g.col_leaf_basis_off = p.sym ? nullptr : h->upload(p.col_leaf_basis_off);
+      g.col_transfer_off = p.sym ? nullptr : h->upload(p.col_transfer_off);
+      g.far_ptr = h->upload(p.far_ptr);
+      g.near_ptr = h->upload(p.near_ptr);
+      g.far_col = h->upload(p.far_col);
+      g.near_col = h->upload(p.near_col);
+      g.xh_off = h->upload(p.xh_off);
+      g.leaf_basis = h->leaf_basis;
+      g.transfer = h->transfer;
+      g.coupling = h->coupling;
+      g.near_block = h->near_block;
+      g.col_leaf_basis = h->col_leaf_basis;
+      g.col_transfer = h->col_transfer;
+      g.leaf0 = p.level_ptr[p.D];
+      std::vector<int32_t> cs(p.ncl, 0), cc(p.ncl, 0);
+      for (int c = p.ncl - 1; c >= 1; --c) {
+        cs[p.parent[c]] = c;
+        cc[p.parent[c]]++;
+      }
+      h->child_start = h->upload(cs);
+      h->child_cnt = h->upload(cc);
+      h->xh = h->alloc<double>(size_t(std::max<int64_t>(p.xh_elems, 1)) * 16);
+      h->yh = h->alloc<double>(size_t(std::max<int64_t>(p.xh_elems, 1)) * 16);
+      h->norms = h->alloc<double>(64);
+    }
+    // ---- symbolic factorization uploads ----
+    {
+      std::vector<FrontDev> fd(p.fronts.size());
+      for (size_t k = 0; k < p.fronts.size(); ++k) {
+        const Front &F = p.fronts[k];
+        fd[k] = FrontDev{F.off, F.piv_off, F.idx_off, F.map_off, F.s, F.b, F.f, F.parent};
+        h->max_s_all = std::max(h->max_s_all, F.s);
+      }
+      h->fr = h->upload(fd);
+      h->fidx = h->upload(p.front_idx);
+      h->fmap = h->upload(p.front_map);
+      h->asm_items = h->upload(p.assemble);
+      for (size_t i = 0; i + 1 < p.front_level_ptr.size(); ++i) {
+        FrontLevel fl{p.front_level_ptr[i], p.front_level_ptr[i + 1], 0, 0, 0};
+        for (int k = fl.lo; k < fl.hi; ++k) {
+          fl.max_s = std::max(fl.max_s, p.fronts[k].s);
+          fl.max_f = std::max(fl.max_f, p.fronts[k].f);
+          fl.max_b = std::max(fl.max_b, p.fronts[k].b);
+        }
+        h->flev.push_back(fl);
+      }
+    }
+    ck(cudaGetLastError());
+  } catch (const CudaFail &f) {
+    h->release();
+    delete h;
+    return status_of(f.e);
+  } catch (const std::bad_alloc &) {
+    h->release();
+    delete h;
+    return H2SP_ENOMEM;
+  }
+  h->device_ready = true;
+  *out = h;
+  return H2SP_OK;
+}
+
+int h2sp_analyze(const h2sp_h2_desc *desc, h2sp_handle **out) {
+  if (!out) return H2SP_EINVAL;
+  *out = nullptr;
+  h2sp_handle *h = new (std::nothrow) h2sp_handle();
+  if (!h) return H2SP_ENOMEM;
+  std::string err;
+  auto t0 = std::chrono::steady_clock::now();
+  int st = build_plan(desc, h->plan, err, false);
+  h->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (st != H2SP_OK) {
+    g_cuda_err = err;
+    delete h;
+    return st;
+  }
+  *out = h;
+  return H2SP_OK;
+}
+
+int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
+  if (!h) return H2SP_EINVAL;
+  if (!h->device_ready) return H2SP_ESTATE;
+  if (prec != H2SP_FP64 && prec != H2SP_FP32) return H2SP_EINVAL;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  const Plan &p = h->plan;
+  cudaStream_t s = h->stream;
+  try {
+    const size_t esz = prec == H2SP_FP64 ? sizeof(double) : sizeof(float);
+    if (h->fronts == nullptr) {
+      // sized for FP64 so that a later factorization in either precision reuses it
+      h->fronts = h->alloc<double>(size_t(std::max<int64_t>(p.front_elems, 1)));
+      h->piv = h->alloc<int32_t>(size_t(std::max<int64_t>(p.piv_elems, 1)));
+      h->perm = h->alloc<int32_t>(size_t(std::max<int64_t>(p.piv_elems, 1)));
+      size_t maxn = 1;
+      for (const FrontLevel &L : h->flev) maxn = std::max<size_t>(maxn, size_t(L.hi - L.lo));
+      h->swaps = h->alloc<int32_t>(maxn * (1 + 2 * kMaxSwapRows));
+      h->err = h->alloc<int>(1);
+    }
+    h->prec = -1;
+    ck(cudaMemsetAsync(h->fronts, 0, size_t(std::max<int64_t>(p.front_elems, 1)) * esz, s));
+    ck(cudaMemsetAsync(h->err, 0, sizeof(int), s));
+    const int64_t na = int64_t(p.assemble.size());
+    if (prec == H2SP_FP64) {
+      double *F = static_cast<double *>(h->fronts);
+      ck(launch_assemble<double>(h->asm_items, na, h->S, F, s));
+      for (const FrontLevel &L : h->flev) {
+        ck(launch_lu_level<double>(h->fr + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv, h->swaps, h->err, s));
+        ck(launch_extend_add_impl<double>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s));
+      }
+      ck(launch_make_perm<double>(h->fr, int(p.fronts.size()), h->max_s_all, h->piv, h->perm, s));
+    } else {
+      float *F = static_cast<float *>(h->fronts);
+      ck(launch_assemble<float>(h->asm_items, na, h->S, F, s));
+      for (const FrontLevel &L : h->flev) {
+        ck(launch_lu_level<float>(h->fr + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv, h->swaps, h->err, s));
+        ck(launch_extend_add_impl<float>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s));
+      }
+      ck(launch_make_perm<float>(h->fr, int(p.fronts.size()), h->max_s_all, h->piv, h->perm, s));
+    }
+    int herr = 0;
+    ck(cudaMemcpyAsync(&herr, h->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    if (herr != 0) return H2SP_ESINGULAR;
+    h->prec = prec;
+  } catch (const CudaFail &f) {
+    return status_of(f.e);
+  }
+  return H2SP_OK;
+}
+
+int h2sp_apply(h2sp_handle *h, int32_t op, int32_t nrhs, const double *in, int64_t ldin, double *out, int64_t ldout,
+               h2sp_stream stream) {
+  if (!h || !in || !out || nrhs <= 0) return H2SP_EINVAL;
+  if (!h->device_ready) return H2SP_ESTATE;
+  const Plan &p = h->plan;
+  if (ldin < p.n || ldout < p.n) return H2SP_EINVAL;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  try {
+    ensure_vectors(h, nrhs);
+    switch (op) {
+      case H2SP_OP_UT: apply_T(h, false, in, ldin, out, ldout, nrhs); break;
+      case H2SP_OP_VT: apply_T(h, true, in, ldin, out, ldout, nrhs); break;
+      case H2SP_OP_U: apply_N(h, false, in, ldin, out, ldout, nrhs); break;
+      case H2SP_OP_V: apply_N(h, true, in, ldin, out, ldout, nrhs); break;
+      case H2SP_OP_S:
+        ck(launch_spmv(h->brow_ptr, h->bcol, h->val_off, h->node_off, int(p.node_size.size()), h->S, in, ldin, out,
+                       ldout, nrhs, h->stream));
+        break;
+      case H2SP_OP_H2: h2_matvec(h, in, ldin, out, ldout, nrhs); break;
+      case H2SP_OP_SINV:
+        if (h->prec < 0) return H2SP_ESTATE;
+        for (int r = 0; r < nrhs; ++r)
+          ck(cudaMemcpyAsync(h->vecS + r * p.n, in + r * ldin, sizeof(double) * p.n, cudaMemcpyDeviceToDevice,
+                             h->stream));
+        solve_S(h, h->vecS, nrhs);
+        for (int r = 0; r < nrhs; ++r)
+          ck(cudaMemcpyAsync(out + r * ldout, h->vecS + r * p.n, sizeof(double) * p.n, cudaMemcpyDeviceToDevice,
+                             h->stream));
+        break;
+      default: return H2SP_EINVAL;
+    }
+    ck(cudaGetLastError());
+  } catch (const CudaFail &f) {
+    return status_of(f.e);
+  }
+  return H2SP_OK;
+}
+
+int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *o, int32_t nrhs, const double *b, int64_t ldb, double *x,
+               int64_t ldx, h2sp_solve_info *info, h2sp_stream stream) {
+  if (!h || !o || !b || !x || nrhs <= 0 || nrhs > 64) return H2SP_EINVAL;
+  if (!h->device_ready) return H2SP_ESTATE;
+  const Plan &p = h->plan;
+  if (ldb < p.n || ldx < p.n) return H2SP_EINVAL;
+  if (o->mode != H2SP_DIRECT && o->mode != H2SP_IR) return H2SP_EUNSUPPORTED;
+  if (h->prec < 0) return H2SP_ESTATE;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  cudaStream_t s = h->stream;
+  if (info) {
+    info->iters = 0;
+    info->rel_residual = -1.0;
+    info->status = H2SP_OK;
+  }
+  try {
+    ensure_vectors(h, nrhs);
+    ensure_work(h, nrhs);
+    if (o->mode == H2SP_DIRECT) {
+      precond(h, b, ldb, x, ldx, nrhs);
+      ck(cudaGetLastError());
+      return H2SP_OK;
+    }
+    // iterative refinement on the FP64 H^2 residual (§5.5)
+    const int64_t n = p.n;
+    std::vector<double> bn2(nrhs), rn2(nrhs);
+    ck(launch_colnorm2(b, ldb, n, nrhs, h->norms, s));
+    ck(cudaMemcpyAsync(bn2.data(), h->norms, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    const int maxit = o->maxit > 0 ? o->maxit : 50;
+    double res = INFINITY;
+    int it = 0;
+    precond(h, b, ldb, x, ldx, nrhs);  // x_0 = M^-1 b
+    for (;;) {
+      h2_matvec(h, x, ldx, h->vecT, n, nrhs);
+      ck(launch_residual(b, ldb, h->vecT, n, h->vecR, n, n, nrhs, h->norms, s));
+      ck(cudaMemcpyAsync(rn2.data(), h->norms, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+      ck(cudaStreamSynchronize(s));
+      res = 0.0;
+      for (int c = 0; c < nrhs; ++c) res = std::max(res, std::sqrt(rn2[c] / std::max(bn2[c], 1e-300)));
+      if (!(res > o->tol) || it >= maxit) break;
+      precond(h, h->vecR, n, h->vecT, n, nrhs);
+      ck(launch_axpy(h->vecT, n, x, ldx, n, nrhs, s));
+      ++it;
+    }
+    if (info) {
+      info->iters = it;
+      info->rel_residual = res;
+      info->status = (res <= o->tol) ? H2SP_OK : H2SP_ENOCONV;
+    }
+    if (!(res <= o->tol)) return H2SP_ENOCONV;
+  } catch (const CudaFail &f) {
+    return status_of(f.e);
+  }
+  return H2SP_OK;
+}
+
+int h2sp_export_S(h2sp_handle *h, int64_t *node_size, int64_t *brow_ptr, int32_t *bcol_idx, int64_t *val_off,
+                  double *vals, h2sp_stream stream) {
+  if (!h) return H2SP_EINVAL;
+  const Plan &p = h->plan;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  if (node_size) std::copy(p.node_size.begin(), p.node_size.end(), node_size);
+  if (brow_ptr) std::copy(p.brow_ptr.begin(), p.brow_ptr.end(), brow_ptr);
+  if (bcol_idx) std::copy(p.bcol.begin(), p.bcol.end(), bcol_idx);
+  if (val_off) std::copy(p.val_off.begin(), p.val_off.end(), val_off);
+  if (!vals) return H2SP_OK;
+  if (!h->device_ready) return H2SP_ESTATE;
+  try {
+    if (vals) ck(cudaMemcpyAsync(vals, h->S, sizeof(double) * p.s_elems, cudaMemcpyDeviceToHost, h->stream));
+    ck(cudaStreamSynchronize(h->stream));
+  } catch (const CudaFail &f) {
+    return status_of(f.e);
+  }
+  return H2SP_OK;
+}
+
+int h2sp_export_Q(h2sp_handle *h, int32_t cluster, int32_t col, int64_t *m, double *q, h2sp_stream stream) {
+  if (!h || !m) return H2SP_EINVAL;
+  const Plan &p = h->plan;
+  if (cluster < 0 || cluster >= p.ncl) return H2SP_EINVAL;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  if (p.q_off[cluster] < 0) {
+    *m = 0;
+    return H2SP_OK;
+  }
+  *m = p.m[cluster];
+  if (q && !h->device_ready) return H2SP_ESTATE;
+  if (q) {
+    try {
+      ck(cudaMemcpyAsync(q, (col ? h->Qc : h->Q) + p.q_off[cluster], sizeof(double) * p.m[cluster] * p.m[cluster],
+                         cudaMemcpyDeviceToHost, h->stream));
+      ck(cudaStreamSynchronize(h->stream));
+    } catch (const CudaFail &f) {
+      return status_of(f.e);
+    }
+  }
+  return H2SP_OK;
+}
+
+int h2sp_export_structure(h2sp_handle *h, int32_t *node_level, int32_t *node_cluster, int32_t *closure,
+                          int32_t *order, int32_t *sn_ptr, int32_t *bnd_ptr, int32_t *bnd, int64_t *nbnd) {
+  if (!h) return H2SP_EINVAL;
+  const Plan &p = h->plan;
+  if (node_level) std::copy(p.node_level.begin(), p.node_level.end(), node_level);
+  if (node_cluster) std::copy(p.node_cluster.begin(), p.node_cluster.end(), node_cluster);
+  if (closure) std::copy(p.closure.begin(), p.closure.end(), closure);
+  if (order) std::copy(p.order.begin(), p.order.end(), order);
+  if (sn_ptr) std::copy(p.sn_ptr.begin(), p.sn_ptr.end(), sn_ptr);
+  if (bnd_ptr) std::copy(p.bnd_ptr.begin(), p.bnd_ptr.end(), bnd_ptr);
+  if (bnd) std::copy(p.bnd.begin(), p.bnd.end(), bnd);
+  if (nbnd) *nbnd = int64_t(p.bnd.size());
+  return H2SP_OK;
+}
+
+int h2sp_query(const h2sp_handle *h, h2sp_stats *st) {
+  if (!h || !st) return H2SP_EINVAL;
+  const Plan &p = h->plan;
+  std::memset(st, 0, sizeof(*st));
+  st->n = p.n;
+  st->depth = p.D;
+  st->lstop = p.lstop;
+  st->nnodes = int32_t(p.node_size.size());
+  st->nnzb = int64_t(p.bcol.size());
+  st->nnz = p.s_elems;
+  st->nsupernodes = int32_t(p.fronts.size());
+  st->nfront_levels = int32_t(h->flev.size());
+  st->max_front = p.max_front;
+  st->front_elems = p.front_elems;
+  st->factor_flops = p.factor_flops;
+  st->sparsify_flops = p.sparsify_flops;
+  st->factor_prec = h->prec;
+  st->plan_seconds = h->plan_seconds;
+  return H2SP_OK;
+}
+
+void h2sp_destroy(h2sp_handle *h) {
+  if (!h) return;
+  h->release();
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,408 @@
+// Applies of U^T and V (the products of Eq. main_uv used in Eq. sp0), the
+// VBR product with S, the FP64 H^2 matrix-vector product of Definition 4.9,
+// and the small vector kernels of the iterative solves (§5.5).
+#include <algorithm>
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace h2sp {
+namespace {
+
+constexpr int kRhs = 16;  // right-hand sides handled per kernel pass
+
+// Q^T applied to X_l(t); basis rows go to the next level, non-basis rows to S space
+__global__ void __launch_bounds__(64) k_apply_qt(const ApItem *__restrict__ items, const double *__restrict__ Q,
+                                                 const double *__restrict__ x, int64_t ldx, double *__restrict__ ys,
+                                                 int64_t ldys, double *__restrict__ xn, int64_t ldxn, int nrhs) {
+  const ApItem it = items[blockIdx.x];
+  __shared__ double sx[kMaxBlock * kRhs];
+  const int m = it.m;
+  for (int e = threadIdx.x; e < m * nrhs; e += blockDim.x) {
+    const int j = e % m, r = e / m;
+    sx[j + r * kMaxBlock] = x[it.xin + j + r * ldx];
+  }
+  __syncthreads();
+  const double *Qt = Q + it.q;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double acc[kRhs];
+#pragma unroll
+    for (int r = 0; r < kRhs; ++r) acc[r] = 0.0;
+    for (int j = 0; j < m; ++j) {
+      const double q = Qt[j + int64_t(i) * m];
+#pragma unroll
+      for (int r = 0; r < kRhs; ++r)
+        if (r < nrhs) acc[r] += q * sx[j + r * kMaxBlock];
+    }
+    if (i < it.kp) {
+      if (it.xout >= 0)
+        for (int r = 0; r < nrhs; ++r) xn[it.xout + i + r * ldxn] = acc[r];
+    } else {
+      for (int r = 0; r < nrhs; ++r) ys[it.yout + (i - it.kp) + r * ldys] = acc[r];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(64) k_apply_q(const ApItem *__restrict__ items, const double *__restrict__ Q,
+                                                const double *__restrict__ xn, int64_t ldxn,
+                                                const double *__restrict__ ys, int64_t ldys, double *__restrict__ x,
+                                                int64_t ldx, int nrhs) {
+  const ApItem it = items[blockIdx.x];
+  __shared__ double sz[kMaxBlock * kRhs];
+  const int m = it.m;
+  for (int e = threadIdx.x; e < m * nrhs; e += blockDim.x) {
+    const int j = e % m, r = e / m;
+    double v = 0.0;
+    if (j < it.kp) {
+      if (it.xout >= 0) v = xn[it.xout + j + r * ldxn];
+    } else {
+      v = ys[it.yout + (j - it.kp) + r * ldys];
+    }
+    sz[j + r * kMaxBlock] = v;
+  }
+  __syncthreads();
+  const double *Qt = Q + it.q;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double acc[kRhs];
+#pragma unroll
+    for (int r = 0; r < kRhs; ++r) acc[r] = 0.0;
+    for (int j = 0; j < m; ++j) {
+      const double q = Qt[i + int64_t(j) * m];
+#pragma unroll
+      for (int r = 0; r < kRhs; ++r)
+        if (r < nrhs) acc[r] += q * sz[j + r * kMaxBlock];
+    }
+    for (int r = 0; r < nrhs; ++r) x[it.xin + i + r * ldx] = acc[r];
+  }
+}
+
+__global__ void k_copy_rows(const int64_t *__restrict__ src_row, const int64_t *__restrict__ dst_row,
+                            const int32_t *__restrict__ len, const double *__restrict__ src, int64_t lds,
+                            double *__restrict__ dst, int64_t ldd, int nrhs) {
+  const int64_t s0 = src_row[blockIdx.x], d0 = dst_row[blockIdx.x];
+  const int n = len[blockIdx.x];
+  for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) {
+    const int i = e % n, r = e / n;
+    dst[d0 + i + r * ldd] = src[s0 + i + r * lds];
+  }
+}
+
+__global__ void __launch_bounds__(128) k_spmv(const int64_t *__restrict__ brow_ptr, const int32_t *__restrict__ bcol,
+                                              const int64_t *__restrict__ val_off, const int64_t *__restrict__ node_off,
+                                              const double *__restrict__ vals, const double *__restrict__ x, int64_t ldx,
+                                              double *__restrict__ y, int64_t ldy, int nrhs) {
+  const int i = blockIdx.x;
+  const int64_t r0 = node_off[i];
+  const int di = int(node_off[i + 1] - r0);
+  __shared__ double sx[64 * kRhs];
+  for (int rb = 0; rb < di; rb += blockDim.x) {
+    const int row = rb + threadIdx.x;
+    double acc[kRhs];
+#pragma unroll
+    for (int r = 0; r < kRhs; ++r) acc[r] = 0.0;
+    for (int64_t z = brow_ptr[i]; z < brow_ptr[i + 1]; ++z) {
+      const int j = bcol[z];
+      const int64_t c0 = node_off[j];
+      const int dj = int(node_off[j + 1] - c0);
+      const double *blk = vals + val_off[z];
+      for (int cb = 0; cb < dj; cb += 64) {
+        const int nc = min(64, dj - cb);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nc * nrhs; e += blockDim.x) {
+          const int c = e % nc, r = e / nc;
+          sx[c + r * 64] = x[c0 + cb + c + r * ldx];
+        }
+        __syncthreads();
+        if (row < di)
+          for (int c = 0; c < nc; ++c) {
+            const double a = blk[row + int64_t(cb + c) * di];
+#pragma unroll
+            for (int r = 0; r < kRhs; ++r)
+              if (r < nrhs) acc[r] += a * sx[c + r * 64];
+          }
+      }
+    }
+    if (row < di)
+      for (int r = 0; r < nrhs; ++r) y[r0 + row + r * ldy] = acc[r];
+  }
+}
+
+// ---------------- H^2 product (Definition 4.9) ----------------
+// x^_t = E_t^T x_t for the leaves
+__global__ void __launch_bounds__(64) k_h2_leaf_up(H2Dev h, const double *__restrict__ x, int64_t ldx,
+                                                   double *__restrict__ xh, int64_t ldh, int nrhs) {
+  const int t = h.leaf0 + blockIdx.x;
+  const int n = int(h.size[t]), k = h.rank[t];
+  const int64_t b0 = h.begin[t];
+  const double *E = h.col_leaf_basis ? h.col_leaf_basis + h.col_leaf_basis_off[blockIdx.x]
+                                     : h.leaf_basis + h.leaf_basis_off[blockIdx.x];
+  __shared__ double sx[kMaxBlock * kRhs];
+  for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) {
+    const int j = e % n, r = e / n;
+    sx[j + r * kMaxBlock] = x[b0 + j + r * ldx];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    double acc[kRhs];
+#pragma unroll
+    for (int r = 0; r < kRhs; ++r) acc[r] = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const double e = E[j + int64_t(i) * n];
+#pragma unroll
+      for (int r = 0; r < kRhs; ++r)
+        if (r < nrhs) acc[r] += e * sx[j + r * kMaxBlock];
+    }
+    for (int r = 0; r < nrhs; ++r) xh[h.xh_off[t] + i + r * ldh] = acc[r];
+  }
+}
+
+// x^_p = sum_c T'_c^T x^_c over the sons of p (clusters [lo, hi) of one depth)
+__global__ void __launch_bounds__(64) k_h2_up(H2Dev h, const int32_t *__restrict__ child_start,
+                                              const int32_t *__restrict__ child_cnt, int lo, double *__restrict__ xh,
+                                              int64_t ldh, int nrhs) {
+  const int p = lo + blockIdx.x;
+  const int kp = h.rank[p];
+  for (int i = threadIdx.x; i < kp; i += blockDim.x) {
+    double acc[kRhs];
+#pragma unroll
+    for (int r = 0; r < kRhs; ++r) acc[r] = 0.0;
+    for (int c = child_start[p]; c < child_start[p] + child_cnt[p]; ++c) {
+      const int kc = h.rank[c];
+      const double *T = h.col_transfer ? h.col_transfer + h.col_transfer_off[c] : h.transfer + h.transfer_off[c];
+      const double *xc = xh + h.xh_off[c];
+      for (int j = 0; j < kc; ++j) {
+        const double tv = T[j + int64_t(i) * kc];
+#pragma unroll
+        for (int r = 0; r < kRhs; ++r)
+          if (r < nrhs) acc[r] += tv * xc[j + r * ldh];
+      }
+    }
+    for (int r = 0; r < nrhs; ++r) xh[h.xh_off[p] + i + r * ldh] = acc[r];
+  }
+}
+
+// y^_t = sum_{s in Far(t)} D_ts x^_s
+__global__ void __launch_bounds__(64) k_h2_couple(H2Dev h, const double *__restrict__ xh, double *__restrict__ yh,
+                                                  int64_t ldh, int nrhs) {
+  const int t = blockIdx.x;
+  const int kt = h.rank[t];
+  for (int i = threadIdx.x; i < kt; i += blockDim.x) {
+    double acc[kRhs];
+#pragma unroll
+    for (int r = 0; r < kRhs; ++r) acc[r] = 0.0;
+    for (int64_t z = h.far_ptr[t]; z < h.far_ptr[t + 1]; ++z) {
+      const int s = h.far_col[z];
+      const int ks = h.rank[s];
+      const double *D = h.coupling + h.coupling_off[z];
+      const double *xs = xh + h.xh_off[s];
+      for (int j = 0; j < ks; ++j) {
+        const double dv = D[i + int64_t(j) * kt];
+#pragma unroll
+        for (int r = 0; r < kRhs; ++r)
+          if (r < nrhs) acc[r] += dv * xs[j + r * ldh];
+      }
+    }
+    for (int r = 0; r < nrhs; ++r) yh[h.xh_off[t] + i + r * ldh] = acc[r];
+  }
+}
+
+// y^_c += T_c y^_parent for the clusters [lo, hi) of one depth
+__global__ void __launch_bounds__(64) k_h2_down(H2Dev h, int lo, double *__restrict__ yh, int64_t ldh, int nrhs) {
+  const int c = lo + blockIdx.x;
+  const int p = h.parent[c];
+  const int kc = h.rank[c], kp = h.rank[p];
+  const double *T = h.transfer + h.transfer_off[c];
+  const double *yp = yh + h.xh_off[p];
+  for (int i = threadIdx.x; i < kc; i += blockDim.x) {
+    for (int r = 0; r < nrhs; ++r) {
+      double acc = 0.0;
+      for (int j = 0; j < kp; ++j) acc += T[i + int64_t(j) * kc] * yp[j + r * ldh];
+      yh[h.xh_off[c] + i + r * ldh] += acc;
+    }
+  }
+}
+
+// y_t = R_t y^_t + sum_{s near t} C_ts x_s
+__global__ void __launch_bounds__(64) k_h2_leaf_out(H2Dev h, const double *__restrict__ x, int64_t ldx,
+                                                    const double *__restrict__ yh, int64_t ldh, double *__restrict__ y,
+                                                    int64_t ldy, int nrhs) {
+  const int lf = blockIdx.x;
+  const int t = h.leaf0 + lf;
+  const int n = int(h.size[t]), k = h.rank[t];
+  const int64_t b0 = h.begin[t];
+  __shared__ double sx[kMaxBlock * kRhs];
+  double acc[kRhs];
+#pragma unroll
+  for (int r = 0; r < kRhs; ++r) acc[r] = 0.0;
+  const int i = threadIdx.x;
+  if (i < n) {
+    const double *R = h.leaf_basis + h.leaf_basis_off[lf];
+    const double *yt = yh + h.xh_off[t];
+    for (int j = 0; j < k; ++j) {
+      const double rv = R[i + int64_t(j) * n];
+#pragma unroll
+      for (int r = 0; r < kRhs; ++r)
+        if (r < nrhs) acc[r] += rv * yt[j + r * ldh];
+    }
+  }
+  for (int64_t z = h.near_ptr[lf]; z < h.near_ptr[lf + 1]; ++z) {
+    const int s = h.near_col[z];
+    const int ns = int(h.size[s]);
+    const int64_t bs = h.begin[s];
+    __syncthreads();
+    for (int e = threadIdx.x; e < ns * nrhs; e += blockDim.x) {
+      const int j = e % ns, r = e / ns;
+      sx[j + r * kMaxBlock] = x[bs + j + r * ldx];
+    }
+    __syncthreads();
+    if (i < n) {
+      const double *C = h.near_block + h.near_off[z];
+      for (int j = 0; j < ns; ++j) {
+        const double cv = C[i + int64_t(j) * n];
+#pragma unroll
+        for (int r = 0; r < kRhs; ++r)
+          if (r < nrhs) acc[r] += cv * sx[j + r * kMaxBlock];
+      }
+    }
+  }
+  if (i < n)
+    for (int r = 0; r < nrhs; ++r) y[b0 + i + r * ldy] = acc[r];
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(256) k_residual(const double *__restrict__ b, int64_t ldb, const double *__restrict__ y,
+                                                  int64_t ldy, double *__restrict__ r, int64_t ldr, int64_t n,
+                                                  double *__restrict__ norms2) {
+  const int c = blockIdx.y;
+  __shared__ double red[8];
+  double part = 0.0;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double v = b[i + c * ldb] - (y ? y[i + c * ldy] : 0.0);
+    if (r) r[i + c * ldr] = v;
+    part += v * v;
+  }
+  part = warp_sum(part);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[w];
+    atomicAdd(&norms2[c], t);
+  }
+}
+
+__global__ void k_axpy(const double *__restrict__ d, int64_t ldd, double *__restrict__ x, int64_t ldx, int64_t n) {
+  const int c = blockIdx.y;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    x[i + c * ldx] += d[i + c * ldd];
+}
+
+template <typename A, typename B>
+__global__ void k_cast(const A *__restrict__ a, int64_t lda, B *__restrict__ b, int64_t ldb, int64_t n) {
+  const int c = blockIdx.y;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    b[i + c * ldb] = B(a[i + c * lda]);
+}
+
+inline unsigned grid_for(int64_t n, int per = 256) {
+  return unsigned(std::max<int64_t>(1, std::min<int64_t>((n + per - 1) / per, 4 * 152)));
+}
+
+}  // namespace
+
+cudaError_t launch_apply_qt(const ApItem *items, int n, const double *Q, const double *x, int64_t ldx, double *ys,
+                            int64_t ldys, double *xn, int64_t ldxn, int nrhs, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  for (int r0 = 0; r0 < nrhs; r0 += kRhs)
+    k_apply_qt<<<n, 64, 0, s>>>(items, Q, x + r0 * ldx, ldx, ys + r0 * ldys, ldys, xn ? xn + r0 * ldxn : nullptr,
+                                ldxn, std::min(kRhs, nrhs - r0));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_q(const ApItem *items, int n, const double *Q, const double *xn, int64_t ldxn,
+                           const double *ys, int64_t ldys, double *x, int64_t ldx, int nrhs, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  for (int r0 = 0; r0 < nrhs; r0 += kRhs)
+    k_apply_q<<<n, 64, 0, s>>>(items, Q, xn ? xn + r0 * ldxn : nullptr, ldxn, ys + r0 * ldys, ldys, x + r0 * ldx, ldx,
+                               std::min(kRhs, nrhs - r0));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_rows(const int64_t *src_row, const int64_t *dst_row, const int32_t *len, int n,
+                             const double *src, int64_t lds, double *dst, int64_t ldd, int nrhs, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_copy_rows<<<n, 128, 0, s>>>(src_row, dst_row, len, src, lds, dst, ldd, nrhs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spmv(const int64_t *brow_ptr, const int32_t *bcol, const int64_t *val_off, const int64_t *node_off,
+                        int nnodes, const double *vals, const double *x, int64_t ldx, double *y, int64_t ldy, int nrhs,
+                        cudaStream_t s) {
+  if (nnodes == 0) return cudaSuccess;
+  for (int r0 = 0; r0 < nrhs; r0 += kRhs)
+    k_spmv<<<nnodes, 128, 0, s>>>(brow_ptr, bcol, val_off, node_off, vals, x + r0 * ldx, ldx, y + r0 * ldy, ldy,
+                                  std::min(kRhs, nrhs - r0));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_h2_matvec(const H2Dev &h, const int32_t *level_ptr_host, const int32_t *child_start,
+                             const int32_t *child_cnt, int depth, const double *x, int64_t ldx, double *y,
+                             int64_t ldy, int nrhs, double *xh, double *yh, int64_t ldh, cudaStream_t s) {
+  const int nleaf = level_ptr_host[depth + 1] - level_ptr_host[depth];
+  const int ncl = level_ptr_host[depth + 1];
+  for (int r0 = 0; r0 < nrhs; r0 += kRhs) {
+    const int nr = std::min(kRhs, nrhs - r0);
+    const double *xr = x + r0 * ldx;
+    double *yr = y + r0 * ldy;
+    k_h2_leaf_up<<<nleaf, 64, 0, s>>>(h, xr, ldx, xh, ldh, nr);
+    for (int d = depth - 1; d >= 0; --d) {
+      const int lo = level_ptr_host[d], hi = level_ptr_host[d + 1];
+      k_h2_up<<<hi - lo, 64, 0, s>>>(h, child_start, child_cnt, lo, xh, ldh, nr);
+    }
+    k_h2_couple<<<ncl, 64, 0, s>>>(h, xh, yh, ldh, nr);
+    for (int d = 1; d <= depth; ++d) {
+      const int lo = level_ptr_host[d], hi = level_ptr_host[d + 1];
+      k_h2_down<<<hi - lo, 64, 0, s>>>(h, lo, yh, ldh, nr);
+    }
+    k_h2_leaf_out<<<nleaf, 64, 0, s>>>(h, xr, ldx, yh, ldh, yr, ldy, nr);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const double *b, int64_t ldb, const double *y, int64_t ldy, double *r, int64_t ldr,
+                            int64_t n, int nrhs, double *norms2, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(norms2, 0, sizeof(double) * nrhs, s);
+  if (e != cudaSuccess) return e;
+  k_residual<<<dim3(grid_for(n), nrhs), 256, 0, s>>>(b, ldb, y, ldy, r, ldr, n, norms2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colnorm2(const double *x, int64_t ldx, int64_t n, int nrhs, double *norms2, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(norms2, 0, sizeof(double) * nrhs, s);
+  if (e != cudaSuccess) return e;
+  // ||x||^2 as the residual of x against zero
+  k_residual<<<dim3(grid_for(n), nrhs), 256, 0, s>>>(x, ldx, nullptr, 0, nullptr, 0, n, norms2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(const double *d, int64_t ldd, double *x, int64_t ldx, int64_t n, int nrhs, cudaStream_t s) {
+  k_axpy<<<dim3(grid_for(n), nrhs), 256, 0, s>>>(d, ldd, x, ldx, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast_d2f(const double *a, int64_t lda, float *b, int64_t ldb, int64_t n, int nrhs, cudaStream_t s) {
+  k_cast<double, float><<<dim3(grid_for(n), nrhs), 256, 0, s>>>(a, lda, b, ldb, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast_f2d(const float *a, int64_t lda, double *b, int64_t ldb, int64_t n, int nrhs, cudaStream_t s) {
+  k_cast<float, double><<<dim3(grid_for(n), nrhs), 256, 0, s>>>(a, lda, b, ldb, n);
+  return cudaGetLastError();
+}
+
+}  // namespace h2sp

@@ -1,0 +1,592 @@
+// Block LU of the sparse S and the triangular solves (multifrontal form).
+//
+// The paper factors S with a sparse direct solver (§5.3-5.4).  Here S is
+// eliminated supernode by supernode in the nested-dissection order built on
+// the host; each supernode owns a dense front
+//       F = [F11 F12; F21 F22]   (s + b rows: supernode rows, then boundary rows)
+// that receives its blocks of S and the contribution blocks of its children.
+// A front is factored by a right-looking blocked LU that stops after its s
+// supernode columns, with partial pivoting restricted to the supernode rows:
+//   panel      : columns [j0, j0+jb), rows [j0, f), pivots searched in [j0, s)
+//   swap+trsm  : the panel's row swaps on the other columns, U12 = L^-1 A12
+//   gemm       : trailing update A22 -= L21 U12
+// The trailing block left in F22 is the contribution block, added into the
+// parent front (extend-add).  All fronts of one elimination level (one depth
+// of the closure clusters) are processed by the same launches.
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace h2sp {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T tabs(T x) {
+  return x < T(0) ? -x : x;
+}
+
+template <typename T>
+__global__ void k_assemble(const AItem *__restrict__ items, const double *__restrict__ S, T *__restrict__ F) {
+  const AItem it = items[blockIdx.x];
+  const int n = it.rows * it.cols;
+  const double *src = S + it.src;
+  T *dst = F + it.dst;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int r = i % it.rows, c = i / it.rows;
+    dst[r + int64_t(c) * it.ld] = T(src[i]);
+  }
+}
+
+constexpr int kPanelThreads = 512;
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(kPanelThreads) k_panel(const FrontDev *__restrict__ fr, int j0, T *__restrict__ fronts,
+                                                         int32_t *__restrict__ piv, int32_t *__restrict__ swaps,
+                                                         int *__restrict__ err) {
+  const FrontDev F = fr[blockIdx.x];
+  if (j0 >= F.s) return;
+  const int jb = min(NB, F.s - j0);
+  T *A = fronts + F.off;
+  const int64_t ld = F.f;
+  __shared__ T urow[NB];
+  __shared__ T redv[kPanelThreads / 32];
+  __shared__ int redi[kPanelThreads / 32];
+  __shared__ int s_p;
+  __shared__ T s_pv;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  for (int j = 0; j < jb; ++j) {
+    const int col = j0 + j;
+    T *Acol = A + int64_t(col) * ld;
+    T bv = T(-1);
+    int bi = INT_MAX;
+    for (int r = col + tid; r < F.s; r += nt) {
+      const T v = tabs(Acol[r]);
+      if (v > bv) bv = v, bi = r;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) bv = ov, bi = oi;
+    }
+    if (lane == 0) redv[wid] = bv, redi[wid] = bi;
+    __syncthreads();
+    if (tid == 0) {
+      T v = redv[0];
+      int i = redi[0];
+      for (int w = 1; w < (nt >> 5); ++w)
+        if (redv[w] > v || (redv[w] == v && redi[w] < i)) v = redv[w], i = redi[w];
+      if (i == INT_MAX) {  // every candidate is NaN
+        i = col;
+        atomicOr(err, 2);
+      }
+      s_p = i;
+      piv[F.piv_off + col] = i;
+      const T pv = A[i + int64_t(col) * ld];
+      s_pv = pv;
+      if (pv == T(0)) atomicOr(err, 1);
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != col)
+      for (int c = j0 + tid; c < j0 + jb; c += nt) {
+        T *a = A + int64_t(c) * ld;
+        const T t = a[col];
+        a[col] = a[p];
+        a[p] = t;
+      }
+    __syncthreads();
+    for (int c = col + 1 + tid; c < j0 + jb; c += nt) urow[c - j0] = A[col + int64_t(c) * ld];
+    __syncthreads();
+    const T pv = s_pv;
+    if (pv != T(0)) {
+      const T inv = T(1) / pv;
+      for (int r = col + 1 + tid; r < F.f; r += nt) {
+        const T l = Acol[r] * inv;
+        Acol[r] = l;
+        for (int c = col + 1; c < j0 + jb; ++c) A[r + int64_t(c) * ld] -= l * urow[c - j0];
+      }
+    }
+    __syncthreads();
+  }
+  // net row movement of this panel: the swaps compose to new_row[r] = old_row[src[r]]
+  if (tid == 0) {
+    int32_t *sw = swaps + int64_t(blockIdx.x) * (1 + 2 * kMaxSwapRows);
+    int nr = 0;
+    int32_t *rows = sw + 1, *src = sw + 1 + kMaxSwapRows;
+    for (int j = 0; j < jb; ++j) {
+      const int a = j0 + j, b = piv[F.piv_off + a];
+      if (a == b) continue;
+      int ia = -1, ib = -1;
+      for (int q = 0; q < nr; ++q) {
+        if (rows[q] == a) ia = q;
+        if (rows[q] == b) ib = q;
+      }
+      if (ia < 0) rows[nr] = a, src[nr] = a, ia = nr++;
+      if (ib < 0) rows[nr] = b, src[nr] = b, ib = nr++;
+      const int32_t t = src[ia];
+      src[ia] = src[ib];
+      src[ib] = t;
+    }
+    sw[0] = nr;
+  }
+}
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) k_swap_trsm(const FrontDev *__restrict__ fr, int j0, T *__restrict__ fronts,
+                                                   const int32_t *__restrict__ swaps) {
+  const FrontDev F = fr[blockIdx.y];
+  if (j0 >= F.s) return;
+  const int jb = min(NB, F.s - j0);
+  T *A = fronts + F.off;
+  const int64_t ld = F.f;
+  __shared__ T L[NB * NB];
+  __shared__ int32_t srow[kMaxSwapRows], ssrc[kMaxSwapRows];
+  const int32_t *sw = swaps + int64_t(blockIdx.y) * (1 + 2 * kMaxSwapRows);
+  const int nsw = sw[0];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int i = tid; i < nsw; i += blockDim.x) srow[i] = sw[1 + i], ssrc[i] = sw[1 + kMaxSwapRows + i];
+  for (int i = tid; i < jb * jb; i += blockDim.x) {
+    const int r = i % jb, c = i / jb;
+    L[r + c * NB] = A[(j0 + r) + int64_t(j0 + c) * ld];
+  }
+  __syncthreads();
+  constexpr int kPer = (kMaxSwapRows + 31) / 32;
+  for (int c = blockIdx.x * 8 + wid; c < F.f; c += gridDim.x * 8) {
+    if (c >= j0 && c < j0 + jb) continue;
+    T *Ac = A + int64_t(c) * ld;
+    if (nsw > 0) {
+      T v[kPer];
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int e = lane + 32 * q;
+        if (e < nsw) v[q] = Ac[ssrc[e]];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int e = lane + 32 * q;
+        if (e < nsw) Ac[srow[e]] = v[q];
+      }
+      __syncwarp();
+    }
+    if (c >= j0 + jb) {
+      T x0 = (lane < jb) ? Ac[j0 + lane] : T(0);
+      T x1 = (NB > 32 && lane + 32 < jb) ? Ac[j0 + 32 + lane] : T(0);
+      for (int i = 0; i < jb; ++i) {
+        const T xi = __shfl_sync(0xffffffffu, i < 32 ? x0 : x1, i & 31);
+        if (lane > i && lane < jb) x0 -= L[lane + i * NB] * xi;
+        if (NB > 32 && lane + 32 > i && lane + 32 < jb) x1 -= L[lane + 32 + i * NB] * xi;
+      }
+      if (lane < jb) Ac[j0 + lane] = x0;
+      if (NB > 32 && lane + 32 < jb) Ac[j0 + 32 + lane] = x1;
+    }
+  }
+}
+
+// trailing update: A[t0:f, t0:f] -= A[t0:f, j0:j0+jb] * A[j0:j0+jb, t0:f], t0 = j0 + jb
+template <typename T, int BM, int BN, int TM, int TN, int NB>
+__global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict__ fr, int j0, T *__restrict__ fronts) {
+  const FrontDev F = fr[blockIdx.z];
+  if (j0 >= F.s) return;
+  const int jb = min(NB, F.s - j0);
+  const int t0 = j0 + jb;
+  const int nrest = F.f - t0;
+  const int rb = blockIdx.y * BM, cb = blockIdx.x * BN;
+  if (rb >= nrest || cb >= nrest) return;
+  T *A = fronts + F.off;
+  const int64_t ld = F.f;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *sA = reinterpret_cast<T *>(smraw);  // [NB][BM]
+  T *sB = sA + NB * BM;                   // [NB][BN]
+  const int tid = threadIdx.x;
+  for (int e = tid; e < jb * BM; e += 256) {
+    const int i = e % BM, k = e / BM;
+    const int r = rb + i;
+    sA[k * BM + i] = (r < nrest) ? A[(t0 + r) + int64_t(j0 + k) * ld] : T(0);
+  }
+  for (int e = tid; e < jb * BN; e += 256) {
+    const int k = e % jb, j = e / jb;
+    const int c = cb + j;
+    sB[k * BN + j] = (c < nrest) ? A[(j0 + k) + int64_t(t0 + c) * ld] : T(0);
+  }
+  __syncthreads();
+  const int tr = tid % 16, tc = tid / 16;
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+  for (int k = 0; k < jb; ++k) {
+    T a[TM], b[TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i) a[i] = sA[k * BM + tr + 16 * i];
+#pragma unroll
+    for (int j = 0; j < TN; ++j) b[j] = sB[k * BN + tc + 16 * j];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * b[j];
+  }
+#pragma unroll
+  for (int j = 0; j < TN; ++j) {
+    const int c = cb + tc + 16 * j;
+    if (c >= nrest) continue;
+    T *Cc = A + int64_t(t0 + c) * ld + t0;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int r = rb + tr + 16 * i;
+      if (r < nrest) Cc[r] -= acc[i][j];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_extend_add(const FrontDev *__restrict__ fr_all, int lo, const int32_t *__restrict__ map,
+                             T *__restrict__ fronts) {
+  const FrontDev F = fr_all[lo + blockIdx.z];
+  if (F.parent < 0 || F.b == 0) return;
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  if (i0 >= F.b || j0 >= F.b) return;
+  const FrontDev P = fr_all[F.parent];
+  const int32_t *mp = map + F.map_off;
+  const T *C = fronts + F.off + int64_t(F.s) * F.f + F.s;
+  T *Pa = fronts + P.off;
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int i = i0 + (e & 31), j = j0 + (e >> 5);
+    if (i < F.b && j < F.b) atomicAdd(&Pa[mp[i] + int64_t(mp[j]) * P.f], C[i + int64_t(j) * F.f]);
+  }
+}
+
+__global__ void k_make_perm(const FrontDev *__restrict__ fr, const int32_t *__restrict__ piv, int32_t *__restrict__ perm,
+                            int smem_cap) {
+  const FrontDev F = fr[blockIdx.x];
+  extern __shared__ int32_t sp[];
+  int32_t *P = perm + F.piv_off;
+  const int32_t *pv = piv + F.piv_off;
+  const bool sm = F.s <= smem_cap;
+  int32_t *W = sm ? sp : P;
+  for (int i = threadIdx.x; i < F.s; i += blockDim.x) W[i] = i;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int j = 0; j < F.s; ++j) {
+      const int p = pv[j];
+      if (p != j) {
+        const int32_t t = W[j];
+        W[j] = W[p];
+        W[p] = t;
+      }
+    }
+  __syncthreads();
+  if (sm)
+    for (int i = threadIdx.x; i < F.s; i += blockDim.x) P[i] = W[i];
+}
+
+// ---------------- triangular solves ----------------
+constexpr int kBS = 64;     // column block of the blocked solves
+constexpr int kMaxRhs = 16;
+constexpr int kRowsPerCta = 128;
+
+template <typename T>
+__global__ void k_fwd_gather(const FrontDev *__restrict__ fr, const int32_t *__restrict__ perm,
+                             const int32_t *__restrict__ idx, const T *__restrict__ y, int64_t ldy, int nrhs,
+                             T *__restrict__ work, const int64_t *__restrict__ work_off, int lo) {
+  const FrontDev F = fr[blockIdx.y];
+  T *W = work + work_off[lo + blockIdx.y];
+  const int32_t *ix = idx + F.idx_off;
+  const int32_t *pm = perm + F.piv_off;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F.f; i += gridDim.x * blockDim.x)
+    for (int r = 0; r < nrhs; ++r) W[i + int64_t(r) * F.f] = (i < F.s) ? y[ix[pm[i]] + r * ldy] : T(0);
+}
+
+template <typename T>
+__global__ void k_fwd_scatter(const FrontDev *__restrict__ fr, const int32_t *__restrict__ idx, T *__restrict__ y,
+                              int64_t ldy, int nrhs, const T *__restrict__ work, const int64_t *__restrict__ work_off,
+                              int lo) {
+  const FrontDev F = fr[blockIdx.y];
+  const T *W = work + work_off[lo + blockIdx.y];
+  const int32_t *ix = idx + F.idx_off;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F.f; i += gridDim.x * blockDim.x)
+    for (int r = 0; r < nrhs; ++r) {
+      const T v = W[i + int64_t(r) * F.f];
+      if (i < F.s)
+        y[ix[i] + r * ldy] = v;
+      else
+        atomicAdd(&y[ix[i] + r * ldy], v);
+    }
+}
+
+// unit lower (fwd) or upper (bwd) solve of the diagonal block [c0, c0+cb)
+template <typename T, bool kUpper>
+__global__ void __launch_bounds__(256) k_diag_solve(const FrontDev *__restrict__ fr, int c0, const T *__restrict__ fronts,
+                                                    int nrhs, T *__restrict__ work, const int64_t *__restrict__ work_off,
+                                                    int lo) {
+  const FrontDev F = fr[blockIdx.x];
+  if (c0 >= F.s) return;
+  const int cb = min(kBS, F.s - c0);
+  const T *A = fronts + F.off;
+  T *W = work + work_off[lo + blockIdx.x];
+  __shared__ T L[kBS * kBS];
+  __shared__ T X[kBS * kMaxRhs];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < cb * cb; e += blockDim.x) {
+    const int r = e % cb, c = e / cb;
+    L[r + c * kBS] = A[(c0 + r) + int64_t(c0 + c) * F.f];
+  }
+  for (int e = tid; e < cb * nrhs; e += blockDim.x) {
+    const int r = e % cb, c = e / cb;
+    X[r + c * kBS] = W[(c0 + r) + int64_t(c) * F.f];
+  }
+  __syncthreads();
+  if (!kUpper) {
+    for (int i = 0; i < cb; ++i) {
+      for (int e = tid; e < (cb - i - 1) * nrhs; e += blockDim.x) {
+        const int q = i + 1 + e % (cb - i - 1), c = e / (cb - i - 1);
+        X[q + c * kBS] -= L[q + i * kBS] * X[i + c * kBS];
+      }
+      __syncthreads();
+    }
+  } else {
+    for (int i = cb - 1; i >= 0; --i) {
+      if (tid < nrhs) X[i + tid * kBS] /= L[i + i * kBS];
+      __syncthreads();
+      for (int e = tid; e < i * nrhs; e += blockDim.x) {
+        const int q = e % i, c = e / i;
+        X[q + c * kBS] -= L[q + i * kBS] * X[i + c * kBS];
+      }
+      __syncthreads();
+    }
+  }
+  for (int e = tid; e < cb * nrhs; e += blockDim.x) {
+    const int r = e % cb, c = e / cb;
+    W[(c0 + r) + int64_t(c) * F.f] = X[r + c * kBS];
+  }
+}
+
+// rows [r_lo, r_hi) of W -= A[rows, k_lo:k_hi] * W[k_lo:k_hi]
+template <typename T>
+__device__ void block_update(const T *A, int64_t ld, T *W, int64_t ldw, int r_lo, int r_hi, int k_lo, int k_hi,
+                             int nrhs, T *sX) {
+  const int tid = threadIdx.x;
+  const int r = r_lo + blockIdx.x * kRowsPerCta + tid;
+  T acc[kMaxRhs];
+#pragma unroll
+  for (int c = 0; c < kMaxRhs; ++c) acc[c] = T(0);
+  for (int k0 = k_lo; k0 < k_hi; k0 += kBS) {
+    const int kb = min(kBS, k_hi - k0);
+    __syncthreads();
+    for (int e = tid; e < kb * nrhs; e += blockDim.x) {
+      const int q = e % kb, c = e / kb;
+      sX[q + c * kBS] = W[(k0 + q) + int64_t(c) * ldw];
+    }
+    __syncthreads();
+    if (r < r_hi) {
+      for (int q = 0; q < kb; ++q) {
+        const T a = A[r + int64_t(k0 + q) * ld];
+#pragma unroll
+        for (int c = 0; c < kMaxRhs; ++c)
+          if (c < nrhs) acc[c] += a * sX[q + c * kBS];
+      }
+    }
+  }
+  if (r < r_hi)
+#pragma unroll
+    for (int c = 0; c < kMaxRhs; ++c)
+      if (c < nrhs) W[r + int64_t(c) * ldw] -= acc[c];
+}
+
+// forward: rows [c0+cb, f) -= L[:, c0:c0+cb] * W[c0:c0+cb]
+template <typename T>
+__global__ void __launch_bounds__(kRowsPerCta) k_fwd_update(const FrontDev *__restrict__ fr, int c0,
+                                                            const T *__restrict__ fronts, int nrhs, T *__restrict__ work,
+                                                            const int64_t *__restrict__ work_off, int lo) {
+  const FrontDev F = fr[blockIdx.y];
+  if (c0 >= F.s) return;
+  const int cb = min(kBS, F.s - c0);
+  const int r_lo = c0 + cb;
+  if (r_lo + int(blockIdx.x) * kRowsPerCta >= F.f) return;
+  __shared__ T sX[kBS * kMaxRhs];
+  block_update<T>(fronts + F.off, F.f, work + work_off[lo + blockIdx.y], F.f, r_lo, F.f, c0, c0 + cb, nrhs, sX);
+}
+
+// backward: rows [0, c0) -= U[:, c0:c0+cb] * W[c0:c0+cb]
+template <typename T>
+__global__ void __launch_bounds__(kRowsPerCta) k_bwd_update(const FrontDev *__restrict__ fr, int c0,
+                                                            const T *__restrict__ fronts, int nrhs, T *__restrict__ work,
+                                                            const int64_t *__restrict__ work_off, int lo) {
+  const FrontDev F = fr[blockIdx.y];
+  if (c0 >= F.s) return;
+  const int cb = min(kBS, F.s - c0);
+  if (int(blockIdx.x) * kRowsPerCta >= c0) return;
+  __shared__ T sX[kBS * kMaxRhs];
+  block_update<T>(fronts + F.off, F.f, work + work_off[lo + blockIdx.y], F.f, 0, c0, c0, c0 + cb, nrhs, sX);
+}
+
+// backward, before the block sweep: rows [0, s) -= U12 * W[s:f]
+template <typename T>
+__global__ void __launch_bounds__(kRowsPerCta) k_bwd_u12(const FrontDev *__restrict__ fr, const T *__restrict__ fronts,
+                                                         int nrhs, T *__restrict__ work,
+                                                         const int64_t *__restrict__ work_off, int lo) {
+  const FrontDev F = fr[blockIdx.y];
+  if (F.b == 0 || int(blockIdx.x) * kRowsPerCta >= F.s) return;
+  __shared__ T sX[kBS * kMaxRhs];
+  block_update<T>(fronts + F.off, F.f, work + work_off[lo + blockIdx.y], F.f, 0, F.s, F.s, F.f, nrhs, sX);
+}
+
+template <typename T>
+__global__ void k_bwd_gather(const FrontDev *__restrict__ fr, const int32_t *__restrict__ idx, const T *__restrict__ y,
+                             int64_t ldy, int nrhs, T *__restrict__ work, const int64_t *__restrict__ work_off, int lo) {
+  const FrontDev F = fr[blockIdx.y];
+  T *W = work + work_off[lo + blockIdx.y];
+  const int32_t *ix = idx + F.idx_off;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F.f; i += gridDim.x * blockDim.x)
+    for (int r = 0; r < nrhs; ++r) W[i + int64_t(r) * F.f] = y[ix[i] + r * ldy];
+}
+
+template <typename T>
+__global__ void k_bwd_scatter(const FrontDev *__restrict__ fr, const int32_t *__restrict__ idx, T *__restrict__ y,
+                              int64_t ldy, int nrhs, const T *__restrict__ work, const int64_t *__restrict__ work_off,
+                              int lo) {
+  const FrontDev F = fr[blockIdx.y];
+  const T *W = work + work_off[lo + blockIdx.y];
+  const int32_t *ix = idx + F.idx_off;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F.s; i += gridDim.x * blockDim.x)
+    for (int r = 0; r < nrhs; ++r) y[ix[i] + r * ldy] = W[i + int64_t(r) * F.f];
+}
+
+inline int cdiv(int64_t a, int64_t b) { return int((a + b - 1) / b); }
+
+template <typename T>
+struct GemmCfg;
+template <>
+struct GemmCfg<double> {
+  static constexpr int BM = 64, BN = 64, TM = 4, TN = 4;
+};
+template <>
+struct GemmCfg<float> {
+  static constexpr int BM = 128, BN = 128, TM = 8, TN = 8;
+};
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_assemble(const AItem *items, int64_t n, const double *S, T *fronts, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_assemble<T><<<unsigned(n), 128, 0, s>>>(items, S, fronts);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_lu_level(const FrontDev *fr, int nfront, int max_s, int max_f, T *fronts, int32_t *piv,
+                            int32_t *swaps, int *err, cudaStream_t s) {
+  constexpr int NB = LuCfg<T>::NB;
+  using G = GemmCfg<T>;
+  auto gemm = k_gemm_update<T, G::BM, G::BN, G::TM, G::TN, NB>;
+  const size_t gsmem = sizeof(T) * NB * (G::BM + G::BN);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gsmem));
+    attr = true;
+  }
+  for (int j0 = 0; j0 < max_s; j0 += NB) {
+    k_panel<T, NB><<<nfront, kPanelThreads, 0, s>>>(fr, j0, fronts, piv, swaps, err);
+    const int ncol_blocks = std::min(cdiv(max_f, 8), 4096);
+    k_swap_trsm<T, NB><<<dim3(ncol_blocks, nfront), 256, 0, s>>>(fr, j0, fronts, swaps);
+    const int rest = max_f - j0 - 1;
+    if (rest > 0) {
+      dim3 g(cdiv(rest, G::BN), cdiv(rest, G::BM), nfront);
+      gemm<<<g, 256, gsmem, s>>>(fr, j0, fronts);
+    }
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_extend_add_impl(const FrontDev *fr_all, int lo, int nfront, int max_b, const int32_t *map,
+                                   T *fronts, cudaStream_t s) {
+  if (nfront == 0 || max_b == 0) return cudaSuccess;
+  dim3 g(cdiv(max_b, 32), cdiv(max_b, 32), nfront);
+  k_extend_add<T><<<g, 256, 0, s>>>(fr_all, lo, map, fronts);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_make_perm(const FrontDev *fr, int nfront, int max_s, const int32_t *piv, int32_t *perm,
+                             cudaStream_t s) {
+  if (nfront == 0) return cudaSuccess;
+  const int cap = 40 * 1024;  // entries staged in shared memory (160 KB)
+  const size_t smem = sizeof(int32_t) * size_t(std::min(max_s, cap));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_make_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(int32_t) * cap));
+    attr = true;
+  }
+  k_make_perm<<<nfront, 256, smem, s>>>(fr, piv, perm, std::min(max_s, cap));
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_solve_fwd_level_impl(const FrontDev *fr, int lo, int nfront, int max_s, int max_f, const T *fronts,
+                                        const int32_t *perm, const int32_t *idx, T *y, int64_t ldy, int nrhs, T *work,
+                                        const int64_t *work_off, cudaStream_t s) {
+  if (nfront == 0) return cudaSuccess;
+  const FrontDev *frl = fr + lo;
+  k_fwd_gather<T><<<dim3(cdiv(max_f, 256), nfront), 256, 0, s>>>(frl, perm, idx, y, ldy, nrhs, work, work_off, lo);
+  for (int c0 = 0; c0 < max_s; c0 += kBS) {
+    k_diag_solve<T, false><<<nfront, 256, 0, s>>>(frl, c0, fronts, nrhs, work, work_off, lo);
+    const int rest = max_f - c0 - 1;
+    if (rest > 0)
+      k_fwd_update<T><<<dim3(cdiv(rest, kRowsPerCta), nfront), kRowsPerCta, 0, s>>>(frl, c0, fronts, nrhs, work,
+                                                                                   work_off, lo);
+  }
+  k_fwd_scatter<T><<<dim3(cdiv(max_f, 256), nfront), 256, 0, s>>>(frl, idx, y, ldy, nrhs, work, work_off, lo);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, int max_s, int max_f, const T *fronts,
+                                        const int32_t *idx, T *y, int64_t ldy, int nrhs, T *work,
+                                        const int64_t *work_off, cudaStream_t s) {
+  if (nfront == 0) return cudaSuccess;
+  const FrontDev *frl = fr + lo;
+  k_bwd_gather<T><<<dim3(cdiv(max_f, 256), nfront), 256, 0, s>>>(frl, idx, y, ldy, nrhs, work, work_off, lo);
+  k_bwd_u12<T><<<dim3(cdiv(max_s, kRowsPerCta), nfront), kRowsPerCta, 0, s>>>(frl, fronts, nrhs, work, work_off, lo);
+  const int last = ((max_s - 1) / kBS) * kBS;
+  for (int c0 = last; c0 >= 0; c0 -= kBS) {
+    k_diag_solve<T, true><<<nfront, 256, 0, s>>>(frl, c0, fronts, nrhs, work, work_off, lo);
+    if (c0 > 0)
+      k_bwd_update<T><<<dim3(cdiv(c0, kRowsPerCta), nfront), kRowsPerCta, 0, s>>>(frl, c0, fronts, nrhs, work,
+                                                                                work_off, lo);
+  }
+  k_bwd_scatter<T><<<dim3(cdiv(max_s, 256), nfront), 256, 0, s>>>(frl, idx, y, ldy, nrhs, work, work_off, lo);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_assemble<double>(const AItem *, int64_t, const double *, double *, cudaStream_t);
+template cudaError_t launch_assemble<float>(const AItem *, int64_t, const double *, float *, cudaStream_t);
+template cudaError_t launch_lu_level<double>(const FrontDev *, int, int, int, double *, int32_t *, int32_t *, int *,
+                                             cudaStream_t);
+template cudaError_t launch_lu_level<float>(const FrontDev *, int, int, int, float *, int32_t *, int32_t *, int *,
+                                            cudaStream_t);
+template cudaError_t launch_make_perm<double>(const FrontDev *, int, int, const int32_t *, int32_t *, cudaStream_t);
+template cudaError_t launch_make_perm<float>(const FrontDev *, int, int, const int32_t *, int32_t *, cudaStream_t);
+template cudaError_t launch_extend_add_impl<double>(const FrontDev *, int, int, int, const int32_t *, double *,
+                                                    cudaStream_t);
+template cudaError_t launch_extend_add_impl<float>(const FrontDev *, int, int, int, const int32_t *, float *,
+                                                   cudaStream_t);
+template cudaError_t launch_solve_fwd_level_impl<double>(const FrontDev *, int, int, int, int, const double *,
+                                                         const int32_t *, const int32_t *, double *, int64_t, int,
+                                                         double *, const int64_t *, cudaStream_t);
+template cudaError_t launch_solve_fwd_level_impl<float>(const FrontDev *, int, int, int, int, const float *,
+                                                        const int32_t *, const int32_t *, float *, int64_t, int,
+                                                        float *, const int64_t *, cudaStream_t);
+template cudaError_t launch_solve_bwd_level_impl<double>(const FrontDev *, int, int, int, int, const double *,
+                                                         const int32_t *, double *, int64_t, int, double *,
+                                                         const int64_t *, cudaStream_t);
+template cudaError_t launch_solve_bwd_level_impl<float>(const FrontDev *, int, int, int, int, const float *,
+                                                        const int32_t *, float *, int64_t, int, float *,
+                                                        const int64_t *, cudaStream_t);
+
+}  // namespace h2sp

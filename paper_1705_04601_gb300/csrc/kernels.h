@@ -1,0 +1,113 @@
+// Launchers of the h2sp kernels (host side declarations).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace h2sp {
+
+// ---- sparsification (sparsify.cu), FP64 ----
+cudaError_t launch_householder(const QItem *items, int n, const double *w_in, const double *w_buf, double *Q,
+                               double *Rr, int max_m, int max_k, cudaStream_t s);
+cudaError_t launch_stack_w(const WItem *items, int n, const double *Rr, const double *T, double *W, cudaStream_t s);
+cudaError_t launch_coupling(const CItem *items, int n, const double *Rr, const double *Rrc, const double *Dc,
+                            double *const *dst_base, int max_k, cudaStream_t s);
+cudaError_t launch_transform(const XItem *items, int n, const double *const *src_base, const double *Qrow,
+                             const double *Qcol, double *const *dst_base, cudaStream_t s);
+
+// ---- block LU of S (factor.cu), T = double or float ----
+struct FrontDev {
+  int64_t off, piv_off, idx_off, map_off;
+  int32_t s, b, f, parent;
+};
+
+// Panel width of the blocked LU per precision.
+template <typename T>
+struct LuCfg;
+template <>
+struct LuCfg<double> {
+  static constexpr int NB = 32;
+};
+template <>
+struct LuCfg<float> {
+  static constexpr int NB = 64;
+};
+
+// Maximum number of rows a panel swaps (2 per column).
+constexpr int kMaxSwapRows = 2 * 64;
+
+template <typename T>
+cudaError_t launch_assemble(const AItem *items, int64_t n, const double *S, T *fronts, cudaStream_t s);
+template <typename T>
+cudaError_t launch_lu_level(const FrontDev *fr, int nfront, int max_s, int max_f, T *fronts, int32_t *piv,
+                            int32_t *swaps, int *err, cudaStream_t s);
+template <typename T>
+cudaError_t launch_extend_add_impl(const FrontDev *fr_all, int lo, int nfront, int max_b, const int32_t *map,
+                                   T *fronts, cudaStream_t s);
+template <typename T>
+cudaError_t launch_make_perm(const FrontDev *fr, int nfront, int max_s, const int32_t *piv, int32_t *perm,
+                             cudaStream_t s);
+// Forward sweep for one level (fronts [lo, lo+nfront) of fr): gathers y into
+// the fronts' work vectors, solves with L, stores z (supernode part) back into
+// y and adds -L21 z into the boundary rows of y.
+template <typename T>
+cudaError_t launch_solve_fwd_level_impl(const FrontDev *fr, int lo, int nfront, int max_s, int max_f, const T *fronts,
+                                        const int32_t *perm, const int32_t *idx, T *y, int64_t ldy, int nrhs, T *work,
+                                        const int64_t *work_off, cudaStream_t s);
+// Backward sweep for one level: x_s = U11^-1 (z - U12 x_b), stored into y.
+template <typename T>
+cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, int max_s, int max_f, const T *fronts,
+                                        const int32_t *idx, T *y, int64_t ldy, int nrhs, T *work,
+                                        const int64_t *work_off, cudaStream_t s);
+
+// ---- applies, H^2 product, vector kernels (apply.cu) ----
+struct ApItem {
+  int64_t q;      // Q offset (m x m)
+  int64_t xin;    // offset of X_l(t) in the level-l vector (rows)
+  int64_t yout;   // S-space row of the non-basis part, -1 if none
+  int64_t xout;   // row in the level-(l+1) vector of the basis part, -1 if none
+  int32_t m, kp;
+};
+// out rows: non-basis -> S space (ys), basis -> next level (xn); op = Q^T
+cudaError_t launch_apply_qt(const ApItem *items, int n, const double *Q, const double *x, int64_t ldx, double *ys,
+                            int64_t ldys, double *xn, int64_t ldxn, int nrhs, cudaStream_t s);
+// reverse: X_l(t) = Q [xn part; ys part]
+cudaError_t launch_apply_q(const ApItem *items, int n, const double *Q, const double *xn, int64_t ldxn,
+                           const double *ys, int64_t ldys, double *x, int64_t ldx, int nrhs, cudaStream_t s);
+// copy rows: dst[dst_row[i] + r] = src[src_row[i] + r] for r < len[i]
+cudaError_t launch_copy_rows(const int64_t *src_row, const int64_t *dst_row, const int32_t *len, int n,
+                             const double *src, int64_t lds, double *dst, int64_t ldd, int nrhs, cudaStream_t s);
+// y = S x (VBR, FP64)
+cudaError_t launch_spmv(const int64_t *brow_ptr, const int32_t *bcol, const int64_t *val_off, const int64_t *node_off,
+                        int nnodes, const double *vals, const double *x, int64_t ldx, double *y, int64_t ldy, int nrhs,
+                        cudaStream_t s);
+
+struct H2Dev {
+  // device copies of the structure
+  const int64_t *begin, *size;
+  const int32_t *rank, *parent;
+  const int64_t *leaf_basis_off, *transfer_off, *coupling_off, *near_off;
+  const int64_t *col_leaf_basis_off, *col_transfer_off;
+  const int64_t *far_ptr, *near_ptr;
+  const int32_t *far_col, *near_col;
+  const int64_t *xh_off;
+  const double *leaf_basis, *transfer, *coupling, *near_block, *col_leaf_basis, *col_transfer;
+  int32_t leaf0;  // first leaf cluster
+};
+// y = A x with A of Definition 4.9 (upward pass, couplings, downward pass, close blocks);
+// xh / yh: coefficient workspaces with leading dimension ldh (>= sum of ranks), 16 columns
+cudaError_t launch_h2_matvec(const H2Dev &h, const int32_t *level_ptr_host, const int32_t *child_start,
+                             const int32_t *child_cnt, int depth, const double *x, int64_t ldx, double *y,
+                             int64_t ldy, int nrhs, double *xh, double *yh, int64_t ldh, cudaStream_t s);
+
+// r = b - y; norms2[c] = ||r_c||^2 (atomic FP64 accumulation), over n rows
+cudaError_t launch_residual(const double *b, int64_t ldb, const double *y, int64_t ldy, double *r, int64_t ldr,
+                            int64_t n, int nrhs, double *norms2, cudaStream_t s);
+cudaError_t launch_colnorm2(const double *x, int64_t ldx, int64_t n, int nrhs, double *norms2, cudaStream_t s);
+// x += d
+cudaError_t launch_axpy(const double *d, int64_t ldd, double *x, int64_t ldx, int64_t n, int nrhs, cudaStream_t s);
+cudaError_t launch_cast_d2f(const double *a, int64_t lda, float *b, int64_t ldb, int64_t n, int nrhs, cudaStream_t s);
+cudaError_t launch_cast_f2d(const float *a, int64_t lda, double *b, int64_t ldb, int64_t n, int nrhs, cudaStream_t s);
+
+}  // namespace h2sp

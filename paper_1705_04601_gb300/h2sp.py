@@ -1,0 +1,296 @@
+"""Python binding of the h2sp C ABI (include/h2sp.h): argument marshalling only.
+
+Every step of the method runs inside libh2sp.so.  PyTorch is used here only to
+hold device memory (tensors whose data pointers are passed through) and to
+name the current CUDA stream.  The functions keep the C names.
+
+Vector layout: a block of ``nrhs`` FP64 columns of length n is a contiguous
+tensor of shape (nrhs, n) (row r = column r, leading dimension n), or shape
+(n,) for one column.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libh2sp.so")
+
+H2SP_OK, H2SP_EINVAL, H2SP_ENOMEM, H2SP_ECUDA, H2SP_ESINGULAR = 0, -1, -2, -3, -4
+H2SP_ESTATE, H2SP_ENOCONV, H2SP_ETIMEOUT, H2SP_EUNSUPPORTED = -5, -6, -7, -8
+H2SP_FP64, H2SP_FP32 = 0, 1
+H2SP_OP_UT, H2SP_OP_V, H2SP_OP_U, H2SP_OP_VT, H2SP_OP_S, H2SP_OP_H2, H2SP_OP_SINV = range(7)
+H2SP_DIRECT, H2SP_IR, H2SP_GMRES = 0, 1, 2
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64), ("depth", ctypes.c_int32),
+        ("level_ptr", _i32p), ("parent", _i32p), ("begin", _i64p), ("size", _i64p), ("rank", _i32p),
+        ("far_ptr", _i64p), ("far_col", _i32p), ("near_ptr", _i64p), ("near_col", _i32p),
+        ("leaf_basis_off", _i64p), ("transfer_off", _i64p), ("coupling_off", _i64p), ("near_off", _i64p),
+        ("col_leaf_basis_off", _i64p), ("col_transfer_off", _i64p),
+        ("leaf_basis", _vp), ("transfer", _vp), ("coupling", _vp), ("near_block", _vp),
+        ("col_leaf_basis", _vp), ("col_transfer", _vp),
+    ]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_int32)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("tol", ctypes.c_double), ("maxit", ctypes.c_int32),
+                ("restart", ctypes.c_int32)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("status", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64), ("depth", ctypes.c_int32), ("lstop", ctypes.c_int32), ("nnodes", ctypes.c_int32),
+        ("nnzb", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nsupernodes", ctypes.c_int32),
+        ("nfront_levels", ctypes.c_int32), ("max_front", ctypes.c_int64), ("front_elems", ctypes.c_int64),
+        ("factor_flops", ctypes.c_double), ("sparsify_flops", ctypes.c_double), ("factor_prec", ctypes.c_int32),
+        ("plan_seconds", ctypes.c_double),
+    ]
+
+
+# name -> (restype, argtypes); every symbol of include/h2sp.h
+SIGNATURES = {
+    "h2sp_sparsify": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.POINTER(Opts), _vp, ctypes.POINTER(_vp)]),
+    "h2sp_analyze": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.POINTER(_vp)]),
+    "h2sp_factor": (ctypes.c_int, [_vp, ctypes.c_int32, _vp]),
+    "h2sp_solve": (ctypes.c_int, [_vp, ctypes.POINTER(SolveOpts), ctypes.c_int32, _vp, ctypes.c_int64, _vp,
+                                  ctypes.c_int64, ctypes.POINTER(SolveInfo), _vp]),
+    "h2sp_apply": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int64, _vp, ctypes.c_int64,
+                                  _vp]),
+    "h2sp_export_S": (ctypes.c_int, [_vp, _i64p, _i64p, _i32p, _i64p, _f64p, _vp]),
+    "h2sp_export_Q": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _i64p, _f64p, _vp]),
+    "h2sp_export_structure": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i64p]),
+    "h2sp_query": (ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
+    "h2sp_destroy": (None, [_vp]),
+    "h2sp_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
+    "h2sp_last_cuda_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libh2sp.so (built in-tree); fail loudly if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libh2sp.so is not built (run __graft_entry__.build() or "
+                               "python -m paper_1705_04601_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class H2spError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        L = lib()
+        msg = L.h2sp_status_string(status).decode()
+        detail = L.h2sp_last_cuda_error().decode()
+        super().__init__("%s: %s (%d)%s" % (where, msg, status, (": " + detail) if detail else ""))
+        self.status = status
+
+
+def _check(st: int, where: str):
+    if st != H2SP_OK:
+        raise H2spError(st, where)
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype)) if a is not None else None
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return _vp(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return _vp(stream)
+    return _vp(stream.cuda_stream)
+
+
+class H2Input:
+    """An H^2 matrix marshalled for the ABI: host structure arrays (kept alive
+    here) and device copies of the numeric arrays (torch tensors on cuda),
+    or ``device=None`` for h2sp_analyze (no numbers)."""
+
+    def __init__(self, h, device="cuda", nonblocking_from=None):
+        self.h = h
+        c = np.ascontiguousarray
+        self.arrs = dict(
+            level_ptr=c(h.level_ptr, np.int32), parent=c(h.parent, np.int32), begin=c(h.begin, np.int64),
+            size=c(h.size, np.int64), rank=c(h.rank, np.int32), far_ptr=c(h.far_ptr, np.int64),
+            far_col=c(h.far_col, np.int32), near_ptr=c(h.near_ptr, np.int64), near_col=c(h.near_col, np.int32),
+            leaf_basis_off=c(h.leaf_basis_off, np.int64), transfer_off=c(h.transfer_off, np.int64),
+            coupling_off=c(h.coupling_off, np.int64), near_off=c(h.near_off, np.int64),
+        )
+        if h.col_rank is not None:
+            self.arrs["col_leaf_basis_off"] = c(h.col_leaf_basis_off, np.int64)
+            self.arrs["col_transfer_off"] = c(h.col_transfer_off, np.int64)
+        self.dev = {}
+        if device is not None:
+            import torch
+            names = ["leaf_basis", "transfer", "coupling", "near_block"]
+            if h.col_rank is not None:
+                names += ["col_leaf_basis", "col_transfer"]
+            for nm in names:
+                a = getattr(h, nm)
+                src = nonblocking_from[nm] if nonblocking_from else torch.from_numpy(c(a, np.float64))
+                t = torch.empty(max(a.size, 1), dtype=torch.float64, device=device)
+                t[:a.size].copy_(src[:a.size] if nonblocking_from else src, non_blocking=bool(nonblocking_from))
+                self.dev[nm] = t
+
+    def desc(self) -> Desc:
+        a = self.arrs
+        d = Desc()
+        d.n = int(self.h.n)
+        d.depth = int(self.h.depth)
+        for nm in ("level_ptr", "parent", "rank", "far_col", "near_col"):
+            setattr(d, nm, _ptr(a[nm], ctypes.c_int32))
+        for nm in ("begin", "size", "far_ptr", "near_ptr", "leaf_basis_off", "transfer_off", "coupling_off",
+                   "near_off", "col_leaf_basis_off", "col_transfer_off"):
+            setattr(d, nm, _ptr(a.get(nm), ctypes.c_int64))
+        for nm in ("leaf_basis", "transfer", "coupling", "near_block", "col_leaf_basis", "col_transfer"):
+            t = self.dev.get(nm)
+            setattr(d, nm, t.data_ptr() if t is not None else None)
+        return d
+
+
+class Handle:
+    """Owns an h2sp handle; destroys it when closed or collected."""
+
+    def __init__(self, ptr: _vp, inp: H2Input):
+        self.ptr = ptr
+        self.inp = inp   # the borrowed device arrays must outlive the handle
+
+    def close(self):
+        if self.ptr is not None and self.ptr.value:
+            lib().h2sp_destroy(self.ptr)
+        self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def h2sp_analyze(inp: H2Input) -> Handle:
+    out = _vp()
+    d = inp.desc()
+    _check(lib().h2sp_analyze(ctypes.byref(d), ctypes.byref(out)), "h2sp_analyze")
+    return Handle(out, inp)
+
+
+def h2sp_sparsify(inp: H2Input, stream=None) -> Handle:
+    out = _vp()
+    d = inp.desc()
+    o = Opts(0)
+    _check(lib().h2sp_sparsify(ctypes.byref(d), ctypes.byref(o), _stream(stream), ctypes.byref(out)),
+           "h2sp_sparsify")
+    return Handle(out, inp)
+
+
+def h2sp_factor(h: Handle, prec: int = H2SP_FP64, stream=None):
+    _check(lib().h2sp_factor(h.ptr, int(prec), _stream(stream)), "h2sp_factor")
+
+
+def _cols(t, n):
+    if t.dim() == 1:
+        return 1, n
+    return int(t.shape[0]), int(t.stride(0))
+
+
+def h2sp_solve(h: Handle, b, x, mode: int = H2SP_DIRECT, tol: float = 1e-10, maxit: int = 50, restart: int = 30,
+               stream=None) -> SolveInfo:
+    n = int(h.inp.h.n)
+    nrhs, ldb = _cols(b, n)
+    _, ldx = _cols(x, n)
+    o = SolveOpts(int(mode), float(tol), int(maxit), int(restart))
+    info = SolveInfo()
+    st = lib().h2sp_solve(h.ptr, ctypes.byref(o), nrhs, _vp(b.data_ptr()), ldb, _vp(x.data_ptr()), ldx,
+                          ctypes.byref(info), _stream(stream))
+    if st not in (H2SP_OK, H2SP_ENOCONV):
+        _check(st, "h2sp_solve")
+    info.status = st
+    return info
+
+
+def h2sp_apply(h: Handle, op: int, x, y, stream=None):
+    n = int(h.inp.h.n)
+    nrhs, ldx = _cols(x, n)
+    _, ldy = _cols(y, n)
+    _check(lib().h2sp_apply(h.ptr, int(op), nrhs, _vp(x.data_ptr()), ldx, _vp(y.data_ptr()), ldy, _stream(stream)),
+           "h2sp_apply")
+
+
+def h2sp_query(h: Handle) -> dict:
+    st = Stats()
+    _check(lib().h2sp_query(h.ptr, ctypes.byref(st)), "h2sp_query")
+    return {name: getattr(st, name) for name, _ in Stats._fields_}
+
+
+def h2sp_export_S(h: Handle, values: bool = True, stream=None) -> dict:
+    q = h2sp_query(h)
+    nn, nnzb, nnz = q["nnodes"], q["nnzb"], q["nnz"]
+    ns = np.zeros(nn, np.int64)
+    bp = np.zeros(nn + 1, np.int64)
+    bc = np.zeros(max(nnzb, 1), np.int32)
+    vo = np.zeros(max(nnzb, 1), np.int64)
+    vals = np.zeros(max(nnz, 1), np.float64) if values else None
+    _check(lib().h2sp_export_S(h.ptr, _ptr(ns, ctypes.c_int64), _ptr(bp, ctypes.c_int64), _ptr(bc, ctypes.c_int32),
+                               _ptr(vo, ctypes.c_int64), _ptr(vals, ctypes.c_double) if values else None,
+                               _stream(stream) if values else _vp(None)), "h2sp_export_S")
+    return dict(node_size=ns, brow_ptr=bp, bcol_idx=bc[:nnzb], val_off=vo[:nnzb],
+                vals=vals[:nnz] if values else None)
+
+
+def h2sp_export_Q(h: Handle, cluster: int, col: bool = False, stream=None):
+    m = ctypes.c_int64(0)
+    _check(lib().h2sp_export_Q(h.ptr, int(cluster), int(col), ctypes.byref(m), None, _vp(None)), "h2sp_export_Q")
+    if m.value == 0:
+        return np.zeros((0, 0))
+    q = np.zeros(m.value * m.value, np.float64)
+    _check(lib().h2sp_export_Q(h.ptr, int(cluster), int(col), ctypes.byref(m), _ptr(q, ctypes.c_double),
+                               _stream(stream)), "h2sp_export_Q")
+    return q.reshape(m.value, m.value).T
+
+
+def h2sp_export_structure(h: Handle) -> dict:
+    q = h2sp_query(h)
+    nn, nsn = q["nnodes"], q["nsupernodes"]
+    nb = ctypes.c_int64(0)
+    _check(lib().h2sp_export_structure(h.ptr, None, None, None, None, None, None, None, ctypes.byref(nb)),
+           "h2sp_export_structure")
+    out = dict(node_level=np.zeros(nn, np.int32), node_cluster=np.zeros(nn, np.int32), closure=np.zeros(nn, np.int32),
+               order=np.zeros(nn, np.int32), sn_ptr=np.zeros(nsn + 1, np.int32), bnd_ptr=np.zeros(nsn + 1, np.int32),
+               bnd=np.zeros(max(nb.value, 1), np.int32))
+    _check(lib().h2sp_export_structure(h.ptr, *[_ptr(out[k], ctypes.c_int32) for k in
+                                                ("node_level", "node_cluster", "closure", "order", "sn_ptr",
+                                                 "bnd_ptr", "bnd")], ctypes.byref(nb)), "h2sp_export_structure")
+    out["bnd"] = out["bnd"][:nb.value]
+    return out
+
+
+def h2sp_destroy(h: Handle):
+    h.close()

@@ -1,0 +1,133 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+* libh2sp.so loads and exports every function include/h2sp.h declares;
+* h2sp_analyze (host planning only, no CUDA call) reproduces the oracle's
+  integer structure bit for bit: S node order and sizes, the VBR pattern of
+  S, closures, elimination order, supernodes and their boundaries;
+* malformed descriptors are rejected with H2SP_EINVAL before any launch.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1705_04601_gb300 import h2sp as H
+from paper_1705_04601_gb300 import synth
+from oracle import factor as ofa
+from oracle import sparsify as osp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1705_04601_gb300 import build
+    build.build()
+
+
+def test_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "h2sp.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    names = set(re.findall(r"\b(h2sp_[a-z_A-Z0-9]+)\s*\(", hdr))
+    assert len(names) >= 12
+    L = ctypes.CDLL(H.LIB_PATH)
+    for nm in sorted(names):
+        assert hasattr(L, nm), nm
+    assert names == set(H.SIGNATURES), names ^ set(H.SIGNATURES)
+
+
+_CASES = {
+    "log1k": dict(n=1024, kernel="log", leaf=32, tol=1e-8, seed=1),
+    "log4k": dict(n=4096, kernel="log", leaf=64, tol=1e-8, seed=1),
+    "skew1k": dict(n=1024, kernel="log_skew", leaf=32, tol=1e-8, seed=2),
+    "raw1k": dict(n=1024, kernel="log", leaf=32, tol=None, seed=3),
+    "tiny": dict(n=48, kernel="log", leaf=64, tol=1e-8, seed=6),
+    "inv3d": dict(n=1500, kernel="inv", leaf=40, tol=1e-6, seed=5, dim=3),
+    "log16k": dict(n=16384, kernel="log", leaf=64, tol=1e-6, seed=9),
+}
+
+
+def _make(name):
+    s = _CASES[name]
+    h, _ = synth.make_small(s["n"], kernel=s["kernel"], leaf=s["leaf"], tol=s["tol"], seed=s["seed"],
+                            dim=s.get("dim", 2))
+    return h
+
+
+@pytest.mark.parametrize("name", list(_CASES))
+def test_analyze_matches_oracle_structure(name):
+    h = _make(name)
+    sp = osp.sparsify(h)
+    sym = ofa.symbolic(h, sp)
+    vbr = osp.to_vbr(sp)
+    hd = H.h2sp_analyze(H.H2Input(h, device=None))
+    q = H.h2sp_query(hd)
+    assert q["lstop"] == sp.sch.lstop
+    assert q["nnodes"] == sp.sch.node_size.size
+    S = H.h2sp_export_S(hd, values=False)
+    assert np.array_equal(S["node_size"], sp.sch.node_size)
+    assert np.array_equal(S["brow_ptr"], vbr.brow_ptr)
+    assert np.array_equal(S["bcol_idx"], vbr.bcol_idx)
+    assert np.array_equal(S["val_off"], vbr.val_off)
+    st = H.h2sp_export_structure(hd)
+    assert np.array_equal(st["node_level"], sp.sch.node_level)
+    assert np.array_equal(st["node_cluster"], sp.sch.node_cluster)
+    assert np.array_equal(st["closure"], sym.closure)
+    assert np.array_equal(st["order"], sym.order)
+    assert np.array_equal(st["sn_ptr"], sym.sn_ptr)
+    assert st["bnd_ptr"][-1] == sum(len(b) for b in sym.boundary)
+    for k, b in enumerate(sym.boundary):
+        assert np.array_equal(st["bnd"][st["bnd_ptr"][k]:st["bnd_ptr"][k + 1]], b)
+    assert q["factor_flops"] == pytest.approx(sym.flops, rel=1e-12)
+    hd.close()
+
+
+def _bad(h, **changes):
+    inp = H.H2Input(h, device=None)
+    for k, v in changes.items():
+        inp.arrs[k] = v
+    return inp
+
+
+def test_malformed_descriptors_are_rejected():
+    h = _make("log1k")
+    base = H.H2Input(h, device=None)
+    # unsorted close list
+    nc = base.arrs["near_col"].copy()
+    lo, hi = int(h.near_ptr[3]), int(h.near_ptr[4])
+    nc[lo:hi] = nc[lo:hi][::-1]
+    bad = [
+        dict(near_col=nc),
+        dict(parent=np.where(np.arange(h.ncl) == 5, 7, base.arrs["parent"]).astype(np.int32)),
+        dict(size=np.where(np.arange(h.ncl) == h.ncl - 1, h.size[-1] + 1, h.size).astype(np.int64)),
+        dict(rank=np.where(np.arange(h.ncl) == 3, -1, h.rank).astype(np.int32)),
+        dict(level_ptr=np.array([0, 2] + list(h.level_ptr[2:]), np.int32)),
+    ]
+    for ch in bad:
+        with pytest.raises(H.H2spError) as e:
+            H.h2sp_analyze(_bad(h, **ch))
+        assert e.value.status == H.H2SP_EINVAL
+    # a far list that crosses depths
+    fc = base.arrs["far_col"].copy()
+    fc[0] = 0
+    with pytest.raises(H.H2spError) as e:
+        H.h2sp_analyze(_bad(h, far_col=fc))
+    assert e.value.status == H.H2SP_EINVAL
+
+
+def test_oversized_blocks_are_reported_unsupported():
+    h, _ = synth.make_small(1000, kernel="log", leaf=300, tol=1e-8, seed=3)
+    assert h.size[h.level_ptr[h.depth]:].max() > 64
+    with pytest.raises(H.H2spError) as e:
+        H.h2sp_analyze(H.H2Input(h, device=None))
+    assert e.value.status == H.H2SP_EUNSUPPORTED
+
+
+def test_device_calls_on_an_analyzed_handle_are_refused():
+    h = _make("log1k")
+    hd = H.h2sp_analyze(H.H2Input(h, device=None))
+    st = H.lib().h2sp_factor(hd.ptr, 0, None)
+    assert st == H.H2SP_ESTATE
+    hd.close()

@@ -1,0 +1,235 @@
+"""GPU parity of the CUDA path against the CPU oracle, through the C ABI.
+
+Bars (spec tolerances):
+* integer structure (S node order, VBR pattern, elimination structure): equal;
+* FP64 values: per block of S, ||S_gpu - S_oracle||_F <= 1e-10 ||row block of S_oracle||_F;
+  per cluster, ||Q_gpu - Q_oracle||_F <= 1e-10 ||Q||_F; solutions
+  ||x_gpu - x_oracle|| <= 1e-10 ||x_oracle|| for the FP64 direct solve;
+* the FP32-factor preconditioned refinement reaches a relative residual of
+  1e-10 on the FP64 H^2 product and then agrees with the FP64 solution to
+  the accuracy that residual implies.
+"""
+import numpy as np
+import pytest
+
+from paper_1705_04601_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1705_04601_gb300 import h2sp as H  # noqa: E402
+from oracle import factor as ofa  # noqa: E402
+from oracle import h2 as oh2  # noqa: E402
+from oracle import sparsify as osp  # noqa: E402
+
+TOL = 1e-10
+
+_CASES = {
+    "log1k": dict(n=1024, kernel="log", leaf=32, tol=1e-8, seed=1),
+    "log4k": dict(n=4096, kernel="log", leaf=64, tol=1e-8, seed=1),
+    "skew1k": dict(n=1024, kernel="log_skew", leaf=32, tol=1e-8, seed=2),
+    "raw1k": dict(n=1024, kernel="log", leaf=32, tol=None, seed=3),
+    "tiny": dict(n=48, kernel="log", leaf=64, tol=1e-8, seed=6),
+    "ragged": dict(n=3001, kernel="log", leaf=23, tol=1e-7, seed=8),
+    "inv3d": dict(n=1500, kernel="inv", leaf=40, tol=1e-6, seed=5, dim=3),
+}
+_cache = {}
+
+
+def case(name):
+    if name not in _cache:
+        s = _CASES[name]
+        h, b = synth.make_small(s["n"], kernel=s["kernel"], leaf=s["leaf"], tol=s["tol"], seed=s["seed"],
+                                dim=s.get("dim", 2), nrhs=3)
+        sp = osp.sparsify(h)
+        _cache[name] = (h, b, sp)
+    return _cache[name]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1705_04601_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA is required for the gpu tests")
+
+
+def dev(a):
+    """(n, nrhs) numpy -> (nrhs, n) cuda tensor (column-major n x nrhs)."""
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, np.float64).reshape(a.shape[0], -1).T)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy().T
+
+
+def sparsified(name):
+    h, b, sp = case(name)
+    inp = H.H2Input(h)
+    hd = H.h2sp_sparsify(inp)
+    return h, b, sp, hd
+
+
+@pytest.mark.parametrize("name", list(_CASES))
+def test_S_and_Q_match_oracle(name):
+    h, b, sp, hd = sparsified(name)
+    S = H.h2sp_export_S(hd)
+    vbr = osp.to_vbr(sp)
+    assert np.array_equal(S["brow_ptr"], vbr.brow_ptr)
+    assert np.array_equal(S["bcol_idx"], vbr.bcol_idx)
+    ns = vbr.node_size
+    for i in range(ns.size):
+        lo, hi = int(vbr.brow_ptr[i]), int(vbr.brow_ptr[i + 1])
+        if hi == lo:
+            continue
+        a, e = int(vbr.val_off[lo]), int(vbr.val_off[hi - 1] + ns[i] * ns[vbr.bcol_idx[hi - 1]])
+        ref_row = np.linalg.norm(vbr.vals[a:e])
+        for z in range(lo, hi):
+            j = int(vbr.bcol_idx[z])
+            o, sz = int(vbr.val_off[z]), int(ns[i] * ns[j])
+            d = np.linalg.norm(S["vals"][o:o + sz] - vbr.vals[o:o + sz])
+            assert d <= TOL * max(ref_row, 1e-300), (i, j, d, ref_row)
+    for t in sp.Q:
+        Qg = H.h2sp_export_Q(hd, t)
+        assert np.linalg.norm(Qg - sp.Q[t]) <= TOL * np.linalg.norm(sp.Q[t]), t
+        if not h.symmetric_bases:
+            Qcg = H.h2sp_export_Q(hd, t, col=True)
+            assert np.linalg.norm(Qcg - sp.Qc[t]) <= TOL * np.linalg.norm(sp.Qc[t]), t
+    hd.close()
+
+
+@pytest.mark.parametrize("name", ["log1k", "skew1k", "tiny", "ragged", "inv3d"])
+def test_applies_and_products(name):
+    h, b, sp, hd = sparsified(name)
+    n = h.n
+    bt = dev(b)
+    out = torch.empty_like(bt)
+    for op, ref in [(H.H2SP_OP_UT, osp.apply_T(sp, h, b, col=False)), (H.H2SP_OP_VT, osp.apply_T(sp, h, b, col=True)),
+                    (H.H2SP_OP_U, osp.apply_N(sp, h, b, col=False)), (H.H2SP_OP_V, osp.apply_N(sp, h, b, col=True)),
+                    (H.H2SP_OP_S, osp.dense_S(sp) @ b), (H.H2SP_OP_H2, oh2.Matvec(h)(b))]:
+        H.h2sp_apply(hd, op, bt, out)
+        torch.cuda.synchronize()
+        g = host(out)
+        assert np.linalg.norm(g - ref) <= 1e-12 * np.linalg.norm(ref) * max(1.0, np.sqrt(n) / 8), op
+    hd.close()
+
+
+@pytest.mark.parametrize("name", ["log1k", "log4k", "skew1k", "raw1k", "tiny", "ragged", "inv3d"])
+def test_fp64_direct_solve_matches_oracle(name):
+    h, b, sp, hd = sparsified(name)
+    H.h2sp_factor(hd, H.H2SP_FP64)
+    fa = ofa.factor(h, sp)
+    xo = ofa.solve(h, sp, fa, b)
+    bt = dev(b)
+    xt = torch.empty_like(bt)
+    H.h2sp_solve(hd, bt, xt, mode=H.H2SP_DIRECT)
+    torch.cuda.synchronize()
+    xg = host(xt)
+    assert np.linalg.norm(xg - xo) <= TOL * np.linalg.norm(xo)
+    # S^{-1} directly
+    c = osp.apply_T(sp, h, b)
+    ct = dev(c)
+    yt = torch.empty_like(ct)
+    H.h2sp_apply(hd, H.H2SP_OP_SINV, ct, yt)
+    torch.cuda.synchronize()
+    yo = ofa.solve_S(fa, c)
+    assert np.linalg.norm(host(yt) - yo) <= TOL * np.linalg.norm(yo)
+    hd.close()
+
+
+@pytest.mark.parametrize("name", ["log4k", "skew1k", "ragged"])
+def test_fp32_refinement_reaches_1e10(name):
+    h, b, sp, hd = sparsified(name)
+    H.h2sp_factor(hd, H.H2SP_FP32)
+    bt = dev(b)
+    xt = torch.empty_like(bt)
+    info = H.h2sp_solve(hd, bt, xt, mode=H.H2SP_IR, tol=1e-10, maxit=30)
+    assert info.status == H.H2SP_OK and info.rel_residual <= 1e-10
+    xg = host(xt)
+    A = oh2.dense(h)
+    res = np.linalg.norm(b - A @ xg, axis=0) / np.linalg.norm(b, axis=0)
+    assert res.max() <= 2e-10
+    xd = np.linalg.solve(A, b)
+    assert np.linalg.norm(xg - xd) <= 1e-7 * np.linalg.norm(xd)
+    hd.close()
+
+
+@pytest.mark.parametrize("nrhs", [1, 16, 20])
+def test_many_rhs_chunks(nrhs):
+    h, _, sp, hd = sparsified("log1k")
+    rng = np.random.default_rng(nrhs)
+    b = rng.standard_normal((h.n, nrhs))
+    H.h2sp_factor(hd, H.H2SP_FP64)
+    fa = ofa.factor(h, sp)
+    xo = ofa.solve(h, sp, fa, b)
+    bt = dev(b)
+    xt = torch.empty_like(bt)
+    H.h2sp_solve(hd, bt, xt, mode=H.H2SP_DIRECT)
+    torch.cuda.synchronize()
+    assert np.linalg.norm(host(xt) - xo) <= TOL * np.linalg.norm(xo)
+    hd.close()
+
+
+def test_singular_pivot_reported():
+    """A zero close matrix and zero bases give S = 0: the factor must report a singular pivot."""
+    h, _, sp = case("log1k")
+    import copy
+    h0 = copy.copy(h)
+    h0.near_block = np.zeros_like(h.near_block)
+    h0.coupling = np.zeros_like(h.coupling)
+    hd = H.h2sp_sparsify(H.H2Input(h0))
+    with pytest.raises(H.H2spError) as e:
+        H.h2sp_factor(hd, H.H2SP_FP64)
+    assert e.value.status == H.H2SP_ESINGULAR
+    hd.close()
+
+
+# ---------------------------------------------------------------------------
+# full size: the 2D log kernel with 65,536 points, leaf <= 64, tol 1e-6, 16 RHS
+# ---------------------------------------------------------------------------
+
+
+@pytest.fixture(scope="module")
+def full():
+    h, b = synth.make_workload("log2d_n65536")
+    sp = osp.sparsify(h)
+    return h, b, sp
+
+
+def test_full_size_S_parity(full):
+    h, b, sp = full
+    hd = H.h2sp_sparsify(H.H2Input(h))
+    S = H.h2sp_export_S(hd)
+    vbr = osp.to_vbr(sp)
+    assert np.array_equal(S["brow_ptr"], vbr.brow_ptr) and np.array_equal(S["bcol_idx"], vbr.bcol_idx)
+    ns = vbr.node_size
+    rng = np.random.default_rng(0)
+    rows = rng.choice(ns.size, size=min(400, ns.size), replace=False)
+    for i in rows:
+        lo, hi = int(vbr.brow_ptr[i]), int(vbr.brow_ptr[i + 1])
+        a = int(vbr.val_off[lo])
+        e = int(vbr.val_off[hi - 1] + ns[i] * ns[vbr.bcol_idx[hi - 1]])
+        assert np.linalg.norm(S["vals"][a:e] - vbr.vals[a:e]) <= TOL * np.linalg.norm(vbr.vals[a:e])
+    hd.close()
+
+
+def test_full_size_fp64_direct_and_mixed_refinement(full):
+    h, b, sp = full
+    mv = oh2.Matvec(h)
+    hd = H.h2sp_sparsify(H.H2Input(h))
+    bt = dev(b)
+    xt = torch.empty_like(bt)
+    H.h2sp_factor(hd, H.H2SP_FP64)
+    H.h2sp_solve(hd, bt, xt, mode=H.H2SP_DIRECT)
+    torch.cuda.synchronize()
+    x64 = host(xt)
+    r = np.linalg.norm(b - mv(x64), axis=0) / np.linalg.norm(b, axis=0)
+    assert r.max() <= 1e-10
+    H.h2sp_factor(hd, H.H2SP_FP32)
+    info = H.h2sp_solve(hd, bt, xt, mode=H.H2SP_IR, tol=1e-10, maxit=30)
+    assert info.status == H.H2SP_OK
+    x32 = host(xt)
+    r = np.linalg.norm(b - mv(x32), axis=0) / np.linalg.norm(b, axis=0)
+    assert r.max() <= 2e-10
+    assert np.linalg.norm(x32 - x64) <= 1e-6 * np.linalg.norm(x64)
+    hd.close()
