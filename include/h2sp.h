@@ -230,6 +230,31 @@ int h2sp_export_Q(h2sp_handle *h, int32_t cluster, int32_t col, int64_t *m, doub
 int h2sp_export_structure(h2sp_handle *h, int32_t *node_level, int32_t *node_cluster, int32_t *closure,
                           int32_t *order, int32_t *sn_ptr, int32_t *bnd_ptr, int32_t *bnd, int64_t *nbnd);
 
+/* Per-kernel-class counters of a handle (h2sp_profile).  Classes:
+ *  0 trailing GEMM update of the fronts     6 basis completions (Householder)
+ *  1 panel factorization with pivoting      7 coupling projections, W stacking
+ *  2 row swaps + U12 triangular solve       8 triangular solves with the fronts
+ *  3 extend-add into parent fronts          9 FP64 H^2 product
+ *  4 S blocks into fronts                  10 U^T / V applies
+ *  5 close-block / panel transforms        11 vector kernels, casts, permutations
+ * work[] is the algorithmic flop count (classes 0, 1, 2, 5), bytes (4, 8, 9)
+ * or elements (3) of the timed launches; 0 where not defined. */
+typedef struct {
+  int64_t launches[16];   /* kernel launches since the last reset (always counted) */
+  int64_t timed[16];      /* launches or launch groups bracketed by CUDA events */
+  double ms[16];          /* summed event time of the timed launches */
+  double work[16];        /* algorithmic work of the timed launches */
+} h2sp_kernel_times;
+
+/*
+ * h2sp_profile -- per-kernel-class timing.  timing = 1 brackets every later
+ * launch (or launch group of a solve sweep) of this handle with CUDA events
+ * recorded on the launching stream, timing = 0 stops, timing = -1 leaves it
+ * as is.  Synchronises on the last recorded event, then copies the counters
+ * to *out (may be NULL) and zeroes them when reset != 0.
+ */
+int h2sp_profile(h2sp_handle *h, int32_t timing, int32_t reset, h2sp_kernel_times *out);
+
 /* h2sp_query -- fill *st with the handle's sizes and counters. */
 int h2sp_query(const h2sp_handle *h, h2sp_stats *st);
 

@@ -46,6 +46,8 @@ struct LevelDev {
 
 struct FrontLevel {
   int lo, hi, max_s, max_f, max_b;
+  double b2 = 0.0;       // sum of b^2 (contribution elements) over the level's fronts
+  double lu_elems = 0.0; // sum of s^2/2 + s*b (factor elements one sweep reads)
 };
 
 }  // namespace
@@ -90,7 +92,10 @@ struct h2sp_handle {
   double *xh = nullptr, *yh = nullptr;
   double *norms = nullptr;
   double plan_seconds = 0.0;
-  bool device_ready = false;  // false for handles made by h2sp_analyze
+  bool device_ready = false;
+  Prof prof;
+  std::vector<double> x_flops;  // algorithmic flops of each level's transform launch
+  double near_bytes = 0.0;      // bytes of the close blocks (Definition 4.8)  // false for handles made by h2sp_analyze
 
   template <class T>
   T *alloc(size_t n) {
@@ -146,6 +151,14 @@ void ensure_vectors(h2sp_handle *h, int nrhs) {
 void apply_T(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *out, int64_t ldout, int nrhs) {
   const Plan &p = h->plan;
   cudaStream_t s = h->stream;
+  const int chunks = (nrhs + 15) / 16;
+  const size_t e0 = h->prof.begin();
+  struct Done {
+    h2sp_handle *h;
+    size_t e0;
+    int n;
+    ~Done() { h->prof.end(P_APPLY, n, e0, 0.0); }
+  } done{h, e0, 1 + p.lstop * chunks};
   const double *Qb = col ? h->Qc : h->Q;
   if (p.lstop == 0) {
     ck(launch_copy_rows(h->top_src, h->top_dst, h->top_len, h->ntop, in, ldin, out, ldout, nrhs, s));
@@ -168,6 +181,14 @@ void apply_T(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *o
 void apply_N(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *out, int64_t ldout, int nrhs) {
   const Plan &p = h->plan;
   cudaStream_t s = h->stream;
+  const int chunks = (nrhs + 15) / 16;
+  const size_t e0 = h->prof.begin();
+  struct Done {
+    h2sp_handle *h;
+    size_t e0;
+    int n;
+    ~Done() { h->prof.end(P_APPLY, n, e0, 0.0); }
+  } done{h, e0, 1 + p.lstop * chunks};
   const double *Qb = col ? h->Qc : h->Q;
   if (p.lstop == 0) {
     ck(launch_copy_rows(h->top_dst, h->top_src, h->top_len, h->ntop, in, ldin, out, ldout, nrhs, s));
@@ -187,8 +208,12 @@ void apply_N(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *o
 
 void h2_matvec(h2sp_handle *h, const double *x, int64_t ldx, double *y, int64_t ldy, int nrhs) {
   const Plan &p = h->plan;
+  const size_t e0 = h->prof.begin();
   ck(launch_h2_matvec(h->h2, p.level_ptr.data(), h->child_start, h->child_cnt, p.D, x, ldx, y, ldy, nrhs, h->xh,
                       h->yh, std::max<int64_t>(p.xh_elems, 1), h->stream));
+  const int chunks = (nrhs + 15) / 16;
+  // bytes of the close blocks each pass streams (the dominant traffic of the product)
+  h->prof.end(P_MATVEC, (3 + 2 * p.D) * chunks, e0, h->near_bytes * chunks);
 }
 
 // per-front work vectors of the triangular solves, for 16 right-hand sides at a time
@@ -222,11 +247,11 @@ void solve_S_T(h2sp_handle *h, T *y, int nrhs) {
     T *yr = y + int64_t(r0) * p.n;
     for (const FrontLevel &L : h->flev)
       ck(launch_solve_fwd_level_impl<T>(h->fr, L.lo, L.hi - L.lo, L.max_s, L.max_f, fronts, h->perm, h->fidx, yr,
-                                        p.n, nr, work, h->work_off, h->stream));
+                                        p.n, nr, work, h->work_off, h->stream, &h->prof, L.lu_elems * sizeof(T)));
     for (int i = int(h->flev.size()) - 1; i >= 0; --i) {
       const FrontLevel &L = h->flev[i];
       ck(launch_solve_bwd_level_impl<T>(h->fr, L.lo, L.hi - L.lo, L.max_s, L.max_f, fronts, h->fidx, yr, p.n, nr,
-                                        work, h->work_off, h->stream));
+                                        work, h->work_off, h->stream, &h->prof, L.lu_elems * sizeof(T)));
     }
   }
 }
@@ -241,6 +266,7 @@ void solve_S(h2sp_handle *h, double *y, int nrhs) {
     ck(launch_cast_d2f(y, n, h->yf, n, n, nrhs, h->stream));
     solve_S_T<float>(h, h->yf, nrhs);
     ck(launch_cast_f2d(h->yf, n, y, n, n, nrhs, h->stream));
+    h->prof.end(P_OTHER, 2, 0, 0.0);
   }
 }
 
@@ -289,6 +315,7 @@ int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream s
     return st;
   }
   h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->prof.stream = h->stream;
   h->leaf_basis = desc->leaf_basis;
   h->transfer = desc->transfer;
   h->coupling = desc->coupling;
@@ -339,6 +366,10 @@ int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream s
       d.nc = int(w.c.size());
       d.x = h->upload(w.x);
       d.nx = int(w.x.size());
+      double xf = 0.0;
+      for (const XItem &it : w.x)
+        xf += (it.qR >= 0 ? 2.0 * it.rows * it.cols * it.cols : 0.0) + (it.qL >= 0 ? 2.0 * it.rows * it.rows * it.cols : 0.0);
+      h->x_flops.push_back(xf);
       if (!p.sym) {
         d.qc = h->upload(w.qc);
         d.wc = h->upload(w.wc);
@@ -360,17 +391,18 @@ int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream s
       LevelDev &d = h->lv[l];
       if (l < L) {
         if (l >= 1) {
-          ck(launch_stack_w(d.w, d.nw, h->Rr, h->transfer, d.W, s));
-          if (!p.sym) ck(launch_stack_w(d.wc, d.nw, h->Rrc, h->col_transfer, d.Wc, s));
+          ck(launch_stack_w(d.w, d.nw, h->Rr, h->transfer, d.W, s, &h->prof));
+          if (!p.sym) ck(launch_stack_w(d.wc, d.nw, h->Rrc, h->col_transfer, d.Wc, s, &h->prof));
         }
         ck(launch_householder(d.q, d.nq, h->leaf_basis, d.W, h->Q, h->Rr, std::max(w.max_m, 1), std::max(w.max_k, 1),
-                              s));
+                              s, &h->prof));
         if (!p.sym)
           ck(launch_householder(d.qc, d.nq, h->col_leaf_basis, d.Wc, h->Qc, h->Rrc, std::max(w.max_m, 1),
-                                std::max(w.max_k, 1), s));
-        ck(launch_coupling(d.c, d.nc, h->Rr, h->Rrc, h->coupling, d.dst_base, max_rank, s));
+                                std::max(w.max_k, 1), s, &h->prof));
+        ck(launch_coupling(d.c, d.nc, h->Rr, h->Rrc, h->coupling, d.dst_base, max_rank, s, &h->prof));
       }
-      ck(launch_transform(d.x, d.nx, const_cast<const double *const *>(d.src_base), h->Q, h->Qc, d.dst_base, s));
+      ck(launch_transform(d.x, d.nx, const_cast<const double *const *>(d.src_base), h->Q, h->Qc, d.dst_base, s,
+                            &h->prof, l < int(h->x_flops.size()) ? h->x_flops[l] : 0.0));
     }
     // ---- apply items ----
     {
@@ -446,6 +478,9 @@ int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream s
       }
       h->child_start = h->upload(cs);
       h->child_cnt = h->upload(cc);
+      for (int lf = 0; lf < p.nleaf; ++lf)
+        for (int64_t z = p.near_ptr[lf]; z < p.near_ptr[lf + 1]; ++z)
+          h->near_bytes += 8.0 * double(p.h_size[p.level_ptr[p.D] + lf]) * double(p.h_size[p.near_col[z]]);
       h->xh = h->alloc<double>(size_t(std::max<int64_t>(p.xh_elems, 1)) * 16);
       h->yh = h->alloc<double>(size_t(std::max<int64_t>(p.xh_elems, 1)) * 16);
       h->norms = h->alloc<double>(64);
@@ -465,9 +500,12 @@ int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream s
       for (size_t i = 0; i + 1 < p.front_level_ptr.size(); ++i) {
         FrontLevel fl{p.front_level_ptr[i], p.front_level_ptr[i + 1], 0, 0, 0};
         for (int k = fl.lo; k < fl.hi; ++k) {
-          fl.max_s = std::max(fl.max_s, p.fronts[k].s);
-          fl.max_f = std::max(fl.max_f, p.fronts[k].f);
-          fl.max_b = std::max(fl.max_b, p.fronts[k].b);
+          const Front &F = p.fronts[k];
+          fl.max_s = std::max(fl.max_s, F.s);
+          fl.max_f = std::max(fl.max_f, F.f);
+          fl.max_b = std::max(fl.max_b, F.b);
+          fl.b2 += double(F.b) * F.b;
+          fl.lu_elems += 0.5 * double(F.s) * F.s + double(F.s) * F.b;
         }
         h->flev.push_back(fl);
       }
@@ -510,6 +548,7 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
   if (!h->device_ready) return H2SP_ESTATE;
   if (prec != H2SP_FP64 && prec != H2SP_FP32) return H2SP_EINVAL;
   h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->prof.stream = h->stream;
   const Plan &p = h->plan;
   cudaStream_t s = h->stream;
   try {
@@ -528,22 +567,25 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
     ck(cudaMemsetAsync(h->fronts, 0, size_t(std::max<int64_t>(p.front_elems, 1)) * esz, s));
     ck(cudaMemsetAsync(h->err, 0, sizeof(int), s));
     const int64_t na = int64_t(p.assemble.size());
+    const double abytes = double(p.s_elems) * double(sizeof(double) + esz);
     if (prec == H2SP_FP64) {
       double *F = static_cast<double *>(h->fronts);
-      ck(launch_assemble<double>(h->asm_items, na, h->S, F, s));
+      ck(launch_assemble<double>(h->asm_items, na, h->S, F, s, &h->prof, abytes));
       for (const FrontLevel &L : h->flev) {
-        ck(launch_lu_level<double>(h->fr + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv, h->swaps, h->err, s));
-        ck(launch_extend_add_impl<double>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s));
+        ck(launch_lu_level<double>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv,
+                                   h->swaps, h->err, s, &h->prof));
+        ck(launch_extend_add_impl<double>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s, &h->prof, L.b2));
       }
-      ck(launch_make_perm<double>(h->fr, int(p.fronts.size()), h->max_s_all, h->piv, h->perm, s));
+      ck(launch_make_perm<double>(h->fr, int(p.fronts.size()), h->max_s_all, h->piv, h->perm, s, &h->prof));
     } else {
       float *F = static_cast<float *>(h->fronts);
-      ck(launch_assemble<float>(h->asm_items, na, h->S, F, s));
+      ck(launch_assemble<float>(h->asm_items, na, h->S, F, s, &h->prof, abytes));
       for (const FrontLevel &L : h->flev) {
-        ck(launch_lu_level<float>(h->fr + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv, h->swaps, h->err, s));
-        ck(launch_extend_add_impl<float>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s));
+        ck(launch_lu_level<float>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv,
+                                  h->swaps, h->err, s, &h->prof));
+        ck(launch_extend_add_impl<float>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s, &h->prof, L.b2));
       }
-      ck(launch_make_perm<float>(h->fr, int(p.fronts.size()), h->max_s_all, h->piv, h->perm, s));
+      ck(launch_make_perm<float>(h->fr, int(p.fronts.size()), h->max_s_all, h->piv, h->perm, s, &h->prof));
     }
     int herr = 0;
     ck(cudaMemcpyAsync(&herr, h->err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -563,6 +605,7 @@ int h2sp_apply(h2sp_handle *h, int32_t op, int32_t nrhs, const double *in, int64
   const Plan &p = h->plan;
   if (ldin < p.n || ldout < p.n) return H2SP_EINVAL;
   h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->prof.stream = h->stream;
   try {
     ensure_vectors(h, nrhs);
     switch (op) {
@@ -621,6 +664,7 @@ int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *o, int32_t nrhs, const dou
     const int64_t n = p.n;
     std::vector<double> bn2(nrhs), rn2(nrhs);
     ck(launch_colnorm2(b, ldb, n, nrhs, h->norms, s));
+    h->prof.end(P_OTHER, 1, 0, 0.0);
     ck(cudaMemcpyAsync(bn2.data(), h->norms, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
     ck(cudaStreamSynchronize(s));
     const int maxit = o->maxit > 0 ? o->maxit : 50;
@@ -630,6 +674,7 @@ int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *o, int32_t nrhs, const dou
     for (;;) {
       h2_matvec(h, x, ldx, h->vecT, n, nrhs);
       ck(launch_residual(b, ldb, h->vecT, n, h->vecR, n, n, nrhs, h->norms, s));
+      h->prof.end(P_OTHER, 1, 0, 0.0);
       ck(cudaMemcpyAsync(rn2.data(), h->norms, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
       ck(cudaStreamSynchronize(s));
       res = 0.0;
@@ -637,6 +682,7 @@ int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *o, int32_t nrhs, const dou
       if (!(res > o->tol) || it >= maxit) break;
       precond(h, h->vecR, n, h->vecT, n, nrhs);
       ck(launch_axpy(h->vecT, n, x, ldx, n, nrhs, s));
+      h->prof.end(P_OTHER, 1, 0, 0.0);
       ++it;
     }
     if (info) {
@@ -727,6 +773,23 @@ int h2sp_query(const h2sp_handle *h, h2sp_stats *st) {
   st->sparsify_flops = p.sparsify_flops;
   st->factor_prec = h->prec;
   st->plan_seconds = h->plan_seconds;
+  return H2SP_OK;
+}
+
+int h2sp_profile(h2sp_handle *h, int32_t timing, int32_t reset, h2sp_kernel_times *out) {
+  if (!h) return H2SP_EINVAL;
+  if (h->device_ready) h->prof.collect();
+  if (out) {
+    std::memset(out, 0, sizeof(*out));
+    for (int c = 0; c < P_NCLASS && c < 16; ++c) {
+      out->launches[c] = h->prof.launches[c];
+      out->timed[c] = h->prof.timed[c];
+      out->ms[c] = h->prof.ms[c];
+      out->work[c] = h->prof.work[c];
+    }
+  }
+  if (reset) h->prof.reset();
+  if (timing >= 0) h->prof.timing = timing != 0 && h->device_ready;
   return H2SP_OK;
 }
 

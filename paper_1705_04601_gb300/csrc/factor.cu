@@ -472,15 +472,18 @@ struct GemmCfg<float> {
 }  // namespace
 
 template <typename T>
-cudaError_t launch_assemble(const AItem *items, int64_t n, const double *S, T *fronts, cudaStream_t s) {
+cudaError_t launch_assemble(const AItem *items, int64_t n, const double *S, T *fronts, cudaStream_t s, Prof *prof,
+                            double bytes) {
   if (n == 0) return cudaSuccess;
+  const size_t e0 = prof->begin();
   k_assemble<T><<<unsigned(n), 128, 0, s>>>(items, S, fronts);
+  prof->end(P_ASSEMBLE, 1, e0, bytes);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_lu_level(const FrontDev *fr, int nfront, int max_s, int max_f, T *fronts, int32_t *piv,
-                            int32_t *swaps, int *err, cudaStream_t s) {
+cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
+                            int32_t *piv, int32_t *swaps, int *err, cudaStream_t s, Prof *prof) {
   constexpr int NB = LuCfg<T>::NB;
   using G = GemmCfg<T>;
   auto gemm = k_gemm_update<T, G::BM, G::BN, G::TM, G::TN, NB>;
@@ -491,13 +494,30 @@ cudaError_t launch_lu_level(const FrontDev *fr, int nfront, int max_s, int max_f
     attr = true;
   }
   for (int j0 = 0; j0 < max_s; j0 += NB) {
+    // algorithmic work of this step over the active fronts
+    double fpanel = 0.0, ftrsm = 0.0, fgemm = 0.0;
+    if (prof->timing)
+      for (int k = 0; k < nfront; ++k) {
+        const Front &F = host_fr[k];
+        if (j0 >= F.s) continue;
+        const double jb = std::min(NB, F.s - j0), rows = F.f - j0, rest = F.f - j0 - jb;
+        fpanel += rows * jb * jb;         // scaling + rank-1 updates inside the panel
+        ftrsm += jb * jb * rest;          // U12 = L^-1 A12
+        fgemm += 2.0 * rest * rest * jb;  // A22 -= L21 U12
+      }
+    size_t e0 = prof->begin();
     k_panel<T, NB><<<nfront, kPanelThreads, 0, s>>>(fr, j0, fronts, piv, swaps, err);
+    prof->end(P_PANEL, 1, e0, fpanel);
     const int ncol_blocks = std::min(cdiv(max_f, 8), 4096);
+    e0 = prof->begin();
     k_swap_trsm<T, NB><<<dim3(ncol_blocks, nfront), 256, 0, s>>>(fr, j0, fronts, swaps);
+    prof->end(P_TRSM, 1, e0, ftrsm);
     const int rest = max_f - j0 - 1;
     if (rest > 0) {
       dim3 g(cdiv(rest, G::BN), cdiv(rest, G::BM), nfront);
+      e0 = prof->begin();
       gemm<<<g, 256, gsmem, s>>>(fr, j0, fronts);
+      prof->end(P_GEMM, 1, e0, fgemm);
     }
   }
   return cudaGetLastError();
@@ -505,16 +525,18 @@ cudaError_t launch_lu_level(const FrontDev *fr, int nfront, int max_s, int max_f
 
 template <typename T>
 cudaError_t launch_extend_add_impl(const FrontDev *fr_all, int lo, int nfront, int max_b, const int32_t *map,
-                                   T *fronts, cudaStream_t s) {
+                                   T *fronts, cudaStream_t s, Prof *prof, double elems) {
   if (nfront == 0 || max_b == 0) return cudaSuccess;
   dim3 g(cdiv(max_b, 32), cdiv(max_b, 32), nfront);
+  const size_t e0 = prof->begin();
   k_extend_add<T><<<g, 256, 0, s>>>(fr_all, lo, map, fronts);
+  prof->end(P_EXTEND, 1, e0, elems);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_make_perm(const FrontDev *fr, int nfront, int max_s, const int32_t *piv, int32_t *perm,
-                             cudaStream_t s) {
+                             cudaStream_t s, Prof *prof) {
   if (nfront == 0) return cudaSuccess;
   const int cap = 40 * 1024;  // entries staged in shared memory (160 KB)
   const size_t smem = sizeof(int32_t) * size_t(std::min(max_s, cap));
@@ -523,70 +545,86 @@ cudaError_t launch_make_perm(const FrontDev *fr, int nfront, int max_s, const in
     cudaFuncSetAttribute(k_make_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(int32_t) * cap));
     attr = true;
   }
+  const size_t e0 = prof->begin();
   k_make_perm<<<nfront, 256, smem, s>>>(fr, piv, perm, std::min(max_s, cap));
+  prof->end(P_OTHER, 1, e0, 0.0);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_solve_fwd_level_impl(const FrontDev *fr, int lo, int nfront, int max_s, int max_f, const T *fronts,
                                         const int32_t *perm, const int32_t *idx, T *y, int64_t ldy, int nrhs, T *work,
-                                        const int64_t *work_off, cudaStream_t s) {
+                                        const int64_t *work_off, cudaStream_t s, Prof *prof, double bytes) {
   if (nfront == 0) return cudaSuccess;
   const FrontDev *frl = fr + lo;
+  const size_t e0 = prof->begin();
+  int nl = 2;
   k_fwd_gather<T><<<dim3(cdiv(max_f, 256), nfront), 256, 0, s>>>(frl, perm, idx, y, ldy, nrhs, work, work_off, lo);
   for (int c0 = 0; c0 < max_s; c0 += kBS) {
     k_diag_solve<T, false><<<nfront, 256, 0, s>>>(frl, c0, fronts, nrhs, work, work_off, lo);
     const int rest = max_f - c0 - 1;
-    if (rest > 0)
+    ++nl;
+    if (rest > 0) {
       k_fwd_update<T><<<dim3(cdiv(rest, kRowsPerCta), nfront), kRowsPerCta, 0, s>>>(frl, c0, fronts, nrhs, work,
                                                                                    work_off, lo);
+      ++nl;
+    }
   }
   k_fwd_scatter<T><<<dim3(cdiv(max_f, 256), nfront), 256, 0, s>>>(frl, idx, y, ldy, nrhs, work, work_off, lo);
+  prof->end(P_SOLVE, nl, e0, bytes);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, int max_s, int max_f, const T *fronts,
                                         const int32_t *idx, T *y, int64_t ldy, int nrhs, T *work,
-                                        const int64_t *work_off, cudaStream_t s) {
+                                        const int64_t *work_off, cudaStream_t s, Prof *prof, double bytes) {
   if (nfront == 0) return cudaSuccess;
   const FrontDev *frl = fr + lo;
+  const size_t e0 = prof->begin();
+  int nl = 3;
   k_bwd_gather<T><<<dim3(cdiv(max_f, 256), nfront), 256, 0, s>>>(frl, idx, y, ldy, nrhs, work, work_off, lo);
   k_bwd_u12<T><<<dim3(cdiv(max_s, kRowsPerCta), nfront), kRowsPerCta, 0, s>>>(frl, fronts, nrhs, work, work_off, lo);
   const int last = ((max_s - 1) / kBS) * kBS;
   for (int c0 = last; c0 >= 0; c0 -= kBS) {
     k_diag_solve<T, true><<<nfront, 256, 0, s>>>(frl, c0, fronts, nrhs, work, work_off, lo);
-    if (c0 > 0)
+    ++nl;
+    if (c0 > 0) {
       k_bwd_update<T><<<dim3(cdiv(c0, kRowsPerCta), nfront), kRowsPerCta, 0, s>>>(frl, c0, fronts, nrhs, work,
                                                                                 work_off, lo);
+      ++nl;
+    }
   }
   k_bwd_scatter<T><<<dim3(cdiv(max_s, 256), nfront), 256, 0, s>>>(frl, idx, y, ldy, nrhs, work, work_off, lo);
+  prof->end(P_SOLVE, nl, e0, bytes);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_assemble<double>(const AItem *, int64_t, const double *, double *, cudaStream_t);
-template cudaError_t launch_assemble<float>(const AItem *, int64_t, const double *, float *, cudaStream_t);
-template cudaError_t launch_lu_level<double>(const FrontDev *, int, int, int, double *, int32_t *, int32_t *, int *,
-                                             cudaStream_t);
-template cudaError_t launch_lu_level<float>(const FrontDev *, int, int, int, float *, int32_t *, int32_t *, int *,
-                                            cudaStream_t);
-template cudaError_t launch_make_perm<double>(const FrontDev *, int, int, const int32_t *, int32_t *, cudaStream_t);
-template cudaError_t launch_make_perm<float>(const FrontDev *, int, int, const int32_t *, int32_t *, cudaStream_t);
-template cudaError_t launch_extend_add_impl<double>(const FrontDev *, int, int, int, const int32_t *, double *,
-                                                    cudaStream_t);
-template cudaError_t launch_extend_add_impl<float>(const FrontDev *, int, int, int, const int32_t *, float *,
-                                                   cudaStream_t);
-template cudaError_t launch_solve_fwd_level_impl<double>(const FrontDev *, int, int, int, int, const double *,
-                                                         const int32_t *, const int32_t *, double *, int64_t, int,
-                                                         double *, const int64_t *, cudaStream_t);
-template cudaError_t launch_solve_fwd_level_impl<float>(const FrontDev *, int, int, int, int, const float *,
-                                                        const int32_t *, const int32_t *, float *, int64_t, int,
-                                                        float *, const int64_t *, cudaStream_t);
-template cudaError_t launch_solve_bwd_level_impl<double>(const FrontDev *, int, int, int, int, const double *,
-                                                         const int32_t *, double *, int64_t, int, double *,
-                                                         const int64_t *, cudaStream_t);
-template cudaError_t launch_solve_bwd_level_impl<float>(const FrontDev *, int, int, int, int, const float *,
-                                                        const int32_t *, float *, int64_t, int, float *,
-                                                        const int64_t *, cudaStream_t);
+template cudaError_t launch_assemble<double>(const AItem *, int64_t, const double *, double *, cudaStream_t, Prof *,
+                                           double);
+template cudaError_t launch_lu_level<double>(const FrontDev *, const Front *, int, int, int, double *, int32_t *, int32_t *,
+                                           int *, cudaStream_t, Prof *);
+template cudaError_t launch_make_perm<double>(const FrontDev *, int, int, const int32_t *, int32_t *, cudaStream_t, Prof *);
+template cudaError_t launch_extend_add_impl<double>(const FrontDev *, int, int, int, const int32_t *, double *, cudaStream_t,
+                                                  Prof *, double);
+template cudaError_t launch_solve_fwd_level_impl<double>(const FrontDev *, int, int, int, int, const double *, const int32_t *,
+                                                       const int32_t *, double *, int64_t, int, double *, const int64_t *,
+                                                       cudaStream_t, Prof *, double);
+template cudaError_t launch_solve_bwd_level_impl<double>(const FrontDev *, int, int, int, int, const double *, const int32_t *,
+                                                       double *, int64_t, int, double *, const int64_t *, cudaStream_t, Prof *,
+                                                       double);
+template cudaError_t launch_assemble<float>(const AItem *, int64_t, const double *, float *, cudaStream_t, Prof *,
+                                           double);
+template cudaError_t launch_lu_level<float>(const FrontDev *, const Front *, int, int, int, float *, int32_t *, int32_t *,
+                                           int *, cudaStream_t, Prof *);
+template cudaError_t launch_make_perm<float>(const FrontDev *, int, int, const int32_t *, int32_t *, cudaStream_t, Prof *);
+template cudaError_t launch_extend_add_impl<float>(const FrontDev *, int, int, int, const int32_t *, float *, cudaStream_t,
+                                                  Prof *, double);
+template cudaError_t launch_solve_fwd_level_impl<float>(const FrontDev *, int, int, int, int, const float *, const int32_t *,
+                                                       const int32_t *, float *, int64_t, int, float *, const int64_t *,
+                                                       cudaStream_t, Prof *, double);
+template cudaError_t launch_solve_bwd_level_impl<float>(const FrontDev *, int, int, int, int, const float *, const int32_t *,
+                                                       float *, int64_t, int, float *, const int64_t *, cudaStream_t, Prof *,
+                                                       double);
 
 }  // namespace h2sp

@@ -132,6 +132,82 @@ struct Plan {
   int64_t xh_elems = 0;
 };
 
+// Kernel classes of the per-launch profiler (h2sp_profile).
+enum ProfClass : int {
+  P_GEMM = 0,        // trailing update of the fronts
+  P_PANEL = 1,       // panel factorization with pivoting
+  P_TRSM = 2,        // row swaps + U12 triangular solve
+  P_EXTEND = 3,      // extend-add into parent fronts
+  P_ASSEMBLE = 4,    // S blocks into fronts
+  P_TRANSFORM = 5,   // close blocks / panels Q^T X Q (sparsification)
+  P_HOUSEHOLDER = 6, // basis completions
+  P_COUPLING = 7,    // coupling projections and W stacking
+  P_SOLVE = 8,       // triangular solves with the fronts
+  P_MATVEC = 9,      // FP64 H^2 product
+  P_APPLY = 10,      // U^T / V applies
+  P_OTHER = 11,      // vector kernels, casts, permutations
+  P_NCLASS = 12
+};
+
+// Counts every launch; when `timing` is on, brackets launches with CUDA events
+// on the launching stream and accumulates their durations per class.
+struct Prof {
+  bool timing = false;
+  cudaStream_t stream = nullptr;
+  int64_t launches[P_NCLASS] = {};
+  int64_t timed[P_NCLASS] = {};
+  double ms[P_NCLASS] = {};
+  double work[P_NCLASS] = {};
+  std::vector<cudaEvent_t> ev;
+  size_t used = 0;
+  struct Rec {
+    int cls;
+    size_t e0, e1;
+    double w;
+  };
+  std::vector<Rec> recs;
+  size_t begin() {
+    if (!timing) return 0;
+    return take();
+  }
+  void end(int cls, int nlaunch, size_t e0, double w) {
+    launches[cls] += nlaunch;
+    if (!timing) return;
+    recs.push_back(Rec{cls, e0, take(), w});
+  }
+  size_t take() {
+    if (used == ev.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      ev.push_back(e);
+    }
+    cudaEventRecord(ev[used], stream);
+    return used++;
+  }
+  void collect() {
+    if (recs.empty()) {
+      used = 0;
+      return;
+    }
+    cudaEventSynchronize(ev[used - 1]);
+    for (const Rec &r : recs) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[r.e0], ev[r.e1]);
+      ms[r.cls] += t;
+      timed[r.cls] += 1;
+      work[r.cls] += r.w;
+    }
+    recs.clear();
+    used = 0;
+  }
+  void reset() {
+    for (int i = 0; i < P_NCLASS; ++i) launches[i] = timed[i] = 0, ms[i] = work[i] = 0.0;
+  }
+  ~Prof() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+};
+
 // Validate the descriptor and build the plan.  Returns an h2sp_status.
 int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbers = true);
 

@@ -9,12 +9,14 @@ namespace h2sp {
 
 // ---- sparsification (sparsify.cu), FP64 ----
 cudaError_t launch_householder(const QItem *items, int n, const double *w_in, const double *w_buf, double *Q,
-                               double *Rr, int max_m, int max_k, cudaStream_t s);
-cudaError_t launch_stack_w(const WItem *items, int n, const double *Rr, const double *T, double *W, cudaStream_t s);
+                               double *Rr, int max_m, int max_k, cudaStream_t s, Prof *prof);
+cudaError_t launch_stack_w(const WItem *items, int n, const double *Rr, const double *T, double *W, cudaStream_t s,
+                           Prof *prof);
 cudaError_t launch_coupling(const CItem *items, int n, const double *Rr, const double *Rrc, const double *Dc,
-                            double *const *dst_base, int max_k, cudaStream_t s);
+                            double *const *dst_base, int max_k, cudaStream_t s, Prof *prof);
 cudaError_t launch_transform(const XItem *items, int n, const double *const *src_base, const double *Qrow,
-                             const double *Qcol, double *const *dst_base, cudaStream_t s);
+                             const double *Qcol, double *const *dst_base, cudaStream_t s, Prof *prof,
+                             double flops);
 
 // ---- block LU of S (factor.cu), T = double or float ----
 struct FrontDev {
@@ -38,28 +40,29 @@ struct LuCfg<float> {
 constexpr int kMaxSwapRows = 2 * 64;
 
 template <typename T>
-cudaError_t launch_assemble(const AItem *items, int64_t n, const double *S, T *fronts, cudaStream_t s);
+cudaError_t launch_assemble(const AItem *items, int64_t n, const double *S, T *fronts, cudaStream_t s, Prof *prof,
+                            double bytes);
 template <typename T>
-cudaError_t launch_lu_level(const FrontDev *fr, int nfront, int max_s, int max_f, T *fronts, int32_t *piv,
-                            int32_t *swaps, int *err, cudaStream_t s);
+cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
+                            int32_t *piv, int32_t *swaps, int *err, cudaStream_t s, Prof *prof);
 template <typename T>
 cudaError_t launch_extend_add_impl(const FrontDev *fr_all, int lo, int nfront, int max_b, const int32_t *map,
-                                   T *fronts, cudaStream_t s);
+                                   T *fronts, cudaStream_t s, Prof *prof, double elems);
 template <typename T>
 cudaError_t launch_make_perm(const FrontDev *fr, int nfront, int max_s, const int32_t *piv, int32_t *perm,
-                             cudaStream_t s);
+                             cudaStream_t s, Prof *prof);
 // Forward sweep for one level (fronts [lo, lo+nfront) of fr): gathers y into
 // the fronts' work vectors, solves with L, stores z (supernode part) back into
 // y and adds -L21 z into the boundary rows of y.
 template <typename T>
 cudaError_t launch_solve_fwd_level_impl(const FrontDev *fr, int lo, int nfront, int max_s, int max_f, const T *fronts,
                                         const int32_t *perm, const int32_t *idx, T *y, int64_t ldy, int nrhs, T *work,
-                                        const int64_t *work_off, cudaStream_t s);
+                                        const int64_t *work_off, cudaStream_t s, Prof *prof, double bytes);
 // Backward sweep for one level: x_s = U11^-1 (z - U12 x_b), stored into y.
 template <typename T>
 cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, int max_s, int max_f, const T *fronts,
                                         const int32_t *idx, T *y, int64_t ldy, int nrhs, T *work,
-                                        const int64_t *work_off, cudaStream_t s);
+                                        const int64_t *work_off, cudaStream_t s, Prof *prof, double bytes);
 
 // ---- applies, H^2 product, vector kernels (apply.cu) ----
 struct ApItem {

@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(kThreads) k_transform(const XItem *__restrict_
 }  // namespace
 
 cudaError_t launch_householder(const QItem *items, int n, const double *w_in, const double *w_buf, double *Q,
-                               double *Rr, int max_m, int max_k, cudaStream_t s) {
+                               double *Rr, int max_m, int max_k, cudaStream_t s, Prof *prof) {
   if (n == 0) return cudaSuccess;
   size_t smem = sizeof(double) * (size_t(max_m) * max_k + size_t(max_m) * max_m + kMaxRank + 1 + 64);
   static bool attr_done = false;
@@ -242,18 +242,23 @@ cudaError_t launch_householder(const QItem *items, int n, const double *w_in, co
     cudaFuncSetAttribute(k_householder, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_done = true;
   }
+  const size_t e0 = prof->begin();
   k_householder<<<n, kThreads, smem, s>>>(items, w_in, w_buf, Q, Rr);
+  prof->end(P_HOUSEHOLDER, 1, e0, 0.0);
   return cudaGetLastError();
 }
 
-cudaError_t launch_stack_w(const WItem *items, int n, const double *Rr, const double *T, double *W, cudaStream_t s) {
+cudaError_t launch_stack_w(const WItem *items, int n, const double *Rr, const double *T, double *W, cudaStream_t s,
+                           Prof *prof) {
   if (n == 0) return cudaSuccess;
+  const size_t e0 = prof->begin();
   k_stack_w<<<n, 64, 0, s>>>(items, Rr, T, W);
+  prof->end(P_COUPLING, 1, e0, 0.0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_coupling(const CItem *items, int n, const double *Rr, const double *Rrc, const double *Dc,
-                            double *const *dst_base, int max_k, cudaStream_t s) {
+                            double *const *dst_base, int max_k, cudaStream_t s, Prof *prof) {
   if (n == 0) return cudaSuccess;
   size_t smem = sizeof(double) * 4 * size_t(max_k) * max_k;
   static bool attr_done = false;
@@ -261,12 +266,14 @@ cudaError_t launch_coupling(const CItem *items, int n, const double *Rr, const d
     cudaFuncSetAttribute(k_coupling, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_done = true;
   }
+  const size_t e0 = prof->begin();
   k_coupling<<<n, 128, smem, s>>>(items, Rr, Rrc, Dc, dst_base);
+  prof->end(P_COUPLING, 1, e0, 0.0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_transform(const XItem *items, int n, const double *const *src_base, const double *Qrow,
-                             const double *Qcol, double *const *dst_base, cudaStream_t s) {
+                             const double *Qcol, double *const *dst_base, cudaStream_t s, Prof *prof, double flops) {
   if (n == 0) return cudaSuccess;
   size_t smem = sizeof(double) * 3 * size_t(kMaxBlock) * kMaxBlock;
   static bool attr_done = false;
@@ -274,7 +281,9 @@ cudaError_t launch_transform(const XItem *items, int n, const double *const *src
     cudaFuncSetAttribute(k_transform, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     attr_done = true;
   }
+  const size_t e0 = prof->begin();
   k_transform<<<n, kThreads, smem, s>>>(items, src_base, Qrow, Qcol, dst_base);
+  prof->end(P_TRANSFORM, 1, e0, flops);
   return cudaGetLastError();
 }
 

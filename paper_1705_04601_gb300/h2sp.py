@@ -65,6 +65,14 @@ class Stats(ctypes.Structure):
     ]
 
 
+class KernelTimes(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 16), ("timed", ctypes.c_int64 * 16), ("ms", ctypes.c_double * 16),
+                ("work", ctypes.c_double * 16)]
+
+
+KERNEL_CLASSES = ["gemm_update", "panel", "swap_trsm", "extend_add", "assemble", "transform", "householder",
+                  "coupling", "solve", "h2_matvec", "apply", "vector"]
+
 # name -> (restype, argtypes); every symbol of include/h2sp.h
 SIGNATURES = {
     "h2sp_sparsify": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.POINTER(Opts), _vp, ctypes.POINTER(_vp)]),
@@ -78,6 +86,7 @@ SIGNATURES = {
     "h2sp_export_Q": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _i64p, _f64p, _vp]),
     "h2sp_export_structure": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i64p]),
     "h2sp_query": (ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
+    "h2sp_profile": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(KernelTimes)]),
     "h2sp_destroy": (None, [_vp]),
     "h2sp_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
     "h2sp_last_cuda_error": (ctypes.c_char_p, []),
@@ -216,9 +225,13 @@ def h2sp_factor(h: Handle, prec: int = H2SP_FP64, stream=None):
 
 
 def _cols(t, n):
+    """(nrhs, leading dimension) of a (nrhs, n) or (n,) tensor; rows must be contiguous."""
     if t.dim() == 1:
         return 1, n
-    return int(t.shape[0]), int(t.stride(0))
+    if int(t.shape[1]) != n or (int(t.shape[1]) > 1 and int(t.stride(1)) != 1):
+        raise ValueError("expected a (nrhs, n) tensor with contiguous rows")
+    nrhs = int(t.shape[0])
+    return nrhs, (n if nrhs == 1 else int(t.stride(0)))
 
 
 def h2sp_solve(h: Handle, b, x, mode: int = H2SP_DIRECT, tol: float = 1e-10, maxit: int = 50, restart: int = 30,
@@ -290,6 +303,14 @@ def h2sp_export_structure(h: Handle) -> dict:
                                                  "bnd_ptr", "bnd")], ctypes.byref(nb)), "h2sp_export_structure")
     out["bnd"] = out["bnd"][:nb.value]
     return out
+
+
+def h2sp_profile(h: Handle, timing: int = -1, reset: bool = False) -> dict:
+    """Per-kernel-class counters: {class: {launches, timed, ms, work}}."""
+    kt = KernelTimes()
+    _check(lib().h2sp_profile(h.ptr, int(timing), int(bool(reset)), ctypes.byref(kt)), "h2sp_profile")
+    return {nm: dict(launches=int(kt.launches[i]), timed=int(kt.timed[i]), ms=float(kt.ms[i]), work=float(kt.work[i]))
+            for i, nm in enumerate(KERNEL_CLASSES)}
 
 
 def h2sp_destroy(h: Handle):
