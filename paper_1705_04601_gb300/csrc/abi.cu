@@ -266,7 +266,7 @@ void solve_S(h2sp_handle *h, double *y, int nrhs) {
     ck(launch_cast_d2f(y, n, h->yf, n, n, nrhs, h->stream));
     solve_S_T<float>(h, h->yf, nrhs);
     ck(launch_cast_f2d(h->yf, n, y, n, n, nrhs, h->stream));
-    h->prof.end(P_OTHER, 2, 0, 0.0);
+    h->prof.count(P_OTHER, 2);
   }
 }
 
@@ -664,7 +664,7 @@ int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *o, int32_t nrhs, const dou
     const int64_t n = p.n;
     std::vector<double> bn2(nrhs), rn2(nrhs);
     ck(launch_colnorm2(b, ldb, n, nrhs, h->norms, s));
-    h->prof.end(P_OTHER, 1, 0, 0.0);
+    h->prof.count(P_OTHER, 1);
     ck(cudaMemcpyAsync(bn2.data(), h->norms, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
     ck(cudaStreamSynchronize(s));
     const int maxit = o->maxit > 0 ? o->maxit : 50;
@@ -674,7 +674,7 @@ int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *o, int32_t nrhs, const dou
     for (;;) {
       h2_matvec(h, x, ldx, h->vecT, n, nrhs);
       ck(launch_residual(b, ldb, h->vecT, n, h->vecR, n, n, nrhs, h->norms, s));
-      h->prof.end(P_OTHER, 1, 0, 0.0);
+      h->prof.count(P_OTHER, 1);
       ck(cudaMemcpyAsync(rn2.data(), h->norms, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
       ck(cudaStreamSynchronize(s));
       res = 0.0;
@@ -682,7 +682,7 @@ int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *o, int32_t nrhs, const dou
       if (!(res > o->tol) || it >= maxit) break;
       precond(h, h->vecR, n, h->vecT, n, nrhs);
       ck(launch_axpy(h->vecT, n, x, ldx, n, nrhs, s));
-      h->prof.end(P_OTHER, 1, 0, 0.0);
+      h->prof.count(P_OTHER, 1);
       ++it;
     }
     if (info) {

@@ -17,6 +17,8 @@
 #include <climits>
 #include <cstdint>
 
+#include <cooperative_groups.h>
+
 #include "kernels.h"
 
 namespace h2sp {
@@ -132,6 +134,153 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel(const FrontDev *__restr
     }
     sw[0] = nr;
   }
+}
+
+// Net row movement of one panel's swaps (rows j0 .. j0+jb-1 exchanged with
+// their pivot rows, in order): new_row[rows[q]] = old_row[src[q]].
+__device__ void compose_swaps(const int32_t *pv, int j0, int jb, int32_t *sw) {
+  int nr = 0;
+  int32_t *rows = sw + 1, *src = sw + 1 + kMaxSwapRows;
+  for (int j = 0; j < jb; ++j) {
+    const int a = j0 + j, b = pv[a];
+    if (a == b) continue;
+    int ia = -1, ib = -1;
+    for (int q = 0; q < nr; ++q) {
+      if (rows[q] == a) ia = q;
+      if (rows[q] == b) ib = q;
+    }
+    if (ia < 0) rows[nr] = a, src[nr] = a, ia = nr++;
+    if (ib < 0) rows[nr] = b, src[nr] = b, ib = nr++;
+    const int32_t t = src[ia];
+    src[ia] = src[ib];
+    src[ib] = t;
+  }
+  sw[0] = nr;
+}
+
+constexpr int kClusterPanelThreads = 512;
+
+// Panel factorization by one thread-block cluster per front.  The panel
+// rows [j0, f) are split into C contiguous chunks, one per CTA, held in
+// shared memory for the whole panel.  Per column: local argmax over the
+// supernode rows, cluster barrier, every CTA reduces the C candidates read
+// through distributed shared memory, reads the pivot row remotely, cluster
+// barrier, the owners of the two rows swap them, and every CTA updates its
+// own rows.  Cluster barriers are hardware barriers of co-scheduled CTAs.
+template <typename T, int NB>
+__global__ void __launch_bounds__(kClusterPanelThreads) k_panel_cluster(const FrontDev *__restrict__ fr, int j0,
+                                                                        T *__restrict__ fronts, int32_t *__restrict__ piv,
+                                                                        int32_t *__restrict__ swaps, int *__restrict__ err) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = int(cluster.num_blocks());
+  const int rank = int(cluster.block_rank());
+  const int fi = blockIdx.x / C;
+  const FrontDev F = fr[fi];
+  if (j0 >= F.s) return;  // uniform over the cluster: no barrier is ever entered
+  const int jb = min(NB, F.s - j0);
+  T *A = fronts + F.off;
+  const int64_t ld = F.f;
+  const int R = F.f - j0;
+  const int per = (R + C - 1) / C;
+  const int r_lo = j0 + rank * per;
+  const int nr = max(0, min(F.f, r_lo + per) - r_lo);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *P = reinterpret_cast<T *>(smraw);  // [NB][per], column c at P + c * per
+  __shared__ T cand_v;
+  __shared__ int cand_i;
+  __shared__ T urow[NB], tmp[NB];
+  __shared__ T redv[kClusterPanelThreads / 32];
+  __shared__ int redi[kClusterPanelThreads / 32];
+  __shared__ int s_p;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  for (int e = tid; e < nr * jb; e += nt) {
+    const int i = e % nr, c = e / nr;
+    P[c * per + i] = A[(r_lo + i) + int64_t(j0 + c) * ld];
+  }
+  __syncthreads();
+  for (int j = 0; j < jb; ++j) {
+    const int col = j0 + j;
+    // local candidates: supernode rows >= col owned by this CTA
+    T bv = T(-1);
+    int bi = INT_MAX;
+    const int i_lo = max(col, r_lo) - r_lo, i_hi = min(F.s, r_lo + nr) - r_lo;
+    for (int i = i_lo + tid; i < i_hi; i += nt) {
+      const T v = tabs(P[j * per + i]);
+      if (v > bv) bv = v, bi = r_lo + i;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) bv = ov, bi = oi;
+    }
+    if (lane == 0) redv[wid] = bv, redi[wid] = bi;
+    __syncthreads();
+    if (tid == 0) {
+      T v = redv[0];
+      int i = redi[0];
+      for (int w = 1; w < (nt >> 5); ++w)
+        if (redv[w] > v || (redv[w] == v && redi[w] < i)) v = redv[w], i = redi[w];
+      cand_v = v;
+      cand_i = i;
+    }
+    cluster.sync();
+    if (tid == 0) {
+      T v = T(-1);
+      int i = INT_MAX;
+      for (int q = 0; q < C; ++q) {
+        const T qv = *cluster.map_shared_rank(&cand_v, q);
+        const int qi = *cluster.map_shared_rank(&cand_i, q);
+        if (qv > v || (qv == v && qi < i)) v = qv, i = qi;
+      }
+      if (i == INT_MAX) {  // no finite candidate
+        i = col;
+        if (rank == 0) atomicOr(err, 2);
+      }
+      s_p = i;
+      if (rank == 0) piv[F.piv_off + col] = i;
+    }
+    __syncthreads();
+    const int p = s_p;
+    const int own_p = (p - j0) / per, own_c = (col - j0) / per;
+    const T *Pp = cluster.map_shared_rank(P, own_p);
+    for (int c = tid; c < jb; c += nt) urow[c] = Pp[c * per + (p - (j0 + own_p * per))];
+    if (rank == own_p && p != col) {
+      const T *Pc = cluster.map_shared_rank(P, own_c);
+      for (int c = tid; c < jb; c += nt) tmp[c] = Pc[c * per + (col - (j0 + own_c * per))];
+    }
+    cluster.sync();
+    if (p != col) {
+      if (rank == own_c)
+        for (int c = tid; c < jb; c += nt) P[c * per + (col - r_lo)] = urow[c];
+      if (rank == own_p)
+        for (int c = tid; c < jb; c += nt) P[c * per + (p - r_lo)] = tmp[c];
+    }
+    __syncthreads();
+    const T pv = urow[j];
+    if (pv == T(0)) {
+      if (tid == 0 && rank == 0) atomicOr(err, 1);
+    } else {
+      const T inv = T(1) / pv;
+      for (int i = max(col + 1, r_lo) - r_lo + tid; i < nr; i += nt) {
+        const T l = P[j * per + i] * inv;
+        P[j * per + i] = l;
+        for (int c = j + 1; c < jb; ++c) P[c * per + i] -= l * urow[c];
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nr * jb; e += nt) {
+    const int i = e % nr, c = e / nr;
+    A[(r_lo + i) + int64_t(j0 + c) * ld] = P[c * per + i];
+  }
+  if (rank == 0 && tid == 0) {
+    __threadfence_block();
+    compose_swaps(piv + F.piv_off, j0, jb, swaps + int64_t(fi) * (1 + 2 * kMaxSwapRows));
+  }
+  // no CTA may exit while others can still read its shared memory
+  cluster.sync();
 }
 
 template <typename T, int NB>
@@ -469,6 +618,50 @@ struct GemmCfg<float> {
   static constexpr int BM = 128, BN = 128, TM = 8, TN = 8;
 };
 
+// Cluster size for a panel of R rows: the smallest C (rows per CTA near 512)
+// that fits the shared-memory budget, up to the largest cluster this device
+// schedules with that budget; 0 means "use the single-CTA kernel".
+template <typename T, int NB>
+int panel_cluster_size(int R) {
+  constexpr size_t kSmemCap = 200 * 1024;
+  static int cmax = -1;
+  if (cmax < 0) {
+    auto k = k_panel_cluster<T, NB>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemCap));
+    cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cmax = 0;
+    for (int c : {16, 8}) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(unsigned(c));
+      cfg.blockDim = dim3(kClusterPanelThreads);
+      cfg.dynamicSmemBytes = kSmemCap;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = unsigned(c);
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) == cudaSuccess && n > 0) {
+        cmax = c;
+        break;
+      }
+    }
+    cudaGetLastError();
+  }
+  if (cmax <= 0 || R <= 0) return 0;
+  const size_t row_bytes = sizeof(T) * NB;
+  const int cap_rows = int(kSmemCap / row_bytes);
+  int C = std::max(1, (R + 511) / 512);
+  C = std::max(C, (R + cap_rows - 1) / cap_rows);
+  if (C > cmax) return 0;
+  // round up to a divisor-friendly power of two
+  int c2 = 1;
+  while (c2 < C) c2 <<= 1;
+  return c2 <= cmax ? c2 : C;
+}
+
 }  // namespace
 
 template <typename T>
@@ -506,7 +699,27 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
         fgemm += 2.0 * rest * rest * jb;  // A22 -= L21 U12
       }
     size_t e0 = prof->begin();
-    k_panel<T, NB><<<nfront, kPanelThreads, 0, s>>>(fr, j0, fronts, piv, swaps, err);
+    const int R = max_f - j0;
+    const int C = panel_cluster_size<T, NB>(R);
+    if (C > 0) {
+      const int per = (R + C - 1) / C;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(unsigned(nfront * C));
+      cfg.blockDim = dim3(kClusterPanelThreads);
+      cfg.dynamicSmemBytes = sizeof(T) * size_t(NB) * per;
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = unsigned(C);
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      cudaError_t le = cudaLaunchKernelEx(&cfg, k_panel_cluster<T, NB>, fr, j0, fronts, piv, swaps, err);
+      if (le != cudaSuccess) return le;
+    } else {
+      k_panel<T, NB><<<nfront, kPanelThreads, 0, s>>>(fr, j0, fronts, piv, swaps, err);
+    }
     prof->end(P_PANEL, 1, e0, fpanel);
     const int ncol_blocks = std::min(cdiv(max_f, 8), 4096);
     e0 = prof->begin();

@@ -175,6 +175,7 @@ struct Prof {
     if (!timing) return;
     recs.push_back(Rec{cls, e0, take(), w});
   }
+  void count(int cls, int nlaunch) { launches[cls] += nlaunch; }
   size_t take() {
     if (used == ev.size()) {
       cudaEvent_t e;
