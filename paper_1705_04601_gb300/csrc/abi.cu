@@ -83,7 +83,7 @@ struct h2sp_handle {
   std::vector<FrontLevel> flev;
   int max_s_all = 0;
   int64_t *work_off = nullptr;
-  void *work = nullptr;
+  void *work = nullptr, *zbuf = nullptr, *dinv = nullptr;
   float *yf = nullptr;
   int work_rhs = 0;
   // H^2 product
@@ -229,6 +229,7 @@ void ensure_work(h2sp_handle *h, int nrhs) {
     }
     h->work_off = h->upload(off);
     h->work = h->alloc<double>(size_t(std::max<int64_t>(acc, 1)));
+    h->zbuf = h->alloc<double>(size_t(std::max<int64_t>(acc, 1)));
   }
   if (h->work_rhs < nrhs) {
     h->yf = h->alloc<float>(size_t(h->plan.n) * nrhs);
@@ -242,16 +243,19 @@ void solve_S_T(h2sp_handle *h, T *y, int nrhs) {
   const Plan &p = h->plan;
   T *fronts = static_cast<T *>(h->fronts);
   T *work = static_cast<T *>(h->work);
+  T *zbuf = static_cast<T *>(h->zbuf);
+  const T *dinv = static_cast<const T *>(h->dinv);
   for (int r0 = 0; r0 < nrhs; r0 += kSolveRhs) {
     const int nr = std::min(kSolveRhs, nrhs - r0);
     T *yr = y + int64_t(r0) * p.n;
     for (const FrontLevel &L : h->flev)
-      ck(launch_solve_fwd_level_impl<T>(h->fr, L.lo, L.hi - L.lo, L.max_s, L.max_f, fronts, h->perm, h->fidx, yr,
-                                        p.n, nr, work, h->work_off, h->stream, &h->prof, L.lu_elems * sizeof(T)));
+      ck(launch_solve_fwd_level_impl<T>(h->fr, L.lo, L.hi - L.lo, L.max_s, L.max_f, fronts, dinv, h->perm, h->fidx,
+                                        yr, p.n, nr, work, zbuf, h->work_off, h->stream, &h->prof,
+                                        L.lu_elems * sizeof(T)));
     for (int i = int(h->flev.size()) - 1; i >= 0; --i) {
       const FrontLevel &L = h->flev[i];
-      ck(launch_solve_bwd_level_impl<T>(h->fr, L.lo, L.hi - L.lo, L.max_s, L.max_f, fronts, h->fidx, yr, p.n, nr,
-                                        work, h->work_off, h->stream, &h->prof, L.lu_elems * sizeof(T)));
+      ck(launch_solve_bwd_level_impl<T>(h->fr, L.lo, L.hi - L.lo, L.max_s, L.max_f, fronts, dinv, h->fidx, yr, p.n,
+                                        nr, work, zbuf, h->work_off, h->stream, &h->prof, L.lu_elems * sizeof(T)));
     }
   }
 }
@@ -490,7 +494,7 @@ int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream s
       std::vector<FrontDev> fd(p.fronts.size());
       for (size_t k = 0; k < p.fronts.size(); ++k) {
         const Front &F = p.fronts[k];
-        fd[k] = FrontDev{F.off, F.piv_off, F.idx_off, F.map_off, F.s, F.b, F.f, F.parent};
+        fd[k] = FrontDev{F.off, F.piv_off, F.idx_off, F.map_off, F.dinv_off, F.s, F.b, F.f, F.parent};
         h->max_s_all = std::max(h->max_s_all, F.s);
       }
       h->fr = h->upload(fd);
@@ -562,6 +566,7 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
       for (const FrontLevel &L : h->flev) maxn = std::max<size_t>(maxn, size_t(L.hi - L.lo));
       h->swaps = h->alloc<int32_t>(maxn * (1 + 2 * kMaxSwapRows));
       h->err = h->alloc<int>(1);
+      h->dinv = h->alloc<double>(size_t(std::max<int64_t>(p.dinv_elems, 1)));
     }
     h->prec = -1;
     ck(cudaMemsetAsync(h->fronts, 0, size_t(std::max<int64_t>(p.front_elems, 1)) * esz, s));
@@ -577,6 +582,8 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
         ck(launch_extend_add_impl<double>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s, &h->prof, L.b2));
       }
       ck(launch_make_perm<double>(h->fr, int(p.fronts.size()), h->max_s_all, h->piv, h->perm, s, &h->prof));
+      ck(launch_invert_diag<double>(h->fr, int(p.fronts.size()), h->max_s_all, F, static_cast<double *>(h->dinv), s,
+                                    &h->prof));
     } else {
       float *F = static_cast<float *>(h->fronts);
       ck(launch_assemble<float>(h->asm_items, na, h->S, F, s, &h->prof, abytes));
@@ -586,6 +593,8 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
         ck(launch_extend_add_impl<float>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s, &h->prof, L.b2));
       }
       ck(launch_make_perm<float>(h->fr, int(p.fronts.size()), h->max_s_all, h->piv, h->perm, s, &h->prof));
+      ck(launch_invert_diag<float>(h->fr, int(p.fronts.size()), h->max_s_all, F, static_cast<float *>(h->dinv), s,
+                                   &h->prof));
     }
     int herr = 0;
     ck(cudaMemcpyAsync(&herr, h->err, sizeof(int), cudaMemcpyDeviceToHost, s));

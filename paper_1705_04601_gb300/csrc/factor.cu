@@ -361,13 +361,18 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
     const int c = cb + j;
     sB[k * BN + j] = (c < nrest) ? A[(j0 + k) + int64_t(t0 + c) * ld] : T(0);
   }
-  __syncthreads();
   const int tr = tid % 16, tc = tid / 16;
   T acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < TM; ++i)
+  for (int j = 0; j < TN; ++j) {
+    const int c = cb + tc + 16 * j;
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+    for (int i = 0; i < TM; ++i) {
+      const int r = rb + tr + 16 * i;
+      acc[i][j] = (c < nrest && r < nrest) ? A[(t0 + r) + int64_t(t0 + c) * ld] : T(0);
+    }
+  }
+  __syncthreads();
   for (int k = 0; k < jb; ++k) {
     T a[TM], b[TN];
 #pragma unroll
@@ -377,7 +382,7 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * b[j];
+      for (int j = 0; j < TN; ++j) acc[i][j] -= a[i] * b[j];
   }
 #pragma unroll
   for (int j = 0; j < TN; ++j) {
@@ -387,7 +392,7 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
       const int r = rb + tr + 16 * i;
-      if (r < nrest) Cc[r] -= acc[i][j];
+      if (r < nrest) Cc[r] = acc[i][j];
     }
   }
 }
@@ -434,7 +439,7 @@ __global__ void k_make_perm(const FrontDev *__restrict__ fr, const int32_t *__re
 }
 
 // ---------------- triangular solves ----------------
-constexpr int kBS = 64;     // column block of the blocked solves
+constexpr int kBS = kSolveBlock;
 constexpr int kMaxRhs = 16;
 constexpr int kRowsPerCta = 128;
 
@@ -452,128 +457,150 @@ __global__ void k_fwd_gather(const FrontDev *__restrict__ fr, const int32_t *__r
 
 template <typename T>
 __global__ void k_fwd_scatter(const FrontDev *__restrict__ fr, const int32_t *__restrict__ idx, T *__restrict__ y,
-                              int64_t ldy, int nrhs, const T *__restrict__ work, const int64_t *__restrict__ work_off,
-                              int lo) {
+                              int64_t ldy, int nrhs, const T *__restrict__ work, const T *__restrict__ zbuf,
+                              const int64_t *__restrict__ work_off, int lo) {
   const FrontDev F = fr[blockIdx.y];
   const T *W = work + work_off[lo + blockIdx.y];
+  const T *Z = zbuf + work_off[lo + blockIdx.y];
   const int32_t *ix = idx + F.idx_off;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F.f; i += gridDim.x * blockDim.x)
     for (int r = 0; r < nrhs; ++r) {
-      const T v = W[i + int64_t(r) * F.f];
       if (i < F.s)
-        y[ix[i] + r * ldy] = v;
+        y[ix[i] + r * ldy] = Z[i + int64_t(r) * F.f];
       else
-        atomicAdd(&y[ix[i] + r * ldy], v);
+        atomicAdd(&y[ix[i] + r * ldy], W[i + int64_t(r) * F.f]);
     }
 }
 
-// unit lower (fwd) or upper (bwd) solve of the diagonal block [c0, c0+cb)
-template <typename T, bool kUpper>
-__global__ void __launch_bounds__(256) k_diag_solve(const FrontDev *__restrict__ fr, int c0, const T *__restrict__ fronts,
-                                                    int nrhs, T *__restrict__ work, const int64_t *__restrict__ work_off,
-                                                    int lo) {
-  const FrontDev F = fr[blockIdx.x];
+// Inverses of the kBS x kBS diagonal blocks of L11 (unit lower) and U11
+// (upper) of every front, so that each column-block step of a triangular
+// solve is a dense product instead of a sequential substitution.
+template <typename T>
+__global__ void __launch_bounds__(kBS) k_invert_diag(const FrontDev *__restrict__ fr, const T *__restrict__ fronts,
+                                                     T *__restrict__ dinv) {
+  const FrontDev F = fr[blockIdx.y];
+  const int q = blockIdx.x;
+  const int c0 = q * kBS;
   if (c0 >= F.s) return;
   const int cb = min(kBS, F.s - c0);
+  __shared__ T D[kBS * kBS];
   const T *A = fronts + F.off;
-  T *W = work + work_off[lo + blockIdx.x];
-  __shared__ T L[kBS * kBS];
-  __shared__ T X[kBS * kMaxRhs];
-  const int tid = threadIdx.x;
-  for (int e = tid; e < cb * cb; e += blockDim.x) {
+  for (int e = threadIdx.x; e < cb * cb; e += blockDim.x) {
     const int r = e % cb, c = e / cb;
-    L[r + c * kBS] = A[(c0 + r) + int64_t(c0 + c) * F.f];
-  }
-  for (int e = tid; e < cb * nrhs; e += blockDim.x) {
-    const int r = e % cb, c = e / cb;
-    X[r + c * kBS] = W[(c0 + r) + int64_t(c) * F.f];
+    D[r + c * kBS] = A[(c0 + r) + int64_t(c0 + c) * F.f];
   }
   __syncthreads();
-  if (!kUpper) {
-    for (int i = 0; i < cb; ++i) {
-      for (int e = tid; e < (cb - i - 1) * nrhs; e += blockDim.x) {
-        const int q = i + 1 + e % (cb - i - 1), c = e / (cb - i - 1);
-        X[q + c * kBS] -= L[q + i * kBS] * X[i + c * kBS];
-      }
-      __syncthreads();
+  T *Li = dinv + F.dinv_off + int64_t(q) * 2 * kBS * kBS;
+  T *Ui = Li + kBS * kBS;
+  const int c = threadIdx.x;  // one column of each inverse per thread
+  if (c < cb) {
+    // L X = e_c (unit lower): rows c.. cb-1
+    for (int r = 0; r < c; ++r) Li[r + c * kBS] = T(0);
+    Li[c + c * kBS] = T(1);
+    for (int r = c + 1; r < cb; ++r) {
+      T acc = T(0);
+      for (int k = c; k < r; ++k) acc += D[r + k * kBS] * Li[k + c * kBS];
+      Li[r + c * kBS] = -acc;
     }
-  } else {
-    for (int i = cb - 1; i >= 0; --i) {
-      if (tid < nrhs) X[i + tid * kBS] /= L[i + i * kBS];
-      __syncthreads();
-      for (int e = tid; e < i * nrhs; e += blockDim.x) {
-        const int q = e % i, c = e / i;
-        X[q + c * kBS] -= L[q + i * kBS] * X[i + c * kBS];
-      }
-      __syncthreads();
+    // U X = e_c (upper): rows c down to 0
+    for (int r = cb - 1; r > c; --r) Ui[r + c * kBS] = T(0);
+    Ui[c + c * kBS] = T(1) / D[c + c * kBS];
+    for (int r = c - 1; r >= 0; --r) {
+      T acc = T(0);
+      for (int k = r + 1; k <= c; ++k) acc += D[r + k * kBS] * Ui[k + c * kBS];
+      Ui[r + c * kBS] = -acc / D[r + r * kBS];
     }
-  }
-  for (int e = tid; e < cb * nrhs; e += blockDim.x) {
-    const int r = e % cb, c = e / cb;
-    W[(c0 + r) + int64_t(c) * F.f] = X[r + c * kBS];
   }
 }
 
-// rows [r_lo, r_hi) of W -= A[rows, k_lo:k_hi] * W[k_lo:k_hi]
+// x = Dinv (cb x cb) * W[c0:c0+cb] into shared memory (every CTA of the step computes it)
 template <typename T>
-__device__ void block_update(const T *A, int64_t ld, T *W, int64_t ldw, int r_lo, int r_hi, int k_lo, int k_hi,
-                             int nrhs, T *sX) {
+__device__ void diag_apply(const T *Dinv, const T *W, int64_t ldw, int c0, int cb, int nrhs, T *sW, T *sX) {
   const int tid = threadIdx.x;
-  const int r = r_lo + blockIdx.x * kRowsPerCta + tid;
+  for (int e = tid; e < cb * nrhs; e += blockDim.x) {
+    const int r = e % cb, c = e / cb;
+    sW[r + c * kBS] = W[(c0 + r) + int64_t(c) * ldw];
+  }
+  __syncthreads();
+  for (int e = tid; e < cb * nrhs; e += blockDim.x) {
+    const int r = e % cb, c = e / cb;
+    T acc = T(0);
+    for (int k = 0; k < cb; ++k) acc += Dinv[r + k * kBS] * sW[k + c * kBS];
+    sX[r + c * kBS] = acc;
+  }
+  __syncthreads();
+}
+
+// rows [r_lo, r_hi) of W -= A[rows, c0:c0+cb] * sX (one row per thread, all right-hand sides)
+template <typename T>
+__device__ void slab_update(const T *A, int64_t ld, T *W, int64_t ldw, int r, int r_hi, int c0, int cb, int nrhs,
+                            const T *sX) {
+  if (r >= r_hi) return;
   T acc[kMaxRhs];
 #pragma unroll
   for (int c = 0; c < kMaxRhs; ++c) acc[c] = T(0);
-  for (int k0 = k_lo; k0 < k_hi; k0 += kBS) {
-    const int kb = min(kBS, k_hi - k0);
-    __syncthreads();
-    for (int e = tid; e < kb * nrhs; e += blockDim.x) {
-      const int q = e % kb, c = e / kb;
-      sX[q + c * kBS] = W[(k0 + q) + int64_t(c) * ldw];
-    }
-    __syncthreads();
-    if (r < r_hi) {
-      for (int q = 0; q < kb; ++q) {
-        const T a = A[r + int64_t(k0 + q) * ld];
-#pragma unroll
-        for (int c = 0; c < kMaxRhs; ++c)
-          if (c < nrhs) acc[c] += a * sX[q + c * kBS];
-      }
-    }
-  }
-  if (r < r_hi)
+  for (int q = 0; q < cb; ++q) {
+    const T a = A[r + int64_t(c0 + q) * ld];
 #pragma unroll
     for (int c = 0; c < kMaxRhs; ++c)
-      if (c < nrhs) W[r + int64_t(c) * ldw] -= acc[c];
+      if (c < nrhs) acc[c] += a * sX[q + c * kBS];
+  }
+#pragma unroll
+  for (int c = 0; c < kMaxRhs; ++c)
+    if (c < nrhs) W[r + int64_t(c) * ldw] -= acc[c];
 }
 
-// forward: rows [c0+cb, f) -= L[:, c0:c0+cb] * W[c0:c0+cb]
+// forward step of column block [c0, c0+cb): x = Linv W_c0 -> Z; rows below -= L x
 template <typename T>
-__global__ void __launch_bounds__(kRowsPerCta) k_fwd_update(const FrontDev *__restrict__ fr, int c0,
-                                                            const T *__restrict__ fronts, int nrhs, T *__restrict__ work,
-                                                            const int64_t *__restrict__ work_off, int lo) {
+__global__ void __launch_bounds__(kRowsPerCta) k_fwd_step(const FrontDev *__restrict__ fr, int c0,
+                                                          const T *__restrict__ fronts, const T *__restrict__ dinv,
+                                                          int nrhs, T *__restrict__ work, T *__restrict__ zbuf,
+                                                          const int64_t *__restrict__ work_off, int lo) {
   const FrontDev F = fr[blockIdx.y];
   if (c0 >= F.s) return;
   const int cb = min(kBS, F.s - c0);
-  const int r_lo = c0 + cb;
-  if (r_lo + int(blockIdx.x) * kRowsPerCta >= F.f) return;
-  __shared__ T sX[kBS * kMaxRhs];
-  block_update<T>(fronts + F.off, F.f, work + work_off[lo + blockIdx.y], F.f, r_lo, F.f, c0, c0 + cb, nrhs, sX);
+  const int r0 = c0 + cb + int(blockIdx.x) * kRowsPerCta;
+  if (blockIdx.x > 0 && r0 >= F.f) return;
+  __shared__ T sW[kBS * kMaxRhs], sX[kBS * kMaxRhs];
+  T *W = work + work_off[lo + blockIdx.y];
+  const T *Li = dinv + F.dinv_off + int64_t(c0 / kBS) * 2 * kBS * kBS;
+  diag_apply<T>(Li, W, F.f, c0, cb, nrhs, sW, sX);
+  if (blockIdx.x == 0) {
+    T *Z = zbuf + work_off[lo + blockIdx.y];
+    for (int e = threadIdx.x; e < cb * nrhs; e += blockDim.x) {
+      const int r = e % cb, c = e / cb;
+      Z[(c0 + r) + int64_t(c) * F.f] = sX[r + c * kBS];
+    }
+  }
+  slab_update<T>(fronts + F.off, F.f, W, F.f, r0 + threadIdx.x, F.f, c0, cb, nrhs, sX);
 }
 
-// backward: rows [0, c0) -= U[:, c0:c0+cb] * W[c0:c0+cb]
+// backward step of column block [c0, c0+cb): x = Uinv W_c0 -> Z; rows above -= U x
 template <typename T>
-__global__ void __launch_bounds__(kRowsPerCta) k_bwd_update(const FrontDev *__restrict__ fr, int c0,
-                                                            const T *__restrict__ fronts, int nrhs, T *__restrict__ work,
-                                                            const int64_t *__restrict__ work_off, int lo) {
+__global__ void __launch_bounds__(kRowsPerCta) k_bwd_step(const FrontDev *__restrict__ fr, int c0,
+                                                          const T *__restrict__ fronts, const T *__restrict__ dinv,
+                                                          int nrhs, T *__restrict__ work, T *__restrict__ zbuf,
+                                                          const int64_t *__restrict__ work_off, int lo) {
   const FrontDev F = fr[blockIdx.y];
   if (c0 >= F.s) return;
   const int cb = min(kBS, F.s - c0);
-  if (int(blockIdx.x) * kRowsPerCta >= c0) return;
-  __shared__ T sX[kBS * kMaxRhs];
-  block_update<T>(fronts + F.off, F.f, work + work_off[lo + blockIdx.y], F.f, 0, c0, c0, c0 + cb, nrhs, sX);
+  const int r0 = int(blockIdx.x) * kRowsPerCta;
+  if (blockIdx.x > 0 && r0 >= c0) return;
+  __shared__ T sW[kBS * kMaxRhs], sX[kBS * kMaxRhs];
+  T *W = work + work_off[lo + blockIdx.y];
+  const T *Ui = dinv + F.dinv_off + int64_t(c0 / kBS) * 2 * kBS * kBS + kBS * kBS;
+  diag_apply<T>(Ui, W, F.f, c0, cb, nrhs, sW, sX);
+  if (blockIdx.x == 0) {
+    T *Z = zbuf + work_off[lo + blockIdx.y];
+    for (int e = threadIdx.x; e < cb * nrhs; e += blockDim.x) {
+      const int r = e % cb, c = e / cb;
+      Z[(c0 + r) + int64_t(c) * F.f] = sX[r + c * kBS];
+    }
+  }
+  slab_update<T>(fronts + F.off, F.f, W, F.f, r0 + threadIdx.x, c0, c0, cb, nrhs, sX);
 }
 
-// backward, before the block sweep: rows [0, s) -= U12 * W[s:f]
+// rows [0, s) of W -= U12 * W[s:f] (before the backward block sweep)
 template <typename T>
 __global__ void __launch_bounds__(kRowsPerCta) k_bwd_u12(const FrontDev *__restrict__ fr, const T *__restrict__ fronts,
                                                          int nrhs, T *__restrict__ work,
@@ -581,7 +608,32 @@ __global__ void __launch_bounds__(kRowsPerCta) k_bwd_u12(const FrontDev *__restr
   const FrontDev F = fr[blockIdx.y];
   if (F.b == 0 || int(blockIdx.x) * kRowsPerCta >= F.s) return;
   __shared__ T sX[kBS * kMaxRhs];
-  block_update<T>(fronts + F.off, F.f, work + work_off[lo + blockIdx.y], F.f, 0, F.s, F.s, F.f, nrhs, sX);
+  T *W = work + work_off[lo + blockIdx.y];
+  const int r = blockIdx.x * kRowsPerCta + threadIdx.x;
+  T acc[kMaxRhs];
+#pragma unroll
+  for (int c = 0; c < kMaxRhs; ++c) acc[c] = T(0);
+  const T *A = fronts + F.off;
+  for (int k0 = F.s; k0 < F.f; k0 += kBS) {
+    const int kb = min(kBS, F.f - k0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kb * nrhs; e += blockDim.x) {
+      const int q = e % kb, c = e / kb;
+      sX[q + c * kBS] = W[(k0 + q) + int64_t(c) * F.f];
+    }
+    __syncthreads();
+    if (r < F.s)
+      for (int q = 0; q < kb; ++q) {
+        const T a = A[r + int64_t(k0 + q) * F.f];
+#pragma unroll
+        for (int c = 0; c < kMaxRhs; ++c)
+          if (c < nrhs) acc[c] += a * sX[q + c * kBS];
+      }
+  }
+  if (r < F.s)
+#pragma unroll
+    for (int c = 0; c < kMaxRhs; ++c)
+      if (c < nrhs) W[r + int64_t(c) * F.f] -= acc[c];
 }
 
 template <typename T>
@@ -596,10 +648,10 @@ __global__ void k_bwd_gather(const FrontDev *__restrict__ fr, const int32_t *__r
 
 template <typename T>
 __global__ void k_bwd_scatter(const FrontDev *__restrict__ fr, const int32_t *__restrict__ idx, T *__restrict__ y,
-                              int64_t ldy, int nrhs, const T *__restrict__ work, const int64_t *__restrict__ work_off,
+                              int64_t ldy, int nrhs, const T *__restrict__ zbuf, const int64_t *__restrict__ work_off,
                               int lo) {
   const FrontDev F = fr[blockIdx.y];
-  const T *W = work + work_off[lo + blockIdx.y];
+  const T *W = zbuf + work_off[lo + blockIdx.y];
   const int32_t *ix = idx + F.idx_off;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F.s; i += gridDim.x * blockDim.x)
     for (int r = 0; r < nrhs; ++r) y[ix[i] + r * ldy] = W[i + int64_t(r) * F.f];
@@ -653,14 +705,12 @@ int panel_cluster_size(int R) {
   if (cmax <= 0 || R <= 0) return 0;
   const size_t row_bytes = sizeof(T) * NB;
   const int cap_rows = int(kSmemCap / row_bytes);
-  int C = std::max(1, (R + 511) / 512);
-  C = std::max(C, (R + cap_rows - 1) / cap_rows);
-  if (C > cmax) return 0;
-  // round up to a divisor-friendly power of two
+  const int need = (R + cap_rows - 1) / cap_rows;  // clusters smaller than this do not fit
+  if (need > cmax) return 0;
+  int C = std::min(cmax, std::max(need, (R + 511) / 512));
   int c2 = 1;
   while (c2 < C) c2 <<= 1;
-  return c2 <= cmax ? c2 : C;
-}
+  return c2 <= cmax ? c2 : C;}
 
 }  // namespace
 
@@ -765,33 +815,40 @@ cudaError_t launch_make_perm(const FrontDev *fr, int nfront, int max_s, const in
 }
 
 template <typename T>
+cudaError_t launch_invert_diag(const FrontDev *fr, int nfront, int max_s, const T *fronts, T *dinv, cudaStream_t s,
+                               Prof *prof) {
+  if (nfront == 0 || max_s == 0) return cudaSuccess;
+  const size_t e0 = prof->begin();
+  k_invert_diag<T><<<dim3(cdiv(max_s, kBS), nfront), kBS, 0, s>>>(fr, fronts, dinv);
+  prof->end(P_OTHER, 1, e0, 0.0);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_solve_fwd_level_impl(const FrontDev *fr, int lo, int nfront, int max_s, int max_f, const T *fronts,
-                                        const int32_t *perm, const int32_t *idx, T *y, int64_t ldy, int nrhs, T *work,
-                                        const int64_t *work_off, cudaStream_t s, Prof *prof, double bytes) {
+                                        const T *dinv, const int32_t *perm, const int32_t *idx, T *y, int64_t ldy,
+                                        int nrhs, T *work, T *zbuf, const int64_t *work_off, cudaStream_t s,
+                                        Prof *prof, double bytes) {
   if (nfront == 0) return cudaSuccess;
   const FrontDev *frl = fr + lo;
   const size_t e0 = prof->begin();
   int nl = 2;
   k_fwd_gather<T><<<dim3(cdiv(max_f, 256), nfront), 256, 0, s>>>(frl, perm, idx, y, ldy, nrhs, work, work_off, lo);
   for (int c0 = 0; c0 < max_s; c0 += kBS) {
-    k_diag_solve<T, false><<<nfront, 256, 0, s>>>(frl, c0, fronts, nrhs, work, work_off, lo);
     const int rest = max_f - c0 - 1;
+    const int nb = std::max(1, cdiv(std::max(rest, 1), kRowsPerCta));
+    k_fwd_step<T><<<dim3(nb, nfront), kRowsPerCta, 0, s>>>(frl, c0, fronts, dinv, nrhs, work, zbuf, work_off, lo);
     ++nl;
-    if (rest > 0) {
-      k_fwd_update<T><<<dim3(cdiv(rest, kRowsPerCta), nfront), kRowsPerCta, 0, s>>>(frl, c0, fronts, nrhs, work,
-                                                                                   work_off, lo);
-      ++nl;
-    }
   }
-  k_fwd_scatter<T><<<dim3(cdiv(max_f, 256), nfront), 256, 0, s>>>(frl, idx, y, ldy, nrhs, work, work_off, lo);
+  k_fwd_scatter<T><<<dim3(cdiv(max_f, 256), nfront), 256, 0, s>>>(frl, idx, y, ldy, nrhs, work, zbuf, work_off, lo);
   prof->end(P_SOLVE, nl, e0, bytes);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, int max_s, int max_f, const T *fronts,
-                                        const int32_t *idx, T *y, int64_t ldy, int nrhs, T *work,
-                                        const int64_t *work_off, cudaStream_t s, Prof *prof, double bytes) {
+                                        const T *dinv, const int32_t *idx, T *y, int64_t ldy, int nrhs, T *work,
+                                        T *zbuf, const int64_t *work_off, cudaStream_t s, Prof *prof, double bytes) {
   if (nfront == 0) return cudaSuccess;
   const FrontDev *frl = fr + lo;
   const size_t e0 = prof->begin();
@@ -800,15 +857,11 @@ cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, 
   k_bwd_u12<T><<<dim3(cdiv(max_s, kRowsPerCta), nfront), kRowsPerCta, 0, s>>>(frl, fronts, nrhs, work, work_off, lo);
   const int last = ((max_s - 1) / kBS) * kBS;
   for (int c0 = last; c0 >= 0; c0 -= kBS) {
-    k_diag_solve<T, true><<<nfront, 256, 0, s>>>(frl, c0, fronts, nrhs, work, work_off, lo);
+    const int nb = std::max(1, cdiv(c0, kRowsPerCta));
+    k_bwd_step<T><<<dim3(nb, nfront), kRowsPerCta, 0, s>>>(frl, c0, fronts, dinv, nrhs, work, zbuf, work_off, lo);
     ++nl;
-    if (c0 > 0) {
-      k_bwd_update<T><<<dim3(cdiv(c0, kRowsPerCta), nfront), kRowsPerCta, 0, s>>>(frl, c0, fronts, nrhs, work,
-                                                                                work_off, lo);
-      ++nl;
-    }
   }
-  k_bwd_scatter<T><<<dim3(cdiv(max_s, 256), nfront), 256, 0, s>>>(frl, idx, y, ldy, nrhs, work, work_off, lo);
+  k_bwd_scatter<T><<<dim3(cdiv(max_s, 256), nfront), 256, 0, s>>>(frl, idx, y, ldy, nrhs, zbuf, work_off, lo);
   prof->end(P_SOLVE, nl, e0, bytes);
   return cudaGetLastError();
 }
@@ -820,12 +873,13 @@ template cudaError_t launch_lu_level<double>(const FrontDev *, const Front *, in
 template cudaError_t launch_make_perm<double>(const FrontDev *, int, int, const int32_t *, int32_t *, cudaStream_t, Prof *);
 template cudaError_t launch_extend_add_impl<double>(const FrontDev *, int, int, int, const int32_t *, double *, cudaStream_t,
                                                   Prof *, double);
-template cudaError_t launch_solve_fwd_level_impl<double>(const FrontDev *, int, int, int, int, const double *, const int32_t *,
-                                                       const int32_t *, double *, int64_t, int, double *, const int64_t *,
-                                                       cudaStream_t, Prof *, double);
-template cudaError_t launch_solve_bwd_level_impl<double>(const FrontDev *, int, int, int, int, const double *, const int32_t *,
-                                                       double *, int64_t, int, double *, const int64_t *, cudaStream_t, Prof *,
-                                                       double);
+template cudaError_t launch_invert_diag<double>(const FrontDev *, int, int, const double *, double *, cudaStream_t, Prof *);
+template cudaError_t launch_solve_fwd_level_impl<double>(const FrontDev *, int, int, int, int, const double *, const double *,
+                                                       const int32_t *, const int32_t *, double *, int64_t, int, double *,
+                                                       double *, const int64_t *, cudaStream_t, Prof *, double);
+template cudaError_t launch_solve_bwd_level_impl<double>(const FrontDev *, int, int, int, int, const double *, const double *,
+                                                       const int32_t *, double *, int64_t, int, double *, double *,
+                                                       const int64_t *, cudaStream_t, Prof *, double);
 template cudaError_t launch_assemble<float>(const AItem *, int64_t, const double *, float *, cudaStream_t, Prof *,
                                            double);
 template cudaError_t launch_lu_level<float>(const FrontDev *, const Front *, int, int, int, float *, int32_t *, int32_t *,
@@ -833,11 +887,12 @@ template cudaError_t launch_lu_level<float>(const FrontDev *, const Front *, int
 template cudaError_t launch_make_perm<float>(const FrontDev *, int, int, const int32_t *, int32_t *, cudaStream_t, Prof *);
 template cudaError_t launch_extend_add_impl<float>(const FrontDev *, int, int, int, const int32_t *, float *, cudaStream_t,
                                                   Prof *, double);
-template cudaError_t launch_solve_fwd_level_impl<float>(const FrontDev *, int, int, int, int, const float *, const int32_t *,
-                                                       const int32_t *, float *, int64_t, int, float *, const int64_t *,
-                                                       cudaStream_t, Prof *, double);
-template cudaError_t launch_solve_bwd_level_impl<float>(const FrontDev *, int, int, int, int, const float *, const int32_t *,
-                                                       float *, int64_t, int, float *, const int64_t *, cudaStream_t, Prof *,
-                                                       double);
+template cudaError_t launch_invert_diag<float>(const FrontDev *, int, int, const float *, float *, cudaStream_t, Prof *);
+template cudaError_t launch_solve_fwd_level_impl<float>(const FrontDev *, int, int, int, int, const float *, const float *,
+                                                       const int32_t *, const int32_t *, float *, int64_t, int, float *,
+                                                       float *, const int64_t *, cudaStream_t, Prof *, double);
+template cudaError_t launch_solve_bwd_level_impl<float>(const FrontDev *, int, int, int, int, const float *, const float *,
+                                                       const int32_t *, float *, int64_t, int, float *, float *,
+                                                       const int64_t *, cudaStream_t, Prof *, double);
 
 }  // namespace h2sp

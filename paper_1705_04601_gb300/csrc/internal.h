@@ -78,6 +78,7 @@ struct Front {
   int64_t piv_off;  // offset into the pivot array (s entries)
   int64_t idx_off;  // offset into the global-index array (f entries)
   int64_t map_off;  // offset into the extend-add map (b entries)
+  int64_t dinv_off; // offset of the inverted diagonal blocks (2 * 64 * 64 per 64 supernode columns)
   int32_t s, b, f;
   int32_t parent;   // parent front, -1 for a root
 };
@@ -119,7 +120,7 @@ struct Plan {
   std::vector<int32_t> front_idx;          // global scalar index of each front row
   std::vector<int32_t> front_map;          // position in the parent front of each boundary row
   std::vector<AItem> assemble;
-  int64_t front_elems = 0, piv_elems = 0, max_front = 0;
+  int64_t front_elems = 0, piv_elems = 0, max_front = 0, dinv_elems = 0;
   double factor_flops = 0.0;
   // H^2 matvec structure (Definition 4.9)
   std::vector<int64_t> h_begin, h_size;

@@ -20,9 +20,12 @@ cudaError_t launch_transform(const XItem *items, int n, const double *const *src
 
 // ---- block LU of S (factor.cu), T = double or float ----
 struct FrontDev {
-  int64_t off, piv_off, idx_off, map_off;
+  int64_t off, piv_off, idx_off, map_off, dinv_off;
   int32_t s, b, f, parent;
 };
+
+// Column block of the blocked triangular solves (and of the inverted diagonal blocks).
+constexpr int kSolveBlock = 64;
 
 // Panel width of the blocked LU per precision.
 template <typename T>
@@ -51,18 +54,23 @@ cudaError_t launch_extend_add_impl(const FrontDev *fr_all, int lo, int nfront, i
 template <typename T>
 cudaError_t launch_make_perm(const FrontDev *fr, int nfront, int max_s, const int32_t *piv, int32_t *perm,
                              cudaStream_t s, Prof *prof);
-// Forward sweep for one level (fronts [lo, lo+nfront) of fr): gathers y into
-// the fronts' work vectors, solves with L, stores z (supernode part) back into
-// y and adds -L21 z into the boundary rows of y.
+// Inverses of the kSolveBlock-square diagonal blocks of L11 and U11 of every front.
+template <typename T>
+cudaError_t launch_invert_diag(const FrontDev *fr, int nfront, int max_s, const T *fronts, T *dinv, cudaStream_t s,
+                               Prof *prof);
+// Forward sweep for one level (fronts [lo, lo+nfront) of fr): gathers P^T y into
+// the fronts' work vectors, z = L11^-1 (.) block by block into zbuf, adds
+// -L21 z into the boundary rows of y and stores z into the supernode rows.
 template <typename T>
 cudaError_t launch_solve_fwd_level_impl(const FrontDev *fr, int lo, int nfront, int max_s, int max_f, const T *fronts,
-                                        const int32_t *perm, const int32_t *idx, T *y, int64_t ldy, int nrhs, T *work,
-                                        const int64_t *work_off, cudaStream_t s, Prof *prof, double bytes);
+                                        const T *dinv, const int32_t *perm, const int32_t *idx, T *y, int64_t ldy,
+                                        int nrhs, T *work, T *zbuf, const int64_t *work_off, cudaStream_t s,
+                                        Prof *prof, double bytes);
 // Backward sweep for one level: x_s = U11^-1 (z - U12 x_b), stored into y.
 template <typename T>
 cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, int max_s, int max_f, const T *fronts,
-                                        const int32_t *idx, T *y, int64_t ldy, int nrhs, T *work,
-                                        const int64_t *work_off, cudaStream_t s, Prof *prof, double bytes);
+                                        const T *dinv, const int32_t *idx, T *y, int64_t ldy, int nrhs, T *work,
+                                        T *zbuf, const int64_t *work_off, cudaStream_t s, Prof *prof, double bytes);
 
 // ---- applies, H^2 product, vector kernels (apply.cu) ----
 struct ApItem {

@@ -663,6 +663,8 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
       F.map_off = 0;
       p.front_elems += int64_t(F.f) * F.f;
       p.piv_elems += s;
+      F.dinv_off = p.dinv_elems;
+      p.dinv_elems += ((s + 63) / 64) * 2 * 64 * 64;
       p.max_front = std::max<int64_t>(p.max_front, F.f);
       for (int i = p.sn_ptr[k]; i < p.sn_ptr[k + 1]; ++i) {
         int v = p.order[i];
