@@ -226,20 +226,28 @@ __global__ void __launch_bounds__(kClusterPanelThreads) k_panel_cluster(const Fr
       cand_i = i;
     }
     cluster.sync();
-    if (tid == 0) {
+    if (wid == 0) {
+      // lane q reads CTA q's candidate (C <= 32), then a warp argmax
       T v = T(-1);
       int i = INT_MAX;
-      for (int q = 0; q < C; ++q) {
-        const T qv = *cluster.map_shared_rank(&cand_v, q);
-        const int qi = *cluster.map_shared_rank(&cand_i, q);
-        if (qv > v || (qv == v && qi < i)) v = qv, i = qi;
+      if (lane < C) {
+        v = *cluster.map_shared_rank(&cand_v, lane);
+        i = *cluster.map_shared_rank(&cand_i, lane);
       }
-      if (i == INT_MAX) {  // no finite candidate
-        i = col;
-        if (rank == 0) atomicOr(err, 2);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        if (ov > v || (ov == v && oi < i)) v = ov, i = oi;
       }
-      s_p = i;
-      if (rank == 0) piv[F.piv_off + col] = i;
+      if (lane == 0) {
+        if (i == INT_MAX) {  // no finite candidate
+          i = col;
+          if (rank == 0) atomicOr(err, 2);
+        }
+        s_p = i;
+        if (rank == 0) piv[F.piv_off + col] = i;
+      }
     }
     __syncthreads();
     const int p = s_p;
@@ -600,40 +608,40 @@ __global__ void __launch_bounds__(kRowsPerCta) k_bwd_step(const FrontDev *__rest
   slab_update<T>(fronts + F.off, F.f, W, F.f, r0 + threadIdx.x, c0, c0, cb, nrhs, sX);
 }
 
-// rows [0, s) of W -= U12 * W[s:f] (before the backward block sweep)
+// rows [0, s) of W -= U12 * W[s:f] (before the backward block sweep); the
+// columns [s, f) are split into chunks over blockIdx.y, partial sums added atomically
+constexpr int kU12Chunk = 256;
 template <typename T>
 __global__ void __launch_bounds__(kRowsPerCta) k_bwd_u12(const FrontDev *__restrict__ fr, const T *__restrict__ fronts,
                                                          int nrhs, T *__restrict__ work,
                                                          const int64_t *__restrict__ work_off, int lo) {
-  const FrontDev F = fr[blockIdx.y];
-  if (F.b == 0 || int(blockIdx.x) * kRowsPerCta >= F.s) return;
-  __shared__ T sX[kBS * kMaxRhs];
-  T *W = work + work_off[lo + blockIdx.y];
+  const FrontDev F = fr[blockIdx.z];
+  const int k_lo = F.s + int(blockIdx.y) * kU12Chunk;
+  if (F.b == 0 || int(blockIdx.x) * kRowsPerCta >= F.s || k_lo >= F.f) return;
+  const int k_hi = min(F.f, k_lo + kU12Chunk);
+  __shared__ T sX[kU12Chunk * kMaxRhs];
+  T *W = work + work_off[lo + blockIdx.z];
+  const int kb = k_hi - k_lo;
+  for (int e = threadIdx.x; e < kb * nrhs; e += blockDim.x) {
+    const int q = e % kb, c = e / kb;
+    sX[q + c * kU12Chunk] = W[(k_lo + q) + int64_t(c) * F.f];
+  }
+  __syncthreads();
   const int r = blockIdx.x * kRowsPerCta + threadIdx.x;
+  if (r >= F.s) return;
   T acc[kMaxRhs];
 #pragma unroll
   for (int c = 0; c < kMaxRhs; ++c) acc[c] = T(0);
   const T *A = fronts + F.off;
-  for (int k0 = F.s; k0 < F.f; k0 += kBS) {
-    const int kb = min(kBS, F.f - k0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < kb * nrhs; e += blockDim.x) {
-      const int q = e % kb, c = e / kb;
-      sX[q + c * kBS] = W[(k0 + q) + int64_t(c) * F.f];
-    }
-    __syncthreads();
-    if (r < F.s)
-      for (int q = 0; q < kb; ++q) {
-        const T a = A[r + int64_t(k0 + q) * F.f];
-#pragma unroll
-        for (int c = 0; c < kMaxRhs; ++c)
-          if (c < nrhs) acc[c] += a * sX[q + c * kBS];
-      }
-  }
-  if (r < F.s)
+  for (int q = 0; q < kb; ++q) {
+    const T a = A[r + int64_t(k_lo + q) * F.f];
 #pragma unroll
     for (int c = 0; c < kMaxRhs; ++c)
-      if (c < nrhs) W[r + int64_t(c) * F.f] -= acc[c];
+      if (c < nrhs) acc[c] += a * sX[q + c * kU12Chunk];
+  }
+#pragma unroll
+  for (int c = 0; c < kMaxRhs; ++c)
+    if (c < nrhs) atomicAdd(&W[r + int64_t(c) * F.f], -acc[c]);
 }
 
 template <typename T>
@@ -854,7 +862,8 @@ cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, 
   const size_t e0 = prof->begin();
   int nl = 3;
   k_bwd_gather<T><<<dim3(cdiv(max_f, 256), nfront), 256, 0, s>>>(frl, idx, y, ldy, nrhs, work, work_off, lo);
-  k_bwd_u12<T><<<dim3(cdiv(max_s, kRowsPerCta), nfront), kRowsPerCta, 0, s>>>(frl, fronts, nrhs, work, work_off, lo);
+  k_bwd_u12<T><<<dim3(cdiv(max_s, kRowsPerCta), cdiv(std::max(max_f - 1, 1), kU12Chunk), nfront), kRowsPerCta, 0, s>>>(
+      frl, fronts, nrhs, work, work_off, lo);
   const int last = ((max_s - 1) / kBS) * kBS;
   for (int c0 = last; c0 >= 0; c0 -= kBS) {
     const int nb = std::max(1, cdiv(c0, kRowsPerCta));

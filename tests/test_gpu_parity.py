@@ -222,6 +222,11 @@ def test_full_size_fp64_direct_and_mixed_refinement(full):
     H.h2sp_factor(hd, H.H2SP_FP64)
     H.h2sp_solve(hd, bt, xt, mode=H.H2SP_DIRECT)
     torch.cuda.synchronize()
+    xd = host(xt)
+    r = np.linalg.norm(b - mv(xd), axis=0) / np.linalg.norm(b, axis=0)
+    assert r.max() <= 1e-9   # one FP64 direct solve (blocked, inverted 64x64 diagonal blocks)
+    info = H.h2sp_solve(hd, bt, xt, mode=H.H2SP_IR, tol=1e-10, maxit=10)
+    assert info.status == H.H2SP_OK and info.iters <= 3
     x64 = host(xt)
     r = np.linalg.norm(b - mv(x64), axis=0) / np.linalg.norm(b, axis=0)
     assert r.max() <= 1e-10
