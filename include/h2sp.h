@@ -255,6 +255,32 @@ typedef struct {
  */
 int h2sp_profile(h2sp_handle *h, int32_t timing, int32_t reset, h2sp_kernel_times *out);
 
+/*
+ * h2sp_h2_matvec_static -- y = A x, the same FP64 H^2 product as
+ * h2sp_apply(H2SP_OP_H2), for callers that cannot allocate device memory at
+ * the point of the call: code running while a memory pool is locked or
+ * budgeted by someone else, inside a tight real-time loop that must not hit
+ * the allocator, or in a plug-in whose host forbids cudaMalloc.  The paper
+ * has no counterpart of this entry point; it is an interface convenience.
+ *
+ * It allocates nothing: the two coefficient workspaces of the upward and
+ * downward passes live in a file-scope __device__ array of the library of
+ * 2^21 doubles (16 MiB), which every GPU that loads the library keeps until
+ * the process exits.  It needs 2 * 16 * (sum of the cluster ranks) doubles;
+ * a larger matrix is rejected with H2SP_EUNSUPPORTED and a message in
+ * h2sp_last_cuda_error.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call shares the one array and
+ * leaves its last contents there (each element is written before it is read,
+ * so nothing needs clearing), so calls that overlap on the GPU -- on
+ * different streams, or from different host threads -- race; serialise them.
+ * h is a handle from h2sp_sparsify (its device structure is read, not
+ * changed); x (ldx >= n) and y (ldy >= n) are device arrays of nrhs columns.
+ * Enqueued on `stream`; does not synchronise.
+ */
+int h2sp_h2_matvec_static(const h2sp_handle *h, int32_t nrhs, const double *x, int64_t ldx, double *y, int64_t ldy,
+                          h2sp_stream stream);
+
 /* h2sp_query -- fill *st with the handle's sizes and counters. */
 int h2sp_query(const h2sp_handle *h, h2sp_stats *st);
 

@@ -785,6 +785,30 @@ int h2sp_query(const h2sp_handle *h, h2sp_stats *st) {
   return H2SP_OK;
 }
 
+int h2sp_h2_matvec_static(const h2sp_handle *h, int32_t nrhs, const double *x, int64_t ldx, double *y, int64_t ldy,
+                          h2sp_stream stream) {
+  if (!h || !x || !y || nrhs <= 0) return H2SP_EINVAL;
+  if (!h->device_ready) return H2SP_ESTATE;
+  const Plan &p = h->plan;
+  if (ldx < p.n || ldy < p.n) return H2SP_EINVAL;
+  const int64_t ldh = std::max<int64_t>(p.xh_elems, 1);
+  const int64_t need = 2 * ldh * 16;  // x^ and y^, 16 right-hand sides per pass
+  if (need > kStaticScratchElems) {
+    g_cuda_err = "h2sp_h2_matvec_static: needs " + std::to_string(need) + " doubles of workspace, the static array has " +
+                 std::to_string(kStaticScratchElems);
+    return H2SP_EUNSUPPORTED;
+  }
+  try {
+    double *scratch = nullptr;
+    ck(static_scratch_address(&scratch));
+    ck(launch_h2_matvec(h->h2, p.level_ptr.data(), h->child_start, h->child_cnt, p.D, x, ldx, y, ldy, nrhs, scratch,
+                        scratch + ldh * 16, ldh, reinterpret_cast<cudaStream_t>(stream)));
+  } catch (const CudaFail &f) {
+    return status_of(f.e);
+  }
+  return H2SP_OK;
+}
+
 int h2sp_profile(h2sp_handle *h, int32_t timing, int32_t reset, h2sp_kernel_times *out) {
   if (!h) return H2SP_EINVAL;
   if (h->device_ready) h->prof.collect();

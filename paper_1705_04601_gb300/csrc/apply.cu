@@ -3,6 +3,7 @@
 // and the small vector kernels of the iterative solves (§5.5).
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 #include "kernels.h"
 
@@ -372,6 +373,32 @@ cudaError_t launch_h2_matvec(const H2Dev &h, const int32_t *level_ptr_host, cons
     k_h2_leaf_out<<<nleaf, 64, 0, s>>>(h, xr, ldx, yh, ldh, yr, ldy, nr);
   }
   return cudaGetLastError();
+}
+
+// Workspace of h2sp_h2_matvec_static: the two coefficient vectors of the
+// upward and downward passes live in this file-scope device array, so that
+// entry point allocates nothing.  Every GPU that loads the library holds it
+// until the process exits.
+static __device__ __align__(256) double g_h2_static_scratch[kStaticScratchElems];
+
+cudaError_t static_scratch_address(double **out) {
+  // cudaGetSymbolAddress gives the device address of the array for the
+  // current device; the host-side name itself is not a device pointer.
+  static std::mutex mu;
+  static double *addr[128] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (addr[dev] == nullptr) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_h2_static_scratch);
+    if (e != cudaSuccess) return e;
+    addr[dev] = static_cast<double *>(p);
+  }
+  *out = addr[dev];
+  return cudaSuccess;
 }
 
 cudaError_t launch_residual(const double *b, int64_t ldb, const double *y, int64_t ldy, double *r, int64_t ldr,

@@ -112,6 +112,11 @@ cudaError_t launch_h2_matvec(const H2Dev &h, const int32_t *level_ptr_host, cons
                              const int32_t *child_cnt, int depth, const double *x, int64_t ldx, double *y,
                              int64_t ldy, int nrhs, double *xh, double *yh, int64_t ldh, cudaStream_t s);
 
+// Size (doubles) of the static device workspace of h2sp_h2_matvec_static (16 MiB).
+constexpr int64_t kStaticScratchElems = int64_t(1) << 21;
+// Device address of that workspace on the current device (looked up once per device).
+cudaError_t static_scratch_address(double **out);
+
 // r = b - y; norms2[c] = ||r_c||^2 (atomic FP64 accumulation), over n rows
 cudaError_t launch_residual(const double *b, int64_t ldb, const double *y, int64_t ldy, double *r, int64_t ldr,
                             int64_t n, int nrhs, double *norms2, cudaStream_t s);

@@ -87,6 +87,7 @@ SIGNATURES = {
     "h2sp_export_structure": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i64p]),
     "h2sp_query": (ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
     "h2sp_profile": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(KernelTimes)]),
+    "h2sp_h2_matvec_static": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int64, _vp, ctypes.c_int64, _vp]),
     "h2sp_destroy": (None, [_vp]),
     "h2sp_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
     "h2sp_last_cuda_error": (ctypes.c_char_p, []),
