@@ -136,37 +136,20 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel(const FrontDev *__restr
   }
 }
 
-// Net row movement of one panel's swaps (rows j0 .. j0+jb-1 exchanged with
-// their pivot rows, in order): new_row[rows[q]] = old_row[src[q]].
-__device__ void compose_swaps(const int32_t *pv, int j0, int jb, int32_t *sw) {
-  int nr = 0;
-  int32_t *rows = sw + 1, *src = sw + 1 + kMaxSwapRows;
-  for (int j = 0; j < jb; ++j) {
-    const int a = j0 + j, b = pv[a];
-    if (a == b) continue;
-    int ia = -1, ib = -1;
-    for (int q = 0; q < nr; ++q) {
-      if (rows[q] == a) ia = q;
-      if (rows[q] == b) ib = q;
-    }
-    if (ia < 0) rows[nr] = a, src[nr] = a, ia = nr++;
-    if (ib < 0) rows[nr] = b, src[nr] = b, ib = nr++;
-    const int32_t t = src[ia];
-    src[ia] = src[ib];
-    src[ib] = t;
-  }
-  sw[0] = nr;
-}
-
 constexpr int kClusterPanelThreads = 512;
 
-// Panel factorization by one thread-block cluster per front.  The panel
-// rows [j0, f) are split into C contiguous chunks, one per CTA, held in
-// shared memory for the whole panel.  Per column: local argmax over the
-// supernode rows, cluster barrier, every CTA reduces the C candidates read
-// through distributed shared memory, reads the pivot row remotely, cluster
-// barrier, the owners of the two rows swap them, and every CTA updates its
-// own rows.  Cluster barriers are hardware barriers of co-scheduled CTAs.
+// Panel factorization by one thread-block cluster per front.  The panel rows
+// [j0, f) are split into C contiguous chunks, one per CTA, held in shared
+// memory for the whole panel.  Rows are not moved while the panel is factored
+// (logical pivoting): per column, every CTA offers its best not-yet-pivoted
+// supernode row, one cluster barrier, every CTA reduces the C candidates read
+// through distributed shared memory and reads the pivot row remotely, the
+// owner retires that row, and every CTA updates its remaining rows.  A pivot
+// row is never written after it is retired, so remote readers need no second
+// barrier; candidate slots alternate between columns.  At the end each CTA
+// turns the pivot sequence into LAPACK's sequential row interchanges and
+// writes its rows to their final positions.  Exact ties between candidates go
+// to the lowest row index.
 template <typename T, int NB>
 __global__ void __launch_bounds__(kClusterPanelThreads) k_panel_cluster(const FrontDev *__restrict__ fr, int j0,
                                                                         T *__restrict__ fronts, int32_t *__restrict__ piv,
@@ -186,26 +169,31 @@ __global__ void __launch_bounds__(kClusterPanelThreads) k_panel_cluster(const Fr
   const int r_lo = j0 + rank * per;
   const int nr = max(0, min(F.f, r_lo + per) - r_lo);
   extern __shared__ __align__(16) unsigned char smraw[];
-  T *P = reinterpret_cast<T *>(smraw);  // [NB][per], column c at P + c * per
-  __shared__ T cand_v;
-  __shared__ int cand_i;
-  __shared__ T urow[NB], tmp[NB];
+  T *P = reinterpret_cast<T *>(smraw);                        // [NB][per], column c at P + c * per
+  int32_t *dest = reinterpret_cast<int32_t *>(P + NB * per);  // [per] final row of each local row
+  unsigned char *done = reinterpret_cast<unsigned char *>(dest + per);  // [per] retired pivot rows
+  __shared__ T cand_v[2];
+  __shared__ int cand_i[2];
+  __shared__ T urow[NB];
   __shared__ T redv[kClusterPanelThreads / 32];
   __shared__ int redi[kClusterPanelThreads / 32];
-  __shared__ int s_p;
+  __shared__ int hist[NB];
+  __shared__ int32_t lrow[2 * NB], lsrc[2 * NB];
+  __shared__ int nswap;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
   for (int e = tid; e < nr * jb; e += nt) {
     const int i = e % nr, c = e / nr;
     P[c * per + i] = A[(r_lo + i) + int64_t(j0 + c) * ld];
   }
+  for (int i = tid; i < per; i += nt) done[i] = 0, dest[i] = r_lo + i;
   __syncthreads();
+  const int i_hi = max(0, min(F.s, r_lo + nr) - r_lo);  // local supernode rows
   for (int j = 0; j < jb; ++j) {
-    const int col = j0 + j;
-    // local candidates: supernode rows >= col owned by this CTA
+    const int buf = j & 1;
     T bv = T(-1);
     int bi = INT_MAX;
-    const int i_lo = max(col, r_lo) - r_lo, i_hi = min(F.s, r_lo + nr) - r_lo;
-    for (int i = i_lo + tid; i < i_hi; i += nt) {
+    for (int i = tid; i < i_hi; i += nt) {
+      if (done[i]) continue;
       const T v = tabs(P[j * per + i]);
       if (v > bv) bv = v, bi = r_lo + i;
     }
@@ -222,17 +210,16 @@ __global__ void __launch_bounds__(kClusterPanelThreads) k_panel_cluster(const Fr
       int i = redi[0];
       for (int w = 1; w < (nt >> 5); ++w)
         if (redv[w] > v || (redv[w] == v && redi[w] < i)) v = redv[w], i = redi[w];
-      cand_v = v;
-      cand_i = i;
+      cand_v[buf] = v;
+      cand_i[buf] = i;
     }
     cluster.sync();
     if (wid == 0) {
-      // lane q reads CTA q's candidate (C <= 32), then a warp argmax
       T v = T(-1);
       int i = INT_MAX;
       if (lane < C) {
-        v = *cluster.map_shared_rank(&cand_v, lane);
-        i = *cluster.map_shared_rank(&cand_i, lane);
+        v = cluster.map_shared_rank(cand_v, lane)[buf];
+        i = cluster.map_shared_rank(cand_i, lane)[buf];
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -241,37 +228,41 @@ __global__ void __launch_bounds__(kClusterPanelThreads) k_panel_cluster(const Fr
         if (ov > v || (ov == v && oi < i)) v = ov, i = oi;
       }
       if (lane == 0) {
-        if (i == INT_MAX) {  // no finite candidate
-          i = col;
+        if (i == INT_MAX) {  // no finite candidate: take the first live row, flag the front
+          i = -1;
           if (rank == 0) atomicOr(err, 2);
         }
-        s_p = i;
-        if (rank == 0) piv[F.piv_off + col] = i;
+        hist[j] = i;
       }
     }
     __syncthreads();
-    const int p = s_p;
-    const int own_p = (p - j0) / per, own_c = (col - j0) / per;
-    const T *Pp = cluster.map_shared_rank(P, own_p);
-    for (int c = tid; c < jb; c += nt) urow[c] = Pp[c * per + (p - (j0 + own_p * per))];
-    if (rank == own_p && p != col) {
-      const T *Pc = cluster.map_shared_rank(P, own_c);
-      for (int c = tid; c < jb; c += nt) tmp[c] = Pc[c * per + (col - (j0 + own_c * per))];
+    int p = hist[j];
+    if (p < 0) {
+      // keep the sequence a permutation: the lowest not-yet-pivoted supernode row
+      p = j0;
+      bool used = true;
+      while (used) {
+        used = false;
+        for (int q = 0; q < j; ++q)
+          if (hist[q] == p) used = true, ++p;
+      }
+      __syncthreads();
+      if (tid == 0) hist[j] = p;
+      __syncthreads();
     }
-    cluster.sync();
-    if (p != col) {
-      if (rank == own_c)
-        for (int c = tid; c < jb; c += nt) P[c * per + (col - r_lo)] = urow[c];
-      if (rank == own_p)
-        for (int c = tid; c < jb; c += nt) P[c * per + (p - r_lo)] = tmp[c];
-    }
+    const int own = (p - j0) / per;
+    const T *Pp = cluster.map_shared_rank(P, own);
+    const int lp = p - (j0 + own * per);
+    for (int c = tid; c < jb; c += nt) urow[c] = Pp[c * per + lp];
+    if (rank == own && tid == 0) done[lp] = 1;
     __syncthreads();
     const T pv = urow[j];
     if (pv == T(0)) {
       if (tid == 0 && rank == 0) atomicOr(err, 1);
     } else {
       const T inv = T(1) / pv;
-      for (int i = max(col + 1, r_lo) - r_lo + tid; i < nr; i += nt) {
+      for (int i = tid; i < nr; i += nt) {
+        if (i < i_hi && done[i]) continue;
         const T l = P[j * per + i] * inv;
         P[j * per + i] = l;
         for (int c = j + 1; c < jb; ++c) P[c * per + i] -= l * urow[c];
@@ -279,13 +270,41 @@ __global__ void __launch_bounds__(kClusterPanelThreads) k_panel_cluster(const Fr
     }
     __syncthreads();
   }
+  // LAPACK-style interchanges from the pivot sequence, and where every row goes
+  if (tid == 0) {
+    int n = 0;  // touched positions: position lrow[q] currently holds physical row lsrc[q]
+    for (int j = 0; j < jb; ++j) {
+      const int col = j0 + j, p = hist[j];
+      int ip = -1, ic = -1;
+      for (int q = 0; q < n; ++q) {
+        if (lsrc[q] == p) ip = q;
+        if (lrow[q] == col) ic = q;
+      }
+      const int pos_p = ip >= 0 ? lrow[ip] : p;  // untouched rows sit at their own position
+      if (rank == 0) piv[F.piv_off + col] = pos_p;
+      if (pos_p == col) continue;
+      if (ic < 0) lrow[n] = col, lsrc[n] = col, ic = n++;
+      if (ip < 0) lrow[n] = p, lsrc[n] = p, ip = n++;
+      const int32_t t = lsrc[ic];
+      lsrc[ic] = lsrc[ip];
+      lsrc[ip] = t;
+    }
+    nswap = n;
+    if (rank == 0) {
+      int32_t *sw = swaps + int64_t(fi) * (1 + 2 * kMaxSwapRows);
+      for (int q = 0; q < n; ++q) sw[1 + q] = lrow[q], sw[1 + kMaxSwapRows + q] = lsrc[q];
+      sw[0] = n;
+    }
+  }
+  __syncthreads();
+  for (int q = tid; q < nswap; q += nt) {
+    const int src = lsrc[q];
+    if (src >= r_lo && src < r_lo + nr) dest[src - r_lo] = lrow[q];
+  }
+  __syncthreads();
   for (int e = tid; e < nr * jb; e += nt) {
     const int i = e % nr, c = e / nr;
-    A[(r_lo + i) + int64_t(j0 + c) * ld] = P[c * per + i];
-  }
-  if (rank == 0 && tid == 0) {
-    __threadfence_block();
-    compose_swaps(piv + F.piv_off, j0, jb, swaps + int64_t(fi) * (1 + 2 * kMaxSwapRows));
+    A[dest[i] + int64_t(j0 + c) * ld] = P[c * per + i];
   }
   // no CTA may exit while others can still read its shared memory
   cluster.sync();
@@ -343,9 +362,12 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const FrontDev *__restrict__ 
   }
 }
 
-// trailing update: A[t0:f, t0:f] -= A[t0:f, j0:j0+jb] * A[j0:j0+jb, t0:f], t0 = j0 + jb
+// trailing update: A[t0:f, t0:f] -= A[t0:f, j0:j0+jb] * A[j0:j0+jb, t0:f], t0 = j0 + jb.
+// Each thread owns a TM x TN block of contiguous rows and columns; the C tile is
+// prefetched into the accumulators while the two operand tiles are staged.
 template <typename T, int BM, int BN, int TM, int TN, int NB>
 __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict__ fr, int j0, T *__restrict__ fronts) {
+  constexpr int PB = BN + 16 / int(sizeof(T));  // padded row of the B tile (keeps 16-byte alignment)
   const FrontDev F = fr[blockIdx.z];
   if (j0 >= F.s) return;
   const int jb = min(NB, F.s - j0);
@@ -357,8 +379,19 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
   const int64_t ld = F.f;
   extern __shared__ __align__(16) unsigned char smraw[];
   T *sA = reinterpret_cast<T *>(smraw);  // [NB][BM]
-  T *sB = sA + NB * BM;                   // [NB][BN]
+  T *sB = sA + NB * BM;                   // [NB][PB]
   const int tid = threadIdx.x;
+  const int tr = tid % (BM / TM), tc = tid / (BM / TM);
+  T acc[TM][TN];
+#pragma unroll
+  for (int j = 0; j < TN; ++j) {
+    const int c = cb + tc * TN + j;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int r = rb + tr * TM + i;
+      acc[i][j] = (c < nrest && r < nrest) ? A[(t0 + r) + int64_t(t0 + c) * ld] : T(0);
+    }
+  }
   for (int e = tid; e < jb * BM; e += 256) {
     const int i = e % BM, k = e / BM;
     const int r = rb + i;
@@ -367,26 +400,15 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
   for (int e = tid; e < jb * BN; e += 256) {
     const int k = e % jb, j = e / jb;
     const int c = cb + j;
-    sB[k * BN + j] = (c < nrest) ? A[(j0 + k) + int64_t(t0 + c) * ld] : T(0);
-  }
-  const int tr = tid % 16, tc = tid / 16;
-  T acc[TM][TN];
-#pragma unroll
-  for (int j = 0; j < TN; ++j) {
-    const int c = cb + tc + 16 * j;
-#pragma unroll
-    for (int i = 0; i < TM; ++i) {
-      const int r = rb + tr + 16 * i;
-      acc[i][j] = (c < nrest && r < nrest) ? A[(t0 + r) + int64_t(t0 + c) * ld] : T(0);
-    }
+    sB[k * PB + j] = (c < nrest) ? A[(j0 + k) + int64_t(t0 + c) * ld] : T(0);
   }
   __syncthreads();
   for (int k = 0; k < jb; ++k) {
     T a[TM], b[TN];
 #pragma unroll
-    for (int i = 0; i < TM; ++i) a[i] = sA[k * BM + tr + 16 * i];
+    for (int i = 0; i < TM; ++i) a[i] = sA[k * BM + tr * TM + i];
 #pragma unroll
-    for (int j = 0; j < TN; ++j) b[j] = sB[k * BN + tc + 16 * j];
+    for (int j = 0; j < TN; ++j) b[j] = sB[k * PB + tc * TN + j];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -394,12 +416,12 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
   }
 #pragma unroll
   for (int j = 0; j < TN; ++j) {
-    const int c = cb + tc + 16 * j;
+    const int c = cb + tc * TN + j;
     if (c >= nrest) continue;
     T *Cc = A + int64_t(t0 + c) * ld + t0;
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
-      const int r = rb + tr + 16 * i;
+      const int r = rb + tr * TM + i;
       if (r < nrest) Cc[r] = acc[i][j];
     }
   }
@@ -523,8 +545,9 @@ __global__ void __launch_bounds__(kBS) k_invert_diag(const FrontDev *__restrict_
 
 // x = Dinv (cb x cb) * W[c0:c0+cb] into shared memory (every CTA of the step computes it)
 template <typename T>
-__device__ void diag_apply(const T *Dinv, const T *W, int64_t ldw, int c0, int cb, int nrhs, T *sW, T *sX) {
+__device__ void diag_apply(const T *Dinv, const T *W, int64_t ldw, int c0, int cb, int nrhs, T *sD, T *sW, T *sX) {
   const int tid = threadIdx.x;
+  for (int e = tid; e < kBS * kBS; e += blockDim.x) sD[e] = Dinv[e];
   for (int e = tid; e < cb * nrhs; e += blockDim.x) {
     const int r = e % cb, c = e / cb;
     sW[r + c * kBS] = W[(c0 + r) + int64_t(c) * ldw];
@@ -533,7 +556,8 @@ __device__ void diag_apply(const T *Dinv, const T *W, int64_t ldw, int c0, int c
   for (int e = tid; e < cb * nrhs; e += blockDim.x) {
     const int r = e % cb, c = e / cb;
     T acc = T(0);
-    for (int k = 0; k < cb; ++k) acc += Dinv[r + k * kBS] * sW[k + c * kBS];
+#pragma unroll 8
+    for (int k = 0; k < cb; ++k) acc += sD[r + k * kBS] * sW[k + c * kBS];
     sX[r + c * kBS] = acc;
   }
   __syncthreads();
@@ -547,6 +571,7 @@ __device__ void slab_update(const T *A, int64_t ld, T *W, int64_t ldw, int r, in
   T acc[kMaxRhs];
 #pragma unroll
   for (int c = 0; c < kMaxRhs; ++c) acc[c] = T(0);
+#pragma unroll 8
   for (int q = 0; q < cb; ++q) {
     const T a = A[r + int64_t(c0 + q) * ld];
 #pragma unroll
@@ -569,10 +594,12 @@ __global__ void __launch_bounds__(kRowsPerCta) k_fwd_step(const FrontDev *__rest
   const int cb = min(kBS, F.s - c0);
   const int r0 = c0 + cb + int(blockIdx.x) * kRowsPerCta;
   if (blockIdx.x > 0 && r0 >= F.f) return;
-  __shared__ T sW[kBS * kMaxRhs], sX[kBS * kMaxRhs];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *sD = reinterpret_cast<T *>(smraw);
+  T *sW = sD + kBS * kBS, *sX = sW + kBS * kMaxRhs;
   T *W = work + work_off[lo + blockIdx.y];
   const T *Li = dinv + F.dinv_off + int64_t(c0 / kBS) * 2 * kBS * kBS;
-  diag_apply<T>(Li, W, F.f, c0, cb, nrhs, sW, sX);
+  diag_apply<T>(Li, W, F.f, c0, cb, nrhs, sD, sW, sX);
   if (blockIdx.x == 0) {
     T *Z = zbuf + work_off[lo + blockIdx.y];
     for (int e = threadIdx.x; e < cb * nrhs; e += blockDim.x) {
@@ -594,10 +621,12 @@ __global__ void __launch_bounds__(kRowsPerCta) k_bwd_step(const FrontDev *__rest
   const int cb = min(kBS, F.s - c0);
   const int r0 = int(blockIdx.x) * kRowsPerCta;
   if (blockIdx.x > 0 && r0 >= c0) return;
-  __shared__ T sW[kBS * kMaxRhs], sX[kBS * kMaxRhs];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *sD = reinterpret_cast<T *>(smraw);
+  T *sW = sD + kBS * kBS, *sX = sW + kBS * kMaxRhs;
   T *W = work + work_off[lo + blockIdx.y];
   const T *Ui = dinv + F.dinv_off + int64_t(c0 / kBS) * 2 * kBS * kBS + kBS * kBS;
-  diag_apply<T>(Ui, W, F.f, c0, cb, nrhs, sW, sX);
+  diag_apply<T>(Ui, W, F.f, c0, cb, nrhs, sD, sW, sX);
   if (blockIdx.x == 0) {
     T *Z = zbuf + work_off[lo + blockIdx.y];
     for (int e = threadIdx.x; e < cb * nrhs; e += blockDim.x) {
@@ -682,6 +711,11 @@ struct GemmCfg<float> {
 // that fits the shared-memory budget, up to the largest cluster this device
 // schedules with that budget; 0 means "use the single-CTA kernel".
 template <typename T, int NB>
+size_t panel_smem_bytes(int per) {
+  return sizeof(T) * size_t(NB) * per + sizeof(int32_t) * size_t(per) + size_t(per) + 16;
+}
+
+template <typename T, int NB>
 int panel_cluster_size(int R) {
   constexpr size_t kSmemCap = 200 * 1024;
   static int cmax = -1;
@@ -711,8 +745,8 @@ int panel_cluster_size(int R) {
     cudaGetLastError();
   }
   if (cmax <= 0 || R <= 0) return 0;
-  const size_t row_bytes = sizeof(T) * NB;
-  const int cap_rows = int(kSmemCap / row_bytes);
+  const size_t row_bytes = sizeof(T) * NB + sizeof(int32_t) + 1;
+  const int cap_rows = int((kSmemCap - 16) / row_bytes);
   const int need = (R + cap_rows - 1) / cap_rows;  // clusters smaller than this do not fit
   if (need > cmax) return 0;
   int C = std::min(cmax, std::max(need, (R + 511) / 512));
@@ -738,7 +772,7 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
   constexpr int NB = LuCfg<T>::NB;
   using G = GemmCfg<T>;
   auto gemm = k_gemm_update<T, G::BM, G::BN, G::TM, G::TN, NB>;
-  const size_t gsmem = sizeof(T) * NB * (G::BM + G::BN);
+  const size_t gsmem = sizeof(T) * NB * (G::BM + G::BN + 16 / sizeof(T));
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gsmem));
@@ -764,7 +798,7 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(unsigned(nfront * C));
       cfg.blockDim = dim3(kClusterPanelThreads);
-      cfg.dynamicSmemBytes = sizeof(T) * size_t(NB) * per;
+      cfg.dynamicSmemBytes = panel_smem_bytes<T, NB>(per);
       cfg.stream = s;
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
@@ -833,6 +867,18 @@ cudaError_t launch_invert_diag(const FrontDev *fr, int nfront, int max_s, const 
 }
 
 template <typename T>
+size_t step_smem() {
+  const size_t bytes = sizeof(T) * (kBS * kBS + 2 * kBS * kMaxRhs);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_fwd_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    cudaFuncSetAttribute(k_bwd_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    attr = true;
+  }
+  return bytes;
+}
+
+template <typename T>
 cudaError_t launch_solve_fwd_level_impl(const FrontDev *fr, int lo, int nfront, int max_s, int max_f, const T *fronts,
                                         const T *dinv, const int32_t *perm, const int32_t *idx, T *y, int64_t ldy,
                                         int nrhs, T *work, T *zbuf, const int64_t *work_off, cudaStream_t s,
@@ -845,7 +891,8 @@ cudaError_t launch_solve_fwd_level_impl(const FrontDev *fr, int lo, int nfront, 
   for (int c0 = 0; c0 < max_s; c0 += kBS) {
     const int rest = max_f - c0 - 1;
     const int nb = std::max(1, cdiv(std::max(rest, 1), kRowsPerCta));
-    k_fwd_step<T><<<dim3(nb, nfront), kRowsPerCta, 0, s>>>(frl, c0, fronts, dinv, nrhs, work, zbuf, work_off, lo);
+    k_fwd_step<T><<<dim3(nb, nfront), kRowsPerCta, step_smem<T>(), s>>>(frl, c0, fronts, dinv, nrhs, work, zbuf,
+                                                                       work_off, lo);
     ++nl;
   }
   k_fwd_scatter<T><<<dim3(cdiv(max_f, 256), nfront), 256, 0, s>>>(frl, idx, y, ldy, nrhs, work, zbuf, work_off, lo);
@@ -867,7 +914,8 @@ cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, 
   const int last = ((max_s - 1) / kBS) * kBS;
   for (int c0 = last; c0 >= 0; c0 -= kBS) {
     const int nb = std::max(1, cdiv(c0, kRowsPerCta));
-    k_bwd_step<T><<<dim3(nb, nfront), kRowsPerCta, 0, s>>>(frl, c0, fronts, dinv, nrhs, work, zbuf, work_off, lo);
+    k_bwd_step<T><<<dim3(nb, nfront), kRowsPerCta, step_smem<T>(), s>>>(frl, c0, fronts, dinv, nrhs, work, zbuf,
+                                                                       work_off, lo);
     ++nl;
   }
   k_bwd_scatter<T><<<dim3(cdiv(max_s, 256), nfront), 256, 0, s>>>(frl, idx, y, ldy, nrhs, zbuf, work_off, lo);
