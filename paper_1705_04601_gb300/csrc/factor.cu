@@ -174,6 +174,11 @@ __global__ void __launch_bounds__(kClusterPanelThreads) k_panel_cluster(const Fr
   unsigned char *done = reinterpret_cast<unsigned char *>(dest + per);  // [per] retired pivot rows
   __shared__ T cand_v[2];
   __shared__ int cand_i[2];
+  __shared__ T cand_row[2][NB];
+  __shared__ T allrow[32 * NB];
+  __shared__ T allv[32];
+  __shared__ int alli[32];
+  __shared__ int s_w;
   __shared__ T urow[NB];
   __shared__ T redv[kClusterPanelThreads / 32];
   __shared__ int redi[kClusterPanelThreads / 32];
@@ -205,34 +210,51 @@ __global__ void __launch_bounds__(kClusterPanelThreads) k_panel_cluster(const Fr
     }
     if (lane == 0) redv[wid] = bv, redi[wid] = bi;
     __syncthreads();
-    if (tid == 0) {
-      T v = redv[0];
-      int i = redi[0];
-      for (int w = 1; w < (nt >> 5); ++w)
-        if (redv[w] > v || (redv[w] == v && redi[w] < i)) v = redv[w], i = redi[w];
-      cand_v[buf] = v;
-      cand_i[buf] = i;
-    }
-    cluster.sync();
     if (wid == 0) {
-      T v = T(-1);
-      int i = INT_MAX;
-      if (lane < C) {
-        v = cluster.map_shared_rank(cand_v, lane)[buf];
-        i = cluster.map_shared_rank(cand_i, lane)[buf];
-      }
+      T v = lane < (nt >> 5) ? redv[lane] : T(-1);
+      int i = lane < (nt >> 5) ? redi[lane] : INT_MAX;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const T ov = __shfl_xor_sync(0xffffffffu, v, o);
         const int oi = __shfl_xor_sync(0xffffffffu, i, o);
         if (ov > v || (ov == v && oi < i)) v = ov, i = oi;
       }
+      if (lane == 0) cand_v[buf] = v, cand_i[buf] = i;
+      // publish the candidate row itself so that one remote round trip suffices
+      const int li = (i == INT_MAX) ? -1 : i - r_lo;
+      for (int c = lane; c < jb; c += 32) cand_row[buf][c] = li >= 0 ? P[c * per + li] : T(0);
+    }
+    cluster.sync();
+    // read every CTA's candidate value, index and row in one go
+    for (int e = tid; e < C * (jb + 2); e += nt) {
+      const int q = e / (jb + 2), c = e % (jb + 2);
+      if (c < jb)
+        allrow[q * NB + c] = cluster.map_shared_rank(&cand_row[0][0], q)[buf * NB + c];
+      else if (c == jb)
+        allv[q] = cluster.map_shared_rank(cand_v, q)[buf];
+      else
+        alli[q] = cluster.map_shared_rank(cand_i, q)[buf];
+    }
+    __syncthreads();
+    if (wid == 0) {
+      T v = lane < C ? allv[lane] : T(-1);
+      int i = lane < C ? alli[lane] : INT_MAX;
+      int w = lane;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        const int ow = __shfl_xor_sync(0xffffffffu, w, o);
+        if (ov > v || (ov == v && oi < i)) v = ov, i = oi, w = ow;
+      }
       if (lane == 0) {
-        if (i == INT_MAX) {  // no finite candidate: take the first live row, flag the front
+        if (i == INT_MAX) {  // no finite candidate
           i = -1;
+          w = -1;
           if (rank == 0) atomicOr(err, 2);
         }
         hist[j] = i;
+        s_w = w;
       }
     }
     __syncthreads();
@@ -249,12 +271,13 @@ __global__ void __launch_bounds__(kClusterPanelThreads) k_panel_cluster(const Fr
       __syncthreads();
       if (tid == 0) hist[j] = p;
       __syncthreads();
+      const int own = (p - j0) / per;
+      const T *Pp = cluster.map_shared_rank(P, own);
+      for (int c = tid; c < jb; c += nt) urow[c] = Pp[c * per + (p - (j0 + own * per))];
+    } else {
+      for (int c = tid; c < jb; c += nt) urow[c] = allrow[s_w * NB + c];
     }
-    const int own = (p - j0) / per;
-    const T *Pp = cluster.map_shared_rank(P, own);
-    const int lp = p - (j0 + own * per);
-    for (int c = tid; c < jb; c += nt) urow[c] = Pp[c * per + lp];
-    if (rank == own && tid == 0) done[lp] = 1;
+    if (p >= r_lo && p < r_lo + nr && tid == 0) done[p - r_lo] = 1;
     __syncthreads();
     const T pv = urow[j];
     if (pv == T(0)) {
@@ -363,8 +386,9 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const FrontDev *__restrict__ 
 }
 
 // trailing update: A[t0:f, t0:f] -= A[t0:f, j0:j0+jb] * A[j0:j0+jb, t0:f], t0 = j0 + jb.
-// Each thread owns a TM x TN block of contiguous rows and columns; the C tile is
-// prefetched into the accumulators while the two operand tiles are staged.
+// Each thread owns TM rows x TN columns of the tile, interleaved so that a warp
+// touches consecutive rows of C (coalesced); the C tile is prefetched into the
+// accumulators while the two operand tiles are staged.
 template <typename T, int BM, int BN, int TM, int TN, int NB>
 __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict__ fr, int j0, T *__restrict__ fronts) {
   constexpr int PB = BN + 16 / int(sizeof(T));  // padded row of the B tile (keeps 16-byte alignment)
@@ -381,14 +405,15 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
   T *sA = reinterpret_cast<T *>(smraw);  // [NB][BM]
   T *sB = sA + NB * BM;                   // [NB][PB]
   const int tid = threadIdx.x;
-  const int tr = tid % (BM / TM), tc = tid / (BM / TM);
+  constexpr int RT = BM / TM, CT = BN / TN;  // thread grid over the tile (rows fastest)
+  const int tr = tid % RT, tc = tid / RT;
   T acc[TM][TN];
 #pragma unroll
   for (int j = 0; j < TN; ++j) {
-    const int c = cb + tc * TN + j;
+    const int c = cb + tc + CT * j;
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
-      const int r = rb + tr * TM + i;
+      const int r = rb + tr + RT * i;
       acc[i][j] = (c < nrest && r < nrest) ? A[(t0 + r) + int64_t(t0 + c) * ld] : T(0);
     }
   }
@@ -406,9 +431,9 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
   for (int k = 0; k < jb; ++k) {
     T a[TM], b[TN];
 #pragma unroll
-    for (int i = 0; i < TM; ++i) a[i] = sA[k * BM + tr * TM + i];
+    for (int i = 0; i < TM; ++i) a[i] = sA[k * BM + tr + RT * i];
 #pragma unroll
-    for (int j = 0; j < TN; ++j) b[j] = sB[k * PB + tc * TN + j];
+    for (int j = 0; j < TN; ++j) b[j] = sB[k * PB + tc + CT * j];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -416,12 +441,12 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
   }
 #pragma unroll
   for (int j = 0; j < TN; ++j) {
-    const int c = cb + tc * TN + j;
+    const int c = cb + tc + CT * j;
     if (c >= nrest) continue;
     T *Cc = A + int64_t(t0 + c) * ld + t0;
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
-      const int r = rb + tr * TM + i;
+      const int r = rb + tr + RT * i;
       if (r < nrest) Cc[r] = acc[i][j];
     }
   }
@@ -563,36 +588,54 @@ __device__ void diag_apply(const T *Dinv, const T *W, int64_t ldw, int c0, int c
   __syncthreads();
 }
 
-// rows [r_lo, r_hi) of W -= A[rows, c0:c0+cb] * sX (one row per thread, all right-hand sides)
+// rows [row0, min(row0 + kStepRows, r_hi)) of W -= A[rows, c0:c0+cb] * sX.
+// Four threads share a row, each a quarter of the cb columns; the partial sums
+// meet in shared memory (sRed may alias the inverted block, no longer needed).
+constexpr int kStepThreads = 256, kStepRows = 64;
 template <typename T>
-__device__ void slab_update(const T *A, int64_t ld, T *W, int64_t ldw, int r, int r_hi, int c0, int cb, int nrhs,
-                            const T *sX) {
-  if (r >= r_hi) return;
+__device__ void slab_update(const T *A, int64_t ld, T *W, int64_t ldw, int row0, int r_hi, int c0, int cb, int nrhs,
+                            const T *sX, T *sRed) {
+  const int tid = threadIdx.x;
+  const int rl = tid % kStepRows, qq = tid / kStepRows;
+  const int r = row0 + rl;
+  constexpr int kQ = kBS / (kStepThreads / kStepRows);
+  const int q0 = qq * kQ, q1 = min(cb, q0 + kQ);
   T acc[kMaxRhs];
 #pragma unroll
   for (int c = 0; c < kMaxRhs; ++c) acc[c] = T(0);
-#pragma unroll 8
-  for (int q = 0; q < cb; ++q) {
-    const T a = A[r + int64_t(c0 + q) * ld];
+  if (r < r_hi) {
+#pragma unroll 4
+    for (int q = q0; q < q1; ++q) {
+      const T a = A[r + int64_t(c0 + q) * ld];
 #pragma unroll
-    for (int c = 0; c < kMaxRhs; ++c)
-      if (c < nrhs) acc[c] += a * sX[q + c * kBS];
+      for (int c = 0; c < kMaxRhs; ++c)
+        if (c < nrhs) acc[c] += a * sX[q + c * kBS];
+    }
   }
+  __syncthreads();  // sRed aliases the inverted block: every thread is done with it
 #pragma unroll
   for (int c = 0; c < kMaxRhs; ++c)
-    if (c < nrhs) W[r + int64_t(c) * ldw] -= acc[c];
+    if (c < nrhs) sRed[(qq * kStepRows + rl) * kMaxRhs + c] = acc[c];
+  __syncthreads();
+  if (qq == 0 && r < r_hi)
+    for (int c = 0; c < nrhs; ++c) {
+      T t = T(0);
+#pragma unroll
+      for (int g = 0; g < kStepThreads / kStepRows; ++g) t += sRed[(g * kStepRows + rl) * kMaxRhs + c];
+      W[r + int64_t(c) * ldw] -= t;
+    }
 }
 
 // forward step of column block [c0, c0+cb): x = Linv W_c0 -> Z; rows below -= L x
 template <typename T>
-__global__ void __launch_bounds__(kRowsPerCta) k_fwd_step(const FrontDev *__restrict__ fr, int c0,
-                                                          const T *__restrict__ fronts, const T *__restrict__ dinv,
-                                                          int nrhs, T *__restrict__ work, T *__restrict__ zbuf,
-                                                          const int64_t *__restrict__ work_off, int lo) {
+__global__ void __launch_bounds__(kStepThreads) k_fwd_step(const FrontDev *__restrict__ fr, int c0,
+                                                           const T *__restrict__ fronts, const T *__restrict__ dinv,
+                                                           int nrhs, T *__restrict__ work, T *__restrict__ zbuf,
+                                                           const int64_t *__restrict__ work_off, int lo) {
   const FrontDev F = fr[blockIdx.y];
   if (c0 >= F.s) return;
   const int cb = min(kBS, F.s - c0);
-  const int r0 = c0 + cb + int(blockIdx.x) * kRowsPerCta;
+  const int r0 = c0 + cb + int(blockIdx.x) * kStepRows;
   if (blockIdx.x > 0 && r0 >= F.f) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   T *sD = reinterpret_cast<T *>(smraw);
@@ -607,19 +650,19 @@ __global__ void __launch_bounds__(kRowsPerCta) k_fwd_step(const FrontDev *__rest
       Z[(c0 + r) + int64_t(c) * F.f] = sX[r + c * kBS];
     }
   }
-  slab_update<T>(fronts + F.off, F.f, W, F.f, r0 + threadIdx.x, F.f, c0, cb, nrhs, sX);
+  slab_update<T>(fronts + F.off, F.f, W, F.f, r0, F.f, c0, cb, nrhs, sX, sD);
 }
 
 // backward step of column block [c0, c0+cb): x = Uinv W_c0 -> Z; rows above -= U x
 template <typename T>
-__global__ void __launch_bounds__(kRowsPerCta) k_bwd_step(const FrontDev *__restrict__ fr, int c0,
-                                                          const T *__restrict__ fronts, const T *__restrict__ dinv,
-                                                          int nrhs, T *__restrict__ work, T *__restrict__ zbuf,
-                                                          const int64_t *__restrict__ work_off, int lo) {
+__global__ void __launch_bounds__(kStepThreads) k_bwd_step(const FrontDev *__restrict__ fr, int c0,
+                                                           const T *__restrict__ fronts, const T *__restrict__ dinv,
+                                                           int nrhs, T *__restrict__ work, T *__restrict__ zbuf,
+                                                           const int64_t *__restrict__ work_off, int lo) {
   const FrontDev F = fr[blockIdx.y];
   if (c0 >= F.s) return;
   const int cb = min(kBS, F.s - c0);
-  const int r0 = int(blockIdx.x) * kRowsPerCta;
+  const int r0 = int(blockIdx.x) * kStepRows;
   if (blockIdx.x > 0 && r0 >= c0) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   T *sD = reinterpret_cast<T *>(smraw);
@@ -634,7 +677,7 @@ __global__ void __launch_bounds__(kRowsPerCta) k_bwd_step(const FrontDev *__rest
       Z[(c0 + r) + int64_t(c) * F.f] = sX[r + c * kBS];
     }
   }
-  slab_update<T>(fronts + F.off, F.f, W, F.f, r0 + threadIdx.x, c0, c0, cb, nrhs, sX);
+  slab_update<T>(fronts + F.off, F.f, W, F.f, r0, c0, c0, cb, nrhs, sX, sD);
 }
 
 // rows [0, s) of W -= U12 * W[s:f] (before the backward block sweep); the
@@ -890,8 +933,8 @@ cudaError_t launch_solve_fwd_level_impl(const FrontDev *fr, int lo, int nfront, 
   k_fwd_gather<T><<<dim3(cdiv(max_f, 256), nfront), 256, 0, s>>>(frl, perm, idx, y, ldy, nrhs, work, work_off, lo);
   for (int c0 = 0; c0 < max_s; c0 += kBS) {
     const int rest = max_f - c0 - 1;
-    const int nb = std::max(1, cdiv(std::max(rest, 1), kRowsPerCta));
-    k_fwd_step<T><<<dim3(nb, nfront), kRowsPerCta, step_smem<T>(), s>>>(frl, c0, fronts, dinv, nrhs, work, zbuf,
+    const int nb = std::max(1, cdiv(std::max(rest, 1), kStepRows));
+    k_fwd_step<T><<<dim3(nb, nfront), kStepThreads, step_smem<T>(), s>>>(frl, c0, fronts, dinv, nrhs, work, zbuf,
                                                                        work_off, lo);
     ++nl;
   }
@@ -913,8 +956,8 @@ cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, 
       frl, fronts, nrhs, work, work_off, lo);
   const int last = ((max_s - 1) / kBS) * kBS;
   for (int c0 = last; c0 >= 0; c0 -= kBS) {
-    const int nb = std::max(1, cdiv(c0, kRowsPerCta));
-    k_bwd_step<T><<<dim3(nb, nfront), kRowsPerCta, step_smem<T>(), s>>>(frl, c0, fronts, dinv, nrhs, work, zbuf,
+    const int nb = std::max(1, cdiv(c0, kStepRows));
+    k_bwd_step<T><<<dim3(nb, nfront), kStepThreads, step_smem<T>(), s>>>(frl, c0, fronts, dinv, nrhs, work, zbuf,
                                                                        work_off, lo);
     ++nl;
   }
