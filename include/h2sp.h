@@ -88,6 +88,13 @@ typedef enum {
  * cluster's children come in increasing number.  Row and column cluster
  * trees are the same tree.  Column ranks equal row ranks.
  *
+ * Batched form: depth 0 may hold several roots.  Each root's tree is then an
+ * independent system (a diagonal block of A; no close or admissible pair may
+ * join two trees, else H2SP_EINVAL).  All systems go through the same
+ * launches level by level, their supernodes are factored in the same
+ * elimination levels, and iterative solves stop when every system's relative
+ * residual (per right-hand side) meets the tolerance.
+ *
  * Blocks are column-major and packed; *_off arrays give each block's first
  * element in the packed array.
  */

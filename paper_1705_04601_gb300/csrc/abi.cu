@@ -91,6 +91,8 @@ struct h2sp_handle {
   int32_t *child_start = nullptr, *child_cnt = nullptr;
   double *xh = nullptr, *yh = nullptr;
   double *norms = nullptr;
+  int64_t *seg_ptr = nullptr;  // row ranges of the independent systems (roots)
+  int nseg = 1;
   double plan_seconds = 0.0;
   bool device_ready = false;
   Prof prof;
@@ -487,7 +489,11 @@ int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream s
           h->near_bytes += 8.0 * double(p.h_size[p.level_ptr[p.D] + lf]) * double(p.h_size[p.near_col[z]]);
       h->xh = h->alloc<double>(size_t(std::max<int64_t>(p.xh_elems, 1)) * 16);
       h->yh = h->alloc<double>(size_t(std::max<int64_t>(p.xh_elems, 1)) * 16);
-      h->norms = h->alloc<double>(64);
+      std::vector<int64_t> sp(1, 0);
+      for (int r = 0; r < p.level_ptr[1]; ++r) sp.push_back(p.h_begin[r] + p.h_size[r]);
+      h->nseg = int(sp.size()) - 1;
+      h->seg_ptr = h->upload(sp);
+      h->norms = h->alloc<double>(size_t(h->nseg) * 64);
     }
     // ---- symbolic factorization uploads ----
     {
@@ -671,10 +677,11 @@ int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *o, int32_t nrhs, const dou
     }
     // iterative refinement on the FP64 H^2 residual (§5.5)
     const int64_t n = p.n;
-    std::vector<double> bn2(nrhs), rn2(nrhs);
-    ck(launch_colnorm2(b, ldb, n, nrhs, h->norms, s));
+    const int ns = h->nseg;
+    std::vector<double> bn2(size_t(nrhs) * ns), rn2(size_t(nrhs) * ns);
+    ck(launch_colnorm2(b, ldb, h->seg_ptr, ns, n, nrhs, h->norms, s));
     h->prof.count(P_OTHER, 1);
-    ck(cudaMemcpyAsync(bn2.data(), h->norms, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+    ck(cudaMemcpyAsync(bn2.data(), h->norms, sizeof(double) * nrhs * ns, cudaMemcpyDeviceToHost, s));
     ck(cudaStreamSynchronize(s));
     const int maxit = o->maxit > 0 ? o->maxit : 50;
     double res = INFINITY;
@@ -682,12 +689,12 @@ int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *o, int32_t nrhs, const dou
     precond(h, b, ldb, x, ldx, nrhs);  // x_0 = M^-1 b
     for (;;) {
       h2_matvec(h, x, ldx, h->vecT, n, nrhs);
-      ck(launch_residual(b, ldb, h->vecT, n, h->vecR, n, n, nrhs, h->norms, s));
+      ck(launch_residual(b, ldb, h->vecT, n, h->vecR, n, h->seg_ptr, ns, n, nrhs, h->norms, s));
       h->prof.count(P_OTHER, 1);
-      ck(cudaMemcpyAsync(rn2.data(), h->norms, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+      ck(cudaMemcpyAsync(rn2.data(), h->norms, sizeof(double) * nrhs * ns, cudaMemcpyDeviceToHost, s));
       ck(cudaStreamSynchronize(s));
-      res = 0.0;
-      for (int c = 0; c < nrhs; ++c) res = std::max(res, std::sqrt(rn2[c] / std::max(bn2[c], 1e-300)));
+      res = 0.0;  // worst system, worst column
+      for (size_t q = 0; q < rn2.size(); ++q) res = std::max(res, std::sqrt(rn2[q] / std::max(bn2[q], 1e-300)));
       if (!(res > o->tol) || it >= maxit) break;
       precond(h, h->vecR, n, h->vecT, n, nrhs);
       ck(launch_axpy(h->vecT, n, x, ldx, n, nrhs, s));

@@ -276,13 +276,17 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// per (segment, column): ||b - y||^2 over the segment's rows (y == nullptr: ||b||^2);
+// r = b - y is stored when r != nullptr.  grid = (chunks, segments, columns)
 __global__ void __launch_bounds__(256) k_residual(const double *__restrict__ b, int64_t ldb, const double *__restrict__ y,
-                                                  int64_t ldy, double *__restrict__ r, int64_t ldr, int64_t n,
+                                                  int64_t ldy, double *__restrict__ r, int64_t ldr,
+                                                  const int64_t *__restrict__ seg_ptr, int nrhs,
                                                   double *__restrict__ norms2) {
-  const int c = blockIdx.y;
+  const int seg = blockIdx.y, c = blockIdx.z;
+  const int64_t lo = seg_ptr[seg], hi = seg_ptr[seg + 1];
   __shared__ double red[8];
   double part = 0.0;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+  for (int64_t i = lo + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < hi; i += int64_t(gridDim.x) * blockDim.x) {
     const double v = b[i + c * ldb] - (y ? y[i + c * ldy] : 0.0);
     if (r) r[i + c * ldr] = v;
     part += v * v;
@@ -293,7 +297,7 @@ __global__ void __launch_bounds__(256) k_residual(const double *__restrict__ b, 
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[w];
-    atomicAdd(&norms2[c], t);
+    atomicAdd(&norms2[int64_t(seg) * nrhs + c], t);
   }
 }
 
@@ -402,19 +406,17 @@ cudaError_t static_scratch_address(double **out) {
 }
 
 cudaError_t launch_residual(const double *b, int64_t ldb, const double *y, int64_t ldy, double *r, int64_t ldr,
-                            int64_t n, int nrhs, double *norms2, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(norms2, 0, sizeof(double) * nrhs, s);
+                            const int64_t *seg_ptr, int nseg, int64_t n, int nrhs, double *norms2, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(norms2, 0, sizeof(double) * nrhs * nseg, s);
   if (e != cudaSuccess) return e;
-  k_residual<<<dim3(grid_for(n), nrhs), 256, 0, s>>>(b, ldb, y, ldy, r, ldr, n, norms2);
+  const unsigned chunks = unsigned(std::max<int64_t>(1, std::min<int64_t>(64, (n / std::max(nseg, 1) + 4095) / 4096)));
+  k_residual<<<dim3(chunks, nseg, nrhs), 256, 0, s>>>(b, ldb, y, ldy, r, ldr, seg_ptr, nrhs, norms2);
   return cudaGetLastError();
 }
 
-cudaError_t launch_colnorm2(const double *x, int64_t ldx, int64_t n, int nrhs, double *norms2, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(norms2, 0, sizeof(double) * nrhs, s);
-  if (e != cudaSuccess) return e;
-  // ||x||^2 as the residual of x against zero
-  k_residual<<<dim3(grid_for(n), nrhs), 256, 0, s>>>(x, ldx, nullptr, 0, nullptr, 0, n, norms2);
-  return cudaGetLastError();
+cudaError_t launch_colnorm2(const double *x, int64_t ldx, const int64_t *seg_ptr, int nseg, int64_t n, int nrhs,
+                            double *norms2, cudaStream_t s) {
+  return launch_residual(x, ldx, nullptr, 0, nullptr, 0, seg_ptr, nseg, n, nrhs, norms2, s);
 }
 
 cudaError_t launch_axpy(const double *d, int64_t ldd, double *x, int64_t ldx, int64_t n, int nrhs, cudaStream_t s) {

@@ -386,12 +386,16 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const FrontDev *__restrict__ 
 }
 
 // trailing update: A[t0:f, t0:f] -= A[t0:f, j0:j0+jb] * A[j0:j0+jb, t0:f], t0 = j0 + jb.
-// Each thread owns TM rows x TN columns of the tile, interleaved so that a warp
-// touches consecutive rows of C (coalesced); the C tile is prefetched into the
-// accumulators while the two operand tiles are staged.
+// Thread (tr, tc) owns rows tr + RT*i and columns tc + CT*j of the tile, so a
+// warp touches consecutive rows of C (coalesced).  The operand tiles are
+// stored permuted in shared memory -- row tr + RT*i of the A tile at
+// tr*TM + i -- so each thread reads its TM (TN) values as 16-byte vectors.
+// The C tile is prefetched into the accumulators while the operands are staged.
 template <typename T, int BM, int BN, int TM, int TN, int NB>
 __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict__ fr, int j0, T *__restrict__ fronts) {
-  constexpr int PB = BN + 16 / int(sizeof(T));  // padded row of the B tile (keeps 16-byte alignment)
+  constexpr int RT = BM / TM, CT = BN / TN;  // thread grid over the tile (rows fastest)
+  constexpr int PA = BM + 16 / int(sizeof(T)), PB = BN + 16 / int(sizeof(T));  // padded rows, 16-byte aligned
+  constexpr int VA = 16 / int(sizeof(T));    // elements per 16-byte vector
   const FrontDev F = fr[blockIdx.z];
   if (j0 >= F.s) return;
   const int jb = min(NB, F.s - j0);
@@ -402,10 +406,9 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
   T *A = fronts + F.off;
   const int64_t ld = F.f;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T *sA = reinterpret_cast<T *>(smraw);  // [NB][BM]
-  T *sB = sA + NB * BM;                   // [NB][PB]
+  T *sA = reinterpret_cast<T *>(smraw);  // [NB][PA]
+  T *sB = sA + NB * PA;                   // [NB][PB]
   const int tid = threadIdx.x;
-  constexpr int RT = BM / TM, CT = BN / TN;  // thread grid over the tile (rows fastest)
   const int tr = tid % RT, tc = tid / RT;
   T acc[TM][TN];
 #pragma unroll
@@ -418,22 +421,40 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
     }
   }
   for (int e = tid; e < jb * BM; e += 256) {
-    const int i = e % BM, k = e / BM;
+    const int i = e % BM, k = e / BM;  // tile row i = (i % RT) + RT * (i / RT)
     const int r = rb + i;
-    sA[k * BM + i] = (r < nrest) ? A[(t0 + r) + int64_t(j0 + k) * ld] : T(0);
+    sA[k * PA + (i % RT) * TM + i / RT] = (r < nrest) ? A[(t0 + r) + int64_t(j0 + k) * ld] : T(0);
   }
   for (int e = tid; e < jb * BN; e += 256) {
     const int k = e % jb, j = e / jb;
     const int c = cb + j;
-    sB[k * PB + j] = (c < nrest) ? A[(j0 + k) + int64_t(t0 + c) * ld] : T(0);
+    sB[k * PB + (j % CT) * TN + j / CT] = (c < nrest) ? A[(j0 + k) + int64_t(t0 + c) * ld] : T(0);
   }
   __syncthreads();
   for (int k = 0; k < jb; ++k) {
     T a[TM], b[TN];
+    const T *pa = sA + k * PA + tr * TM;
+    const T *pb = sB + k * PB + tc * TN;
 #pragma unroll
-    for (int i = 0; i < TM; ++i) a[i] = sA[k * BM + tr + RT * i];
+    for (int v = 0; v < TM; v += VA) {
+      if constexpr (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(pa + v);
+        a[v] = q.x, a[v + 1] = q.y, a[v + 2] = q.z, a[v + 3] = q.w;
+      } else {
+        const double2 q = *reinterpret_cast<const double2 *>(pa + v);
+        a[v] = q.x, a[v + 1] = q.y;
+      }
+    }
 #pragma unroll
-    for (int j = 0; j < TN; ++j) b[j] = sB[k * PB + tc + CT * j];
+    for (int v = 0; v < TN; v += VA) {
+      if constexpr (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(pb + v);
+        b[v] = q.x, b[v + 1] = q.y, b[v + 2] = q.z, b[v + 3] = q.w;
+      } else {
+        const double2 q = *reinterpret_cast<const double2 *>(pb + v);
+        b[v] = q.x, b[v + 1] = q.y;
+      }
+    }
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -815,7 +836,7 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
   constexpr int NB = LuCfg<T>::NB;
   using G = GemmCfg<T>;
   auto gemm = k_gemm_update<T, G::BM, G::BN, G::TM, G::TN, NB>;
-  const size_t gsmem = sizeof(T) * NB * (G::BM + G::BN + 16 / sizeof(T));
+  const size_t gsmem = sizeof(T) * NB * (G::BM + G::BN + 2 * (16 / sizeof(T)));
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gsmem));

@@ -98,7 +98,7 @@ struct Plan {
   int D = 0, lstop = 0, ncl = 0, nleaf = 0;
   bool sym = true;
   // per cluster
-  std::vector<int32_t> level, parent, rank;
+  std::vector<int32_t> level, parent, rank, root;
   std::vector<int64_t> m, kp, d, off, xoff;
   std::vector<int64_t> q_off, rr_off;   // offsets in the Q / Rr buffers (-1 if none)
   // S nodes

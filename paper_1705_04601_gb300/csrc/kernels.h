@@ -117,10 +117,11 @@ constexpr int64_t kStaticScratchElems = int64_t(1) << 21;
 // Device address of that workspace on the current device (looked up once per device).
 cudaError_t static_scratch_address(double **out);
 
-// r = b - y; norms2[c] = ||r_c||^2 (atomic FP64 accumulation), over n rows
+// r = b - y; norms2[seg * nrhs + c] = ||r_c||^2 over the rows [seg_ptr[seg], seg_ptr[seg+1])
 cudaError_t launch_residual(const double *b, int64_t ldb, const double *y, int64_t ldy, double *r, int64_t ldr,
-                            int64_t n, int nrhs, double *norms2, cudaStream_t s);
-cudaError_t launch_colnorm2(const double *x, int64_t ldx, int64_t n, int nrhs, double *norms2, cudaStream_t s);
+                            const int64_t *seg_ptr, int nseg, int64_t n, int nrhs, double *norms2, cudaStream_t s);
+cudaError_t launch_colnorm2(const double *x, int64_t ldx, const int64_t *seg_ptr, int nseg, int64_t n, int nrhs,
+                            double *norms2, cudaStream_t s);
 // x += d
 cudaError_t launch_axpy(const double *d, int64_t ldd, double *x, int64_t ldx, int64_t n, int nrhs, cudaStream_t s);
 cudaError_t launch_cast_d2f(const double *a, int64_t lda, float *b, int64_t ldb, int64_t n, int nrhs, cudaStream_t s);

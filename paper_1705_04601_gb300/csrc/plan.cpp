@@ -61,7 +61,7 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
     REQUIRE(sym || (d->col_leaf_basis_off && d->col_transfer_off), "missing column offset arrays");
     const int D = d->depth;
     const int32_t *lp = d->level_ptr;
-    REQUIRE(lp[0] == 0 && lp[1] == 1, "depth 0 must hold exactly the root");
+    REQUIRE(lp[0] == 0 && lp[1] >= 1, "depth 0 must hold the root(s)");
     for (int dd = 1; dd <= D; ++dd) REQUIRE(lp[dd + 1] > lp[dd], "empty depth");
     const int ncl = lp[D + 1];
     const int nleaf = lp[D + 1] - lp[D];
@@ -78,9 +78,9 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
     std::vector<int32_t> dep(ncl);
     for (int dd = 0; dd <= D; ++dd)
       for (int t = lp[dd]; t < lp[dd + 1]; ++t) dep[t] = dd;
-    REQUIRE(p.parent[0] == -1, "root parent must be -1");
+    for (int c = 0; c < lp[1]; ++c) REQUIRE(p.parent[c] == -1, "root parent must be -1");
     std::vector<int32_t> nkids(ncl, 0);
-    for (int c = 1; c < ncl; ++c) {
+    for (int c = lp[1]; c < ncl; ++c) {
       int pa = p.parent[c];
       REQUIRE(pa >= 0 && pa < ncl && dep[pa] == dep[c] - 1, "parent not one depth up");
       if (c > lp[dep[c]]) REQUIRE(pa >= p.parent[c - 1], "children of a cluster must be consecutive");
@@ -98,7 +98,7 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
     {
       std::vector<int64_t> sz(ncl, 0), bg(ncl, -1);
       for (int t = lp[D]; t < lp[D + 1]; ++t) sz[t] = p.h_size[t], bg[t] = p.h_begin[t];
-      for (int c = ncl - 1; c >= 1; --c) {
+      for (int c = ncl - 1; c >= lp[1]; --c) {
         int pa = p.parent[c];
         sz[pa] += sz[c];
         bg[pa] = bg[c];  // children visited downwards: ends at the first child
@@ -106,6 +106,9 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
       for (int t = 0; t < lp[D]; ++t)
         REQUIRE(sz[t] == p.h_size[t] && bg[t] == p.h_begin[t], "cluster range differs from its children");
     }
+    // root of every cluster: depth 0 may hold several roots (independent systems)
+    p.root.assign(ncl, 0);
+    for (int c = 0; c < ncl; ++c) p.root[c] = c < lp[1] ? c : p.root[p.parent[c]];
     // lists
     p.far_ptr.assign(d->far_ptr, d->far_ptr + ncl + 1);
     const int64_t nfar = p.far_ptr[ncl];
@@ -118,7 +121,8 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
         int s = p.far_col[i];
         REQUIRE(s >= 0 && s < ncl && dep[s] == dep[t], "far pair across depths");
         if (i > p.far_ptr[t]) REQUIRE(s > p.far_col[i - 1], "far_col not ascending");
-        REQUIRE(t != 0, "the root cannot be admissible");
+        REQUIRE(dep[t] > 0, "a root cannot be admissible");
+        REQUIRE(p.root[s] == p.root[t], "admissible pair across independent systems");
       }
     }
     p.near_ptr.assign(d->near_ptr, d->near_ptr + nleaf + 1);
@@ -131,6 +135,7 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
         int s = p.near_col[i];
         REQUIRE(s >= lp[D] && s < lp[D + 1], "close pair with a non-leaf");
         if (i > p.near_ptr[lf]) REQUIRE(s > p.near_col[i - 1], "near_col not ascending");
+        REQUIRE(p.root[s] == p.root[lp[D] + lf], "close pair across independent systems");
       }
     }
     p.leaf_basis_off.assign(d->leaf_basis_off, d->leaf_basis_off + nleaf);
@@ -560,7 +565,7 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
     for (int v = 0; v < nn; ++v) {
       int l = p.node_level[v], t = p.node_cluster[v];
       if (l == lstop) {
-        p.closure[v] = 0;
+        p.closure[v] = p.root[t];
         continue;
       }
       int c = t;

@@ -636,3 +636,160 @@ def make_small(n: int = 512, kernel: str = "log", leaf: int = 32, tol: Optional[
     h = build_h2(pts, kernel, leaf, tol=tol)
     b = rng.standard_normal((n, nrhs))
     return h, b
+
+
+# --------------------------------------------------------------------------
+# batched form: several independent H^2 matrices as one forest
+# --------------------------------------------------------------------------
+
+
+def _push_down(h: H2Matrix, D: int) -> dict:
+    """Per-depth cluster lists of h extended to leaf depth D: every leaf gets a
+    chain of virtual single-child clusters with an identity transfer."""
+    lp = h.level_ptr
+    d0 = h.depth
+    kids = [[] for _ in range(h.ncl)]
+    for c in range(1, h.ncl):
+        kids[int(h.parent[c])].append(c)
+    # node = (orig cluster id, virtual level offset)
+    levels = [[(t, 0) for t in range(lp[d], lp[d + 1])] for d in range(d0 + 1)]
+    for dd in range(d0 + 1, D + 1):
+        levels.append([(t, v + 1) for (t, v) in levels[dd - 1]])
+    return {"levels": levels}
+
+
+def make_forest(systems: list) -> H2Matrix:
+    """Concatenate independent H^2 matrices into one forest descriptor.
+
+    Depth 0 holds one root per system; every tree is pushed down to the
+    deepest leaf depth by virtual single-child chains (identity transfers,
+    same points); clusters are renumbered depth by depth, system by system,
+    so the children of a cluster stay consecutive and every system owns a
+    contiguous range of rows.  No pair of clusters of different systems is
+    close or admissible, so A is block diagonal with the given blocks."""
+    D = max(h.depth for h in systems)
+    sym = all(h.col_rank is None for h in systems)
+    if not sym and any(h.col_rank is None for h in systems):
+        raise ValueError("mixed symmetric / non-symmetric systems")
+    ext = [_push_down(h, D) for h in systems]
+    # new ids
+    newid = []     # per system: dict (depth, t, v) -> new id
+    level_ptr = [0]
+    order = []     # per depth: list of (sys, t, v)
+    for d in range(D + 1):
+        lst = []
+        for k, h in enumerate(systems):
+            lst.extend((k, t, v) for (t, v) in ext[k]["levels"][d])
+        order.append(lst)
+        level_ptr.append(level_ptr[-1] + len(lst))
+    ids = [dict() for _ in systems]
+    for d in range(D + 1):
+        for j, (k, t, v) in enumerate(order[d]):
+            ids[k][(d, t, v)] = level_ptr[d] + j
+    ncl = level_ptr[-1]
+    parent = np.full(ncl, -1, dtype=np.int32)
+    begin = np.zeros(ncl, dtype=np.int64)
+    size = np.zeros(ncl, dtype=np.int64)
+    rank = np.zeros(ncl, dtype=np.int32)
+    crank = np.zeros(ncl, dtype=np.int32)
+    orig = [None] * ncl
+    row0 = np.cumsum([0] + [h.n for h in systems])
+    for d in range(D + 1):
+        for (k, t, v) in order[d]:
+            h = systems[k]
+            nid = ids[k][(d, t, v)]
+            orig[nid] = (k, t, v, d)
+            begin[nid] = row0[k] + h.begin[t]
+            size[nid] = h.size[t]
+            rank[nid] = h.rank[t]
+            crank[nid] = h.crank()[t]
+            if d > 0:
+                if v == 0:
+                    parent[nid] = ids[k][(d - 1, int(h.parent[t]), 0)]
+                else:
+                    parent[nid] = ids[k][(d - 1, t, v - 1)]
+    leaf0 = level_ptr[D]
+    # bases and transfers
+    lb, lbc, tr, trc = [], [], [np.zeros((0, 0))], [np.zeros((0, 0))]
+    for nid in range(leaf0, ncl):
+        k, t, v, d = orig[nid]
+        lb.append(systems[k].leaf_R(t))
+        lbc.append(systems[k].leaf_R(t, col=True))
+    for nid in range(1, ncl):
+        k, t, v, d = orig[nid]
+        if parent[nid] < 0:
+            tr.append(np.zeros((rank[nid], 0)))
+            trc.append(np.zeros((crank[nid], 0)))
+        elif v == 0:
+            tr.append(systems[k].T(t))
+            trc.append(systems[k].T(t, col=True))
+        else:
+            tr.append(np.eye(rank[nid]))
+            trc.append(np.eye(crank[nid]))
+    leaf_basis, leaf_basis_off = _pack_colmajor(lb)
+    transfer, transfer_off = _pack_colmajor(tr)
+    # far pairs keep their depth; close pairs move to the new leaf depth
+    far_rows = [[] for _ in range(ncl)]
+    for k, h in enumerate(systems):
+        for t in range(h.ncl):
+            d = int(np.searchsorted(h.level_ptr, t, side="right") - 1)
+            for i in range(int(h.far_ptr[t]), int(h.far_ptr[t + 1])):
+                s = int(h.far_col[i])
+                far_rows[ids[k][(d, t, 0)]].append((ids[k][(d, s, 0)], h.D(i, t, s)))
+    far_ptr = np.zeros(ncl + 1, dtype=np.int64)
+    far_col, Dl = [], []
+    for r in range(ncl):
+        far_rows[r].sort(key=lambda x: x[0])
+        far_ptr[r + 1] = far_ptr[r] + len(far_rows[r])
+        for (s, blk) in far_rows[r]:
+            far_col.append(s)
+            Dl.append(blk)
+    coupling, coupling_off = _pack_colmajor(Dl)
+    near_rows = [[] for _ in range(ncl - leaf0)]
+    for k, h in enumerate(systems):
+        hl0 = int(h.level_ptr[h.depth])
+        off = D - h.depth
+        for lf in range(h.nleaf):
+            t = hl0 + lf
+            for i in range(int(h.near_ptr[lf]), int(h.near_ptr[lf + 1])):
+                s = int(h.near_col[i])
+                near_rows[ids[k][(D, t, off)] - leaf0].append((ids[k][(D, s, off)], h.C(i, t, s)))
+    near_ptr = np.zeros(ncl - leaf0 + 1, dtype=np.int64)
+    near_col, Cl = [], []
+    for r in range(ncl - leaf0):
+        near_rows[r].sort(key=lambda x: x[0])
+        near_ptr[r + 1] = near_ptr[r] + len(near_rows[r])
+        for (s, blk) in near_rows[r]:
+            near_col.append(s)
+            Cl.append(blk)
+    near_block, near_off = _pack_colmajor(Cl)
+    out = H2Matrix(
+        n=int(row0[-1]), dim=systems[0].dim, depth=D, level_ptr=np.array(level_ptr, dtype=np.int32), parent=parent,
+        begin=begin, size=size, rank=rank, leaf_basis=leaf_basis, leaf_basis_off=leaf_basis_off,
+        transfer=transfer, transfer_off=transfer_off, far_ptr=far_ptr, far_col=np.array(far_col, dtype=np.int32),
+        coupling=coupling, coupling_off=coupling_off, near_ptr=near_ptr, near_col=np.array(near_col, dtype=np.int32),
+        near_block=near_block, near_off=near_off, kernel=systems[0].kernel, diag=float("nan"),
+    )
+    if not sym:
+        out.col_rank = crank
+        out.col_leaf_basis, out.col_leaf_basis_off = _pack_colmajor(lbc)
+        out.col_transfer, out.col_transfer_off = _pack_colmajor(trc)
+    out.points = np.concatenate([h.points for h in systems]) if all(h.points is not None for h in systems) else None
+    return out
+
+
+def make_batched(nsys: int, n_lo: int, n_hi: int, seed: int = SEED_BASE + 4, leaf: int = 64, tol: float = 1e-6,
+                 nrhs: int = 1):
+    """Independent 2D -log r systems on random ellipses (the batched workload).
+
+    N_k ~ U[n_lo, n_hi]; ellipse centre (0.5, 0.5), full axes ~ U[0.2, 1],
+    random rotation; diagonal -log(0.5/sqrt(N_k)).  Returns (systems, forest, b)."""
+    rng = np.random.default_rng(seed)
+    systems = []
+    for k in range(nsys):
+        nk = int(rng.integers(n_lo, n_hi + 1))
+        pts = points_ellipse(nk, np.random.default_rng(seed + 1000 * (k + 1)))
+        systems.append(build_h2(pts, "log", leaf, tol=tol))
+    forest = make_forest(systems)
+    b = rng.standard_normal((forest.n, nrhs))
+    return systems, forest, b

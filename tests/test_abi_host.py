@@ -131,3 +131,40 @@ def test_device_calls_on_an_analyzed_handle_are_refused():
     st = H.lib().h2sp_factor(hd.ptr, 0, None)
     assert st == H.H2SP_ESTATE
     hd.close()
+
+
+def test_forest_plan_is_block_diagonal():
+    """Batched form: several roots = independent systems; S never couples two of them."""
+    systems, f, _ = synth.make_batched(5, 400, 1500, leaf=32, tol=1e-8)
+    hd = H.h2sp_analyze(H.H2Input(f, device=None))
+    st = H.h2sp_export_structure(hd)
+    S = H.h2sp_export_S(hd, values=False)
+    nroots = int(f.level_ptr[1])
+    assert nroots == 5
+    root = np.zeros(f.ncl, dtype=np.int64)
+    for c in range(f.ncl):
+        root[c] = c if c < nroots else root[f.parent[c]]
+    node_root = root[st["node_cluster"]]
+    for i in range(len(S["node_size"])):
+        cols = S["bcol_idx"][S["brow_ptr"][i]:S["brow_ptr"][i + 1]]
+        assert np.all(node_root[cols] == node_root[i])
+    # every supernode lies in one system; its closure is a cluster of that system
+    for k in range(len(st["sn_ptr"]) - 1):
+        nodes = st["order"][st["sn_ptr"][k]:st["sn_ptr"][k + 1]]
+        assert len(set(node_root[nodes])) == 1
+        assert root[st["closure"][nodes[0]]] == node_root[nodes[0]]
+    assert int(S["node_size"].sum()) == f.n
+    hd.close()
+
+
+def test_forest_rejects_pairs_across_systems():
+    systems, f, _ = synth.make_batched(3, 400, 800, leaf=32, tol=1e-8)
+    inp = H.H2Input(f, device=None)
+    nc = inp.arrs["near_col"].copy()
+    last = int(f.level_ptr[-1]) - 1          # a leaf of the last system
+    nc[0] = last                              # first leaf (system 0) now "close" to it
+    inp.arrs["near_col"] = np.sort(nc[:int(f.near_ptr[1])]).tolist() + nc[int(f.near_ptr[1]):].tolist()
+    inp.arrs["near_col"] = np.array(inp.arrs["near_col"], dtype=np.int32)
+    with pytest.raises(H.H2spError) as e:
+        H.h2sp_analyze(inp)
+    assert e.value.status == H.H2SP_EINVAL

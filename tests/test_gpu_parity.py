@@ -238,3 +238,37 @@ def test_full_size_fp64_direct_and_mixed_refinement(full):
     assert r.max() <= 2e-10
     assert np.linalg.norm(x32 - x64) <= 1e-6 * np.linalg.norm(x64)
     hd.close()
+
+
+# ---------------------------------------------------------------------------
+# batched form: independent systems on random ellipses in one forest
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batched_forest_matches_individual_systems(prec):
+    systems, f, b = synth.make_batched(6, 600, 3000, leaf=32, tol=1e-8, nrhs=2)
+    hd = H.h2sp_sparsify(H.H2Input(f))
+    bt = dev(b)
+    xt = torch.empty_like(bt)
+    if prec == "fp64":
+        H.h2sp_factor(hd, H.H2SP_FP64)
+        H.h2sp_solve(hd, bt, xt, mode=H.H2SP_DIRECT)
+    else:
+        H.h2sp_factor(hd, H.H2SP_FP32)
+        info = H.h2sp_solve(hd, bt, xt, mode=H.H2SP_IR, tol=1e-10, maxit=30)
+        assert info.status == H.H2SP_OK and info.rel_residual <= 1e-10
+    torch.cuda.synchronize()
+    xg = host(xt)
+    o = 0
+    for s in systems:
+        bs = b[o:o + s.n]
+        sp = osp.sparsify(s)
+        xo = ofa.solve(s, sp, ofa.factor(s, sp), bs)
+        tol = TOL if prec == "fp64" else 1e-7
+        assert np.linalg.norm(xg[o:o + s.n] - xo) <= tol * np.linalg.norm(xo)
+        if prec == "fp32":  # every system meets the residual bound on its own
+            r = np.linalg.norm(bs - oh2.Matvec(s)(xg[o:o + s.n]), axis=0) / np.linalg.norm(bs, axis=0)
+            assert r.max() <= 2e-10
+        o += s.n
+    hd.close()
