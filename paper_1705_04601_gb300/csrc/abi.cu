@@ -478,7 +478,7 @@ int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream s
       g.col_transfer = h->col_transfer;
       g.leaf0 = p.level_ptr[p.D];
       std::vector<int32_t> cs(p.ncl, 0), cc(p.ncl, 0);
-      for (int c = p.ncl - 1; c >= 1; --c) {
+      for (int c = p.ncl - 1; c >= p.level_ptr[1]; --c) {  // every non-root cluster
         cs[p.parent[c]] = c;
         cc[p.parent[c]]++;
       }
@@ -605,6 +605,7 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
     int herr = 0;
     ck(cudaMemcpyAsync(&herr, h->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     ck(cudaStreamSynchronize(s));
+    if (herr & 4) return H2SP_ETIMEOUT;
     if (herr != 0) return H2SP_ESINGULAR;
     h->prec = prec;
   } catch (const CudaFail &f) {

@@ -16,6 +16,9 @@
 #include <algorithm>
 #include <climits>
 #include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <type_traits>
 
 #include <cooperative_groups.h>
 
@@ -830,6 +833,17 @@ cudaError_t launch_assemble(const AItem *items, int64_t n, const double *S, T *f
   return cudaGetLastError();
 }
 
+// The FP32 trailing update runs on the tensor cores (three-term TF32 split);
+// H2SP_GEMM=simt in the environment selects the FP32 SIMT kernel instead.
+inline bool use_tensor_core_gemm() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = std::getenv("H2SP_GEMM");
+    v = (e && std::strcmp(e, "simt") == 0) ? 0 : 1;
+  }
+  return v == 1;
+}
+
 template <typename T>
 cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
                             int32_t *piv, int32_t *swaps, int *err, cudaStream_t s, Prof *prof) {
@@ -883,9 +897,19 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
     prof->end(P_TRSM, 1, e0, ftrsm);
     const int rest = max_f - j0 - 1;
     if (rest > 0) {
-      dim3 g(cdiv(rest, G::BN), cdiv(rest, G::BM), nfront);
       e0 = prof->begin();
-      gemm<<<g, 256, gsmem, s>>>(fr, j0, fronts);
+      if constexpr (std::is_same<T, float>::value) {
+        if (use_tensor_core_gemm()) {
+          cudaError_t ge = launch_gemm_tc(fr, j0, nfront, max_f, fronts, err, s);
+          if (ge != cudaSuccess) return ge;
+        } else {
+          dim3 g(cdiv(rest, G::BN), cdiv(rest, G::BM), nfront);
+          gemm<<<g, 256, gsmem, s>>>(fr, j0, fronts);
+        }
+      } else {
+        dim3 g(cdiv(rest, G::BN), cdiv(rest, G::BM), nfront);
+        gemm<<<g, 256, gsmem, s>>>(fr, j0, fronts);
+      }
       prof->end(P_GEMM, 1, e0, fgemm);
     }
   }

@@ -1,0 +1,200 @@
+// Trailing update of the FP32 fronts on the 5th-generation tensor cores.
+//
+// C[t0:f, t0:f] -= L21 U12 with K = the panel width (<= 64), one 128 x 128
+// output tile per CTA.  FP32 accuracy is kept with the three-term TF32 split:
+// every operand x = x_hi + x_lo with x_hi = x truncated to TF32 and
+// x_lo = x - x_hi (exact), and D = A_hi B_hi + A_hi B_lo + A_lo B_hi is
+// accumulated in FP32 in tensor memory by tcgen05.mma (kind::tf32).  The
+// dropped A_lo B_lo term is below FP32 rounding.
+//
+// Operands are staged by the CTA's threads into shared memory in the
+// canonical K-major layout without swizzle: 8-row x 16-byte core matrices,
+// K-adjacent cores 128 bytes apart (leading byte offset), 8-row groups
+// (K/4) * 128 bytes apart (stride byte offset).  One thread issues the MMAs
+// and commits them to an mbarrier; all four warps then read their 32 lanes of
+// the accumulator with tcgen05.ld and subtract it from C (coalesced: one lane
+// per row).  The mbarrier wait is bounded: on timeout the kernel raises an
+// error flag, releases its tensor memory and returns.
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace h2sp {
+namespace {
+
+constexpr int kTcM = 128, kTcN = 128, kTcK = 64;
+constexpr int kTcThreads = 128;
+constexpr uint32_t kTcCols = 128;                          // TMEM columns of the FP32 accumulator
+constexpr int kTileFloats = kTcM * kTcK;                   // 8192 floats = 32 KB per operand tile
+constexpr uint32_t kLbo = 128;                             // K-adjacent core matrices
+constexpr uint32_t kSbo = (kTcK / 4) * 128;                // 8-row groups (2048 bytes)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// byte offset of element (row, k) of a 128 x 64 tile in the canonical layout
+__device__ __forceinline__ int core_off(int row, int k) {
+  return (row >> 3) * int(kSbo) + (k >> 2) * int(kLbo) + (row & 7) * 16 + (k & 3) * 4;
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr >> 4) & 0x3FFFu);
+  d |= uint64_t((kLbo >> 4) & 0x3FFFu) << 16;
+  d |= uint64_t((kSbo >> 4) & 0x3FFFu) << 32;
+  d |= uint64_t(1) << 46;  // descriptor version; base offset 0, no swizzle
+  return d;
+}
+
+// kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = 128
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(kTcN >> 3) << 17) |
+                            (uint32_t(kTcM >> 4) << 24);
+
+__device__ __forceinline__ void split_tf32(float v, float &hi, float &lo) {
+  hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+  lo = v - hi;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(kIdesc), "r"(accumulate));
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__restrict__ fr, int j0,
+                                                          float *__restrict__ fronts, int *__restrict__ err) {
+  const FrontDev F = fr[blockIdx.z];
+  if (j0 >= F.s) return;
+  const int jb = min(kTcK, F.s - j0);
+  const int t0 = j0 + jb;
+  const int nrest = F.f - t0;
+  const int rb = blockIdx.y * kTcM, cb = blockIdx.x * kTcN;
+  if (rb >= nrest || cb >= nrest) return;
+  float *A = fronts + F.off;
+  const int64_t ld = F.f;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char *sAh = smraw, *sAl = smraw + 4 * kTileFloats, *sBh = smraw + 8 * kTileFloats,
+                *sBl = smraw + 12 * kTileFloats;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // stage the operands, split into TF32 hi / lo parts (zero outside the block)
+  for (int e = tid; e < kTcM * kTcK; e += kTcThreads) {
+    const int m = e % kTcM, k = e / kTcM;  // A: column-major in the front, rows contiguous
+    const int r = rb + m;
+    const float v = (k < jb && r < nrest) ? A[(t0 + r) + int64_t(j0 + k) * ld] : 0.f;
+    float hi, lo;
+    split_tf32(v, hi, lo);
+    const int o = core_off(m, k);
+    *reinterpret_cast<float *>(sAh + o) = hi;
+    *reinterpret_cast<float *>(sAl + o) = lo;
+  }
+  for (int e = tid; e < kTcN * kTcK; e += kTcThreads) {
+    const int k = e % kTcK, n = e / kTcK;  // B: element (n, k) = U12[k, n], K contiguous in the front
+    const int c = cb + n;
+    const float v = (k < jb && c < nrest) ? A[(j0 + k) + int64_t(t0 + c) * ld] : 0.f;
+    float hi, lo;
+    split_tf32(v, hi, lo);
+    const int o = core_off(n, k);
+    *reinterpret_cast<float *>(sBh + o) = hi;
+    *reinterpret_cast<float *>(sBl + o) = lo;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(kTcCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  // generic-proxy writes of the operands become visible to the tensor cores
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+
+  if (tid == 0) {
+    const int ksteps = (jb + 7) / 8;
+    for (int kk = 0; kk < ksteps; ++kk) {
+      const uint32_t koff = uint32_t(kk) * 2 * kLbo;  // 8 TF32 = two K-adjacent cores
+      const uint64_t ah = smem_desc(smem_u32(sAh) + koff), al = smem_desc(smem_u32(sAl) + koff);
+      const uint64_t bh = smem_desc(smem_u32(sBh) + koff), bl = smem_desc(smem_u32(sBl) + koff);
+      mma_tf32(tmem, ah, bh, kk > 0 ? 1u : 0u);
+      mma_tf32(tmem, ah, bl, 1u);
+      mma_tf32(tmem, al, bh, 1u);
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        smem_u32(&mbar)));
+  }
+  // bounded wait for the MMAs (phase 0)
+  bool ok = false;
+  for (uint32_t it = 0; it < (1u << 24); ++it) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n\t.reg .pred P1;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P1;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_u32(&mbar)), "r"(0u));
+    if (done) {
+      ok = true;
+      break;
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (!ok) {
+    if (lane == 0) atomicOr(err, 4);
+  } else {
+    // epilogue: warp w holds accumulator lanes [32w, 32w + 32) = tile rows
+    const int row = rb + warp * 32 + lane;
+    for (int c0 = 0; c0 < kTcN; c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+          "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (row < nrest) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int c = cb + c0 + j;
+          if (c < nrest) A[(t0 + row) + int64_t(t0 + c) * ld] -= __uint_as_float(v[j]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
+}
+
+}  // namespace
+
+size_t gemm_tc_smem() { return size_t(16) * kTileFloats + 1024; }
+
+cudaError_t launch_gemm_tc(const FrontDev *fr, int j0, int nfront, int max_f, float *fronts, int *err,
+                           cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gemm_tc_smem()));
+    attr = true;
+  }
+  const int rest = max_f - j0 - 1;
+  if (rest <= 0) return cudaSuccess;
+  dim3 g((rest + kTcN - 1) / kTcN, (rest + kTcM - 1) / kTcM, nfront);
+  k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err);
+  return cudaGetLastError();
+}
+
+}  // namespace h2sp

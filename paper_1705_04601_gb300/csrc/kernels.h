@@ -72,6 +72,10 @@ cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, 
                                         const T *dinv, const int32_t *idx, T *y, int64_t ldy, int nrhs, T *work,
                                         T *zbuf, const int64_t *work_off, cudaStream_t s, Prof *prof, double bytes);
 
+// FP32 trailing update C -= L21 U12 of one panel step on the tensor cores (gemm_tc.cu).
+cudaError_t launch_gemm_tc(const FrontDev *fr, int j0, int nfront, int max_f, float *fronts, int *err,
+                           cudaStream_t s);
+
 // ---- applies, H^2 product, vector kernels (apply.cu) ----
 struct ApItem {
   int64_t q;      // Q offset (m x m)

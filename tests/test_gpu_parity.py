@@ -272,3 +272,21 @@ def test_batched_forest_matches_individual_systems(prec):
             assert r.max() <= 2e-10
         o += s.n
     hd.close()
+
+
+@pytest.mark.parametrize("name", ["log4k", "ragged"])
+def test_fp32_factor_direct_accuracy(name):
+    """One FP32-factor direct solve is accurate to FP32 level (the trailing
+    updates keep FP32 accuracy whichever GEMM path runs)."""
+    import os
+    h, b, sp, hd = sparsified(name)
+    H.h2sp_factor(hd, H.H2SP_FP32)
+    bt = dev(b)
+    xt = torch.empty_like(bt)
+    H.h2sp_solve(hd, bt, xt, mode=H.H2SP_DIRECT)
+    torch.cuda.synchronize()
+    xo = ofa.solve(h, sp, ofa.factor(h, sp), b)
+    err = np.linalg.norm(host(xt) - xo) / np.linalg.norm(xo)
+    print("fp32 direct rel err (%s, GEMM=%s): %.3e" % (name, os.environ.get("H2SP_GEMM", "tc"), err))
+    assert err <= 1e-4
+    hd.close()
