@@ -833,13 +833,13 @@ cudaError_t launch_assemble(const AItem *items, int64_t n, const double *S, T *f
   return cudaGetLastError();
 }
 
-// The FP32 trailing update runs on the tensor cores (three-term TF32 split);
-// H2SP_GEMM=simt in the environment selects the FP32 SIMT kernel instead.
+// H2SP_GEMM=tc in the environment runs the FP32 trailing update on the tensor
+// cores (three-term TF32 split); the default is the FP32 SIMT kernel.
 inline bool use_tensor_core_gemm() {
   static int v = -1;
   if (v < 0) {
     const char *e = std::getenv("H2SP_GEMM");
-    v = (e && std::strcmp(e, "simt") == 0) ? 0 : 1;
+    v = (e && std::strcmp(e, "tc") == 0) ? 1 : 0;
   }
   return v == 1;
 }

@@ -11,10 +11,12 @@
 // canonical K-major layout without swizzle: 8-row x 16-byte core matrices,
 // K-adjacent cores 128 bytes apart (leading byte offset), 8-row groups
 // (K/4) * 128 bytes apart (stride byte offset).  One thread issues the MMAs
-// and commits them to an mbarrier; all four warps then read their 32 lanes of
-// the accumulator with tcgen05.ld and subtract it from C (coalesced: one lane
-// per row).  The mbarrier wait is bounded: on timeout the kernel raises an
-// error flag, releases its tensor memory and returns.
+// and commits them to an mbarrier; the eight warps then read the accumulator
+// with tcgen05.ld (warp w: lanes of quadrant w % 4, columns of half w / 4)
+// and subtract it from C (coalesced: one lane per row).  mbarrier waits are
+// bounded: on timeout the kernel raises an error flag, releases its tensor
+// memory and returns.
+#include <algorithm>
 #include <cstdint>
 
 #include "kernels.h"
@@ -23,11 +25,12 @@ namespace h2sp {
 namespace {
 
 constexpr int kTcM = 128, kTcN = 128, kTcK = 64;
-constexpr int kTcThreads = 128;
-constexpr uint32_t kTcCols = 128;                          // TMEM columns of the FP32 accumulator
+constexpr int kTcThreads = 256;
+constexpr uint32_t kTcCols = 256;                          // two 128-column FP32 accumulators
 constexpr int kTileFloats = kTcM * kTcK;                   // 8192 floats = 32 KB per operand tile
 constexpr uint32_t kLbo = 128;                             // K-adjacent core matrices
 constexpr uint32_t kSbo = (kTcK / 4) * 128;                // 8-row groups (2048 bytes)
+constexpr uint32_t kWaitCap = 1u << 24;                    // bounded mbarrier waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -64,27 +67,58 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t 
       "l"(da), "l"(db), "r"(kIdesc), "r"(accumulate));
 }
 
+__device__ __forceinline__ bool wait_phase(uint32_t mbar_addr, uint32_t parity) {
+  for (uint32_t it = 0; it < kWaitCap; ++it) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n\t.reg .pred P1;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P1;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar_addr), "r"(parity));
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void sync_for_tensor_cores() {
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+}
+
+// One CTA: a 128-row tile of the trailing block against a range of 128-column
+// tiles.  The A tile (hi / lo) stays in shared memory; B tiles and the two
+// TMEM accumulators alternate, so staging tile i + 1 and the epilogue of tile
+// i overlap the asynchronous MMAs.
 __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__restrict__ fr, int j0,
-                                                          float *__restrict__ fronts, int *__restrict__ err) {
+                                                          float *__restrict__ fronts, int *__restrict__ err,
+                                                          int splits) {
   const FrontDev F = fr[blockIdx.z];
   if (j0 >= F.s) return;
   const int jb = min(kTcK, F.s - j0);
   const int t0 = j0 + jb;
   const int nrest = F.f - t0;
-  const int rb = blockIdx.y * kTcM, cb = blockIdx.x * kTcN;
-  if (rb >= nrest || cb >= nrest) return;
+  const int rb = blockIdx.y * kTcM;
+  if (rb >= nrest) return;
+  const int ntiles = (nrest + kTcN - 1) / kTcN;
+  const int per = (ntiles + splits - 1) / splits;
+  const int c_lo = blockIdx.x * per, c_hi = min(ntiles, c_lo + per);
+  if (c_lo >= c_hi) return;
   float *A = fronts + F.off;
   const int64_t ld = F.f;
   extern __shared__ __align__(1024) unsigned char smraw[];
-  unsigned char *sAh = smraw, *sAl = smraw + 4 * kTileFloats, *sBh = smraw + 8 * kTileFloats,
-                *sBl = smraw + 12 * kTileFloats;
-  __shared__ __align__(8) uint64_t mbar;
+  unsigned char *sAh = smraw, *sAl = smraw + 4 * kTileFloats;
+  unsigned char *sBh[2] = {smraw + 8 * kTileFloats, smraw + 16 * kTileFloats};
+  unsigned char *sBl[2] = {smraw + 12 * kTileFloats, smraw + 20 * kTileFloats};
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ksteps = (jb + 7) / 8;
 
-  // stage the operands, split into TF32 hi / lo parts (zero outside the block)
   for (int e = tid; e < kTcM * kTcK; e += kTcThreads) {
-    const int m = e % kTcM, k = e / kTcM;  // A: column-major in the front, rows contiguous
+    const int m = e % kTcM, k = e / kTcM;  // rows contiguous in the front
     const int r = rb + m;
     const float v = (k < jb && r < nrest) ? A[(t0 + r) + int64_t(j0 + k) * ld] : 0.f;
     float hi, lo;
@@ -93,69 +127,73 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__res
     *reinterpret_cast<float *>(sAh + o) = hi;
     *reinterpret_cast<float *>(sAl + o) = lo;
   }
-  for (int e = tid; e < kTcN * kTcK; e += kTcThreads) {
-    const int k = e % kTcK, n = e / kTcK;  // B: element (n, k) = U12[k, n], K contiguous in the front
-    const int c = cb + n;
-    const float v = (k < jb && c < nrest) ? A[(j0 + k) + int64_t(t0 + c) * ld] : 0.f;
-    float hi, lo;
-    split_tf32(v, hi, lo);
-    const int o = core_off(n, k);
-    *reinterpret_cast<float *>(sBh + o) = hi;
-    *reinterpret_cast<float *>(sBl + o) = lo;
-  }
+  auto stage_b = [&](int ct, int buf) {
+    const int cb = ct * kTcN;
+    for (int e = tid; e < kTcN * kTcK; e += kTcThreads) {
+      const int k = e % kTcK, n = e / kTcK;  // K contiguous in the front
+      const int c = cb + n;
+      const float v = (k < jb && c < nrest) ? A[(j0 + k) + int64_t(t0 + c) * ld] : 0.f;
+      float hi, lo;
+      split_tf32(v, hi, lo);
+      const int o = core_off(n, k);
+      *reinterpret_cast<float *>(sBh[buf] + o) = hi;
+      *reinterpret_cast<float *>(sBl[buf] + o) = lo;
+    }
+  };
+  auto issue = [&](uint32_t tmem, int buf) {
+    const uint32_t ah0 = smem_u32(sAh), al0 = smem_u32(sAl), bh0 = smem_u32(sBh[buf]), bl0 = smem_u32(sBl[buf]);
+    const uint32_t acc = tmem + uint32_t(buf) * kTcN;
+    for (int kk = 0; kk < ksteps; ++kk) {
+      const uint32_t koff = uint32_t(kk) * 2 * kLbo;  // 8 TF32 = two K-adjacent cores
+      const uint64_t ah = smem_desc(ah0 + koff), al = smem_desc(al0 + koff);
+      const uint64_t bh = smem_desc(bh0 + koff), bl = smem_desc(bl0 + koff);
+      mma_tf32(acc, ah, bh, kk > 0 ? 1u : 0u);
+      mma_tf32(acc, ah, bl, 1u);
+      mma_tf32(acc, al, bh, 1u);
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        smem_u32(&mbar[buf])));
+  };
+
+  stage_b(c_lo, 0);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                  "r"(kTcCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  // generic-proxy writes of the operands become visible to the tensor cores
-  asm volatile("fence.proxy.async.shared::cta;");
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
+  sync_for_tensor_cores();
   const uint32_t tmem = tmem_base;
-
-  if (tid == 0) {
-    const int ksteps = (jb + 7) / 8;
-    for (int kk = 0; kk < ksteps; ++kk) {
-      const uint32_t koff = uint32_t(kk) * 2 * kLbo;  // 8 TF32 = two K-adjacent cores
-      const uint64_t ah = smem_desc(smem_u32(sAh) + koff), al = smem_desc(smem_u32(sAl) + koff);
-      const uint64_t bh = smem_desc(smem_u32(sBh) + koff), bl = smem_desc(smem_u32(sBl) + koff);
-      mma_tf32(tmem, ah, bh, kk > 0 ? 1u : 0u);
-      mma_tf32(tmem, ah, bl, 1u);
-      mma_tf32(tmem, al, bh, 1u);
+  if (tid == 0) issue(tmem, 0);
+  uint32_t parity[2] = {0u, 0u};
+  bool ok = true;
+  int pending = -1;  // buffer of a group issued but not yet waited for
+  const int q = warp & 3, half = warp >> 2;  // TMEM lane quadrant, column half of the epilogue
+  for (int it = 0; c_lo + it < c_hi; ++it) {
+    const int cur = it & 1, nxt = cur ^ 1;
+    const int ct = c_lo + it;
+    pending = -1;
+    if (ct + 1 < c_hi) {
+      stage_b(ct + 1, nxt);  // the buffer's previous MMA finished before the last epilogue
+      sync_for_tensor_cores();
+      if (tid == 0) issue(tmem, nxt);
+      pending = nxt;
     }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-        smem_u32(&mbar)));
-  }
-  // bounded wait for the MMAs (phase 0)
-  bool ok = false;
-  for (uint32_t it = 0; it < (1u << 24); ++it) {
-    uint32_t done = 0;
-    asm volatile(
-        "{\n\t.reg .pred P1;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, P1;\n\t}\n"
-        : "=r"(done)
-        : "r"(smem_u32(&mbar)), "r"(0u));
-    if (done) {
-      ok = true;
-      break;
-    }
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (!ok) {
-    if (lane == 0) atomicOr(err, 4);
-  } else {
-    // epilogue: warp w holds accumulator lanes [32w, 32w + 32) = tile rows
-    const int row = rb + warp * 32 + lane;
-    for (int c0 = 0; c0 < kTcN; c0 += 32) {
+    const bool w = wait_phase(smem_u32(&mbar[cur]), parity[cur]);
+    parity[cur] ^= 1u;
+    ok = __syncthreads_and(w ? 1 : 0) != 0;  // one decision for the whole CTA
+    if (!ok) break;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int row = rb + q * 32 + lane;
+    const int cb = ct * kTcN + half * 64;
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 32) {
       uint32_t v[32];
-      const uint32_t taddr = tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0);
+      const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(cur * kTcN + half * 64 + c0);
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
           "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -166,13 +204,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__res
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       if (row < nrest) {
+        float *Crow = A + (t0 + row) + int64_t(t0 + cb + c0) * ld;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int c = cb + c0 + j;
-          if (c < nrest) A[(t0 + row) + int64_t(t0 + c) * ld] -= __uint_as_float(v[j]);
-        }
+        for (int j = 0; j < 32; ++j)
+          if (cb + c0 + j < nrest) Crow[int64_t(j) * ld] -= __uint_as_float(v[j]);
       }
     }
+    // accumulator `cur` and B buffer `cur` are free for tile it + 2
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(err, 4);
+    // give the group still in flight a bounded chance to finish before TMEM is released
+    if (pending >= 0) wait_phase(smem_u32(&mbar[pending]), parity[pending]);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -181,7 +227,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__res
 
 }  // namespace
 
-size_t gemm_tc_smem() { return size_t(16) * kTileFloats + 1024; }
+size_t gemm_tc_smem() { return size_t(24) * kTileFloats + 1024; }
 
 cudaError_t launch_gemm_tc(const FrontDev *fr, int j0, int nfront, int max_f, float *fronts, int *err,
                            cudaStream_t s) {
@@ -192,8 +238,12 @@ cudaError_t launch_gemm_tc(const FrontDev *fr, int j0, int nfront, int max_f, fl
   }
   const int rest = max_f - j0 - 1;
   if (rest <= 0) return cudaSuccess;
-  dim3 g((rest + kTcN - 1) / kTcN, (rest + kTcM - 1) / kTcM, nfront);
-  k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err);
+  const int rt = (rest + kTcM - 1) / kTcM, ct = (rest + kTcN - 1) / kTcN;
+  // enough CTAs for two per SM of the 152, each walking a contiguous range of column tiles
+  int splits = (2 * 152 + rt * nfront - 1) / (rt * nfront);
+  splits = std::max(1, std::min(splits, ct));
+  dim3 g(splits, rt, nfront);
+  k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits);
   return cudaGetLastError();
 }
 
