@@ -423,15 +423,39 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
       acc[i][j] = (c < nrest && r < nrest) ? A[(t0 + r) + int64_t(t0 + c) * ld] : T(0);
     }
   }
-  for (int e = tid; e < jb * BM; e += 256) {
-    const int i = e % BM, k = e / BM;  // tile row i = (i % RT) + RT * (i / RT)
-    const int r = rb + i;
-    sA[k * PA + (i % RT) * TM + i / RT] = (r < nrest) ? A[(t0 + r) + int64_t(j0 + k) * ld] : T(0);
+  // operand tiles: all loads of a pass are issued before any store (fixed trip counts)
+  constexpr int kIA = NB * BM / 256, kIB = NB * BN / 256;
+  {
+    T v[kIA];
+#pragma unroll
+    for (int it = 0; it < kIA; ++it) {
+      const int e = tid + it * 256;
+      const int i = e % BM, k = e / BM;  // tile row i = (i % RT) + RT * (i / RT)
+      const int r = rb + i;
+      v[it] = (k < jb && r < nrest) ? A[(t0 + r) + int64_t(j0 + k) * ld] : T(0);
+    }
+#pragma unroll
+    for (int it = 0; it < kIA; ++it) {
+      const int e = tid + it * 256;
+      const int i = e % BM, k = e / BM;
+      sA[k * PA + (i % RT) * TM + i / RT] = v[it];
+    }
   }
-  for (int e = tid; e < jb * BN; e += 256) {
-    const int k = e % jb, j = e / jb;
-    const int c = cb + j;
-    sB[k * PB + (j % CT) * TN + j / CT] = (c < nrest) ? A[(j0 + k) + int64_t(t0 + c) * ld] : T(0);
+  {
+    T v[kIB];
+#pragma unroll
+    for (int it = 0; it < kIB; ++it) {
+      const int e = tid + it * 256;
+      const int k = e % NB, j = e / NB;
+      const int c = cb + j;
+      v[it] = (k < jb && c < nrest) ? A[(j0 + k) + int64_t(t0 + c) * ld] : T(0);
+    }
+#pragma unroll
+    for (int it = 0; it < kIB; ++it) {
+      const int e = tid + it * 256;
+      const int k = e % NB, j = e / NB;
+      sB[k * PB + (j % CT) * TN + j / CT] = v[it];
+    }
   }
   __syncthreads();
   for (int k = 0; k < jb; ++k) {

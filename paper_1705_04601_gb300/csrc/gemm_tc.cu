@@ -36,11 +36,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// byte offset of element (row, k) of a 128 x 64 tile in the canonical layout
-__device__ __forceinline__ int core_off(int row, int k) {
-  return (row >> 3) * int(kSbo) + (k >> 2) * int(kLbo) + (row & 7) * 16 + (k & 3) * 4;
-}
-
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= uint64_t((saddr >> 4) & 0x3FFFu);
@@ -117,27 +112,46 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__res
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ksteps = (jb + 7) / 8;
 
-  for (int e = tid; e < kTcM * kTcK; e += kTcThreads) {
-    const int m = e % kTcM, k = e / kTcM;  // rows contiguous in the front
-    const int r = rb + m;
-    const float v = (k < jb && r < nrest) ? A[(t0 + r) + int64_t(j0 + k) * ld] : 0.f;
-    float hi, lo;
-    split_tf32(v, hi, lo);
-    const int o = core_off(m, k);
-    *reinterpret_cast<float *>(sAh + o) = hi;
-    *reinterpret_cast<float *>(sAl + o) = lo;
+  // Element e of a tile in the canonical layout sits at word e when
+  // row = (e >> 9) * 8 + ((e & 31) >> 2) and k = ((e >> 5) & 15) * 4 + (e & 3):
+  // stores are linear (conflict-free), a warp loads 4 K-steps x 8 rows.
+  constexpr int kIters = kTcM * kTcK / kTcThreads;
+  {
+    float v[kIters];
+#pragma unroll
+    for (int it = 0; it < kIters; ++it) {
+      const int e = tid + it * kTcThreads;
+      const int m = (e >> 9) * 8 + ((e & 31) >> 2), k = ((e >> 5) & 15) * 4 + (e & 3);
+      const int r = rb + m;
+      v[it] = (k < jb && r < nrest) ? A[(t0 + r) + int64_t(j0 + k) * ld] : 0.f;
+    }
+#pragma unroll
+    for (int it = 0; it < kIters; ++it) {
+      const int e = tid + it * kTcThreads;
+      float hi, lo;
+      split_tf32(v[it], hi, lo);
+      reinterpret_cast<float *>(sAh)[e] = hi;
+      reinterpret_cast<float *>(sAl)[e] = lo;
+    }
   }
   auto stage_b = [&](int ct, int buf) {
     const int cb = ct * kTcN;
-    for (int e = tid; e < kTcN * kTcK; e += kTcThreads) {
-      const int k = e % kTcK, n = e / kTcK;  // K contiguous in the front
+    float v[kIters];
+#pragma unroll
+    for (int it = 0; it < kIters; ++it) {
+      const int e = tid + it * kTcThreads;
+      const int n = (e >> 9) * 8 + ((e & 31) >> 2), k = ((e >> 5) & 15) * 4 + (e & 3);
       const int c = cb + n;
-      const float v = (k < jb && c < nrest) ? A[(j0 + k) + int64_t(t0 + c) * ld] : 0.f;
+      v[it] = (k < jb && c < nrest) ? A[(j0 + k) + int64_t(t0 + c) * ld] : 0.f;
+    }
+    float *bh = reinterpret_cast<float *>(sBh[buf]), *bl = reinterpret_cast<float *>(sBl[buf]);
+#pragma unroll
+    for (int it = 0; it < kIters; ++it) {
+      const int e = tid + it * kTcThreads;
       float hi, lo;
-      split_tf32(v, hi, lo);
-      const int o = core_off(n, k);
-      *reinterpret_cast<float *>(sBh[buf] + o) = hi;
-      *reinterpret_cast<float *>(sBl[buf] + o) = lo;
+      split_tf32(v[it], hi, lo);
+      bh[e] = hi;
+      bl[e] = lo;
     }
   };
   auto issue = [&](uint32_t tmem, int buf) {
