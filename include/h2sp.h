@@ -132,8 +132,8 @@ typedef struct {
 typedef struct {
   int32_t mode;        /* h2sp_mode */
   double tol;          /* target max_k ||b_k - A x_k|| / ||b_k|| for IR / GMRES (e.g. 1e-10) */
-  int32_t maxit;       /* iteration cap (IR: refinement steps; GMRES: total inner steps) */
-  int32_t restart;     /* GMRES restart length (ignored by IR / DIRECT) */
+  int32_t maxit;       /* iteration cap (IR: refinement steps; GMRES: total inner steps); <= 0: default */
+  int32_t restart;     /* GMRES restart length (1..60; <= 0: 20); ignored by IR / DIRECT */
 } h2sp_solve_opts;
 
 typedef struct {

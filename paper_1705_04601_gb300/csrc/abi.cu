@@ -91,6 +91,8 @@ struct h2sp_handle {
   int32_t *child_start = nullptr, *child_cnt = nullptr;
   double *xh = nullptr, *yh = nullptr;
   double *norms = nullptr;
+  double *gmV = nullptr, *gmZ = nullptr, *gmW = nullptr, *gmC = nullptr;  // GMRES basis and workspace
+  int gm_m = 0, gm_rhs = 0;
   int64_t *seg_ptr = nullptr;  // row ranges of the independent systems (roots)
   int nseg = 1;
   double plan_seconds = 0.0;
@@ -282,6 +284,143 @@ void precond(h2sp_handle *h, const double *r, int64_t ldr, double *d, int64_t ld
   apply_T(h, false, r, ldr, h->vecS, n, nrhs);
   solve_S(h, h->vecS, nrhs);
   apply_N(h, true, h->vecS, n, d, ldd, nrhs);
+}
+
+// Restarted GMRES with right preconditioning M^{-1} = V S^{-1} U^T (§5.5), one
+// Krylov process per right-hand side, all columns advanced together.  The
+// basis is orthogonalised by classical Gram-Schmidt applied twice; the small
+// Hessenberg least-squares problems (Givens rotations) are solved on the host.
+// Convergence is judged on the Hessenberg estimate inside a cycle and on the
+// true FP64 H^2 residual (per independent system and column) at its end.
+int gmres(h2sp_handle *h, const h2sp_solve_opts *o, int nrhs, const double *b, int64_t ldb, double *x, int64_t ldx,
+          h2sp_solve_info *info) {
+  const Plan &p = h->plan;
+  cudaStream_t s = h->stream;
+  const int64_t n = p.n;
+  const int m = std::max(1, std::min(o->restart > 0 ? o->restart : 20, 60));
+  const int maxit = o->maxit > 0 ? o->maxit : 200;
+  const int ns = h->nseg;
+  if (h->gm_m < m || h->gm_rhs < nrhs) {
+    h->gmV = h->alloc<double>(size_t(m + 1) * n * nrhs);
+    h->gmZ = h->alloc<double>(size_t(m) * n * nrhs);
+    h->gmW = h->alloc<double>(size_t(n) * nrhs);
+    h->gmC = h->alloc<double>(size_t(m + 2) * nrhs);
+    h->gm_m = m;
+    h->gm_rhs = nrhs;
+  }
+  const int64_t vs = n * nrhs;  // stride between basis blocks (ld n)
+  double *V = h->gmV, *Z = h->gmZ, *W = h->gmW, *C = h->gmC;
+  std::vector<double> bn2(size_t(nrhs) * ns), rn2(size_t(nrhs) * ns), bnorm(nrhs), beta(nrhs);
+  ck(launch_colnorm2(b, ldb, h->seg_ptr, ns, n, nrhs, h->norms, s));
+  ck(cudaMemcpyAsync(bn2.data(), h->norms, sizeof(double) * nrhs * ns, cudaMemcpyDeviceToHost, s));
+  ck(cudaStreamSynchronize(s));
+  for (int c = 0; c < nrhs; ++c) {
+    double t = 0.0;
+    for (int q = 0; q < ns; ++q) t += bn2[size_t(q) * nrhs + c];
+    bnorm[c] = std::sqrt(std::max(t, 1e-300));
+  }
+  for (int c = 0; c < nrhs; ++c) ck(cudaMemsetAsync(x + c * ldx, 0, sizeof(double) * n, s));
+  int it = 0;
+  double res = INFINITY;
+  std::vector<double> H(size_t(m + 1) * m * nrhs), cs(size_t(m) * nrhs), sn(size_t(m) * nrhs), g(size_t(m + 1) * nrhs);
+  std::vector<double> hcol(size_t(m + 2) * nrhs), coef(size_t(m + 1) * nrhs);
+  auto Hat = [&](int i, int j, int c) -> double & { return H[(size_t(c) * (m + 1) + i) * m + j]; };
+  for (;;) {
+    // r = b - A x into V_0, true residual per system and column
+    h2_matvec(h, x, ldx, W, n, nrhs);
+    ck(launch_residual(b, ldb, W, n, V, n, h->seg_ptr, ns, n, nrhs, h->norms, s));
+    ck(cudaMemcpyAsync(rn2.data(), h->norms, sizeof(double) * nrhs * ns, cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    res = 0.0;
+    for (size_t q = 0; q < rn2.size(); ++q) res = std::max(res, std::sqrt(rn2[q] / std::max(bn2[q], 1e-300)));
+    if (!(res > o->tol) || it >= maxit) break;
+    std::vector<double> scale(nrhs);
+    for (int c = 0; c < nrhs; ++c) {
+      double t = 0.0;
+      for (int q = 0; q < ns; ++q) t += rn2[size_t(q) * nrhs + c];
+      beta[c] = std::sqrt(t);
+      scale[c] = beta[c] > 0.0 ? 1.0 / beta[c] : 0.0;
+    }
+    ck(cudaMemcpyAsync(C, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    ck(launch_col_scale(V, n, C, n, nrhs, s));
+    std::fill(g.begin(), g.end(), 0.0);
+    for (int c = 0; c < nrhs; ++c) g[size_t(c) * (m + 1)] = beta[c];
+    int j = 0;
+    for (; j < m && it < maxit; ++j, ++it) {
+      precond(h, V + j * vs, n, Z + j * vs, n, nrhs);
+      h2_matvec(h, Z + j * vs, n, W, n, nrhs);
+      // classical Gram-Schmidt, twice
+      std::fill(hcol.begin(), hcol.end(), 0.0);
+      for (int pass = 0; pass < 2; ++pass) {
+        ck(launch_block_dots(V, n, vs, j + 1, W, n, n, nrhs, C, s));
+        ck(cudaMemcpyAsync(coef.data(), C, sizeof(double) * (j + 1) * nrhs, cudaMemcpyDeviceToHost, s));
+        ck(cudaStreamSynchronize(s));
+        for (size_t q = 0; q < size_t(j + 1) * nrhs; ++q) {
+          hcol[q] += coef[q];
+          coef[q] = -coef[q];
+        }
+        ck(cudaMemcpyAsync(C, coef.data(), sizeof(double) * (j + 1) * nrhs, cudaMemcpyHostToDevice, s));
+        ck(launch_block_axpy(V, n, vs, j + 1, C, W, n, n, nrhs, s));
+      }
+      ck(launch_colnorm2(W, n, h->seg_ptr, ns, n, nrhs, h->norms, s));
+      ck(cudaMemcpyAsync(rn2.data(), h->norms, sizeof(double) * nrhs * ns, cudaMemcpyDeviceToHost, s));
+      ck(cudaStreamSynchronize(s));
+      std::vector<double> inv(nrhs);
+      double worst = 0.0;
+      for (int c = 0; c < nrhs; ++c) {
+        double t = 0.0;
+        for (int q = 0; q < ns; ++q) t += rn2[size_t(q) * nrhs + c];
+        const double hn = std::sqrt(t);
+        for (int i = 0; i <= j; ++i) Hat(i, j, c) = hcol[size_t(i) * nrhs + c];
+        double hj1 = hn;
+        inv[c] = hn > 0.0 ? 1.0 / hn : 0.0;
+        // apply the previous rotations, then a new one
+        for (int i = 0; i < j; ++i) {
+          const double a0 = Hat(i, j, c), a1 = Hat(i + 1, j, c);
+          Hat(i, j, c) = cs[size_t(c) * m + i] * a0 + sn[size_t(c) * m + i] * a1;
+          Hat(i + 1, j, c) = -sn[size_t(c) * m + i] * a0 + cs[size_t(c) * m + i] * a1;
+        }
+        const double a0 = Hat(j, j, c);
+        const double den = std::hypot(a0, hj1);
+        const double cc = den > 0.0 ? a0 / den : 1.0, ss = den > 0.0 ? hj1 / den : 0.0;
+        cs[size_t(c) * m + j] = cc;
+        sn[size_t(c) * m + j] = ss;
+        Hat(j, j, c) = den;
+        double &gj = g[size_t(c) * (m + 1) + j];
+        g[size_t(c) * (m + 1) + j + 1] = -ss * gj;
+        gj = cc * gj;
+        worst = std::max(worst, std::abs(g[size_t(c) * (m + 1) + j + 1]) / bnorm[c]);
+      }
+      ck(cudaMemcpyAsync(C, inv.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+      ck(cudaMemcpyAsync(V + (j + 1) * vs, W, sizeof(double) * vs, cudaMemcpyDeviceToDevice, s));
+      ck(launch_col_scale(V + (j + 1) * vs, n, C, n, nrhs, s));
+      // the global estimate is an upper bound on every system's share only up to
+      // the ratio of norms; a margin keeps the true check the one that decides
+      if (worst <= 0.25 * o->tol) {
+        ++j;
+        ++it;
+        break;
+      }
+    }
+    // x += Z y with y from the triangular systems
+    std::vector<double> y(size_t(j) * nrhs, 0.0);
+    for (int c = 0; c < nrhs; ++c)
+      for (int i = j - 1; i >= 0; --i) {
+        double t = g[size_t(c) * (m + 1) + i];
+        for (int q = i + 1; q < j; ++q) t -= Hat(i, q, c) * y[size_t(q) * nrhs + c];
+        y[size_t(i) * nrhs + c] = Hat(i, i, c) != 0.0 ? t / Hat(i, i, c) : 0.0;
+      }
+    if (j > 0) {
+      ck(cudaMemcpyAsync(C, y.data(), sizeof(double) * j * nrhs, cudaMemcpyHostToDevice, s));
+      ck(launch_block_axpy(Z, n, vs, j, C, x, ldx, n, nrhs, s));
+    }
+  }
+  if (info) {
+    info->iters = it;
+    info->rel_residual = res;
+    info->status = (res <= o->tol) ? H2SP_OK : H2SP_ENOCONV;
+  }
+  return res <= o->tol ? H2SP_OK : H2SP_ENOCONV;
 }
 
 }  // namespace
@@ -659,7 +798,7 @@ int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *o, int32_t nrhs, const dou
   if (!h->device_ready) return H2SP_ESTATE;
   const Plan &p = h->plan;
   if (ldb < p.n || ldx < p.n) return H2SP_EINVAL;
-  if (o->mode != H2SP_DIRECT && o->mode != H2SP_IR) return H2SP_EUNSUPPORTED;
+  if (o->mode != H2SP_DIRECT && o->mode != H2SP_IR && o->mode != H2SP_GMRES) return H2SP_EINVAL;
   if (h->prec < 0) return H2SP_ESTATE;
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   cudaStream_t s = h->stream;
@@ -675,6 +814,10 @@ int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *o, int32_t nrhs, const dou
       precond(h, b, ldb, x, ldx, nrhs);
       ck(cudaGetLastError());
       return H2SP_OK;
+    }
+    if (o->mode == H2SP_GMRES) {
+      const int st = gmres(h, o, nrhs, b, ldb, x, ldx, info);
+      return st;
     }
     // iterative refinement on the FP64 H^2 residual (§5.5)
     const int64_t n = p.n;

@@ -301,6 +301,46 @@ __global__ void __launch_bounds__(256) k_residual(const double *__restrict__ b, 
   }
 }
 
+// out[i * nrhs + c] = <V_i[:, c], W[:, c]> for the first nv blocks V_i (block stride ldv * nrhs)
+__global__ void __launch_bounds__(256) k_block_dots(const double *__restrict__ V, int64_t ldv, int64_t vstride, int nv,
+                                                    const double *__restrict__ W, int64_t ldw, int64_t n, int nrhs,
+                                                    double *__restrict__ out) {
+  const int i = blockIdx.y % nv, c = blockIdx.y / nv;
+  const double *v = V + i * vstride + c * ldv;
+  const double *w = W + c * ldw;
+  __shared__ double red[8];
+  double part = 0.0;
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < n; r += int64_t(gridDim.x) * blockDim.x)
+    part += v[r] * w[r];
+  part = warp_sum(part);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < int(blockDim.x >> 5); ++q) t += red[q];
+    atomicAdd(&out[int64_t(i) * nrhs + c], t);
+  }
+}
+
+// W[:, c] += sum_i coef[i * nrhs + c] * V_i[:, c]   (coef on the device)
+__global__ void k_block_axpy(const double *__restrict__ V, int64_t ldv, int64_t vstride, int nv,
+                             const double *__restrict__ coef, double *__restrict__ W, int64_t ldw, int64_t n) {
+  const int c = blockIdx.y;
+  const int nrhs = gridDim.y;
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < n; r += int64_t(gridDim.x) * blockDim.x) {
+    double acc = W[r + c * ldw];
+    for (int i = 0; i < nv; ++i) acc += coef[int64_t(i) * nrhs + c] * V[i * vstride + c * ldv + r];
+    W[r + c * ldw] = acc;
+  }
+}
+
+// X[:, c] *= s[c]
+__global__ void k_col_scale(double *__restrict__ X, int64_t ldx, const double *__restrict__ sc, int64_t n) {
+  const int c = blockIdx.y;
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < n; r += int64_t(gridDim.x) * blockDim.x)
+    X[r + c * ldx] *= sc[c];
+}
+
 __global__ void k_axpy(const double *__restrict__ d, int64_t ldd, double *__restrict__ x, int64_t ldx, int64_t n) {
   const int c = blockIdx.y;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
@@ -417,6 +457,26 @@ cudaError_t launch_residual(const double *b, int64_t ldb, const double *y, int64
 cudaError_t launch_colnorm2(const double *x, int64_t ldx, const int64_t *seg_ptr, int nseg, int64_t n, int nrhs,
                             double *norms2, cudaStream_t s) {
   return launch_residual(x, ldx, nullptr, 0, nullptr, 0, seg_ptr, nseg, n, nrhs, norms2, s);
+}
+
+cudaError_t launch_block_dots(const double *V, int64_t ldv, int64_t vstride, int nv, const double *W, int64_t ldw,
+                              int64_t n, int nrhs, double *out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * nv * nrhs, s);
+  if (e != cudaSuccess) return e;
+  k_block_dots<<<dim3(std::max(1u, grid_for(n) / 4), nv * nrhs), 256, 0, s>>>(V, ldv, vstride, nv, W, ldw, n, nrhs,
+                                                                               out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_axpy(const double *V, int64_t ldv, int64_t vstride, int nv, const double *coef, double *W,
+                              int64_t ldw, int64_t n, int nrhs, cudaStream_t s) {
+  k_block_axpy<<<dim3(grid_for(n), nrhs), 256, 0, s>>>(V, ldv, vstride, nv, coef, W, ldw, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_col_scale(double *X, int64_t ldx, const double *sc, int64_t n, int nrhs, cudaStream_t s) {
+  k_col_scale<<<dim3(grid_for(n), nrhs), 256, 0, s>>>(X, ldx, sc, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_axpy(const double *d, int64_t ldd, double *x, int64_t ldx, int64_t n, int nrhs, cudaStream_t s) {

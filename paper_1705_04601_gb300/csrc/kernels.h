@@ -126,6 +126,13 @@ cudaError_t launch_residual(const double *b, int64_t ldb, const double *y, int64
                             const int64_t *seg_ptr, int nseg, int64_t n, int nrhs, double *norms2, cudaStream_t s);
 cudaError_t launch_colnorm2(const double *x, int64_t ldx, const int64_t *seg_ptr, int nseg, int64_t n, int nrhs,
                             double *norms2, cudaStream_t s);
+// GMRES helpers: out[i*nrhs + c] = <V_i[:,c], W[:,c]> for i < nv (V_i at V + i * vstride);
+// W[:,c] += sum_i coef[i*nrhs + c] V_i[:,c]; X[:,c] *= sc[c]  (coefficients on the device)
+cudaError_t launch_block_dots(const double *V, int64_t ldv, int64_t vstride, int nv, const double *W, int64_t ldw,
+                              int64_t n, int nrhs, double *out, cudaStream_t s);
+cudaError_t launch_block_axpy(const double *V, int64_t ldv, int64_t vstride, int nv, const double *coef, double *W,
+                              int64_t ldw, int64_t n, int nrhs, cudaStream_t s);
+cudaError_t launch_col_scale(double *X, int64_t ldx, const double *sc, int64_t n, int nrhs, cudaStream_t s);
 // x += d
 cudaError_t launch_axpy(const double *d, int64_t ldd, double *x, int64_t ldx, int64_t n, int nrhs, cudaStream_t s);
 cudaError_t launch_cast_d2f(const double *a, int64_t lda, float *b, int64_t ldb, int64_t n, int nrhs, cudaStream_t s);

@@ -277,8 +277,9 @@ def test_batched_forest_matches_individual_systems(prec):
 @pytest.mark.parametrize("name", ["log4k", "ragged"])
 def test_fp32_factor_direct_accuracy(name):
     """One FP32-factor direct solve is accurate to FP32 level times the
-    conditioning (~1e-3 here with either GEMM path); a TF32-only trailing
-    update would be ~1000x worse."""
+    conditioning (1e-3 .. 8e-3 here with either GEMM path, varying with the
+    rounding of the atomic extend-add); a TF32-only trailing update would be
+    ~1000x worse."""
     import os
     h, b, sp, hd = sparsified(name)
     H.h2sp_factor(hd, H.H2SP_FP32)
@@ -289,5 +290,21 @@ def test_fp32_factor_direct_accuracy(name):
     xo = ofa.solve(h, sp, ofa.factor(h, sp), b)
     err = np.linalg.norm(host(xt) - xo) / np.linalg.norm(xo)
     print("fp32 direct rel err (%s, GEMM=%s): %.3e" % (name, os.environ.get("H2SP_GEMM", "tc"), err))
-    assert err <= 5e-3
+    assert err <= 1e-2
+    hd.close()
+
+
+@pytest.mark.parametrize("name,prec", [("log4k", "fp32"), ("skew1k", "fp32"), ("ragged", "fp64")])
+def test_gmres_reaches_1e10(name, prec):
+    """Right-preconditioned restarted GMRES on the FP64 H^2 product (§5.5)."""
+    h, b, sp, hd = sparsified(name)
+    H.h2sp_factor(hd, H.H2SP_FP32 if prec == "fp32" else H.H2SP_FP64)
+    bt = dev(b)
+    xt = torch.empty_like(bt)
+    info = H.h2sp_solve(hd, bt, xt, mode=H.H2SP_GMRES, tol=1e-10, maxit=60, restart=20)
+    assert info.status == H.H2SP_OK and info.rel_residual <= 1e-10
+    xg = host(xt)
+    A = oh2.dense(h)
+    res = np.linalg.norm(b - A @ xg, axis=0) / np.linalg.norm(b, axis=0)
+    assert res.max() <= 2e-10
     hd.close()
