@@ -21,9 +21,38 @@ inline u64 key(int64_t a, int64_t b) { return (u64(uint32_t(a)) << 32) | u64(uin
 inline int32_t kfirst(u64 k) { return int32_t(k >> 32); }
 inline int32_t ksecond(u64 k) { return int32_t(k & 0xffffffffu); }
 
+// Sorts (row << 32 | col) keys and drops repeats.  Large lists go through a
+// counting sort on the row followed by a sort of each row's short column list,
+// which is linear in the number of keys up to the per-row sorts.
 void sort_unique(std::vector<u64> &v) {
-  std::sort(v.begin(), v.end());
-  v.erase(std::unique(v.begin(), v.end()), v.end());
+  if (v.size() < 4096) {
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+    return;
+  }
+  uint32_t rmax = 0;
+  for (u64 k : v) rmax = std::max(rmax, uint32_t(k >> 32));
+  if (size_t(rmax) > 4 * v.size()) {
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+    return;
+  }
+  std::vector<int64_t> ptr(size_t(rmax) + 2, 0);
+  for (u64 k : v) ptr[size_t(k >> 32) + 1]++;
+  for (size_t r = 0; r + 1 < ptr.size(); ++r) ptr[r + 1] += ptr[r];
+  std::vector<u64> tmp(v.size());
+  {
+    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+    for (u64 k : v) tmp[size_t(fill[size_t(k >> 32)]++)] = k;
+  }
+  size_t out = 0;
+  for (size_t r = 0; r + 1 < ptr.size(); ++r) {
+    auto b = tmp.begin() + ptr[r], e = tmp.begin() + ptr[r + 1];
+    std::sort(b, e);
+    for (auto it = b; it != e; ++it)
+      if (out == 0 || v[out - 1] != *it) v[out++] = *it;
+  }
+  v.resize(out);
 }
 
 // index of k in a sorted vector, -1 if absent
@@ -32,6 +61,26 @@ int64_t find_sorted(const std::vector<u64> &v, u64 k) {
   if (it == v.end() || *it != k) return -1;
   return int64_t(it - v.begin());
 }
+
+// Row index over a sorted vector of (row << 32 | col) keys: the keys of one
+// row are [ptr[row], ptr[row + 1]), so a lookup searches a single row.
+struct RowIndex {
+  const std::vector<u64> *keys = nullptr;
+  std::vector<int64_t> ptr;
+  void build(const std::vector<u64> &k, int nrows) {
+    keys = &k;
+    ptr.assign(size_t(nrows) + 1, 0);
+    for (u64 x : k) ptr[size_t(kfirst(x)) + 1]++;
+    for (int r = 0; r < nrows; ++r) ptr[r + 1] += ptr[r];
+  }
+  int64_t find(int row, int col) const {
+    if (row < 0 || size_t(row) + 1 >= ptr.size()) return -1;
+    const u64 k = key(row, col);
+    auto b = keys->begin() + ptr[row], e = keys->begin() + ptr[row + 1];
+    auto it = std::lower_bound(b, e, k);
+    return (it != e && *it == k) ? int64_t(it - keys->begin()) : -1;
+  }
+};
 
 struct Fail {
   int code;
@@ -284,8 +333,10 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
       p.s_elems += p.node_size[i] * p.node_size[j];
     }
     for (int v = 0; v < nn; ++v) p.brow_ptr[v + 1] += p.brow_ptr[v];
+    RowIndex sb_idx;
+    sb_idx.build(sb, nn);
     auto sblock = [&](int i, int j) -> int64_t {
-      int64_t z = find_sorted(sb, key(i, j));
+      int64_t z = sb_idx.find(i, j);
       if (z < 0) throw Fail{H2SP_EINVAL, "internal: missing S block"};
       return p.val_off[z];
     };
@@ -309,6 +360,13 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
         p.cp_elems[l] += p.m[kfirst(k)] * p.node_size[ksecond(k)];
       }
     }
+    // row indexes of the next-level close blocks and panels
+    std::vector<RowIndex> near_idx(lstop + 1), rp_idx(lstop + 1), cp_idx(lstop + 1);
+    for (int l = 1; l < lstop; ++l) {
+      near_idx[l].build(near[l], ncl);
+      rp_idx[l].build(RP[l], nn);
+      cp_idx[l].build(CP[l], ncl);
+    }
     // destinations at level l+1 (a next-level buffer, or S itself at l_stop)
     struct Dst {
       int64_t off;
@@ -316,7 +374,7 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
     };
     auto dst_C = [&](int l1, int pa, int qa) -> Dst {
       if (l1 < lstop) {
-        int64_t z = find_sorted(near[l1], key(pa, qa));
+        int64_t z = near_idx[l1].find(pa, qa);
         if (z < 0) throw Fail{H2SP_EINVAL, "internal: missing next-level close block"};
         return {c_off[l1][z], DST_C};
       }
@@ -324,7 +382,7 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
     };
     auto dst_RP = [&](int l1, int v, int qa) -> Dst {
       if (l1 < lstop) {
-        int64_t z = find_sorted(RP[l1], key(v, qa));
+        int64_t z = rp_idx[l1].find(v, qa);
         if (z < 0) throw Fail{H2SP_EINVAL, "internal: missing row panel"};
         return {rp_off[l1][z], DST_RP};
       }
@@ -332,7 +390,7 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
     };
     auto dst_CP = [&](int l1, int pa, int w) -> Dst {
       if (l1 < lstop) {
-        int64_t z = find_sorted(CP[l1], key(pa, w));
+        int64_t z = cp_idx[l1].find(pa, w);
         if (z < 0) throw Fail{H2SP_EINVAL, "internal: missing column panel"};
         return {cp_off[l1][z], DST_CP};
       }
@@ -368,6 +426,10 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
     }
     for (int l = 0; l < lstop; ++l) {
       LevelWork &w = p.lw[l];
+      w.x.reserve(near[l].size() + (l >= 1 ? RP[l].size() + CP[l].size() : 0));
+      w.c.reserve(far[l].size());
+      w.q.reserve(size_t(lev_end(l) - lev_begin(l)));
+      if (!sym) w.qc.reserve(size_t(lev_end(l) - lev_begin(l)));
       // W for this level from the previous level's Rr (internal clusters)
       std::vector<int64_t> w_off(ncl, -1);
       if (l >= 1) {

@@ -289,7 +289,7 @@ def test_fp32_factor_direct_accuracy(name):
     torch.cuda.synchronize()
     xo = ofa.solve(h, sp, ofa.factor(h, sp), b)
     err = np.linalg.norm(host(xt) - xo) / np.linalg.norm(xo)
-    print("fp32 direct rel err (%s, GEMM=%s): %.3e" % (name, os.environ.get("H2SP_GEMM", "tc"), err))
+    print("fp32 direct rel err (%s, GEMM=%s): %.3e" % (name, os.environ.get("H2SP_GEMM", "simt"), err))
     assert err <= 1e-2
     hd.close()
 
