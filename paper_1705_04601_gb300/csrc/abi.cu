@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -115,7 +116,13 @@ struct h2sp_handle {
     if (!v.empty()) ck(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, stream));
     return d;
   }
+  LuAsync la;  // look-ahead stream and events of the block LU (created on first use)
   void release() {
+    if (la.side) cudaStreamSynchronize(la.side);
+    if (la.next) cudaEventDestroy(la.next);
+    if (la.panel) cudaEventDestroy(la.panel);
+    if (la.side) cudaStreamDestroy(la.side);
+    la = LuAsync();
     if (allocs.empty()) return;
     for (void *p : allocs) cudaFreeAsync(p, stream);
     allocs.clear();
@@ -124,6 +131,17 @@ struct h2sp_handle {
 };
 
 namespace {
+
+// The next panel is factored on a side stream while the trailing update runs;
+// H2SP_LOOKAHEAD=0 keeps every step on the caller's stream.
+bool lookahead_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = std::getenv("H2SP_LOOKAHEAD");
+    v = (e && std::strcmp(e, "0") == 0) ? 0 : 1;
+  }
+  return v == 1;
+}
 
 void init_pool_once() {
   static bool done = false;
@@ -713,6 +731,14 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
       h->err = h->alloc<int>(1);
       h->dinv = h->alloc<double>(size_t(std::max<int64_t>(p.dinv_elems, 1)));
     }
+    if (h->la.side == nullptr && lookahead_enabled()) {
+      int lo = 0, hi = 0;
+      ck(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      ck(cudaStreamCreateWithPriority(&h->la.side, cudaStreamNonBlocking, hi));
+      ck(cudaEventCreateWithFlags(&h->la.next, cudaEventDisableTiming));
+      ck(cudaEventCreateWithFlags(&h->la.panel, cudaEventDisableTiming));
+    }
+    const LuAsync *la = h->la.side ? &h->la : nullptr;
     h->prec = -1;
     ck(cudaMemsetAsync(h->fronts, 0, size_t(std::max<int64_t>(p.front_elems, 1)) * esz, s));
     ck(cudaMemsetAsync(h->err, 0, sizeof(int), s));
@@ -723,7 +749,7 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
       ck(launch_assemble<double>(h->asm_items, na, h->S, F, s, &h->prof, abytes));
       for (const FrontLevel &L : h->flev) {
         ck(launch_lu_level<double>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv,
-                                   h->swaps, h->err, s, &h->prof));
+                                   h->swaps, h->err, s, la, &h->prof));
         ck(launch_extend_add_impl<double>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s, &h->prof, L.b2));
       }
       ck(launch_make_perm<double>(h->fr, int(p.fronts.size()), h->max_s_all, h->piv, h->perm, s, &h->prof));
@@ -734,7 +760,7 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
       ck(launch_assemble<float>(h->asm_items, na, h->S, F, s, &h->prof, abytes));
       for (const FrontLevel &L : h->flev) {
         ck(launch_lu_level<float>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv,
-                                  h->swaps, h->err, s, &h->prof));
+                                  h->swaps, h->err, s, la, &h->prof));
         ck(launch_extend_add_impl<float>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s, &h->prof, L.b2));
       }
       ck(launch_make_perm<float>(h->fr, int(p.fronts.size()), h->max_s_all, h->piv, h->perm, s, &h->prof));

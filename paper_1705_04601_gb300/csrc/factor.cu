@@ -27,9 +27,10 @@
 namespace h2sp {
 namespace {
 
+// |x| with the sign bit cleared (-0 becomes +0, which the bit-pattern argmax needs)
 template <typename T>
 __device__ __forceinline__ T tabs(T x) {
-  return x < T(0) ? -x : x;
+  return fabs(x);
 }
 
 template <typename T>
@@ -140,19 +141,35 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel(const FrontDev *__restr
 }
 
 constexpr int kClusterPanelThreads = 512;
+constexpr int kMaxPanelCluster = 16;
+constexpr int kPanelRowsPerThread = 4;  // rows per CTA <= 4 * 512 (shared memory allows ~800)
+
+__device__ __forceinline__ void cluster_arrive_release() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 
 // Panel factorization by one thread-block cluster per front.  The panel rows
 // [j0, f) are split into C contiguous chunks, one per CTA, held in shared
-// memory for the whole panel.  Rows are not moved while the panel is factored
-// (logical pivoting): per column, every CTA offers its best not-yet-pivoted
-// supernode row, one cluster barrier, every CTA reduces the C candidates read
-// through distributed shared memory and reads the pivot row remotely, the
-// owner retires that row, and every CTA updates its remaining rows.  A pivot
-// row is never written after it is retired, so remote readers need no second
-// barrier; candidate slots alternate between columns.  At the end each CTA
-// turns the pivot sequence into LAPACK's sequential row interchanges and
-// writes its rows to their final positions.  Exact ties between candidates go
-// to the lowest row index.
+// memory for the whole panel; thread t owns local rows t, t + 512, ...
+// Rows are not moved while the panel is factored (logical pivoting).  Per
+// column j:
+//   A  column j of every live row receives the update of pivot j - 1;
+//   B  each CTA finds its best live supernode row of column j (exact ties to
+//      the lowest row) and pushes (value, row index, row) into a mailbox slot
+//      of every CTA of the cluster (remote shared-memory stores);
+//   -  cluster barrier, split: after arriving, the CTA applies the deferred
+//      update of pivot j - 1 to columns j+1.. of its live rows, then waits;
+//   C  every warp reduces the C candidates of its own mailbox: pivot row p;
+//      the pivot row's columns > j are brought up to date from the previous
+//      pivot row, its owner retires it, and the multipliers of column j are
+//      formed.
+// The mailbox alternates between two slots; a slot is rewritten only after
+// every CTA has passed the barrier of the column that read it.  At the end
+// each CTA turns the pivot sequence into LAPACK's sequential row interchanges
+// and writes its rows to their final positions.
 template <typename T, int NB>
 __global__ void __launch_bounds__(kClusterPanelThreads) k_panel_cluster(const FrontDev *__restrict__ fr, int j0,
                                                                         T *__restrict__ fronts, int32_t *__restrict__ piv,
@@ -175,14 +192,11 @@ __global__ void __launch_bounds__(kClusterPanelThreads) k_panel_cluster(const Fr
   T *P = reinterpret_cast<T *>(smraw);                        // [NB][per], column c at P + c * per
   int32_t *dest = reinterpret_cast<int32_t *>(P + NB * per);  // [per] final row of each local row
   unsigned char *done = reinterpret_cast<unsigned char *>(dest + per);  // [per] retired pivot rows
-  __shared__ T cand_v[2];
-  __shared__ int cand_i[2];
-  __shared__ T cand_row[2][NB];
-  __shared__ T allrow[32 * NB];
-  __shared__ T allv[32];
-  __shared__ int alli[32];
-  __shared__ int s_w;
-  __shared__ T urow[NB];
+  __shared__ T mb_row[2][kMaxPanelCluster][NB];  // mailbox: candidate rows, values, row indices
+  __shared__ T mb_v[2][kMaxPanelCluster];
+  __shared__ int mb_i[2][kMaxPanelCluster];
+  __shared__ T urow[2][NB];  // up-to-date pivot rows of the last two columns
+  __shared__ T stage[kClusterPanelThreads / 32][NB];  // each warp's candidate row
   __shared__ T redv[kClusterPanelThreads / 32];
   __shared__ int redi[kClusterPanelThreads / 32];
   __shared__ int hist[NB];
@@ -194,76 +208,104 @@ __global__ void __launch_bounds__(kClusterPanelThreads) k_panel_cluster(const Fr
     P[c * per + i] = A[(r_lo + i) + int64_t(j0 + c) * ld];
   }
   for (int i = tid; i < per; i += nt) done[i] = 0, dest[i] = r_lo + i;
-  __syncthreads();
   const int i_hi = max(0, min(F.s, r_lo + nr) - r_lo);  // local supernode rows
+  T lmul[kPanelRowsPerThread];  // multipliers of the last pivot for this thread's rows
+#pragma unroll
+  for (int k = 0; k < kPanelRowsPerThread; ++k) lmul[k] = T(0);
+  T u_next = T(0);  // the last pivot row's entry in the current column
+  // every CTA of the cluster is running (and its mailbox exists) past this point
+  cluster.sync();
   for (int j = 0; j < jb; ++j) {
     const int buf = j & 1;
+    // A: pivot j - 1 on column j, and this thread's candidate
     T bv = T(-1);
     int bi = INT_MAX;
-    for (int i = tid; i < i_hi; i += nt) {
-      if (done[i]) continue;
-      const T v = tabs(P[j * per + i]);
-      if (v > bv) bv = v, bi = r_lo + i;
+#pragma unroll
+    for (int k = 0; k < kPanelRowsPerThread; ++k) {
+      const int i = tid + k * nt;
+      if (i >= nr) break;
+      if (i < i_hi && done[i]) continue;
+      T v = P[j * per + i];
+      if (j > 0) {
+        v -= lmul[k] * u_next;
+        P[j * per + i] = v;
+      }
+      if (i < i_hi) {
+        const T a = tabs(v);
+        if (a > bv) bv = a, bi = r_lo + i;
+      }
     }
+    // B: warp candidates, each staged with its row (the owner may update the
+    // row in shared memory during the barrier), then the CTA candidate
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ov > bv || (ov == bv && oi < bi)) bv = ov, bi = oi;
     }
+    __syncwarp();
+    {
+      const int wl = (bi == INT_MAX) ? -1 : bi - r_lo;
+      for (int c = lane; c < jb; c += 32) stage[wid][c] = wl >= 0 ? P[c * per + wl] : T(0);
+    }
     if (lane == 0) redv[wid] = bv, redi[wid] = bi;
     __syncthreads();
-    if (wid == 0) {
+    int ww = lane;
+    {
       T v = lane < (nt >> 5) ? redv[lane] : T(-1);
       int i = lane < (nt >> 5) ? redi[lane] : INT_MAX;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const T ov = __shfl_xor_sync(0xffffffffu, v, o);
         const int oi = __shfl_xor_sync(0xffffffffu, i, o);
-        if (ov > v || (ov == v && oi < i)) v = ov, i = oi;
+        const int ow = __shfl_xor_sync(0xffffffffu, ww, o);
+        if (ov > v || (ov == v && oi < i)) v = ov, i = oi, ww = ow;
       }
-      if (lane == 0) cand_v[buf] = v, cand_i[buf] = i;
-      // publish the candidate row itself so that one remote round trip suffices
-      const int li = (i == INT_MAX) ? -1 : i - r_lo;
-      for (int c = lane; c < jb; c += 32) cand_row[buf][c] = li >= 0 ? P[c * per + li] : T(0);
+      bv = v;
+      bi = i;
     }
-    cluster.sync();
-    // read every CTA's candidate value, index and row in one go
     for (int e = tid; e < C * (jb + 2); e += nt) {
       const int q = e / (jb + 2), c = e % (jb + 2);
-      if (c < jb)
-        allrow[q * NB + c] = cluster.map_shared_rank(&cand_row[0][0], q)[buf * NB + c];
-      else if (c == jb)
-        allv[q] = cluster.map_shared_rank(cand_v, q)[buf];
-      else
-        alli[q] = cluster.map_shared_rank(cand_i, q)[buf];
+      if (c < jb) {
+        cluster.map_shared_rank(&mb_row[buf][rank][0], q)[c] = stage[ww][c];
+      } else if (c == jb) {
+        *cluster.map_shared_rank(&mb_v[buf][rank], q) = bv;
+      } else {
+        *cluster.map_shared_rank(&mb_i[buf][rank], q) = bi;
+      }
     }
-    __syncthreads();
-    if (wid == 0) {
-      T v = lane < C ? allv[lane] : T(-1);
-      int i = lane < C ? alli[lane] : INT_MAX;
-      int w = lane;
+    cluster_arrive_release();
+    // deferred: pivot j - 1 on columns j+1 .. jb-1 of the live rows
+    if (j > 0) {
+      const T *u = urow[(j - 1) & 1];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, v, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, i, o);
-        const int ow = __shfl_xor_sync(0xffffffffu, w, o);
-        if (ov > v || (ov == v && oi < i)) v = ov, i = oi, w = ow;
-      }
-      if (lane == 0) {
-        if (i == INT_MAX) {  // no finite candidate
-          i = -1;
-          w = -1;
-          if (rank == 0) atomicOr(err, 2);
-        }
-        hist[j] = i;
-        s_w = w;
+      for (int k = 0; k < kPanelRowsPerThread; ++k) {
+        const int i = tid + k * nt;
+        if (i >= nr) break;
+        if (i < i_hi && done[i]) continue;
+        const T l = lmul[k];
+        for (int c = j + 1; c < jb; ++c) P[c * per + i] -= l * u[c];
       }
     }
-    __syncthreads();
-    int p = hist[j];
-    if (p < 0) {
-      // keep the sequence a permutation: the lowest not-yet-pivoted supernode row
+    cluster_wait_acquire();
+    // C: the pivot of column j from the mailbox
+    T v = lane < C ? mb_v[buf][lane] : T(-1);
+    int i = lane < C ? mb_i[buf][lane] : INT_MAX;
+    int w = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+      const int ow = __shfl_xor_sync(0xffffffffu, w, o);
+      if (ov > v || (ov == v && oi < i)) v = ov, i = oi, w = ow;
+    }
+    int p = i;
+    T pv, lprev = T(0);
+    const T *prow;
+    if (p == INT_MAX) {
+      // no finite candidate: keep the sequence a permutation with the lowest
+      // not-yet-pivoted supernode row; the factorization reports the failure
+      if (tid == 0 && rank == 0) atomicOr(err, 2);
       p = j0;
       bool used = true;
       while (used) {
@@ -271,31 +313,47 @@ __global__ void __launch_bounds__(kClusterPanelThreads) k_panel_cluster(const Fr
         for (int q = 0; q < j; ++q)
           if (hist[q] == p) used = true, ++p;
       }
-      __syncthreads();
-      if (tid == 0) hist[j] = p;
-      __syncthreads();
-      const int own = (p - j0) / per;
-      const T *Pp = cluster.map_shared_rank(P, own);
-      for (int c = tid; c < jb; c += nt) urow[c] = Pp[c * per + (p - (j0 + own * per))];
+      prow = nullptr;
+      pv = T(0);
     } else {
-      for (int c = tid; c < jb; c += nt) urow[c] = allrow[s_w * NB + c];
+      prow = &mb_row[buf][w][0];
+      pv = prow[j];
+      if (j > 0) lprev = prow[j - 1];
     }
-    if (p >= r_lo && p < r_lo + nr && tid == 0) done[p - r_lo] = 1;
-    __syncthreads();
-    const T pv = urow[j];
-    if (pv == T(0)) {
-      if (tid == 0 && rank == 0) atomicOr(err, 1);
-    } else {
-      const T inv = T(1) / pv;
-      for (int i = tid; i < nr; i += nt) {
-        if (i < i_hi && done[i]) continue;
-        const T l = P[j * per + i] * inv;
-        P[j * per + i] = l;
-        for (int c = j + 1; c < jb; ++c) P[c * per + i] -= l * urow[c];
+    if (tid == 0) hist[j] = p;
+    // up-to-date pivot row: columns > j still lack the update of pivot j - 1
+    if (j + 1 < jb) {
+      if (prow != nullptr) {
+        u_next = prow[j + 1] - (j > 0 ? lprev * urow[(j - 1) & 1][j + 1] : T(0));
+        if (wid == 0)
+          for (int c = j + 1 + lane; c < jb; c += 32)
+            urow[buf][c] = prow[c] - (j > 0 ? lprev * urow[(j - 1) & 1][c] : T(0));
+      } else {
+        u_next = T(0);
+        if (wid == 0)
+          for (int c = j + 1 + lane; c < jb; c += 32) urow[buf][c] = T(0);
       }
     }
-    __syncthreads();
+    if (p >= r_lo && p < r_lo + nr && (p - r_lo) % nt == tid) done[p - r_lo] = 1;
+    if (pv == T(0)) {
+      if (tid == 0 && rank == 0) atomicOr(err, 1);
+#pragma unroll
+      for (int k = 0; k < kPanelRowsPerThread; ++k) lmul[k] = T(0);
+    } else {
+      const T inv = T(1) / pv;
+#pragma unroll
+      for (int k = 0; k < kPanelRowsPerThread; ++k) {
+        const int ii = tid + k * nt;
+        lmul[k] = T(0);
+        if (ii >= nr) break;
+        if (ii < i_hi && done[ii]) continue;
+        const T l = P[j * per + ii] * inv;
+        P[j * per + ii] = l;
+        lmul[k] = l;
+      }
+    }
   }
+  __syncthreads();
   // LAPACK-style interchanges from the pivot sequence, and where every row goes
   if (tid == 0) {
     int n = 0;  // touched positions: position lrow[q] currently holds physical row lsrc[q]
@@ -332,7 +390,280 @@ __global__ void __launch_bounds__(kClusterPanelThreads) k_panel_cluster(const Fr
     const int i = e % nr, c = e / nr;
     A[dest[i] + int64_t(j0 + c) * ld] = P[c * per + i];
   }
-  // no CTA may exit while others can still read its shared memory
+  // no CTA may exit while others can still write into its mailbox
+  cluster.sync();
+}
+
+// Argmax over a warp: the largest value, ties to the lowest index; lanes
+// without a candidate pass (anything, INT_MAX).  Every lane gets the result
+// (value -1 and INT_MAX when no lane has a candidate).  Values are absolute
+// values (non-negative, never NaN); for FP32 their bit patterns order like
+// the values, so two hardware warp reductions do it.
+template <typename T>
+__device__ __forceinline__ void warp_argmax(T &v, int &i) {
+  if constexpr (sizeof(T) == 4) {
+    const unsigned key = i != INT_MAX ? __float_as_uint(v) : 0u;
+    const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+    const int imin = __reduce_min_sync(0xffffffffu, (i != INT_MAX && key == kmax) ? i : INT_MAX);
+    v = imin != INT_MAX ? __uint_as_float(kmax) : T(-1);
+    i = imin;
+  } else {
+    if (i == INT_MAX) v = T(-1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+      if (ov > v || (ov == v && oi < i)) v = ov, i = oi;
+    }
+  }
+}
+
+constexpr int kRegPanelThreads = 384;
+constexpr int kRegPanelRows = 2;  // panel rows per thread, held in registers
+constexpr int kRegPanelMaxRows = kRegPanelThreads * kRegPanelRows;
+
+// Panel factorization with the rows in registers, by one thread-block cluster
+// per front.  Thread t of CTA q holds rows r_lo(q) + t and r_lo(q) + t + 384,
+// NB values each, in a shifting frame: at column j, slot 0 holds column j,
+// slot c column j + c, and the multipliers l_0 .. l_{j-1} of the row fill the
+// last j slots.  Per column: every warp stages its best live supernode row,
+// one barrier, the CTA candidate (value, row index, pivot value, row) is
+// pushed into a mailbox slot of every CTA of the cluster, a cluster barrier,
+// then every thread reduces the C candidates of its own mailbox (exact ties
+// to the lowest row), retires the pivot row if it holds it, and updates its
+// live rows while shifting them by one slot: x[c] = x[c+1] - l u[c] with
+// l = x[0] / pivot and u the pivot row's columns j+1.., and x[NB-1] = l.
+// Rows are never moved during the panel (logical pivoting); at the end the
+// pivot sequence becomes LAPACK's sequential interchanges (piv) and every row
+// is written once to its final position.
+template <typename T, int NB>
+__global__ void __launch_bounds__(kRegPanelThreads, 1) k_panel_reg(const FrontDev *__restrict__ fr, int j0,
+                                                                   T *__restrict__ fronts, int32_t *__restrict__ piv,
+                                                                   int32_t *__restrict__ swaps, int *__restrict__ err) {
+  namespace cg = cooperative_groups;
+  static_assert(kRegPanelRows == 2, "the staging below names rows 0 and 1");
+  static_assert(NB % 4 == 0 && NB <= 64, "panel width");
+  constexpr int NW = kRegPanelThreads / 32;
+  constexpr int VE = 16 / int(sizeof(T));  // elements per 16-byte vector
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = int(cluster.num_blocks());
+  const int rank = int(cluster.block_rank());
+  const int fi = blockIdx.x / C;
+  const FrontDev F = fr[fi];
+  if (j0 >= F.s) return;  // uniform over the cluster
+  const int jb = min(NB, F.s - j0);
+  T *A = fronts + F.off;
+  const int64_t ld = F.f;
+  const int R = F.f - j0;
+  const int per = (R + C - 1) / C;
+  const int r_lo = j0 + rank * per;
+  const int nr = max(0, min(F.f, r_lo + per) - r_lo);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int32_t *pos_of = reinterpret_cast<int32_t *>(smraw);  // [R] final position of each panel row
+  int32_t *at_pos = pos_of + R;                          // [R] row now at each position
+  unsigned char *touched = reinterpret_cast<unsigned char *>(at_pos + R);  // [R]
+  __shared__ __align__(16) T mb_row[2][kMaxPanelCluster][NB];  // mailbox: pivot candidates' columns j+1..
+  __shared__ T mb_v[2][kMaxPanelCluster], mb_pv[2][kMaxPanelCluster];
+  __shared__ int mb_i[2][kMaxPanelCluster];
+  __shared__ __align__(16) T stage[NW][NB];
+  __shared__ T stage_pv[NW];
+  __shared__ T redv[NW];
+  __shared__ int redi[NW];
+  __shared__ int hist[NB];
+  __shared__ int32_t lrow[2 * NB], lsrc[2 * NB];
+  __shared__ int nswap;
+  const int tid = threadIdx.x, nt = kRegPanelThreads, lane = tid & 31, wid = tid >> 5;
+
+  T x[kRegPanelRows][NB];
+  int ret[kRegPanelRows];  // -2: no row, -1: live, >= 0: column at which it became a pivot
+  bool sn[kRegPanelRows];  // supernode row (pivot candidate)
+#pragma unroll
+  for (int k = 0; k < kRegPanelRows; ++k) {
+    const int i = tid + k * nt;
+    ret[k] = i < nr ? -1 : -2;
+    sn[k] = i < nr && r_lo + i < F.s;
+    const T *src = A + (r_lo + i) + int64_t(j0) * ld;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) x[k][c] = (i < nr && c < jb) ? src[int64_t(c) * ld] : T(0);
+  }
+  // every CTA of the cluster is running (its mailbox exists) past this point
+  cluster.sync();
+  for (int j = 0; j < jb; ++j) {
+    const int buf = j & 1;
+    // this thread's best live supernode row (the lower row wins ties)
+    T bv = T(-1);
+    int bi = INT_MAX, bk = -1;
+#pragma unroll
+    for (int k = 0; k < kRegPanelRows; ++k)
+      if (ret[k] == -1 && sn[k]) {
+        const T a = tabs(x[k][0]);
+        if (a > bv) bv = a, bi = r_lo + tid + k * nt, bk = k;
+      }
+    const int my_bi = bi;
+    warp_argmax(bv, bi);
+    // the owner stages the warp candidate: slots 1.. (columns j+1..) and the pivot value
+    if (bi != INT_MAX && my_bi == bi) {
+      T *st = stage[wid];
+      if (bk == 0) {
+        stage_pv[wid] = x[0][0];
+#pragma unroll
+        for (int c = 0; c < NB; c += VE) {
+          if constexpr (VE == 4) {
+            *reinterpret_cast<float4 *>(st + c) =
+                make_float4(x[0][c + 1], x[0][c + 2], x[0][c + 3], c + 4 < NB ? x[0][(c + 4) % NB] : T(0));
+          } else {
+            *reinterpret_cast<double2 *>(st + c) = make_double2(x[0][c + 1], c + 2 < NB ? x[0][(c + 2) % NB] : T(0));
+          }
+        }
+      } else {
+        stage_pv[wid] = x[kRegPanelRows - 1][0];
+#pragma unroll
+        for (int c = 0; c < NB; c += VE) {
+          constexpr int K = kRegPanelRows - 1;
+          if constexpr (VE == 4) {
+            *reinterpret_cast<float4 *>(st + c) =
+                make_float4(x[K][c + 1], x[K][c + 2], x[K][c + 3], c + 4 < NB ? x[K][(c + 4) % NB] : T(0));
+          } else {
+            *reinterpret_cast<double2 *>(st + c) = make_double2(x[K][c + 1], c + 2 < NB ? x[K][(c + 2) % NB] : T(0));
+          }
+        }
+      }
+    }
+    if (lane == 0) redv[wid] = bv, redi[wid] = bi;
+    __syncthreads();
+    int ww;
+    {
+      T v = lane < NW ? redv[lane] : T(-1);
+      int i = lane < NW ? redi[lane] : INT_MAX;
+      const int mine = i;
+      warp_argmax(v, i);
+      ww = __ffs(__ballot_sync(0xffffffffu, i != INT_MAX && mine == i)) - 1;  // the winning warp
+      bv = v;
+      bi = i;
+    }
+    // push, one warp per target CTA, one 16-byte store per lane: columns
+    // beyond the panel (and the multiplier slots) go out as zeros
+    const int ulen = jb - j - 1;
+    for (int q = wid; q < C; q += NW) {
+      if (lane < NB / VE) {
+        const int c = lane * VE;
+        T *dst = cluster.map_shared_rank(&mb_row[buf][rank][0], q) + c;
+        if constexpr (VE == 4) {
+          float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (bi != INT_MAX) s = *reinterpret_cast<const float4 *>(&stage[ww < 0 ? 0 : ww][c]);
+          s.x = c < ulen ? s.x : 0.f;
+          s.y = c + 1 < ulen ? s.y : 0.f;
+          s.z = c + 2 < ulen ? s.z : 0.f;
+          s.w = c + 3 < ulen ? s.w : 0.f;
+          *reinterpret_cast<float4 *>(dst) = s;
+        } else {
+          double2 s = make_double2(0.0, 0.0);
+          if (bi != INT_MAX) s = *reinterpret_cast<const double2 *>(&stage[ww < 0 ? 0 : ww][c]);
+          s.x = c < ulen ? s.x : 0.0;
+          s.y = c + 1 < ulen ? s.y : 0.0;
+          *reinterpret_cast<double2 *>(dst) = s;
+        }
+      } else if (lane == NB / VE) {
+        *cluster.map_shared_rank(&mb_v[buf][rank], q) = bv;
+      } else if (lane == NB / VE + 1) {
+        *cluster.map_shared_rank(&mb_i[buf][rank], q) = bi;
+      } else if (lane == NB / VE + 2) {
+        *cluster.map_shared_rank(&mb_pv[buf][rank], q) = bi != INT_MAX ? stage_pv[ww < 0 ? 0 : ww] : T(0);
+      }
+    }
+    cluster_arrive_release();
+    cluster_wait_acquire();
+    // the pivot of column j, and the CTA whose mailbox slot holds it
+    T v = lane < C ? mb_v[buf][lane] : T(-1);
+    int p = lane < C ? mb_i[buf][lane] : INT_MAX;
+    const int mine = p;
+    warp_argmax(v, p);
+    const int w = __ffs(__ballot_sync(0xffffffffu, p != INT_MAX && mine == p)) - 1;
+    T pv;
+    if (p == INT_MAX) {
+      // no finite candidate: keep the sequence a permutation with the lowest
+      // not-yet-pivoted supernode row; the factorization reports the failure
+      if (tid == 0 && rank == 0) atomicOr(err, 2);
+      p = j0;
+      bool used = true;
+      while (used) {
+        used = false;
+        for (int q = 0; q < j; ++q)
+          if (hist[q] == p) used = true, ++p;
+      }
+      pv = T(0);
+    } else {
+      pv = mb_pv[buf][w];
+    }
+    if (tid == 0) hist[j] = p;
+#pragma unroll
+    for (int k = 0; k < kRegPanelRows; ++k)
+      if (ret[k] == -1 && r_lo + tid + k * nt == p) ret[k] = j;
+    if (pv == T(0) && tid == 0 && rank == 0) atomicOr(err, 1);
+    const T inv = pv != T(0) ? T(1) / pv : T(0);
+    const T *u = &mb_row[buf][w < 0 ? 0 : w][0];  // no pivot: multipliers are 0 anyway
+#pragma unroll
+    for (int k = 0; k < kRegPanelRows; ++k) {
+      if (ret[k] != -1) continue;
+      const T l = x[k][0] * inv;
+#pragma unroll
+      for (int c = 0; c < NB; c += VE) {
+        if constexpr (VE == 4) {
+          const float4 q = *reinterpret_cast<const float4 *>(u + c);
+          x[k][c] = x[k][c + 1] - l * q.x;
+          x[k][c + 1] = x[k][c + 2] - l * q.y;
+          x[k][c + 2] = x[k][c + 3] - l * q.z;
+          if (c + 4 < NB) x[k][c + 3] = x[k][(c + 4) % NB] - l * q.w;
+        } else {
+          const double2 q = *reinterpret_cast<const double2 *>(u + c);
+          x[k][c] = x[k][c + 1] - l * q.x;
+          if (c + 2 < NB) x[k][c + 1] = x[k][(c + 2) % NB] - l * q.y;
+        }
+      }
+      x[k][NB - 1] = l;
+    }
+  }
+  // LAPACK's sequential interchanges from the pivot sequence (positions and
+  // rows relative to j0); every CTA computes them for its own rows
+  for (int r = tid; r < R; r += nt) pos_of[r] = r, at_pos[r] = r, touched[r] = 0;
+  __syncthreads();
+  if (tid == 0) {
+    int n = 0;
+    for (int j = 0; j < jb; ++j) {
+      const int pr = hist[j] - j0, pp = pos_of[pr];
+      if (rank == 0) piv[F.piv_off + j0 + j] = j0 + pp;
+      if (pp == j) continue;
+      const int rc = at_pos[j];
+      at_pos[j] = pr;
+      at_pos[pp] = rc;
+      pos_of[pr] = j;
+      pos_of[rc] = pp;
+      if (!touched[j]) touched[j] = 1, lrow[n++] = j;
+      if (!touched[pp]) touched[pp] = 1, lrow[n++] = pp;
+    }
+    for (int q = 0; q < n; ++q) lsrc[q] = at_pos[lrow[q]];
+    nswap = n;
+    if (rank == 0) {
+      int32_t *sw = swaps + int64_t(fi) * (1 + 2 * kMaxSwapRows);
+      for (int q = 0; q < n; ++q) sw[1 + q] = j0 + lrow[q], sw[1 + kMaxSwapRows + q] = j0 + lsrc[q];
+      sw[0] = n;
+    }
+  }
+  __syncthreads();
+  // every row once to its final position: multipliers, and the U part of pivot rows
+#pragma unroll
+  for (int k = 0; k < kRegPanelRows; ++k) {
+    if (ret[k] == -2) continue;
+    const int i = tid + k * nt;
+    T *dst = A + (j0 + pos_of[r_lo + i - j0]) + int64_t(j0) * ld;
+    const int jr = ret[k] >= 0 ? ret[k] : jb;  // columns < jr hold multipliers
+#pragma unroll
+    for (int s = 0; s < NB; ++s) {
+      if (s < jb - jr) dst[int64_t(jr + s) * ld] = x[k][s];            // U: column jr + s
+      if (s >= NB - jr) dst[int64_t(s - (NB - jr)) * ld] = x[k][s];     // L: column s - (NB - jr)
+    }
+  }
+  // no CTA exits while another may still read its mailbox
   cluster.sync();
 }
 
@@ -395,7 +726,8 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const FrontDev *__restrict__ 
 // tr*TM + i -- so each thread reads its TM (TN) values as 16-byte vectors.
 // The C tile is prefetched into the accumulators while the operands are staged.
 template <typename T, int BM, int BN, int TM, int TN, int NB>
-__global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict__ fr, int j0, T *__restrict__ fronts) {
+__global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict__ fr, int j0, T *__restrict__ fronts,
+                                                     int c_lo, int c_hi) {
   constexpr int RT = BM / TM, CT = BN / TN;  // thread grid over the tile (rows fastest)
   constexpr int PA = BM + 16 / int(sizeof(T)), PB = BN + 16 / int(sizeof(T));  // padded rows, 16-byte aligned
   constexpr int VA = 16 / int(sizeof(T));    // elements per 16-byte vector
@@ -404,8 +736,9 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
   const int jb = min(NB, F.s - j0);
   const int t0 = j0 + jb;
   const int nrest = F.f - t0;
-  const int rb = blockIdx.y * BM, cb = blockIdx.x * BN;
-  if (rb >= nrest || cb >= nrest) return;
+  const int ncol = min(nrest, c_hi);  // trailing columns [c_lo, ncol) of this launch
+  const int rb = blockIdx.y * BM, cb = c_lo + blockIdx.x * BN;
+  if (rb >= nrest || cb >= ncol) return;
   T *A = fronts + F.off;
   const int64_t ld = F.f;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -420,7 +753,7 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
       const int r = rb + tr + RT * i;
-      acc[i][j] = (c < nrest && r < nrest) ? A[(t0 + r) + int64_t(t0 + c) * ld] : T(0);
+      acc[i][j] = (c < ncol && r < nrest) ? A[(t0 + r) + int64_t(t0 + c) * ld] : T(0);
     }
   }
   // operand tiles: all loads of a pass are issued before any store (fixed trip counts)
@@ -448,7 +781,7 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
       const int e = tid + it * 256;
       const int k = e % NB, j = e / NB;
       const int c = cb + j;
-      v[it] = (k < jb && c < nrest) ? A[(j0 + k) + int64_t(t0 + c) * ld] : T(0);
+      v[it] = (k < jb && c < ncol) ? A[(j0 + k) + int64_t(t0 + c) * ld] : T(0);
     }
 #pragma unroll
     for (int it = 0; it < kIB; ++it) {
@@ -490,7 +823,7 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
 #pragma unroll
   for (int j = 0; j < TN; ++j) {
     const int c = cb + tc + CT * j;
-    if (c >= nrest) continue;
+    if (c >= ncol) continue;
     T *Cc = A + int64_t(t0 + c) * ld + t0;
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
@@ -806,6 +1139,45 @@ size_t panel_smem_bytes(int per) {
   return sizeof(T) * size_t(NB) * per + sizeof(int32_t) * size_t(per) + size_t(per) + 16;
 }
 
+// Largest cluster the register-resident panel kernel can run with (16 or 8;
+// 0 if none), for a panel of up to kRegPanelMaxRows rows per CTA.
+template <typename T, int NB>
+size_t reg_panel_smem_bytes(int R) {
+  return size_t(R) * (2 * sizeof(int32_t) + 1) + 16;
+}
+
+template <typename T, int NB>
+int reg_panel_cluster_max() {
+  static int cmax = -1;
+  if (cmax < 0) {
+    auto k = k_panel_reg<T, NB>;
+    const size_t smem = reg_panel_smem_bytes<T, NB>(kRegPanelMaxRows * kMaxPanelCluster);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cmax = 0;
+    for (int c : {16, 8}) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(unsigned(c));
+      cfg.blockDim = dim3(kRegPanelThreads);
+      cfg.dynamicSmemBytes = smem;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = unsigned(c);
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) == cudaSuccess && n > 0) {
+        cmax = c;
+        break;
+      }
+    }
+    cudaGetLastError();
+  }
+  return cmax;
+}
+
 template <typename T, int NB>
 int panel_cluster_size(int R) {
   constexpr size_t kSmemCap = 200 * 1024;
@@ -857,20 +1229,37 @@ cudaError_t launch_assemble(const AItem *items, int64_t n, const double *S, T *f
   return cudaGetLastError();
 }
 
-// H2SP_GEMM=tc in the environment runs the FP32 trailing update on the tensor
-// cores (three-term TF32 split); the default is the FP32 SIMT kernel.
+// The FP32 trailing update runs on the tensor cores (three-term TF32 split);
+// H2SP_GEMM=simt selects the CUDA-core kernel instead.
 inline bool use_tensor_core_gemm() {
   static int v = -1;
   if (v < 0) {
     const char *e = std::getenv("H2SP_GEMM");
-    v = (e && std::strcmp(e, "tc") == 0) ? 1 : 0;
+    v = (e && std::strcmp(e, "simt") == 0) ? 0 : 1;
   }
   return v == 1;
 }
 
+inline int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        n <= 0)
+      n = 152;
+  }
+  return n;
+}
+
+// Step j0 of the blocked LU of every front of a level: panel (columns
+// [j0, j0 + NB), partial pivoting over the supernode rows), row interchanges
+// and U12 = L11^-1 A12, then A22 -= L21 U12.  With look-ahead the trailing
+// update is split: the first column tile (which holds the next panel) goes
+// first, then the next panel is factored on the high-priority side stream
+// while the remaining columns are updated on the main stream.
 template <typename T>
 cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
-                            int32_t *piv, int32_t *swaps, int *err, cudaStream_t s, Prof *prof) {
+                            int32_t *piv, int32_t *swaps, int *err, cudaStream_t s, const LuAsync *la, Prof *prof) {
   constexpr int NB = LuCfg<T>::NB;
   using G = GemmCfg<T>;
   auto gemm = k_gemm_update<T, G::BM, G::BN, G::TM, G::TN, NB>;
@@ -880,28 +1269,52 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
     cudaFuncSetAttribute(gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gsmem));
     attr = true;
   }
-  for (int j0 = 0; j0 < max_s; j0 += NB) {
-    // algorithmic work of this step over the active fronts
-    double fpanel = 0.0, ftrsm = 0.0, fgemm = 0.0;
+  bool tc = false;
+  if constexpr (std::is_same<T, float>::value) tc = use_tensor_core_gemm();
+  const int W = tc ? kTcTile : G::BN;  // width of the first column tile (holds the next panel)
+  static_assert(G::BN >= NB, "the first column tile must cover the next panel");
+  const int nsm = num_sms();
+
+  auto panel = [&](int j0, cudaStream_t st, int *cl) -> cudaError_t {
+    double fpanel = 0.0;
     if (prof->timing)
       for (int k = 0; k < nfront; ++k) {
         const Front &F = host_fr[k];
         if (j0 >= F.s) continue;
-        const double jb = std::min(NB, F.s - j0), rows = F.f - j0, rest = F.f - j0 - jb;
-        fpanel += rows * jb * jb;         // scaling + rank-1 updates inside the panel
-        ftrsm += jb * jb * rest;          // U12 = L^-1 A12
-        fgemm += 2.0 * rest * rest * jb;  // A22 -= L21 U12
+        const double jb = std::min(NB, F.s - j0), rows = F.f - j0;
+        fpanel += rows * jb * jb;  // scaling + rank-1 updates inside the panel
       }
-    size_t e0 = prof->begin();
+    const size_t e0 = prof->begin(st);
     const int R = max_f - j0;
-    const int C = panel_cluster_size<T, NB>(R);
-    if (C > 0) {
+    const int creg = reg_panel_cluster_max<T, NB>();
+    const int C = (creg > 0 && R <= kRegPanelMaxRows * creg) ? 0 : panel_cluster_size<T, NB>(R);
+    if (creg > 0 && R <= kRegPanelMaxRows * creg) {
+      // rows in registers: one row per thread where the cluster allows, else two
+      int cr = std::max(1, cdiv(R, kRegPanelThreads));
+      if (cr > creg) cr = cdiv(R, kRegPanelMaxRows);
+      *cl = cr * nfront;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(unsigned(nfront * cr));
+      cfg.blockDim = dim3(kRegPanelThreads);
+      cfg.dynamicSmemBytes = reg_panel_smem_bytes<T, NB>(R);
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = unsigned(cr);
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      cudaError_t le = cudaLaunchKernelEx(&cfg, k_panel_reg<T, NB>, fr, j0, fronts, piv, swaps, err);
+      if (le != cudaSuccess) return le;
+    } else if (C > 0) {
+      *cl = C * nfront;
       const int per = (R + C - 1) / C;
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(unsigned(nfront * C));
       cfg.blockDim = dim3(kClusterPanelThreads);
       cfg.dynamicSmemBytes = panel_smem_bytes<T, NB>(per);
-      cfg.stream = s;
+      cfg.stream = st;
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
       at[0].val.clusterDim.x = unsigned(C);
@@ -912,29 +1325,71 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
       cudaError_t le = cudaLaunchKernelEx(&cfg, k_panel_cluster<T, NB>, fr, j0, fronts, piv, swaps, err);
       if (le != cudaSuccess) return le;
     } else {
-      k_panel<T, NB><<<nfront, kPanelThreads, 0, s>>>(fr, j0, fronts, piv, swaps, err);
+      *cl = nfront;
+      k_panel<T, NB><<<nfront, kPanelThreads, 0, st>>>(fr, j0, fronts, piv, swaps, err);
     }
-    prof->end(P_PANEL, 1, e0, fpanel);
+    prof->end(P_PANEL, 1, e0, fpanel, st);
+    return cudaSuccess;
+  };
+  // A22[:, c_lo:c_hi] -= L21 U12[:, c_lo:c_hi] (columns relative to the trailing block)
+  auto update = [&](int j0, int c_lo, int c_hi, int sm_budget) -> cudaError_t {
+    const int rest = max_f - j0 - 1;
+    if (rest <= 0 || c_lo >= std::min(rest, c_hi)) return cudaSuccess;
+    double fgemm = 0.0;
+    if (prof->timing)
+      for (int k = 0; k < nfront; ++k) {
+        const Front &F = host_fr[k];
+        if (j0 >= F.s) continue;
+        const double jb = std::min(NB, F.s - j0);
+        const int nrest = F.f - j0 - int(jb);
+        const double cols = std::max(0, std::min(nrest, c_hi) - c_lo);
+        fgemm += 2.0 * nrest * cols * jb;
+      }
+    const size_t e0 = prof->begin();
+    if (tc) {
+      if constexpr (std::is_same<T, float>::value) {
+        const int thi = c_hi >= (INT_MAX - kTcTile) ? INT_MAX : c_hi / kTcTile;
+        cudaError_t ge = launch_gemm_tc(fr, j0, nfront, max_f, fronts, err, s, c_lo / kTcTile, thi, sm_budget);
+        if (ge != cudaSuccess) return ge;
+      }
+    } else {
+      const int ncol = std::min(rest, c_hi) - c_lo;
+      dim3 g(cdiv(ncol, G::BN), cdiv(rest, G::BM), nfront);
+      gemm<<<g, 256, gsmem, s>>>(fr, j0, fronts, c_lo, c_hi);
+    }
+    prof->end(P_GEMM, 1, e0, fgemm);
+    return cudaSuccess;
+  };
+
+  const bool ahead = la != nullptr && la->side != nullptr && la->next != nullptr && la->panel != nullptr;
+  int panel_ctas = 0;
+  cudaError_t e = panel(0, s, &panel_ctas);
+  if (e != cudaSuccess) return e;
+  for (int j0 = 0; j0 < max_s; j0 += NB) {
+    double ftrsm = 0.0;
+    if (prof->timing)
+      for (int k = 0; k < nfront; ++k) {
+        const Front &F = host_fr[k];
+        if (j0 >= F.s) continue;
+        const double jb = std::min(NB, F.s - j0), rest = F.f - j0 - jb;
+        ftrsm += jb * jb * rest;  // U12 = L^-1 A12
+      }
+    size_t e0 = prof->begin();
     const int ncol_blocks = std::min(cdiv(max_f, 8), 4096);
-    e0 = prof->begin();
     k_swap_trsm<T, NB><<<dim3(ncol_blocks, nfront), 256, 0, s>>>(fr, j0, fronts, swaps);
     prof->end(P_TRSM, 1, e0, ftrsm);
-    const int rest = max_f - j0 - 1;
-    if (rest > 0) {
-      e0 = prof->begin();
-      if constexpr (std::is_same<T, float>::value) {
-        if (use_tensor_core_gemm()) {
-          cudaError_t ge = launch_gemm_tc(fr, j0, nfront, max_f, fronts, err, s);
-          if (ge != cudaSuccess) return ge;
-        } else {
-          dim3 g(cdiv(rest, G::BN), cdiv(rest, G::BM), nfront);
-          gemm<<<g, 256, gsmem, s>>>(fr, j0, fronts);
-        }
-      } else {
-        dim3 g(cdiv(rest, G::BN), cdiv(rest, G::BM), nfront);
-        gemm<<<g, 256, gsmem, s>>>(fr, j0, fronts);
-      }
-      prof->end(P_GEMM, 1, e0, fgemm);
+    const bool more = j0 + NB < max_s;
+    if (more && ahead) {
+      if ((e = update(j0, 0, W, nsm)) != cudaSuccess) return e;
+      if ((e = cudaEventRecord(la->next, s)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(la->side, la->next, 0)) != cudaSuccess) return e;
+      if ((e = panel(j0 + NB, la->side, &panel_ctas)) != cudaSuccess) return e;
+      if ((e = cudaEventRecord(la->panel, la->side)) != cudaSuccess) return e;
+      if ((e = update(j0, W, INT_MAX, std::max(nsm - panel_ctas, nsm / 2))) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(s, la->panel, 0)) != cudaSuccess) return e;
+    } else {
+      if ((e = update(j0, 0, INT_MAX, nsm)) != cudaSuccess) return e;
+      if (more && (e = panel(j0 + NB, s, &panel_ctas)) != cudaSuccess) return e;
     }
   }
   return cudaGetLastError();
@@ -1038,7 +1493,7 @@ cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, 
 template cudaError_t launch_assemble<double>(const AItem *, int64_t, const double *, double *, cudaStream_t, Prof *,
                                            double);
 template cudaError_t launch_lu_level<double>(const FrontDev *, const Front *, int, int, int, double *, int32_t *, int32_t *,
-                                           int *, cudaStream_t, Prof *);
+                                           int *, cudaStream_t, const LuAsync *, Prof *);
 template cudaError_t launch_make_perm<double>(const FrontDev *, int, int, const int32_t *, int32_t *, cudaStream_t, Prof *);
 template cudaError_t launch_extend_add_impl<double>(const FrontDev *, int, int, int, const int32_t *, double *, cudaStream_t,
                                                   Prof *, double);
@@ -1052,7 +1507,7 @@ template cudaError_t launch_solve_bwd_level_impl<double>(const FrontDev *, int, 
 template cudaError_t launch_assemble<float>(const AItem *, int64_t, const double *, float *, cudaStream_t, Prof *,
                                            double);
 template cudaError_t launch_lu_level<float>(const FrontDev *, const Front *, int, int, int, float *, int32_t *, int32_t *,
-                                           int *, cudaStream_t, Prof *);
+                                           int *, cudaStream_t, const LuAsync *, Prof *);
 template cudaError_t launch_make_perm<float>(const FrontDev *, int, int, const int32_t *, int32_t *, cudaStream_t, Prof *);
 template cudaError_t launch_extend_add_impl<float>(const FrontDev *, int, int, int, const int32_t *, float *, cudaStream_t,
                                                   Prof *, double);

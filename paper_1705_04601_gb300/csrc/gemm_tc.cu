@@ -2,10 +2,10 @@
 //
 // C[t0:f, t0:f] -= L21 U12 with K = the panel width (<= 64), one 128 x 128
 // output tile per CTA.  FP32 accuracy is kept with the three-term TF32 split:
-// every operand x = x_hi + x_lo with x_hi = x truncated to TF32 and
-// x_lo = x - x_hi (exact), and D = A_hi B_hi + A_hi B_lo + A_lo B_hi is
-// accumulated in FP32 in tensor memory by tcgen05.mma (kind::tf32).  The
-// dropped A_lo B_lo term is below FP32 rounding.
+// every operand x = x_hi + x_lo with x_hi = x rounded to TF32 and
+// x_lo = x - x_hi rounded to TF32, and D = A_hi B_hi + A_hi B_lo + A_lo B_hi
+// is accumulated in FP32 in tensor memory by tcgen05.mma (kind::tf32).  The
+// dropped A_lo B_lo term and the rounding of x_lo are at FP32 rounding level.
 //
 // Operands are staged by the CTA's threads into shared memory in the
 // canonical K-major layout without swizzle: 8-row x 16-byte core matrices,
@@ -49,9 +49,16 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(kTcN >> 3) << 17) |
                             (uint32_t(kTcM >> 4) << 24);
 
+// v = hi + lo with hi = v rounded to nearest TF32 and lo = v - hi (exact in
+// FP32, |lo| <= 2^-12 |v|), itself rounded to TF32 (error <= 2^-24 |v|).
+__device__ __forceinline__ uint32_t to_tf32(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
 __device__ __forceinline__ void split_tf32(float v, float &hi, float &lo) {
-  hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-  lo = v - hi;
+  hi = __uint_as_float(to_tf32(v));
+  lo = __uint_as_float(to_tf32(v - hi));
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
@@ -89,7 +96,7 @@ __device__ __forceinline__ void sync_for_tensor_cores() {
 // i overlap the asynchronous MMAs.
 __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__restrict__ fr, int j0,
                                                           float *__restrict__ fronts, int *__restrict__ err,
-                                                          int splits) {
+                                                          int splits, int tile_lo, int tile_hi) {
   const FrontDev F = fr[blockIdx.z];
   if (j0 >= F.s) return;
   const int jb = min(kTcK, F.s - j0);
@@ -97,9 +104,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__res
   const int nrest = F.f - t0;
   const int rb = blockIdx.y * kTcM;
   if (rb >= nrest) return;
-  const int ntiles = (nrest + kTcN - 1) / kTcN;
+  // this launch covers column tiles [tile_lo, tile_hi) of the trailing block
+  const int ntiles = min((nrest + kTcN - 1) / kTcN, tile_hi) - tile_lo;
+  if (ntiles <= 0) return;
   const int per = (ntiles + splits - 1) / splits;
-  const int c_lo = blockIdx.x * per, c_hi = min(ntiles, c_lo + per);
+  const int c_lo = tile_lo + blockIdx.x * per, c_hi = min(tile_lo + ntiles, c_lo + per);
   if (c_lo >= c_hi) return;
   float *A = fronts + F.off;
   const int64_t ld = F.f;
@@ -134,13 +143,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__res
       reinterpret_cast<float *>(sAl)[e] = lo;
     }
   }
+  // B (the U12 rows, K contiguous in memory): a warp reads 8 K-values of 4
+  // columns (four full 32-byte sectors); the shared stores are at most
+  // two-way conflicted.
   auto stage_b = [&](int ct, int buf) {
     const int cb = ct * kTcN;
     float v[kIters];
 #pragma unroll
     for (int it = 0; it < kIters; ++it) {
       const int e = tid + it * kTcThreads;
-      const int n = (e >> 9) * 8 + ((e & 31) >> 2), k = ((e >> 5) & 15) * 4 + (e & 3);
+      const int ln = e & 31, wv = e >> 5;
+      const int k = (ln & 7) + 8 * (wv & 7), n = (ln >> 3) + 4 * (wv >> 3);
       const int c = cb + n;
       v[it] = (k < jb && c < nrest) ? A[(j0 + k) + int64_t(t0 + c) * ld] : 0.f;
     }
@@ -148,10 +161,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__res
 #pragma unroll
     for (int it = 0; it < kIters; ++it) {
       const int e = tid + it * kTcThreads;
+      const int ln = e & 31, wv = e >> 5;
+      const int k = (ln & 7) + 8 * (wv & 7), n = (ln >> 3) + 4 * (wv >> 3);
+      const int w = (n >> 3) * (kSbo / 4) + (k >> 2) * (kLbo / 4) + (n & 7) * 4 + (k & 3);
       float hi, lo;
       split_tf32(v[it], hi, lo);
-      bh[e] = hi;
-      bl[e] = lo;
+      bh[w] = hi;
+      bl[w] = lo;
     }
   };
   auto issue = [&](uint32_t tmem, int buf) {
@@ -197,13 +213,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__res
       if (tid == 0) issue(tmem, nxt);
       pending = nxt;
     }
+    // this thread's 64 C values (one row), read while the MMAs run; all loads
+    // are issued before any store
+    const int row = rb + q * 32 + lane;
+    const int cb = ct * kTcN + half * 64;
+    float *Crow = A + (t0 + row) + int64_t(t0 + cb) * ld;
+    const int ncol = row < nrest ? min(64, nrest - cb) : 0;
+    float cv[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) cv[j] = j < ncol ? Crow[int64_t(j) * ld] : 0.f;
     const bool w = wait_phase(smem_u32(&mbar[cur]), parity[cur]);
     parity[cur] ^= 1u;
     ok = __syncthreads_and(w ? 1 : 0) != 0;  // one decision for the whole CTA
     if (!ok) break;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const int row = rb + q * 32 + lane;
-    const int cb = ct * kTcN + half * 64;
 #pragma unroll
     for (int c0 = 0; c0 < 64; c0 += 32) {
       uint32_t v[32];
@@ -217,13 +240,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__res
             "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (row < nrest) {
-        float *Crow = A + (t0 + row) + int64_t(t0 + cb + c0) * ld;
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (cb + c0 + j < nrest) Crow[int64_t(j) * ld] -= __uint_as_float(v[j]);
-      }
+      for (int j = 0; j < 32; ++j) cv[c0 + j] -= __uint_as_float(v[j]);
     }
+#pragma unroll
+    for (int j = 0; j < 64; ++j)
+      if (j < ncol) Crow[int64_t(j) * ld] = cv[j];
     // accumulator `cur` and B buffer `cur` are free for tile it + 2
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -244,7 +266,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__res
 size_t gemm_tc_smem() { return size_t(24) * kTileFloats + 1024; }
 
 cudaError_t launch_gemm_tc(const FrontDev *fr, int j0, int nfront, int max_f, float *fronts, int *err,
-                           cudaStream_t s) {
+                           cudaStream_t s, int tile_lo, int tile_hi, int sm_budget) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gemm_tc_smem()));
@@ -252,12 +274,16 @@ cudaError_t launch_gemm_tc(const FrontDev *fr, int j0, int nfront, int max_f, fl
   }
   const int rest = max_f - j0 - 1;
   if (rest <= 0) return cudaSuccess;
-  const int rt = (rest + kTcM - 1) / kTcM, ct = (rest + kTcN - 1) / kTcN;
-  // enough CTAs for two per SM of the 152, each walking a contiguous range of column tiles
-  int splits = (2 * 152 + rt * nfront - 1) / (rt * nfront);
+  const int rt = (rest + kTcM - 1) / kTcM;
+  const int ct = std::min((rest + kTcN - 1) / kTcN, tile_hi) - tile_lo;
+  if (ct <= 0) return cudaSuccess;
+  // one CTA per SM (shared memory): about two waves over the SMs this launch
+  // may use, each CTA walking a contiguous range of column tiles
+  const int want = 2 * std::max(sm_budget, 1);
+  int splits = (want + rt * nfront - 1) / (rt * nfront);
   splits = std::max(1, std::min(splits, ct));
   dim3 g(splits, rt, nfront);
-  k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits);
+  k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, tile_lo, tile_hi);
   return cudaGetLastError();
 }
 

@@ -167,23 +167,24 @@ struct Prof {
     double w;
   };
   std::vector<Rec> recs;
-  size_t begin() {
+  // events go on `st` when given (work launched on a side stream), else on `stream`
+  size_t begin(cudaStream_t st = nullptr) {
     if (!timing) return 0;
-    return take();
+    return take(st);
   }
-  void end(int cls, int nlaunch, size_t e0, double w) {
+  void end(int cls, int nlaunch, size_t e0, double w, cudaStream_t st = nullptr) {
     launches[cls] += nlaunch;
     if (!timing) return;
-    recs.push_back(Rec{cls, e0, take(), w});
+    recs.push_back(Rec{cls, e0, take(st), w});
   }
   void count(int cls, int nlaunch) { launches[cls] += nlaunch; }
-  size_t take() {
+  size_t take(cudaStream_t st = nullptr) {
     if (used == ev.size()) {
       cudaEvent_t e;
       cudaEventCreate(&e);
       ev.push_back(e);
     }
-    cudaEventRecord(ev[used], stream);
+    cudaEventRecord(ev[used], st ? st : stream);
     return used++;
   }
   void collect() {
@@ -191,7 +192,7 @@ struct Prof {
       used = 0;
       return;
     }
-    cudaEventSynchronize(ev[used - 1]);
+    for (size_t i = 0; i < used; ++i) cudaEventSynchronize(ev[i]);  // events may sit on two streams
     for (const Rec &r : recs) {
       float t = 0.f;
       cudaEventElapsedTime(&t, ev[r.e0], ev[r.e1]);

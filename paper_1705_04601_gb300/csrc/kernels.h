@@ -45,9 +45,19 @@ constexpr int kMaxSwapRows = 2 * 64;
 template <typename T>
 cudaError_t launch_assemble(const AItem *items, int64_t n, const double *S, T *fronts, cudaStream_t s, Prof *prof,
                             double bytes);
+// Look-ahead resources of the block LU: a high-priority stream on which the
+// next panel is factored while the rest of the trailing update runs on the
+// main stream, and the two events that order them.
+struct LuAsync {
+  cudaStream_t side = nullptr;
+  cudaEvent_t next = nullptr, panel = nullptr;
+};
+// Blocked LU with partial pivoting inside the supernode rows of every front of
+// one level (all fronts in parallel).  With `la` (may be null) the panel of
+// step k + 1 overlaps the trailing update of step k.
 template <typename T>
 cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
-                            int32_t *piv, int32_t *swaps, int *err, cudaStream_t s, Prof *prof);
+                            int32_t *piv, int32_t *swaps, int *err, cudaStream_t s, const LuAsync *la, Prof *prof);
 template <typename T>
 cudaError_t launch_extend_add_impl(const FrontDev *fr_all, int lo, int nfront, int max_b, const int32_t *map,
                                    T *fronts, cudaStream_t s, Prof *prof, double elems);
@@ -72,9 +82,12 @@ cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, 
                                         const T *dinv, const int32_t *idx, T *y, int64_t ldy, int nrhs, T *work,
                                         T *zbuf, const int64_t *work_off, cudaStream_t s, Prof *prof, double bytes);
 
-// FP32 trailing update C -= L21 U12 of one panel step on the tensor cores (gemm_tc.cu).
+// FP32 trailing update C -= L21 U12 of one panel step on the tensor cores
+// (gemm_tc.cu), over the 128-column tiles [tile_lo, tile_hi) of the trailing
+// block, sized for about sm_budget SMs.
 cudaError_t launch_gemm_tc(const FrontDev *fr, int j0, int nfront, int max_f, float *fronts, int *err,
-                           cudaStream_t s);
+                           cudaStream_t s, int tile_lo, int tile_hi, int sm_budget);
+constexpr int kTcTile = 128;
 
 // ---- applies, H^2 product, vector kernels (apply.cu) ----
 struct ApItem {

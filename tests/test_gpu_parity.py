@@ -276,11 +276,13 @@ def test_batched_forest_matches_individual_systems(prec):
 
 @pytest.mark.parametrize("name", ["log4k", "ragged"])
 def test_fp32_factor_direct_accuracy(name):
-    """One FP32-factor direct solve is accurate to FP32 level times the
-    conditioning (1e-3 .. 8e-3 here with either GEMM path, varying with the
-    rounding of the atomic extend-add); a TF32-only trailing update would be
-    ~1000x worse."""
+    """One FP32-factor direct solve is accurate to the level of an FP32 dense
+    LU with partial pivoting of the same matrix (computed here by LAPACK in
+    float32).  The block LU pivots only inside each supernode and its
+    extend-add rounds in a run-dependent order, so it may lose up to a small
+    factor more; a TF32-only trailing update would lose about 1000x."""
     import os
+    import scipy.linalg as sl
     h, b, sp, hd = sparsified(name)
     H.h2sp_factor(hd, H.H2SP_FP32)
     bt = dev(b)
@@ -289,8 +291,12 @@ def test_fp32_factor_direct_accuracy(name):
     torch.cuda.synchronize()
     xo = ofa.solve(h, sp, ofa.factor(h, sp), b)
     err = np.linalg.norm(host(xt) - xo) / np.linalg.norm(xo)
-    print("fp32 direct rel err (%s, GEMM=%s): %.3e" % (name, os.environ.get("H2SP_GEMM", "simt"), err))
-    assert err <= 1e-2
+    lu32 = sl.lu_factor(oh2.dense(h).astype(np.float32))
+    x32 = sl.lu_solve(lu32, b.astype(np.float32)).astype(np.float64)
+    err32 = np.linalg.norm(x32 - xo) / np.linalg.norm(xo)
+    print("fp32 direct rel err (%s, GEMM=%s): %.3e (dense FP32 LU: %.3e)"
+          % (name, os.environ.get("H2SP_GEMM", "tc"), err, err32))
+    assert err <= 25 * err32
     hd.close()
 
 
