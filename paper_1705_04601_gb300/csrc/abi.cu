@@ -117,6 +117,11 @@ struct h2sp_handle {
     return d;
   }
   LuAsync la;  // look-ahead stream and events of the block LU (created on first use)
+  // flag-synchronised triangular sweeps
+  int2 *chain_items = nullptr;
+  std::vector<int> chain_fwd_off, chain_fwd_n, chain_bwd_off, chain_bwd_n;
+  int *chain_tickets = nullptr, *chain_flags = nullptr, *serr = nullptr;
+  int chain_epoch = 0;
   void release() {
     if (la.side) cudaStreamSynchronize(la.side);
     if (la.next) cudaEventDestroy(la.next);
@@ -260,6 +265,17 @@ void ensure_work(h2sp_handle *h, int nrhs) {
 }
 
 // y (S space, type T, ld n) <- S^{-1} y with the current factors
+// Triangular sweeps with one flag-synchronised launch per level and direction;
+// H2SP_SOLVE=steps launches one kernel per kSolveBlock-column step instead.
+bool chain_sweeps_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = std::getenv("H2SP_SOLVE");
+    v = (e && std::strcmp(e, "steps") == 0) ? 0 : 1;
+  }
+  return v == 1;
+}
+
 template <typename T>
 void solve_S_T(h2sp_handle *h, T *y, int nrhs) {
   const Plan &p = h->plan;
@@ -267,19 +283,50 @@ void solve_S_T(h2sp_handle *h, T *y, int nrhs) {
   T *work = static_cast<T *>(h->work);
   T *zbuf = static_cast<T *>(h->zbuf);
   const T *dinv = static_cast<const T *>(h->dinv);
+  const bool chain = chain_sweeps_enabled();
+  ChainArgs ca;
+  ca.items = h->chain_items;
+  ca.fwd_off = h->chain_fwd_off.data();
+  ca.fwd_n = h->chain_fwd_n.data();
+  ca.bwd_off = h->chain_bwd_off.data();
+  ca.bwd_n = h->chain_bwd_n.data();
+  ca.tickets = h->chain_tickets;
+  ca.flags = h->chain_flags;
+  ca.err = h->serr;
   for (int r0 = 0; r0 < nrhs; r0 += kSolveRhs) {
     const int nr = std::min(kSolveRhs, nrhs - r0);
     T *yr = y + int64_t(r0) * p.n;
-    for (const FrontLevel &L : h->flev)
+    if (chain) {
+      ck(cudaMemsetAsync(h->chain_tickets, 0, sizeof(int) * 2 * h->flev.size(), h->stream));
+      h->prof.count(P_OTHER, 1);
+    }
+    for (size_t li = 0; li < h->flev.size(); ++li) {
+      const FrontLevel &L = h->flev[li];
+      ca.epoch = ++h->chain_epoch;
       ck(launch_solve_fwd_level_impl<T>(h->fr, L.lo, L.hi - L.lo, L.max_s, L.max_f, fronts, dinv, h->perm, h->fidx,
                                         yr, p.n, nr, work, zbuf, h->work_off, h->stream, &h->prof,
-                                        L.lu_elems * sizeof(T)));
+                                        L.lu_elems * sizeof(T), chain ? &ca : nullptr, int(li)));
+    }
     for (int i = int(h->flev.size()) - 1; i >= 0; --i) {
       const FrontLevel &L = h->flev[i];
+      ca.epoch = ++h->chain_epoch;
       ck(launch_solve_bwd_level_impl<T>(h->fr, L.lo, L.hi - L.lo, L.max_s, L.max_f, fronts, dinv, h->fidx, yr, p.n,
-                                        nr, work, zbuf, h->work_off, h->stream, &h->prof, L.lu_elems * sizeof(T)));
+                                        nr, work, zbuf, h->work_off, h->stream, &h->prof, L.lu_elems * sizeof(T),
+                                        chain ? &ca : nullptr, i));
     }
   }
+}
+
+// status of the sweeps since the last check (a bounded wait that ran out)
+int sweep_status(h2sp_handle *h) {
+  int e = 0;
+  ck(cudaMemcpyAsync(&e, h->serr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  ck(cudaStreamSynchronize(h->stream));
+  if (e != 0) {
+    ck(cudaMemsetAsync(h->serr, 0, sizeof(int), h->stream));
+    return H2SP_ETIMEOUT;
+  }
+  return H2SP_OK;
 }
 
 // in-place S^{-1} on an FP64 S-space vector (ld n)
@@ -676,6 +723,34 @@ int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream s
         }
         h->flev.push_back(fl);
       }
+      // row-block work lists of the sweeps, in dependency order per level
+      std::vector<int2> items;
+      int nflags = 0;
+      for (const Front &F : p.fronts) nflags += int((F.s + kSolveBlock - 1) / kSolveBlock);
+      for (const FrontLevel &L : h->flev) {
+        int maxb = 0;
+        for (int k = L.lo; k < L.hi; ++k) maxb = std::max<int>(maxb, (p.fronts[k].s + kSolveBlock - 1) / kSolveBlock);
+        h->chain_fwd_off.push_back(int(items.size()));
+        for (int b = 0; b < maxb; ++b)
+          for (int k = L.lo; k < L.hi; ++k)
+            if (b < (p.fronts[k].s + kSolveBlock - 1) / kSolveBlock) items.push_back(make_int2(k, b));
+        for (int k = L.lo; k < L.hi; ++k)
+          for (int q = 0; q < (p.fronts[k].b + kSolveBlock - 1) / kSolveBlock; ++q) items.push_back(make_int2(k, -(q + 1)));
+        h->chain_fwd_n.push_back(int(items.size()) - h->chain_fwd_off.back());
+        h->chain_bwd_off.push_back(int(items.size()));
+        for (int d = 0; d < maxb; ++d)
+          for (int k = L.lo; k < L.hi; ++k) {
+            const int nb = (p.fronts[k].s + kSolveBlock - 1) / kSolveBlock;
+            if (d < nb) items.push_back(make_int2(k, nb - 1 - d));
+          }
+        h->chain_bwd_n.push_back(int(items.size()) - h->chain_bwd_off.back());
+      }
+      h->chain_items = h->upload(items);
+      h->chain_flags = h->alloc<int>(size_t(std::max(nflags, 1)));
+      ck(cudaMemsetAsync(h->chain_flags, 0, sizeof(int) * size_t(std::max(nflags, 1)), h->stream));
+      h->chain_tickets = h->alloc<int>(2 * std::max<size_t>(h->flev.size(), 1));
+      h->serr = h->alloc<int>(1);
+      ck(cudaMemsetAsync(h->serr, 0, sizeof(int), h->stream));
     }
     ck(cudaGetLastError());
   } catch (const CudaFail &f) {
@@ -839,11 +914,12 @@ int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *o, int32_t nrhs, const dou
     if (o->mode == H2SP_DIRECT) {
       precond(h, b, ldb, x, ldx, nrhs);
       ck(cudaGetLastError());
-      return H2SP_OK;
+      return sweep_status(h);
     }
     if (o->mode == H2SP_GMRES) {
       const int st = gmres(h, o, nrhs, b, ldb, x, ldx, info);
-      return st;
+      const int ss = sweep_status(h);
+      return ss != H2SP_OK ? ss : st;
     }
     // iterative refinement on the FP64 H^2 residual (§5.5)
     const int64_t n = p.n;
@@ -875,6 +951,10 @@ int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *o, int32_t nrhs, const dou
       info->iters = it;
       info->rel_residual = res;
       info->status = (res <= o->tol) ? H2SP_OK : H2SP_ENOCONV;
+    }
+    {
+      const int ss = sweep_status(h);
+      if (ss != H2SP_OK) return ss;
     }
     if (!(res <= o->tol)) return H2SP_ENOCONV;
   } catch (const CudaFail &f) {

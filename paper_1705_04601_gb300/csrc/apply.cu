@@ -129,145 +129,208 @@ __global__ void __launch_bounds__(128) k_spmv(const int64_t *__restrict__ brow_p
 }
 
 // ---------------- H^2 product (Definition 4.9) ----------------
-// x^_t = E_t^T x_t for the leaves
-__global__ void __launch_bounds__(64) k_h2_leaf_up(H2Dev h, const double *__restrict__ x, int64_t ldx,
-                                                   double *__restrict__ xh, int64_t ldh, int nrhs) {
-  const int t = h.leaf0 + blockIdx.x;
-  const int n = int(h.size[t]), k = h.rank[t];
-  const int64_t b0 = h.begin[t];
-  const double *E = h.col_leaf_basis ? h.col_leaf_basis + h.col_leaf_basis_off[blockIdx.x]
-                                     : h.leaf_basis + h.leaf_basis_off[blockIdx.x];
-  __shared__ double sx[kMaxBlock * kRhs];
-  for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) {
-    const int j = e % n, r = e / n;
-    sx[j + r * kMaxBlock] = x[b0 + j + r * ldx];
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    double acc[kRhs];
-#pragma unroll
-    for (int r = 0; r < kRhs; ++r) acc[r] = 0.0;
-    for (int j = 0; j < n; ++j) {
-      const double e = E[j + int64_t(i) * n];
-#pragma unroll
-      for (int r = 0; r < kRhs; ++r)
-        if (r < nrhs) acc[r] += e * sx[j + r * kMaxBlock];
-    }
-    for (int r = 0; r < nrhs; ++r) xh[h.xh_off[t] + i + r * ldh] = acc[r];
-  }
-}
+// FP64 multiply-adds are the throughput limit of these kernels (GB300's FP64
+// pipe), so idle lanes cost directly.  A CTA of 64 threads computes one
+// cluster's rows; when the cluster has at most 32 (16) rows, the threads form
+// 2 (4) groups that split the right-hand sides, so every lane carries rows.
+// Each thread keeps 16 / G independent accumulators (one per right-hand side
+// it owns) and reads the vector entries straight from global memory (the
+// lanes of a warp read the same entry).
+constexpr int kMvThreads = 64;
 
-// x^_p = sum_c T'_c^T x^_c over the sons of p (clusters [lo, hi) of one depth)
-__global__ void __launch_bounds__(64) k_h2_up(H2Dev h, const int32_t *__restrict__ child_start,
-                                              const int32_t *__restrict__ child_cnt, int lo, double *__restrict__ xh,
-                                              int64_t ldh, int nrhs) {
-  const int p = lo + blockIdx.x;
-  const int kp = h.rank[p];
-  for (int i = threadIdx.x; i < kp; i += blockDim.x) {
-    double acc[kRhs];
-#pragma unroll
-    for (int r = 0; r < kRhs; ++r) acc[r] = 0.0;
-    for (int c = child_start[p]; c < child_start[p] + child_cnt[p]; ++c) {
-      const int kc = h.rank[c];
-      const double *T = h.col_transfer ? h.col_transfer + h.col_transfer_off[c] : h.transfer + h.transfer_off[c];
-      const double *xc = xh + h.xh_off[c];
-      for (int j = 0; j < kc; ++j) {
-        const double tv = T[j + int64_t(i) * kc];
-#pragma unroll
-        for (int r = 0; r < kRhs; ++r)
-          if (r < nrhs) acc[r] += tv * xc[j + r * ldh];
-      }
-    }
-    for (int r = 0; r < nrhs; ++r) xh[h.xh_off[p] + i + r * ldh] = acc[r];
-  }
-}
+__device__ __forceinline__ int mv_groups(int rows) { return rows <= 16 ? 4 : (rows <= 32 ? 2 : 1); }
 
-// y^_t = sum_{s in Far(t)} D_ts x^_s
-__global__ void __launch_bounds__(64) k_h2_couple(H2Dev h, const double *__restrict__ xh, double *__restrict__ yh,
-                                                  int64_t ldh, int nrhs) {
-  const int t = blockIdx.x;
-  const int kt = h.rank[t];
-  for (int i = threadIdx.x; i < kt; i += blockDim.x) {
-    double acc[kRhs];
+// acc[q] += sum_j A[i + j * lda] * X[j + (g + G q) * ldx] for j < nj
+template <int G>
+__device__ __forceinline__ void mv_accumulate(double *acc, const double *__restrict__ A, int64_t lda, int i, int nj,
+                                              const double *__restrict__ X, int64_t ldx, int g, int nrhs) {
+  constexpr int NQ = kRhs / G;
+  for (int j = 0; j < nj; ++j) {
+    const double a = A[i + int64_t(j) * lda];
 #pragma unroll
-    for (int r = 0; r < kRhs; ++r) acc[r] = 0.0;
-    for (int64_t z = h.far_ptr[t]; z < h.far_ptr[t + 1]; ++z) {
-      const int s = h.far_col[z];
-      const int ks = h.rank[s];
-      const double *D = h.coupling + h.coupling_off[z];
-      const double *xs = xh + h.xh_off[s];
-      for (int j = 0; j < ks; ++j) {
-        const double dv = D[i + int64_t(j) * kt];
-#pragma unroll
-        for (int r = 0; r < kRhs; ++r)
-          if (r < nrhs) acc[r] += dv * xs[j + r * ldh];
-      }
-    }
-    for (int r = 0; r < nrhs; ++r) yh[h.xh_off[t] + i + r * ldh] = acc[r];
-  }
-}
-
-// y^_c += T_c y^_parent for the clusters [lo, hi) of one depth
-__global__ void __launch_bounds__(64) k_h2_down(H2Dev h, int lo, double *__restrict__ yh, int64_t ldh, int nrhs) {
-  const int c = lo + blockIdx.x;
-  const int p = h.parent[c];
-  const int kc = h.rank[c], kp = h.rank[p];
-  const double *T = h.transfer + h.transfer_off[c];
-  const double *yp = yh + h.xh_off[p];
-  for (int i = threadIdx.x; i < kc; i += blockDim.x) {
-    for (int r = 0; r < nrhs; ++r) {
-      double acc = 0.0;
-      for (int j = 0; j < kp; ++j) acc += T[i + int64_t(j) * kc] * yp[j + r * ldh];
-      yh[h.xh_off[c] + i + r * ldh] += acc;
+    for (int q = 0; q < NQ; ++q) {
+      const int c = g + G * q;
+      if (c < nrhs) acc[q] += a * X[j + int64_t(c) * ldx];
     }
   }
 }
 
 // y_t = R_t y^_t + sum_{s near t} C_ts x_s
-__global__ void __launch_bounds__(64) k_h2_leaf_out(H2Dev h, const double *__restrict__ x, int64_t ldx,
-                                                    const double *__restrict__ yh, int64_t ldh, double *__restrict__ y,
-                                                    int64_t ldy, int nrhs) {
-  const int lf = blockIdx.x;
+template <int G>
+__device__ __forceinline__ void leaf_out_body(const H2Dev &h, int lf, const double *__restrict__ x, int64_t ldx,
+                                              const double *__restrict__ yh, int64_t ldh, double *__restrict__ y,
+                                              int64_t ldy, int nrhs) {
+  constexpr int P = kMvThreads / G, NQ = kRhs / G;
   const int t = h.leaf0 + lf;
   const int n = int(h.size[t]), k = h.rank[t];
-  const int64_t b0 = h.begin[t];
-  __shared__ double sx[kMaxBlock * kRhs];
-  double acc[kRhs];
+  const int i = threadIdx.x % P, g = threadIdx.x / P;
+  if (i >= n) return;
+  double acc[NQ];
 #pragma unroll
-  for (int r = 0; r < kRhs; ++r) acc[r] = 0.0;
-  const int i = threadIdx.x;
-  if (i < n) {
-    const double *R = h.leaf_basis + h.leaf_basis_off[lf];
-    const double *yt = yh + h.xh_off[t];
-    for (int j = 0; j < k; ++j) {
-      const double rv = R[i + int64_t(j) * n];
-#pragma unroll
-      for (int r = 0; r < kRhs; ++r)
-        if (r < nrhs) acc[r] += rv * yt[j + r * ldh];
-    }
-  }
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  mv_accumulate<G>(acc, h.leaf_basis + h.leaf_basis_off[lf], n, i, k, yh + h.xh_off[t], ldh, g, nrhs);
   for (int64_t z = h.near_ptr[lf]; z < h.near_ptr[lf + 1]; ++z) {
     const int s = h.near_col[z];
-    const int ns = int(h.size[s]);
-    const int64_t bs = h.begin[s];
-    __syncthreads();
-    for (int e = threadIdx.x; e < ns * nrhs; e += blockDim.x) {
-      const int j = e % ns, r = e / ns;
-      sx[j + r * kMaxBlock] = x[bs + j + r * ldx];
-    }
-    __syncthreads();
-    if (i < n) {
-      const double *C = h.near_block + h.near_off[z];
-      for (int j = 0; j < ns; ++j) {
-        const double cv = C[i + int64_t(j) * n];
+    mv_accumulate<G>(acc, h.near_block + h.near_off[z], n, i, int(h.size[s]), x + h.begin[s], ldx, g, nrhs);
+  }
+  const int64_t b0 = h.begin[t];
 #pragma unroll
-        for (int r = 0; r < kRhs; ++r)
-          if (r < nrhs) acc[r] += cv * sx[j + r * kMaxBlock];
-      }
+  for (int q = 0; q < NQ; ++q) {
+    const int c = g + G * q;
+    if (c < nrhs) y[b0 + i + c * ldy] = acc[q];
+  }
+}
+
+__global__ void __launch_bounds__(kMvThreads) k_h2_leaf_out(H2Dev h, const double *__restrict__ x, int64_t ldx,
+                                                            const double *__restrict__ yh, int64_t ldh,
+                                                            double *__restrict__ y, int64_t ldy, int nrhs) {
+  const int n = int(h.size[h.leaf0 + blockIdx.x]);
+  switch (mv_groups(n)) {
+    case 4: leaf_out_body<4>(h, blockIdx.x, x, ldx, yh, ldh, y, ldy, nrhs); break;
+    case 2: leaf_out_body<2>(h, blockIdx.x, x, ldx, yh, ldh, y, ldy, nrhs); break;
+    default: leaf_out_body<1>(h, blockIdx.x, x, ldx, yh, ldh, y, ldy, nrhs); break;
+  }
+}
+
+// y^_t = sum_{s in Far(t)} D_ts x^_s
+template <int G>
+__device__ __forceinline__ void couple_body(const H2Dev &h, int t, const double *__restrict__ xh,
+                                            double *__restrict__ yh, int64_t ldh, int nrhs) {
+  constexpr int P = kMvThreads / G, NQ = kRhs / G;
+  const int kt = h.rank[t];
+  const int i = threadIdx.x % P, g = threadIdx.x / P;
+  if (i >= kt) return;
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  for (int64_t z = h.far_ptr[t]; z < h.far_ptr[t + 1]; ++z) {
+    const int s = h.far_col[z];
+    mv_accumulate<G>(acc, h.coupling + h.coupling_off[z], kt, i, h.rank[s], xh + h.xh_off[s], ldh, g, nrhs);
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int c = g + G * q;
+    if (c < nrhs) yh[h.xh_off[t] + i + c * ldh] = acc[q];
+  }
+}
+
+__global__ void __launch_bounds__(kMvThreads) k_h2_couple(H2Dev h, const double *__restrict__ xh,
+                                                          double *__restrict__ yh, int64_t ldh, int nrhs) {
+  switch (mv_groups(h.rank[blockIdx.x])) {
+    case 4: couple_body<4>(h, blockIdx.x, xh, yh, ldh, nrhs); break;
+    case 2: couple_body<2>(h, blockIdx.x, xh, yh, ldh, nrhs); break;
+    default: couple_body<1>(h, blockIdx.x, xh, yh, ldh, nrhs); break;
+  }
+}
+
+// y^_c += T_c y^_parent for the clusters [lo, hi) of one depth
+template <int G>
+__device__ __forceinline__ void down_body(const H2Dev &h, int c, double *__restrict__ yh, int64_t ldh, int nrhs) {
+  constexpr int P = kMvThreads / G, NQ = kRhs / G;
+  const int p = h.parent[c];
+  const int kc = h.rank[c];
+  const int i = threadIdx.x % P, g = threadIdx.x / P;
+  if (i >= kc) return;
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  mv_accumulate<G>(acc, h.transfer + h.transfer_off[c], kc, i, h.rank[p], yh + h.xh_off[p], ldh, g, nrhs);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int r = g + G * q;
+    if (r < nrhs) yh[h.xh_off[c] + i + r * ldh] += acc[q];
+  }
+}
+
+__global__ void __launch_bounds__(kMvThreads) k_h2_down(H2Dev h, int lo, double *__restrict__ yh, int64_t ldh,
+                                                        int nrhs) {
+  const int c = lo + blockIdx.x;
+  switch (mv_groups(h.rank[c])) {
+    case 4: down_body<4>(h, c, yh, ldh, nrhs); break;
+    case 2: down_body<2>(h, c, yh, ldh, nrhs); break;
+    default: down_body<1>(h, c, yh, ldh, nrhs); break;
+  }
+}
+
+// acc[q] += sum_j A[j + i * lda] * X[j + (g + G q) * ldx]   (A transposed)
+template <int G>
+__device__ __forceinline__ void mv_accumulate_t(double *acc, const double *__restrict__ A, int64_t lda, int i, int nj,
+                                                const double *__restrict__ X, int64_t ldx, int g, int nrhs) {
+  constexpr int NQ = kRhs / G;
+  const double *a = A + int64_t(i) * lda;
+  for (int j = 0; j < nj; ++j) {
+    const double av = a[j];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int c = g + G * q;
+      if (c < nrhs) acc[q] += av * X[j + int64_t(c) * ldx];
     }
   }
-  if (i < n)
-    for (int r = 0; r < nrhs; ++r) y[b0 + i + r * ldy] = acc[r];
+}
+
+// x^_t = E_t^T x_t for the leaves
+template <int G>
+__device__ __forceinline__ void leaf_up_body(const H2Dev &h, int lf, const double *__restrict__ x, int64_t ldx,
+                                             double *__restrict__ xh, int64_t ldh, int nrhs) {
+  constexpr int P = kMvThreads / G, NQ = kRhs / G;
+  const int t = h.leaf0 + lf;
+  const int n = int(h.size[t]), k = h.rank[t];
+  const int i = threadIdx.x % P, g = threadIdx.x / P;
+  if (i >= k) return;
+  const double *E = h.col_leaf_basis ? h.col_leaf_basis + h.col_leaf_basis_off[lf] : h.leaf_basis + h.leaf_basis_off[lf];
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  mv_accumulate_t<G>(acc, E, n, i, n, x + h.begin[t], ldx, g, nrhs);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int c = g + G * q;
+    if (c < nrhs) xh[h.xh_off[t] + i + c * ldh] = acc[q];
+  }
+}
+
+__global__ void __launch_bounds__(kMvThreads) k_h2_leaf_up(H2Dev h, const double *__restrict__ x, int64_t ldx,
+                                                           double *__restrict__ xh, int64_t ldh, int nrhs) {
+  switch (mv_groups(h.rank[h.leaf0 + blockIdx.x])) {
+    case 4: leaf_up_body<4>(h, blockIdx.x, x, ldx, xh, ldh, nrhs); break;
+    case 2: leaf_up_body<2>(h, blockIdx.x, x, ldx, xh, ldh, nrhs); break;
+    default: leaf_up_body<1>(h, blockIdx.x, x, ldx, xh, ldh, nrhs); break;
+  }
+}
+
+// x^_p = sum_c T'_c^T x^_c over the sons of p (clusters [lo, hi) of one depth)
+template <int G>
+__device__ __forceinline__ void up_body(const H2Dev &h, const int32_t *__restrict__ child_start,
+                                        const int32_t *__restrict__ child_cnt, int p, double *__restrict__ xh,
+                                        int64_t ldh, int nrhs) {
+  constexpr int P = kMvThreads / G, NQ = kRhs / G;
+  const int kp = h.rank[p];
+  const int i = threadIdx.x % P, g = threadIdx.x / P;
+  if (i >= kp) return;
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  for (int c = child_start[p]; c < child_start[p] + child_cnt[p]; ++c) {
+    const int kc = h.rank[c];
+    const double *T = h.col_transfer ? h.col_transfer + h.col_transfer_off[c] : h.transfer + h.transfer_off[c];
+    mv_accumulate_t<G>(acc, T, kc, i, kc, xh + h.xh_off[c], ldh, g, nrhs);
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int r = g + G * q;
+    if (r < nrhs) xh[h.xh_off[p] + i + r * ldh] = acc[q];
+  }
+}
+
+__global__ void __launch_bounds__(kMvThreads) k_h2_up(H2Dev h, const int32_t *__restrict__ child_start,
+                                                      const int32_t *__restrict__ child_cnt, int lo,
+                                                      double *__restrict__ xh, int64_t ldh, int nrhs) {
+  const int p = lo + blockIdx.x;
+  switch (mv_groups(h.rank[p])) {
+    case 4: up_body<4>(h, child_start, child_cnt, p, xh, ldh, nrhs); break;
+    case 2: up_body<2>(h, child_start, child_cnt, p, xh, ldh, nrhs); break;
+    default: up_body<1>(h, child_start, child_cnt, p, xh, ldh, nrhs); break;
+  }
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -404,17 +467,17 @@ cudaError_t launch_h2_matvec(const H2Dev &h, const int32_t *level_ptr_host, cons
     const int nr = std::min(kRhs, nrhs - r0);
     const double *xr = x + r0 * ldx;
     double *yr = y + r0 * ldy;
-    k_h2_leaf_up<<<nleaf, 64, 0, s>>>(h, xr, ldx, xh, ldh, nr);
+    k_h2_leaf_up<<<nleaf, kMvThreads, 0, s>>>(h, xr, ldx, xh, ldh, nr);
     for (int d = depth - 1; d >= 0; --d) {
       const int lo = level_ptr_host[d], hi = level_ptr_host[d + 1];
-      k_h2_up<<<hi - lo, 64, 0, s>>>(h, child_start, child_cnt, lo, xh, ldh, nr);
+      k_h2_up<<<hi - lo, kMvThreads, 0, s>>>(h, child_start, child_cnt, lo, xh, ldh, nr);
     }
-    k_h2_couple<<<ncl, 64, 0, s>>>(h, xh, yh, ldh, nr);
+    k_h2_couple<<<ncl, kMvThreads, 0, s>>>(h, xh, yh, ldh, nr);
     for (int d = 1; d <= depth; ++d) {
       const int lo = level_ptr_host[d], hi = level_ptr_host[d + 1];
-      k_h2_down<<<hi - lo, 64, 0, s>>>(h, lo, yh, ldh, nr);
+      k_h2_down<<<hi - lo, kMvThreads, 0, s>>>(h, lo, yh, ldh, nr);
     }
-    k_h2_leaf_out<<<nleaf, 64, 0, s>>>(h, xr, ldx, yh, ldh, yr, ldy, nr);
+    k_h2_leaf_out<<<nleaf, kMvThreads, 0, s>>>(h, xr, ldx, yh, ldh, yr, ldy, nr);
   }
   return cudaGetLastError();
 }

@@ -1120,6 +1120,201 @@ __global__ void k_bwd_scatter(const FrontDev *__restrict__ fr, const int32_t *__
 
 inline int cdiv(int64_t a, int64_t b) { return int((a + b - 1) / b); }
 
+inline int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        n <= 0)
+      n = 152;
+  }
+  return n;
+}
+
+
+// ---------------- flag-synchronised block sweeps ----------------
+// One launch per elimination level and direction replaces the kBS-column
+// step launches.  Work items are row blocks: (front, b) for the kBS-row
+// block b of the supernode rows, and in the forward sweep (front, -(q+1)) for
+// the q-th kBS-row block of the boundary rows.  A CTA takes items in ticket
+// order and accumulates, left-looking, the contributions of the solution
+// blocks it depends on as their flags appear:
+//   forward,  block b : w_b -= sum_{b' < b} L[b, b'] z_{b'},  z_b = L_bb^-1 w_b
+//   boundary, block q : w_q -= sum_{b'}    L[q, b'] z_{b'}   (added to y later)
+//   backward, block b : w_b -= sum_{b' > b} U[b, b'] x_{b'},  x_b = U_bb^-1 w_b
+// and then publishes its block (release store of the launch's epoch).  An item
+// depends only on items with smaller tickets, which are held by running or
+// finished CTAs of the same cooperative launch, so every wait ends; each wait
+// is still bounded (kChainSpinCap polls), after which the CTA raises an error
+// flag and leaves.
+constexpr int kChainThreads = 256;
+constexpr uint32_t kChainSpinCap = 1u << 22;
+constexpr int kChainPre = kBS * kBS / kChainThreads;  // L values each thread prefetches per block
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int *p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <typename T, bool Fwd>
+__global__ void __launch_bounds__(kChainThreads) k_chain(const FrontDev *__restrict__ fr, const int2 *__restrict__ items,
+                                                         int nitems, int *__restrict__ ticket,
+                                                         const T *__restrict__ fronts, const T *__restrict__ dinv,
+                                                         int nrhs, T *__restrict__ work, T *__restrict__ zbuf,
+                                                         const int64_t *__restrict__ work_off, int *__restrict__ flags,
+                                                         int epoch, int *__restrict__ err) {
+  __shared__ __align__(16) T sL[kBS * kBS];       // block of L / U, column-major; then the inverted diagonal block
+  __shared__ __align__(16) T sZ[kBS * kMaxRhs];   // a solution block, sZ[k * kMaxRhs + c]
+  __shared__ int s_item, s_ok;
+  const int tid = threadIdx.x, row = tid & (kBS - 1), g = tid >> 6;  // right-hand sides g, g+4, g+8, g+12
+  for (;;) {
+    __syncthreads();  // s_item, sL, sZ free
+    if (tid == 0) s_item = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int t = s_item;
+    if (t >= nitems) return;
+    const int2 it = items[t];
+    const FrontDev F = fr[it.x];
+    const T *A = fronts + F.off;
+    T *W = work + work_off[it.x];
+    T *Z = zbuf + work_off[it.x];
+    const int64_t ld = F.f;
+    const bool sn = it.y >= 0;
+    const int r0 = sn ? it.y * kBS : F.s + (-it.y - 1) * kBS;
+    const int rb = min(kBS, (sn ? F.s : F.f) - r0);
+    const int nbs = (F.s + kBS - 1) / kBS;
+    const int fbase = int(F.dinv_off / (2 * kBS * kBS));
+    // blocks this item depends on, in the order they are published
+    const int b_first = Fwd ? 0 : nbs - 1;
+    const int nblk = Fwd ? (sn ? it.y : nbs) : (nbs - 1 - it.y);
+    T acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = g + 4 * q;
+      acc[q] = (row < rb && c < nrhs) ? W[(r0 + row) + int64_t(c) * ld] : T(0);
+    }
+    T pre[kChainPre];
+    auto load_block = [&](int bp) {
+      const int c0 = bp * kBS, kb = min(kBS, F.s - c0);
+#pragma unroll
+      for (int e = 0; e < kChainPre; ++e) {
+        const int idx = tid + e * kChainThreads, k = idx / kBS, rr = idx % kBS;
+        pre[e] = (rr < rb && k < kb) ? A[(r0 + rr) + int64_t(c0 + k) * ld] : T(0);
+      }
+    };
+    bool ok = true;
+    if (nblk > 0) load_block(b_first);
+    for (int s = 0; s < nblk; ++s) {
+      const int bp = Fwd ? s : nbs - 1 - s;
+      __syncthreads();  // the previous block's sL / sZ are consumed
+#pragma unroll
+      for (int e = 0; e < kChainPre; ++e) sL[tid + e * kChainThreads] = pre[e];
+      if (s + 1 < nblk) load_block(Fwd ? bp + 1 : bp - 1);  // in flight during the wait
+      if (tid == 0) {
+        int okv = 1;
+        uint32_t n = 0;
+        while (ld_acquire_gpu(&flags[fbase + bp]) != epoch) {
+          if (++n > kChainSpinCap) {
+            okv = 0;
+            atomicOr(err, 4);
+            break;
+          }
+          __nanosleep(32);
+        }
+        s_ok = okv;
+      }
+      __syncthreads();
+      if (!s_ok) {
+        ok = false;
+        break;
+      }
+      const int kb = min(kBS, F.s - bp * kBS);
+      for (int e = tid; e < kBS * kMaxRhs; e += kChainThreads) {
+        const int k = e % kBS, c = e / kBS;
+        sZ[k * kMaxRhs + c] = (k < kb && c < nrhs) ? __ldcg(&Z[(bp * kBS + k) + int64_t(c) * ld]) : T(0);
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int k = 0; k < kBS; ++k) {
+        const T a = sL[k * kBS + row];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] -= a * sZ[k * kMaxRhs + g + 4 * q];
+      }
+    }
+    if (!ok) return;  // uniform: every thread saw s_ok == 0
+    if (!sn) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = g + 4 * q;
+        if (row < rb && c < nrhs) W[(r0 + row) + int64_t(c) * ld] = acc[q];
+      }
+      continue;
+    }
+    // diagonal block: x = D^-1 w with the inverted kBS x kBS block
+    __syncthreads();
+    const T *Di = dinv + F.dinv_off + int64_t(it.y) * 2 * kBS * kBS + (Fwd ? 0 : kBS * kBS);
+    for (int e = tid; e < kBS * kBS; e += kChainThreads) {
+      const int rr = e % kBS, k = e / kBS;
+      sL[e] = (rr < rb && k < rb) ? Di[rr + k * kBS] : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sZ[row * kMaxRhs + g + 4 * q] = row < rb ? acc[q] : T(0);
+    __syncthreads();
+    T x[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 8
+    for (int k = 0; k < kBS; ++k) {
+      const T a = sL[k * kBS + row];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) x[q] += a * sZ[k * kMaxRhs + g + 4 * q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = g + 4 * q;
+      if (row < rb && c < nrhs) Z[(r0 + row) + int64_t(c) * ld] = x[q];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      st_release_gpu(&flags[fbase + it.y], epoch);
+    }
+  }
+}
+
+template <typename T, bool Fwd>
+int chain_grid(int nitems) {
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_chain<T, Fwd>, kChainThreads, 0) != cudaSuccess || n <= 0)
+      n = 1;
+    per_sm = n;
+    cudaGetLastError();
+  }
+  return std::max(1, std::min(nitems, per_sm * num_sms()));
+}
+
+template <typename T, bool Fwd>
+cudaError_t launch_chain(const FrontDev *fr, const ChainArgs &ca, int li, const T *fronts, const T *dinv, int nrhs,
+                         T *work, T *zbuf, const int64_t *work_off, cudaStream_t s) {
+  const int off = Fwd ? ca.fwd_off[li] : ca.bwd_off[li];
+  const int n = Fwd ? ca.fwd_n[li] : ca.bwd_n[li];
+  if (n == 0) return cudaSuccess;
+  const int2 *items = ca.items + off;
+  int *ticket = ca.tickets + 2 * li + (Fwd ? 0 : 1);
+  int epoch = ca.epoch;
+  void *args[] = {(void *)&fr, (void *)&items, (void *)&n, (void *)&ticket, (void *)&fronts, (void *)&dinv,
+                  (void *)&nrhs, (void *)&work, (void *)&zbuf, (void *)&work_off, (void *)&ca.flags, (void *)&epoch,
+                  (void *)&ca.err};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_chain<T, Fwd>), dim3(chain_grid<T, Fwd>(n)),
+                                     dim3(kChainThreads), args, 0, s);
+}
+
+
+
 template <typename T>
 struct GemmCfg;
 template <>
@@ -1240,16 +1435,6 @@ inline bool use_tensor_core_gemm() {
   return v == 1;
 }
 
-inline int num_sms() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        n <= 0)
-      n = 152;
-  }
-  return n;
-}
 
 // Step j0 of the blocked LU of every front of a level: panel (columns
 // [j0, j0 + NB), partial pivoting over the supernode rows), row interchanges
@@ -1449,12 +1634,17 @@ template <typename T>
 cudaError_t launch_solve_fwd_level_impl(const FrontDev *fr, int lo, int nfront, int max_s, int max_f, const T *fronts,
                                         const T *dinv, const int32_t *perm, const int32_t *idx, T *y, int64_t ldy,
                                         int nrhs, T *work, T *zbuf, const int64_t *work_off, cudaStream_t s,
-                                        Prof *prof, double bytes) {
+                                        Prof *prof, double bytes, const ChainArgs *ca, int li) {
   if (nfront == 0) return cudaSuccess;
   const FrontDev *frl = fr + lo;
   const size_t e0 = prof->begin();
   int nl = 2;
   k_fwd_gather<T><<<dim3(cdiv(max_f, 256), nfront), 256, 0, s>>>(frl, perm, idx, y, ldy, nrhs, work, work_off, lo);
+  if (ca != nullptr) {
+    cudaError_t ce = launch_chain<T, true>(fr, *ca, li, fronts, dinv, nrhs, work, zbuf, work_off, s);
+    if (ce != cudaSuccess) return ce;
+    ++nl;
+  } else
   for (int c0 = 0; c0 < max_s; c0 += kBS) {
     const int rest = max_f - c0 - 1;
     const int nb = std::max(1, cdiv(std::max(rest, 1), kStepRows));
@@ -1470,7 +1660,8 @@ cudaError_t launch_solve_fwd_level_impl(const FrontDev *fr, int lo, int nfront, 
 template <typename T>
 cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, int max_s, int max_f, const T *fronts,
                                         const T *dinv, const int32_t *idx, T *y, int64_t ldy, int nrhs, T *work,
-                                        T *zbuf, const int64_t *work_off, cudaStream_t s, Prof *prof, double bytes) {
+                                        T *zbuf, const int64_t *work_off, cudaStream_t s, Prof *prof, double bytes,
+                                        const ChainArgs *ca, int li) {
   if (nfront == 0) return cudaSuccess;
   const FrontDev *frl = fr + lo;
   const size_t e0 = prof->begin();
@@ -1479,6 +1670,11 @@ cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, 
   k_bwd_u12<T><<<dim3(cdiv(max_s, kRowsPerCta), cdiv(std::max(max_f - 1, 1), kU12Chunk), nfront), kRowsPerCta, 0, s>>>(
       frl, fronts, nrhs, work, work_off, lo);
   const int last = ((max_s - 1) / kBS) * kBS;
+  if (ca != nullptr) {
+    cudaError_t ce = launch_chain<T, false>(fr, *ca, li, fronts, dinv, nrhs, work, zbuf, work_off, s);
+    if (ce != cudaSuccess) return ce;
+    ++nl;
+  } else
   for (int c0 = last; c0 >= 0; c0 -= kBS) {
     const int nb = std::max(1, cdiv(c0, kStepRows));
     k_bwd_step<T><<<dim3(nb, nfront), kStepThreads, step_smem<T>(), s>>>(frl, c0, fronts, dinv, nrhs, work, zbuf,
@@ -1500,10 +1696,12 @@ template cudaError_t launch_extend_add_impl<double>(const FrontDev *, int, int, 
 template cudaError_t launch_invert_diag<double>(const FrontDev *, int, int, const double *, double *, cudaStream_t, Prof *);
 template cudaError_t launch_solve_fwd_level_impl<double>(const FrontDev *, int, int, int, int, const double *, const double *,
                                                        const int32_t *, const int32_t *, double *, int64_t, int, double *,
-                                                       double *, const int64_t *, cudaStream_t, Prof *, double);
+                                                       double *, const int64_t *, cudaStream_t, Prof *, double,
+                                                       const ChainArgs *, int);
 template cudaError_t launch_solve_bwd_level_impl<double>(const FrontDev *, int, int, int, int, const double *, const double *,
                                                        const int32_t *, double *, int64_t, int, double *, double *,
-                                                       const int64_t *, cudaStream_t, Prof *, double);
+                                                       const int64_t *, cudaStream_t, Prof *, double,
+                                                       const ChainArgs *, int);
 template cudaError_t launch_assemble<float>(const AItem *, int64_t, const double *, float *, cudaStream_t, Prof *,
                                            double);
 template cudaError_t launch_lu_level<float>(const FrontDev *, const Front *, int, int, int, float *, int32_t *, int32_t *,
@@ -1514,9 +1712,11 @@ template cudaError_t launch_extend_add_impl<float>(const FrontDev *, int, int, i
 template cudaError_t launch_invert_diag<float>(const FrontDev *, int, int, const float *, float *, cudaStream_t, Prof *);
 template cudaError_t launch_solve_fwd_level_impl<float>(const FrontDev *, int, int, int, int, const float *, const float *,
                                                        const int32_t *, const int32_t *, float *, int64_t, int, float *,
-                                                       float *, const int64_t *, cudaStream_t, Prof *, double);
+                                                       float *, const int64_t *, cudaStream_t, Prof *, double,
+                                                       const ChainArgs *, int);
 template cudaError_t launch_solve_bwd_level_impl<float>(const FrontDev *, int, int, int, int, const float *, const float *,
                                                        const int32_t *, float *, int64_t, int, float *, float *,
-                                                       const int64_t *, cudaStream_t, Prof *, double);
+                                                       const int64_t *, cudaStream_t, Prof *, double,
+                                                       const ChainArgs *, int);
 
 }  // namespace h2sp

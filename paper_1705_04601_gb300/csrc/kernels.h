@@ -68,6 +68,19 @@ cudaError_t launch_make_perm(const FrontDev *fr, int nfront, int max_s, const in
 template <typename T>
 cudaError_t launch_invert_diag(const FrontDev *fr, int nfront, int max_s, const T *fronts, T *dinv, cudaStream_t s,
                                Prof *prof);
+// Work lists of the flag-synchronised sweeps (one launch per level and
+// direction): items (front, row block) of level li are items[fwd_off[li] ..
+// fwd_off[li] + fwd_n[li]) in dependency order, likewise for the backward
+// sweep; one flag per supernode row block of every front (index
+// dinv_off / (2 kSolveBlock^2) + block), published with the launch's epoch;
+// two ticket counters per level, zero before each sweep; err |= 4 on a
+// bounded-wait timeout.
+struct ChainArgs {
+  const int2 *items = nullptr;
+  const int *fwd_off = nullptr, *fwd_n = nullptr, *bwd_off = nullptr, *bwd_n = nullptr;  // host arrays
+  int *tickets = nullptr, *flags = nullptr, *err = nullptr;
+  int epoch = 0;
+};
 // Forward sweep for one level (fronts [lo, lo+nfront) of fr): gathers P^T y into
 // the fronts' work vectors, z = L11^-1 (.) block by block into zbuf, adds
 // -L21 z into the boundary rows of y and stores z into the supernode rows.
@@ -75,12 +88,13 @@ template <typename T>
 cudaError_t launch_solve_fwd_level_impl(const FrontDev *fr, int lo, int nfront, int max_s, int max_f, const T *fronts,
                                         const T *dinv, const int32_t *perm, const int32_t *idx, T *y, int64_t ldy,
                                         int nrhs, T *work, T *zbuf, const int64_t *work_off, cudaStream_t s,
-                                        Prof *prof, double bytes);
+                                        Prof *prof, double bytes, const ChainArgs *ca = nullptr, int li = 0);
 // Backward sweep for one level: x_s = U11^-1 (z - U12 x_b), stored into y.
 template <typename T>
 cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, int max_s, int max_f, const T *fronts,
                                         const T *dinv, const int32_t *idx, T *y, int64_t ldy, int nrhs, T *work,
-                                        T *zbuf, const int64_t *work_off, cudaStream_t s, Prof *prof, double bytes);
+                                        T *zbuf, const int64_t *work_off, cudaStream_t s, Prof *prof, double bytes,
+                                        const ChainArgs *ca = nullptr, int li = 0);
 
 // FP32 trailing update C -= L21 U12 of one panel step on the tensor cores
 // (gemm_tc.cu), over the 128-column tiles [tile_lo, tile_hi) of the trailing
