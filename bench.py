@@ -151,18 +151,31 @@ def kernel_source_hash():
 
 
 def roofline(prof, timed_launches_ok=True):
-    """Dominant kernel class by event time -> achieved vs its peak."""
+    """Dominant kernel class by event time -> achieved vs its peak.
+
+    The library's profiler records per class the algorithmic work of its
+    launches: bytes for HBM-bound classes, flops for ALU-bound ones.
+      gemm_update   tensor-core rank-64 update: HBM-bound, bytes (C read + written, L21, U12)
+                    (H2SP_GEMM=simt: FP32 CUDA-core flops)
+      panel, swap_trsm   FP32 flops (CUDA cores)
+      transform, householder, coupling, h2_matvec   FP64 flops (FP64 pipe)
+      solve, apply, assemble, extend_add, vector    bytes
+    """
     cls = max(prof, key=lambda c: prof[c]["ms"])
     p = prof[cls]
     per_launch_ms = p["ms"] / max(p["timed"], 1)
     work_per_launch = p["work"] / max(p["timed"], 1)
     peaks = measured_peaks()
     out = {"kernel": cls, "launches_timed": p["timed"], "avg_launch_ms": per_launch_ms}
-    if cls in ("gemm_update", "panel", "swap_trsm", "transform"):
-        # FP32 fronts in the mixed step: SIMT FP32 pipe (alu)
+    simt_gemm = os.environ.get("H2SP_GEMM", "") == "simt"
+    if cls in ("panel", "swap_trsm") or (cls == "gemm_update" and simt_gemm):
         achieved = p["work"] / (p["ms"] * 1e-3) / 1e12
         out.update(bound="alu", achieved=achieved, peak=FP32_SIMT_TFLOPS, unit="TFLOP/s",
                    peak_source="derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal max clock)")
+    elif cls in ("transform", "householder", "coupling", "h2_matvec"):
+        achieved = p["work"] / (p["ms"] * 1e-3) / 1e12
+        out.update(bound="alu", achieved=achieved, peak=FP64_TFLOPS, unit="TFLOP/s",
+                   peak_source="nominal GB300 FP64 (1.25 TFLOP/s); no measured FP64 peak on this pool")
     else:
         achieved = p["work"] / (p["ms"] * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)

@@ -100,7 +100,8 @@ struct h2sp_handle {
   bool device_ready = false;
   Prof prof;
   std::vector<double> x_flops;  // algorithmic flops of each level's transform launch
-  double near_bytes = 0.0;      // bytes of the close blocks (Definition 4.8)  // false for handles made by h2sp_analyze
+  double near_bytes = 0.0;      // bytes of the close blocks (Definition 4.8)
+  double mv_flops_per_rhs = 0.0;  // FP64 flops of one H^2 product per right-hand side
 
   template <class T>
   T *alloc(size_t n) {
@@ -124,9 +125,12 @@ struct h2sp_handle {
   int chain_epoch = 0;
   void release() {
     if (la.side) cudaStreamSynchronize(la.side);
+    if (la.rest) cudaStreamSynchronize(la.rest);
     if (la.next) cudaEventDestroy(la.next);
     if (la.panel) cudaEventDestroy(la.panel);
+    if (la.done) cudaEventDestroy(la.done);
     if (la.side) cudaStreamDestroy(la.side);
+    if (la.rest) cudaStreamDestroy(la.rest);
     la = LuAsync();
     if (allocs.empty()) return;
     for (void *p : allocs) cudaFreeAsync(p, stream);
@@ -239,8 +243,8 @@ void h2_matvec(h2sp_handle *h, const double *x, int64_t ldx, double *y, int64_t 
   ck(launch_h2_matvec(h->h2, p.level_ptr.data(), h->child_start, h->child_cnt, p.D, x, ldx, y, ldy, nrhs, h->xh,
                       h->yh, std::max<int64_t>(p.xh_elems, 1), h->stream));
   const int chunks = (nrhs + 15) / 16;
-  // bytes of the close blocks each pass streams (the dominant traffic of the product)
-  h->prof.end(P_MATVEC, (3 + 2 * p.D) * chunks, e0, h->near_bytes * chunks);
+  // FP64 flops: the product is bound by the FP64 pipe
+  h->prof.end(P_MATVEC, (3 + 2 * p.D) * chunks, e0, h->mv_flops_per_rhs * nrhs);
 }
 
 // per-front work vectors of the triangular solves, for 16 right-hand sides at a time
@@ -688,9 +692,23 @@ int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream s
       }
       h->child_start = h->upload(cs);
       h->child_cnt = h->upload(cc);
-      for (int lf = 0; lf < p.nleaf; ++lf)
-        for (int64_t z = p.near_ptr[lf]; z < p.near_ptr[lf + 1]; ++z)
-          h->near_bytes += 8.0 * double(p.h_size[p.level_ptr[p.D] + lf]) * double(p.h_size[p.near_col[z]]);
+      // FP64 multiply-adds per right-hand side of one product: close blocks,
+      // couplings, the leaf bases (up and down) and the transfers (up and down)
+      double mv = 0.0;
+      for (int lf = 0; lf < p.nleaf; ++lf) {
+        const int t = p.level_ptr[p.D] + lf;
+        for (int64_t z = p.near_ptr[lf]; z < p.near_ptr[lf + 1]; ++z) {
+          const double e = double(p.h_size[t]) * double(p.h_size[p.near_col[z]]);
+          h->near_bytes += 8.0 * e;
+          mv += e;
+        }
+        mv += 2.0 * double(p.h_size[t]) * p.rank[t];
+      }
+      for (int t = 0; t < p.ncl; ++t) {
+        for (int64_t z = p.far_ptr[t]; z < p.far_ptr[t + 1]; ++z) mv += double(p.rank[t]) * p.rank[p.far_col[z]];
+        if (t >= p.level_ptr[1]) mv += 2.0 * double(p.rank[t]) * p.rank[p.parent[t]];
+      }
+      h->mv_flops_per_rhs = 2.0 * mv;
       h->xh = h->alloc<double>(size_t(std::max<int64_t>(p.xh_elems, 1)) * 16);
       h->yh = h->alloc<double>(size_t(std::max<int64_t>(p.xh_elems, 1)) * 16);
       std::vector<int64_t> sp(1, 0);
@@ -704,7 +722,7 @@ int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream s
       std::vector<FrontDev> fd(p.fronts.size());
       for (size_t k = 0; k < p.fronts.size(); ++k) {
         const Front &F = p.fronts[k];
-        fd[k] = FrontDev{F.off, F.piv_off, F.idx_off, F.map_off, F.dinv_off, F.s, F.b, F.f, F.parent};
+        fd[k] = FrontDev{F.off, F.piv_off, F.idx_off, F.map_off, F.dinv_off, F.s, F.b, F.f, F.parent, F.ld};
         h->max_s_all = std::max(h->max_s_all, F.s);
       }
       h->fr = h->upload(fd);
@@ -810,8 +828,10 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
       int lo = 0, hi = 0;
       ck(cudaDeviceGetStreamPriorityRange(&lo, &hi));
       ck(cudaStreamCreateWithPriority(&h->la.side, cudaStreamNonBlocking, hi));
+      ck(cudaStreamCreateWithPriority(&h->la.rest, cudaStreamNonBlocking, lo));
       ck(cudaEventCreateWithFlags(&h->la.next, cudaEventDisableTiming));
       ck(cudaEventCreateWithFlags(&h->la.panel, cudaEventDisableTiming));
+      ck(cudaEventCreateWithFlags(&h->la.done, cudaEventDisableTiming));
     }
     const LuAsync *la = h->la.side ? &h->la : nullptr;
     h->prec = -1;

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel(const FrontDev *__restr
   if (j0 >= F.s) return;
   const int jb = min(NB, F.s - j0);
   T *A = fronts + F.off;
-  const int64_t ld = F.f;
+  const int64_t ld = F.ld;
   __shared__ T urow[NB];
   __shared__ T redv[kPanelThreads / 32];
   __shared__ int redi[kPanelThreads / 32];
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kClusterPanelThreads) k_panel_cluster(const Fr
   if (j0 >= F.s) return;  // uniform over the cluster: no barrier is ever entered
   const int jb = min(NB, F.s - j0);
   T *A = fronts + F.off;
-  const int64_t ld = F.f;
+  const int64_t ld = F.ld;
   const int R = F.f - j0;
   const int per = (R + C - 1) / C;
   const int r_lo = j0 + rank * per;
@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(kRegPanelThreads, 1) k_panel_reg(const FrontDe
   if (j0 >= F.s) return;  // uniform over the cluster
   const int jb = min(NB, F.s - j0);
   T *A = fronts + F.off;
-  const int64_t ld = F.f;
+  const int64_t ld = F.ld;
   const int R = F.f - j0;
   const int per = (R + C - 1) / C;
   const int r_lo = j0 + rank * per;
@@ -674,7 +674,7 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const FrontDev *__restrict__ 
   if (j0 >= F.s) return;
   const int jb = min(NB, F.s - j0);
   T *A = fronts + F.off;
-  const int64_t ld = F.f;
+  const int64_t ld = F.ld;
   __shared__ T L[NB * NB];
   __shared__ int32_t srow[kMaxSwapRows], ssrc[kMaxSwapRows];
   const int32_t *sw = swaps + int64_t(blockIdx.y) * (1 + 2 * kMaxSwapRows);
@@ -740,7 +740,7 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
   const int rb = blockIdx.y * BM, cb = c_lo + blockIdx.x * BN;
   if (rb >= nrest || cb >= ncol) return;
   T *A = fronts + F.off;
-  const int64_t ld = F.f;
+  const int64_t ld = F.ld;
   extern __shared__ __align__(16) unsigned char smraw[];
   T *sA = reinterpret_cast<T *>(smraw);  // [NB][PA]
   T *sB = sA + NB * PA;                   // [NB][PB]
@@ -842,11 +842,11 @@ __global__ void k_extend_add(const FrontDev *__restrict__ fr_all, int lo, const 
   if (i0 >= F.b || j0 >= F.b) return;
   const FrontDev P = fr_all[F.parent];
   const int32_t *mp = map + F.map_off;
-  const T *C = fronts + F.off + int64_t(F.s) * F.f + F.s;
+  const T *C = fronts + F.off + int64_t(F.s) * F.ld + F.s;
   T *Pa = fronts + P.off;
   for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
     const int i = i0 + (e & 31), j = j0 + (e >> 5);
-    if (i < F.b && j < F.b) atomicAdd(&Pa[mp[i] + int64_t(mp[j]) * P.f], C[i + int64_t(j) * F.f]);
+    if (i < F.b && j < F.b) atomicAdd(&Pa[mp[i] + int64_t(mp[j]) * P.ld], C[i + int64_t(j) * F.ld]);
   }
 }
 
@@ -923,7 +923,7 @@ __global__ void __launch_bounds__(kBS) k_invert_diag(const FrontDev *__restrict_
   const T *A = fronts + F.off;
   for (int e = threadIdx.x; e < cb * cb; e += blockDim.x) {
     const int r = e % cb, c = e / cb;
-    D[r + c * kBS] = A[(c0 + r) + int64_t(c0 + c) * F.f];
+    D[r + c * kBS] = A[(c0 + r) + int64_t(c0 + c) * F.ld];
   }
   __syncthreads();
   T *Li = dinv + F.dinv_off + int64_t(q) * 2 * kBS * kBS;
@@ -1031,7 +1031,7 @@ __global__ void __launch_bounds__(kStepThreads) k_fwd_step(const FrontDev *__res
       Z[(c0 + r) + int64_t(c) * F.f] = sX[r + c * kBS];
     }
   }
-  slab_update<T>(fronts + F.off, F.f, W, F.f, r0, F.f, c0, cb, nrhs, sX, sD);
+  slab_update<T>(fronts + F.off, F.ld, W, F.f, r0, F.f, c0, cb, nrhs, sX, sD);
 }
 
 // backward step of column block [c0, c0+cb): x = Uinv W_c0 -> Z; rows above -= U x
@@ -1058,7 +1058,7 @@ __global__ void __launch_bounds__(kStepThreads) k_bwd_step(const FrontDev *__res
       Z[(c0 + r) + int64_t(c) * F.f] = sX[r + c * kBS];
     }
   }
-  slab_update<T>(fronts + F.off, F.f, W, F.f, r0, c0, c0, cb, nrhs, sX, sD);
+  slab_update<T>(fronts + F.off, F.ld, W, F.f, r0, c0, c0, cb, nrhs, sX, sD);
 }
 
 // rows [0, s) of W -= U12 * W[s:f] (before the backward block sweep); the
@@ -1087,7 +1087,7 @@ __global__ void __launch_bounds__(kRowsPerCta) k_bwd_u12(const FrontDev *__restr
   for (int c = 0; c < kMaxRhs; ++c) acc[c] = T(0);
   const T *A = fronts + F.off;
   for (int q = 0; q < kb; ++q) {
-    const T a = A[r + int64_t(k_lo + q) * F.f];
+    const T a = A[r + int64_t(k_lo + q) * F.ld];
 #pragma unroll
     for (int c = 0; c < kMaxRhs; ++c)
       if (c < nrhs) acc[c] += a * sX[q + c * kU12Chunk];
@@ -1182,7 +1182,7 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrontDev *__restr
     const T *A = fronts + F.off;
     T *W = work + work_off[it.x];
     T *Z = zbuf + work_off[it.x];
-    const int64_t ld = F.f;
+    const int64_t lda = F.ld, ld = F.f;  // front matrix / work vectors
     const bool sn = it.y >= 0;
     const int r0 = sn ? it.y * kBS : F.s + (-it.y - 1) * kBS;
     const int rb = min(kBS, (sn ? F.s : F.f) - r0);
@@ -1203,7 +1203,7 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrontDev *__restr
 #pragma unroll
       for (int e = 0; e < kChainPre; ++e) {
         const int idx = tid + e * kChainThreads, k = idx / kBS, rr = idx % kBS;
-        pre[e] = (rr < rb && k < kb) ? A[(r0 + rr) + int64_t(c0 + k) * ld] : T(0);
+        pre[e] = (rr < rb && k < kb) ? A[(r0 + rr) + int64_t(c0 + k) * lda] : T(0);
       }
     };
     bool ok = true;
@@ -1516,8 +1516,8 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
     prof->end(P_PANEL, 1, e0, fpanel, st);
     return cudaSuccess;
   };
-  // A22[:, c_lo:c_hi] -= L21 U12[:, c_lo:c_hi] (columns relative to the trailing block)
-  auto update = [&](int j0, int c_lo, int c_hi, int sm_budget) -> cudaError_t {
+  // A22[:, c_lo:c_hi] -= L21 U12[:, c_lo:c_hi] (columns relative to the trailing block), on stream us
+  auto update = [&](int j0, int c_lo, int c_hi, int sm_budget, cudaStream_t us) -> cudaError_t {
     const int rest = max_f - j0 - 1;
     if (rest <= 0 || c_lo >= std::min(rest, c_hi)) return cudaSuccess;
     double fgemm = 0.0;
@@ -1528,25 +1528,28 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
         const double jb = std::min(NB, F.s - j0);
         const int nrest = F.f - j0 - int(jb);
         const double cols = std::max(0, std::min(nrest, c_hi) - c_lo);
-        fgemm += 2.0 * nrest * cols * jb;
+        // tensor cores: HBM-bound rank-jb update, work = algorithmic bytes
+        // (C read and written, L21 and U12 read); CUDA cores: flops
+        fgemm += tc ? double(sizeof(T)) * (2.0 * nrest * cols + jb * (nrest + cols)) : 2.0 * nrest * cols * jb;
       }
-    const size_t e0 = prof->begin();
+    const size_t e0 = prof->begin(us);
     if (tc) {
       if constexpr (std::is_same<T, float>::value) {
         const int thi = c_hi >= (INT_MAX - kTcTile) ? INT_MAX : c_hi / kTcTile;
-        cudaError_t ge = launch_gemm_tc(fr, j0, nfront, max_f, fronts, err, s, c_lo / kTcTile, thi, sm_budget);
+        cudaError_t ge = launch_gemm_tc(fr, j0, nfront, max_f, fronts, err, us, c_lo / kTcTile, thi, sm_budget);
         if (ge != cudaSuccess) return ge;
       }
     } else {
       const int ncol = std::min(rest, c_hi) - c_lo;
       dim3 g(cdiv(ncol, G::BN), cdiv(rest, G::BM), nfront);
-      gemm<<<g, 256, gsmem, s>>>(fr, j0, fronts, c_lo, c_hi);
+      gemm<<<g, 256, gsmem, us>>>(fr, j0, fronts, c_lo, c_hi);
     }
-    prof->end(P_GEMM, 1, e0, fgemm);
+    prof->end(P_GEMM, 1, e0, fgemm, us);
     return cudaSuccess;
   };
 
-  const bool ahead = la != nullptr && la->side != nullptr && la->next != nullptr && la->panel != nullptr;
+  const bool ahead = la != nullptr && la->side != nullptr && la->rest != nullptr && la->next != nullptr &&
+                     la->panel != nullptr && la->done != nullptr;
   int panel_ctas = 0;
   cudaError_t e = panel(0, s, &panel_ctas);
   if (e != cudaSuccess) return e;
@@ -1565,15 +1568,18 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
     prof->end(P_TRSM, 1, e0, ftrsm);
     const bool more = j0 + NB < max_s;
     if (more && ahead) {
-      if ((e = update(j0, 0, W, nsm)) != cudaSuccess) return e;
+      if ((e = update(j0, 0, W, nsm, s)) != cudaSuccess) return e;
       if ((e = cudaEventRecord(la->next, s)) != cudaSuccess) return e;
       if ((e = cudaStreamWaitEvent(la->side, la->next, 0)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(la->rest, la->next, 0)) != cudaSuccess) return e;
       if ((e = panel(j0 + NB, la->side, &panel_ctas)) != cudaSuccess) return e;
       if ((e = cudaEventRecord(la->panel, la->side)) != cudaSuccess) return e;
-      if ((e = update(j0, W, INT_MAX, std::max(nsm - panel_ctas, nsm / 2))) != cudaSuccess) return e;
+      if ((e = update(j0, W, INT_MAX, std::max(nsm - panel_ctas, nsm / 2), la->rest)) != cudaSuccess) return e;
+      if ((e = cudaEventRecord(la->done, la->rest)) != cudaSuccess) return e;
       if ((e = cudaStreamWaitEvent(s, la->panel, 0)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(s, la->done, 0)) != cudaSuccess) return e;
     } else {
-      if ((e = update(j0, 0, INT_MAX, nsm)) != cudaSuccess) return e;
+      if ((e = update(j0, 0, INT_MAX, nsm, s)) != cudaSuccess) return e;
       if (more && (e = panel(j0 + NB, s, &panel_ctas)) != cudaSuccess) return e;
     }
   }

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__res
   const int c_lo = tile_lo + blockIdx.x * per, c_hi = min(tile_lo + ntiles, c_lo + per);
   if (c_lo >= c_hi) return;
   float *A = fronts + F.off;
-  const int64_t ld = F.f;
+  const int64_t ld = F.ld;
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char *sAh = smraw, *sAl = smraw + 4 * kTileFloats;
   unsigned char *sBh[2] = {smraw + 8 * kTileFloats, smraw + 16 * kTileFloats};
@@ -277,11 +277,20 @@ cudaError_t launch_gemm_tc(const FrontDev *fr, int j0, int nfront, int max_f, fl
   const int rt = (rest + kTcM - 1) / kTcM;
   const int ct = std::min((rest + kTcN - 1) / kTcN, tile_hi) - tile_lo;
   if (ct <= 0) return cudaSuccess;
-  // one CTA per SM (shared memory): about two waves over the SMs this launch
-  // may use, each CTA walking a contiguous range of column tiles
-  const int want = 2 * std::max(sm_budget, 1);
-  int splits = (want + rt * nfront - 1) / (rt * nfront);
-  splits = std::max(1, std::min(splits, ct));
+  // One CTA per SM (shared memory).  Each CTA takes a contiguous range of
+  // ceil(ct / splits) column tiles of one row tile; the launch lasts about
+  // ceil(CTAs / SMs) such ranges (plus the A staging, ~0.3 tile), so splits
+  // is chosen to minimise that over whole waves.
+  const int slots = std::max(sm_budget, 1);
+  int splits = 1;
+  double best = 1e300;
+  for (int sp = 1; sp <= ct; ++sp) {
+    const int per = (ct + sp - 1) / sp;
+    if (sp > 1 && (ct + sp - 2) / (sp - 1) == per) continue;  // same range length, more CTAs
+    const double waves = double((int64_t(rt) * nfront * sp + slots - 1) / slots);
+    const double cost = waves * (per + 0.3);
+    if (cost < best - 1e-9) best = cost, splits = sp;
+  }
   dim3 g(splits, rt, nfront);
   k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, tile_lo, tile_hi);
   return cudaGetLastError();

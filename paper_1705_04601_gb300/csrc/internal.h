@@ -74,13 +74,14 @@ struct AItem {
 };
 
 struct Front {
-  int64_t off;      // element offset of the f x f front (column-major, ld f)
+  int64_t off;      // element offset of the f x f front (column-major, leading dimension ld)
   int64_t piv_off;  // offset into the pivot array (s entries)
   int64_t idx_off;  // offset into the global-index array (f entries)
   int64_t map_off;  // offset into the extend-add map (b entries)
   int64_t dinv_off; // offset of the inverted diagonal blocks (2 * 64 * 64 per 64 supernode columns)
   int32_t s, b, f;
   int32_t parent;   // parent front, -1 for a root
+  int32_t ld;       // f rounded up to a multiple of 4: every column starts on a 16-byte boundary
 };
 
 struct LevelWork {

@@ -22,6 +22,7 @@ cudaError_t launch_transform(const XItem *items, int n, const double *const *src
 struct FrontDev {
   int64_t off, piv_off, idx_off, map_off, dinv_off;
   int32_t s, b, f, parent;
+  int32_t ld;  // leading dimension of the front (f rounded up to a multiple of 4)
 };
 
 // Column block of the blocked triangular solves (and of the inverted diagonal blocks).
@@ -46,11 +47,13 @@ template <typename T>
 cudaError_t launch_assemble(const AItem *items, int64_t n, const double *S, T *fronts, cudaStream_t s, Prof *prof,
                             double bytes);
 // Look-ahead resources of the block LU: a high-priority stream on which the
-// next panel is factored while the rest of the trailing update runs on the
-// main stream, and the two events that order them.
+// next panel is factored and a low-priority one on which the rest of the
+// trailing update runs meanwhile (both released by the same event, so the
+// panel is dispatched first), and the events that order them.
 struct LuAsync {
-  cudaStream_t side = nullptr;
-  cudaEvent_t next = nullptr, panel = nullptr;
+  cudaStream_t side = nullptr;  // high priority: the next panel
+  cudaStream_t rest = nullptr;  // low priority: the rest of the trailing update
+  cudaEvent_t next = nullptr, panel = nullptr, done = nullptr;
 };
 // Blocked LU with partial pivoting inside the supernode rows of every front of
 // one level (all fronts in parallel).  With `la` (may be null) the panel of

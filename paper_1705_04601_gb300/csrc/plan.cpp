@@ -723,12 +723,13 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
       F.s = int32_t(s);
       F.b = int32_t(b);
       F.f = int32_t(s + b);
+      F.ld = int32_t((F.f + 3) / 4 * 4);
       F.parent = sn_parent[k];
       F.off = p.front_elems;
       F.piv_off = p.piv_elems;
       F.idx_off = int64_t(p.front_idx.size());
       F.map_off = 0;
-      p.front_elems += int64_t(F.f) * F.f;
+      p.front_elems += int64_t(F.ld) * F.f;
       p.piv_elems += s;
       F.dinv_off = p.dinv_elems;
       p.dinv_elems += ((s + 63) / 64) * 2 * 64 * 64;
@@ -770,8 +771,8 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
         a.src = p.val_off[z];
         a.rows = int32_t(p.node_size[i]);
         a.cols = int32_t(p.node_size[j]);
-        a.ld = F.f;
-        a.dst = F.off + pos_in_front(k, j) * F.f + pos_in_front(k, i);
+        a.ld = F.ld;
+        a.dst = F.off + pos_in_front(k, j) * F.ld + pos_in_front(k, i);
         p.assemble.push_back(a);
       }
     // elimination levels: consecutive supernodes of equal closure depth
@@ -831,7 +832,7 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
       }
       for (size_t k = 0; k < p.fronts.size(); ++k) {
         const Front &F = p.fronts[k];
-        inside(F.off, F.f, F.f, F.f, p.front_elems, "front");
+        inside(F.off, F.f, F.f, F.ld, p.front_elems, "front");
         if (F.piv_off + F.s > p.piv_elems || F.idx_off + F.f > int64_t(p.front_idx.size()))
           throw Fail{H2SP_EINVAL, "internal: front index arrays"};
         if (F.parent >= 0) {
