@@ -171,6 +171,21 @@ typedef struct {
 int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream stream, h2sp_handle **out);
 
 /*
+ * h2sp_sparsify_analyzed -- h2sp_sparsify reusing the host analysis held by
+ * `an` (a handle from h2sp_analyze or h2sp_sparsify) for a descriptor with the
+ * same structure (every HOST array equal: sizes, tree, ranks, both lists and
+ * all offsets) and new numbers.  This is the split of a sparse direct solver
+ * into symbolic analysis and numeric phases; the paper builds its plan once
+ * per structure as well (§4).  The structure is checked (its sizes, then a
+ * 64-bit fingerprint of every structure array) before anything is launched:
+ * a mismatch returns H2SP_EINVAL.  `an` stays valid and may be destroyed
+ * before or after *out (the analysis is shared, reference counted).  The
+ * device arrays of `desc` are borrowed as in h2sp_sparsify.
+ */
+int h2sp_sparsify_analyzed(const h2sp_handle *an, const h2sp_h2_desc *desc, const h2sp_opts *opts,
+                           h2sp_stream stream, h2sp_handle **out);
+
+/*
  * h2sp_analyze -- the host-only part of h2sp_sparsify: validate the
  * descriptor and plan the level recursion, the block pattern of S (§3) and
  * the symbolic factorization of S.  Makes no CUDA call and does not read the

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
@@ -54,7 +55,8 @@ struct FrontLevel {
 }  // namespace
 
 struct h2sp_handle {
-  Plan plan;
+  std::shared_ptr<const Plan> plan_ptr;  // host analysis, shared with the handles planned from it
+  uint64_t structure_hash = 0;          // fingerprint of the descriptor's structure arrays
   cudaStream_t stream = nullptr;
   std::vector<void *> allocs;
   // borrowed H^2 numbers
@@ -168,7 +170,7 @@ void init_pool_once() {
 // ---------------- vectors of the applies ----------------
 void ensure_vectors(h2sp_handle *h, int nrhs) {
   if (h->vec_rhs >= nrhs) return;
-  const int64_t n = h->plan.n;
+  const int64_t n = (*h->plan_ptr).n;
   const int64_t w = std::max<int64_t>(h->max_width, n);
   h->vecA = h->alloc<double>(size_t(w) * nrhs);
   h->vecB = h->alloc<double>(size_t(w) * nrhs);
@@ -180,7 +182,7 @@ void ensure_vectors(h2sp_handle *h, int nrhs) {
 
 // out (S space, ld n) = Qside^T in (point space)
 void apply_T(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *out, int64_t ldout, int nrhs) {
-  const Plan &p = h->plan;
+  const Plan &p = (*h->plan_ptr);
   cudaStream_t s = h->stream;
   const int chunks = (nrhs + 15) / 16;
   const size_t e0 = h->prof.begin();
@@ -210,7 +212,7 @@ void apply_T(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *o
 
 // out (point space) = Qside in (S space)
 void apply_N(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *out, int64_t ldout, int nrhs) {
-  const Plan &p = h->plan;
+  const Plan &p = (*h->plan_ptr);
   cudaStream_t s = h->stream;
   const int chunks = (nrhs + 15) / 16;
   const size_t e0 = h->prof.begin();
@@ -238,7 +240,7 @@ void apply_N(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *o
 }
 
 void h2_matvec(h2sp_handle *h, const double *x, int64_t ldx, double *y, int64_t ldy, int nrhs) {
-  const Plan &p = h->plan;
+  const Plan &p = (*h->plan_ptr);
   const size_t e0 = h->prof.begin();
   ck(launch_h2_matvec(h->h2, p.level_ptr.data(), h->child_start, h->child_cnt, p.D, x, ldx, y, ldy, nrhs, h->xh,
                       h->yh, std::max<int64_t>(p.xh_elems, 1), h->stream));
@@ -251,7 +253,7 @@ void h2_matvec(h2sp_handle *h, const double *x, int64_t ldx, double *y, int64_t 
 constexpr int kSolveRhs = 16;
 void ensure_work(h2sp_handle *h, int nrhs) {
   if (h->work_off == nullptr) {
-    const Plan &p = h->plan;
+    const Plan &p = (*h->plan_ptr);
     std::vector<int64_t> off(p.fronts.size());
     int64_t acc = 0;
     for (size_t k = 0; k < p.fronts.size(); ++k) {
@@ -263,7 +265,7 @@ void ensure_work(h2sp_handle *h, int nrhs) {
     h->zbuf = h->alloc<double>(size_t(std::max<int64_t>(acc, 1)));
   }
   if (h->work_rhs < nrhs) {
-    h->yf = h->alloc<float>(size_t(h->plan.n) * nrhs);
+    h->yf = h->alloc<float>(size_t((*h->plan_ptr).n) * nrhs);
     h->work_rhs = nrhs;
   }
 }
@@ -282,7 +284,7 @@ bool chain_sweeps_enabled() {
 
 template <typename T>
 void solve_S_T(h2sp_handle *h, T *y, int nrhs) {
-  const Plan &p = h->plan;
+  const Plan &p = (*h->plan_ptr);
   T *fronts = static_cast<T *>(h->fronts);
   T *work = static_cast<T *>(h->work);
   T *zbuf = static_cast<T *>(h->zbuf);
@@ -336,7 +338,7 @@ int sweep_status(h2sp_handle *h) {
 // in-place S^{-1} on an FP64 S-space vector (ld n)
 void solve_S(h2sp_handle *h, double *y, int nrhs) {
   ensure_work(h, nrhs);
-  const int64_t n = h->plan.n;
+  const int64_t n = (*h->plan_ptr).n;
   if (h->prec == H2SP_FP64) {
     solve_S_T<double>(h, y, nrhs);
   } else {
@@ -349,7 +351,7 @@ void solve_S(h2sp_handle *h, double *y, int nrhs) {
 
 // d = V S^{-1} U^T r   (the direct solve of Eq. sp0)
 void precond(h2sp_handle *h, const double *r, int64_t ldr, double *d, int64_t ldd, int nrhs) {
-  const int64_t n = h->plan.n;
+  const int64_t n = (*h->plan_ptr).n;
   apply_T(h, false, r, ldr, h->vecS, n, nrhs);
   solve_S(h, h->vecS, nrhs);
   apply_N(h, true, h->vecS, n, d, ldd, nrhs);
@@ -363,7 +365,7 @@ void precond(h2sp_handle *h, const double *r, int64_t ldr, double *d, int64_t ld
 // true FP64 H^2 residual (per independent system and column) at its end.
 int gmres(h2sp_handle *h, const h2sp_solve_opts *o, int nrhs, const double *b, int64_t ldb, double *x, int64_t ldx,
           h2sp_solve_info *info) {
-  const Plan &p = h->plan;
+  const Plan &p = (*h->plan_ptr);
   cudaStream_t s = h->stream;
   const int64_t n = p.n;
   const int m = std::max(1, std::min(o->restart > 0 ? o->restart : 20, 60));
@@ -494,40 +496,45 @@ int gmres(h2sp_handle *h, const h2sp_solve_opts *o, int nrhs, const double *b, i
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-const char *h2sp_status_string(int32_t st) {
-  switch (st) {
-    case H2SP_OK: return "ok";
-    case H2SP_EINVAL: return "invalid argument or descriptor";
-    case H2SP_ENOMEM: return "out of device memory";
-    case H2SP_ECUDA: return "CUDA error";
-    case H2SP_ESINGULAR: return "singular pivot block";
-    case H2SP_ESTATE: return "call out of order";
-    case H2SP_ENOCONV: return "no convergence";
-    case H2SP_ETIMEOUT: return "device wait timed out";
-    case H2SP_EUNSUPPORTED: return "unsupported size";
-    default: return "unknown status";
+// FNV-1a over the structure arrays of a descriptor whose sizes match plan p
+// (the sizes come from the plan, which validated the descriptor it was built from)
+uint64_t structure_hash(const h2sp_h2_desc *d, const Plan &p) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](const void *a, size_t bytes) {
+    if (!a) {
+      h = (h ^ 0xA5u) * 1099511628211ull;
+      return;
+    }
+    const unsigned char *b = static_cast<const unsigned char *>(a);
+    for (size_t i = 0; i < bytes; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  };
+  const size_t ncl = size_t(p.ncl), nleaf = size_t(p.nleaf);
+  const size_t nfar = size_t(p.far_ptr[p.ncl]), nnear = size_t(p.near_ptr[p.nleaf]);
+  mix(&d->n, sizeof(d->n));
+  mix(d->level_ptr, sizeof(int32_t) * size_t(p.D + 2));
+  mix(d->parent, sizeof(int32_t) * ncl);
+  mix(d->begin, sizeof(int64_t) * ncl);
+  mix(d->size, sizeof(int64_t) * ncl);
+  mix(d->rank, sizeof(int32_t) * ncl);
+  mix(d->far_ptr, sizeof(int64_t) * (ncl + 1));
+  mix(d->far_col, sizeof(int32_t) * nfar);
+  mix(d->near_ptr, sizeof(int64_t) * (nleaf + 1));
+  mix(d->near_col, sizeof(int32_t) * nnear);
+  mix(d->leaf_basis_off, sizeof(int64_t) * nleaf);
+  mix(d->transfer_off, sizeof(int64_t) * ncl);
+  mix(d->coupling_off, sizeof(int64_t) * nfar);
+  mix(d->near_off, sizeof(int64_t) * nnear);
+  if (!p.sym) {
+    mix(d->col_leaf_basis_off, sizeof(int64_t) * nleaf);
+    mix(d->col_transfer_off, sizeof(int64_t) * ncl);
   }
+  return h;
 }
 
-const char *h2sp_last_cuda_error(void) { return g_cuda_err.c_str(); }
-
-int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream stream, h2sp_handle **out) {
-  (void)opts;
-  if (!out) return H2SP_EINVAL;
-  *out = nullptr;
-  h2sp_handle *h = new (std::nothrow) h2sp_handle();
-  if (!h) return H2SP_ENOMEM;
-  std::string err;
-  auto t0 = std::chrono::steady_clock::now();
-  int st = build_plan(desc, h->plan, err);
-  h->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  if (st != H2SP_OK) {
-    g_cuda_err = err;
-    delete h;
-    return st;
-  }
+// numeric part of the sparsification: device buffers, uploads and kernels
+int sparsify_numeric(h2sp_handle *h, const h2sp_h2_desc *desc, h2sp_stream stream, h2sp_handle **out) {
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   h->prof.stream = h->stream;
   h->leaf_basis = desc->leaf_basis;
@@ -536,7 +543,7 @@ int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream s
   h->near_block = desc->near_block;
   h->col_leaf_basis = desc->col_leaf_basis;
   h->col_transfer = desc->col_transfer;
-  const Plan &p = h->plan;
+  const Plan &p = (*h->plan_ptr);
   cudaStream_t s = h->stream;
   try {
     init_pool_once();
@@ -785,6 +792,73 @@ int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream s
   return H2SP_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+const char *h2sp_status_string(int32_t st) {
+  switch (st) {
+    case H2SP_OK: return "ok";
+    case H2SP_EINVAL: return "invalid argument or descriptor";
+    case H2SP_ENOMEM: return "out of device memory";
+    case H2SP_ECUDA: return "CUDA error";
+    case H2SP_ESINGULAR: return "singular pivot block";
+    case H2SP_ESTATE: return "call out of order";
+    case H2SP_ENOCONV: return "no convergence";
+    case H2SP_ETIMEOUT: return "device wait timed out";
+    case H2SP_EUNSUPPORTED: return "unsupported size";
+    default: return "unknown status";
+  }
+}
+
+const char *h2sp_last_cuda_error(void) { return g_cuda_err.c_str(); }
+
+int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream stream, h2sp_handle **out) {
+  (void)opts;
+  if (!out) return H2SP_EINVAL;
+  *out = nullptr;
+  h2sp_handle *h = new (std::nothrow) h2sp_handle();
+  if (!h) return H2SP_ENOMEM;
+  std::string err;
+  auto t0 = std::chrono::steady_clock::now();
+  auto plan = std::make_shared<Plan>();
+  int st = build_plan(desc, *plan, err);
+  h->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (st != H2SP_OK) {
+    g_cuda_err = err;
+    delete h;
+    return st;
+  }
+  h->plan_ptr = plan;
+  h->structure_hash = structure_hash(desc, *plan);
+  return sparsify_numeric(h, desc, stream, out);
+}
+
+int h2sp_sparsify_analyzed(const h2sp_handle *an, const h2sp_h2_desc *desc, const h2sp_opts *opts,
+                           h2sp_stream stream, h2sp_handle **out) {
+  (void)opts;
+  if (!out) return H2SP_EINVAL;
+  *out = nullptr;
+  if (!an || !an->plan_ptr || !desc) return H2SP_EINVAL;
+  const Plan &ap = *an->plan_ptr;
+  // same structure as the analysed descriptor (sizes first, then every structure array)
+  if (desc->n != ap.n || desc->depth != ap.D || !desc->level_ptr || !desc->far_ptr || !desc->near_ptr) return H2SP_EINVAL;
+  for (int l = 0; l <= ap.D + 1; ++l)
+    if (desc->level_ptr[l] != ap.level_ptr[l]) return H2SP_EINVAL;
+  if (desc->far_ptr[ap.ncl] != ap.far_ptr[ap.ncl] || desc->near_ptr[ap.nleaf] != ap.near_ptr[ap.nleaf])
+    return H2SP_EINVAL;
+  if (!desc->leaf_basis || !desc->transfer || !desc->coupling || !desc->near_block) return H2SP_EINVAL;
+  if ((desc->col_leaf_basis == nullptr) != ap.sym || (desc->col_transfer == nullptr) != ap.sym) return H2SP_EINVAL;
+  if (structure_hash(desc, ap) != an->structure_hash) return H2SP_EINVAL;
+  h2sp_handle *h = new (std::nothrow) h2sp_handle();
+  if (!h) return H2SP_ENOMEM;
+  h->plan_ptr = an->plan_ptr;
+  h->structure_hash = an->structure_hash;
+  h->plan_seconds = 0.0;
+  return sparsify_numeric(h, desc, stream, out);
+}
+
+
 int h2sp_analyze(const h2sp_h2_desc *desc, h2sp_handle **out) {
   if (!out) return H2SP_EINVAL;
   *out = nullptr;
@@ -792,13 +866,16 @@ int h2sp_analyze(const h2sp_h2_desc *desc, h2sp_handle **out) {
   if (!h) return H2SP_ENOMEM;
   std::string err;
   auto t0 = std::chrono::steady_clock::now();
-  int st = build_plan(desc, h->plan, err, false);
+  auto plan = std::make_shared<Plan>();
+  int st = build_plan(desc, *plan, err, false);
   h->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (st != H2SP_OK) {
     g_cuda_err = err;
     delete h;
     return st;
   }
+  h->plan_ptr = plan;
+  h->structure_hash = structure_hash(desc, *plan);
   *out = h;
   return H2SP_OK;
 }
@@ -809,7 +886,7 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
   if (prec != H2SP_FP64 && prec != H2SP_FP32) return H2SP_EINVAL;
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   h->prof.stream = h->stream;
-  const Plan &p = h->plan;
+  const Plan &p = (*h->plan_ptr);
   cudaStream_t s = h->stream;
   try {
     const size_t esz = prec == H2SP_FP64 ? sizeof(double) : sizeof(float);
@@ -878,7 +955,7 @@ int h2sp_apply(h2sp_handle *h, int32_t op, int32_t nrhs, const double *in, int64
                h2sp_stream stream) {
   if (!h || !in || !out || nrhs <= 0) return H2SP_EINVAL;
   if (!h->device_ready) return H2SP_ESTATE;
-  const Plan &p = h->plan;
+  const Plan &p = (*h->plan_ptr);
   if (ldin < p.n || ldout < p.n) return H2SP_EINVAL;
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   h->prof.stream = h->stream;
@@ -917,7 +994,7 @@ int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *o, int32_t nrhs, const dou
                int64_t ldx, h2sp_solve_info *info, h2sp_stream stream) {
   if (!h || !o || !b || !x || nrhs <= 0 || nrhs > 64) return H2SP_EINVAL;
   if (!h->device_ready) return H2SP_ESTATE;
-  const Plan &p = h->plan;
+  const Plan &p = (*h->plan_ptr);
   if (ldb < p.n || ldx < p.n) return H2SP_EINVAL;
   if (o->mode != H2SP_DIRECT && o->mode != H2SP_IR && o->mode != H2SP_GMRES) return H2SP_EINVAL;
   if (h->prec < 0) return H2SP_ESTATE;
@@ -986,7 +1063,7 @@ int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *o, int32_t nrhs, const dou
 int h2sp_export_S(h2sp_handle *h, int64_t *node_size, int64_t *brow_ptr, int32_t *bcol_idx, int64_t *val_off,
                   double *vals, h2sp_stream stream) {
   if (!h) return H2SP_EINVAL;
-  const Plan &p = h->plan;
+  const Plan &p = (*h->plan_ptr);
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   if (node_size) std::copy(p.node_size.begin(), p.node_size.end(), node_size);
   if (brow_ptr) std::copy(p.brow_ptr.begin(), p.brow_ptr.end(), brow_ptr);
@@ -1005,7 +1082,7 @@ int h2sp_export_S(h2sp_handle *h, int64_t *node_size, int64_t *brow_ptr, int32_t
 
 int h2sp_export_Q(h2sp_handle *h, int32_t cluster, int32_t col, int64_t *m, double *q, h2sp_stream stream) {
   if (!h || !m) return H2SP_EINVAL;
-  const Plan &p = h->plan;
+  const Plan &p = (*h->plan_ptr);
   if (cluster < 0 || cluster >= p.ncl) return H2SP_EINVAL;
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   if (p.q_off[cluster] < 0) {
@@ -1029,7 +1106,7 @@ int h2sp_export_Q(h2sp_handle *h, int32_t cluster, int32_t col, int64_t *m, doub
 int h2sp_export_structure(h2sp_handle *h, int32_t *node_level, int32_t *node_cluster, int32_t *closure,
                           int32_t *order, int32_t *sn_ptr, int32_t *bnd_ptr, int32_t *bnd, int64_t *nbnd) {
   if (!h) return H2SP_EINVAL;
-  const Plan &p = h->plan;
+  const Plan &p = (*h->plan_ptr);
   if (node_level) std::copy(p.node_level.begin(), p.node_level.end(), node_level);
   if (node_cluster) std::copy(p.node_cluster.begin(), p.node_cluster.end(), node_cluster);
   if (closure) std::copy(p.closure.begin(), p.closure.end(), closure);
@@ -1043,7 +1120,7 @@ int h2sp_export_structure(h2sp_handle *h, int32_t *node_level, int32_t *node_clu
 
 int h2sp_query(const h2sp_handle *h, h2sp_stats *st) {
   if (!h || !st) return H2SP_EINVAL;
-  const Plan &p = h->plan;
+  const Plan &p = (*h->plan_ptr);
   std::memset(st, 0, sizeof(*st));
   st->n = p.n;
   st->depth = p.D;
@@ -1066,7 +1143,7 @@ int h2sp_h2_matvec_static(const h2sp_handle *h, int32_t nrhs, const double *x, i
                           h2sp_stream stream) {
   if (!h || !x || !y || nrhs <= 0) return H2SP_EINVAL;
   if (!h->device_ready) return H2SP_ESTATE;
-  const Plan &p = h->plan;
+  const Plan &p = (*h->plan_ptr);
   if (ldx < p.n || ldy < p.n) return H2SP_EINVAL;
   const int64_t ldh = std::max<int64_t>(p.xh_elems, 1);
   const int64_t need = 2 * ldh * 16;  // x^ and y^, 16 right-hand sides per pass

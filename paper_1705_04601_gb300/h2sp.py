@@ -76,6 +76,8 @@ KERNEL_CLASSES = ["gemm_update", "panel", "swap_trsm", "extend_add", "assemble",
 # name -> (restype, argtypes); every symbol of include/h2sp.h
 SIGNATURES = {
     "h2sp_sparsify": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.POINTER(Opts), _vp, ctypes.POINTER(_vp)]),
+    "h2sp_sparsify_analyzed": (ctypes.c_int, [_vp, ctypes.POINTER(Desc), ctypes.POINTER(Opts), _vp,
+                                              ctypes.POINTER(_vp)]),
     "h2sp_analyze": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.POINTER(_vp)]),
     "h2sp_factor": (ctypes.c_int, [_vp, ctypes.c_int32, _vp]),
     "h2sp_solve": (ctypes.c_int, [_vp, ctypes.POINTER(SolveOpts), ctypes.c_int32, _vp, ctypes.c_int64, _vp,
@@ -218,6 +220,16 @@ def h2sp_sparsify(inp: H2Input, stream=None) -> Handle:
     o = Opts(0)
     _check(lib().h2sp_sparsify(ctypes.byref(d), ctypes.byref(o), _stream(stream), ctypes.byref(out)),
            "h2sp_sparsify")
+    return Handle(out, inp)
+
+
+def h2sp_sparsify_analyzed(an: Handle, inp: H2Input, stream=None) -> Handle:
+    """h2sp_sparsify with the host analysis of `an` (same structure, new numbers)."""
+    out = _vp()
+    d = inp.desc()
+    o = Opts(0)
+    _check(lib().h2sp_sparsify_analyzed(an.ptr, ctypes.byref(d), ctypes.byref(o), _stream(stream),
+                                        ctypes.byref(out)), "h2sp_sparsify_analyzed")
     return Handle(out, inp)
 
 

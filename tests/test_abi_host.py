@@ -168,3 +168,38 @@ def test_forest_rejects_pairs_across_systems():
     with pytest.raises(H.H2spError) as e:
         H.h2sp_analyze(inp)
     assert e.value.status == H.H2SP_EINVAL
+
+
+def _with_fake_numbers(inp):
+    """Descriptor of `inp` with non-null numeric pointers that must never be
+    dereferenced (the calls below fail on the host before any launch)."""
+    d = inp.desc()
+    buf = (ctypes.c_double * 4)()
+    for nm in ("leaf_basis", "transfer", "coupling", "near_block"):
+        setattr(d, nm, ctypes.addressof(buf))
+    return d, buf
+
+
+def test_sparsify_analyzed_rejects_a_different_structure():
+    h = _make("log1k")
+    an = H.h2sp_analyze(H.H2Input(h, device=None))
+    out = H._vp()
+    o = H.Opts(0)
+    # another point set: different lists
+    h2, _ = synth.make_small(1024, kernel="log", leaf=32, tol=1e-8, seed=11)
+    d2, keep2 = _with_fake_numbers(H.H2Input(h2, device=None))
+    assert H.lib().h2sp_sparsify_analyzed(an.ptr, ctypes.byref(d2), ctypes.byref(o), None,
+                                          ctypes.byref(out)) == H.H2SP_EINVAL
+    # same lists, one close-block offset changed: only the fingerprint sees it
+    inp = H.H2Input(h, device=None)
+    inp.arrs["near_off"] = inp.arrs["near_off"].copy()
+    inp.arrs["near_off"][5] += 1
+    d3, keep3 = _with_fake_numbers(inp)
+    assert H.lib().h2sp_sparsify_analyzed(an.ptr, ctypes.byref(d3), ctypes.byref(o), None,
+                                          ctypes.byref(out)) == H.H2SP_EINVAL
+    # missing numbers
+    d4 = H.H2Input(h, device=None).desc()
+    assert H.lib().h2sp_sparsify_analyzed(an.ptr, ctypes.byref(d4), ctypes.byref(o), None,
+                                          ctypes.byref(out)) == H.H2SP_EINVAL
+    assert not out
+    an.close()

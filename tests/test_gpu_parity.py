@@ -314,3 +314,28 @@ def test_gmres_reaches_1e10(name, prec):
     res = np.linalg.norm(b - A @ xg, axis=0) / np.linalg.norm(b, axis=0)
     assert res.max() <= 2e-10
     hd.close()
+
+
+@pytest.mark.parametrize("name", ["log4k", "skew1k"])
+def test_sparsify_analyzed_matches_sparsify(name):
+    """The numeric phase on a shared host analysis gives the same S, Q and
+    solution as the full h2sp_sparsify, also after the analysis handle is gone."""
+    h, b, sp = case(name)
+    inp = H.H2Input(h)
+    full = H.h2sp_sparsify(inp)
+    an = H.h2sp_analyze(H.H2Input(h, device=None))
+    hd = H.h2sp_sparsify_analyzed(an, inp)
+    an.close()
+    Sf = H.h2sp_export_S(full)
+    Sa = H.h2sp_export_S(hd)
+    assert np.array_equal(Sf["brow_ptr"], Sa["brow_ptr"]) and np.array_equal(Sf["bcol_idx"], Sa["bcol_idx"])
+    assert np.array_equal(Sf["vals"], Sa["vals"])
+    H.h2sp_factor(hd, H.H2SP_FP64)
+    bt = dev(b)
+    xt = torch.empty_like(bt)
+    H.h2sp_solve(hd, bt, xt, mode=H.H2SP_DIRECT)
+    torch.cuda.synchronize()
+    xo = ofa.solve(h, sp, ofa.factor(h, sp), b)
+    assert np.linalg.norm(host(xt) - xo) / np.linalg.norm(xo) <= 1e-10
+    full.close()
+    hd.close()
