@@ -199,17 +199,26 @@ int h2sp_analyze(const h2sp_h2_desc *desc, h2sp_handle **out);
  * h2sp_factor -- block LU of S (the paper factors S with a sparse direct
  * method, §5.3-5.4): nested-dissection order along the cluster tree,
  * multifrontal elimination level by level, partial pivoting inside each
- * supernode's diagonal block.  `prec` selects FP64 or FP32 fronts.
- * Synchronises the stream; returns H2SP_ESINGULAR on a zero pivot.
+ * supernode's diagonal block.  `prec` selects FP64 or FP32 fronts; FP32
+ * trailing updates run on the tensor cores with operands split into two TF32
+ * terms (FP32-level products).  The next panel is factored on an internal
+ * high-priority stream while the rest of the update runs on an internal
+ * low-priority one; both are joined back to `stream` before the call
+ * returns.  Synchronises the stream; returns H2SP_ESINGULAR on a zero or
+ * non-finite pivot and H2SP_ETIMEOUT if a bounded device wait gave up.
  */
 int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream);
 
 /*
  * h2sp_solve -- x = A^{-1} b through S y = U^T b, x = V y (Eq. sp0), either
- * once (DIRECT, needs h2sp_factor) or iterated on the FP64 H^2 residual.
- * b (ldb >= n) and x (ldx >= n) are device arrays of nrhs columns; x may not
- * alias b.  `info` (host, may be NULL) receives iterations and the final
- * relative residual.  Synchronises the stream for IR / GMRES.
+ * once (DIRECT, needs h2sp_factor) or iterated on the FP64 H^2 residual
+ * (IR, or GMRES right-preconditioned by the factored S, §5.5).  b (ldb >= n)
+ * and x (ldx >= n) are device arrays of nrhs columns; x may not alias b.
+ * `info` (host, may be NULL) receives iterations and the final relative
+ * residual.  The triangular sweeps are one cooperative launch per level and
+ * direction whose row blocks wait (bounded) for the blocks they depend on;
+ * a wait that gives up makes the call return H2SP_ETIMEOUT.  Synchronises
+ * the stream.
  */
 int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *opts, int32_t nrhs, const double *b, int64_t ldb,
                double *x, int64_t ldx, h2sp_solve_info *info, h2sp_stream stream);
