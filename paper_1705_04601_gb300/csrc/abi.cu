@@ -755,15 +755,16 @@ int sparsify_numeric(h2sp_handle *h, const h2sp_h2_desc *desc, h2sp_stream strea
       for (const FrontLevel &L : h->flev) {
         int maxb = 0;
         for (int k = L.lo; k < L.hi; ++k) maxb = std::max<int>(maxb, (p.fronts[k].s + kSolveBlock - 1) / kSolveBlock);
+        // supernode items are pairs of row blocks: (b, b+1) forward, (b, b-1) backward
         h->chain_fwd_off.push_back(int(items.size()));
-        for (int b = 0; b < maxb; ++b)
+        for (int b = 0; b < maxb; b += 2)
           for (int k = L.lo; k < L.hi; ++k)
             if (b < (p.fronts[k].s + kSolveBlock - 1) / kSolveBlock) items.push_back(make_int2(k, b));
         for (int k = L.lo; k < L.hi; ++k)
           for (int q = 0; q < (p.fronts[k].b + kSolveBlock - 1) / kSolveBlock; ++q) items.push_back(make_int2(k, -(q + 1)));
         h->chain_fwd_n.push_back(int(items.size()) - h->chain_fwd_off.back());
         h->chain_bwd_off.push_back(int(items.size()));
-        for (int d = 0; d < maxb; ++d)
+        for (int d = 0; d < maxb; d += 2)
           for (int k = L.lo; k < L.hi; ++k) {
             const int nb = (p.fronts[k].s + kSolveBlock - 1) / kSolveBlock;
             if (d < nb) items.push_back(make_int2(k, nb - 1 - d));

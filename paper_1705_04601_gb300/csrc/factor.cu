@@ -1134,22 +1134,27 @@ inline int num_sms() {
 
 // ---------------- flag-synchronised block sweeps ----------------
 // One launch per elimination level and direction replaces the kBS-column
-// step launches.  Work items are row blocks: (front, b) for the kBS-row
-// block b of the supernode rows, and in the forward sweep (front, -(q+1)) for
-// the q-th kBS-row block of the boundary rows.  A CTA takes items in ticket
-// order and accumulates, left-looking, the contributions of the solution
-// blocks it depends on as their flags appear:
+// step launches.  Work items are row blocks: (front, b) for the supernode
+// rows of kBS-row blocks b and b+1 (forward) or b and b-1 (backward), and in
+// the forward sweep (front, -(q+1)) for the q-th kBS-row block of the
+// boundary rows.  A CTA takes items in ticket order and accumulates,
+// left-looking, the contributions of the solution blocks it depends on as
+// their flags appear:
 //   forward,  block b : w_b -= sum_{b' < b} L[b, b'] z_{b'},  z_b = L_bb^-1 w_b
 //   boundary, block q : w_q -= sum_{b'}    L[q, b'] z_{b'}   (added to y later)
 //   backward, block b : w_b -= sum_{b' > b} U[b, b'] x_{b'},  x_b = U_bb^-1 w_b
-// and then publishes its block (release store of the launch's epoch).  An item
-// depends only on items with smaller tickets, which are held by running or
-// finished CTAs of the same cooperative launch, so every wait ends; each wait
-// is still bounded (kChainSpinCap polls), after which the CTA raises an error
-// flag and leaves.
+// The two blocks of an item share the external contributions; the second
+// then takes the first's solution inside the CTA, so a hop between CTAs
+// (flag, release / acquire, reload) happens once per two blocks.  Each block
+// is published as soon as it is solved (release store of the launch's
+// epoch).  An item depends only on items with smaller tickets, which are held
+// by running or finished CTAs of the same cooperative launch, so every wait
+// ends; each wait is still bounded (kChainSpinCap polls), after which the CTA
+// raises an error flag and leaves.
 constexpr int kChainThreads = 256;
 constexpr uint32_t kChainSpinCap = 1u << 22;
-constexpr int kChainPre = kBS * kBS / kChainThreads;  // L values each thread prefetches per block
+constexpr int kChainSub = 2;                          // row blocks per supernode item
+constexpr int kChainPre = kBS * kBS / kChainThreads;  // values of one 64 x 64 block per thread
 
 __device__ __forceinline__ int ld_acquire_gpu(const int *p) {
   int v;
@@ -1160,6 +1165,25 @@ __device__ __forceinline__ void st_release_gpu(int *p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// bounded wait of thread 0 for flag == epoch; the verdict is shared through *s_ok
+__device__ __forceinline__ bool chain_wait(const int *flag, int epoch, int *err, int *s_ok) {
+  if (threadIdx.x == 0) {
+    int okv = 1;
+    uint32_t n = 0;
+    while (ld_acquire_gpu(flag) != epoch) {
+      if (++n > kChainSpinCap) {
+        okv = 0;
+        atomicOr(err, 4);
+        break;
+      }
+      __nanosleep(32);
+    }
+    *s_ok = okv;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
 template <typename T, bool Fwd>
 __global__ void __launch_bounds__(kChainThreads) k_chain(const FrontDev *__restrict__ fr, const int2 *__restrict__ items,
                                                          int nitems, int *__restrict__ ticket,
@@ -1167,8 +1191,8 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrontDev *__restr
                                                          int nrhs, T *__restrict__ work, T *__restrict__ zbuf,
                                                          const int64_t *__restrict__ work_off, int *__restrict__ flags,
                                                          int epoch, int *__restrict__ err) {
-  __shared__ __align__(16) T sL[kBS * kBS];       // block of L / U, column-major; then the inverted diagonal block
-  __shared__ __align__(16) T sZ[kBS * kMaxRhs];   // a solution block, sZ[k * kMaxRhs + c]
+  __shared__ __align__(16) T sL[kChainSub * kBS * kBS];  // blocks of L / U for both sub-blocks, column-major
+  __shared__ __align__(16) T sZ[kBS * kMaxRhs];           // a solution block, sZ[k * kMaxRhs + c]
   __shared__ int s_item, s_ok;
   const int tid = threadIdx.x, row = tid & (kBS - 1), g = tid >> 6;  // right-hand sides g, g+4, g+8, g+12
   for (;;) {
@@ -1184,51 +1208,80 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrontDev *__restr
     T *Z = zbuf + work_off[it.x];
     const int64_t lda = F.ld, ld = F.f;  // front matrix / work vectors
     const bool sn = it.y >= 0;
-    const int r0 = sn ? it.y * kBS : F.s + (-it.y - 1) * kBS;
-    const int rb = min(kBS, (sn ? F.s : F.f) - r0);
     const int nbs = (F.s + kBS - 1) / kBS;
     const int fbase = int(F.dinv_off / (2 * kBS * kBS));
-    // blocks this item depends on, in the order they are published
+    // the item's row blocks: sub u is block blk[u] (boundary items: one block of boundary rows)
+    int nsub, blk[kChainSub], r0[kChainSub], rb[kChainSub];
+    if (sn) {
+      nsub = Fwd ? min(kChainSub, nbs - it.y) : min(kChainSub, it.y + 1);
+#pragma unroll
+      for (int u = 0; u < kChainSub; ++u) {
+        blk[u] = Fwd ? it.y + u : it.y - u;
+        r0[u] = blk[u] * kBS;
+        rb[u] = u < nsub ? min(kBS, F.s - r0[u]) : 0;
+      }
+    } else {
+      nsub = 1;
+      blk[0] = -1;
+      r0[0] = F.s + (-it.y - 1) * kBS;
+      rb[0] = min(kBS, F.f - r0[0]);
+#pragma unroll
+      for (int u = 1; u < kChainSub; ++u) blk[u] = -1, r0[u] = 0, rb[u] = 0;
+    }
+    // external dependencies, in the order they are published
     const int b_first = Fwd ? 0 : nbs - 1;
     const int nblk = Fwd ? (sn ? it.y : nbs) : (nbs - 1 - it.y);
-    T acc[4];
+    T acc[kChainSub][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int c = g + 4 * q;
-      acc[q] = (row < rb && c < nrhs) ? W[(r0 + row) + int64_t(c) * ld] : T(0);
-    }
-    T pre[kChainPre];
+    for (int u = 0; u < kChainSub; ++u)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = g + 4 * q;
+        acc[u][q] = (row < rb[u] && c < nrhs) ? W[(r0[u] + row) + int64_t(c) * ld] : T(0);
+      }
+    T pre[kChainSub][kChainPre];
     auto load_block = [&](int bp) {
       const int c0 = bp * kBS, kb = min(kBS, F.s - c0);
 #pragma unroll
+      for (int u = 0; u < kChainSub; ++u)
+#pragma unroll
+        for (int e = 0; e < kChainPre; ++e) {
+          const int idx = tid + e * kChainThreads, k = idx / kBS, rr = idx % kBS;
+          pre[u][e] = (rr < rb[u] && k < kb) ? A[(r0[u] + rr) + int64_t(c0 + k) * lda] : T(0);
+        }
+    };
+    // the item's own inverted diagonal blocks and the block coupling its two
+    // sub-blocks do not depend on any other item: request them now, so that
+    // they are not on the chain's critical path
+    T preD[kChainSub][kChainPre], preI[kChainPre];
+    if (sn) {
+#pragma unroll
+      for (int u = 0; u < kChainSub; ++u) {
+        const T *Di = dinv + F.dinv_off + int64_t(max(blk[u], 0)) * 2 * kBS * kBS + (Fwd ? 0 : kBS * kBS);
+#pragma unroll
+        for (int e = 0; e < kChainPre; ++e) {
+          const int idx = tid + e * kChainThreads, rr = idx % kBS, k = idx / kBS;
+          preD[u][e] = (u < nsub && rr < rb[u] && k < rb[u]) ? Di[rr + k * kBS] : T(0);
+        }
+      }
+      const int c0 = max(blk[0], 0) * kBS;
+#pragma unroll
       for (int e = 0; e < kChainPre; ++e) {
         const int idx = tid + e * kChainThreads, k = idx / kBS, rr = idx % kBS;
-        pre[e] = (rr < rb && k < kb) ? A[(r0 + rr) + int64_t(c0 + k) * lda] : T(0);
+        preI[e] = (nsub > 1 && rr < rb[1] && k < rb[0]) ? A[(r0[1] + rr) + int64_t(c0 + k) * lda] : T(0);
       }
-    };
+    }
     bool ok = true;
     if (nblk > 0) load_block(b_first);
     for (int s = 0; s < nblk; ++s) {
       const int bp = Fwd ? s : nbs - 1 - s;
       __syncthreads();  // the previous block's sL / sZ are consumed
 #pragma unroll
-      for (int e = 0; e < kChainPre; ++e) sL[tid + e * kChainThreads] = pre[e];
+      for (int u = 0; u < kChainSub; ++u)
+#pragma unroll
+        for (int e = 0; e < kChainPre; ++e) sL[u * kBS * kBS + tid + e * kChainThreads] = pre[u][e];
       if (s + 1 < nblk) load_block(Fwd ? bp + 1 : bp - 1);  // in flight during the wait
-      if (tid == 0) {
-        int okv = 1;
-        uint32_t n = 0;
-        while (ld_acquire_gpu(&flags[fbase + bp]) != epoch) {
-          if (++n > kChainSpinCap) {
-            okv = 0;
-            atomicOr(err, 4);
-            break;
-          }
-          __nanosleep(32);
-        }
-        s_ok = okv;
-      }
-      __syncthreads();
-      if (!s_ok) {
+      if (!chain_wait(&flags[fbase + bp], epoch, err, &s_ok)) {
         ok = false;
         break;
       }
@@ -1238,11 +1291,17 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrontDev *__restr
         sZ[k * kMaxRhs + c] = (k < kb && c < nrhs) ? __ldcg(&Z[(bp * kBS + k) + int64_t(c) * ld]) : T(0);
       }
       __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
       for (int k = 0; k < kBS; ++k) {
-        const T a = sL[k * kBS + row];
+        T a[kChainSub];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] -= a * sZ[k * kMaxRhs + g + 4 * q];
+        for (int u = 0; u < kChainSub; ++u) a[u] = sL[u * kBS * kBS + k * kBS + row];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const T z = sZ[k * kMaxRhs + g + 4 * q];
+#pragma unroll
+          for (int u = 0; u < kChainSub; ++u) acc[u][q] -= a[u] * z;
+        }
       }
     }
     if (!ok) return;  // uniform: every thread saw s_ok == 0
@@ -1250,36 +1309,54 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrontDev *__restr
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int c = g + 4 * q;
-        if (row < rb && c < nrhs) W[(r0 + row) + int64_t(c) * ld] = acc[q];
+        if (row < rb[0] && c < nrhs) W[(r0[0] + row) + int64_t(c) * ld] = acc[0][q];
       }
       continue;
     }
-    // diagonal block: x = D^-1 w with the inverted kBS x kBS block
-    __syncthreads();
-    const T *Di = dinv + F.dinv_off + int64_t(it.y) * 2 * kBS * kBS + (Fwd ? 0 : kBS * kBS);
-    for (int e = tid; e < kBS * kBS; e += kChainThreads) {
-      const int rr = e % kBS, k = e / kBS;
-      sL[e] = (rr < rb && k < rb) ? Di[rr + k * kBS] : T(0);
-    }
+    // the item's own blocks: solve, publish, and hand the solution to the next sub-block
 #pragma unroll
-    for (int q = 0; q < 4; ++q) sZ[row * kMaxRhs + g + 4 * q] = row < rb ? acc[q] : T(0);
-    __syncthreads();
-    T x[4] = {T(0), T(0), T(0), T(0)};
+    for (int u = 0; u < kChainSub; ++u) {
+      if (u >= nsub) break;
+      if (u > 0) {
+        // acc[u] -= (L or U)[block u, block u-1] * (solution of block u-1, still in sZ)
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < kChainPre; ++e) sL[tid + e * kChainThreads] = preI[e];
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < kBS; ++k) {
+          const T a = sL[k * kBS + row];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[u][q] -= a * sZ[k * kMaxRhs + g + 4 * q];
+        }
+      }
+      // x = D^-1 w with the inverted kBS x kBS block
+      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < kChainPre; ++e) sL[tid + e * kChainThreads] = preD[u][e];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sZ[row * kMaxRhs + g + 4 * q] = row < rb[u] ? acc[u][q] : T(0);
+      __syncthreads();
+      T x[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll 8
-    for (int k = 0; k < kBS; ++k) {
-      const T a = sL[k * kBS + row];
+      for (int k = 0; k < kBS; ++k) {
+        const T a = sL[k * kBS + row];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) x[q] += a * sZ[k * kMaxRhs + g + 4 * q];
-    }
+        for (int q = 0; q < 4; ++q) x[q] += a * sZ[k * kMaxRhs + g + 4 * q];
+      }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int c = g + 4 * q;
-      if (row < rb && c < nrhs) Z[(r0 + row) + int64_t(c) * ld] = x[q];
-    }
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      st_release_gpu(&flags[fbase + it.y], epoch);
+      for (int q = 0; q < 4; ++q) {
+        const int c = g + 4 * q;
+        if (row < rb[u] && c < nrhs) Z[(r0[u] + row) + int64_t(c) * ld] = x[q];
+      }
+      __syncthreads();  // every Z store issued; sZ free
+      if (tid == 0) {
+        __threadfence();
+        st_release_gpu(&flags[fbase + blk[u]], epoch);
+      }
+      // keep this block's solution in sZ for the next sub-block
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sZ[row * kMaxRhs + g + 4 * q] = row < rb[u] ? x[q] : T(0);
     }
   }
 }

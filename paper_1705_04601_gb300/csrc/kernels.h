@@ -73,7 +73,8 @@ cudaError_t launch_invert_diag(const FrontDev *fr, int nfront, int max_s, const 
                                Prof *prof);
 // Work lists of the flag-synchronised sweeps (one launch per level and
 // direction): items (front, row block) of level li are items[fwd_off[li] ..
-// fwd_off[li] + fwd_n[li]) in dependency order, likewise for the backward
+// fwd_off[li] + fwd_n[li]) in dependency order (a supernode item covers row
+// blocks b and b+1 forward, b and b-1 backward), likewise for the backward
 // sweep; one flag per supernode row block of every front (index
 // dinv_off / (2 kSolveBlock^2) + block), published with the launch's epoch;
 // two ticket counters per level, zero before each sweep; err |= 4 on a
