@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -52,10 +53,61 @@ struct FrontLevel {
   double lu_elems = 0.0; // sum of s^2/2 + s*b (factor elements one sweep reads)
 };
 
+// Device copies of everything the numeric phases read that depends only on
+// the structure (work items of every level, apply items, the VBR index of S,
+// the H^2 index arrays, fronts, extend-add maps, assembly items, sweep work
+// lists).  Built once per analysis, on the first numeric sparsification, and
+// shared by every handle planned from it; freed with the last of them.
+struct StructureDev {
+  int device = -1;
+  std::vector<void *> allocs;
+  std::vector<LevelDev> lv;  // item arrays only
+  std::vector<double> x_flops;
+  int max_rank = 1;
+  int64_t max_width = 0;
+  int64_t *top_src = nullptr, *top_dst = nullptr;
+  int32_t *top_len = nullptr;
+  int ntop = 0;
+  int64_t *brow_ptr = nullptr, *val_off = nullptr, *node_off = nullptr;
+  int32_t *bcol = nullptr;
+  H2Dev h2{};  // structure pointers only
+  int32_t *child_start = nullptr, *child_cnt = nullptr;
+  double near_bytes = 0.0, mv_flops_per_rhs = 0.0;
+  int64_t *seg_ptr = nullptr;
+  int nseg = 1;
+  FrontDev *fr = nullptr;
+  int32_t *fidx = nullptr, *fmap = nullptr;
+  AItem *asm_items = nullptr;
+  int max_s_all = 0;
+  std::vector<FrontLevel> flev;
+  int2 *chain_items = nullptr;
+  std::vector<int> chain_fwd_off, chain_fwd_n, chain_bwd_off, chain_bwd_n;
+  int nflags = 0;
+  template <class T>
+  T *upload(const std::vector<T> &v) {
+    void *d = nullptr;
+    ck(cudaMalloc(&d, std::max<size_t>(v.size(), 1) * sizeof(T)));
+    allocs.push_back(d);
+    if (!v.empty()) ck(cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return static_cast<T *>(d);
+  }
+  ~StructureDev() {
+    for (void *q : allocs) cudaFree(q);
+  }
+};
+
+// the shared slot of one analysis
+struct StructureCell {
+  std::mutex m;
+  std::shared_ptr<StructureDev> dev;
+};
+
 }  // namespace
 
 struct h2sp_handle {
   std::shared_ptr<const Plan> plan_ptr;  // host analysis, shared with the handles planned from it
+  std::shared_ptr<StructureCell> cell;   // its device copy (filled on first use), shared likewise
+  std::shared_ptr<StructureDev> sdev;    // kept alive while this handle lives
   uint64_t structure_hash = 0;          // fingerprint of the descriptor's structure arrays
   cudaStream_t stream = nullptr;
   std::vector<void *> allocs;
@@ -533,7 +585,178 @@ uint64_t structure_hash(const h2sp_h2_desc *d, const Plan &p) {
   return h;
 }
 
-// numeric part of the sparsification: device buffers, uploads and kernels
+// device copies of the structure (see StructureDev); synchronous uploads, once per analysis
+std::shared_ptr<StructureDev> build_structure(const Plan &p) {
+  auto sd = std::make_shared<StructureDev>();
+  cudaGetDevice(&sd->device);
+  const int L = p.lstop;
+  for (int t = 0; t < p.ncl; ++t) sd->max_rank = std::max(sd->max_rank, p.rank[t]);
+  // work items of every level
+  const int nlw = int(p.lw.size());
+  sd->lv.assign(std::max(nlw, 1), LevelDev());
+  for (int l = 0; l < nlw; ++l) {
+    const LevelWork &w = p.lw[l];
+    LevelDev &d = sd->lv[l];
+    d.q = sd->upload(w.q);
+    d.nq = int(w.q.size());
+    d.w = sd->upload(w.w);
+    d.nw = int(w.w.size());
+    d.c = sd->upload(w.c);
+    d.nc = int(w.c.size());
+    d.x = sd->upload(w.x);
+    d.nx = int(w.x.size());
+    double xf = 0.0;
+    for (const XItem &it : w.x)
+      xf += (it.qR >= 0 ? 2.0 * it.rows * it.cols * it.cols : 0.0) + (it.qL >= 0 ? 2.0 * it.rows * it.rows * it.cols : 0.0);
+    sd->x_flops.push_back(xf);
+    if (!p.sym) {
+      d.qc = sd->upload(w.qc);
+      d.wc = sd->upload(w.wc);
+    }
+  }
+  // apply items
+  {
+    int64_t width = 0;
+    for (int l = 0; l <= L; ++l) {
+      int64_t wl = 0;
+      for (int t = p.level_ptr[p.D - l]; t < p.level_ptr[p.D - l + 1]; ++t) wl += p.m[t];
+      width = std::max(width, wl);
+    }
+    sd->max_width = width;
+    for (int l = 0; l < L; ++l) {
+      std::vector<ApItem> ap;
+      for (int t = p.level_ptr[p.D - l]; t < p.level_ptr[p.D - l + 1]; ++t) {
+        if (p.m[t] == 0) continue;
+        ApItem a{};
+        a.q = p.q_off[t];
+        a.m = int32_t(p.m[t]);
+        a.kp = int32_t(p.kp[t]);
+        a.xin = p.xoff[t];
+        a.yout = p.d[t] > 0 ? p.node_off[p.node_of[t]] : -1;
+        a.xout = p.kp[t] > 0 ? p.xoff[p.parent[t]] + p.off[t] : -1;
+        ap.push_back(a);
+      }
+      sd->lv[l].ap = sd->upload(ap);
+      sd->lv[l].nap = int(ap.size());
+    }
+    std::vector<int64_t> ts, td;
+    std::vector<int32_t> tl;
+    for (int t = p.level_ptr[p.D - L]; t < p.level_ptr[p.D - L + 1]; ++t)
+      if (p.m[t] > 0) {
+        ts.push_back(L == 0 ? p.h_begin[t] : p.xoff[t]);
+        td.push_back(p.node_off[p.node_of[t]]);
+        tl.push_back(int32_t(p.m[t]));
+      }
+    sd->top_src = sd->upload(ts);
+    sd->top_dst = sd->upload(td);
+    sd->top_len = sd->upload(tl);
+    sd->ntop = int(ts.size());
+  }
+  // S structure, H^2 structure
+  sd->brow_ptr = sd->upload(p.brow_ptr);
+  sd->bcol = sd->upload(p.bcol);
+  sd->val_off = sd->upload(p.val_off);
+  sd->node_off = sd->upload(p.node_off);
+  {
+    H2Dev &g = sd->h2;
+    g.begin = sd->upload(p.h_begin);
+    g.size = sd->upload(p.h_size);
+    g.rank = sd->upload(p.rank);
+    g.parent = sd->upload(p.parent);
+    g.leaf_basis_off = sd->upload(p.leaf_basis_off);
+    g.transfer_off = sd->upload(p.transfer_off);
+    g.coupling_off = sd->upload(p.coupling_off);
+    g.near_off = sd->upload(p.near_off);
+    g.col_leaf_basis_off = p.sym ? nullptr : sd->upload(p.col_leaf_basis_off);
+    g.col_transfer_off = p.sym ? nullptr : sd->upload(p.col_transfer_off);
+    g.far_ptr = sd->upload(p.far_ptr);
+    g.near_ptr = sd->upload(p.near_ptr);
+    g.far_col = sd->upload(p.far_col);
+    g.near_col = sd->upload(p.near_col);
+    g.xh_off = sd->upload(p.xh_off);
+    g.leaf0 = p.level_ptr[p.D];
+    std::vector<int32_t> cs(p.ncl, 0), cc(p.ncl, 0);
+    for (int c = p.ncl - 1; c >= p.level_ptr[1]; --c) {  // every non-root cluster
+      cs[p.parent[c]] = c;
+      cc[p.parent[c]]++;
+    }
+    sd->child_start = sd->upload(cs);
+    sd->child_cnt = sd->upload(cc);
+    // FP64 multiply-adds per right-hand side of one product: close blocks,
+    // couplings, the leaf bases (up and down) and the transfers (up and down)
+    double mv = 0.0;
+    for (int lf = 0; lf < p.nleaf; ++lf) {
+      const int t = p.level_ptr[p.D] + lf;
+      for (int64_t z = p.near_ptr[lf]; z < p.near_ptr[lf + 1]; ++z) {
+        const double e = double(p.h_size[t]) * double(p.h_size[p.near_col[z]]);
+        sd->near_bytes += 8.0 * e;
+        mv += e;
+      }
+      mv += 2.0 * double(p.h_size[t]) * p.rank[t];
+    }
+    for (int t = 0; t < p.ncl; ++t) {
+      for (int64_t z = p.far_ptr[t]; z < p.far_ptr[t + 1]; ++z) mv += double(p.rank[t]) * p.rank[p.far_col[z]];
+      if (t >= p.level_ptr[1]) mv += 2.0 * double(p.rank[t]) * p.rank[p.parent[t]];
+    }
+    sd->mv_flops_per_rhs = 2.0 * mv;
+    std::vector<int64_t> sp(1, 0);
+    for (int r = 0; r < p.level_ptr[1]; ++r) sp.push_back(p.h_begin[r] + p.h_size[r]);
+    sd->nseg = int(sp.size()) - 1;
+    sd->seg_ptr = sd->upload(sp);
+  }
+  // symbolic factorization
+  {
+    std::vector<FrontDev> fd(p.fronts.size());
+    for (size_t k = 0; k < p.fronts.size(); ++k) {
+      const Front &F = p.fronts[k];
+      fd[k] = FrontDev{F.off, F.piv_off, F.idx_off, F.map_off, F.dinv_off, F.s, F.b, F.f, F.parent, F.ld};
+      sd->max_s_all = std::max(sd->max_s_all, F.s);
+    }
+    sd->fr = sd->upload(fd);
+    sd->fidx = sd->upload(p.front_idx);
+    sd->fmap = sd->upload(p.front_map);
+    sd->asm_items = sd->upload(p.assemble);
+    for (size_t i = 0; i + 1 < p.front_level_ptr.size(); ++i) {
+      FrontLevel fl{p.front_level_ptr[i], p.front_level_ptr[i + 1], 0, 0, 0};
+      for (int k = fl.lo; k < fl.hi; ++k) {
+        const Front &F = p.fronts[k];
+        fl.max_s = std::max(fl.max_s, F.s);
+        fl.max_f = std::max(fl.max_f, F.f);
+        fl.max_b = std::max(fl.max_b, F.b);
+        fl.b2 += double(F.b) * F.b;
+        fl.lu_elems += 0.5 * double(F.s) * F.s + double(F.s) * F.b;
+      }
+      sd->flev.push_back(fl);
+    }
+    // row-block work lists of the sweeps, in dependency order per level
+    std::vector<int2> items;
+    for (const Front &F : p.fronts) sd->nflags += int((F.s + kSolveBlock - 1) / kSolveBlock);
+    for (const FrontLevel &L : sd->flev) {
+      int maxb = 0;
+      for (int k = L.lo; k < L.hi; ++k) maxb = std::max<int>(maxb, (p.fronts[k].s + kSolveBlock - 1) / kSolveBlock);
+      // supernode items are pairs of row blocks: (b, b+1) forward, (b, b-1) backward
+      sd->chain_fwd_off.push_back(int(items.size()));
+      for (int b = 0; b < maxb; b += 2)
+        for (int k = L.lo; k < L.hi; ++k)
+          if (b < (p.fronts[k].s + kSolveBlock - 1) / kSolveBlock) items.push_back(make_int2(k, b));
+      for (int k = L.lo; k < L.hi; ++k)
+        for (int q = 0; q < (p.fronts[k].b + kSolveBlock - 1) / kSolveBlock; ++q) items.push_back(make_int2(k, -(q + 1)));
+      sd->chain_fwd_n.push_back(int(items.size()) - sd->chain_fwd_off.back());
+      sd->chain_bwd_off.push_back(int(items.size()));
+      for (int d = 0; d < maxb; d += 2)
+        for (int k = L.lo; k < L.hi; ++k) {
+          const int nb = (p.fronts[k].s + kSolveBlock - 1) / kSolveBlock;
+          if (d < nb) items.push_back(make_int2(k, nb - 1 - d));
+        }
+      sd->chain_bwd_n.push_back(int(items.size()) - sd->chain_bwd_off.back());
+    }
+    sd->chain_items = sd->upload(items);
+  }
+  return sd;
+}
+
+// numeric part of the sparsification: the handle's buffers and the kernels,
+// on the (shared) device copy of the structure
 int sparsify_numeric(h2sp_handle *h, const h2sp_h2_desc *desc, h2sp_stream stream, h2sp_handle **out) {
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   h->prof.stream = h->stream;
@@ -547,6 +770,14 @@ int sparsify_numeric(h2sp_handle *h, const h2sp_h2_desc *desc, h2sp_stream strea
   cudaStream_t s = h->stream;
   try {
     init_pool_once();
+    {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      std::lock_guard<std::mutex> lock(h->cell->m);
+      if (!h->cell->dev || h->cell->dev->device != dev) h->cell->dev = build_structure(p);
+      h->sdev = h->cell->dev;
+    }
+    const StructureDev &sd = *h->sdev;
     // ---- owned buffers ----
     h->Q = h->alloc<double>(size_t(p.q_elems));
     h->Rr = h->alloc<double>(size_t(p.rr_elems));
@@ -571,30 +802,14 @@ int sparsify_numeric(h2sp_handle *h, const h2sp_h2_desc *desc, h2sp_stream strea
       ck(cudaMemsetAsync(h->RPbuf[l], 0, sizeof(double) * size_t(std::max<int64_t>(p.rp_elems[l], 1)), s));
       ck(cudaMemsetAsync(h->CPbuf[l], 0, sizeof(double) * size_t(std::max<int64_t>(p.cp_elems[l], 1)), s));
     }
-    // ---- per-level work items ----
+    // ---- per-level buffers and source / destination tables ----
     const int nlw = int(p.lw.size());
-    h->lv.assign(std::max(nlw, 1), LevelDev());
-    int max_rank = 1;
-    for (int t = 0; t < p.ncl; ++t) max_rank = std::max(max_rank, p.rank[t]);
+    h->lv = sd.lv;
+    h->x_flops = sd.x_flops;
+    const int max_rank = sd.max_rank;
     for (int l = 0; l < nlw; ++l) {
       const LevelWork &w = p.lw[l];
       LevelDev &d = h->lv[l];
-      d.q = h->upload(w.q);
-      d.nq = int(w.q.size());
-      d.w = h->upload(w.w);
-      d.nw = int(w.w.size());
-      d.c = h->upload(w.c);
-      d.nc = int(w.c.size());
-      d.x = h->upload(w.x);
-      d.nx = int(w.x.size());
-      double xf = 0.0;
-      for (const XItem &it : w.x)
-        xf += (it.qR >= 0 ? 2.0 * it.rows * it.cols * it.cols : 0.0) + (it.qL >= 0 ? 2.0 * it.rows * it.rows * it.cols : 0.0);
-      h->x_flops.push_back(xf);
-      if (!p.sym) {
-        d.qc = h->upload(w.qc);
-        d.wc = h->upload(w.wc);
-      }
       if (l >= 1) {
         d.W = h->alloc<double>(size_t(w.w_elems));
         if (!p.sym) d.Wc = h->alloc<double>(size_t(w.wc_elems));
@@ -625,159 +840,48 @@ int sparsify_numeric(h2sp_handle *h, const h2sp_h2_desc *desc, h2sp_stream strea
       ck(launch_transform(d.x, d.nx, const_cast<const double *const *>(d.src_base), h->Q, h->Qc, d.dst_base, s,
                             &h->prof, l < int(h->x_flops.size()) ? h->x_flops[l] : 0.0));
     }
-    // ---- apply items ----
-    {
-      int64_t width = 0;
-      for (int l = 0; l <= L; ++l) {
-        int64_t wl = 0;
-        for (int t = p.level_ptr[p.D - l]; t < p.level_ptr[p.D - l + 1]; ++t) wl += p.m[t];
-        width = std::max(width, wl);
-      }
-      h->max_width = width;
-      for (int l = 0; l < L; ++l) {
-        std::vector<ApItem> ap;
-        for (int t = p.level_ptr[p.D - l]; t < p.level_ptr[p.D - l + 1]; ++t) {
-          if (p.m[t] == 0) continue;
-          ApItem a{};
-          a.q = p.q_off[t];
-          a.m = int32_t(p.m[t]);
-          a.kp = int32_t(p.kp[t]);
-          a.xin = p.xoff[t];
-          a.yout = p.d[t] > 0 ? p.node_off[p.node_of[t]] : -1;
-          a.xout = p.kp[t] > 0 ? p.xoff[p.parent[t]] + p.off[t] : -1;
-          ap.push_back(a);
-        }
-        h->lv[l].ap = h->upload(ap);
-        h->lv[l].nap = int(ap.size());
-      }
-      std::vector<int64_t> ts, td;
-      std::vector<int32_t> tl;
-      for (int t = p.level_ptr[p.D - L]; t < p.level_ptr[p.D - L + 1]; ++t)
-        if (p.m[t] > 0) {
-          ts.push_back(L == 0 ? p.h_begin[t] : p.xoff[t]);
-          td.push_back(p.node_off[p.node_of[t]]);
-          tl.push_back(int32_t(p.m[t]));
-        }
-      h->top_src = h->upload(ts);
-      h->top_dst = h->upload(td);
-      h->top_len = h->upload(tl);
-      h->ntop = int(ts.size());
-    }
-    // ---- S structure, H^2 structure ----
-    h->brow_ptr = h->upload(p.brow_ptr);
-    h->bcol = h->upload(p.bcol);
-    h->val_off = h->upload(p.val_off);
-    h->node_off = h->upload(p.node_off);
-    {
-      H2Dev &g = h->h2;
-      g.begin = h->upload(p.h_begin);
-      g.size = h->upload(p.h_size);
-      g.rank = h->upload(p.rank);
-      g.parent = h->upload(p.parent);
-      g.leaf_basis_off = h->upload(p.leaf_basis_off);
-      g.transfer_off = h->upload(p.transfer_off);
-      g.coupling_off = h->upload(p.coupling_off);
-      g.near_off = h->upload(p.near_off);
-      g.col_leaf_basis_off = p.sym ? nullptr : h->upload(p.col_leaf_basis_off);
-      g.col_transfer_off = p.sym ? nullptr : h->upload(p.col_transfer_off);
-      g.far_ptr = h->upload(p.far_ptr);
-      g.near_ptr = h->upload(p.near_ptr);
-      g.far_col = h->upload(p.far_col);
-      g.near_col = h->upload(p.near_col);
-      g.xh_off = h->upload(p.xh_off);
-      g.leaf_basis = h->leaf_basis;
-      g.transfer = h->transfer;
-      g.coupling = h->coupling;
-      g.near_block = h->near_block;
-      g.col_leaf_basis = h->col_leaf_basis;
-      g.col_transfer = h->col_transfer;
-      g.leaf0 = p.level_ptr[p.D];
-      std::vector<int32_t> cs(p.ncl, 0), cc(p.ncl, 0);
-      for (int c = p.ncl - 1; c >= p.level_ptr[1]; --c) {  // every non-root cluster
-        cs[p.parent[c]] = c;
-        cc[p.parent[c]]++;
-      }
-      h->child_start = h->upload(cs);
-      h->child_cnt = h->upload(cc);
-      // FP64 multiply-adds per right-hand side of one product: close blocks,
-      // couplings, the leaf bases (up and down) and the transfers (up and down)
-      double mv = 0.0;
-      for (int lf = 0; lf < p.nleaf; ++lf) {
-        const int t = p.level_ptr[p.D] + lf;
-        for (int64_t z = p.near_ptr[lf]; z < p.near_ptr[lf + 1]; ++z) {
-          const double e = double(p.h_size[t]) * double(p.h_size[p.near_col[z]]);
-          h->near_bytes += 8.0 * e;
-          mv += e;
-        }
-        mv += 2.0 * double(p.h_size[t]) * p.rank[t];
-      }
-      for (int t = 0; t < p.ncl; ++t) {
-        for (int64_t z = p.far_ptr[t]; z < p.far_ptr[t + 1]; ++z) mv += double(p.rank[t]) * p.rank[p.far_col[z]];
-        if (t >= p.level_ptr[1]) mv += 2.0 * double(p.rank[t]) * p.rank[p.parent[t]];
-      }
-      h->mv_flops_per_rhs = 2.0 * mv;
-      h->xh = h->alloc<double>(size_t(std::max<int64_t>(p.xh_elems, 1)) * 16);
-      h->yh = h->alloc<double>(size_t(std::max<int64_t>(p.xh_elems, 1)) * 16);
-      std::vector<int64_t> sp(1, 0);
-      for (int r = 0; r < p.level_ptr[1]; ++r) sp.push_back(p.h_begin[r] + p.h_size[r]);
-      h->nseg = int(sp.size()) - 1;
-      h->seg_ptr = h->upload(sp);
-      h->norms = h->alloc<double>(size_t(h->nseg) * 64);
-    }
-    // ---- symbolic factorization uploads ----
-    {
-      std::vector<FrontDev> fd(p.fronts.size());
-      for (size_t k = 0; k < p.fronts.size(); ++k) {
-        const Front &F = p.fronts[k];
-        fd[k] = FrontDev{F.off, F.piv_off, F.idx_off, F.map_off, F.dinv_off, F.s, F.b, F.f, F.parent, F.ld};
-        h->max_s_all = std::max(h->max_s_all, F.s);
-      }
-      h->fr = h->upload(fd);
-      h->fidx = h->upload(p.front_idx);
-      h->fmap = h->upload(p.front_map);
-      h->asm_items = h->upload(p.assemble);
-      for (size_t i = 0; i + 1 < p.front_level_ptr.size(); ++i) {
-        FrontLevel fl{p.front_level_ptr[i], p.front_level_ptr[i + 1], 0, 0, 0};
-        for (int k = fl.lo; k < fl.hi; ++k) {
-          const Front &F = p.fronts[k];
-          fl.max_s = std::max(fl.max_s, F.s);
-          fl.max_f = std::max(fl.max_f, F.f);
-          fl.max_b = std::max(fl.max_b, F.b);
-          fl.b2 += double(F.b) * F.b;
-          fl.lu_elems += 0.5 * double(F.s) * F.s + double(F.s) * F.b;
-        }
-        h->flev.push_back(fl);
-      }
-      // row-block work lists of the sweeps, in dependency order per level
-      std::vector<int2> items;
-      int nflags = 0;
-      for (const Front &F : p.fronts) nflags += int((F.s + kSolveBlock - 1) / kSolveBlock);
-      for (const FrontLevel &L : h->flev) {
-        int maxb = 0;
-        for (int k = L.lo; k < L.hi; ++k) maxb = std::max<int>(maxb, (p.fronts[k].s + kSolveBlock - 1) / kSolveBlock);
-        // supernode items are pairs of row blocks: (b, b+1) forward, (b, b-1) backward
-        h->chain_fwd_off.push_back(int(items.size()));
-        for (int b = 0; b < maxb; b += 2)
-          for (int k = L.lo; k < L.hi; ++k)
-            if (b < (p.fronts[k].s + kSolveBlock - 1) / kSolveBlock) items.push_back(make_int2(k, b));
-        for (int k = L.lo; k < L.hi; ++k)
-          for (int q = 0; q < (p.fronts[k].b + kSolveBlock - 1) / kSolveBlock; ++q) items.push_back(make_int2(k, -(q + 1)));
-        h->chain_fwd_n.push_back(int(items.size()) - h->chain_fwd_off.back());
-        h->chain_bwd_off.push_back(int(items.size()));
-        for (int d = 0; d < maxb; d += 2)
-          for (int k = L.lo; k < L.hi; ++k) {
-            const int nb = (p.fronts[k].s + kSolveBlock - 1) / kSolveBlock;
-            if (d < nb) items.push_back(make_int2(k, nb - 1 - d));
-          }
-        h->chain_bwd_n.push_back(int(items.size()) - h->chain_bwd_off.back());
-      }
-      h->chain_items = h->upload(items);
-      h->chain_flags = h->alloc<int>(size_t(std::max(nflags, 1)));
-      ck(cudaMemsetAsync(h->chain_flags, 0, sizeof(int) * size_t(std::max(nflags, 1)), h->stream));
-      h->chain_tickets = h->alloc<int>(2 * std::max<size_t>(h->flev.size(), 1));
-      h->serr = h->alloc<int>(1);
-      ck(cudaMemsetAsync(h->serr, 0, sizeof(int), h->stream));
-    }
+    // ---- structure views for the applies, products, factor and solves ----
+    h->max_width = sd.max_width;
+    h->top_src = sd.top_src;
+    h->top_dst = sd.top_dst;
+    h->top_len = sd.top_len;
+    h->ntop = sd.ntop;
+    h->brow_ptr = sd.brow_ptr;
+    h->bcol = sd.bcol;
+    h->val_off = sd.val_off;
+    h->node_off = sd.node_off;
+    h->h2 = sd.h2;
+    h->h2.leaf_basis = h->leaf_basis;
+    h->h2.transfer = h->transfer;
+    h->h2.coupling = h->coupling;
+    h->h2.near_block = h->near_block;
+    h->h2.col_leaf_basis = h->col_leaf_basis;
+    h->h2.col_transfer = h->col_transfer;
+    h->child_start = sd.child_start;
+    h->child_cnt = sd.child_cnt;
+    h->near_bytes = sd.near_bytes;
+    h->mv_flops_per_rhs = sd.mv_flops_per_rhs;
+    h->xh = h->alloc<double>(size_t(std::max<int64_t>(p.xh_elems, 1)) * 16);
+    h->yh = h->alloc<double>(size_t(std::max<int64_t>(p.xh_elems, 1)) * 16);
+    h->nseg = sd.nseg;
+    h->seg_ptr = sd.seg_ptr;
+    h->norms = h->alloc<double>(size_t(h->nseg) * 64);
+    h->fr = sd.fr;
+    h->fidx = sd.fidx;
+    h->fmap = sd.fmap;
+    h->asm_items = sd.asm_items;
+    h->max_s_all = sd.max_s_all;
+    h->flev = sd.flev;
+    h->chain_items = sd.chain_items;
+    h->chain_fwd_off = sd.chain_fwd_off;
+    h->chain_fwd_n = sd.chain_fwd_n;
+    h->chain_bwd_off = sd.chain_bwd_off;
+    h->chain_bwd_n = sd.chain_bwd_n;
+    h->chain_flags = h->alloc<int>(size_t(std::max(sd.nflags, 1)));
+    ck(cudaMemsetAsync(h->chain_flags, 0, sizeof(int) * size_t(std::max(sd.nflags, 1)), h->stream));
+    h->chain_tickets = h->alloc<int>(2 * std::max<size_t>(h->flev.size(), 1));
+    h->serr = h->alloc<int>(1);
+    ck(cudaMemsetAsync(h->serr, 0, sizeof(int), h->stream));
     ck(cudaGetLastError());
   } catch (const CudaFail &f) {
     h->release();
@@ -831,6 +935,7 @@ int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream s
     return st;
   }
   h->plan_ptr = plan;
+  h->cell = std::make_shared<StructureCell>();
   h->structure_hash = structure_hash(desc, *plan);
   return sparsify_numeric(h, desc, stream, out);
 }
@@ -840,7 +945,7 @@ int h2sp_sparsify_analyzed(const h2sp_handle *an, const h2sp_h2_desc *desc, cons
   (void)opts;
   if (!out) return H2SP_EINVAL;
   *out = nullptr;
-  if (!an || !an->plan_ptr || !desc) return H2SP_EINVAL;
+  if (!an || !an->plan_ptr || !an->cell || !desc) return H2SP_EINVAL;
   const Plan &ap = *an->plan_ptr;
   // same structure as the analysed descriptor (sizes first, then every structure array)
   if (desc->n != ap.n || desc->depth != ap.D || !desc->level_ptr || !desc->far_ptr || !desc->near_ptr) return H2SP_EINVAL;
@@ -854,6 +959,7 @@ int h2sp_sparsify_analyzed(const h2sp_handle *an, const h2sp_h2_desc *desc, cons
   h2sp_handle *h = new (std::nothrow) h2sp_handle();
   if (!h) return H2SP_ENOMEM;
   h->plan_ptr = an->plan_ptr;
+  h->cell = an->cell;
   h->structure_hash = an->structure_hash;
   h->plan_seconds = 0.0;
   return sparsify_numeric(h, desc, stream, out);
@@ -876,6 +982,7 @@ int h2sp_analyze(const h2sp_h2_desc *desc, h2sp_handle **out) {
     return st;
   }
   h->plan_ptr = plan;
+  h->cell = std::make_shared<StructureCell>();
   h->structure_hash = structure_hash(desc, *plan);
   *out = h;
   return H2SP_OK;
@@ -898,7 +1005,7 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
       h->perm = h->alloc<int32_t>(size_t(std::max<int64_t>(p.piv_elems, 1)));
       size_t maxn = 1;
       for (const FrontLevel &L : h->flev) maxn = std::max<size_t>(maxn, size_t(L.hi - L.lo));
-      h->swaps = h->alloc<int32_t>(maxn * (1 + 2 * kMaxSwapRows));
+      h->swaps = h->alloc<int32_t>(2 * maxn * (1 + 2 * kMaxSwapRows));  // two steps in flight
       h->err = h->alloc<int>(1);
       h->dinv = h->alloc<double>(size_t(std::max<int64_t>(p.dinv_elems, 1)));
     }

@@ -669,7 +669,7 @@ __global__ void __launch_bounds__(kRegPanelThreads, 1) k_panel_reg(const FrontDe
 
 template <typename T, int NB>
 __global__ void __launch_bounds__(256) k_swap_trsm(const FrontDev *__restrict__ fr, int j0, T *__restrict__ fronts,
-                                                   const int32_t *__restrict__ swaps) {
+                                                   const int32_t *__restrict__ swaps, int part, int w) {
   const FrontDev F = fr[blockIdx.y];
   if (j0 >= F.s) return;
   const int jb = min(NB, F.s - j0);
@@ -687,8 +687,13 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const FrontDev *__restrict__ 
   }
   __syncthreads();
   constexpr int kPer = (kMaxSwapRows + 31) / 32;
-  for (int c = blockIdx.x * 8 + wid; c < F.f; c += gridDim.x * 8) {
-    if (c >= j0 && c < j0 + jb) continue;
+  // part 0: every column but the panel's; part 1: the w columns after the
+  // panel (what the next panel needs); part 2: the others
+  const int t0 = j0 + jb;
+  const int c_begin = part == 1 ? t0 : 0, c_end = part == 1 ? min(F.f, t0 + w) : F.f;
+  for (int c = c_begin + blockIdx.x * 8 + wid; c < c_end; c += gridDim.x * 8) {
+    if (c >= j0 && c < t0) continue;
+    if (part == 2 && c >= t0 && c < t0 + w) continue;
     T *Ac = A + int64_t(c) * ld;
     if (nsw > 0) {
       T v[kPer];
@@ -1537,7 +1542,12 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
   static_assert(G::BN >= NB, "the first column tile must cover the next panel");
   const int nsm = num_sms();
 
+  // the interchanges of step j0 go to half (j0 / NB) & 1 of the swaps buffer: the
+  // next panel writes the other half while this step's remaining columns are
+  // still being interchanged on the low-priority stream
+  const size_t swap_stride = size_t(nfront) * (1 + 2 * kMaxSwapRows);
   auto panel = [&](int j0, cudaStream_t st, int *cl) -> cudaError_t {
+    int32_t *swp = swaps + size_t((j0 / NB) & 1) * swap_stride;
     double fpanel = 0.0;
     if (prof->timing)
       for (int k = 0; k < nfront; ++k) {
@@ -1567,7 +1577,7 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
       at[0].val.clusterDim.z = 1;
       cfg.attrs = at;
       cfg.numAttrs = 1;
-      cudaError_t le = cudaLaunchKernelEx(&cfg, k_panel_reg<T, NB>, fr, j0, fronts, piv, swaps, err);
+      cudaError_t le = cudaLaunchKernelEx(&cfg, k_panel_reg<T, NB>, fr, j0, fronts, piv, swp, err);
       if (le != cudaSuccess) return le;
     } else if (C > 0) {
       *cl = C * nfront;
@@ -1584,11 +1594,11 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
       at[0].val.clusterDim.z = 1;
       cfg.attrs = at;
       cfg.numAttrs = 1;
-      cudaError_t le = cudaLaunchKernelEx(&cfg, k_panel_cluster<T, NB>, fr, j0, fronts, piv, swaps, err);
+      cudaError_t le = cudaLaunchKernelEx(&cfg, k_panel_cluster<T, NB>, fr, j0, fronts, piv, swp, err);
       if (le != cudaSuccess) return le;
     } else {
       *cl = nfront;
-      k_panel<T, NB><<<nfront, kPanelThreads, 0, st>>>(fr, j0, fronts, piv, swaps, err);
+      k_panel<T, NB><<<nfront, kPanelThreads, 0, st>>>(fr, j0, fronts, piv, swp, err);
     }
     prof->end(P_PANEL, 1, e0, fpanel, st);
     return cudaSuccess;
@@ -1639,23 +1649,33 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
         const double jb = std::min(NB, F.s - j0), rest = F.f - j0 - jb;
         ftrsm += jb * jb * rest;  // U12 = L^-1 A12
       }
-    size_t e0 = prof->begin();
-    const int ncol_blocks = std::min(cdiv(max_f, 8), 4096);
-    k_swap_trsm<T, NB><<<dim3(ncol_blocks, nfront), 256, 0, s>>>(fr, j0, fronts, swaps);
-    prof->end(P_TRSM, 1, e0, ftrsm);
+    const int32_t *sw = swaps + size_t((j0 / NB) & 1) * swap_stride;  // this step's interchanges
     const bool more = j0 + NB < max_s;
+    auto swap_trsm = [&](int part, cudaStream_t st) {
+      const size_t e0 = prof->begin(st);
+      const int span = part == 1 ? W : max_f;
+      const int ncol_blocks = std::min(cdiv(span, 8), 4096);
+      k_swap_trsm<T, NB><<<dim3(ncol_blocks, nfront), 256, 0, st>>>(fr, j0, fronts, sw, part, W);
+      const double share = std::min(1.0, double(W) / std::max(max_f, 1));
+      prof->end(P_TRSM, 1, e0, part == 0 ? ftrsm : part == 1 ? ftrsm * share : ftrsm * (1.0 - share), st);
+    };
     if (more && ahead) {
+      // the next panel's columns first; the other columns' interchanges and
+      // U12 move to the low-priority stream, ahead of the rest of the update
+      swap_trsm(1, s);
       if ((e = update(j0, 0, W, nsm, s)) != cudaSuccess) return e;
       if ((e = cudaEventRecord(la->next, s)) != cudaSuccess) return e;
       if ((e = cudaStreamWaitEvent(la->side, la->next, 0)) != cudaSuccess) return e;
       if ((e = cudaStreamWaitEvent(la->rest, la->next, 0)) != cudaSuccess) return e;
       if ((e = panel(j0 + NB, la->side, &panel_ctas)) != cudaSuccess) return e;
       if ((e = cudaEventRecord(la->panel, la->side)) != cudaSuccess) return e;
+      swap_trsm(2, la->rest);
       if ((e = update(j0, W, INT_MAX, std::max(nsm - panel_ctas, nsm / 2), la->rest)) != cudaSuccess) return e;
       if ((e = cudaEventRecord(la->done, la->rest)) != cudaSuccess) return e;
       if ((e = cudaStreamWaitEvent(s, la->panel, 0)) != cudaSuccess) return e;
       if ((e = cudaStreamWaitEvent(s, la->done, 0)) != cudaSuccess) return e;
     } else {
+      swap_trsm(0, s);
       if ((e = update(j0, 0, INT_MAX, nsm, s)) != cudaSuccess) return e;
       if (more && (e = panel(j0 + NB, s, &panel_ctas)) != cudaSuccess) return e;
     }
