@@ -682,6 +682,24 @@ std::shared_ptr<StructureDev> build_structure(const Plan &p) {
     }
     sd->child_start = sd->upload(cs);
     sd->child_cnt = sd->upload(cc);
+    // heaviest-first launch orders of the close-block and coupling kernels
+    {
+      std::vector<double> wl(p.nleaf, 0.0), wc(p.ncl, 0.0);
+      for (int lf = 0; lf < p.nleaf; ++lf) {
+        const int t = p.level_ptr[p.D] + lf;
+        for (int64_t z = p.near_ptr[lf]; z < p.near_ptr[lf + 1]; ++z)
+          wl[lf] += double(p.h_size[t]) * double(p.h_size[p.near_col[z]]);
+      }
+      for (int t = 0; t < p.ncl; ++t)
+        for (int64_t z = p.far_ptr[t]; z < p.far_ptr[t + 1]; ++z) wc[t] += double(p.rank[t]) * p.rank[p.far_col[z]];
+      std::vector<int32_t> ol(p.nleaf), oc(p.ncl);
+      for (int i = 0; i < p.nleaf; ++i) ol[i] = i;
+      for (int i = 0; i < p.ncl; ++i) oc[i] = i;
+      std::stable_sort(ol.begin(), ol.end(), [&](int a, int b) { return wl[a] > wl[b]; });
+      std::stable_sort(oc.begin(), oc.end(), [&](int a, int b) { return wc[a] > wc[b]; });
+      g.leaf_order = sd->upload(ol);
+      g.couple_order = sd->upload(oc);
+    }
     // FP64 multiply-adds per right-hand side of one product: close blocks,
     // couplings, the leaf bases (up and down) and the transfers (up and down)
     double mv = 0.0;

@@ -181,14 +181,15 @@ __device__ __forceinline__ void leaf_out_body(const H2Dev &h, int lf, const doub
   }
 }
 
-__global__ void __launch_bounds__(kMvThreads) k_h2_leaf_out(H2Dev h, const double *__restrict__ x, int64_t ldx,
+__global__ void __launch_bounds__(kMvThreads, 10) k_h2_leaf_out(H2Dev h, const double *__restrict__ x, int64_t ldx,
                                                             const double *__restrict__ yh, int64_t ldh,
                                                             double *__restrict__ y, int64_t ldy, int nrhs) {
-  const int n = int(h.size[h.leaf0 + blockIdx.x]);
+  const int lf = h.leaf_order ? h.leaf_order[blockIdx.x] : int(blockIdx.x);
+  const int n = int(h.size[h.leaf0 + lf]);
   switch (mv_groups(n)) {
-    case 4: leaf_out_body<4>(h, blockIdx.x, x, ldx, yh, ldh, y, ldy, nrhs); break;
-    case 2: leaf_out_body<2>(h, blockIdx.x, x, ldx, yh, ldh, y, ldy, nrhs); break;
-    default: leaf_out_body<1>(h, blockIdx.x, x, ldx, yh, ldh, y, ldy, nrhs); break;
+    case 4: leaf_out_body<4>(h, lf, x, ldx, yh, ldh, y, ldy, nrhs); break;
+    case 2: leaf_out_body<2>(h, lf, x, ldx, yh, ldh, y, ldy, nrhs); break;
+    default: leaf_out_body<1>(h, lf, x, ldx, yh, ldh, y, ldy, nrhs); break;
   }
 }
 
@@ -214,12 +215,13 @@ __device__ __forceinline__ void couple_body(const H2Dev &h, int t, const double 
   }
 }
 
-__global__ void __launch_bounds__(kMvThreads) k_h2_couple(H2Dev h, const double *__restrict__ xh,
+__global__ void __launch_bounds__(kMvThreads, 10) k_h2_couple(H2Dev h, const double *__restrict__ xh,
                                                           double *__restrict__ yh, int64_t ldh, int nrhs) {
-  switch (mv_groups(h.rank[blockIdx.x])) {
-    case 4: couple_body<4>(h, blockIdx.x, xh, yh, ldh, nrhs); break;
-    case 2: couple_body<2>(h, blockIdx.x, xh, yh, ldh, nrhs); break;
-    default: couple_body<1>(h, blockIdx.x, xh, yh, ldh, nrhs); break;
+  const int t = h.couple_order ? h.couple_order[blockIdx.x] : int(blockIdx.x);
+  switch (mv_groups(h.rank[t])) {
+    case 4: couple_body<4>(h, t, xh, yh, ldh, nrhs); break;
+    case 2: couple_body<2>(h, t, xh, yh, ldh, nrhs); break;
+    default: couple_body<1>(h, t, xh, yh, ldh, nrhs); break;
   }
 }
 

@@ -139,6 +139,9 @@ struct H2Dev {
   const int32_t *far_col, *near_col;
   const int64_t *xh_off;
   const double *leaf_basis, *transfer, *coupling, *near_block, *col_leaf_basis, *col_transfer;
+  // launch order of the close-block and coupling CTAs: heaviest first, so that
+  // the last wave is made of the lightest clusters
+  const int32_t *leaf_order, *couple_order;
   int32_t leaf0;  // first leaf cluster
 };
 // y = A x with A of Definition 4.9 (upward pass, couplings, downward pass, close blocks);
