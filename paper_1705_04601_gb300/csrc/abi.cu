@@ -172,6 +172,7 @@ struct h2sp_handle {
     return d;
   }
   LuAsync la;  // look-ahead stream and events of the block LU (created on first use)
+  uint8_t *tmaps = nullptr;  // TMA descriptors of the FP32 fronts (built on the first FP32 factorization)
   // flag-synchronised triangular sweeps
   int2 *chain_items = nullptr;
   std::vector<int> chain_fwd_off, chain_fwd_n, chain_bwd_off, chain_bwd_n;
@@ -194,6 +195,17 @@ struct h2sp_handle {
 };
 
 namespace {
+
+// FP32 trailing updates with a full panel move their C tiles by TMA;
+// H2SP_GEMM_TMA=0 keeps them on thread loads and stores.
+bool tma_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = std::getenv("H2SP_GEMM_TMA");
+    v = (e && std::strcmp(e, "0") == 0) ? 0 : 1;
+  }
+  return v == 1;
+}
 
 // The next panel is factored on a side stream while the trailing update runs;
 // H2SP_LOOKAHEAD=0 keeps every step on the caller's stream.
@@ -1055,10 +1067,17 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
                                     &h->prof));
     } else {
       float *F = static_cast<float *>(h->fronts);
+      if (h->tmaps == nullptr && tma_enabled() && !p.fronts.empty()) {
+        uint8_t *m = h->alloc<uint8_t>(p.fronts.size() * kTmapBytes);
+        ck(cudaStreamSynchronize(s));  // the allocation is usable by the synchronous copy
+        if (make_front_tmaps(p.fronts.data(), int(p.fronts.size()), F, m) == cudaSuccess) h->tmaps = m;
+        cudaGetLastError();
+      }
       ck(launch_assemble<float>(h->asm_items, na, h->S, F, s, &h->prof, abytes));
       for (const FrontLevel &L : h->flev) {
         ck(launch_lu_level<float>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv,
-                                  h->swaps, h->err, s, la, &h->prof));
+                                  h->swaps, h->err, s, la, &h->prof,
+                                  h->tmaps ? h->tmaps + size_t(L.lo) * kTmapBytes : nullptr));
         ck(launch_extend_add_impl<float>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s, &h->prof, L.b2));
       }
       ck(launch_make_perm<float>(h->fr, int(p.fronts.size()), h->max_s_all, h->piv, h->perm, s, &h->prof));

@@ -1526,7 +1526,8 @@ inline bool use_tensor_core_gemm() {
 // while the remaining columns are updated on the main stream.
 template <typename T>
 cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
-                            int32_t *piv, int32_t *swaps, int *err, cudaStream_t s, const LuAsync *la, Prof *prof) {
+                            int32_t *piv, int32_t *swaps, int *err, cudaStream_t s, const LuAsync *la, Prof *prof,
+                            const uint8_t *maps) {
   constexpr int NB = LuCfg<T>::NB;
   using G = GemmCfg<T>;
   auto gemm = k_gemm_update<T, G::BM, G::BN, G::TM, G::TN, NB>;
@@ -1623,7 +1624,14 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
     if (tc) {
       if constexpr (std::is_same<T, float>::value) {
         const int thi = c_hi >= (INT_MAX - kTcTile) ? INT_MAX : c_hi / kTcTile;
-        cudaError_t ge = launch_gemm_tc(fr, j0, nfront, max_f, fronts, err, us, c_lo / kTcTile, thi, sm_budget);
+        bool any_full = false, any_partial = false;
+        for (int k = 0; k < nfront; ++k) {
+          const int left = host_fr[k].s - j0;
+          if (left >= NB) any_full = true;
+          else if (left > 0) any_partial = true;
+        }
+        cudaError_t ge = launch_gemm_tc(fr, j0, nfront, max_f, fronts, err, us, c_lo / kTcTile, thi, sm_budget,
+                                        maps, any_full, any_partial);
         if (ge != cudaSuccess) return ge;
       }
     } else {
@@ -1792,7 +1800,8 @@ cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, 
 template cudaError_t launch_assemble<double>(const AItem *, int64_t, const double *, double *, cudaStream_t, Prof *,
                                            double);
 template cudaError_t launch_lu_level<double>(const FrontDev *, const Front *, int, int, int, double *, int32_t *, int32_t *,
-                                           int *, cudaStream_t, const LuAsync *, Prof *);
+                                           int *, cudaStream_t, const LuAsync *, Prof *,
+                                           const uint8_t *);
 template cudaError_t launch_make_perm<double>(const FrontDev *, int, int, const int32_t *, int32_t *, cudaStream_t, Prof *);
 template cudaError_t launch_extend_add_impl<double>(const FrontDev *, int, int, int, const int32_t *, double *, cudaStream_t,
                                                   Prof *, double);
@@ -1808,7 +1817,8 @@ template cudaError_t launch_solve_bwd_level_impl<double>(const FrontDev *, int, 
 template cudaError_t launch_assemble<float>(const AItem *, int64_t, const double *, float *, cudaStream_t, Prof *,
                                            double);
 template cudaError_t launch_lu_level<float>(const FrontDev *, const Front *, int, int, int, float *, int32_t *, int32_t *,
-                                           int *, cudaStream_t, const LuAsync *, Prof *);
+                                           int *, cudaStream_t, const LuAsync *, Prof *,
+                                           const uint8_t *);
 template cudaError_t launch_make_perm<float>(const FrontDev *, int, int, const int32_t *, int32_t *, cudaStream_t, Prof *);
 template cudaError_t launch_extend_add_impl<float>(const FrontDev *, int, int, int, const int32_t *, float *, cudaStream_t,
                                                   Prof *, double);

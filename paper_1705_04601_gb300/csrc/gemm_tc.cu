@@ -18,6 +18,10 @@
 // memory and returns.
 #include <algorithm>
 #include <cstdint>
+#include <vector>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "kernels.h"
 
@@ -96,10 +100,11 @@ __device__ __forceinline__ void sync_for_tensor_cores() {
 // i overlap the asynchronous MMAs.
 __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__restrict__ fr, int j0,
                                                           float *__restrict__ fronts, int *__restrict__ err,
-                                                          int splits, int tile_lo, int tile_hi) {
+                                                          int splits, int tile_lo, int tile_hi, int partial_only) {
   const FrontDev F = fr[blockIdx.z];
   if (j0 >= F.s) return;
   const int jb = min(kTcK, F.s - j0);
+  if (partial_only && jb == kTcK) return;  // full panels are done by k_gemm_tc_tma
   const int t0 = j0 + jb;
   const int nrest = F.f - t0;
   const int rb = blockIdx.y * kTcM;
@@ -261,15 +266,196 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__res
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
 }
 
+// TMA helpers (2D tiles of an FP32 front: x = row, y = column)
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const void *tmap, int x, int y, uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(tmap), "r"(x),
+               "r"(y), "r"(src)
+               : "memory");
+}
+
+// The update with a full panel (jb = 64): the C tile moves by TMA (one
+// 128 x 128 FP32 box in, one out, per column tile) instead of 128 scalar
+// accesses per thread, so the load/store queues carry only the B operand.
+// Per column tile: the C load is requested first, the threads stage B
+// (hi / lo), one thread issues the MMAs, the epilogue subtracts the
+// accumulator from the tile in shared memory, and the tile is stored back
+// asynchronously while the next one starts.  Shared memory: A hi/lo, B hi/lo
+// and the C tile, 192 KB.
+__global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc_tma(const FrontDev *__restrict__ fr, int j0,
+                                                              float *__restrict__ fronts, int *__restrict__ err,
+                                                              int splits, int tile_lo, int tile_hi,
+                                                              const uint8_t *__restrict__ maps) {
+  const FrontDev F = fr[blockIdx.z];
+  if (j0 >= F.s || F.s - j0 < kTcK) return;  // full panels only
+  const int jb = kTcK;
+  const int t0 = j0 + jb;
+  const int nrest = F.f - t0;
+  const int rb = blockIdx.y * kTcM;
+  if (rb >= nrest) return;
+  const int ntiles = min((nrest + kTcN - 1) / kTcN, tile_hi) - tile_lo;
+  if (ntiles <= 0) return;
+  const int per = (ntiles + splits - 1) / splits;
+  const int c_lo = tile_lo + blockIdx.x * per, c_hi = min(tile_lo + ntiles, c_lo + per);
+  if (c_lo >= c_hi) return;
+  const void *tmap = maps + size_t(blockIdx.z) * kTmapBytes;
+  float *A = fronts + F.off;
+  const int64_t ld = F.ld;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  float *sAh = reinterpret_cast<float *>(smraw), *sAl = sAh + kTileFloats;
+  float *sBh = sAl + kTileFloats, *sBl = sBh + kTileFloats;
+  float *sC = sBl + kTileFloats;  // 128 x 128, column-major (TMA box order)
+  __shared__ __align__(8) uint64_t bar_mma, bar_c;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int kIters = kTcM * kTcK / kTcThreads;
+#pragma unroll 4
+  for (int it = 0; it < kIters; ++it) {
+    const int e = tid + it * kTcThreads;
+    const int m = (e >> 9) * 8 + ((e & 31) >> 2), k = ((e >> 5) & 15) * 4 + (e & 3);
+    const int r = rb + m;
+    const float v = r < nrest ? A[(t0 + r) + int64_t(j0 + k) * ld] : 0.f;
+    float hi, lo;
+    split_tf32(v, hi, lo);
+    sAh[e] = hi;
+    sAl[e] = lo;
+  }
+  auto stage_b = [&](int ct) {
+    const int cb = ct * kTcN;
+    float v[kIters];
+#pragma unroll
+    for (int it = 0; it < kIters; ++it) {
+      const int e = tid + it * kTcThreads;
+      const int ln = e & 31, wv = e >> 5;
+      const int k = (ln & 7) + 8 * (wv & 7), n = (ln >> 3) + 4 * (wv >> 3);
+      const int c = cb + n;
+      v[it] = c < nrest ? A[(j0 + k) + int64_t(t0 + c) * ld] : 0.f;
+    }
+#pragma unroll
+    for (int it = 0; it < kIters; ++it) {
+      const int e = tid + it * kTcThreads;
+      const int ln = e & 31, wv = e >> 5;
+      const int k = (ln & 7) + 8 * (wv & 7), n = (ln >> 3) + 4 * (wv >> 3);
+      const int w = (n >> 3) * (kSbo / 4) + (k >> 2) * (kLbo / 4) + (n & 7) * 4 + (k & 3);
+      float hi, lo;
+      split_tf32(v[it], hi, lo);
+      sBh[w] = hi;
+      sBl[w] = lo;
+    }
+  };
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(uint32_t(kTcN)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_mma)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_c)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  uint32_t ph_mma = 0u, ph_c = 0u;
+  bool ok = true, mma_pending = false, c_pending = false;
+  const int q = warp & 3, half = warp >> 2;
+  for (int ct = c_lo; ct < c_hi; ++ct) {
+    const int x = t0 + rb, y = t0 + ct * kTcN;
+    if (tid == 0) {
+      // the previous tile's store has read the shared tile
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar_c)),
+                   "r"(uint32_t(kTcM * kTcN * 4))
+                   : "memory");
+      tma_load_2d(smem_u32(sC), tmap, x, y, smem_u32(&bar_c));
+    }
+    c_pending = true;
+    stage_b(ct);  // the previous tile's MMAs completed before its epilogue
+    sync_for_tensor_cores();
+    if (tid == 0) {
+      const uint32_t ah0 = smem_u32(sAh), al0 = smem_u32(sAl), bh0 = smem_u32(sBh), bl0 = smem_u32(sBl);
+      for (int kk = 0; kk < kTcK / 8; ++kk) {
+        const uint32_t koff = uint32_t(kk) * 2 * kLbo;
+        const uint64_t ah = smem_desc(ah0 + koff), al = smem_desc(al0 + koff);
+        const uint64_t bh = smem_desc(bh0 + koff), bl = smem_desc(bl0 + koff);
+        mma_tf32(tmem, ah, bh, kk > 0 ? 1u : 0u);
+        mma_tf32(tmem, ah, bl, 1u);
+        mma_tf32(tmem, al, bh, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&bar_mma)));
+    }
+    mma_pending = true;
+    const bool w1 = wait_phase(smem_u32(&bar_mma), ph_mma);
+    const bool w2 = wait_phase(smem_u32(&bar_c), ph_c);
+    ok = __syncthreads_and((w1 && w2) ? 1 : 0) != 0;
+    if (!ok) {
+      // a wait gave up: keep track of what may still be in flight
+      mma_pending = !w1;
+      c_pending = !w2;
+      break;
+    }
+    ph_mma ^= 1u;
+    ph_c ^= 1u;
+    mma_pending = c_pending = false;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int row = q * 32 + lane;
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(half * 64 + c0);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+          "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      float *col = sC + (half * 64 + c0) * kTcM + row;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) col[j * kTcM] -= __uint_as_float(v[j]);
+    }
+    // the tile goes back asynchronously; TMEM and the B tile are free
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      tma_store_2d(tmap, x, y, smem_u32(sC));
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(err, 4);
+    // bounded waits for what may still target this CTA's memory
+    if (mma_pending) wait_phase(smem_u32(&bar_mma), ph_mma);
+    if (c_pending) wait_phase(smem_u32(&bar_c), ph_c);
+  }
+  if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(kTcN)));
+}
+
 }  // namespace
 
 size_t gemm_tc_smem() { return size_t(24) * kTileFloats + 1024; }
 
 cudaError_t launch_gemm_tc(const FrontDev *fr, int j0, int nfront, int max_f, float *fronts, int *err,
-                           cudaStream_t s, int tile_lo, int tile_hi, int sm_budget) {
+                           cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps,
+                           bool any_full, bool any_partial) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gemm_tc_smem()));
+    cudaFuncSetAttribute(k_gemm_tc_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gemm_tc_smem()));
     attr = true;
   }
   const int rest = max_f - j0 - 1;
@@ -292,8 +478,41 @@ cudaError_t launch_gemm_tc(const FrontDev *fr, int j0, int nfront, int max_f, fl
     if (cost < best - 1e-9) best = cost, splits = sp;
   }
   dim3 g(splits, rt, nfront);
-  k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, tile_lo, tile_hi);
+  if (maps != nullptr) {
+    if (any_full)
+      k_gemm_tc_tma<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, tile_lo, tile_hi, maps);
+    if (any_partial) k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, tile_lo, tile_hi, 1);
+  } else {
+    k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, tile_lo, tile_hi, 0);
+  }
   return cudaGetLastError();
+}
+
+// One TMA descriptor per FP32 front: 2D, rows x columns, leading dimension
+// ld (16-byte multiple), 128 x 128 boxes, zero fill outside the front.
+cudaError_t make_front_tmaps(const Front *fronts, int n, const float *base, uint8_t *maps_dev) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (encode == nullptr) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || fn == nullptr || q != cudaDriverEntryPointSuccess) return e != cudaSuccess ? e : cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  static_assert(sizeof(CUtensorMap) == kTmapBytes, "tensor map size");
+  std::vector<CUtensorMap> maps(std::max(n, 1));
+  for (int k = 0; k < n; ++k) {
+    const Front &F = fronts[k];
+    const cuuint64_t dims[2] = {cuuint64_t(std::max(F.f, 1)), cuuint64_t(std::max(F.f, 1))};
+    const cuuint64_t strides[1] = {cuuint64_t(F.ld) * sizeof(float)};
+    const cuuint32_t box[2] = {cuuint32_t(kTcM), cuuint32_t(kTcN)};
+    const cuuint32_t es[2] = {1, 1};
+    CUresult r = encode(&maps[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base + F.off), dims, strides,
+                        box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  return cudaMemcpy(maps_dev, maps.data(), sizeof(CUtensorMap) * size_t(n), cudaMemcpyHostToDevice);
 }
 
 }  // namespace h2sp

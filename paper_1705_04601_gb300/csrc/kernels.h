@@ -60,7 +60,8 @@ struct LuAsync {
 // step k + 1 overlaps the trailing update of step k.
 template <typename T>
 cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
-                            int32_t *piv, int32_t *swaps, int *err, cudaStream_t s, const LuAsync *la, Prof *prof);
+                            int32_t *piv, int32_t *swaps, int *err, cudaStream_t s, const LuAsync *la, Prof *prof,
+                            const uint8_t *maps = nullptr);
 template <typename T>
 cudaError_t launch_extend_add_impl(const FrontDev *fr_all, int lo, int nfront, int max_b, const int32_t *map,
                                    T *fronts, cudaStream_t s, Prof *prof, double elems);
@@ -103,8 +104,14 @@ cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, 
 // FP32 trailing update C -= L21 U12 of one panel step on the tensor cores
 // (gemm_tc.cu), over the 128-column tiles [tile_lo, tile_hi) of the trailing
 // block, sized for about sm_budget SMs.
+// With `maps` (one TMA descriptor per front of the launch, make_front_tmaps),
+// fronts with a full 64-column panel move their C tiles by TMA; any_full /
+// any_partial say which kinds of front the step has.
+constexpr int kTmapBytes = 128;
 cudaError_t launch_gemm_tc(const FrontDev *fr, int j0, int nfront, int max_f, float *fronts, int *err,
-                           cudaStream_t s, int tile_lo, int tile_hi, int sm_budget);
+                           cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps,
+                           bool any_full, bool any_partial);
+cudaError_t make_front_tmaps(const Front *fronts, int n, const float *base, uint8_t *maps_dev);
 constexpr int kTcTile = 128;
 
 // ---- applies, H^2 product, vector kernels (apply.cu) ----
