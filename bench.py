@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="log2d_n65536")
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--sparsify-prec", default="fp32", choices=["fp32", "fp64"],
+                    help="precision of U, S, V on the mixed path (the FP64 path always sparsifies in FP64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--solver", default="gmres", choices=["gmres", "ir"],
@@ -162,7 +164,7 @@ def kernel_source_hash(fname):
     return hashlib.sha256(src).hexdigest()[:16]
 
 
-def roofline(prof, timed_launches_ok=True):
+def roofline(prof, timed_launches_ok=True, sparsify_fp32=False):
     """Dominant kernel class by event time -> achieved vs its peak.
 
     The library's profiler records per class the algorithmic work of its
@@ -170,7 +172,8 @@ def roofline(prof, timed_launches_ok=True):
       gemm_update   tensor-core rank-64 update: HBM-bound, bytes (C read + written, L21, U12)
                     (H2SP_GEMM=simt: FP32 CUDA-core flops)
       panel, swap_trsm   FP32 flops (CUDA cores)
-      transform, householder, coupling, h2_matvec   FP64 flops (FP64 pipe)
+      transform, householder, coupling   FP64 flops (FP64 pipe), FP32 flops with an FP32 sparsification
+      h2_matvec     FP64 flops (FP64 pipe)
       solve, apply, assemble, extend_add, vector    bytes
     """
     cls = max(prof, key=lambda c: prof[c]["ms"])
@@ -180,11 +183,12 @@ def roofline(prof, timed_launches_ok=True):
     peaks = measured_peaks()
     out = {"kernel": cls, "launches_timed": p["timed"], "avg_launch_ms": per_launch_ms}
     simt_gemm = os.environ.get("H2SP_GEMM", "") == "simt"
-    if cls in ("panel", "swap_trsm") or (cls == "gemm_update" and simt_gemm):
+    sp_cls = ("transform", "householder", "coupling")
+    if cls in ("panel", "swap_trsm") or (cls == "gemm_update" and simt_gemm) or (cls in sp_cls and sparsify_fp32):
         achieved = p["work"] / (p["ms"] * 1e-3) / 1e12
         out.update(bound="alu", achieved=achieved, peak=FP32_SIMT_TFLOPS, unit="TFLOP/s",
                    peak_source="derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal max clock)")
-    elif cls in ("transform", "householder", "coupling", "h2_matvec"):
+    elif cls in sp_cls or cls == "h2_matvec":
         achieved = p["work"] / (p["ms"] * 1e-3) / 1e12
         out.update(bound="alu", achieved=achieved, peak=FP64_TFLOPS, unit="TFLOP/s",
                    peak_source="nominal GB300 FP64 (1.25 TFLOP/s); no measured FP64 peak on this pool")
@@ -229,8 +233,10 @@ def run_ours(args, ws, rank, local):
 
     mode = H.H2SP_GMRES if args.solver == "gmres" else H.H2SP_IR
 
+    sp_flags = H.H2SP_SPARSIFY_FP32 if args.sparsify_prec == "fp32" else 0
+
     def mixed_step(profile=False):
-        hd = H.h2sp_sparsify_analyzed(an, inp)
+        hd = H.h2sp_sparsify_analyzed(an, inp, flags=sp_flags)
         if profile:
             H.h2sp_profile(hd, timing=1, reset=True)
         H.h2sp_factor(hd, H.H2SP_FP32)
@@ -301,7 +307,7 @@ def run_ours(args, ws, rank, local):
     phase = {}
     e = [ev() for _ in range(4)]
     e[0].record(stream)
-    hd = H.h2sp_sparsify_analyzed(an, inp)
+    hd = H.h2sp_sparsify_analyzed(an, inp, flags=sp_flags)
     e[1].record(stream)
     H.h2sp_factor(hd, H.H2SP_FP32)
     e[2].record(stream)
@@ -326,7 +332,7 @@ def run_ours(args, ws, rank, local):
             inp2 = H.H2Input(h, nonblocking_from=pinned)
             b2 = b_pin.cuda(non_blocking=True)
             x2 = torch.empty_like(b2)
-            hd2 = H.h2sp_sparsify_analyzed(an, inp2)
+            hd2 = H.h2sp_sparsify_analyzed(an, inp2, flags=sp_flags)
             H.h2sp_factor(hd2, H.H2SP_FP32)
             H.h2sp_solve(hd2, b2, x2, mode=mode, tol=1e-10, maxit=60, restart=20)
             x_pin.copy_(x2, non_blocking=True)
@@ -354,7 +360,7 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(args.workload)
 
-    roof = roofline(prof_sum)
+    roof = roofline(prof_sum, sparsify_fp32=(args.sparsify_prec == "fp32"))
     fl = stats["factor_flops"]
     res_mixed = max(r for (_, r, _) in infos)
     out = {
@@ -364,13 +370,15 @@ def run_ours(args, ws, rank, local):
         "config": {"workload": args.workload, "n": int(h.n), "leaf": 64, "basis_tol": 1e-6, "nrhs": int(b.shape[1]),
                    "kernel": "-log r", "points": "uniform [0,1]^2 (seeded)",
                    "l2": "inputs larger than L2 (443 MB of close blocks resident in HBM)",
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "sparsify_prec": args.sparsify_prec, "factor_prec": "fp32"},
         "mixed_s": mixed_s, "fp64_direct_s": fp64_s, "speedup_mixed_vs_fp64": fp64_s / mixed_s,
         "factor_flops": fl, "factor_gflops_fp32": None, "factor_gflops_fp64": None,
         "solver": args.solver, "refine_iters": [i for (i, _, _) in infos], "rel_residual_mixed": res_mixed, "rel_residual_fp64": res64,
         "fp64_refine_iters": info64.iters,
         "mixed_vs_fp64_rel_diff": diff, "phase_ms": phase, "input_gen_s": gen_s,
-        "roofline": roof, "e2e": e2e, "gpu_launches": int(launches / max(args.steps, 1)),
+        "roofline": roof, "e2e": e2e, "gpu_launches": int(launches),
+        "gpu_launches_per_step": int(launches / max(args.steps, 1)),
         "kernel_ms_per_step": {c: v["ms"] / args.steps for c, v in prof_sum.items() if v["ms"] > 0},
         "clocks": clk, "cpu_baseline": cpu,
     }

@@ -125,8 +125,19 @@ typedef struct {
   const double *col_transfer;        /* column transfer matrices; NULL iff col_leaf_basis is NULL */
 } h2sp_h2_desc;
 
+/* Bits of h2sp_opts.flags. */
+enum {
+  /* Sparsify in FP32: Q, the coupling projections, the level buffers and S
+   * are computed and stored in FP32 (the H^2 inputs stay FP64 and are rounded
+   * on load).  Meant for the mixed-precision solve, where U, S and V only
+   * build the FP32 preconditioner and the FP64 H^2 product of Definition 4.9
+   * decides convergence (§5.5); the applies and products of the handle still
+   * take and return FP64 vectors and sum in FP64. */
+  H2SP_SPARSIFY_FP32 = 1
+};
+
 typedef struct {
-  int32_t flags;       /* reserved, pass 0 */
+  int32_t flags;       /* 0 or H2SP_SPARSIFY_FP32; any other bit is H2SP_EINVAL; opts may be NULL (= 0) */
 } h2sp_opts;
 
 typedef struct {
@@ -155,6 +166,7 @@ typedef struct {
   double sparsify_flops;          /* algorithmic flops of the sparsification */
   int32_t factor_prec;            /* h2sp_prec of the current factors, -1 if none */
   double plan_seconds;            /* host time spent planning in the last h2sp_sparsify */
+  int32_t sparsify_prec;          /* h2sp_prec of U, V and S; -1 for an analysis-only handle */
 } h2sp_stats;
 
 /*
@@ -163,7 +175,8 @@ typedef struct {
  * H2SP_EINVAL without launching anything if it is malformed: unsorted lists,
  * inconsistent tree, ranks that do not fit, a missing column array), plans
  * the level recursion and the symbolic factorization of S on the host, and
- * enqueues the FP64 kernels on `stream`: the Householder completions of the
+ * enqueues the kernels (FP64, or FP32 with H2SP_SPARSIFY_FP32) on `stream`:
+ * the Householder completions of the
  * cluster bases per level, the coupling projections, the transforms of the
  * close blocks and of the cross-level panels, and the scatter into S.
  * On success *out owns a new handle.

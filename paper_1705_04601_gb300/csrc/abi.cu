@@ -41,8 +41,8 @@ struct LevelDev {
   CItem *c = nullptr;
   XItem *x = nullptr;
   int nq = 0, nw = 0, nc = 0, nx = 0;
-  double **src_base = nullptr, **dst_base = nullptr;  // device arrays of 4 pointers
-  double *W = nullptr, *Wc = nullptr;
+  void **src_base = nullptr, **dst_base = nullptr;  // device arrays of 4 pointers
+  void *W = nullptr, *Wc = nullptr;                 // stacked bases, in the sparsification's precision
   ApItem *ap = nullptr;  // applies of this level's Q blocks
   int nap = 0;
 };
@@ -114,9 +114,11 @@ struct h2sp_handle {
   // borrowed H^2 numbers
   const double *leaf_basis = nullptr, *transfer = nullptr, *coupling = nullptr, *near_block = nullptr;
   const double *col_leaf_basis = nullptr, *col_transfer = nullptr;
-  // sparsification
-  double *Q = nullptr, *Qc = nullptr, *Rr = nullptr, *Rrc = nullptr, *S = nullptr;
-  std::vector<double *> Cbuf, RPbuf, CPbuf;
+  // sparsification: Q, R, S and the level buffers hold doubles, or floats
+  // when sp_prec is H2SP_FP32
+  int sp_prec = H2SP_FP64;
+  void *Q = nullptr, *Qc = nullptr, *Rr = nullptr, *Rrc = nullptr, *S = nullptr;
+  std::vector<void *> Cbuf, RPbuf, CPbuf;
   std::vector<LevelDev> lv;
   // applies
   int64_t *top_src = nullptr, *top_dst = nullptr;
@@ -256,7 +258,7 @@ void apply_T(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *o
     int n;
     ~Done() { h->prof.end(P_APPLY, n, e0, 0.0); }
   } done{h, e0, 1 + p.lstop * chunks};
-  const double *Qb = col ? h->Qc : h->Q;
+  const void *Qb = col ? h->Qc : h->Q;
   if (p.lstop == 0) {
     ck(launch_copy_rows(h->top_src, h->top_dst, h->top_len, h->ntop, in, ldin, out, ldout, nrhs, s));
     return;
@@ -267,7 +269,12 @@ void apply_T(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *o
   double *bufs[2] = {h->vecA, h->vecB};
   for (int l = 0; l < p.lstop; ++l) {
     double *xn = bufs[l & 1];
-    ck(launch_apply_qt(h->lv[l].ap, h->lv[l].nap, Qb, x, ldx, out, ldout, xn, ldw, nrhs, s));
+    if (h->sp_prec == H2SP_FP32)
+      ck(launch_apply_qt(h->lv[l].ap, h->lv[l].nap, static_cast<const float *>(Qb), x, ldx, out, ldout, xn, ldw, nrhs,
+                         s));
+    else
+      ck(launch_apply_qt(h->lv[l].ap, h->lv[l].nap, static_cast<const double *>(Qb), x, ldx, out, ldout, xn, ldw,
+                         nrhs, s));
     x = xn;
     ldx = ldw;
   }
@@ -286,7 +293,7 @@ void apply_N(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *o
     int n;
     ~Done() { h->prof.end(P_APPLY, n, e0, 0.0); }
   } done{h, e0, 1 + p.lstop * chunks};
-  const double *Qb = col ? h->Qc : h->Q;
+  const void *Qb = col ? h->Qc : h->Q;
   if (p.lstop == 0) {
     ck(launch_copy_rows(h->top_dst, h->top_src, h->top_len, h->ntop, in, ldin, out, ldout, nrhs, s));
     return;
@@ -298,7 +305,12 @@ void apply_N(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *o
   for (int l = p.lstop - 1; l >= 0; --l) {
     double *x = (l == 0) ? out : bufs[l & 1];
     const int64_t ldx = (l == 0) ? ldout : ldw;
-    ck(launch_apply_q(h->lv[l].ap, h->lv[l].nap, Qb, xn, ldw, in, ldin, x, ldx, nrhs, s));
+    if (h->sp_prec == H2SP_FP32)
+      ck(launch_apply_q(h->lv[l].ap, h->lv[l].nap, static_cast<const float *>(Qb), xn, ldw, in, ldin, x, ldx, nrhs,
+                        s));
+    else
+      ck(launch_apply_q(h->lv[l].ap, h->lv[l].nap, static_cast<const double *>(Qb), xn, ldw, in, ldin, x, ldx, nrhs,
+                        s));
     xn = x;
   }
 }
@@ -785,9 +797,54 @@ std::shared_ptr<StructureDev> build_structure(const Plan &p) {
   return sd;
 }
 
+// the level recursion of the sparsification (§2.1-2.3, §4.2-4.3) in working
+// precision W on the handle's buffers
+template <typename W>
+void sparsify_levels(h2sp_handle *h, const Plan &p, const StructureDev &sd, cudaStream_t s) {
+  const int L = p.lstop;
+  const int nlw = int(p.lw.size());
+  auto buf = [](void *q) { return static_cast<W *>(q); };
+  for (int l = 0; l < nlw; ++l) {
+    const LevelWork &w = p.lw[l];
+    LevelDev &d = h->lv[l];
+    if (l >= 1) {
+      d.W = h->alloc<W>(size_t(w.w_elems));
+      if (!p.sym) d.Wc = h->alloc<W>(size_t(w.wc_elems));
+    }
+    std::vector<void *> sb = {const_cast<double *>(h->near_block), l < L ? h->Cbuf[l] : nullptr,
+                              l < L ? h->RPbuf[l] : nullptr, l < L ? h->CPbuf[l] : nullptr};
+    std::vector<void *> db = {h->S, l + 1 < L ? h->Cbuf[l + 1] : nullptr, l + 1 < L ? h->RPbuf[l + 1] : nullptr,
+                              l + 1 < L ? h->CPbuf[l + 1] : nullptr};
+    d.src_base = h->upload(sb);
+    d.dst_base = h->upload(db);
+  }
+  for (int l = 0; l < nlw; ++l) {
+    const LevelWork &w = p.lw[l];
+    LevelDev &d = h->lv[l];
+    if (l < L) {
+      if (l >= 1) {
+        ck(launch_stack_w<W>(d.w, d.nw, buf(h->Rr), h->transfer, buf(d.W), s, &h->prof));
+        if (!p.sym) ck(launch_stack_w<W>(d.wc, d.nw, buf(h->Rrc), h->col_transfer, buf(d.Wc), s, &h->prof));
+      }
+      ck(launch_householder<W>(d.q, d.nq, h->leaf_basis, buf(d.W), buf(h->Q), buf(h->Rr), std::max(w.max_m, 1),
+                               std::max(w.max_k, 1), s, &h->prof));
+      if (!p.sym)
+        ck(launch_householder<W>(d.qc, d.nq, h->col_leaf_basis, buf(d.Wc), buf(h->Qc), buf(h->Rrc),
+                                 std::max(w.max_m, 1), std::max(w.max_k, 1), s, &h->prof));
+      ck(launch_coupling<W>(d.c, d.nc, buf(h->Rr), buf(h->Rrc), h->coupling,
+                            reinterpret_cast<W *const *>(d.dst_base), sd.max_rank, s, &h->prof));
+    }
+    ck(launch_transform<W>(d.x, d.nx, const_cast<const void *const *>(d.src_base), buf(h->Q), buf(h->Qc),
+                           reinterpret_cast<W *const *>(d.dst_base), s, &h->prof,
+                           l < int(h->x_flops.size()) ? h->x_flops[l] : 0.0));
+  }
+}
+
 // numeric part of the sparsification: the handle's buffers and the kernels,
 // on the (shared) device copy of the structure
-int sparsify_numeric(h2sp_handle *h, const h2sp_h2_desc *desc, h2sp_stream stream, h2sp_handle **out) {
+int sparsify_numeric(h2sp_handle *h, const h2sp_h2_desc *desc, int32_t sp_prec, h2sp_stream stream,
+                     h2sp_handle **out) {
+  h->sp_prec = sp_prec;
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   h->prof.stream = h->stream;
   h->leaf_basis = desc->leaf_basis;
@@ -809,67 +866,38 @@ int sparsify_numeric(h2sp_handle *h, const h2sp_h2_desc *desc, h2sp_stream strea
     }
     const StructureDev &sd = *h->sdev;
     // ---- owned buffers ----
-    h->Q = h->alloc<double>(size_t(p.q_elems));
-    h->Rr = h->alloc<double>(size_t(p.rr_elems));
+    const size_t wsz = (sp_prec == H2SP_FP32) ? sizeof(float) : sizeof(double);
+    auto walloc = [&](int64_t n) -> void * { return h->alloc<char>(size_t(std::max<int64_t>(n, 1)) * wsz); };
+    h->Q = walloc(p.q_elems);
+    h->Rr = walloc(p.rr_elems);
     if (p.sym) {
       h->Qc = h->Q;
       h->Rrc = h->Rr;
     } else {
-      h->Qc = h->alloc<double>(size_t(p.q_elems));
-      h->Rrc = h->alloc<double>(size_t(p.rr_elems));
+      h->Qc = walloc(p.q_elems);
+      h->Rrc = walloc(p.rr_elems);
     }
-    h->S = h->alloc<double>(size_t(p.s_elems));
-    ck(cudaMemsetAsync(h->S, 0, sizeof(double) * size_t(std::max<int64_t>(p.s_elems, 1)), s));
+    h->S = walloc(p.s_elems);
+    ck(cudaMemsetAsync(h->S, 0, wsz * size_t(std::max<int64_t>(p.s_elems, 1)), s));
     const int L = p.lstop;
     h->Cbuf.assign(L + 1, nullptr);
     h->RPbuf.assign(L + 1, nullptr);
     h->CPbuf.assign(L + 1, nullptr);
     for (int l = 1; l < L; ++l) {
-      h->Cbuf[l] = h->alloc<double>(size_t(p.c_elems[l]));
-      h->RPbuf[l] = h->alloc<double>(size_t(p.rp_elems[l]));
-      h->CPbuf[l] = h->alloc<double>(size_t(p.cp_elems[l]));
-      ck(cudaMemsetAsync(h->Cbuf[l], 0, sizeof(double) * size_t(std::max<int64_t>(p.c_elems[l], 1)), s));
-      ck(cudaMemsetAsync(h->RPbuf[l], 0, sizeof(double) * size_t(std::max<int64_t>(p.rp_elems[l], 1)), s));
-      ck(cudaMemsetAsync(h->CPbuf[l], 0, sizeof(double) * size_t(std::max<int64_t>(p.cp_elems[l], 1)), s));
+      h->Cbuf[l] = walloc(p.c_elems[l]);
+      h->RPbuf[l] = walloc(p.rp_elems[l]);
+      h->CPbuf[l] = walloc(p.cp_elems[l]);
+      ck(cudaMemsetAsync(h->Cbuf[l], 0, wsz * size_t(std::max<int64_t>(p.c_elems[l], 1)), s));
+      ck(cudaMemsetAsync(h->RPbuf[l], 0, wsz * size_t(std::max<int64_t>(p.rp_elems[l], 1)), s));
+      ck(cudaMemsetAsync(h->CPbuf[l], 0, wsz * size_t(std::max<int64_t>(p.cp_elems[l], 1)), s));
     }
-    // ---- per-level buffers and source / destination tables ----
-    const int nlw = int(p.lw.size());
+    // ---- per-level tables and the sparsification kernels, level by level ----
     h->lv = sd.lv;
     h->x_flops = sd.x_flops;
-    const int max_rank = sd.max_rank;
-    for (int l = 0; l < nlw; ++l) {
-      const LevelWork &w = p.lw[l];
-      LevelDev &d = h->lv[l];
-      if (l >= 1) {
-        d.W = h->alloc<double>(size_t(w.w_elems));
-        if (!p.sym) d.Wc = h->alloc<double>(size_t(w.wc_elems));
-      }
-      std::vector<double *> sb = {const_cast<double *>(h->near_block), l < L ? h->Cbuf[l] : nullptr,
-                                  l < L ? h->RPbuf[l] : nullptr, l < L ? h->CPbuf[l] : nullptr};
-      std::vector<double *> db = {h->S, l + 1 < L ? h->Cbuf[l + 1] : nullptr, l + 1 < L ? h->RPbuf[l + 1] : nullptr,
-                                  l + 1 < L ? h->CPbuf[l + 1] : nullptr};
-      d.src_base = h->upload(sb);
-      d.dst_base = h->upload(db);
-    }
-    // ---- sparsification kernels, level by level ----
-    for (int l = 0; l < nlw; ++l) {
-      const LevelWork &w = p.lw[l];
-      LevelDev &d = h->lv[l];
-      if (l < L) {
-        if (l >= 1) {
-          ck(launch_stack_w(d.w, d.nw, h->Rr, h->transfer, d.W, s, &h->prof));
-          if (!p.sym) ck(launch_stack_w(d.wc, d.nw, h->Rrc, h->col_transfer, d.Wc, s, &h->prof));
-        }
-        ck(launch_householder(d.q, d.nq, h->leaf_basis, d.W, h->Q, h->Rr, std::max(w.max_m, 1), std::max(w.max_k, 1),
-                              s, &h->prof));
-        if (!p.sym)
-          ck(launch_householder(d.qc, d.nq, h->col_leaf_basis, d.Wc, h->Qc, h->Rrc, std::max(w.max_m, 1),
-                                std::max(w.max_k, 1), s, &h->prof));
-        ck(launch_coupling(d.c, d.nc, h->Rr, h->Rrc, h->coupling, d.dst_base, max_rank, s, &h->prof));
-      }
-      ck(launch_transform(d.x, d.nx, const_cast<const double *const *>(d.src_base), h->Q, h->Qc, d.dst_base, s,
-                            &h->prof, l < int(h->x_flops.size()) ? h->x_flops[l] : 0.0));
-    }
+    if (sp_prec == H2SP_FP32)
+      sparsify_levels<float>(h, p, sd, s);
+    else
+      sparsify_levels<double>(h, p, sd, s);
     // ---- structure views for the applies, products, factor and solves ----
     h->max_width = sd.max_width;
     h->top_src = sd.top_src;
@@ -927,6 +955,27 @@ int sparsify_numeric(h2sp_handle *h, const h2sp_h2_desc *desc, h2sp_stream strea
   return H2SP_OK;
 }
 
+// working precision of the sparsification selected by the options, -1 if they are malformed
+int32_t sparsify_prec_of(const h2sp_opts *opts) {
+  const int32_t f = opts ? opts->flags : 0;
+  if (f & ~int32_t(H2SP_SPARSIFY_FP32)) return -1;
+  return (f & H2SP_SPARSIFY_FP32) ? H2SP_FP32 : H2SP_FP64;
+}
+
+// device array of n values in the sparsification's precision -> n host doubles (synchronises)
+void copy_out(h2sp_handle *h, double *dst, const void *src, int64_t n) {
+  if (n <= 0) return;
+  if (h->sp_prec == H2SP_FP32) {
+    std::vector<float> tmp(static_cast<size_t>(n));
+    ck(cudaMemcpyAsync(tmp.data(), src, sizeof(float) * size_t(n), cudaMemcpyDeviceToHost, h->stream));
+    ck(cudaStreamSynchronize(h->stream));
+    for (int64_t i = 0; i < n; ++i) dst[i] = double(tmp[size_t(i)]);
+  } else {
+    ck(cudaMemcpyAsync(dst, src, sizeof(double) * size_t(n), cudaMemcpyDeviceToHost, h->stream));
+    ck(cudaStreamSynchronize(h->stream));
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -949,9 +998,10 @@ const char *h2sp_status_string(int32_t st) {
 const char *h2sp_last_cuda_error(void) { return g_cuda_err.c_str(); }
 
 int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream stream, h2sp_handle **out) {
-  (void)opts;
   if (!out) return H2SP_EINVAL;
   *out = nullptr;
+  const int32_t sp_prec = sparsify_prec_of(opts);
+  if (sp_prec < 0) return H2SP_EINVAL;
   h2sp_handle *h = new (std::nothrow) h2sp_handle();
   if (!h) return H2SP_ENOMEM;
   std::string err;
@@ -967,14 +1017,15 @@ int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream s
   h->plan_ptr = plan;
   h->cell = std::make_shared<StructureCell>();
   h->structure_hash = structure_hash(desc, *plan);
-  return sparsify_numeric(h, desc, stream, out);
+  return sparsify_numeric(h, desc, sp_prec, stream, out);
 }
 
 int h2sp_sparsify_analyzed(const h2sp_handle *an, const h2sp_h2_desc *desc, const h2sp_opts *opts,
                            h2sp_stream stream, h2sp_handle **out) {
-  (void)opts;
   if (!out) return H2SP_EINVAL;
   *out = nullptr;
+  const int32_t sp_prec = sparsify_prec_of(opts);
+  if (sp_prec < 0) return H2SP_EINVAL;
   if (!an || !an->plan_ptr || !an->cell || !desc) return H2SP_EINVAL;
   const Plan &ap = *an->plan_ptr;
   // same structure as the analysed descriptor (sizes first, then every structure array)
@@ -992,7 +1043,7 @@ int h2sp_sparsify_analyzed(const h2sp_handle *an, const h2sp_h2_desc *desc, cons
   h->cell = an->cell;
   h->structure_hash = an->structure_hash;
   h->plan_seconds = 0.0;
-  return sparsify_numeric(h, desc, stream, out);
+  return sparsify_numeric(h, desc, sp_prec, stream, out);
 }
 
 
@@ -1053,10 +1104,14 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
     ck(cudaMemsetAsync(h->fronts, 0, size_t(std::max<int64_t>(p.front_elems, 1)) * esz, s));
     ck(cudaMemsetAsync(h->err, 0, sizeof(int), s));
     const int64_t na = int64_t(p.assemble.size());
-    const double abytes = double(p.s_elems) * double(sizeof(double) + esz);
+    const double abytes = double(p.s_elems) * double((h->sp_prec == H2SP_FP32 ? sizeof(float) : sizeof(double)) + esz);
     if (prec == H2SP_FP64) {
       double *F = static_cast<double *>(h->fronts);
-      ck(launch_assemble<double>(h->asm_items, na, h->S, F, s, &h->prof, abytes));
+      if (h->sp_prec == H2SP_FP32)
+        ck(launch_assemble<float, double>(h->asm_items, na, static_cast<const float *>(h->S), F, s, &h->prof, abytes));
+      else
+        ck(launch_assemble<double, double>(h->asm_items, na, static_cast<const double *>(h->S), F, s, &h->prof,
+                                           abytes));
       for (const FrontLevel &L : h->flev) {
         ck(launch_lu_level<double>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv,
                                    h->swaps, h->err, s, la, &h->prof));
@@ -1073,7 +1128,11 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
         if (make_front_tmaps(p.fronts.data(), int(p.fronts.size()), F, m) == cudaSuccess) h->tmaps = m;
         cudaGetLastError();
       }
-      ck(launch_assemble<float>(h->asm_items, na, h->S, F, s, &h->prof, abytes));
+      if (h->sp_prec == H2SP_FP32)
+        ck(launch_assemble<float, float>(h->asm_items, na, static_cast<const float *>(h->S), F, s, &h->prof, abytes));
+      else
+        ck(launch_assemble<double, float>(h->asm_items, na, static_cast<const double *>(h->S), F, s, &h->prof,
+                                          abytes));
       for (const FrontLevel &L : h->flev) {
         ck(launch_lu_level<float>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv,
                                   h->swaps, h->err, s, la, &h->prof,
@@ -1112,8 +1171,12 @@ int h2sp_apply(h2sp_handle *h, int32_t op, int32_t nrhs, const double *in, int64
       case H2SP_OP_U: apply_N(h, false, in, ldin, out, ldout, nrhs); break;
       case H2SP_OP_V: apply_N(h, true, in, ldin, out, ldout, nrhs); break;
       case H2SP_OP_S:
-        ck(launch_spmv(h->brow_ptr, h->bcol, h->val_off, h->node_off, int(p.node_size.size()), h->S, in, ldin, out,
-                       ldout, nrhs, h->stream));
+        if (h->sp_prec == H2SP_FP32)
+          ck(launch_spmv(h->brow_ptr, h->bcol, h->val_off, h->node_off, int(p.node_size.size()),
+                         static_cast<const float *>(h->S), in, ldin, out, ldout, nrhs, h->stream));
+        else
+          ck(launch_spmv(h->brow_ptr, h->bcol, h->val_off, h->node_off, int(p.node_size.size()),
+                         static_cast<const double *>(h->S), in, ldin, out, ldout, nrhs, h->stream));
         break;
       case H2SP_OP_H2: h2_matvec(h, in, ldin, out, ldout, nrhs); break;
       case H2SP_OP_SINV:
@@ -1217,8 +1280,7 @@ int h2sp_export_S(h2sp_handle *h, int64_t *node_size, int64_t *brow_ptr, int32_t
   if (!vals) return H2SP_OK;
   if (!h->device_ready) return H2SP_ESTATE;
   try {
-    if (vals) ck(cudaMemcpyAsync(vals, h->S, sizeof(double) * p.s_elems, cudaMemcpyDeviceToHost, h->stream));
-    ck(cudaStreamSynchronize(h->stream));
+    copy_out(h, vals, h->S, p.s_elems);
   } catch (const CudaFail &f) {
     return status_of(f.e);
   }
@@ -1238,9 +1300,9 @@ int h2sp_export_Q(h2sp_handle *h, int32_t cluster, int32_t col, int64_t *m, doub
   if (q && !h->device_ready) return H2SP_ESTATE;
   if (q) {
     try {
-      ck(cudaMemcpyAsync(q, (col ? h->Qc : h->Q) + p.q_off[cluster], sizeof(double) * p.m[cluster] * p.m[cluster],
-                         cudaMemcpyDeviceToHost, h->stream));
-      ck(cudaStreamSynchronize(h->stream));
+      const size_t esz = (h->sp_prec == H2SP_FP32) ? sizeof(float) : sizeof(double);
+      copy_out(h, q, static_cast<const char *>(col ? h->Qc : h->Q) + esz * size_t(p.q_off[cluster]),
+               int64_t(p.m[cluster]) * p.m[cluster]);
     } catch (const CudaFail &f) {
       return status_of(f.e);
     }
@@ -1280,6 +1342,7 @@ int h2sp_query(const h2sp_handle *h, h2sp_stats *st) {
   st->factor_flops = p.factor_flops;
   st->sparsify_flops = p.sparsify_flops;
   st->factor_prec = h->prec;
+  st->sparsify_prec = h->device_ready ? h->sp_prec : -1;
   st->plan_seconds = h->plan_seconds;
   return H2SP_OK;
 }

@@ -13,7 +13,8 @@ namespace {
 constexpr int kRhs = 16;  // right-hand sides handled per kernel pass
 
 // Q^T applied to X_l(t); basis rows go to the next level, non-basis rows to S space
-__global__ void __launch_bounds__(64) k_apply_qt(const ApItem *__restrict__ items, const double *__restrict__ Q,
+template <typename TQ>
+__global__ void __launch_bounds__(64) k_apply_qt(const ApItem *__restrict__ items, const TQ *__restrict__ Q,
                                                  const double *__restrict__ x, int64_t ldx, double *__restrict__ ys,
                                                  int64_t ldys, double *__restrict__ xn, int64_t ldxn, int nrhs) {
   const ApItem it = items[blockIdx.x];
@@ -24,13 +25,13 @@ __global__ void __launch_bounds__(64) k_apply_qt(const ApItem *__restrict__ item
     sx[j + r * kMaxBlock] = x[it.xin + j + r * ldx];
   }
   __syncthreads();
-  const double *Qt = Q + it.q;
+  const TQ *Qt = Q + it.q;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     double acc[kRhs];
 #pragma unroll
     for (int r = 0; r < kRhs; ++r) acc[r] = 0.0;
     for (int j = 0; j < m; ++j) {
-      const double q = Qt[j + int64_t(i) * m];
+      const double q = double(Qt[j + int64_t(i) * m]);
 #pragma unroll
       for (int r = 0; r < kRhs; ++r)
         if (r < nrhs) acc[r] += q * sx[j + r * kMaxBlock];
@@ -44,7 +45,8 @@ __global__ void __launch_bounds__(64) k_apply_qt(const ApItem *__restrict__ item
   }
 }
 
-__global__ void __launch_bounds__(64) k_apply_q(const ApItem *__restrict__ items, const double *__restrict__ Q,
+template <typename TQ>
+__global__ void __launch_bounds__(64) k_apply_q(const ApItem *__restrict__ items, const TQ *__restrict__ Q,
                                                 const double *__restrict__ xn, int64_t ldxn,
                                                 const double *__restrict__ ys, int64_t ldys, double *__restrict__ x,
                                                 int64_t ldx, int nrhs) {
@@ -62,13 +64,13 @@ __global__ void __launch_bounds__(64) k_apply_q(const ApItem *__restrict__ items
     sz[j + r * kMaxBlock] = v;
   }
   __syncthreads();
-  const double *Qt = Q + it.q;
+  const TQ *Qt = Q + it.q;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     double acc[kRhs];
 #pragma unroll
     for (int r = 0; r < kRhs; ++r) acc[r] = 0.0;
     for (int j = 0; j < m; ++j) {
-      const double q = Qt[i + int64_t(j) * m];
+      const double q = double(Qt[i + int64_t(j) * m]);
 #pragma unroll
       for (int r = 0; r < kRhs; ++r)
         if (r < nrhs) acc[r] += q * sz[j + r * kMaxBlock];
@@ -88,9 +90,10 @@ __global__ void k_copy_rows(const int64_t *__restrict__ src_row, const int64_t *
   }
 }
 
+template <typename TS>
 __global__ void __launch_bounds__(128) k_spmv(const int64_t *__restrict__ brow_ptr, const int32_t *__restrict__ bcol,
                                               const int64_t *__restrict__ val_off, const int64_t *__restrict__ node_off,
-                                              const double *__restrict__ vals, const double *__restrict__ x, int64_t ldx,
+                                              const TS *__restrict__ vals, const double *__restrict__ x, int64_t ldx,
                                               double *__restrict__ y, int64_t ldy, int nrhs) {
   const int i = blockIdx.x;
   const int64_t r0 = node_off[i];
@@ -105,7 +108,7 @@ __global__ void __launch_bounds__(128) k_spmv(const int64_t *__restrict__ brow_p
       const int j = bcol[z];
       const int64_t c0 = node_off[j];
       const int dj = int(node_off[j + 1] - c0);
-      const double *blk = vals + val_off[z];
+      const TS *blk = vals + val_off[z];
       for (int cb = 0; cb < dj; cb += 64) {
         const int nc = min(64, dj - cb);
         __syncthreads();
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(128) k_spmv(const int64_t *__restrict__ brow_p
         __syncthreads();
         if (row < di)
           for (int c = 0; c < nc; ++c) {
-            const double a = blk[row + int64_t(cb + c) * di];
+            const double a = double(blk[row + int64_t(cb + c) * di]);
 #pragma unroll
             for (int r = 0; r < kRhs; ++r)
               if (r < nrhs) acc[r] += a * sx[c + r * 64];
@@ -425,23 +428,34 @@ inline unsigned grid_for(int64_t n, int per = 256) {
 
 }  // namespace
 
-cudaError_t launch_apply_qt(const ApItem *items, int n, const double *Q, const double *x, int64_t ldx, double *ys,
+template <typename TQ>
+cudaError_t launch_apply_qt(const ApItem *items, int n, const TQ *Q, const double *x, int64_t ldx, double *ys,
                             int64_t ldys, double *xn, int64_t ldxn, int nrhs, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   for (int r0 = 0; r0 < nrhs; r0 += kRhs)
-    k_apply_qt<<<n, 64, 0, s>>>(items, Q, x + r0 * ldx, ldx, ys + r0 * ldys, ldys, xn ? xn + r0 * ldxn : nullptr,
-                                ldxn, std::min(kRhs, nrhs - r0));
+    k_apply_qt<TQ><<<n, 64, 0, s>>>(items, Q, x + r0 * ldx, ldx, ys + r0 * ldys, ldys, xn ? xn + r0 * ldxn : nullptr,
+                                    ldxn, std::min(kRhs, nrhs - r0));
   return cudaGetLastError();
 }
 
-cudaError_t launch_apply_q(const ApItem *items, int n, const double *Q, const double *xn, int64_t ldxn,
-                           const double *ys, int64_t ldys, double *x, int64_t ldx, int nrhs, cudaStream_t s) {
+template <typename TQ>
+cudaError_t launch_apply_q(const ApItem *items, int n, const TQ *Q, const double *xn, int64_t ldxn, const double *ys,
+                           int64_t ldys, double *x, int64_t ldx, int nrhs, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   for (int r0 = 0; r0 < nrhs; r0 += kRhs)
-    k_apply_q<<<n, 64, 0, s>>>(items, Q, xn ? xn + r0 * ldxn : nullptr, ldxn, ys + r0 * ldys, ldys, x + r0 * ldx, ldx,
-                               std::min(kRhs, nrhs - r0));
+    k_apply_q<TQ><<<n, 64, 0, s>>>(items, Q, xn ? xn + r0 * ldxn : nullptr, ldxn, ys + r0 * ldys, ldys, x + r0 * ldx,
+                                   ldx, std::min(kRhs, nrhs - r0));
   return cudaGetLastError();
 }
+
+template cudaError_t launch_apply_qt<double>(const ApItem *, int, const double *, const double *, int64_t, double *,
+                                             int64_t, double *, int64_t, int, cudaStream_t);
+template cudaError_t launch_apply_qt<float>(const ApItem *, int, const float *, const double *, int64_t, double *,
+                                            int64_t, double *, int64_t, int, cudaStream_t);
+template cudaError_t launch_apply_q<double>(const ApItem *, int, const double *, const double *, int64_t,
+                                            const double *, int64_t, double *, int64_t, int, cudaStream_t);
+template cudaError_t launch_apply_q<float>(const ApItem *, int, const float *, const double *, int64_t, const double *,
+                                           int64_t, double *, int64_t, int, cudaStream_t);
 
 cudaError_t launch_copy_rows(const int64_t *src_row, const int64_t *dst_row, const int32_t *len, int n,
                              const double *src, int64_t lds, double *dst, int64_t ldd, int nrhs, cudaStream_t s) {
@@ -450,15 +464,22 @@ cudaError_t launch_copy_rows(const int64_t *src_row, const int64_t *dst_row, con
   return cudaGetLastError();
 }
 
+template <typename TS>
 cudaError_t launch_spmv(const int64_t *brow_ptr, const int32_t *bcol, const int64_t *val_off, const int64_t *node_off,
-                        int nnodes, const double *vals, const double *x, int64_t ldx, double *y, int64_t ldy, int nrhs,
+                        int nnodes, const TS *vals, const double *x, int64_t ldx, double *y, int64_t ldy, int nrhs,
                         cudaStream_t s) {
   if (nnodes == 0) return cudaSuccess;
   for (int r0 = 0; r0 < nrhs; r0 += kRhs)
-    k_spmv<<<nnodes, 128, 0, s>>>(brow_ptr, bcol, val_off, node_off, vals, x + r0 * ldx, ldx, y + r0 * ldy, ldy,
-                                  std::min(kRhs, nrhs - r0));
+    k_spmv<TS><<<nnodes, 128, 0, s>>>(brow_ptr, bcol, val_off, node_off, vals, x + r0 * ldx, ldx, y + r0 * ldy, ldy,
+                                      std::min(kRhs, nrhs - r0));
   return cudaGetLastError();
 }
+
+template cudaError_t launch_spmv<double>(const int64_t *, const int32_t *, const int64_t *, const int64_t *, int,
+                                         const double *, const double *, int64_t, double *, int64_t, int,
+                                         cudaStream_t);
+template cudaError_t launch_spmv<float>(const int64_t *, const int32_t *, const int64_t *, const int64_t *, int,
+                                        const float *, const double *, int64_t, double *, int64_t, int, cudaStream_t);
 
 cudaError_t launch_h2_matvec(const H2Dev &h, const int32_t *level_ptr_host, const int32_t *child_start,
                              const int32_t *child_cnt, int depth, const double *x, int64_t ldx, double *y,

@@ -33,11 +33,11 @@ __device__ __forceinline__ T tabs(T x) {
   return fabs(x);
 }
 
-template <typename T>
-__global__ void k_assemble(const AItem *__restrict__ items, const double *__restrict__ S, T *__restrict__ F) {
+template <typename TS, typename T>
+__global__ void k_assemble(const AItem *__restrict__ items, const TS *__restrict__ S, T *__restrict__ F) {
   const AItem it = items[blockIdx.x];
   const int n = it.rows * it.cols;
-  const double *src = S + it.src;
+  const TS *src = S + it.src;
   T *dst = F + it.dst;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int r = i % it.rows, c = i / it.rows;
@@ -1496,12 +1496,12 @@ int panel_cluster_size(int R) {
 
 }  // namespace
 
-template <typename T>
-cudaError_t launch_assemble(const AItem *items, int64_t n, const double *S, T *fronts, cudaStream_t s, Prof *prof,
+template <typename TS, typename T>
+cudaError_t launch_assemble(const AItem *items, int64_t n, const TS *S, T *fronts, cudaStream_t s, Prof *prof,
                             double bytes) {
   if (n == 0) return cudaSuccess;
   const size_t e0 = prof->begin();
-  k_assemble<T><<<unsigned(n), 128, 0, s>>>(items, S, fronts);
+  k_assemble<TS, T><<<unsigned(n), 128, 0, s>>>(items, S, fronts);
   prof->end(P_ASSEMBLE, 1, e0, bytes);
   return cudaGetLastError();
 }
@@ -1797,8 +1797,10 @@ cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, 
   return cudaGetLastError();
 }
 
-template cudaError_t launch_assemble<double>(const AItem *, int64_t, const double *, double *, cudaStream_t, Prof *,
-                                           double);
+template cudaError_t launch_assemble<double, double>(const AItem *, int64_t, const double *, double *, cudaStream_t,
+                                                     Prof *, double);
+template cudaError_t launch_assemble<float, double>(const AItem *, int64_t, const float *, double *, cudaStream_t,
+                                                    Prof *, double);
 template cudaError_t launch_lu_level<double>(const FrontDev *, const Front *, int, int, int, double *, int32_t *, int32_t *,
                                            int *, cudaStream_t, const LuAsync *, Prof *,
                                            const uint8_t *);
@@ -1814,8 +1816,10 @@ template cudaError_t launch_solve_bwd_level_impl<double>(const FrontDev *, int, 
                                                        const int32_t *, double *, int64_t, int, double *, double *,
                                                        const int64_t *, cudaStream_t, Prof *, double,
                                                        const ChainArgs *, int);
-template cudaError_t launch_assemble<float>(const AItem *, int64_t, const double *, float *, cudaStream_t, Prof *,
-                                           double);
+template cudaError_t launch_assemble<double, float>(const AItem *, int64_t, const double *, float *, cudaStream_t,
+                                                    Prof *, double);
+template cudaError_t launch_assemble<float, float>(const AItem *, int64_t, const float *, float *, cudaStream_t, Prof *,
+                                                   double);
 template cudaError_t launch_lu_level<float>(const FrontDev *, const Front *, int, int, int, float *, int32_t *, int32_t *,
                                            int *, cudaStream_t, const LuAsync *, Prof *,
                                            const uint8_t *);

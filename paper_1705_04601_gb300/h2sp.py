@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "libh2sp.so")
 H2SP_OK, H2SP_EINVAL, H2SP_ENOMEM, H2SP_ECUDA, H2SP_ESINGULAR = 0, -1, -2, -3, -4
 H2SP_ESTATE, H2SP_ENOCONV, H2SP_ETIMEOUT, H2SP_EUNSUPPORTED = -5, -6, -7, -8
 H2SP_FP64, H2SP_FP32 = 0, 1
+H2SP_SPARSIFY_FP32 = 1  # h2sp_opts.flags bit
 H2SP_OP_UT, H2SP_OP_V, H2SP_OP_U, H2SP_OP_VT, H2SP_OP_S, H2SP_OP_H2, H2SP_OP_SINV = range(7)
 H2SP_DIRECT, H2SP_IR, H2SP_GMRES = 0, 1, 2
 
@@ -61,7 +62,7 @@ class Stats(ctypes.Structure):
         ("nnzb", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nsupernodes", ctypes.c_int32),
         ("nfront_levels", ctypes.c_int32), ("max_front", ctypes.c_int64), ("front_elems", ctypes.c_int64),
         ("factor_flops", ctypes.c_double), ("sparsify_flops", ctypes.c_double), ("factor_prec", ctypes.c_int32),
-        ("plan_seconds", ctypes.c_double),
+        ("plan_seconds", ctypes.c_double), ("sparsify_prec", ctypes.c_int32),
     ]
 
 
@@ -214,20 +215,20 @@ def h2sp_analyze(inp: H2Input) -> Handle:
     return Handle(out, inp)
 
 
-def h2sp_sparsify(inp: H2Input, stream=None) -> Handle:
+def h2sp_sparsify(inp: H2Input, stream=None, flags: int = 0) -> Handle:
     out = _vp()
     d = inp.desc()
-    o = Opts(0)
+    o = Opts(int(flags))
     _check(lib().h2sp_sparsify(ctypes.byref(d), ctypes.byref(o), _stream(stream), ctypes.byref(out)),
            "h2sp_sparsify")
     return Handle(out, inp)
 
 
-def h2sp_sparsify_analyzed(an: Handle, inp: H2Input, stream=None) -> Handle:
+def h2sp_sparsify_analyzed(an: Handle, inp: H2Input, stream=None, flags: int = 0) -> Handle:
     """h2sp_sparsify with the host analysis of `an` (same structure, new numbers)."""
     out = _vp()
     d = inp.desc()
-    o = Opts(0)
+    o = Opts(int(flags))
     _check(lib().h2sp_sparsify_analyzed(an.ptr, ctypes.byref(d), ctypes.byref(o), _stream(stream),
                                         ctypes.byref(out)), "h2sp_sparsify_analyzed")
     return Handle(out, inp)

@@ -203,3 +203,28 @@ def test_sparsify_analyzed_rejects_a_different_structure():
                                           ctypes.byref(out)) == H.H2SP_EINVAL
     assert not out
     an.close()
+
+
+def test_unknown_option_bits_are_rejected():
+    """h2sp_opts.flags accepts H2SP_SPARSIFY_FP32 only; any other bit is
+    refused on the host before planning or launching."""
+    h = _make("log1k")
+    inp = H.H2Input(h, device=None)
+    d, keep = _with_fake_numbers(inp)
+    out = H._vp()
+    for bad in (2, 4, 1 << 30, -1):
+        o = H.Opts(bad)
+        assert H.lib().h2sp_sparsify(ctypes.byref(d), ctypes.byref(o), None, ctypes.byref(out)) == H.H2SP_EINVAL
+        an = H.h2sp_analyze(H.H2Input(h, device=None))
+        assert H.lib().h2sp_sparsify_analyzed(an.ptr, ctypes.byref(d), ctypes.byref(o), None,
+                                              ctypes.byref(out)) == H.H2SP_EINVAL
+        an.close()
+    assert not out
+
+
+def test_analysis_handle_reports_no_sparsify_precision():
+    h = _make("log1k")
+    an = H.h2sp_analyze(H.H2Input(h, device=None))
+    st = H.h2sp_query(an)
+    assert st["sparsify_prec"] == -1 and st["factor_prec"] == -1
+    an.close()

@@ -339,3 +339,84 @@ def test_sparsify_analyzed_matches_sparsify(name):
     assert np.linalg.norm(host(xt) - xo) / np.linalg.norm(xo) <= 1e-10
     full.close()
     hd.close()
+
+
+@pytest.mark.parametrize("name", ["log1k", "skew1k", "ragged", "inv3d"])
+def test_fp32_sparsification_matches_oracle(name):
+    """H2SP_SPARSIFY_FP32 computes Q and S in FP32 from the FP64 H^2 numbers.
+    Householder QR and the two-sided orthogonal transforms are backward stable,
+    so each Q and each block row of S stays within a small multiple of the
+    FP32 unit roundoff (6e-8) times the block sizes (<= 64) and levels of the
+    FP64 result; 1e-4 allows ~25 u per level for up to 6 levels of 64-row
+    blocks.  The pattern is integer work and must be identical."""
+    h, b, sp = case(name)
+    hd = H.h2sp_sparsify(H.H2Input(h), flags=H.H2SP_SPARSIFY_FP32)
+    assert H.h2sp_query(hd)["sparsify_prec"] == H.H2SP_FP32
+    S = H.h2sp_export_S(hd)
+    vbr = osp.to_vbr(sp)
+    assert np.array_equal(S["brow_ptr"], vbr.brow_ptr) and np.array_equal(S["bcol_idx"], vbr.bcol_idx)
+    ns = vbr.node_size
+    worst = 0.0
+    for i in range(ns.size):
+        lo, hi = int(vbr.brow_ptr[i]), int(vbr.brow_ptr[i + 1])
+        if hi == lo:
+            continue
+        a, e = int(vbr.val_off[lo]), int(vbr.val_off[hi - 1] + ns[i] * ns[vbr.bcol_idx[hi - 1]])
+        ref_row = max(np.linalg.norm(vbr.vals[a:e]), 1e-300)
+        worst = max(worst, np.linalg.norm(S["vals"][a:e] - vbr.vals[a:e]) / ref_row)
+    qworst = 0.0
+    for t in sp.Q:
+        qworst = max(qworst, np.linalg.norm(H.h2sp_export_Q(hd, t) - sp.Q[t]) / np.linalg.norm(sp.Q[t]))
+        if not h.symmetric_bases:
+            qworst = max(qworst, np.linalg.norm(H.h2sp_export_Q(hd, t, col=True) - sp.Qc[t]) /
+                         np.linalg.norm(sp.Qc[t]))
+    print("fp32 sparsify (%s): S row-block rel %.2e, Q rel %.2e" % (name, worst, qworst))
+    assert worst <= 1e-4 and qworst <= 1e-4
+    hd.close()
+
+
+@pytest.mark.parametrize("name,mode", [("log4k", "gmres"), ("skew1k", "gmres"), ("ragged", "gmres"),
+                                       ("log4k", "ir")])
+def test_fp32_sparsify_and_factor_reach_1e10(name, mode):
+    """The all-FP32 preconditioner (FP32 U, S, V and FP32 factors) still
+    drives GMRES / refinement on the FP64 H^2 residual to 1e-10 (§5.5), and
+    the solution agrees with the dense FP64 solve to what that residual
+    implies."""
+    h, b, sp = case(name)
+    hd = H.h2sp_sparsify(H.H2Input(h), flags=H.H2SP_SPARSIFY_FP32)
+    H.h2sp_factor(hd, H.H2SP_FP32)
+    bt = dev(b)
+    xt = torch.empty_like(bt)
+    if mode == "gmres":
+        info = H.h2sp_solve(hd, bt, xt, mode=H.H2SP_GMRES, tol=1e-10, maxit=60, restart=20)
+    else:
+        info = H.h2sp_solve(hd, bt, xt, mode=H.H2SP_IR, tol=1e-10, maxit=30)
+    print("fp32 sparsify + fp32 factor (%s, %s): %d iterations, residual %.2e" %
+          (name, mode, info.iters, info.rel_residual))
+    assert info.status == H.H2SP_OK and info.rel_residual <= 1e-10
+    A = oh2.dense(h)
+    xg = host(xt)
+    res = np.linalg.norm(b - A @ xg, axis=0) / np.linalg.norm(b, axis=0)
+    assert res.max() <= 2e-10
+    xd = np.linalg.solve(A, b)
+    assert np.linalg.norm(xg - xd) <= 1e-7 * np.linalg.norm(xd)
+    hd.close()
+
+
+def test_fp32_sparsify_products_stay_fp64_vectors():
+    """With FP32 U, S and V the applies still take and return FP64 vectors;
+    each differs from the FP64 oracle's by FP32 rounding of the operator
+    only (<= 1e-4 relative)."""
+    h, b, sp = case("skew1k")
+    hd = H.h2sp_sparsify(H.H2Input(h), flags=H.H2SP_SPARSIFY_FP32)
+    bt = dev(b)
+    out = torch.empty_like(bt)
+    for op, ref in [(H.H2SP_OP_UT, osp.apply_T(sp, h, b, col=False)), (H.H2SP_OP_VT, osp.apply_T(sp, h, b, col=True)),
+                    (H.H2SP_OP_U, osp.apply_N(sp, h, b, col=False)), (H.H2SP_OP_V, osp.apply_N(sp, h, b, col=True)),
+                    (H.H2SP_OP_S, osp.dense_S(sp) @ b), (H.H2SP_OP_H2, oh2.Matvec(h)(b))]:
+        H.h2sp_apply(hd, op, bt, out)
+        torch.cuda.synchronize()
+        rel = np.linalg.norm(host(out) - ref) / np.linalg.norm(ref)
+        # the H^2 product does not use the sparsification: still FP64-exact
+        assert rel <= (1e-12 if op == H.H2SP_OP_H2 else 1e-4), (op, rel)
+    hd.close()
