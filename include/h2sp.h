@@ -127,12 +127,13 @@ typedef struct {
 
 /* Bits of h2sp_opts.flags. */
 enum {
-  /* Sparsify in FP32: Q, the coupling projections, the level buffers and S
-   * are computed and stored in FP32 (the H^2 inputs stay FP64 and are rounded
-   * on load).  Meant for the mixed-precision solve, where U, S and V only
-   * build the FP32 preconditioner and the FP64 H^2 product of Definition 4.9
-   * decides convergence (§5.5); the applies and products of the handle still
-   * take and return FP64 vectors and sum in FP64. */
+  /* Sparsify with FP32 products: the sandwich products of the close blocks
+   * and cross-level panels (Eq. cl0) run in FP32 and S is stored in FP32,
+   * while the Householder completions (U and V orthogonal to FP64 accuracy)
+   * and the coupling projections stay FP64.  Meant for the mixed-precision
+   * solve, where S only builds the FP32 preconditioner and the FP64 H^2
+   * product of Definition 4.9 decides convergence (§5.5); every apply and
+   * product of the handle still takes and returns FP64 vectors. */
   H2SP_SPARSIFY_FP32 = 1
 };
 
@@ -166,7 +167,7 @@ typedef struct {
   double sparsify_flops;          /* algorithmic flops of the sparsification */
   int32_t factor_prec;            /* h2sp_prec of the current factors, -1 if none */
   double plan_seconds;            /* host time spent planning in the last h2sp_sparsify */
-  int32_t sparsify_prec;          /* h2sp_prec of U, V and S; -1 for an analysis-only handle */
+  int32_t sparsify_prec;          /* h2sp_prec of S (U and V are always FP64); -1 for an analysis-only handle */
 } h2sp_stats;
 
 /*
@@ -175,8 +176,8 @@ typedef struct {
  * H2SP_EINVAL without launching anything if it is malformed: unsorted lists,
  * inconsistent tree, ranks that do not fit, a missing column array), plans
  * the level recursion and the symbolic factorization of S on the host, and
- * enqueues the kernels (FP64, or FP32 with H2SP_SPARSIFY_FP32) on `stream`:
- * the Householder completions of the
+ * enqueues the kernels on `stream` (FP64; the products into S in FP32 with
+ * H2SP_SPARSIFY_FP32): the Householder completions of the
  * cluster bases per level, the coupling projections, the transforms of the
  * close blocks and of the cross-level panels, and the scatter into S.
  * On success *out owns a new handle.

@@ -42,7 +42,7 @@ struct LevelDev {
   XItem *x = nullptr;
   int nq = 0, nw = 0, nc = 0, nx = 0;
   void **src_base = nullptr, **dst_base = nullptr;  // device arrays of 4 pointers
-  void *W = nullptr, *Wc = nullptr;                 // stacked bases, in the sparsification's precision
+  double *W = nullptr, *Wc = nullptr;
   ApItem *ap = nullptr;  // applies of this level's Q blocks
   int nap = 0;
 };
@@ -114,10 +114,11 @@ struct h2sp_handle {
   // borrowed H^2 numbers
   const double *leaf_basis = nullptr, *transfer = nullptr, *coupling = nullptr, *near_block = nullptr;
   const double *col_leaf_basis = nullptr, *col_transfer = nullptr;
-  // sparsification: Q, R, S and the level buffers hold doubles, or floats
-  // when sp_prec is H2SP_FP32
+  // sparsification: Q and R are FP64; S and the level buffers that feed it
+  // hold doubles, or floats when sp_prec is H2SP_FP32
   int sp_prec = H2SP_FP64;
-  void *Q = nullptr, *Qc = nullptr, *Rr = nullptr, *Rrc = nullptr, *S = nullptr;
+  double *Q = nullptr, *Qc = nullptr, *Rr = nullptr, *Rrc = nullptr;
+  void *S = nullptr;
   std::vector<void *> Cbuf, RPbuf, CPbuf;
   std::vector<LevelDev> lv;
   // applies
@@ -258,7 +259,7 @@ void apply_T(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *o
     int n;
     ~Done() { h->prof.end(P_APPLY, n, e0, 0.0); }
   } done{h, e0, 1 + p.lstop * chunks};
-  const void *Qb = col ? h->Qc : h->Q;
+  const double *Qb = col ? h->Qc : h->Q;
   if (p.lstop == 0) {
     ck(launch_copy_rows(h->top_src, h->top_dst, h->top_len, h->ntop, in, ldin, out, ldout, nrhs, s));
     return;
@@ -269,12 +270,7 @@ void apply_T(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *o
   double *bufs[2] = {h->vecA, h->vecB};
   for (int l = 0; l < p.lstop; ++l) {
     double *xn = bufs[l & 1];
-    if (h->sp_prec == H2SP_FP32)
-      ck(launch_apply_qt(h->lv[l].ap, h->lv[l].nap, static_cast<const float *>(Qb), x, ldx, out, ldout, xn, ldw, nrhs,
-                         s));
-    else
-      ck(launch_apply_qt(h->lv[l].ap, h->lv[l].nap, static_cast<const double *>(Qb), x, ldx, out, ldout, xn, ldw,
-                         nrhs, s));
+    ck(launch_apply_qt(h->lv[l].ap, h->lv[l].nap, Qb, x, ldx, out, ldout, xn, ldw, nrhs, s));
     x = xn;
     ldx = ldw;
   }
@@ -293,7 +289,7 @@ void apply_N(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *o
     int n;
     ~Done() { h->prof.end(P_APPLY, n, e0, 0.0); }
   } done{h, e0, 1 + p.lstop * chunks};
-  const void *Qb = col ? h->Qc : h->Q;
+  const double *Qb = col ? h->Qc : h->Q;
   if (p.lstop == 0) {
     ck(launch_copy_rows(h->top_dst, h->top_src, h->top_len, h->ntop, in, ldin, out, ldout, nrhs, s));
     return;
@@ -305,12 +301,7 @@ void apply_N(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *o
   for (int l = p.lstop - 1; l >= 0; --l) {
     double *x = (l == 0) ? out : bufs[l & 1];
     const int64_t ldx = (l == 0) ? ldout : ldw;
-    if (h->sp_prec == H2SP_FP32)
-      ck(launch_apply_q(h->lv[l].ap, h->lv[l].nap, static_cast<const float *>(Qb), xn, ldw, in, ldin, x, ldx, nrhs,
-                        s));
-    else
-      ck(launch_apply_q(h->lv[l].ap, h->lv[l].nap, static_cast<const double *>(Qb), xn, ldw, in, ldin, x, ldx, nrhs,
-                        s));
+    ck(launch_apply_q(h->lv[l].ap, h->lv[l].nap, Qb, xn, ldw, in, ldin, x, ldx, nrhs, s));
     xn = x;
   }
 }
@@ -797,19 +788,18 @@ std::shared_ptr<StructureDev> build_structure(const Plan &p) {
   return sd;
 }
 
-// the level recursion of the sparsification (§2.1-2.3, §4.2-4.3) in working
-// precision W on the handle's buffers
+// the level recursion of the sparsification (§2.1-2.3, §4.2-4.3): FP64
+// Householder completions and couplings, products into S in precision W
 template <typename W>
 void sparsify_levels(h2sp_handle *h, const Plan &p, const StructureDev &sd, cudaStream_t s) {
   const int L = p.lstop;
   const int nlw = int(p.lw.size());
-  auto buf = [](void *q) { return static_cast<W *>(q); };
   for (int l = 0; l < nlw; ++l) {
     const LevelWork &w = p.lw[l];
     LevelDev &d = h->lv[l];
     if (l >= 1) {
-      d.W = h->alloc<W>(size_t(w.w_elems));
-      if (!p.sym) d.Wc = h->alloc<W>(size_t(w.wc_elems));
+      d.W = h->alloc<double>(size_t(w.w_elems));
+      if (!p.sym) d.Wc = h->alloc<double>(size_t(w.wc_elems));
     }
     std::vector<void *> sb = {const_cast<double *>(h->near_block), l < L ? h->Cbuf[l] : nullptr,
                               l < L ? h->RPbuf[l] : nullptr, l < L ? h->CPbuf[l] : nullptr};
@@ -823,18 +813,18 @@ void sparsify_levels(h2sp_handle *h, const Plan &p, const StructureDev &sd, cuda
     LevelDev &d = h->lv[l];
     if (l < L) {
       if (l >= 1) {
-        ck(launch_stack_w<W>(d.w, d.nw, buf(h->Rr), h->transfer, buf(d.W), s, &h->prof));
-        if (!p.sym) ck(launch_stack_w<W>(d.wc, d.nw, buf(h->Rrc), h->col_transfer, buf(d.Wc), s, &h->prof));
+        ck(launch_stack_w(d.w, d.nw, h->Rr, h->transfer, d.W, s, &h->prof));
+        if (!p.sym) ck(launch_stack_w(d.wc, d.nw, h->Rrc, h->col_transfer, d.Wc, s, &h->prof));
       }
-      ck(launch_householder<W>(d.q, d.nq, h->leaf_basis, buf(d.W), buf(h->Q), buf(h->Rr), std::max(w.max_m, 1),
-                               std::max(w.max_k, 1), s, &h->prof));
+      ck(launch_householder(d.q, d.nq, h->leaf_basis, d.W, h->Q, h->Rr, std::max(w.max_m, 1), std::max(w.max_k, 1),
+                            s, &h->prof));
       if (!p.sym)
-        ck(launch_householder<W>(d.qc, d.nq, h->col_leaf_basis, buf(d.Wc), buf(h->Qc), buf(h->Rrc),
-                                 std::max(w.max_m, 1), std::max(w.max_k, 1), s, &h->prof));
-      ck(launch_coupling<W>(d.c, d.nc, buf(h->Rr), buf(h->Rrc), h->coupling,
-                            reinterpret_cast<W *const *>(d.dst_base), sd.max_rank, s, &h->prof));
+        ck(launch_householder(d.qc, d.nq, h->col_leaf_basis, d.Wc, h->Qc, h->Rrc, std::max(w.max_m, 1),
+                              std::max(w.max_k, 1), s, &h->prof));
+      ck(launch_coupling<W>(d.c, d.nc, h->Rr, h->Rrc, h->coupling, reinterpret_cast<W *const *>(d.dst_base),
+                            sd.max_rank, s, &h->prof));
     }
-    ck(launch_transform<W>(d.x, d.nx, const_cast<const void *const *>(d.src_base), buf(h->Q), buf(h->Qc),
+    ck(launch_transform<W>(d.x, d.nx, const_cast<const void *const *>(d.src_base), h->Q, h->Qc,
                            reinterpret_cast<W *const *>(d.dst_base), s, &h->prof,
                            l < int(h->x_flops.size()) ? h->x_flops[l] : 0.0));
   }
@@ -868,14 +858,14 @@ int sparsify_numeric(h2sp_handle *h, const h2sp_h2_desc *desc, int32_t sp_prec, 
     // ---- owned buffers ----
     const size_t wsz = (sp_prec == H2SP_FP32) ? sizeof(float) : sizeof(double);
     auto walloc = [&](int64_t n) -> void * { return h->alloc<char>(size_t(std::max<int64_t>(n, 1)) * wsz); };
-    h->Q = walloc(p.q_elems);
-    h->Rr = walloc(p.rr_elems);
+    h->Q = h->alloc<double>(size_t(p.q_elems));
+    h->Rr = h->alloc<double>(size_t(p.rr_elems));
     if (p.sym) {
       h->Qc = h->Q;
       h->Rrc = h->Rr;
     } else {
-      h->Qc = walloc(p.q_elems);
-      h->Rrc = walloc(p.rr_elems);
+      h->Qc = h->alloc<double>(size_t(p.q_elems));
+      h->Rrc = h->alloc<double>(size_t(p.rr_elems));
     }
     h->S = walloc(p.s_elems);
     ck(cudaMemsetAsync(h->S, 0, wsz * size_t(std::max<int64_t>(p.s_elems, 1)), s));
@@ -962,7 +952,7 @@ int32_t sparsify_prec_of(const h2sp_opts *opts) {
   return (f & H2SP_SPARSIFY_FP32) ? H2SP_FP32 : H2SP_FP64;
 }
 
-// device array of n values in the sparsification's precision -> n host doubles (synchronises)
+// device array of n values of S's precision -> n host doubles (synchronises)
 void copy_out(h2sp_handle *h, double *dst, const void *src, int64_t n) {
   if (n <= 0) return;
   if (h->sp_prec == H2SP_FP32) {
@@ -1300,9 +1290,9 @@ int h2sp_export_Q(h2sp_handle *h, int32_t cluster, int32_t col, int64_t *m, doub
   if (q && !h->device_ready) return H2SP_ESTATE;
   if (q) {
     try {
-      const size_t esz = (h->sp_prec == H2SP_FP32) ? sizeof(float) : sizeof(double);
-      copy_out(h, q, static_cast<const char *>(col ? h->Qc : h->Q) + esz * size_t(p.q_off[cluster]),
-               int64_t(p.m[cluster]) * p.m[cluster]);
+      ck(cudaMemcpyAsync(q, (col ? h->Qc : h->Q) + p.q_off[cluster], sizeof(double) * p.m[cluster] * p.m[cluster],
+                         cudaMemcpyDeviceToHost, h->stream));
+      ck(cudaStreamSynchronize(h->stream));
     } catch (const CudaFail &f) {
       return status_of(f.e);
     }

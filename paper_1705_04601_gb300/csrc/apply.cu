@@ -13,8 +13,7 @@ namespace {
 constexpr int kRhs = 16;  // right-hand sides handled per kernel pass
 
 // Q^T applied to X_l(t); basis rows go to the next level, non-basis rows to S space
-template <typename TQ>
-__global__ void __launch_bounds__(64) k_apply_qt(const ApItem *__restrict__ items, const TQ *__restrict__ Q,
+__global__ void __launch_bounds__(64) k_apply_qt(const ApItem *__restrict__ items, const double *__restrict__ Q,
                                                  const double *__restrict__ x, int64_t ldx, double *__restrict__ ys,
                                                  int64_t ldys, double *__restrict__ xn, int64_t ldxn, int nrhs) {
   const ApItem it = items[blockIdx.x];
@@ -25,13 +24,13 @@ __global__ void __launch_bounds__(64) k_apply_qt(const ApItem *__restrict__ item
     sx[j + r * kMaxBlock] = x[it.xin + j + r * ldx];
   }
   __syncthreads();
-  const TQ *Qt = Q + it.q;
+  const double *Qt = Q + it.q;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     double acc[kRhs];
 #pragma unroll
     for (int r = 0; r < kRhs; ++r) acc[r] = 0.0;
     for (int j = 0; j < m; ++j) {
-      const double q = double(Qt[j + int64_t(i) * m]);
+      const double q = Qt[j + int64_t(i) * m];
 #pragma unroll
       for (int r = 0; r < kRhs; ++r)
         if (r < nrhs) acc[r] += q * sx[j + r * kMaxBlock];
@@ -45,8 +44,7 @@ __global__ void __launch_bounds__(64) k_apply_qt(const ApItem *__restrict__ item
   }
 }
 
-template <typename TQ>
-__global__ void __launch_bounds__(64) k_apply_q(const ApItem *__restrict__ items, const TQ *__restrict__ Q,
+__global__ void __launch_bounds__(64) k_apply_q(const ApItem *__restrict__ items, const double *__restrict__ Q,
                                                 const double *__restrict__ xn, int64_t ldxn,
                                                 const double *__restrict__ ys, int64_t ldys, double *__restrict__ x,
                                                 int64_t ldx, int nrhs) {
@@ -64,13 +62,13 @@ __global__ void __launch_bounds__(64) k_apply_q(const ApItem *__restrict__ items
     sz[j + r * kMaxBlock] = v;
   }
   __syncthreads();
-  const TQ *Qt = Q + it.q;
+  const double *Qt = Q + it.q;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     double acc[kRhs];
 #pragma unroll
     for (int r = 0; r < kRhs; ++r) acc[r] = 0.0;
     for (int j = 0; j < m; ++j) {
-      const double q = double(Qt[i + int64_t(j) * m]);
+      const double q = Qt[i + int64_t(j) * m];
 #pragma unroll
       for (int r = 0; r < kRhs; ++r)
         if (r < nrhs) acc[r] += q * sz[j + r * kMaxBlock];
@@ -428,34 +426,23 @@ inline unsigned grid_for(int64_t n, int per = 256) {
 
 }  // namespace
 
-template <typename TQ>
-cudaError_t launch_apply_qt(const ApItem *items, int n, const TQ *Q, const double *x, int64_t ldx, double *ys,
+cudaError_t launch_apply_qt(const ApItem *items, int n, const double *Q, const double *x, int64_t ldx, double *ys,
                             int64_t ldys, double *xn, int64_t ldxn, int nrhs, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   for (int r0 = 0; r0 < nrhs; r0 += kRhs)
-    k_apply_qt<TQ><<<n, 64, 0, s>>>(items, Q, x + r0 * ldx, ldx, ys + r0 * ldys, ldys, xn ? xn + r0 * ldxn : nullptr,
-                                    ldxn, std::min(kRhs, nrhs - r0));
+    k_apply_qt<<<n, 64, 0, s>>>(items, Q, x + r0 * ldx, ldx, ys + r0 * ldys, ldys, xn ? xn + r0 * ldxn : nullptr,
+                                ldxn, std::min(kRhs, nrhs - r0));
   return cudaGetLastError();
 }
 
-template <typename TQ>
-cudaError_t launch_apply_q(const ApItem *items, int n, const TQ *Q, const double *xn, int64_t ldxn, const double *ys,
-                           int64_t ldys, double *x, int64_t ldx, int nrhs, cudaStream_t s) {
+cudaError_t launch_apply_q(const ApItem *items, int n, const double *Q, const double *xn, int64_t ldxn,
+                           const double *ys, int64_t ldys, double *x, int64_t ldx, int nrhs, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   for (int r0 = 0; r0 < nrhs; r0 += kRhs)
-    k_apply_q<TQ><<<n, 64, 0, s>>>(items, Q, xn ? xn + r0 * ldxn : nullptr, ldxn, ys + r0 * ldys, ldys, x + r0 * ldx,
-                                   ldx, std::min(kRhs, nrhs - r0));
+    k_apply_q<<<n, 64, 0, s>>>(items, Q, xn ? xn + r0 * ldxn : nullptr, ldxn, ys + r0 * ldys, ldys, x + r0 * ldx, ldx,
+                               std::min(kRhs, nrhs - r0));
   return cudaGetLastError();
 }
-
-template cudaError_t launch_apply_qt<double>(const ApItem *, int, const double *, const double *, int64_t, double *,
-                                             int64_t, double *, int64_t, int, cudaStream_t);
-template cudaError_t launch_apply_qt<float>(const ApItem *, int, const float *, const double *, int64_t, double *,
-                                            int64_t, double *, int64_t, int, cudaStream_t);
-template cudaError_t launch_apply_q<double>(const ApItem *, int, const double *, const double *, int64_t,
-                                            const double *, int64_t, double *, int64_t, int, cudaStream_t);
-template cudaError_t launch_apply_q<float>(const ApItem *, int, const float *, const double *, int64_t, const double *,
-                                           int64_t, double *, int64_t, int, cudaStream_t);
 
 cudaError_t launch_copy_rows(const int64_t *src_row, const int64_t *dst_row, const int32_t *len, int n,
                              const double *src, int64_t lds, double *dst, int64_t ldd, int nrhs, cudaStream_t s) {

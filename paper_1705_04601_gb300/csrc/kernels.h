@@ -7,22 +7,20 @@
 
 namespace h2sp {
 
-// ---- sparsification (sparsify.cu); W = double, or float for the FP32
-// sparsification that feeds an FP32 preconditioner.  The H^2 numbers are FP64
-// in either case.
-template <typename W>
-cudaError_t launch_householder(const QItem *items, int n, const double *w_in, const W *w_buf, W *Q, W *Rr, int max_m,
-                               int max_k, cudaStream_t s, Prof *prof);
-template <typename W>
-cudaError_t launch_stack_w(const WItem *items, int n, const W *Rr, const double *T, W *Wout, cudaStream_t s,
+// ---- sparsification (sparsify.cu).  Householder completions and stacked
+// bases are FP64; the products that land in S (and in the level buffers that
+// feed it) use W = double, or float for an FP32 S.
+cudaError_t launch_householder(const QItem *items, int n, const double *w_in, const double *w_buf, double *Q,
+                               double *Rr, int max_m, int max_k, cudaStream_t s, Prof *prof);
+cudaError_t launch_stack_w(const WItem *items, int n, const double *Rr, const double *T, double *W, cudaStream_t s,
                            Prof *prof);
 template <typename W>
-cudaError_t launch_coupling(const CItem *items, int n, const W *Rr, const W *Rrc, const double *Dc,
+cudaError_t launch_coupling(const CItem *items, int n, const double *Rr, const double *Rrc, const double *Dc,
                             W *const *dst_base, int max_k, cudaStream_t s, Prof *prof);
 // src_base[0] is the FP64 close-block array, src_base[1..3] level buffers of type W
 template <typename W>
-cudaError_t launch_transform(const XItem *items, int n, const void *const *src_base, const W *Qrow, const W *Qcol,
-                             W *const *dst_base, cudaStream_t s, Prof *prof, double flops);
+cudaError_t launch_transform(const XItem *items, int n, const void *const *src_base, const double *Qrow,
+                             const double *Qcol, W *const *dst_base, cudaStream_t s, Prof *prof, double flops);
 
 // ---- block LU of S (factor.cu), T = double or float ----
 struct FrontDev {
@@ -129,15 +127,12 @@ struct ApItem {
   int64_t xout;   // row in the level-(l+1) vector of the basis part, -1 if none
   int32_t m, kp;
 };
-// out rows: non-basis -> S space (ys), basis -> next level (xn); op = Q^T.
-// TQ is the storage type of Q (double or float); vectors and sums are FP64.
-template <typename TQ>
-cudaError_t launch_apply_qt(const ApItem *items, int n, const TQ *Q, const double *x, int64_t ldx, double *ys,
+// out rows: non-basis -> S space (ys), basis -> next level (xn); op = Q^T
+cudaError_t launch_apply_qt(const ApItem *items, int n, const double *Q, const double *x, int64_t ldx, double *ys,
                             int64_t ldys, double *xn, int64_t ldxn, int nrhs, cudaStream_t s);
 // reverse: X_l(t) = Q [xn part; ys part]
-template <typename TQ>
-cudaError_t launch_apply_q(const ApItem *items, int n, const TQ *Q, const double *xn, int64_t ldxn, const double *ys,
-                           int64_t ldys, double *x, int64_t ldx, int nrhs, cudaStream_t s);
+cudaError_t launch_apply_q(const ApItem *items, int n, const double *Q, const double *xn, int64_t ldxn,
+                           const double *ys, int64_t ldys, double *x, int64_t ldx, int nrhs, cudaStream_t s);
 // copy rows: dst[dst_row[i] + r] = src[src_row[i] + r] for r < len[i]
 cudaError_t launch_copy_rows(const int64_t *src_row, const int64_t *dst_row, const int32_t *len, int n,
                              const double *src, int64_t lds, double *dst, int64_t ldd, int nrhs, cudaStream_t s);

@@ -343,12 +343,13 @@ def test_sparsify_analyzed_matches_sparsify(name):
 
 @pytest.mark.parametrize("name", ["log1k", "skew1k", "ragged", "inv3d"])
 def test_fp32_sparsification_matches_oracle(name):
-    """H2SP_SPARSIFY_FP32 computes Q and S in FP32 from the FP64 H^2 numbers.
-    Householder QR and the two-sided orthogonal transforms are backward stable,
-    so each Q and each block row of S stays within a small multiple of the
-    FP32 unit roundoff (6e-8) times the block sizes (<= 64) and levels of the
-    FP64 result; 1e-4 allows ~25 u per level for up to 6 levels of 64-row
-    blocks.  The pattern is integer work and must be identical."""
+    """H2SP_SPARSIFY_FP32: the Householder completions stay FP64, so every Q
+    meets the FP64 bar (1e-10); the sandwich products run in FP32 with Q
+    rounded to FP32, so each block row of S carries the rounding of two
+    64-term FP32 products per level (about 2 x 64 x 6e-8 = 8e-6 per level in
+    the worst case, a few e-7 typically) summed over at most 6 levels: 1e-4
+    of the row-block norm.  The pattern is integer work and must be
+    identical."""
     h, b, sp = case(name)
     hd = H.h2sp_sparsify(H.H2Input(h), flags=H.H2SP_SPARSIFY_FP32)
     assert H.h2sp_query(hd)["sparsify_prec"] == H.H2SP_FP32
@@ -364,24 +365,23 @@ def test_fp32_sparsification_matches_oracle(name):
         a, e = int(vbr.val_off[lo]), int(vbr.val_off[hi - 1] + ns[i] * ns[vbr.bcol_idx[hi - 1]])
         ref_row = max(np.linalg.norm(vbr.vals[a:e]), 1e-300)
         worst = max(worst, np.linalg.norm(S["vals"][a:e] - vbr.vals[a:e]) / ref_row)
-    qworst = 0.0
+    print("fp32 products (%s): S row-block rel %.2e" % (name, worst))
+    assert worst <= 1e-4
     for t in sp.Q:
-        qworst = max(qworst, np.linalg.norm(H.h2sp_export_Q(hd, t) - sp.Q[t]) / np.linalg.norm(sp.Q[t]))
+        assert np.linalg.norm(H.h2sp_export_Q(hd, t) - sp.Q[t]) <= TOL * np.linalg.norm(sp.Q[t]), t
         if not h.symmetric_bases:
-            qworst = max(qworst, np.linalg.norm(H.h2sp_export_Q(hd, t, col=True) - sp.Qc[t]) /
-                         np.linalg.norm(sp.Qc[t]))
-    print("fp32 sparsify (%s): S row-block rel %.2e, Q rel %.2e" % (name, worst, qworst))
-    assert worst <= 1e-4 and qworst <= 1e-4
+            Qcg = H.h2sp_export_Q(hd, t, col=True)
+            assert np.linalg.norm(Qcg - sp.Qc[t]) <= TOL * np.linalg.norm(sp.Qc[t]), t
     hd.close()
 
 
 @pytest.mark.parametrize("name,mode", [("log4k", "gmres"), ("skew1k", "gmres"), ("ragged", "gmres"),
                                        ("log4k", "ir")])
 def test_fp32_sparsify_and_factor_reach_1e10(name, mode):
-    """The all-FP32 preconditioner (FP32 U, S, V and FP32 factors) still
-    drives GMRES / refinement on the FP64 H^2 residual to 1e-10 (§5.5), and
-    the solution agrees with the dense FP64 solve to what that residual
-    implies."""
+    """The preconditioner built from an FP32 S and FP32 factors (U and V
+    FP64) still drives GMRES / refinement on the FP64 H^2 residual to 1e-10
+    (§5.5), and the solution agrees with the dense FP64 solve to what that
+    residual implies."""
     h, b, sp = case(name)
     hd = H.h2sp_sparsify(H.H2Input(h), flags=H.H2SP_SPARSIFY_FP32)
     H.h2sp_factor(hd, H.H2SP_FP32)
@@ -404,10 +404,11 @@ def test_fp32_sparsify_and_factor_reach_1e10(name, mode):
 
 
 def test_fp32_sparsify_products_stay_fp64_vectors():
-    """With FP32 U, S and V the applies still take and return FP64 vectors;
-    each differs from the FP64 oracle's by FP32 rounding of the operator
-    only (<= 1e-4 relative)."""
+    """With an FP32 S the applies still take and return FP64 vectors: U^T, V,
+    U, V^T and the H^2 product do not touch S and keep the FP64 bar; S x
+    differs from the oracle's by the FP32 rounding of S only (<= 1e-4)."""
     h, b, sp = case("skew1k")
+    n = h.n
     hd = H.h2sp_sparsify(H.H2Input(h), flags=H.H2SP_SPARSIFY_FP32)
     bt = dev(b)
     out = torch.empty_like(bt)
@@ -417,6 +418,6 @@ def test_fp32_sparsify_products_stay_fp64_vectors():
         H.h2sp_apply(hd, op, bt, out)
         torch.cuda.synchronize()
         rel = np.linalg.norm(host(out) - ref) / np.linalg.norm(ref)
-        # the H^2 product does not use the sparsification: still FP64-exact
-        assert rel <= (1e-12 if op == H.H2SP_OP_H2 else 1e-4), (op, rel)
+        bound = 1e-4 if op == H.H2SP_OP_S else 1e-12 * max(1.0, np.sqrt(n) / 8)
+        assert rel <= bound, (op, rel)
     hd.close()
