@@ -421,3 +421,29 @@ def test_fp32_sparsify_products_stay_fp64_vectors():
         bound = 1e-4 if op == H.H2SP_OP_S else 1e-12 * max(1.0, np.sqrt(n) / 8)
         assert rel <= bound, (op, rel)
     hd.close()
+
+
+def test_fp32_factor_backward_error():
+    """The FP32 block LU of S is a backward-stable factorization, also where
+    the panels pivot by tournament (supernodes of more than one block of
+    candidate rows, as in the top fronts here): y = S^{-1} c from the FP32
+    factors has a normwise backward error ||c - S y|| / (||S||_F ||y|| + ||c||)
+    of FP32 order (u = 6e-8 times a modest growth), required <= 1e-5; a
+    wrong pivot row, a stale update or a misplaced row gives O(1e-2) or more."""
+    n = 16384
+    h, _ = synth.make_workload("log2d_n65536", n=n)
+    hd = H.h2sp_sparsify(H.H2Input(h))
+    H.h2sp_factor(hd, H.H2SP_FP32)
+    c = np.random.default_rng(5).standard_normal((n, 4))
+    ct = dev(c)
+    yt = torch.empty_like(ct)
+    rt = torch.empty_like(ct)
+    H.h2sp_apply(hd, H.H2SP_OP_SINV, ct, yt)
+    H.h2sp_apply(hd, H.H2SP_OP_S, yt, rt)
+    torch.cuda.synchronize()
+    nS = np.linalg.norm(H.h2sp_export_S(hd)["vals"])
+    y, r = host(yt), c - host(rt)
+    eta = (np.linalg.norm(r, axis=0) / (nS * np.linalg.norm(y, axis=0) + np.linalg.norm(c, axis=0))).max()
+    print("fp32 factor backward error (n=%d): %.2e" % (n, eta))
+    assert eta <= 1e-5
+    hd.close()
