@@ -64,6 +64,7 @@ struct StructureDev {
   std::vector<LevelDev> lv;  // item arrays only
   std::vector<double> x_flops;
   int max_rank = 1;
+  int64_t max_pack_tiles = 0;  // largest sum over a level's fronts of ceil(f / 128)
   int64_t max_width = 0;
   int64_t *top_src = nullptr, *top_dst = nullptr;
   int32_t *top_len = nullptr;
@@ -176,6 +177,7 @@ struct h2sp_handle {
   }
   LuAsync la;  // look-ahead stream and events of the block LU (created on first use)
   uint8_t *tmaps = nullptr;  // TMA descriptors of the FP32 fronts (built on the first FP32 factorization)
+  float *pack = nullptr;     // packed GEMM operands of the blocked FP32 LU (3 buffers of the largest level)
   // flag-synchronised triangular sweeps
   int2 *chain_items = nullptr;
   std::vector<int> chain_fwd_off, chain_fwd_n, chain_bwd_off, chain_bwd_n;
@@ -742,8 +744,17 @@ std::shared_ptr<StructureDev> build_structure(const Plan &p) {
     std::vector<FrontDev> fd(p.fronts.size());
     for (size_t k = 0; k < p.fronts.size(); ++k) {
       const Front &F = p.fronts[k];
-      fd[k] = FrontDev{F.off, F.piv_off, F.idx_off, F.map_off, F.dinv_off, F.s, F.b, F.f, F.parent, F.ld};
+      fd[k] = FrontDev{F.off, F.piv_off, F.idx_off, F.map_off, F.dinv_off, F.s, F.b, F.f, F.parent, F.ld, 0};
       sd->max_s_all = std::max(sd->max_s_all, F.s);
+    }
+    // 128-row tiles of the packed operands of the blocked FP32 LU, per level
+    for (size_t i = 0; i + 1 < p.front_level_ptr.size(); ++i) {
+      int64_t acc = 0;
+      for (int k = p.front_level_ptr[i]; k < p.front_level_ptr[i + 1]; ++k) {
+        fd[k].pack_off = int32_t(acc);
+        acc += (p.fronts[k].f + 127) / 128;
+      }
+      sd->max_pack_tiles = std::max(sd->max_pack_tiles, acc);
     }
     sd->fr = sd->upload(fd);
     sd->fidx = sd->upload(p.front_idx);
@@ -1076,7 +1087,7 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
       h->perm = h->alloc<int32_t>(size_t(std::max<int64_t>(p.piv_elems, 1)));
       size_t maxn = 1;
       for (const FrontLevel &L : h->flev) maxn = std::max<size_t>(maxn, size_t(L.hi - L.lo));
-      h->swaps = h->alloc<int32_t>(2 * maxn * (1 + 2 * kMaxSwapRows));  // two steps in flight
+      h->swaps = h->alloc<int32_t>(8 * maxn * (1 + 2 * kMaxSwapRows));  // two outer blocks of panels in flight
       h->err = h->alloc<int>(1);
       h->dinv = h->alloc<double>(size_t(std::max<int64_t>(p.dinv_elems, 1)));
     }
@@ -1117,6 +1128,8 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
         ck(cudaStreamSynchronize(s));  // the allocation is usable by the synchronous copy
         if (make_front_tmaps(p.fronts.data(), int(p.fronts.size()), F, m) == cudaSuccess) h->tmaps = m;
         cudaGetLastError();
+        if (h->tmaps != nullptr && h->sdev->max_pack_tiles > 0)
+          h->pack = h->alloc<float>(size_t(3 * h->sdev->max_pack_tiles * kPackTileFloats));
       }
       if (h->sp_prec == H2SP_FP32)
         ck(launch_assemble<float, float>(h->asm_items, na, static_cast<const float *>(h->S), F, s, &h->prof, abytes));
@@ -1126,7 +1139,7 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
       for (const FrontLevel &L : h->flev) {
         ck(launch_lu_level<float>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv,
                                   h->swaps, h->err, s, la, &h->prof,
-                                  h->tmaps ? h->tmaps + size_t(L.lo) * kTmapBytes : nullptr));
+                                  h->tmaps ? h->tmaps + size_t(L.lo) * kTmapBytes : nullptr, h->pack));
         ck(launch_extend_add_impl<float>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s, &h->prof, L.b2));
       }
       ck(launch_make_perm<float>(h->fr, int(p.fronts.size()), h->max_s_all, h->piv, h->perm, s, &h->prof));

@@ -688,9 +688,12 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const FrontDev *__restrict__ 
   __syncthreads();
   constexpr int kPer = (kMaxSwapRows + 31) / 32;
   // part 0: every column but the panel's; part 1: the w columns after the
-  // panel (what the next panel needs); part 2: the others
+  // panel (what the next panel needs); part 2: the others; part 3 (an inner
+  // step of the blocked LU, w = the outer block width): the columns of the
+  // panel's outer block [J, min(J + w, s)), J = w floor(j0 / w)
   const int t0 = j0 + jb;
-  const int c_begin = part == 1 ? t0 : 0, c_end = part == 1 ? min(F.f, t0 + w) : F.f;
+  int c_begin = part == 1 ? t0 : 0, c_end = part == 1 ? min(F.f, t0 + w) : F.f;
+  if (part == 3) c_begin = (j0 / w) * w, c_end = min(c_begin + w, F.s);
   for (int c = c_begin + blockIdx.x * 8 + wid; c < c_end; c += gridDim.x * 8) {
     if (c >= j0 && c < t0) continue;
     if (part == 2 && c >= t0 && c < t0 + w) continue;
@@ -720,6 +723,121 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const FrontDev *__restrict__ 
       }
       if (lane < jb) Ac[j0 + lane] = x0;
       if (NB > 32 && lane + 32 < jb) Ac[j0 + 32 + lane] = x1;
+    }
+  }
+}
+
+// Block end of the blocked FP32 LU for the outer block [J, J + jbo), jbo =
+// min(KB, s - J): the block's panels interchanged rows only inside the block,
+// so every other column now takes their interchanges (panel by panel, in
+// order), and the columns after the block also take U12 = L11^-1 A12 on rows
+// [J, J + jbo), L11 the block's unit lower triangle.  A warp takes kBlkCols
+// adjacent columns, lane l holding rows J + l + 32 i (i < KB / 32) of each in
+// registers; L11 passes through shared memory one 64-column block at a time
+// (zero above the diagonal and below row jbo, so the updates need no row
+// tests), each value read once for all the warp's columns.
+// trsm = 1: columns [t0 + c_lo, t0 + c_hi) clipped to f (t0 = J + jbo);
+// trsm = 0: interchanges only, columns [c_lo, min(c_hi, J)).
+constexpr int kBlkCols = 8;                    // columns per warp
+constexpr int kBlkCtaCols = 8 * kBlkCols;      // columns per CTA (eight warps)
+template <int KB>
+__global__ void __launch_bounds__(256) k_blk_swap_trsm(const FrontDev *__restrict__ fr, int J, float *__restrict__ fronts,
+                                                      const int32_t *__restrict__ swaps, int64_t swap_stride, int c_lo,
+                                                      int c_hi, int trsm) {
+  static_assert(KB % 64 == 0 && KB <= 256, "outer block");
+  constexpr int NR = KB / 32;
+  constexpr int CW = kBlkCols;
+  const int fi = blockIdx.y;
+  const FrontDev F = fr[fi];
+  if (J >= F.s) return;
+  const int jbo = min(KB, F.s - J);
+  const int t0 = J + jbo;
+  float *A = fronts + F.off;
+  const int64_t ld = F.ld;
+  int lo, hi;
+  if (trsm) {
+    if (c_lo >= F.f - t0) return;
+    lo = t0 + c_lo;
+    hi = c_hi >= F.f - t0 ? F.f : t0 + c_hi;
+  } else {
+    lo = c_lo;
+    hi = min(c_hi, J);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lo + int(blockIdx.x) * kBlkCtaCols >= hi) return;  // uniform over the CTA
+  const int cw = lo + blockIdx.x * kBlkCtaCols + warp * CW;  // this warp's first column
+  const int npan = (jbo + 63) / 64;
+  constexpr int kPer = (kMaxSwapRows + 31) / 32;
+  for (int i = 0; i < npan; ++i) {
+    const int32_t *sw = swaps + int64_t(((J / 64) + i) & 7) * swap_stride + int64_t(fi) * (1 + 2 * kMaxSwapRows);
+    const int n = sw[0];
+    if (n <= 0) continue;
+    int srow[kPer], ssrc[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int e = lane + 32 * q;
+      srow[q] = e < n ? sw[1 + e] : 0;
+      ssrc[q] = e < n ? sw[1 + kMaxSwapRows + e] : 0;
+    }
+    for (int j = 0; j < CW; ++j) {
+      if (cw + j >= hi) break;
+      float *col = A + int64_t(cw + j) * ld;
+      float v[kPer];
+#pragma unroll
+      for (int q = 0; q < kPer; ++q)
+        if (lane + 32 * q < n) v[q] = col[ssrc[q]];
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < kPer; ++q)
+        if (lane + 32 * q < n) col[srow[q]] = v[q];
+      __syncwarp();
+    }
+  }
+  if (!trsm) return;
+  extern __shared__ float Ls[];  // [64][KB]: column kl of the current 64-column block of L11, rows 0..KB-1
+  float x[CW][NR];
+#pragma unroll
+  for (int j = 0; j < CW; ++j)
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+      const int row = 32 * i + lane;
+      x[j][i] = (cw + j < hi && row < jbo) ? A[(J + row) + int64_t(cw + j) * ld] : 0.f;
+    }
+#pragma unroll
+  for (int b = 0; b < KB / 64; ++b) {
+    if (b >= npan) break;  // uniform
+    const int kb0 = 64 * b, kbn = min(64, jbo - kb0);
+    __syncthreads();  // the previous block of L11 has been used
+    for (int e = threadIdx.x; e < 64 * KB; e += blockDim.x) {
+      const int kl = e / KB, row = e % KB;
+      Ls[e] = (kl < kbn && row > kb0 + kl && row < jbo) ? A[(J + row) + int64_t(J + kb0 + kl) * ld] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      for (int kl2 = 0; kl2 < 32; ++kl2) {
+        const int kl = 32 * h + kl2;
+        if (kl >= kbn) break;  // uniform
+        float xk[CW];
+#pragma unroll
+        for (int j = 0; j < CW; ++j) xk[j] = __shfl_sync(0xffffffffu, x[j][2 * b + h], kl2);
+        const float *Lk = Ls + kl * KB + lane;
+#pragma unroll
+        for (int i = 2 * b + h; i < NR; ++i) {
+          const float l = Lk[32 * i];
+#pragma unroll
+          for (int j = 0; j < CW; ++j) x[j][i] -= l * xk[j];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < CW; ++j) {
+    if (cw + j >= hi) break;
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+      const int row = 32 * i + lane;
+      if (row < jbo) A[(J + row) + int64_t(cw + j) * ld] = x[j][i];
     }
   }
 }
@@ -1506,6 +1624,21 @@ cudaError_t launch_assemble(const AItem *items, int64_t n, const TS *S, T *front
   return cudaGetLastError();
 }
 
+// Outer block width of the blocked FP32 LU (four 64-column panels).
+constexpr int kLuOuter = 256;
+
+// The FP32 fronts are factored in outer blocks of kLuOuter columns (with
+// tensor cores and TMA descriptors); H2SP_LU=step keeps one trailing update
+// per 64-column panel.
+inline bool blocked_lu_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = std::getenv("H2SP_LU");
+    v = (e && std::strcmp(e, "step") == 0) ? 0 : 1;
+  }
+  return v == 1;
+}
+
 // The FP32 trailing update runs on the tensor cores (three-term TF32 split);
 // H2SP_GEMM=simt selects the CUDA-core kernel instead.
 inline bool use_tensor_core_gemm() {
@@ -1527,7 +1660,7 @@ inline bool use_tensor_core_gemm() {
 template <typename T>
 cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
                             int32_t *piv, int32_t *swaps, int *err, cudaStream_t s, const LuAsync *la, Prof *prof,
-                            const uint8_t *maps) {
+                            const uint8_t *maps, float *pack) {
   constexpr int NB = LuCfg<T>::NB;
   using G = GemmCfg<T>;
   auto gemm = k_gemm_update<T, G::BM, G::BN, G::TM, G::TN, NB>;
@@ -1547,8 +1680,9 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
   // next panel writes the other half while this step's remaining columns are
   // still being interchanged on the low-priority stream
   const size_t swap_stride = size_t(nfront) * (1 + 2 * kMaxSwapRows);
+  int slot_mask = 1;  // swap-list slots in use: 2 (one panel step ahead) or 8 (two outer blocks of 4 panels)
   auto panel = [&](int j0, cudaStream_t st, int *cl) -> cudaError_t {
-    int32_t *swp = swaps + size_t((j0 / NB) & 1) * swap_stride;
+    int32_t *swp = swaps + size_t((j0 / NB) & slot_mask) * swap_stride;
     double fpanel = 0.0;
     if (prof->timing)
       for (int k = 0; k < nfront; ++k) {
@@ -1646,7 +1780,138 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
   const bool ahead = la != nullptr && la->side != nullptr && la->rest != nullptr && la->next != nullptr &&
                      la->panel != nullptr && la->done != nullptr;
   int panel_ctas = 0;
-  cudaError_t e = panel(0, s, &panel_ctas);
+  cudaError_t e = cudaSuccess;
+  if constexpr (std::is_same<T, float>::value && NB == 64) {
+    if (tc && maps != nullptr && blocked_lu_enabled()) {
+      // ---- blocked LU: outer blocks of KB columns = KB / NB panels ----
+      constexpr int KB = kLuOuter;
+      slot_mask = 7;
+      // packed operands: two L21 buffers (by block parity) and one U12 buffer,
+      // each kPackTileFloats per 128-row tile of the level's fronts
+      int64_t pack_tiles = 0;
+      for (int k = 0; k < nfront; ++k) pack_tiles += cdiv(host_fr[k].f, kTcTile);
+      const int64_t pack_stride = pack_tiles * kPackTileFloats;
+      cudaStream_t ms = ahead ? la->side : s;  // panels, inner steps, the next block's columns
+      cudaStream_t rs = ahead ? la->rest : s;  // the rest of each block-end update
+      cudaEvent_t done_ev[2] = {ahead ? la->panel : nullptr, ahead ? la->done : nullptr};
+      if (ahead) {
+        if ((e = cudaEventRecord(la->next, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(ms, la->next, 0)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(rs, la->next, 0)) != cudaSuccess) return e;
+      }
+      static bool blk_attr = false;
+      if (!blk_attr) {
+        cudaFuncSetAttribute(k_blk_swap_trsm<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(sizeof(float) * 64 * KB));
+        blk_attr = true;
+      }
+      auto fl_trsm = [&](int j0, int lo_col, int hi_col) {  // U12 flops of a panel step over a column range
+        double f = 0.0;
+        if (prof->timing)
+          for (int k = 0; k < nfront; ++k) {
+            const Front &F = host_fr[k];
+            if (j0 >= F.s) continue;
+            const double jb = std::min(NB, F.s - j0);
+            f += jb * jb * std::max(0, std::min(hi_col, F.s) - std::max(lo_col, j0 + int(jb)));
+          }
+        return f;
+      };
+      // block end, over the columns [t0 + lo, t0 + hi) of the trailing block
+      // (and, with left, the interchanges of the columns before the block)
+      float *apack[2] = {pack, pack ? pack + pack_stride : nullptr};
+      float *bpack = pack ? pack + 2 * pack_stride : nullptr;
+      auto block_end = [&](int J, int lo, int hi, bool left, int budget, cudaStream_t st) -> cudaError_t {
+        double ft = 0.0, fg = 0.0;
+        int wcols = 0;
+        for (int k = 0; k < nfront; ++k) {
+          const Front &F = host_fr[k];
+          if (J >= F.s) continue;
+          const int jbo = std::min(KB, F.s - J), t0 = J + jbo, nrest = F.f - t0;
+          const int cols = std::max(0, std::min(nrest, hi) - lo);
+          wcols = std::max(wcols, cols);
+          ft += 0.5 * double(jbo) * jbo * cols;
+          // algorithmic bytes of the rank-jbo update: C in and out, L21 and U12 read
+          fg += double(sizeof(float)) * (2.0 * nrest * cols + double(jbo) * (nrest + cols));
+        }
+        size_t e0 = prof->begin(st);
+        if (left && J > 0)
+          k_blk_swap_trsm<KB><<<dim3(cdiv(J, kBlkCtaCols), nfront), 256, 0, st>>>(fr, J, fronts, swaps,
+                                                                                  int64_t(swap_stride), 0, J, 0);
+        if (wcols > 0)
+          k_blk_swap_trsm<KB><<<dim3(cdiv(wcols, kBlkCtaCols), nfront), 256, sizeof(float) * 64 * KB, st>>>(
+              fr, J, fronts, swaps, int64_t(swap_stride), lo, hi, 1);
+        prof->end(P_TRSM, (left && J > 0 ? 1 : 0) + (wcols > 0 ? 1 : 0), e0, ft, st);
+        if (wcols <= 0) return cudaGetLastError();
+        const int tlo = lo / kTcTile, thi = hi >= (INT_MAX - kTcTile) ? INT_MAX : hi / kTcTile;
+        e0 = prof->begin(st);
+        cudaError_t ge;
+        if (bpack != nullptr) {
+          ge = launch_pack_b(fr, J, KB, nfront, max_f, fronts, bpack, tlo, thi, st);
+          if (ge == cudaSuccess)
+            ge = launch_gemm_tc_ws(fr, J, KB, nfront, max_f, fronts, err, st, tlo, thi, budget, maps,
+                                   apack[(J / KB) & 1], bpack);
+        } else {
+          ge = launch_gemm_tc_outer(fr, J, KB, nfront, max_f, fronts, err, st, tlo, thi, budget, maps);
+        }
+        prof->end(P_GEMM, 1, e0, fg, st);
+        return ge != cudaSuccess ? ge : cudaGetLastError();
+      };
+      const int nblk = cdiv(max_s, KB);
+      if ((e = panel(0, ms, &panel_ctas)) != cudaSuccess) return e;
+      for (int b = 0; b < nblk; ++b) {
+        const int J = b * KB;
+        for (int i = 0; i < KB / NB; ++i) {
+          const int jp = J + i * NB;
+          if (jp >= max_s) break;
+          if (i > 0 && (e = panel(jp, ms, &panel_ctas)) != cudaSuccess) return e;
+          {
+            const int32_t *sw = swaps + size_t((jp / NB) & slot_mask) * swap_stride;
+            const size_t e0 = prof->begin(ms);
+            k_swap_trsm<T, NB><<<dim3(cdiv(KB, 8), nfront), 256, 0, ms>>>(fr, jp, fronts, sw, 3, KB);
+            prof->end(P_TRSM, 1, e0, fl_trsm(jp, J, J + KB), ms);
+          }
+          if (i + 1 < KB / NB) {
+            double fgemm = 0.0;
+            if (prof->timing)
+              for (int k = 0; k < nfront; ++k) {
+                const Front &F = host_fr[k];
+                if (jp >= F.s) continue;
+                const int jb = std::min(NB, F.s - jp), nrest = F.f - jp - jb;
+                const int cols = std::max(0, std::min(J + KB, F.s) - (jp + jb));
+                fgemm += double(sizeof(float)) * (2.0 * nrest * cols + double(jb) * (nrest + cols));
+              }
+            const size_t e0 = prof->begin(ms);
+            if ((e = launch_gemm_tc_inner(fr, jp, KB, nfront, max_f, fronts, err, ms, nsm)) != cudaSuccess) return e;
+            prof->end(P_GEMM, 1, e0, fgemm, ms);
+          }
+        }
+        const bool more = J + KB < max_s;
+        if (pack != nullptr && (e = launch_pack_a(fr, J, KB, nfront, max_f, fronts, apack[b & 1], ms)) != cudaSuccess)
+          return e;
+        if (ahead) {
+          // the rest of the block end goes to the low-priority stream as soon
+          // as the block's panels are done; the next block's columns stay here
+          if ((e = cudaEventRecord(la->next, ms)) != cudaSuccess) return e;
+          if ((e = cudaStreamWaitEvent(rs, la->next, 0)) != cudaSuccess) return e;
+          if ((e = block_end(J, KB, INT_MAX, true, std::max(nsm - panel_ctas, nsm / 2), rs)) != cudaSuccess) return e;
+          if ((e = cudaEventRecord(done_ev[b & 1], rs)) != cudaSuccess) return e;
+          // the previous block's rest covered these columns
+          if (b > 0 && (e = cudaStreamWaitEvent(ms, done_ev[(b - 1) & 1], 0)) != cudaSuccess) return e;
+          if ((e = block_end(J, 0, KB, false, nsm, ms)) != cudaSuccess) return e;
+        } else {
+          if ((e = block_end(J, 0, INT_MAX, true, nsm, s)) != cudaSuccess) return e;
+        }
+        if (more && (e = panel(J + KB, ms, &panel_ctas)) != cudaSuccess) return e;
+      }
+      if (ahead) {
+        if ((e = cudaStreamWaitEvent(ms, done_ev[(nblk - 1) & 1], 0)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(la->next, ms)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, la->next, 0)) != cudaSuccess) return e;
+      }
+      return cudaGetLastError();
+    }
+  }
+  e = panel(0, s, &panel_ctas);
   if (e != cudaSuccess) return e;
   for (int j0 = 0; j0 < max_s; j0 += NB) {
     double ftrsm = 0.0;
@@ -1803,7 +2068,7 @@ template cudaError_t launch_assemble<float, double>(const AItem *, int64_t, cons
                                                     Prof *, double);
 template cudaError_t launch_lu_level<double>(const FrontDev *, const Front *, int, int, int, double *, int32_t *, int32_t *,
                                            int *, cudaStream_t, const LuAsync *, Prof *,
-                                           const uint8_t *);
+                                           const uint8_t *, float *);
 template cudaError_t launch_make_perm<double>(const FrontDev *, int, int, const int32_t *, int32_t *, cudaStream_t, Prof *);
 template cudaError_t launch_extend_add_impl<double>(const FrontDev *, int, int, int, const int32_t *, double *, cudaStream_t,
                                                   Prof *, double);
@@ -1822,7 +2087,7 @@ template cudaError_t launch_assemble<float, float>(const AItem *, int64_t, const
                                                    double);
 template cudaError_t launch_lu_level<float>(const FrontDev *, const Front *, int, int, int, float *, int32_t *, int32_t *,
                                            int *, cudaStream_t, const LuAsync *, Prof *,
-                                           const uint8_t *);
+                                           const uint8_t *, float *);
 template cudaError_t launch_make_perm<float>(const FrontDev *, int, int, const int32_t *, int32_t *, cudaStream_t, Prof *);
 template cudaError_t launch_extend_add_impl<float>(const FrontDev *, int, int, int, const int32_t *, float *, cudaStream_t,
                                                   Prof *, double);

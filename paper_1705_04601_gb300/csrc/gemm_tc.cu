@@ -98,19 +98,24 @@ __device__ __forceinline__ void sync_for_tensor_cores() {
 // tiles.  The A tile (hi / lo) stays in shared memory; B tiles and the two
 // TMEM accumulators alternate, so staging tile i + 1 and the epilogue of tile
 // i overlap the asynchronous MMAs.
+// With kb > 0 (an inner step of the blocked LU) only the columns left in the
+// step's kb-wide outer block, [t0, min(J + kb, s)) with J = kb floor(j0 / kb),
+// are updated; the columns after the block wait for the block's rank-kb update.
 __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__restrict__ fr, int j0,
                                                           float *__restrict__ fronts, int *__restrict__ err,
-                                                          int splits, int tile_lo, int tile_hi, int partial_only) {
+                                                          int splits, int tile_lo, int tile_hi, int partial_only,
+                                                          int kb) {
   const FrontDev F = fr[blockIdx.z];
   if (j0 >= F.s) return;
   const int jb = min(kTcK, F.s - j0);
   if (partial_only && jb == kTcK) return;  // full panels are done by k_gemm_tc_tma
   const int t0 = j0 + jb;
   const int nrest = F.f - t0;
+  const int ncols = kb > 0 ? min(nrest, min((j0 / kb) * kb + kb, F.s) - t0) : nrest;
   const int rb = blockIdx.y * kTcM;
-  if (rb >= nrest) return;
+  if (rb >= nrest || ncols <= 0) return;
   // this launch covers column tiles [tile_lo, tile_hi) of the trailing block
-  const int ntiles = min((nrest + kTcN - 1) / kTcN, tile_hi) - tile_lo;
+  const int ntiles = min((ncols + kTcN - 1) / kTcN, tile_hi) - tile_lo;
   if (ntiles <= 0) return;
   const int per = (ntiles + splits - 1) / splits;
   const int c_lo = tile_lo + blockIdx.x * per, c_hi = min(tile_lo + ntiles, c_lo + per);
@@ -160,7 +165,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__res
       const int ln = e & 31, wv = e >> 5;
       const int k = (ln & 7) + 8 * (wv & 7), n = (ln >> 3) + 4 * (wv >> 3);
       const int c = cb + n;
-      v[it] = (k < jb && c < nrest) ? A[(j0 + k) + int64_t(t0 + c) * ld] : 0.f;
+      v[it] = (k < jb && c < ncols) ? A[(j0 + k) + int64_t(t0 + c) * ld] : 0.f;
     }
     float *bh = reinterpret_cast<float *>(sBh[buf]), *bl = reinterpret_cast<float *>(sBl[buf]);
 #pragma unroll
@@ -223,7 +228,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__res
     const int row = rb + q * 32 + lane;
     const int cb = ct * kTcN + half * 64;
     float *Crow = A + (t0 + row) + int64_t(t0 + cb) * ld;
-    const int ncol = row < nrest ? min(64, nrest - cb) : 0;
+    const int ncol = row < nrest ? min(64, ncols - cb) : 0;
     float cv[64];
 #pragma unroll
     for (int j = 0; j < 64; ++j) cv[j] = j < ncol ? Crow[int64_t(j) * ld] : 0.f;
@@ -445,6 +450,531 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc_tma(const FrontDev *_
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(kTcN)));
 }
 
+// Block-end update of the blocked LU: C[t0:f, t0:f] -= L21 U12 with K = jb
+// = min(kb, s - j0) <= 256, t0 = j0 + jb.  Per 128 x 128 output tile the C
+// tile comes in by TMA, K runs in chunks of 64 (A and B chunks staged as
+// hi / lo TF32 pairs, 24 MMAs into the tensor-memory accumulator per chunk),
+// and the tile goes back by TMA: C crosses HBM once per kb columns of L
+// instead of once per 64.  A TMA box must start on a 16-byte boundary, so a
+// front whose trailing block starts at a row t0 that is not a multiple of 4
+// (its last block ends inside the kb-wide block) moves C with plain loads and
+// stores instead.  Shared memory as in k_gemm_tc_tma (192 KB).
+__global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc_outer(const FrontDev *__restrict__ fr, int j0, int kb,
+                                                                float *__restrict__ fronts, int *__restrict__ err,
+                                                                int splits, int tile_lo, int tile_hi,
+                                                                const uint8_t *__restrict__ maps) {
+  const FrontDev F = fr[blockIdx.z];
+  if (j0 >= F.s) return;
+  const int jb = min(kb, F.s - j0);
+  const int t0 = j0 + jb;
+  const int nrest = F.f - t0;
+  const int rb = blockIdx.y * kTcM;
+  if (rb >= nrest) return;
+  const int ntiles = min((nrest + kTcN - 1) / kTcN, tile_hi) - tile_lo;
+  if (ntiles <= 0) return;
+  const int per = (ntiles + splits - 1) / splits;
+  const int c_lo = tile_lo + blockIdx.x * per, c_hi = min(tile_lo + ntiles, c_lo + per);
+  if (c_lo >= c_hi) return;
+  const void *tmap = maps + size_t(blockIdx.z) * kTmapBytes;
+  float *A = fronts + F.off;
+  const int64_t ld = F.ld;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  float *sAh = reinterpret_cast<float *>(smraw), *sAl = sAh + kTileFloats;
+  float *sBh = sAl + kTileFloats, *sBl = sBh + kTileFloats;
+  float *sC = sBl + kTileFloats;  // 128 x 128, column-major (TMA box order)
+  __shared__ __align__(8) uint64_t bar_mma, bar_c;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int kIters = kTcM * kTcK / kTcThreads;
+  const int nchunks = (jb + kTcK - 1) / kTcK;
+  // chunk q of A (rows rb.., K columns j0 + 64 q ..) and of B (its U12 rows)
+  auto stage = [&](int ct, int q) {
+    const int k0 = q * kTcK, kq = min(kTcK, jb - k0);
+    const int cb = ct * kTcN;
+    float va[kIters], vb[kIters];
+#pragma unroll
+    for (int it = 0; it < kIters; ++it) {
+      const int e = tid + it * kTcThreads;
+      const int m = (e >> 9) * 8 + ((e & 31) >> 2), k = ((e >> 5) & 15) * 4 + (e & 3);
+      const int r = rb + m;
+      va[it] = (k < kq && r < nrest) ? A[(t0 + r) + int64_t(j0 + k0 + k) * ld] : 0.f;
+      const int ln = e & 31, wv = e >> 5;
+      const int kk = (ln & 7) + 8 * (wv & 7), n = (ln >> 3) + 4 * (wv >> 3);
+      const int c = cb + n;
+      vb[it] = (kk < kq && c < nrest) ? A[(j0 + k0 + kk) + int64_t(t0 + c) * ld] : 0.f;
+    }
+#pragma unroll
+    for (int it = 0; it < kIters; ++it) {
+      const int e = tid + it * kTcThreads;
+      float hi, lo;
+      split_tf32(va[it], hi, lo);
+      sAh[e] = hi;
+      sAl[e] = lo;
+      const int ln = e & 31, wv = e >> 5;
+      const int kk = (ln & 7) + 8 * (wv & 7), n = (ln >> 3) + 4 * (wv >> 3);
+      const int w = (n >> 3) * (kSbo / 4) + (kk >> 2) * (kLbo / 4) + (n & 7) * 4 + (kk & 3);
+      split_tf32(vb[it], hi, lo);
+      sBh[w] = hi;
+      sBl[w] = lo;
+    }
+  };
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(uint32_t(kTcN)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_mma)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_c)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  uint32_t ph_mma = 0u, ph_c = 0u;
+  bool ok = true, mma_pending = false, c_pending = false;
+  const int q4 = warp & 3, half = warp >> 2;
+  const bool use_tma = (t0 & 3) == 0;  // uniform over the CTA
+  for (int ct = c_lo; ct < c_hi && ok; ++ct) {
+    const int x = t0 + rb, y = t0 + ct * kTcN;
+    if (use_tma) {
+      if (tid == 0) {
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar_c)),
+                     "r"(uint32_t(kTcM * kTcN * 4))
+                     : "memory");
+        tma_load_2d(smem_u32(sC), tmap, x, y, smem_u32(&bar_c));
+      }
+      c_pending = true;
+    }
+    for (int q = 0; q < nchunks; ++q) {
+      stage(ct, q);  // the previous chunk's MMAs have completed
+      sync_for_tensor_cores();
+      if (tid == 0) {
+        const int ksteps = (min(kTcK, jb - q * kTcK) + 7) / 8;
+        const uint32_t ah0 = smem_u32(sAh), al0 = smem_u32(sAl), bh0 = smem_u32(sBh), bl0 = smem_u32(sBl);
+        for (int kk = 0; kk < ksteps; ++kk) {
+          const uint32_t koff = uint32_t(kk) * 2 * kLbo;
+          const uint64_t ah = smem_desc(ah0 + koff), al = smem_desc(al0 + koff);
+          const uint64_t bh = smem_desc(bh0 + koff), bl = smem_desc(bl0 + koff);
+          mma_tf32(tmem, ah, bh, (q > 0 || kk > 0) ? 1u : 0u);
+          mma_tf32(tmem, ah, bl, 1u);
+          mma_tf32(tmem, al, bh, 1u);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&bar_mma)));
+      }
+      mma_pending = true;
+      const bool w1 = wait_phase(smem_u32(&bar_mma), ph_mma);
+      ok = __syncthreads_and(w1 ? 1 : 0) != 0;
+      if (!ok) {
+        mma_pending = !w1;
+        break;
+      }
+      ph_mma ^= 1u;
+      mma_pending = false;
+    }
+    if (!ok) break;
+    if (!use_tma) {
+      // plain epilogue: this thread's row, 64 columns of its half
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int row = rb + q4 * 32 + lane;
+      const int cb = ct * kTcN + half * 64;
+      float *Crow = A + (t0 + row) + int64_t(t0 + cb) * ld;
+      const int ncol = row < nrest ? min(64, nrest - cb) : 0;
+#pragma unroll
+      for (int c0 = 0; c0 < 64; c0 += 32) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(half * 64 + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+              "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+              "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (c0 + j < ncol) Crow[int64_t(c0 + j) * ld] -= __uint_as_float(v[j]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();  // TMEM is read before the next tile's MMAs
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      continue;
+    }
+    const bool w2 = wait_phase(smem_u32(&bar_c), ph_c);
+    ok = __syncthreads_and(w2 ? 1 : 0) != 0;
+    if (!ok) {
+      c_pending = !w2;
+      break;
+    }
+    ph_c ^= 1u;
+    c_pending = false;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int row = q4 * 32 + lane;
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(half * 64 + c0);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+          "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      float *col = sC + (half * 64 + c0) * kTcM + row;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) col[j * kTcM] -= __uint_as_float(v[j]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      tma_store_2d(tmap, x, y, smem_u32(sC));
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(err, 4);
+    if (mma_pending) wait_phase(smem_u32(&bar_mma), ph_mma);
+    if (c_pending) wait_phase(smem_u32(&bar_c), ph_c);
+  }
+  if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(kTcN)));
+}
+
+// ---- packed operands and the warp-specialised block-end update ----
+constexpr int kPkK = 32;                          // K values per packed chunk
+constexpr int kPkTile = kTcM * kPkK;              // floats per hi (or lo) array: 4096 = 16 KB
+constexpr uint32_t kPkSbo = (kPkK / 4) * 128;     // 8-row groups of a packed array (1024 bytes)
+static_assert(kPackTileFloats == int64_t(kPackChunks) * 2 * kPkTile, "packed tile size");
+
+__device__ __forceinline__ uint64_t smem_desc_pk(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr >> 4) & 0x3FFFu);
+  d |= uint64_t((kLbo >> 4) & 0x3FFFu) << 16;
+  d |= uint64_t((kPkSbo >> 4) & 0x3FFFu) << 32;
+  d |= uint64_t(1) << 46;
+  return d;
+}
+
+// Word w of a packed 128 x 32 array holds element (m, k) (m = row of A or
+// column of B, k = K index): 8-row x 4-K core matrices of 128 bytes, K-adjacent
+// cores 128 bytes apart, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ void pk_coords(int w, int &m, int &k) {
+  m = ((w >> 8) << 3) | ((w >> 2) & 7);
+  k = (((w >> 5) & 7) << 2) | (w & 3);
+}
+
+// L21 of the outer block [j0, j0 + jb): rows [t0, f), t0 = j0 + jb, one CTA
+// per 128-row tile; zero beyond the front and beyond jb.
+__global__ void __launch_bounds__(256) k_pack_a(const FrontDev *__restrict__ fr, int j0, int kb,
+                                                const float *__restrict__ fronts, float *__restrict__ pack) {
+  const FrontDev F = fr[blockIdx.y];
+  if (j0 >= F.s) return;
+  const int jb = min(kb, F.s - j0), t0 = j0 + jb, nrest = F.f - t0;
+  const int rt = blockIdx.x;
+  if (rt * kTcM >= nrest) return;
+  const float *A = fronts + F.off;
+  const int64_t ld = F.ld;
+  float *dst = pack + (int64_t(F.pack_off) + rt) * kPackTileFloats;
+  const int nq = (jb + kPkK - 1) / kPkK;
+  for (int q = 0; q < nq; ++q)
+    for (int w = threadIdx.x; w < kPkTile; w += blockDim.x) {
+      int m, k;
+      pk_coords(w, m, k);
+      const int r = rt * kTcM + m, kk = q * kPkK + k;
+      const float v = (r < nrest && kk < jb) ? A[(t0 + r) + int64_t(j0 + kk) * ld] : 0.f;
+      float hi, lo;
+      split_tf32(v, hi, lo);
+      dst[int64_t(2 * q) * kPkTile + w] = hi;
+      dst[int64_t(2 * q + 1) * kPkTile + w] = lo;
+    }
+}
+
+// U12 (rows [j0, j0 + jb)) of the trailing-block column tiles [ct_lo, ct_hi).
+__global__ void __launch_bounds__(256) k_pack_b(const FrontDev *__restrict__ fr, int j0, int kb,
+                                                const float *__restrict__ fronts, float *__restrict__ pack, int ct_lo,
+                                                int ct_hi) {
+  const FrontDev F = fr[blockIdx.y];
+  if (j0 >= F.s) return;
+  const int jb = min(kb, F.s - j0), t0 = j0 + jb, nrest = F.f - t0;
+  const int ct = ct_lo + blockIdx.x;
+  if (ct >= ct_hi || ct * kTcN >= nrest) return;
+  const float *A = fronts + F.off;
+  const int64_t ld = F.ld;
+  float *dst = pack + (int64_t(F.pack_off) + ct) * kPackTileFloats;
+  const int nq = (jb + kPkK - 1) / kPkK;
+  for (int q = 0; q < nq; ++q)
+    for (int w = threadIdx.x; w < kPkTile; w += blockDim.x) {
+      int n, k;
+      pk_coords(w, n, k);
+      const int c = ct * kTcN + n, kk = q * kPkK + k;
+      const float v = (c < nrest && kk < jb) ? A[(j0 + kk) + int64_t(t0 + c) * ld] : 0.f;
+      float hi, lo;
+      split_tf32(v, hi, lo);
+      dst[int64_t(2 * q) * kPkTile + w] = hi;
+      dst[int64_t(2 * q + 1) * kPkTile + w] = lo;
+    }
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+// named barrier of the epilogue warps, with an AND over the threads' votes
+__device__ __forceinline__ bool epi_bar_and(bool v) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.s32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, 1, 256, p;\n\t"
+      "selp.s32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"(int(v)));
+  return r != 0;
+}
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+constexpr int kWsThreads = 288;  // eight epilogue warps and one producer / MMA warp
+
+// Block-end update C[t0:f, t0:f] -= L21 U12 (K = jb <= 256) from packed
+// operands.  Warp 8 streams the (A, B) chunk pairs of the CTA's tiles through
+// two shared-memory stages with bulk copies and issues the MMAs of each chunk
+// as soon as it lands, into one of two TMEM accumulators (alternating by
+// tile); warps 0-7 take a finished accumulator, subtract it from the C tile
+// (TMA in and out, or plain loads and stores when t0 is not a multiple of 4)
+// and hand it back, so the epilogue of tile i overlaps the MMAs of tile i + 1.
+// Every wait is bounded; on timeout the kernel raises the error flag, waits
+// (bounded) for its copies and MMAs in flight, releases TMEM and returns.
+__global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__restrict__ fr, int j0, int kb,
+                                                             float *__restrict__ fronts, int *__restrict__ err,
+                                                             int splits, int tile_lo, int tile_hi,
+                                                             const uint8_t *__restrict__ maps,
+                                                             const float *__restrict__ apack,
+                                                             const float *__restrict__ bpack) {
+  const FrontDev F = fr[blockIdx.z];
+  if (j0 >= F.s) return;
+  const int jb = min(kb, F.s - j0);
+  const int t0 = j0 + jb;
+  const int nrest = F.f - t0;
+  const int rb = blockIdx.y * kTcM;
+  if (rb >= nrest) return;
+  const int ntiles = min((nrest + kTcN - 1) / kTcN, tile_hi) - tile_lo;
+  if (ntiles <= 0) return;
+  const int per = (ntiles + splits - 1) / splits;
+  const int c_lo = tile_lo + blockIdx.x * per, c_hi = min(tile_lo + ntiles, c_lo + per);
+  if (c_lo >= c_hi) return;
+  const int nt = c_hi - c_lo;
+  const int nq = (jb + kPkK - 1) / kPkK;
+  const int G = nt * nq;  // chunk steps of this CTA
+  const void *tmap = maps + size_t(blockIdx.z) * kTmapBytes;
+  float *A = fronts + F.off;
+  const int64_t ld = F.ld;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  float *stage0 = reinterpret_cast<float *>(smraw);  // 2 stages x (Ah, Al, Bh, Bl)
+  float *sC = stage0 + 2 * 4 * kPkTile;               // 128 x 128, column-major (TMA box order)
+  __shared__ __align__(8) uint64_t full[2], empty[2], accf[2], acce[2], cbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool use_tma = (t0 & 3) == 0;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(uint32_t(2 * kTcN)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&accf[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acce[i])), "r"(1));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&cbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const float *Ab = apack + (int64_t(F.pack_off) + blockIdx.y) * kPackTileFloats;
+  const float *Bb = bpack + int64_t(F.pack_off) * kPackTileFloats;
+  constexpr uint32_t kHalfBytes = 2 * kPkTile * 4;  // a hi and a lo array: 32 KB
+
+  if (warp == 8) {
+    // ---- producer and MMA issuer ----
+    if (lane == 0) {
+      int issued = 0, consumed = 0, last_mma = -1;
+      bool ok = true;
+      auto copy = [&](int g) {
+        const int s = g & 1, i = g / nq, q = g % nq;
+        const float *a = Ab + int64_t(q) * 2 * kPkTile;
+        const float *b = Bb + int64_t(c_lo + i) * kPackTileFloats + int64_t(q) * 2 * kPkTile;
+        const uint32_t dst = smem_u32(stage0 + s * 4 * kPkTile);
+        const uint32_t mb = smem_u32(&full[s]);
+        mbar_expect_tx(mb, 2 * kHalfBytes);
+        bulk_copy_g2s(dst, a, kHalfBytes, mb);
+        bulk_copy_g2s(dst + kHalfBytes, b, kHalfBytes, mb);
+        ++issued;
+      };
+      copy(0);
+      if (G > 1) copy(1);
+      for (int g = 0; g < G; ++g) {
+        const int s = g & 1, i = g / nq, q = g % nq, a = i & 1;
+        if (!wait_phase(smem_u32(&full[s]), uint32_t((g >> 1) & 1))) {
+          ok = false;
+          break;
+        }
+        ++consumed;
+        if (q == 0 && i >= 2 && !wait_phase(smem_u32(&acce[a]), uint32_t(((i - 2) >> 1) & 1))) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t base = smem_u32(stage0 + s * 4 * kPkTile);
+        const uint32_t ah0 = base, al0 = base + kPkTile * 4, bh0 = base + 2 * kPkTile * 4, bl0 = base + 3 * kPkTile * 4;
+        const uint32_t acc = tmem + uint32_t(a * kTcN);
+#pragma unroll
+        for (int kk = 0; kk < kPkK / 8; ++kk) {
+          const uint32_t koff = uint32_t(kk) * 2 * kLbo;
+          const uint64_t ah = smem_desc_pk(ah0 + koff), al = smem_desc_pk(al0 + koff);
+          const uint64_t bh = smem_desc_pk(bh0 + koff), bl = smem_desc_pk(bl0 + koff);
+          mma_tf32(acc, ah, bh, (q > 0 || kk > 0) ? 1u : 0u);
+          mma_tf32(acc, ah, bl, 1u);
+          mma_tf32(acc, al, bh, 1u);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&empty[s])));
+        last_mma = g;
+        if (q == nq - 1)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&accf[a])));
+        if (g + 2 < G) {
+          if (!wait_phase(smem_u32(&empty[s]), uint32_t((g >> 1) & 1))) {  // this stage's MMAs are done
+            ok = false;
+            break;
+          }
+          copy(g + 2);
+        }
+      }
+      if (!ok) {
+        abort_flag = 1;
+        atomicOr(err, 4);
+        // bounded waits for what still targets this CTA's shared and tensor memory
+        for (int g = consumed; g < issued; ++g) wait_phase(smem_u32(&full[g & 1]), uint32_t((g >> 1) & 1));
+        if (last_mma >= 0) wait_phase(smem_u32(&empty[last_mma & 1]), uint32_t((last_mma >> 1) & 1));
+      }
+    }
+  } else {
+    // ---- epilogue warps ----
+    const int q4 = warp & 3, half = warp >> 2;
+    bool c_pending = false;  // thread 0: a C load (for tile c_next) is in flight
+    int c_next = 0;
+    if (use_tma && tid == 0) {
+      mbar_expect_tx(smem_u32(&cbar), uint32_t(kTcM * kTcN * 4));
+      tma_load_2d(smem_u32(sC), tmap, t0 + rb, t0 + c_lo * kTcN, smem_u32(&cbar));
+      c_pending = true;
+    }
+    for (int i = 0; i < nt; ++i) {
+      const int a = i & 1, ct = c_lo + i;
+      bool w = !abort_flag && wait_phase(smem_u32(&accf[a]), uint32_t((i >> 1) & 1));
+      if (use_tma && w) w = wait_phase(smem_u32(&cbar), uint32_t(i & 1));
+      if (!epi_bar_and(w)) {
+        if (tid == 0) abort_flag = 1, atomicOr(err, 4);
+        break;
+      }
+      if (tid == 0) c_pending = false;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int row = q4 * 32 + lane;
+      const int cb = ct * kTcN + half * 64;
+      float *Crow = A + (t0 + rb + row) + int64_t(t0 + cb) * ld;
+      const int ncol = rb + row < nrest ? min(64, nrest - cb) : 0;
+#pragma unroll
+      for (int c0 = 0; c0 < 64; c0 += 32) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(a * kTcN + half * 64 + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+              "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+              "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (use_tma) {
+          float *col = sC + (half * 64 + c0) * kTcM + row;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) col[j * kTcM] -= __uint_as_float(v[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (c0 + j < ncol) Crow[int64_t(c0 + j) * ld] -= __uint_as_float(v[j]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      if (use_tma) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      epi_bar();
+      if (tid == 0) {
+        mbar_arrive(smem_u32(&acce[a]));  // the accumulator is free again
+        if (use_tma) {
+          tma_store_2d(tmap, t0 + rb, t0 + ct * kTcN, smem_u32(sC));
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          if (i + 1 < nt) {
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // the store has read the tile
+            mbar_expect_tx(smem_u32(&cbar), uint32_t(kTcM * kTcN * 4));
+            tma_load_2d(smem_u32(sC), tmap, t0 + rb, t0 + (ct + 1) * kTcN, smem_u32(&cbar));
+            c_pending = true;
+            c_next = i + 1;
+          }
+        }
+      }
+    }
+    if (tid == 0) {
+      if (c_pending) wait_phase(smem_u32(&cbar), uint32_t(c_next & 1));  // bounded; only after an abort
+      asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(2 * kTcN)));
+}
+
+// Whole-wave split count: each CTA takes ceil(ct / splits) column tiles of one
+// row tile; the launch lasts about ceil(CTAs / slots) such ranges (plus the
+// A staging, `lead` tiles), minimised over whole waves.
+int wave_splits(int rt, int ct, int nfront, int slots, double lead) {
+  int splits = 1;
+  double best = 1e300;
+  for (int sp = 1; sp <= ct; ++sp) {
+    const int per = (ct + sp - 1) / sp;
+    if (sp > 1 && (ct + sp - 2) / (sp - 1) == per) continue;  // same range length, more CTAs
+    const double waves = double((int64_t(rt) * nfront * sp + slots - 1) / slots);
+    const double cost = waves * (per + lead);
+    if (cost < best - 1e-9) best = cost, splits = sp;
+  }
+  return splits;
+}
+
 }  // namespace
 
 size_t gemm_tc_smem() { return size_t(24) * kTileFloats + 1024; }
@@ -467,24 +997,95 @@ cudaError_t launch_gemm_tc(const FrontDev *fr, int j0, int nfront, int max_f, fl
   // ceil(ct / splits) column tiles of one row tile; the launch lasts about
   // ceil(CTAs / SMs) such ranges (plus the A staging, ~0.3 tile), so splits
   // is chosen to minimise that over whole waves.
-  const int slots = std::max(sm_budget, 1);
-  int splits = 1;
-  double best = 1e300;
-  for (int sp = 1; sp <= ct; ++sp) {
-    const int per = (ct + sp - 1) / sp;
-    if (sp > 1 && (ct + sp - 2) / (sp - 1) == per) continue;  // same range length, more CTAs
-    const double waves = double((int64_t(rt) * nfront * sp + slots - 1) / slots);
-    const double cost = waves * (per + 0.3);
-    if (cost < best - 1e-9) best = cost, splits = sp;
-  }
+  const int splits = wave_splits(rt, ct, nfront, std::max(sm_budget, 1), 0.3);
   dim3 g(splits, rt, nfront);
   if (maps != nullptr) {
     if (any_full)
       k_gemm_tc_tma<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, tile_lo, tile_hi, maps);
-    if (any_partial) k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, tile_lo, tile_hi, 1);
+    if (any_partial)
+      k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, tile_lo, tile_hi, 1, 0);
   } else {
-    k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, tile_lo, tile_hi, 0);
+    k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, tile_lo, tile_hi, 0, 0);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tc_inner(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
+                                 cudaStream_t s, int sm_budget) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gemm_tc_smem()));
+    attr = true;
+  }
+  const int rest = max_f - j0 - 1;
+  const int cols = (j0 / kb) * kb + kb - (j0 + kTcK);  // columns left in the outer block (at most)
+  if (rest <= 0 || cols <= 0) return cudaSuccess;
+  const int rt = (rest + kTcM - 1) / kTcM;
+  const int ct = (cols + kTcN - 1) / kTcN;
+  const int splits = wave_splits(rt, ct, nfront, std::max(sm_budget, 1), 0.3);
+  dim3 g(splits, rt, nfront);
+  k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, 0, ct, 0, kb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tc_outer(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
+                                 cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gemm_tc_outer, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gemm_tc_smem()));
+    attr = true;
+  }
+  if (maps == nullptr) return cudaErrorInvalidValue;
+  const int rest = max_f - j0 - 1;
+  if (rest <= 0) return cudaSuccess;
+  const int rt = (rest + kTcM - 1) / kTcM;
+  const int ct = std::min((rest + kTcN - 1) / kTcN, tile_hi) - tile_lo;
+  if (ct <= 0) return cudaSuccess;
+  // per tile: kb / 64 chunks of staging and MMAs; the lead is small
+  const int splits = wave_splits(rt, ct, nfront, std::max(sm_budget, 1), 0.05);
+  dim3 g(splits, rt, nfront);
+  k_gemm_tc_outer<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi, maps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_a(const FrontDev *fr, int j0, int kb, int nfront, int max_f, const float *fronts, float *apack,
+                          cudaStream_t s) {
+  const int rest = max_f - j0 - 1;
+  if (rest <= 0 || nfront == 0) return cudaSuccess;
+  k_pack_a<<<dim3((rest + kTcM - 1) / kTcM, nfront), 256, 0, s>>>(fr, j0, kb, fronts, apack);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_b(const FrontDev *fr, int j0, int kb, int nfront, int max_f, const float *fronts, float *bpack,
+                          int ct_lo, int ct_hi, cudaStream_t s) {
+  const int rest = max_f - j0 - 1;
+  if (rest <= 0 || nfront == 0) return cudaSuccess;
+  const int nct = std::min((rest + kTcN - 1) / kTcN, ct_hi) - ct_lo;
+  if (nct <= 0) return cudaSuccess;
+  k_pack_b<<<dim3(nct, nfront), 256, 0, s>>>(fr, j0, kb, fronts, bpack, ct_lo, ct_hi);
+  return cudaGetLastError();
+}
+
+size_t gemm_ws_smem() { return size_t(2 * 4 * kPkTile + kTcM * kTcN) * sizeof(float) + 1024; }
+
+cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
+                              cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps,
+                              const float *apack, const float *bpack) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gemm_tc_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gemm_ws_smem()));
+    attr = true;
+  }
+  if (maps == nullptr || apack == nullptr || bpack == nullptr) return cudaErrorInvalidValue;
+  const int rest = max_f - j0 - 1;
+  if (rest <= 0) return cudaSuccess;
+  const int rt = (rest + kTcM - 1) / kTcM;
+  const int ct = std::min((rest + kTcN - 1) / kTcN, tile_hi) - tile_lo;
+  if (ct <= 0) return cudaSuccess;
+  const int splits = wave_splits(rt, ct, nfront, std::max(sm_budget, 1), 0.05);
+  dim3 g(splits, rt, nfront);
+  k_gemm_tc_ws<<<g, kWsThreads, gemm_ws_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi, maps, apack,
+                                                     bpack);
   return cudaGetLastError();
 }
 

@@ -26,8 +26,15 @@ cudaError_t launch_transform(const XItem *items, int n, const void *const *src_b
 struct FrontDev {
   int64_t off, piv_off, idx_off, map_off, dinv_off;
   int32_t s, b, f, parent;
-  int32_t ld;  // leading dimension of the front (f rounded up to a multiple of 4)
+  int32_t ld;        // leading dimension of the front (f rounded up to a multiple of 4)
+  int32_t pack_off;  // first 128-row tile of the front in its level's packed GEMM operands
 };
+
+// Packed operands of the blocked FP32 LU's block-end update: per 128-row
+// (or 128-column) tile, kPackChunks chunks of 32 K values, each a TF32 hi
+// array and a lo array of 128 x 32 in the tensor cores' shared-memory layout.
+constexpr int kPackChunks = 8;
+constexpr int64_t kPackTileFloats = int64_t(kPackChunks) * 2 * 128 * 32;
 
 // Column block of the blocked triangular solves (and of the inverted diagonal blocks).
 constexpr int kSolveBlock = 64;
@@ -66,7 +73,7 @@ struct LuAsync {
 template <typename T>
 cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
                             int32_t *piv, int32_t *swaps, int *err, cudaStream_t s, const LuAsync *la, Prof *prof,
-                            const uint8_t *maps = nullptr);
+                            const uint8_t *maps = nullptr, float *pack = nullptr);
 template <typename T>
 cudaError_t launch_extend_add_impl(const FrontDev *fr_all, int lo, int nfront, int max_b, const int32_t *map,
                                    T *fronts, cudaStream_t s, Prof *prof, double elems);
@@ -116,6 +123,26 @@ constexpr int kTmapBytes = 128;
 cudaError_t launch_gemm_tc(const FrontDev *fr, int j0, int nfront, int max_f, float *fronts, int *err,
                            cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps,
                            bool any_full, bool any_partial);
+// Blocked FP32 LU (kb-column outer blocks of 64-column panels):
+// inner step at panel j0: C -= L21 U12 on the columns left in the outer block
+// only, [j0 + 64, min(J + kb, s)) with J = kb floor(j0 / kb);
+cudaError_t launch_gemm_tc_inner(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
+                                 cudaStream_t s, int sm_budget);
+// block end at J = j0: C[t0:f, t0:f] -= L21 U12 with K = min(kb, s - j0)
+// (t0 = j0 + K), over the 128-column tiles [tile_lo, tile_hi); needs `maps`.
+cudaError_t launch_gemm_tc_outer(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
+                                 cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps);
+// the same update from packed operands: k_pack_a writes L21 (the rows after
+// the block, K = the block's columns) into apack, k_pack_b the U12 columns of
+// tiles [ct_lo, ct_hi) of the trailing block into bpack; the warp-specialised
+// GEMM then streams both with bulk copies.
+cudaError_t launch_pack_a(const FrontDev *fr, int j0, int kb, int nfront, int max_f, const float *fronts, float *apack,
+                          cudaStream_t s);
+cudaError_t launch_pack_b(const FrontDev *fr, int j0, int kb, int nfront, int max_f, const float *fronts, float *bpack,
+                          int ct_lo, int ct_hi, cudaStream_t s);
+cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
+                              cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps,
+                              const float *apack, const float *bpack);
 cudaError_t make_front_tmaps(const Front *fronts, int n, const float *base, uint8_t *maps_dev);
 constexpr int kTcTile = 128;
 
