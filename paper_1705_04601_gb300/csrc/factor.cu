@@ -738,10 +738,10 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const FrontDev *__restrict__ 
 // tests), each value read once for all the warp's columns.
 // trsm = 1: columns [t0 + c_lo, t0 + c_hi) clipped to f (t0 = J + jbo);
 // trsm = 0: interchanges only, columns [c_lo, min(c_hi, J)).
-constexpr int kBlkCols = 8;                    // columns per warp
+constexpr int kBlkCols = 4;                    // columns per warp
 constexpr int kBlkCtaCols = 8 * kBlkCols;      // columns per CTA (eight warps)
 template <int KB>
-__global__ void __launch_bounds__(256) k_blk_swap_trsm(const FrontDev *__restrict__ fr, int J, float *__restrict__ fronts,
+__global__ void __launch_bounds__(256, 3) k_blk_swap_trsm(const FrontDev *__restrict__ fr, int J, float *__restrict__ fronts,
                                                       const int32_t *__restrict__ swaps, int64_t swap_stride, int c_lo,
                                                       int c_hi, int trsm) {
   static_assert(KB % 64 == 0 && KB <= 256, "outer block");
@@ -768,6 +768,8 @@ __global__ void __launch_bounds__(256) k_blk_swap_trsm(const FrontDev *__restric
   const int cw = lo + blockIdx.x * kBlkCtaCols + warp * CW;  // this warp's first column
   const int npan = (jbo + 63) / 64;
   constexpr int kPer = (kMaxSwapRows + 31) / 32;
+  // one gather and one scatter round per panel for all the warp's columns
+  const int ncw = max(0, min(CW, hi - cw));
   for (int i = 0; i < npan; ++i) {
     const int32_t *sw = swaps + int64_t(((J / 64) + i) & 7) * swap_stride + int64_t(fi) * (1 + 2 * kMaxSwapRows);
     const int n = sw[0];
@@ -779,19 +781,19 @@ __global__ void __launch_bounds__(256) k_blk_swap_trsm(const FrontDev *__restric
       srow[q] = e < n ? sw[1 + e] : 0;
       ssrc[q] = e < n ? sw[1 + kMaxSwapRows + e] : 0;
     }
-    for (int j = 0; j < CW; ++j) {
-      if (cw + j >= hi) break;
-      float *col = A + int64_t(cw + j) * ld;
-      float v[kPer];
+    float v[CW][kPer];
+#pragma unroll
+    for (int j = 0; j < CW; ++j)
 #pragma unroll
       for (int q = 0; q < kPer; ++q)
-        if (lane + 32 * q < n) v[q] = col[ssrc[q]];
-      __syncwarp();
+        if (j < ncw && lane + 32 * q < n) v[j][q] = A[ssrc[q] + int64_t(cw + j) * ld];
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < CW; ++j)
 #pragma unroll
       for (int q = 0; q < kPer; ++q)
-        if (lane + 32 * q < n) col[srow[q]] = v[q];
-      __syncwarp();
-    }
+        if (j < ncw && lane + 32 * q < n) A[srow[q] + int64_t(cw + j) * ld] = v[j][q];
+    __syncwarp();
   }
   if (!trsm) return;
   extern __shared__ float Ls[];  // [64][KB]: column kl of the current 64-column block of L11, rows 0..KB-1

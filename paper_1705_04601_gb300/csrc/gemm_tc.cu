@@ -653,9 +653,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc_outer(const FrontDev 
 }
 
 // ---- packed operands and the warp-specialised block-end update ----
-constexpr int kPkK = 32;                          // K values per packed chunk
-constexpr int kPkTile = kTcM * kPkK;              // floats per hi (or lo) array: 4096 = 16 KB
-constexpr uint32_t kPkSbo = (kPkK / 4) * 128;     // 8-row groups of a packed array (1024 bytes)
+constexpr int kPkK = 16;                          // K values per packed chunk
+constexpr int kPkTile = kTcM * kPkK;              // floats per hi (or lo) array: 2048 = 8 KB
+constexpr uint32_t kPkSbo = (kPkK / 4) * 128;     // 8-row groups of a packed array (512 bytes)
+constexpr int kWsStages = 6;                      // chunks in flight (32 KB each)
 static_assert(kPackTileFloats == int64_t(kPackChunks) * 2 * kPkTile, "packed tile size");
 
 __device__ __forceinline__ uint64_t smem_desc_pk(uint32_t saddr) {
@@ -667,64 +668,76 @@ __device__ __forceinline__ uint64_t smem_desc_pk(uint32_t saddr) {
   return d;
 }
 
-// Word w of a packed 128 x 32 array holds element (m, k) (m = row of A or
+// Word w of a packed 128 x 16 array holds element (m, k) (m = row of A or
 // column of B, k = K index): 8-row x 4-K core matrices of 128 bytes, K-adjacent
-// cores 128 bytes apart, 8-row groups 1024 bytes apart.
+// cores 128 bytes apart, 8-row groups 512 bytes apart.
 __device__ __forceinline__ void pk_coords(int w, int &m, int &k) {
-  m = ((w >> 8) << 3) | ((w >> 2) & 7);
-  k = (((w >> 5) & 7) << 2) | (w & 3);
+  m = ((w >> 7) << 3) | ((w >> 2) & 7);
+  k = (((w >> 5) & 3) << 2) | (w & 3);
 }
 
 // L21 of the outer block [j0, j0 + jb): rows [t0, f), t0 = j0 + jb, one CTA
-// per 128-row tile; zero beyond the front and beyond jb.
+// per 128-row tile and 16-wide K chunk; zero beyond the front and beyond jb.
+constexpr int kPkPer = kPkTile / 256;  // elements per thread of a chunk
 __global__ void __launch_bounds__(256) k_pack_a(const FrontDev *__restrict__ fr, int j0, int kb,
                                                 const float *__restrict__ fronts, float *__restrict__ pack) {
   const FrontDev F = fr[blockIdx.y];
   if (j0 >= F.s) return;
   const int jb = min(kb, F.s - j0), t0 = j0 + jb, nrest = F.f - t0;
-  const int rt = blockIdx.x;
-  if (rt * kTcM >= nrest) return;
+  const int rt = blockIdx.x / kPackChunks, q = blockIdx.x % kPackChunks;
+  if (rt * kTcM >= nrest || q * kPkK >= jb) return;
   const float *A = fronts + F.off;
   const int64_t ld = F.ld;
-  float *dst = pack + (int64_t(F.pack_off) + rt) * kPackTileFloats;
-  const int nq = (jb + kPkK - 1) / kPkK;
-  for (int q = 0; q < nq; ++q)
-    for (int w = threadIdx.x; w < kPkTile; w += blockDim.x) {
-      int m, k;
-      pk_coords(w, m, k);
-      const int r = rt * kTcM + m, kk = q * kPkK + k;
-      const float v = (r < nrest && kk < jb) ? A[(t0 + r) + int64_t(j0 + kk) * ld] : 0.f;
-      float hi, lo;
-      split_tf32(v, hi, lo);
-      dst[int64_t(2 * q) * kPkTile + w] = hi;
-      dst[int64_t(2 * q + 1) * kPkTile + w] = lo;
-    }
+  float *dst = pack + (int64_t(F.pack_off) + rt) * kPackTileFloats + int64_t(2 * q) * kPkTile;
+  float v[kPkPer];
+#pragma unroll
+  for (int it = 0; it < kPkPer; ++it) {
+    const int w = threadIdx.x + it * 256;
+    int m, k;
+    pk_coords(w, m, k);
+    const int r = rt * kTcM + m, kk = q * kPkK + k;
+    v[it] = (r < nrest && kk < jb) ? A[(t0 + r) + int64_t(j0 + kk) * ld] : 0.f;
+  }
+#pragma unroll
+  for (int it = 0; it < kPkPer; ++it) {
+    const int w = threadIdx.x + it * 256;
+    float hi, lo;
+    split_tf32(v[it], hi, lo);
+    dst[w] = hi;
+    dst[kPkTile + w] = lo;
+  }
 }
 
-// U12 (rows [j0, j0 + jb)) of the trailing-block column tiles [ct_lo, ct_hi).
+// U12 (rows [j0, j0 + jb)) of the trailing-block column tiles [ct_lo, ct_hi),
+// one CTA per tile and chunk.
 __global__ void __launch_bounds__(256) k_pack_b(const FrontDev *__restrict__ fr, int j0, int kb,
                                                 const float *__restrict__ fronts, float *__restrict__ pack, int ct_lo,
                                                 int ct_hi) {
   const FrontDev F = fr[blockIdx.y];
   if (j0 >= F.s) return;
   const int jb = min(kb, F.s - j0), t0 = j0 + jb, nrest = F.f - t0;
-  const int ct = ct_lo + blockIdx.x;
-  if (ct >= ct_hi || ct * kTcN >= nrest) return;
+  const int ct = ct_lo + int(blockIdx.x) / kPackChunks, q = blockIdx.x % kPackChunks;
+  if (ct >= ct_hi || ct * kTcN >= nrest || q * kPkK >= jb) return;
   const float *A = fronts + F.off;
   const int64_t ld = F.ld;
-  float *dst = pack + (int64_t(F.pack_off) + ct) * kPackTileFloats;
-  const int nq = (jb + kPkK - 1) / kPkK;
-  for (int q = 0; q < nq; ++q)
-    for (int w = threadIdx.x; w < kPkTile; w += blockDim.x) {
-      int n, k;
-      pk_coords(w, n, k);
-      const int c = ct * kTcN + n, kk = q * kPkK + k;
-      const float v = (c < nrest && kk < jb) ? A[(j0 + kk) + int64_t(t0 + c) * ld] : 0.f;
-      float hi, lo;
-      split_tf32(v, hi, lo);
-      dst[int64_t(2 * q) * kPkTile + w] = hi;
-      dst[int64_t(2 * q + 1) * kPkTile + w] = lo;
-    }
+  float *dst = pack + (int64_t(F.pack_off) + ct) * kPackTileFloats + int64_t(2 * q) * kPkTile;
+  float v[kPkPer];
+#pragma unroll
+  for (int it = 0; it < kPkPer; ++it) {
+    const int w = threadIdx.x + it * 256;
+    int n, k;
+    pk_coords(w, n, k);
+    const int c = ct * kTcN + n, kk = q * kPkK + k;
+    v[it] = (c < nrest && kk < jb) ? A[(j0 + kk) + int64_t(t0 + c) * ld] : 0.f;
+  }
+#pragma unroll
+  for (int it = 0; it < kPkPer; ++it) {
+    const int w = threadIdx.x + it * 256;
+    float hi, lo;
+    split_tf32(v[it], hi, lo);
+    dst[w] = hi;
+    dst[kPkTile + w] = lo;
+  }
 }
 
 __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
@@ -739,34 +752,36 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 // named barrier of the epilogue warps, with an AND over the threads' votes
+constexpr int kWsEpiWarps = 16;
 __device__ __forceinline__ bool epi_bar_and(bool v) {
   int r;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\t"
       "setp.ne.s32 p, %1, 0;\n\t"
-      "bar.red.and.pred q, 1, 256, p;\n\t"
+      "bar.red.and.pred q, 1, %2, p;\n\t"
       "selp.s32 %0, 1, 0, q;\n\t}\n"
       : "=r"(r)
-      : "r"(int(v)));
+      : "r"(int(v)), "n"(kWsEpiWarps * 32));
   return r != 0;
 }
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kWsEpiWarps * 32) : "memory"); }
 
-constexpr int kWsThreads = 288;  // eight epilogue warps and one producer / MMA warp
+constexpr int kWsThreads = (kWsEpiWarps + 2) * 32;  // sixteen epilogue warps, a copy warp and an MMA warp
 
 // Block-end update C[t0:f, t0:f] -= L21 U12 (K = jb <= 256) from packed
-// operands.  Warp 8 streams the (A, B) chunk pairs of the CTA's tiles through
-// two shared-memory stages with bulk copies and issues the MMAs of each chunk
-// as soon as it lands, into one of two TMEM accumulators (alternating by
-// tile); warps 0-7 take a finished accumulator, subtract it from the C tile
-// (TMA in and out, or plain loads and stores when t0 is not a multiple of 4)
-// and hand it back, so the epilogue of tile i overlaps the MMAs of tile i + 1.
-// Every wait is bounded; on timeout the kernel raises the error flag, waits
-// (bounded) for its copies and MMAs in flight, releases TMEM and returns.
+// operands.  Warp 16 streams the (A, B) chunk pairs of the CTA's tiles through
+// kWsStages shared-memory stages with bulk copies, refilling a stage once the
+// MMAs that read it have finished; warp 17 issues the MMAs of each chunk as
+// soon as it lands, into one of two TMEM accumulators (alternating by tile).  Warps
+// 0-15 prefetch their rows of the next C tile (a row and 32 columns per
+// thread) into registers while its MMAs run, then subtract the finished
+// accumulator and store (one lane per row: coalesced), and hand the
+// accumulator back.  Every wait is bounded; on
+// timeout the kernel raises the error flag, waits (bounded) for its copies and
+// MMAs in flight, releases TMEM and returns.
 __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__restrict__ fr, int j0, int kb,
                                                              float *__restrict__ fronts, int *__restrict__ err,
                                                              int splits, int tile_lo, int tile_hi,
-                                                             const uint8_t *__restrict__ maps,
                                                              const float *__restrict__ apack,
                                                              const float *__restrict__ bpack) {
   const FrontDev F = fr[blockIdx.z];
@@ -784,30 +799,28 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__
   const int nt = c_hi - c_lo;
   const int nq = (jb + kPkK - 1) / kPkK;
   const int G = nt * nq;  // chunk steps of this CTA
-  const void *tmap = maps + size_t(blockIdx.z) * kTmapBytes;
   float *A = fronts + F.off;
   const int64_t ld = F.ld;
   extern __shared__ __align__(1024) unsigned char smraw[];
-  float *stage0 = reinterpret_cast<float *>(smraw);  // 2 stages x (Ah, Al, Bh, Bl)
-  float *sC = stage0 + 2 * 4 * kPkTile;               // 128 x 128, column-major (TMA box order)
-  __shared__ __align__(8) uint64_t full[2], empty[2], accf[2], acce[2], cbar;
+  float *stage0 = reinterpret_cast<float *>(smraw);  // kWsStages x (Ah, Al, Bh, Bl)
+  __shared__ __align__(8) uint64_t full[kWsStages], empty[kWsStages], accf[2], acce[2];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool use_tma = (t0 & 3) == 0;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                  "r"(uint32_t(2 * kTcN)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kWsStages; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(1));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(1));
+    }
+    for (int i = 0; i < 2; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&accf[i])), "r"(1));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acce[i])), "r"(1));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&cbar)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
   }
@@ -816,39 +829,60 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__
   const uint32_t tmem = tmem_base;
   const float *Ab = apack + (int64_t(F.pack_off) + blockIdx.y) * kPackTileFloats;
   const float *Bb = bpack + int64_t(F.pack_off) * kPackTileFloats;
-  constexpr uint32_t kHalfBytes = 2 * kPkTile * 4;  // a hi and a lo array: 32 KB
+  constexpr uint32_t kHalfBytes = 2 * kPkTile * 4;  // a hi and a lo array: 16 KB
+  constexpr int kStageFloats = 4 * kPkTile;
 
-  if (warp == 8) {
-    // ---- producer and MMA issuer ----
+  __shared__ volatile int s_consumed;  // chunks whose copies the MMA warp has waited for
+  if (tid == 0) s_consumed = 0;
+  __syncthreads();
+  if (warp == kWsEpiWarps) {
+    // ---- copy producer ----
     if (lane == 0) {
-      int issued = 0, consumed = 0, last_mma = -1;
-      bool ok = true;
-      auto copy = [&](int g) {
-        const int s = g & 1, i = g / nq, q = g % nq;
+      int issued = 0;
+      for (int g = 0; g < G; ++g) {
+        const int st = g % kWsStages, i = g / nq, q = g % nq;
+        if (g >= kWsStages) {
+          // the MMAs of chunk g - kWsStages (same stage) have finished
+          const bool w = !abort_flag && wait_phase(smem_u32(&empty[st]), uint32_t(((g - kWsStages) / kWsStages) & 1));
+          if (!w) {
+            abort_flag = 1;
+            break;
+          }
+        }
         const float *a = Ab + int64_t(q) * 2 * kPkTile;
         const float *b = Bb + int64_t(c_lo + i) * kPackTileFloats + int64_t(q) * 2 * kPkTile;
-        const uint32_t dst = smem_u32(stage0 + s * 4 * kPkTile);
-        const uint32_t mb = smem_u32(&full[s]);
+        const uint32_t dst = smem_u32(stage0 + st * kStageFloats);
+        const uint32_t mb = smem_u32(&full[st]);
         mbar_expect_tx(mb, 2 * kHalfBytes);
         bulk_copy_g2s(dst, a, kHalfBytes, mb);
         bulk_copy_g2s(dst + kHalfBytes, b, kHalfBytes, mb);
         ++issued;
-      };
-      copy(0);
-      if (G > 1) copy(1);
-      for (int g = 0; g < G; ++g) {
-        const int s = g & 1, i = g / nq, q = g % nq, a = i & 1;
-        if (!wait_phase(smem_u32(&full[s]), uint32_t((g >> 1) & 1))) {
+      }
+      if (abort_flag) {
+        atomicOr(err, 4);
+        // bounded waits for the copies still writing this CTA's shared memory
+        for (int g = s_consumed; g < issued; ++g)
+          wait_phase(smem_u32(&full[g % kWsStages]), uint32_t((g / kWsStages) & 1));
+      }
+    }
+  } else if (warp == kWsEpiWarps + 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      int last_mma = -1;
+      bool ok = true;
+      for (int g = 0; g < G && ok; ++g) {
+        const int st = g % kWsStages, i = g / nq, q = g % nq, a = i & 1;
+        if (abort_flag || !wait_phase(smem_u32(&full[st]), uint32_t((g / kWsStages) & 1))) {
           ok = false;
           break;
         }
-        ++consumed;
+        s_consumed = g + 1;
         if (q == 0 && i >= 2 && !wait_phase(smem_u32(&acce[a]), uint32_t(((i - 2) >> 1) & 1))) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t base = smem_u32(stage0 + s * 4 * kPkTile);
+        const uint32_t base = smem_u32(stage0 + st * kStageFloats);
         const uint32_t ah0 = base, al0 = base + kPkTile * 4, bh0 = base + 2 * kPkTile * 4, bl0 = base + 3 * kPkTile * 4;
         const uint32_t acc = tmem + uint32_t(a * kTcN);
 #pragma unroll
@@ -861,96 +895,63 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__
           mma_tf32(acc, al, bh, 1u);
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(&empty[s])));
+            smem_u32(&empty[st])));
         last_mma = g;
         if (q == nq - 1)
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
               smem_u32(&accf[a])));
-        if (g + 2 < G) {
-          if (!wait_phase(smem_u32(&empty[s]), uint32_t((g >> 1) & 1))) {  // this stage's MMAs are done
-            ok = false;
-            break;
-          }
-          copy(g + 2);
-        }
       }
       if (!ok) {
         abort_flag = 1;
         atomicOr(err, 4);
-        // bounded waits for what still targets this CTA's shared and tensor memory
-        for (int g = consumed; g < issued; ++g) wait_phase(smem_u32(&full[g & 1]), uint32_t((g >> 1) & 1));
-        if (last_mma >= 0) wait_phase(smem_u32(&empty[last_mma & 1]), uint32_t((last_mma >> 1) & 1));
+        if (last_mma >= 0)
+          wait_phase(smem_u32(&empty[last_mma % kWsStages]), uint32_t((last_mma / kWsStages) & 1));
       }
     }
   } else {
-    // ---- epilogue warps ----
-    const int q4 = warp & 3, half = warp >> 2;
-    bool c_pending = false;  // thread 0: a C load (for tile c_next) is in flight
-    int c_next = 0;
-    if (use_tma && tid == 0) {
-      mbar_expect_tx(smem_u32(&cbar), uint32_t(kTcM * kTcN * 4));
-      tma_load_2d(smem_u32(sC), tmap, t0 + rb, t0 + c_lo * kTcN, smem_u32(&cbar));
-      c_pending = true;
-    }
+    // ---- epilogue warps: thread (q4, qc) owns row q4 * 32 + lane, columns qc * 32 .. + 31 ----
+    const int q4 = warp & 3, qc = warp >> 2;
+    const int row = rb + q4 * 32 + lane;
     for (int i = 0; i < nt; ++i) {
       const int a = i & 1, ct = c_lo + i;
-      bool w = !abort_flag && wait_phase(smem_u32(&accf[a]), uint32_t((i >> 1) & 1));
-      if (use_tma && w) w = wait_phase(smem_u32(&cbar), uint32_t(i & 1));
+      const int cb = ct * kTcN + qc * 32;
+      float *Crow = A + (t0 + row) + int64_t(t0 + cb) * ld;
+      const int ncol = row < nrest ? min(32, nrest - cb) : 0;
+      float cv[32];
+      {
+        const float *p = Crow;  // one pointer, bumped by ld (not 32 live addresses)
+#pragma unroll
+        for (int j = 0; j < 32; ++j, p += ld) cv[j] = j < ncol ? *p : 0.f;
+      }
+      const bool w = !abort_flag && wait_phase(smem_u32(&accf[a]), uint32_t((i >> 1) & 1));
       if (!epi_bar_and(w)) {
         if (tid == 0) abort_flag = 1, atomicOr(err, 4);
         break;
       }
-      if (tid == 0) c_pending = false;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const int row = q4 * 32 + lane;
-      const int cb = ct * kTcN + half * 64;
-      float *Crow = A + (t0 + rb + row) + int64_t(t0 + cb) * ld;
-      const int ncol = rb + row < nrest ? min(64, nrest - cb) : 0;
 #pragma unroll
-      for (int c0 = 0; c0 < 64; c0 += 32) {
-        uint32_t v[32];
-        const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(a * kTcN + half * 64 + c0);
+      for (int c0 = 0; c0 < 32; c0 += 16) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(a * kTcN + qc * 32 + c0);
         asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
-              "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-              "=r"(v[30]), "=r"(v[31])
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;");
-        if (use_tma) {
-          float *col = sC + (half * 64 + c0) * kTcM + row;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) col[j * kTcM] -= __uint_as_float(v[j]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (c0 + j < ncol) Crow[int64_t(c0 + j) * ld] -= __uint_as_float(v[j]);
-        }
+        for (int j = 0; j < 16; ++j) cv[c0 + j] -= __uint_as_float(v[j]);
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
-      if (use_tma) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       epi_bar();
-      if (tid == 0) {
-        mbar_arrive(smem_u32(&acce[a]));  // the accumulator is free again
-        if (use_tma) {
-          tma_store_2d(tmap, t0 + rb, t0 + ct * kTcN, smem_u32(sC));
-          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-          if (i + 1 < nt) {
-            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // the store has read the tile
-            mbar_expect_tx(smem_u32(&cbar), uint32_t(kTcM * kTcN * 4));
-            tma_load_2d(smem_u32(sC), tmap, t0 + rb, t0 + (ct + 1) * kTcN, smem_u32(&cbar));
-            c_pending = true;
-            c_next = i + 1;
-          }
-        }
+      if (tid == 0) mbar_arrive(smem_u32(&acce[a]));  // the accumulator is free again
+      {
+        float *p = Crow;
+#pragma unroll
+        for (int j = 0; j < 32; ++j, p += ld)
+          if (j < ncol) *p = cv[j];
       }
-    }
-    if (tid == 0) {
-      if (c_pending) wait_phase(smem_u32(&cbar), uint32_t(c_next & 1));  // bounded; only after an abort
-      asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1052,7 +1053,7 @@ cudaError_t launch_pack_a(const FrontDev *fr, int j0, int kb, int nfront, int ma
                           cudaStream_t s) {
   const int rest = max_f - j0 - 1;
   if (rest <= 0 || nfront == 0) return cudaSuccess;
-  k_pack_a<<<dim3((rest + kTcM - 1) / kTcM, nfront), 256, 0, s>>>(fr, j0, kb, fronts, apack);
+  k_pack_a<<<dim3(((rest + kTcM - 1) / kTcM) * kPackChunks, nfront), 256, 0, s>>>(fr, j0, kb, fronts, apack);
   return cudaGetLastError();
 }
 
@@ -1062,11 +1063,11 @@ cudaError_t launch_pack_b(const FrontDev *fr, int j0, int kb, int nfront, int ma
   if (rest <= 0 || nfront == 0) return cudaSuccess;
   const int nct = std::min((rest + kTcN - 1) / kTcN, ct_hi) - ct_lo;
   if (nct <= 0) return cudaSuccess;
-  k_pack_b<<<dim3(nct, nfront), 256, 0, s>>>(fr, j0, kb, fronts, bpack, ct_lo, ct_hi);
+  k_pack_b<<<dim3(nct * kPackChunks, nfront), 256, 0, s>>>(fr, j0, kb, fronts, bpack, ct_lo, ct_hi);
   return cudaGetLastError();
 }
 
-size_t gemm_ws_smem() { return size_t(2 * 4 * kPkTile + kTcM * kTcN) * sizeof(float) + 1024; }
+size_t gemm_ws_smem() { return size_t(kWsStages) * 4 * kPkTile * sizeof(float) + 1024; }
 
 cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
                               cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps,
@@ -1076,15 +1077,17 @@ cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, in
     cudaFuncSetAttribute(k_gemm_tc_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gemm_ws_smem()));
     attr = true;
   }
-  if (maps == nullptr || apack == nullptr || bpack == nullptr) return cudaErrorInvalidValue;
+  (void)maps;
+  if (apack == nullptr || bpack == nullptr) return cudaErrorInvalidValue;
   const int rest = max_f - j0 - 1;
   if (rest <= 0) return cudaSuccess;
   const int rt = (rest + kTcM - 1) / kTcM;
   const int ct = std::min((rest + kTcN - 1) / kTcN, tile_hi) - tile_lo;
   if (ct <= 0) return cudaSuccess;
-  const int splits = wave_splits(rt, ct, nfront, std::max(sm_budget, 1), 0.05);
+  // a CTA's first tile costs about one more tile (set-up, first copies and C)
+  const int splits = wave_splits(rt, ct, nfront, std::max(sm_budget, 1), 1.0);
   dim3 g(splits, rt, nfront);
-  k_gemm_tc_ws<<<g, kWsThreads, gemm_ws_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi, maps, apack,
+  k_gemm_tc_ws<<<g, kWsThreads, gemm_ws_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi, apack,
                                                      bpack);
   return cudaGetLastError();
 }

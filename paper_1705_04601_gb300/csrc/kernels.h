@@ -31,10 +31,10 @@ struct FrontDev {
 };
 
 // Packed operands of the blocked FP32 LU's block-end update: per 128-row
-// (or 128-column) tile, kPackChunks chunks of 32 K values, each a TF32 hi
-// array and a lo array of 128 x 32 in the tensor cores' shared-memory layout.
-constexpr int kPackChunks = 8;
-constexpr int64_t kPackTileFloats = int64_t(kPackChunks) * 2 * 128 * 32;
+// (or 128-column) tile, kPackChunks chunks of 16 K values, each a TF32 hi
+// array and a lo array of 128 x 16 in the tensor cores' shared-memory layout.
+constexpr int kPackChunks = 16;
+constexpr int64_t kPackTileFloats = int64_t(kPackChunks) * 2 * 128 * 16;
 
 // Column block of the blocked triangular solves (and of the inverted diagonal blocks).
 constexpr int kSolveBlock = 64;
