@@ -783,8 +783,7 @@ std::shared_ptr<StructureDev> build_structure(const Plan &p) {
       for (int b = 0; b < maxb; b += 2)
         for (int k = L.lo; k < L.hi; ++k)
           if (b < (p.fronts[k].s + kSolveBlock - 1) / kSolveBlock) items.push_back(make_int2(k, b));
-      for (int k = L.lo; k < L.hi; ++k)
-        for (int q = 0; q < (p.fronts[k].b + kSolveBlock - 1) / kSolveBlock; ++q) items.push_back(make_int2(k, -(q + 1)));
+      // (the boundary rows take their L21 product after the forward sweep, in one rectangular product)
       sd->chain_fwd_n.push_back(int(items.size()) - sd->chain_fwd_off.back());
       sd->chain_bwd_off.push_back(int(items.size()));
       for (int d = 0; d < maxb; d += 2)

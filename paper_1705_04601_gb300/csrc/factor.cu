@@ -1186,40 +1186,81 @@ __global__ void __launch_bounds__(kStepThreads) k_bwd_step(const FrontDev *__res
   slab_update<T>(fronts + F.off, F.ld, W, F.f, r0, c0, c0, cb, nrhs, sX, sD);
 }
 
-// rows [0, s) of W -= U12 * W[s:f] (before the backward block sweep); the
-// columns [s, f) are split into chunks over blockIdx.y, partial sums added atomically
+// The rectangular products of the sweeps that do not lie on the block chain:
+//   mode 0 (backward, before the sweep): W[0:s]  -= U12 W[s:f]   (U12 = rows [0, s), columns [s, f))
+//   mode 1 (forward, after the sweep):   W[s:f]  -= L21 Z[0:s]   (L21 = rows [s, f), columns [0, s))
+// Two output rows per thread and a 256-wide K chunk per CTA (blockIdx.y).
+// The chunk's X values are staged in shared memory with the right-hand sides
+// of one k contiguous, so a thread reads them as 16-byte vectors shared by its
+// two rows; eight matrix loads per row are in flight.  Partial sums over the
+// chunks are added atomically.
 constexpr int kU12Chunk = 256;
+constexpr int kRectRows = 2 * kRowsPerCta;  // output rows per CTA
 template <typename T>
-__global__ void __launch_bounds__(kRowsPerCta) k_bwd_u12(const FrontDev *__restrict__ fr, const T *__restrict__ fronts,
-                                                         int nrhs, T *__restrict__ work,
-                                                         const int64_t *__restrict__ work_off, int lo) {
+__global__ void __launch_bounds__(kRowsPerCta) k_rect_update(const FrontDev *__restrict__ fr, const T *__restrict__ fronts,
+                                                             int nrhs, T *__restrict__ work, const T *__restrict__ zbuf,
+                                                             const int64_t *__restrict__ work_off, int lo, int mode) {
+  constexpr int VE = 16 / int(sizeof(T));  // right-hand sides per 16-byte vector
   const FrontDev F = fr[blockIdx.z];
-  const int k_lo = F.s + int(blockIdx.y) * kU12Chunk;
-  if (F.b == 0 || int(blockIdx.x) * kRowsPerCta >= F.s || k_lo >= F.f) return;
-  const int k_hi = min(F.f, k_lo + kU12Chunk);
-  __shared__ T sX[kU12Chunk * kMaxRhs];
+  const int r_lo = mode ? F.s : 0, r_hi = mode ? F.f : F.s;
+  const int kk_lo = mode ? 0 : F.s, kk_hi = mode ? F.s : F.f;
+  const int k_lo = kk_lo + int(blockIdx.y) * kU12Chunk;
+  const int rb = r_lo + int(blockIdx.x) * kRectRows;
+  if (F.b == 0 || rb >= r_hi || k_lo >= kk_hi) return;
+  const int k_hi = min(kk_hi, k_lo + kU12Chunk);
+  __shared__ __align__(16) T sX[kU12Chunk * kMaxRhs];  // sX[q * kMaxRhs + c]
   T *W = work + work_off[lo + blockIdx.z];
+  const T *X = (mode ? zbuf : work) + work_off[lo + blockIdx.z];
   const int kb = k_hi - k_lo;
-  for (int e = threadIdx.x; e < kb * nrhs; e += blockDim.x) {
-    const int q = e % kb, c = e / kb;
-    sX[q + c * kU12Chunk] = W[(k_lo + q) + int64_t(c) * F.f];
+  for (int e = threadIdx.x; e < kU12Chunk * kMaxRhs; e += blockDim.x) {
+    const int q = e % kU12Chunk, c = e / kU12Chunk;
+    sX[q * kMaxRhs + c] = (q < kb && c < nrhs) ? X[(k_lo + q) + int64_t(c) * F.f] : T(0);
   }
   __syncthreads();
-  const int r = blockIdx.x * kRowsPerCta + threadIdx.x;
-  if (r >= F.s) return;
-  T acc[kMaxRhs];
+  const int r0 = rb + int(threadIdx.x), r1 = r0 + kRowsPerCta;
+  if (r0 >= r_hi) return;
+  const bool has1 = r1 < r_hi;
+  T acc0[kMaxRhs], acc1[kMaxRhs];
 #pragma unroll
-  for (int c = 0; c < kMaxRhs; ++c) acc[c] = T(0);
-  const T *A = fronts + F.off;
-  for (int q = 0; q < kb; ++q) {
-    const T a = A[r + int64_t(k_lo + q) * F.ld];
+  for (int c = 0; c < kMaxRhs; ++c) acc0[c] = acc1[c] = T(0);
+  const T *A0 = fronts + F.off + r0;
+  const T *A1 = fronts + F.off + (has1 ? r1 : r0);
+  constexpr int U = 8;
+  for (int q0 = 0; q0 < kb; q0 += U) {
+    T a0[U], a1[U];
 #pragma unroll
-    for (int c = 0; c < kMaxRhs; ++c)
-      if (c < nrhs) acc[c] += a * sX[q + c * kU12Chunk];
+    for (int u = 0; u < U; ++u) {
+      const bool in = q0 + u < kb;
+      a0[u] = in ? A0[int64_t(k_lo + q0 + u) * F.ld] : T(0);
+      a1[u] = (in && has1) ? A1[int64_t(k_lo + q0 + u) * F.ld] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const T *xq = sX + (q0 + u) * kMaxRhs;
+#pragma unroll
+      for (int c = 0; c < kMaxRhs; c += VE) {
+        T xv[VE];
+        if constexpr (VE == 4) {
+          const float4 v = *reinterpret_cast<const float4 *>(xq + c);
+          xv[0] = v.x, xv[1] = v.y, xv[2] = v.z, xv[3] = v.w;
+        } else {
+          const double2 v = *reinterpret_cast<const double2 *>(xq + c);
+          xv[0] = v.x, xv[1] = v.y;
+        }
+#pragma unroll
+        for (int j = 0; j < VE; ++j) {
+          acc0[c + j] += a0[u] * xv[j];
+          acc1[c + j] += a1[u] * xv[j];
+        }
+      }
+    }
   }
 #pragma unroll
   for (int c = 0; c < kMaxRhs; ++c)
-    if (c < nrhs) atomicAdd(&W[r + int64_t(c) * F.f], -acc[c]);
+    if (c < nrhs) {
+      atomicAdd(&W[r0 + int64_t(c) * F.f], -acc0[c]);
+      if (has1) atomicAdd(&W[r1 + int64_t(c) * F.f], -acc1[c]);
+    }
 }
 
 template <typename T>
@@ -2021,7 +2062,10 @@ cudaError_t launch_solve_fwd_level_impl(const FrontDev *fr, int lo, int nfront, 
   if (ca != nullptr) {
     cudaError_t ce = launch_chain<T, true>(fr, *ca, li, fronts, dinv, nrhs, work, zbuf, work_off, s);
     if (ce != cudaSuccess) return ce;
-    ++nl;
+    // the boundary rows take the whole L21 Z product after the chain
+    k_rect_update<T><<<dim3(cdiv(std::max(max_f - 1, 1), kRectRows), cdiv(max_s, kU12Chunk), nfront), kRowsPerCta, 0,
+                       s>>>(frl, fronts, nrhs, work, zbuf, work_off, lo, 1);
+    nl += 2;
   } else
   for (int c0 = 0; c0 < max_s; c0 += kBS) {
     const int rest = max_f - c0 - 1;
@@ -2045,8 +2089,8 @@ cudaError_t launch_solve_bwd_level_impl(const FrontDev *fr, int lo, int nfront, 
   const size_t e0 = prof->begin();
   int nl = 3;
   k_bwd_gather<T><<<dim3(cdiv(max_f, 256), nfront), 256, 0, s>>>(frl, idx, y, ldy, nrhs, work, work_off, lo);
-  k_bwd_u12<T><<<dim3(cdiv(max_s, kRowsPerCta), cdiv(std::max(max_f - 1, 1), kU12Chunk), nfront), kRowsPerCta, 0, s>>>(
-      frl, fronts, nrhs, work, work_off, lo);
+  k_rect_update<T><<<dim3(cdiv(max_s, kRectRows), cdiv(std::max(max_f - 1, 1), kU12Chunk), nfront), kRowsPerCta, 0,
+                     s>>>(frl, fronts, nrhs, work, zbuf, work_off, lo, 0);
   const int last = ((max_s - 1) / kBS) * kBS;
   if (ca != nullptr) {
     cudaError_t ce = launch_chain<T, false>(fr, *ca, li, fronts, dinv, nrhs, work, zbuf, work_off, s);
