@@ -213,13 +213,18 @@ int h2sp_analyze(const h2sp_h2_desc *desc, h2sp_handle **out);
  * h2sp_factor -- block LU of S (the paper factors S with a sparse direct
  * method, §5.3-5.4): nested-dissection order along the cluster tree,
  * multifrontal elimination level by level, partial pivoting inside each
- * supernode's diagonal block.  `prec` selects FP64 or FP32 fronts; FP32
- * trailing updates run on the tensor cores with operands split into two TF32
- * terms (FP32-level products).  The next panel is factored on an internal
- * high-priority stream while the rest of the update runs on an internal
- * low-priority one; both are joined back to `stream` before the call
- * returns.  Synchronises the stream; returns H2SP_ESINGULAR on a zero or
- * non-finite pivot and H2SP_ETIMEOUT if a bounded device wait gave up.
+ * supernode's diagonal block.  `prec` selects FP64 or FP32 fronts.  FP64
+ * fronts take one trailing update per 64-column panel.  FP32 fronts are
+ * factored in 256-column outer blocks of four panels: interchanges and
+ * updates stay inside the block until its end, then the other columns take
+ * the interchanges, the triangular solve for U12 and one rank-256 update on
+ * the tensor cores with operands split into two TF32 terms (FP32-level
+ * products); the same factorization up to rounding order.  The panels and
+ * the next block's columns run on an internal high-priority stream, the rest
+ * of each block end on an internal low-priority one; both are joined back to
+ * `stream` before the call returns.  Synchronises the stream; returns
+ * H2SP_ESINGULAR on a zero or non-finite pivot and H2SP_ETIMEOUT if a bounded
+ * device wait gave up.
  */
 int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream);
 
