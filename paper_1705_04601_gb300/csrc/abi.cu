@@ -144,6 +144,9 @@ struct h2sp_handle {
   int64_t *work_off = nullptr;
   void *work = nullptr, *zbuf = nullptr, *dinv = nullptr;
   float *yf = nullptr;
+  // FP32 preconditioner: Q rounded to FP32, apply work vectors and the input
+  float *Qf = nullptr, *Qcf = nullptr, *vecAf = nullptr, *vecBf = nullptr, *rf = nullptr;
+  int vecf_rhs = 0;
   int work_rhs = 0;
   // H^2 product
   H2Dev h2{};
@@ -249,8 +252,10 @@ void ensure_vectors(h2sp_handle *h, int nrhs) {
   h->vec_rhs = nrhs;
 }
 
-// out (S space, ld n) = Qside^T in (point space)
-void apply_T(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *out, int64_t ldout, int nrhs) {
+// out (S space, ld n) = Q^T in (point space) with the blocks Qb of one side
+template <typename T>
+void apply_T_impl(h2sp_handle *h, const T *Qb, const T *in, int64_t ldin, T *out, int64_t ldout, int nrhs, T *bufA,
+                  T *bufB) {
   const Plan &p = (*h->plan_ptr);
   cudaStream_t s = h->stream;
   const int chunks = (nrhs + 15) / 16;
@@ -261,17 +266,16 @@ void apply_T(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *o
     int n;
     ~Done() { h->prof.end(P_APPLY, n, e0, 0.0); }
   } done{h, e0, 1 + p.lstop * chunks};
-  const double *Qb = col ? h->Qc : h->Q;
   if (p.lstop == 0) {
     ck(launch_copy_rows(h->top_src, h->top_dst, h->top_len, h->ntop, in, ldin, out, ldout, nrhs, s));
     return;
   }
   const int64_t ldw = std::max<int64_t>(h->max_width, p.n);
-  const double *x = in;
+  const T *x = in;
   int64_t ldx = ldin;
-  double *bufs[2] = {h->vecA, h->vecB};
+  T *bufs[2] = {bufA, bufB};
   for (int l = 0; l < p.lstop; ++l) {
-    double *xn = bufs[l & 1];
+    T *xn = bufs[l & 1];
     ck(launch_apply_qt(h->lv[l].ap, h->lv[l].nap, Qb, x, ldx, out, ldout, xn, ldw, nrhs, s));
     x = xn;
     ldx = ldw;
@@ -279,8 +283,10 @@ void apply_T(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *o
   ck(launch_copy_rows(h->top_src, h->top_dst, h->top_len, h->ntop, x, ldx, out, ldout, nrhs, s));
 }
 
-// out (point space) = Qside in (S space)
-void apply_N(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *out, int64_t ldout, int nrhs) {
+// out (point space) = Q in (S space) with the blocks Qb of one side
+template <typename T>
+void apply_N_impl(h2sp_handle *h, const T *Qb, const T *in, int64_t ldin, T *out, int64_t ldout, int nrhs, T *bufA,
+                  T *bufB) {
   const Plan &p = (*h->plan_ptr);
   cudaStream_t s = h->stream;
   const int chunks = (nrhs + 15) / 16;
@@ -291,21 +297,30 @@ void apply_N(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *o
     int n;
     ~Done() { h->prof.end(P_APPLY, n, e0, 0.0); }
   } done{h, e0, 1 + p.lstop * chunks};
-  const double *Qb = col ? h->Qc : h->Q;
   if (p.lstop == 0) {
     ck(launch_copy_rows(h->top_dst, h->top_src, h->top_len, h->ntop, in, ldin, out, ldout, nrhs, s));
     return;
   }
   const int64_t ldw = std::max<int64_t>(h->max_width, p.n);
-  double *bufs[2] = {h->vecA, h->vecB};
-  double *xn = bufs[p.lstop & 1];
+  T *bufs[2] = {bufA, bufB};
+  T *xn = bufs[p.lstop & 1];
   ck(launch_copy_rows(h->top_dst, h->top_src, h->top_len, h->ntop, in, ldin, xn, ldw, nrhs, s));
   for (int l = p.lstop - 1; l >= 0; --l) {
-    double *x = (l == 0) ? out : bufs[l & 1];
+    T *x = (l == 0) ? out : bufs[l & 1];
     const int64_t ldx = (l == 0) ? ldout : ldw;
     ck(launch_apply_q(h->lv[l].ap, h->lv[l].nap, Qb, xn, ldw, in, ldin, x, ldx, nrhs, s));
     xn = x;
   }
+}
+
+// out (S space, ld n) = Qside^T in (point space)
+void apply_T(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *out, int64_t ldout, int nrhs) {
+  apply_T_impl<double>(h, col ? h->Qc : h->Q, in, ldin, out, ldout, nrhs, h->vecA, h->vecB);
+}
+
+// out (point space) = Qside in (S space)
+void apply_N(h2sp_handle *h, bool col, const double *in, int64_t ldin, double *out, int64_t ldout, int nrhs) {
+  apply_N_impl<double>(h, col ? h->Qc : h->Q, in, ldin, out, ldout, nrhs, h->vecA, h->vecB);
 }
 
 void h2_matvec(h2sp_handle *h, const double *x, int64_t ldx, double *y, int64_t ldy, int nrhs) {
@@ -418,9 +433,54 @@ void solve_S(h2sp_handle *h, double *y, int nrhs) {
   }
 }
 
+// The FP32 factors are applied with FP32 U^T and V (Q rounded to FP32) and
+// FP32 vectors; H2SP_PRECOND=fp64 keeps the FP64 applies around them.
+bool fp32_applies_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = std::getenv("H2SP_PRECOND");
+    v = (e && std::strcmp(e, "fp64") == 0) ? 0 : 1;
+  }
+  return v == 1;
+}
+
+void ensure_vectors_f32(h2sp_handle *h, int nrhs) {
+  const Plan &p = (*h->plan_ptr);
+  if (h->Qf == nullptr) {
+    const int64_t q = std::max<int64_t>(p.q_elems, 1);
+    h->Qf = h->alloc<float>(size_t(q));
+    ck(launch_cast_d2f(h->Q, q, h->Qf, q, q, 1, h->stream));
+    if (p.sym) {
+      h->Qcf = h->Qf;
+    } else {
+      h->Qcf = h->alloc<float>(size_t(q));
+      ck(launch_cast_d2f(h->Qc, q, h->Qcf, q, q, 1, h->stream));
+    }
+  }
+  if (h->vecf_rhs < nrhs) {
+    const int64_t w = std::max<int64_t>(h->max_width, p.n);
+    h->vecAf = h->alloc<float>(size_t(w) * nrhs);
+    h->vecBf = h->alloc<float>(size_t(w) * nrhs);
+    h->rf = h->alloc<float>(size_t(p.n) * nrhs);
+    h->vecf_rhs = nrhs;
+  }
+}
+
 // d = V S^{-1} U^T r   (the direct solve of Eq. sp0)
 void precond(h2sp_handle *h, const double *r, int64_t ldr, double *d, int64_t ldd, int nrhs) {
   const int64_t n = (*h->plan_ptr).n;
+  if (h->prec == H2SP_FP32 && fp32_applies_enabled()) {
+    // all of M^{-1} in FP32: the FP64 residual around it decides convergence
+    ensure_work(h, nrhs);
+    ensure_vectors_f32(h, nrhs);
+    ck(launch_cast_d2f(r, ldr, h->rf, n, n, nrhs, h->stream));
+    apply_T_impl<float>(h, h->Qf, h->rf, n, h->yf, n, nrhs, h->vecAf, h->vecBf);
+    solve_S_T<float>(h, h->yf, nrhs);
+    apply_N_impl<float>(h, h->Qcf, h->yf, n, h->rf, n, nrhs, h->vecAf, h->vecBf);
+    ck(launch_cast_f2d(h->rf, n, d, ldd, n, nrhs, h->stream));
+    h->prof.count(P_OTHER, 2);
+    return;
+  }
   apply_T(h, false, r, ldr, h->vecS, n, nrhs);
   solve_S(h, h->vecS, nrhs);
   apply_N(h, true, h->vecS, n, d, ldd, nrhs);

@@ -13,24 +13,27 @@ namespace {
 constexpr int kRhs = 16;  // right-hand sides handled per kernel pass
 
 // Q^T applied to X_l(t); basis rows go to the next level, non-basis rows to S space
-__global__ void __launch_bounds__(64) k_apply_qt(const ApItem *__restrict__ items, const double *__restrict__ Q,
-                                                 const double *__restrict__ x, int64_t ldx, double *__restrict__ ys,
-                                                 int64_t ldys, double *__restrict__ xn, int64_t ldxn, int nrhs) {
+// T is the precision of Q, the vectors and the sums: FP64 for the applies
+// of the API, FP32 inside the FP32 preconditioner.
+template <typename T>
+__global__ void __launch_bounds__(64) k_apply_qt(const ApItem *__restrict__ items, const T *__restrict__ Q,
+                                                 const T *__restrict__ x, int64_t ldx, T *__restrict__ ys,
+                                                 int64_t ldys, T *__restrict__ xn, int64_t ldxn, int nrhs) {
   const ApItem it = items[blockIdx.x];
-  __shared__ double sx[kMaxBlock * kRhs];
+  __shared__ T sx[kMaxBlock * kRhs];
   const int m = it.m;
   for (int e = threadIdx.x; e < m * nrhs; e += blockDim.x) {
     const int j = e % m, r = e / m;
     sx[j + r * kMaxBlock] = x[it.xin + j + r * ldx];
   }
   __syncthreads();
-  const double *Qt = Q + it.q;
+  const T *Qt = Q + it.q;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    double acc[kRhs];
+    T acc[kRhs];
 #pragma unroll
-    for (int r = 0; r < kRhs; ++r) acc[r] = 0.0;
+    for (int r = 0; r < kRhs; ++r) acc[r] = T(0);
     for (int j = 0; j < m; ++j) {
-      const double q = Qt[j + int64_t(i) * m];
+      const T q = Qt[j + int64_t(i) * m];
 #pragma unroll
       for (int r = 0; r < kRhs; ++r)
         if (r < nrhs) acc[r] += q * sx[j + r * kMaxBlock];
@@ -44,16 +47,17 @@ __global__ void __launch_bounds__(64) k_apply_qt(const ApItem *__restrict__ item
   }
 }
 
-__global__ void __launch_bounds__(64) k_apply_q(const ApItem *__restrict__ items, const double *__restrict__ Q,
-                                                const double *__restrict__ xn, int64_t ldxn,
-                                                const double *__restrict__ ys, int64_t ldys, double *__restrict__ x,
+template <typename T>
+__global__ void __launch_bounds__(64) k_apply_q(const ApItem *__restrict__ items, const T *__restrict__ Q,
+                                                const T *__restrict__ xn, int64_t ldxn,
+                                                const T *__restrict__ ys, int64_t ldys, T *__restrict__ x,
                                                 int64_t ldx, int nrhs) {
   const ApItem it = items[blockIdx.x];
-  __shared__ double sz[kMaxBlock * kRhs];
+  __shared__ T sz[kMaxBlock * kRhs];
   const int m = it.m;
   for (int e = threadIdx.x; e < m * nrhs; e += blockDim.x) {
     const int j = e % m, r = e / m;
-    double v = 0.0;
+    T v = T(0);
     if (j < it.kp) {
       if (it.xout >= 0) v = xn[it.xout + j + r * ldxn];
     } else {
@@ -62,13 +66,13 @@ __global__ void __launch_bounds__(64) k_apply_q(const ApItem *__restrict__ items
     sz[j + r * kMaxBlock] = v;
   }
   __syncthreads();
-  const double *Qt = Q + it.q;
+  const T *Qt = Q + it.q;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    double acc[kRhs];
+    T acc[kRhs];
 #pragma unroll
-    for (int r = 0; r < kRhs; ++r) acc[r] = 0.0;
+    for (int r = 0; r < kRhs; ++r) acc[r] = T(0);
     for (int j = 0; j < m; ++j) {
-      const double q = Qt[i + int64_t(j) * m];
+      const T q = Qt[i + int64_t(j) * m];
 #pragma unroll
       for (int r = 0; r < kRhs; ++r)
         if (r < nrhs) acc[r] += q * sz[j + r * kMaxBlock];
@@ -77,9 +81,10 @@ __global__ void __launch_bounds__(64) k_apply_q(const ApItem *__restrict__ items
   }
 }
 
+template <typename T>
 __global__ void k_copy_rows(const int64_t *__restrict__ src_row, const int64_t *__restrict__ dst_row,
-                            const int32_t *__restrict__ len, const double *__restrict__ src, int64_t lds,
-                            double *__restrict__ dst, int64_t ldd, int nrhs) {
+                            const int32_t *__restrict__ len, const T *__restrict__ src, int64_t lds,
+                            T *__restrict__ dst, int64_t ldd, int nrhs) {
   const int64_t s0 = src_row[blockIdx.x], d0 = dst_row[blockIdx.x];
   const int n = len[blockIdx.x];
   for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) {
@@ -426,30 +431,44 @@ inline unsigned grid_for(int64_t n, int per = 256) {
 
 }  // namespace
 
-cudaError_t launch_apply_qt(const ApItem *items, int n, const double *Q, const double *x, int64_t ldx, double *ys,
-                            int64_t ldys, double *xn, int64_t ldxn, int nrhs, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_apply_qt(const ApItem *items, int n, const T *Q, const T *x, int64_t ldx, T *ys, int64_t ldys, T *xn,
+                            int64_t ldxn, int nrhs, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   for (int r0 = 0; r0 < nrhs; r0 += kRhs)
-    k_apply_qt<<<n, 64, 0, s>>>(items, Q, x + r0 * ldx, ldx, ys + r0 * ldys, ldys, xn ? xn + r0 * ldxn : nullptr,
-                                ldxn, std::min(kRhs, nrhs - r0));
+    k_apply_qt<T><<<n, 64, 0, s>>>(items, Q, x + r0 * ldx, ldx, ys + r0 * ldys, ldys, xn ? xn + r0 * ldxn : nullptr,
+                                   ldxn, std::min(kRhs, nrhs - r0));
   return cudaGetLastError();
 }
 
-cudaError_t launch_apply_q(const ApItem *items, int n, const double *Q, const double *xn, int64_t ldxn,
-                           const double *ys, int64_t ldys, double *x, int64_t ldx, int nrhs, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_apply_q(const ApItem *items, int n, const T *Q, const T *xn, int64_t ldxn, const T *ys, int64_t ldys,
+                           T *x, int64_t ldx, int nrhs, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   for (int r0 = 0; r0 < nrhs; r0 += kRhs)
-    k_apply_q<<<n, 64, 0, s>>>(items, Q, xn ? xn + r0 * ldxn : nullptr, ldxn, ys + r0 * ldys, ldys, x + r0 * ldx, ldx,
-                               std::min(kRhs, nrhs - r0));
+    k_apply_q<T><<<n, 64, 0, s>>>(items, Q, xn ? xn + r0 * ldxn : nullptr, ldxn, ys + r0 * ldys, ldys, x + r0 * ldx,
+                                  ldx, std::min(kRhs, nrhs - r0));
   return cudaGetLastError();
 }
 
-cudaError_t launch_copy_rows(const int64_t *src_row, const int64_t *dst_row, const int32_t *len, int n,
-                             const double *src, int64_t lds, double *dst, int64_t ldd, int nrhs, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_copy_rows(const int64_t *src_row, const int64_t *dst_row, const int32_t *len, int n, const T *src,
+                             int64_t lds, T *dst, int64_t ldd, int nrhs, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_copy_rows<<<n, 128, 0, s>>>(src_row, dst_row, len, src, lds, dst, ldd, nrhs);
+  k_copy_rows<T><<<n, 128, 0, s>>>(src_row, dst_row, len, src, lds, dst, ldd, nrhs);
   return cudaGetLastError();
 }
+
+#define H2SP_APPLY_INSTANTIATE(T)                                                                                      \
+  template cudaError_t launch_apply_qt<T>(const ApItem *, int, const T *, const T *, int64_t, T *, int64_t, T *,       \
+                                          int64_t, int, cudaStream_t);                                                 \
+  template cudaError_t launch_apply_q<T>(const ApItem *, int, const T *, const T *, int64_t, const T *, int64_t, T *,  \
+                                         int64_t, int, cudaStream_t);                                                  \
+  template cudaError_t launch_copy_rows<T>(const int64_t *, const int64_t *, const int32_t *, int, const T *, int64_t, \
+                                           T *, int64_t, int, cudaStream_t);
+H2SP_APPLY_INSTANTIATE(double)
+H2SP_APPLY_INSTANTIATE(float)
+#undef H2SP_APPLY_INSTANTIATE
 
 template <typename TS>
 cudaError_t launch_spmv(const int64_t *brow_ptr, const int32_t *bcol, const int64_t *val_off, const int64_t *node_off,

@@ -154,15 +154,19 @@ struct ApItem {
   int64_t xout;   // row in the level-(l+1) vector of the basis part, -1 if none
   int32_t m, kp;
 };
-// out rows: non-basis -> S space (ys), basis -> next level (xn); op = Q^T
-cudaError_t launch_apply_qt(const ApItem *items, int n, const double *Q, const double *x, int64_t ldx, double *ys,
-                            int64_t ldys, double *xn, int64_t ldxn, int nrhs, cudaStream_t s);
+// out rows: non-basis -> S space (ys), basis -> next level (xn); op = Q^T.
+// T = double (the API's applies) or float (inside the FP32 preconditioner).
+template <typename T>
+cudaError_t launch_apply_qt(const ApItem *items, int n, const T *Q, const T *x, int64_t ldx, T *ys, int64_t ldys, T *xn,
+                            int64_t ldxn, int nrhs, cudaStream_t s);
 // reverse: X_l(t) = Q [xn part; ys part]
-cudaError_t launch_apply_q(const ApItem *items, int n, const double *Q, const double *xn, int64_t ldxn,
-                           const double *ys, int64_t ldys, double *x, int64_t ldx, int nrhs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_apply_q(const ApItem *items, int n, const T *Q, const T *xn, int64_t ldxn, const T *ys, int64_t ldys,
+                           T *x, int64_t ldx, int nrhs, cudaStream_t s);
 // copy rows: dst[dst_row[i] + r] = src[src_row[i] + r] for r < len[i]
-cudaError_t launch_copy_rows(const int64_t *src_row, const int64_t *dst_row, const int32_t *len, int n,
-                             const double *src, int64_t lds, double *dst, int64_t ldd, int nrhs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_copy_rows(const int64_t *src_row, const int64_t *dst_row, const int32_t *len, int n, const T *src,
+                             int64_t lds, T *dst, int64_t ldd, int nrhs, cudaStream_t s);
 // y = S x (VBR; values of type TS, FP64 vectors and sums)
 template <typename TS>
 cudaError_t launch_spmv(const int64_t *brow_ptr, const int32_t *bcol, const int64_t *val_off, const int64_t *node_off,
