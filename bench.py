@@ -47,17 +47,14 @@ CPU_SAMPLE_N = 16384
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FP64_TFLOPS = 1.25
 
-# DRAM traffic of the dominant kernel from one ncu capture (see profiles/):
-# dram bytes read + written over the algorithmic bytes of the captured launch,
-# valid while the kernel's source file is unchanged (sha256 prefix).  The
-# bench's traffic figure is this ratio times its average algorithmic bytes per
-# launch (the capture is a 32,768-point case; the full-size workload is too
-# large to capture under the profiling size rule).
-TRAFFIC = {
-    "gemm_update": {"src": "gemm_tc.cu", "src_hash": "7660f0030d500c78",
-                    "dram_over_algorithmic": (140.42752e6 + 80.493056e6) / 276.6e6,
-                    "capture": "k_gemm_tc, root step 4 of N=32768 (trailing 5,848^2 FP32), 85.0 us"},
-}
+# DRAM traffic of the dominant kernel from an ncu capture: per kernel class,
+# dram bytes read + written over the class's algorithmic work in the captured
+# run, valid while the kernel's source file is unchanged (sha256 prefix of
+# "src").  The bench's traffic figure is this ratio times the class's average
+# work per launch.  Empty: the current captures (profiles/) are single
+# small-case launches whose algorithmic work is not known per launch, so the
+# traffic field is null.
+TRAFFIC = {}
 
 
 def parse():
