@@ -229,6 +229,19 @@ int h2sp_analyze(const h2sp_h2_desc *desc, h2sp_handle **out);
 int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream);
 
 /*
+ * h2sp_refactor -- repeat the numeric sparsification and the factorization of
+ * `h`, in the precision of its last h2sp_factor, for new numbers written into
+ * the borrowed H^2 arrays the handle was built from (same device pointers,
+ * same structure): the persistent form of the batched path.  The first call
+ * captures every launch of both phases, on every internal stream, into a CUDA
+ * graph that the handle owns; later calls replay it with one graph launch.
+ * No counterpart in the paper, which refactors by running its pipeline again.
+ * Needs a previous h2sp_factor (H2SP_ESTATE otherwise).  Synchronises the
+ * stream; returns H2SP_ESINGULAR / H2SP_ETIMEOUT as h2sp_factor.
+ */
+int h2sp_refactor(h2sp_handle *h, h2sp_stream stream);
+
+/*
  * h2sp_solve -- x = A^{-1} b through S y = U^T b, x = V y (Eq. sp0), either
  * once (DIRECT, needs h2sp_factor) or iterated on the FP64 H^2 residual
  * (IR, or GMRES right-preconditioned by the factored S, §5.5).  b (ldb >= n)

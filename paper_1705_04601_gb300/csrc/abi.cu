@@ -181,12 +181,24 @@ struct h2sp_handle {
   LuAsync la;  // look-ahead stream and events of the block LU (created on first use)
   uint8_t *tmaps = nullptr;  // TMA descriptors of the FP32 fronts (built on the first FP32 factorization)
   float *pack = nullptr;     // packed GEMM operands of the blocked FP32 LU (3 buffers of the largest level)
+  int32_t last_prec = -1;    // precision of the last h2sp_factor (h2sp_refactor repeats it)
+  cudaGraphExec_t graph_exec = nullptr;  // sparsification + factorization, captured by h2sp_refactor
+  cudaStream_t graph_stream = nullptr;    // the graph is captured and launched here (the caller's may be legacy)
+  cudaEvent_t graph_in = nullptr, graph_out = nullptr;
   // flag-synchronised triangular sweeps
   int2 *chain_items = nullptr;
   std::vector<int> chain_fwd_off, chain_fwd_n, chain_bwd_off, chain_bwd_n;
   int *chain_tickets = nullptr, *chain_flags = nullptr, *serr = nullptr;
   int chain_epoch = 0;
   void release() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    graph_exec = nullptr;
+    if (graph_stream) cudaStreamSynchronize(graph_stream);
+    if (graph_in) cudaEventDestroy(graph_in);
+    if (graph_out) cudaEventDestroy(graph_out);
+    if (graph_stream) cudaStreamDestroy(graph_stream);
+    graph_stream = nullptr;
+    graph_in = graph_out = nullptr;
     if (la.side) cudaStreamSynchronize(la.side);
     if (la.rest) cudaStreamSynchronize(la.rest);
     if (la.next) cudaEventDestroy(la.next);
@@ -858,10 +870,9 @@ std::shared_ptr<StructureDev> build_structure(const Plan &p) {
   return sd;
 }
 
-// the level recursion of the sparsification (§2.1-2.3, §4.2-4.3): FP64
-// Householder completions and couplings, products into S in precision W
-template <typename W>
-void sparsify_levels(h2sp_handle *h, const Plan &p, const StructureDev &sd, cudaStream_t s) {
+// per-level buffers of the sparsification (stacked bases) and the source /
+// destination tables of its kernels
+void sparsify_setup_levels(h2sp_handle *h, const Plan &p) {
   const int L = p.lstop;
   const int nlw = int(p.lw.size());
   for (int l = 0; l < nlw; ++l) {
@@ -878,6 +889,15 @@ void sparsify_levels(h2sp_handle *h, const Plan &p, const StructureDev &sd, cuda
     d.src_base = h->upload(sb);
     d.dst_base = h->upload(db);
   }
+}
+
+// the level recursion of the sparsification (§2.1-2.3, §4.2-4.3), kernels
+// only: FP64 Householder completions and couplings, products into S in
+// precision W
+template <typename W>
+void sparsify_kernels(h2sp_handle *h, const Plan &p, const StructureDev &sd, cudaStream_t s) {
+  const int L = p.lstop;
+  const int nlw = int(p.lw.size());
   for (int l = 0; l < nlw; ++l) {
     const LevelWork &w = p.lw[l];
     LevelDev &d = h->lv[l];
@@ -898,6 +918,24 @@ void sparsify_levels(h2sp_handle *h, const Plan &p, const StructureDev &sd, cuda
                            reinterpret_cast<W *const *>(d.dst_base), s, &h->prof,
                            l < int(h->x_flops.size()) ? h->x_flops[l] : 0.0));
   }
+}
+
+// every launch of the numeric sparsification (no allocation, no host
+// synchronisation): zero the accumulated buffers, then the level recursion
+void sparsify_launch(h2sp_handle *h) {
+  const Plan &p = (*h->plan_ptr);
+  cudaStream_t s = h->stream;
+  const size_t wsz = (h->sp_prec == H2SP_FP32) ? sizeof(float) : sizeof(double);
+  ck(cudaMemsetAsync(h->S, 0, wsz * size_t(std::max<int64_t>(p.s_elems, 1)), s));
+  for (int l = 1; l < p.lstop; ++l) {
+    ck(cudaMemsetAsync(h->Cbuf[l], 0, wsz * size_t(std::max<int64_t>(p.c_elems[l], 1)), s));
+    ck(cudaMemsetAsync(h->RPbuf[l], 0, wsz * size_t(std::max<int64_t>(p.rp_elems[l], 1)), s));
+    ck(cudaMemsetAsync(h->CPbuf[l], 0, wsz * size_t(std::max<int64_t>(p.cp_elems[l], 1)), s));
+  }
+  if (h->sp_prec == H2SP_FP32)
+    sparsify_kernels<float>(h, p, *h->sdev, s);
+  else
+    sparsify_kernels<double>(h, p, *h->sdev, s);
 }
 
 // numeric part of the sparsification: the handle's buffers and the kernels,
@@ -938,7 +976,6 @@ int sparsify_numeric(h2sp_handle *h, const h2sp_h2_desc *desc, int32_t sp_prec, 
       h->Rrc = h->alloc<double>(size_t(p.rr_elems));
     }
     h->S = walloc(p.s_elems);
-    ck(cudaMemsetAsync(h->S, 0, wsz * size_t(std::max<int64_t>(p.s_elems, 1)), s));
     const int L = p.lstop;
     h->Cbuf.assign(L + 1, nullptr);
     h->RPbuf.assign(L + 1, nullptr);
@@ -947,17 +984,12 @@ int sparsify_numeric(h2sp_handle *h, const h2sp_h2_desc *desc, int32_t sp_prec, 
       h->Cbuf[l] = walloc(p.c_elems[l]);
       h->RPbuf[l] = walloc(p.rp_elems[l]);
       h->CPbuf[l] = walloc(p.cp_elems[l]);
-      ck(cudaMemsetAsync(h->Cbuf[l], 0, wsz * size_t(std::max<int64_t>(p.c_elems[l], 1)), s));
-      ck(cudaMemsetAsync(h->RPbuf[l], 0, wsz * size_t(std::max<int64_t>(p.rp_elems[l], 1)), s));
-      ck(cudaMemsetAsync(h->CPbuf[l], 0, wsz * size_t(std::max<int64_t>(p.cp_elems[l], 1)), s));
     }
     // ---- per-level tables and the sparsification kernels, level by level ----
     h->lv = sd.lv;
     h->x_flops = sd.x_flops;
-    if (sp_prec == H2SP_FP32)
-      sparsify_levels<float>(h, p, sd, s);
-    else
-      sparsify_levels<double>(h, p, sd, s);
+    sparsify_setup_levels(h, p);
+    sparsify_launch(h);
     // ---- structure views for the applies, products, factor and solves ----
     h->max_width = sd.max_width;
     h->top_src = sd.top_src;
@@ -1034,6 +1066,96 @@ void copy_out(h2sp_handle *h, double *dst, const void *src, int64_t n) {
     ck(cudaMemcpyAsync(dst, src, sizeof(double) * size_t(n), cudaMemcpyDeviceToHost, h->stream));
     ck(cudaStreamSynchronize(h->stream));
   }
+}
+
+// ---- factorization, in three parts: buffers (first call), launches, check ----
+void factor_prepare(h2sp_handle *h, int32_t prec) {
+  const Plan &p = (*h->plan_ptr);
+  cudaStream_t s = h->stream;
+  if (h->fronts == nullptr) {
+    // sized for FP64 so that a later factorization in either precision reuses it
+    h->fronts = h->alloc<double>(size_t(std::max<int64_t>(p.front_elems, 1)));
+    h->piv = h->alloc<int32_t>(size_t(std::max<int64_t>(p.piv_elems, 1)));
+    h->perm = h->alloc<int32_t>(size_t(std::max<int64_t>(p.piv_elems, 1)));
+    size_t maxn = 1;
+    for (const FrontLevel &L : h->flev) maxn = std::max<size_t>(maxn, size_t(L.hi - L.lo));
+    h->swaps = h->alloc<int32_t>(8 * maxn * (1 + 2 * kMaxSwapRows));  // two outer blocks of panels in flight
+    h->err = h->alloc<int>(1);
+    h->dinv = h->alloc<double>(size_t(std::max<int64_t>(p.dinv_elems, 1)));
+  }
+  if (h->la.side == nullptr && lookahead_enabled()) {
+    int lo = 0, hi = 0;
+    ck(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    ck(cudaStreamCreateWithPriority(&h->la.side, cudaStreamNonBlocking, hi));
+    ck(cudaStreamCreateWithPriority(&h->la.rest, cudaStreamNonBlocking, lo));
+    ck(cudaEventCreateWithFlags(&h->la.next, cudaEventDisableTiming));
+    ck(cudaEventCreateWithFlags(&h->la.panel, cudaEventDisableTiming));
+    ck(cudaEventCreateWithFlags(&h->la.done, cudaEventDisableTiming));
+  }
+  if (prec == H2SP_FP32 && h->tmaps == nullptr && tma_enabled() && !p.fronts.empty()) {
+    uint8_t *m = h->alloc<uint8_t>(p.fronts.size() * kTmapBytes);
+    ck(cudaStreamSynchronize(s));  // the allocation is usable by the synchronous copy
+    if (make_front_tmaps(p.fronts.data(), int(p.fronts.size()), static_cast<float *>(h->fronts), m) == cudaSuccess)
+      h->tmaps = m;
+    cudaGetLastError();
+    if (h->tmaps != nullptr && h->sdev->max_pack_tiles > 0)
+      h->pack = h->alloc<float>(size_t(3 * h->sdev->max_pack_tiles * kPackTileFloats));
+  }
+}
+
+// every launch of the factorization (no allocation, no host synchronisation)
+void factor_launch(h2sp_handle *h, int32_t prec) {
+  const Plan &p = (*h->plan_ptr);
+  cudaStream_t s = h->stream;
+  const size_t esz = prec == H2SP_FP64 ? sizeof(double) : sizeof(float);
+  const LuAsync *la = h->la.side ? &h->la : nullptr;
+  ck(cudaMemsetAsync(h->fronts, 0, size_t(std::max<int64_t>(p.front_elems, 1)) * esz, s));
+  ck(cudaMemsetAsync(h->err, 0, sizeof(int), s));
+  const int64_t na = int64_t(p.assemble.size());
+  const double abytes = double(p.s_elems) * double((h->sp_prec == H2SP_FP32 ? sizeof(float) : sizeof(double)) + esz);
+  if (prec == H2SP_FP64) {
+    double *F = static_cast<double *>(h->fronts);
+    if (h->sp_prec == H2SP_FP32)
+      ck(launch_assemble<float, double>(h->asm_items, na, static_cast<const float *>(h->S), F, s, &h->prof, abytes));
+    else
+      ck(launch_assemble<double, double>(h->asm_items, na, static_cast<const double *>(h->S), F, s, &h->prof,
+                                         abytes));
+    for (const FrontLevel &L : h->flev) {
+      ck(launch_lu_level<double>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv,
+                                 h->swaps, h->err, s, la, &h->prof));
+      ck(launch_extend_add_impl<double>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s, &h->prof, L.b2));
+    }
+    ck(launch_make_perm<double>(h->fr, int(p.fronts.size()), h->max_s_all, h->piv, h->perm, s, &h->prof));
+    ck(launch_invert_diag<double>(h->fr, int(p.fronts.size()), h->max_s_all, F, static_cast<double *>(h->dinv), s,
+                                  &h->prof));
+  } else {
+    float *F = static_cast<float *>(h->fronts);
+    if (h->sp_prec == H2SP_FP32)
+      ck(launch_assemble<float, float>(h->asm_items, na, static_cast<const float *>(h->S), F, s, &h->prof, abytes));
+    else
+      ck(launch_assemble<double, float>(h->asm_items, na, static_cast<const double *>(h->S), F, s, &h->prof,
+                                        abytes));
+    for (const FrontLevel &L : h->flev) {
+      ck(launch_lu_level<float>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv,
+                                h->swaps, h->err, s, la, &h->prof,
+                                h->tmaps ? h->tmaps + size_t(L.lo) * kTmapBytes : nullptr, h->pack));
+      ck(launch_extend_add_impl<float>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s, &h->prof, L.b2));
+    }
+    ck(launch_make_perm<float>(h->fr, int(p.fronts.size()), h->max_s_all, h->piv, h->perm, s, &h->prof));
+    ck(launch_invert_diag<float>(h->fr, int(p.fronts.size()), h->max_s_all, F, static_cast<float *>(h->dinv), s,
+                                 &h->prof));
+  }
+}
+
+// the factorization's error word, after the stream has drained
+int factor_finish(h2sp_handle *h, int32_t prec) {
+  int herr = 0;
+  ck(cudaMemcpyAsync(&herr, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  ck(cudaStreamSynchronize(h->stream));
+  if (herr & 4) return H2SP_ETIMEOUT;
+  if (herr != 0) return H2SP_ESINGULAR;
+  h->prec = prec;
+  return H2SP_OK;
 }
 
 }  // namespace
@@ -1135,86 +1257,71 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
   if (prec != H2SP_FP64 && prec != H2SP_FP32) return H2SP_EINVAL;
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   h->prof.stream = h->stream;
-  const Plan &p = (*h->plan_ptr);
-  cudaStream_t s = h->stream;
   try {
-    const size_t esz = prec == H2SP_FP64 ? sizeof(double) : sizeof(float);
-    if (h->fronts == nullptr) {
-      // sized for FP64 so that a later factorization in either precision reuses it
-      h->fronts = h->alloc<double>(size_t(std::max<int64_t>(p.front_elems, 1)));
-      h->piv = h->alloc<int32_t>(size_t(std::max<int64_t>(p.piv_elems, 1)));
-      h->perm = h->alloc<int32_t>(size_t(std::max<int64_t>(p.piv_elems, 1)));
-      size_t maxn = 1;
-      for (const FrontLevel &L : h->flev) maxn = std::max<size_t>(maxn, size_t(L.hi - L.lo));
-      h->swaps = h->alloc<int32_t>(8 * maxn * (1 + 2 * kMaxSwapRows));  // two outer blocks of panels in flight
-      h->err = h->alloc<int>(1);
-      h->dinv = h->alloc<double>(size_t(std::max<int64_t>(p.dinv_elems, 1)));
-    }
-    if (h->la.side == nullptr && lookahead_enabled()) {
-      int lo = 0, hi = 0;
-      ck(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-      ck(cudaStreamCreateWithPriority(&h->la.side, cudaStreamNonBlocking, hi));
-      ck(cudaStreamCreateWithPriority(&h->la.rest, cudaStreamNonBlocking, lo));
-      ck(cudaEventCreateWithFlags(&h->la.next, cudaEventDisableTiming));
-      ck(cudaEventCreateWithFlags(&h->la.panel, cudaEventDisableTiming));
-      ck(cudaEventCreateWithFlags(&h->la.done, cudaEventDisableTiming));
-    }
-    const LuAsync *la = h->la.side ? &h->la : nullptr;
+    factor_prepare(h, prec);
     h->prec = -1;
-    ck(cudaMemsetAsync(h->fronts, 0, size_t(std::max<int64_t>(p.front_elems, 1)) * esz, s));
-    ck(cudaMemsetAsync(h->err, 0, sizeof(int), s));
-    const int64_t na = int64_t(p.assemble.size());
-    const double abytes = double(p.s_elems) * double((h->sp_prec == H2SP_FP32 ? sizeof(float) : sizeof(double)) + esz);
-    if (prec == H2SP_FP64) {
-      double *F = static_cast<double *>(h->fronts);
-      if (h->sp_prec == H2SP_FP32)
-        ck(launch_assemble<float, double>(h->asm_items, na, static_cast<const float *>(h->S), F, s, &h->prof, abytes));
-      else
-        ck(launch_assemble<double, double>(h->asm_items, na, static_cast<const double *>(h->S), F, s, &h->prof,
-                                           abytes));
-      for (const FrontLevel &L : h->flev) {
-        ck(launch_lu_level<double>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv,
-                                   h->swaps, h->err, s, la, &h->prof));
-        ck(launch_extend_add_impl<double>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s, &h->prof, L.b2));
-      }
-      ck(launch_make_perm<double>(h->fr, int(p.fronts.size()), h->max_s_all, h->piv, h->perm, s, &h->prof));
-      ck(launch_invert_diag<double>(h->fr, int(p.fronts.size()), h->max_s_all, F, static_cast<double *>(h->dinv), s,
-                                    &h->prof));
-    } else {
-      float *F = static_cast<float *>(h->fronts);
-      if (h->tmaps == nullptr && tma_enabled() && !p.fronts.empty()) {
-        uint8_t *m = h->alloc<uint8_t>(p.fronts.size() * kTmapBytes);
-        ck(cudaStreamSynchronize(s));  // the allocation is usable by the synchronous copy
-        if (make_front_tmaps(p.fronts.data(), int(p.fronts.size()), F, m) == cudaSuccess) h->tmaps = m;
-        cudaGetLastError();
-        if (h->tmaps != nullptr && h->sdev->max_pack_tiles > 0)
-          h->pack = h->alloc<float>(size_t(3 * h->sdev->max_pack_tiles * kPackTileFloats));
-      }
-      if (h->sp_prec == H2SP_FP32)
-        ck(launch_assemble<float, float>(h->asm_items, na, static_cast<const float *>(h->S), F, s, &h->prof, abytes));
-      else
-        ck(launch_assemble<double, float>(h->asm_items, na, static_cast<const double *>(h->S), F, s, &h->prof,
-                                          abytes));
-      for (const FrontLevel &L : h->flev) {
-        ck(launch_lu_level<float>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv,
-                                  h->swaps, h->err, s, la, &h->prof,
-                                  h->tmaps ? h->tmaps + size_t(L.lo) * kTmapBytes : nullptr, h->pack));
-        ck(launch_extend_add_impl<float>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s, &h->prof, L.b2));
-      }
-      ck(launch_make_perm<float>(h->fr, int(p.fronts.size()), h->max_s_all, h->piv, h->perm, s, &h->prof));
-      ck(launch_invert_diag<float>(h->fr, int(p.fronts.size()), h->max_s_all, F, static_cast<float *>(h->dinv), s,
-                                   &h->prof));
-    }
-    int herr = 0;
-    ck(cudaMemcpyAsync(&herr, h->err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    ck(cudaStreamSynchronize(s));
-    if (herr & 4) return H2SP_ETIMEOUT;
-    if (herr != 0) return H2SP_ESINGULAR;
-    h->prec = prec;
+    factor_launch(h, prec);
+    h->last_prec = prec;
+    return factor_finish(h, prec);
   } catch (const CudaFail &f) {
     return status_of(f.e);
   }
-  return H2SP_OK;
+}
+
+int h2sp_refactor(h2sp_handle *h, h2sp_stream stream) {
+  if (!h) return H2SP_EINVAL;
+  if (!h->device_ready || h->last_prec < 0) return H2SP_ESTATE;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->prof.stream = h->stream;
+  cudaStream_t s = h->stream;
+  const int32_t prec = h->last_prec;
+  bool capturing = false;
+  try {
+    if (h->graph_stream == nullptr) {
+      ck(cudaStreamCreateWithFlags(&h->graph_stream, cudaStreamNonBlocking));
+      ck(cudaEventCreateWithFlags(&h->graph_in, cudaEventDisableTiming));
+      ck(cudaEventCreateWithFlags(&h->graph_out, cudaEventDisableTiming));
+    }
+    cudaStream_t gs = h->graph_stream;
+    if (h->graph_exec == nullptr) {
+      // capture every launch of both phases, on every stream they use (the
+      // handle's buffers exist since the first factorization); the capture
+      // runs on the handle's own stream, since the caller's may be the legacy
+      // default stream, which cannot be captured
+      ck(cudaStreamSynchronize(s));
+      const int timing = h->prof.timing;
+      h->prof.timing = 0;
+      h->stream = gs;
+      ck(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+      capturing = true;
+      sparsify_launch(h);
+      factor_launch(h, prec);
+      cudaGraph_t g = nullptr;
+      capturing = false;
+      const cudaError_t ee = cudaStreamEndCapture(gs, &g);
+      h->stream = s;
+      h->prof.timing = timing;
+      ck(ee);
+      const cudaError_t ie = cudaGraphInstantiate(&h->graph_exec, g, 0);
+      cudaGraphDestroy(g);
+      ck(ie);
+    }
+    h->prec = -1;
+    ck(cudaEventRecord(h->graph_in, s));
+    ck(cudaStreamWaitEvent(gs, h->graph_in, 0));
+    ck(cudaGraphLaunch(h->graph_exec, gs));
+    ck(cudaEventRecord(h->graph_out, gs));
+    ck(cudaStreamWaitEvent(s, h->graph_out, 0));
+    return factor_finish(h, prec);
+  } catch (const CudaFail &f) {
+    if (capturing) {
+      cudaGraph_t g = nullptr;
+      if (cudaStreamEndCapture(h->graph_stream, &g) == cudaSuccess && g) cudaGraphDestroy(g);
+      cudaGetLastError();
+    }
+    h->stream = s;
+    return status_of(f.e);
+  }
 }
 
 int h2sp_apply(h2sp_handle *h, int32_t op, int32_t nrhs, const double *in, int64_t ldin, double *out, int64_t ldout,

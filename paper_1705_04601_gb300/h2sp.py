@@ -81,6 +81,7 @@ SIGNATURES = {
                                               ctypes.POINTER(_vp)]),
     "h2sp_analyze": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.POINTER(_vp)]),
     "h2sp_factor": (ctypes.c_int, [_vp, ctypes.c_int32, _vp]),
+    "h2sp_refactor": (ctypes.c_int, [_vp, _vp]),
     "h2sp_solve": (ctypes.c_int, [_vp, ctypes.POINTER(SolveOpts), ctypes.c_int32, _vp, ctypes.c_int64, _vp,
                                   ctypes.c_int64, ctypes.POINTER(SolveInfo), _vp]),
     "h2sp_apply": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int64, _vp, ctypes.c_int64,
@@ -236,6 +237,11 @@ def h2sp_sparsify_analyzed(an: Handle, inp: H2Input, stream=None, flags: int = 0
 
 def h2sp_factor(h: Handle, prec: int = H2SP_FP64, stream=None):
     _check(lib().h2sp_factor(h.ptr, int(prec), _stream(stream)), "h2sp_factor")
+
+
+def h2sp_refactor(h: Handle, stream=None):
+    """Sparsify and factor again (graph replay) after new numbers were written into the input arrays."""
+    _check(lib().h2sp_refactor(h.ptr, _stream(stream)), "h2sp_refactor")
 
 
 def _cols(t, n):

@@ -447,3 +447,41 @@ def test_fp32_factor_backward_error():
     print("fp32 factor backward error (n=%d): %.2e" % (n, eta))
     assert eta <= 1e-5
     hd.close()
+
+
+@pytest.mark.parametrize("name,prec,flags", [("log4k", "fp32", 1), ("skew1k", "fp32", 0), ("log1k", "fp64", 0)])
+def test_refactor_replays_on_new_numbers(name, prec, flags):
+    """h2sp_refactor: after new numbers are written into the borrowed arrays
+    (here the close blocks and couplings doubled in place, so A becomes 2A
+    exactly), the captured sparsification + factorization gives the solution
+    of 2 A x = b: the dense solution halved, on the first call (capture) and
+    on the second (replay)."""
+    h, b, sp = case(name)
+    inp = H.H2Input(h)
+    hd = H.h2sp_sparsify(inp, flags=flags)
+    P = H.H2SP_FP32 if prec == "fp32" else H.H2SP_FP64
+    with pytest.raises(H.H2spError) as e:
+        H.h2sp_refactor(hd)
+    assert e.value.status == H.H2SP_ESTATE
+    H.h2sp_factor(hd, P)
+    A = oh2.dense(h)
+    xd = np.linalg.solve(A, b)
+    bt = dev(b)
+    xt = torch.empty_like(bt)
+    for scale in (2.0, 4.0):
+        inp.dev["near_block"].mul_(2.0)
+        inp.dev["coupling"].mul_(2.0)
+        H.h2sp_refactor(hd)
+        if prec == "fp32":
+            info = H.h2sp_solve(hd, bt, xt, mode=H.H2SP_GMRES, tol=1e-10, maxit=60, restart=20)
+            assert info.status == H.H2SP_OK and info.rel_residual <= 1e-10
+            bound = 1e-7
+        else:
+            H.h2sp_solve(hd, bt, xt, mode=H.H2SP_DIRECT)
+            bound = 1e-9
+        torch.cuda.synchronize()
+        xg = host(xt)
+        err = np.linalg.norm(xg - xd / scale) / np.linalg.norm(xd / scale)
+        print("refactor (%s, %s, x%g): rel err %.2e" % (name, prec, scale, err))
+        assert err <= bound
+    hd.close()
