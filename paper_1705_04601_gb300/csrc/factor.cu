@@ -1825,7 +1825,7 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
   int panel_ctas = 0;
   cudaError_t e = cudaSuccess;
   if constexpr (std::is_same<T, float>::value && NB == 64) {
-    if (tc && maps != nullptr && blocked_lu_enabled()) {
+    if (tc && maps != nullptr && pack != nullptr && blocked_lu_enabled()) {
       // ---- blocked LU: outer blocks of KB columns = KB / NB panels ----
       constexpr int KB = kLuOuter;
       slot_mask = 7;
@@ -1861,8 +1861,8 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
       };
       // block end, over the columns [t0 + lo, t0 + hi) of the trailing block
       // (and, with left, the interchanges of the columns before the block)
-      float *apack[2] = {pack, pack ? pack + pack_stride : nullptr};
-      float *bpack = pack ? pack + 2 * pack_stride : nullptr;
+      float *apack[2] = {pack, pack + pack_stride};
+      float *bpack = pack + 2 * pack_stride;
       auto block_end = [&](int J, int lo, int hi, bool left, int budget, cudaStream_t st) -> cudaError_t {
         double ft = 0.0, fg = 0.0;
         int wcols = 0;
@@ -1887,15 +1887,10 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
         if (wcols <= 0) return cudaGetLastError();
         const int tlo = lo / kTcTile, thi = hi >= (INT_MAX - kTcTile) ? INT_MAX : hi / kTcTile;
         e0 = prof->begin(st);
-        cudaError_t ge;
-        if (bpack != nullptr) {
-          ge = launch_pack_b(fr, J, KB, nfront, max_f, fronts, bpack, tlo, thi, st);
-          if (ge == cudaSuccess)
-            ge = launch_gemm_tc_ws(fr, J, KB, nfront, max_f, fronts, err, st, tlo, thi, budget, maps,
-                                   apack[(J / KB) & 1], bpack);
-        } else {
-          ge = launch_gemm_tc_outer(fr, J, KB, nfront, max_f, fronts, err, st, tlo, thi, budget, maps);
-        }
+        cudaError_t ge = launch_pack_b(fr, J, KB, nfront, max_f, fronts, bpack, tlo, thi, st);
+        if (ge == cudaSuccess)
+          ge = launch_gemm_tc_ws(fr, J, KB, nfront, max_f, fronts, err, st, tlo, thi, budget, maps,
+                                 apack[(J / KB) & 1], bpack);
         prof->end(P_GEMM, 1, e0, fg, st);
         return ge != cudaSuccess ? ge : cudaGetLastError();
       };
@@ -1929,8 +1924,7 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
           }
         }
         const bool more = J + KB < max_s;
-        if (pack != nullptr && (e = launch_pack_a(fr, J, KB, nfront, max_f, fronts, apack[b & 1], ms)) != cudaSuccess)
-          return e;
+        if ((e = launch_pack_a(fr, J, KB, nfront, max_f, fronts, apack[b & 1], ms)) != cudaSuccess) return e;
         if (ahead) {
           // the rest of the block end goes to the low-priority stream as soon
           // as the block's panels are done; the next block's columns stay here

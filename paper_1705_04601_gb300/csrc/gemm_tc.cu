@@ -450,208 +450,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc_tma(const FrontDev *_
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(kTcN)));
 }
 
-// Block-end update of the blocked LU: C[t0:f, t0:f] -= L21 U12 with K = jb
-// = min(kb, s - j0) <= 256, t0 = j0 + jb.  Per 128 x 128 output tile the C
-// tile comes in by TMA, K runs in chunks of 64 (A and B chunks staged as
-// hi / lo TF32 pairs, 24 MMAs into the tensor-memory accumulator per chunk),
-// and the tile goes back by TMA: C crosses HBM once per kb columns of L
-// instead of once per 64.  A TMA box must start on a 16-byte boundary, so a
-// front whose trailing block starts at a row t0 that is not a multiple of 4
-// (its last block ends inside the kb-wide block) moves C with plain loads and
-// stores instead.  Shared memory as in k_gemm_tc_tma (192 KB).
-__global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc_outer(const FrontDev *__restrict__ fr, int j0, int kb,
-                                                                float *__restrict__ fronts, int *__restrict__ err,
-                                                                int splits, int tile_lo, int tile_hi,
-                                                                const uint8_t *__restrict__ maps) {
-  const FrontDev F = fr[blockIdx.z];
-  if (j0 >= F.s) return;
-  const int jb = min(kb, F.s - j0);
-  const int t0 = j0 + jb;
-  const int nrest = F.f - t0;
-  const int rb = blockIdx.y * kTcM;
-  if (rb >= nrest) return;
-  const int ntiles = min((nrest + kTcN - 1) / kTcN, tile_hi) - tile_lo;
-  if (ntiles <= 0) return;
-  const int per = (ntiles + splits - 1) / splits;
-  const int c_lo = tile_lo + blockIdx.x * per, c_hi = min(tile_lo + ntiles, c_lo + per);
-  if (c_lo >= c_hi) return;
-  const void *tmap = maps + size_t(blockIdx.z) * kTmapBytes;
-  float *A = fronts + F.off;
-  const int64_t ld = F.ld;
-  extern __shared__ __align__(1024) unsigned char smraw[];
-  float *sAh = reinterpret_cast<float *>(smraw), *sAl = sAh + kTileFloats;
-  float *sBh = sAl + kTileFloats, *sBl = sBh + kTileFloats;
-  float *sC = sBl + kTileFloats;  // 128 x 128, column-major (TMA box order)
-  __shared__ __align__(8) uint64_t bar_mma, bar_c;
-  __shared__ uint32_t tmem_base;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr int kIters = kTcM * kTcK / kTcThreads;
-  const int nchunks = (jb + kTcK - 1) / kTcK;
-  // chunk q of A (rows rb.., K columns j0 + 64 q ..) and of B (its U12 rows)
-  auto stage = [&](int ct, int q) {
-    const int k0 = q * kTcK, kq = min(kTcK, jb - k0);
-    const int cb = ct * kTcN;
-    float va[kIters], vb[kIters];
-#pragma unroll
-    for (int it = 0; it < kIters; ++it) {
-      const int e = tid + it * kTcThreads;
-      const int m = (e >> 9) * 8 + ((e & 31) >> 2), k = ((e >> 5) & 15) * 4 + (e & 3);
-      const int r = rb + m;
-      va[it] = (k < kq && r < nrest) ? A[(t0 + r) + int64_t(j0 + k0 + k) * ld] : 0.f;
-      const int ln = e & 31, wv = e >> 5;
-      const int kk = (ln & 7) + 8 * (wv & 7), n = (ln >> 3) + 4 * (wv >> 3);
-      const int c = cb + n;
-      vb[it] = (kk < kq && c < nrest) ? A[(j0 + k0 + kk) + int64_t(t0 + c) * ld] : 0.f;
-    }
-#pragma unroll
-    for (int it = 0; it < kIters; ++it) {
-      const int e = tid + it * kTcThreads;
-      float hi, lo;
-      split_tf32(va[it], hi, lo);
-      sAh[e] = hi;
-      sAl[e] = lo;
-      const int ln = e & 31, wv = e >> 5;
-      const int kk = (ln & 7) + 8 * (wv & 7), n = (ln >> 3) + 4 * (wv >> 3);
-      const int w = (n >> 3) * (kSbo / 4) + (kk >> 2) * (kLbo / 4) + (n & 7) * 4 + (kk & 3);
-      split_tf32(vb[it], hi, lo);
-      sBh[w] = hi;
-      sBl[w] = lo;
-    }
-  };
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"(uint32_t(kTcN)));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_mma)), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_c)), "r"(1));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = tmem_base;
-  uint32_t ph_mma = 0u, ph_c = 0u;
-  bool ok = true, mma_pending = false, c_pending = false;
-  const int q4 = warp & 3, half = warp >> 2;
-  const bool use_tma = (t0 & 3) == 0;  // uniform over the CTA
-  for (int ct = c_lo; ct < c_hi && ok; ++ct) {
-    const int x = t0 + rb, y = t0 + ct * kTcN;
-    if (use_tma) {
-      if (tid == 0) {
-        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar_c)),
-                     "r"(uint32_t(kTcM * kTcN * 4))
-                     : "memory");
-        tma_load_2d(smem_u32(sC), tmap, x, y, smem_u32(&bar_c));
-      }
-      c_pending = true;
-    }
-    for (int q = 0; q < nchunks; ++q) {
-      stage(ct, q);  // the previous chunk's MMAs have completed
-      sync_for_tensor_cores();
-      if (tid == 0) {
-        const int ksteps = (min(kTcK, jb - q * kTcK) + 7) / 8;
-        const uint32_t ah0 = smem_u32(sAh), al0 = smem_u32(sAl), bh0 = smem_u32(sBh), bl0 = smem_u32(sBl);
-        for (int kk = 0; kk < ksteps; ++kk) {
-          const uint32_t koff = uint32_t(kk) * 2 * kLbo;
-          const uint64_t ah = smem_desc(ah0 + koff), al = smem_desc(al0 + koff);
-          const uint64_t bh = smem_desc(bh0 + koff), bl = smem_desc(bl0 + koff);
-          mma_tf32(tmem, ah, bh, (q > 0 || kk > 0) ? 1u : 0u);
-          mma_tf32(tmem, ah, bl, 1u);
-          mma_tf32(tmem, al, bh, 1u);
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(&bar_mma)));
-      }
-      mma_pending = true;
-      const bool w1 = wait_phase(smem_u32(&bar_mma), ph_mma);
-      ok = __syncthreads_and(w1 ? 1 : 0) != 0;
-      if (!ok) {
-        mma_pending = !w1;
-        break;
-      }
-      ph_mma ^= 1u;
-      mma_pending = false;
-    }
-    if (!ok) break;
-    if (!use_tma) {
-      // plain epilogue: this thread's row, 64 columns of its half
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const int row = rb + q4 * 32 + lane;
-      const int cb = ct * kTcN + half * 64;
-      float *Crow = A + (t0 + row) + int64_t(t0 + cb) * ld;
-      const int ncol = row < nrest ? min(64, nrest - cb) : 0;
-#pragma unroll
-      for (int c0 = 0; c0 < 64; c0 += 32) {
-        uint32_t v[32];
-        const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(half * 64 + c0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
-              "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-              "=r"(v[30]), "=r"(v[31])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (c0 + j < ncol) Crow[int64_t(c0 + j) * ld] -= __uint_as_float(v[j]);
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();  // TMEM is read before the next tile's MMAs
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      continue;
-    }
-    const bool w2 = wait_phase(smem_u32(&bar_c), ph_c);
-    ok = __syncthreads_and(w2 ? 1 : 0) != 0;
-    if (!ok) {
-      c_pending = !w2;
-      break;
-    }
-    ph_c ^= 1u;
-    c_pending = false;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const int row = q4 * 32 + lane;
-#pragma unroll
-    for (int c0 = 0; c0 < 64; c0 += 32) {
-      uint32_t v[32];
-      const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(half * 64 + c0);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-          "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      float *col = sC + (half * 64 + c0) * kTcM + row;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) col[j * kTcM] -= __uint_as_float(v[j]);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (tid == 0) {
-      tma_store_2d(tmap, x, y, smem_u32(sC));
-      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-    }
-  }
-  if (!ok) {
-    if (tid == 0) atomicOr(err, 4);
-    if (mma_pending) wait_phase(smem_u32(&bar_mma), ph_mma);
-    if (c_pending) wait_phase(smem_u32(&bar_c), ph_c);
-  }
-  if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(kTcN)));
-}
-
 // ---- packed operands and the warp-specialised block-end update ----
 constexpr int kPkK = 16;                          // K values per packed chunk
 constexpr int kPkTile = kTcM * kPkK;              // floats per hi (or lo) array: 2048 = 8 KB
@@ -1026,26 +824,6 @@ cudaError_t launch_gemm_tc_inner(const FrontDev *fr, int j0, int kb, int nfront,
   const int splits = wave_splits(rt, ct, nfront, std::max(sm_budget, 1), 0.3);
   dim3 g(splits, rt, nfront);
   k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, 0, ct, 0, kb);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gemm_tc_outer(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
-                                 cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gemm_tc_outer, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gemm_tc_smem()));
-    attr = true;
-  }
-  if (maps == nullptr) return cudaErrorInvalidValue;
-  const int rest = max_f - j0 - 1;
-  if (rest <= 0) return cudaSuccess;
-  const int rt = (rest + kTcM - 1) / kTcM;
-  const int ct = std::min((rest + kTcN - 1) / kTcN, tile_hi) - tile_lo;
-  if (ct <= 0) return cudaSuccess;
-  // per tile: kb / 64 chunks of staging and MMAs; the lead is small
-  const int splits = wave_splits(rt, ct, nfront, std::max(sm_budget, 1), 0.05);
-  dim3 g(splits, rt, nfront);
-  k_gemm_tc_outer<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi, maps);
   return cudaGetLastError();
 }
 

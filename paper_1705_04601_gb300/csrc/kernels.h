@@ -129,13 +129,11 @@ cudaError_t launch_gemm_tc(const FrontDev *fr, int j0, int nfront, int max_f, fl
 cudaError_t launch_gemm_tc_inner(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
                                  cudaStream_t s, int sm_budget);
 // block end at J = j0: C[t0:f, t0:f] -= L21 U12 with K = min(kb, s - j0)
-// (t0 = j0 + K), over the 128-column tiles [tile_lo, tile_hi); needs `maps`.
-cudaError_t launch_gemm_tc_outer(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
-                                 cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps);
-// the same update from packed operands: k_pack_a writes L21 (the rows after
-// the block, K = the block's columns) into apack, k_pack_b the U12 columns of
-// tiles [ct_lo, ct_hi) of the trailing block into bpack; the warp-specialised
-// GEMM then streams both with bulk copies.
+// (t0 = j0 + K), over the 128-column tiles [tile_lo, tile_hi), from packed
+// operands: k_pack_a writes L21 (the rows after the block, K = the block's
+// columns) into apack, k_pack_b the U12 columns of tiles [ct_lo, ct_hi) of the
+// trailing block into bpack; the warp-specialised GEMM streams both with bulk
+// copies.
 cudaError_t launch_pack_a(const FrontDev *fr, int j0, int kb, int nfront, int max_f, const float *fronts, float *apack,
                           cudaStream_t s);
 cudaError_t launch_pack_b(const FrontDev *fr, int j0, int kb, int nfront, int max_f, const float *fronts, float *bpack,
