@@ -9,10 +9,13 @@ level schedule, block pattern of S, symbolic factorization) runs once per
 structure, before the timed steps, and is reported as ``analysis_ms``.  Two
 paths:
 
-* mixed (the headline): FP32 factorization of S, then restarted GMRES (or
-  iterative refinement, --solver ir) on the FP64 H^2 product, preconditioned
-  by the factored S, until max_k ||b_k - A x_k|| / ||b_k|| <= 1e-10;
-* fp64: FP64 factorization of S and one direct solve (reported beside it).
+* mixed (the headline): S from FP32 sandwich products (the Householder
+  completions stay FP64; --sparsify-prec fp64 keeps them all FP64), FP32
+  factorization of S, then restarted GMRES (or iterative refinement,
+  --solver ir) on the FP64 H^2 product, preconditioned by FP32 U^T, S^-1 and
+  V, until max_k ||b_k - A x_k|| / ||b_k|| <= 1e-10;
+* fp64: FP64 sparsification and factorization of S, refinement on the FP64
+  H^2 residual to 1e-10 (reported beside it).
 
 Inputs are resident in HBM when the timed region starts (the close blocks are
 443 MB, larger than the 129 MB L2, so no flush is needed); ``e2e`` repeats the
