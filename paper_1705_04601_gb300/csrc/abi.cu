@@ -1258,6 +1258,11 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   h->prof.stream = h->stream;
   try {
+    if (h->graph_exec != nullptr && prec != h->last_prec) {
+      // the captured refactorization is of the other precision
+      ck(cudaGraphExecDestroy(h->graph_exec));
+      h->graph_exec = nullptr;
+    }
     factor_prepare(h, prec);
     h->prec = -1;
     factor_launch(h, prec);

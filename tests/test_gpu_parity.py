@@ -484,4 +484,14 @@ def test_refactor_replays_on_new_numbers(name, prec, flags):
         err = np.linalg.norm(xg - xd / scale) / np.linalg.norm(xd / scale)
         print("refactor (%s, %s, x%g): rel err %.2e" % (name, prec, scale, err))
         assert err <= bound
+    if prec == "fp32":
+        # a factorization in the other precision replaces the captured one
+        H.h2sp_factor(hd, H.H2SP_FP64)
+        H.h2sp_refactor(hd)
+        assert H.h2sp_query(hd)["factor_prec"] == H.H2SP_FP64
+        info = H.h2sp_solve(hd, bt, xt, mode=H.H2SP_GMRES, tol=1e-10, maxit=60, restart=20)
+        assert info.status == H.H2SP_OK and info.rel_residual <= 1e-10
+        torch.cuda.synchronize()
+        err = np.linalg.norm(host(xt) - xd / 4.0) / np.linalg.norm(xd / 4.0)
+        assert err <= 1e-7
     hd.close()
