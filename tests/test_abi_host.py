@@ -228,3 +228,14 @@ def test_analysis_handle_reports_no_sparsify_precision():
     st = H.h2sp_query(an)
     assert st["sparsify_prec"] == -1 and st["factor_prec"] == -1
     an.close()
+
+
+def test_refactor_needs_a_factorized_handle():
+    """h2sp_refactor on a null handle is EINVAL; on an analysis-only handle
+    (no device buffers, no factorization to repeat) it is ESTATE, decided on
+    the host before any CUDA call."""
+    assert H.lib().h2sp_refactor(None, None) == H.H2SP_EINVAL
+    h = _make("log1k")
+    an = H.h2sp_analyze(H.H2Input(h, device=None))
+    assert H.lib().h2sp_refactor(an.ptr, None) == H.H2SP_ESTATE
+    an.close()
