@@ -223,6 +223,28 @@ def solve_S(fa: Factors, c: np.ndarray) -> np.ndarray:
     return y.reshape(np.shape(c))
 
 
+def logdet(fa: Factors) -> tuple[float, int]:
+    """log|det A| and the sign of det S of one system, from the block LU of S.
+
+    §5.3 proposes the factorization of the sparse S as the way to the
+    determinant of the dense matrix (the use HODLR factorizations are put to).
+    U and V are orthogonal (Eq. main_uv), so A = U S V^T (Eq. main_fact) has
+    |det A| = |det S|; with symmetric bases (V = U) also det A = det U^2 det S
+    = det S.  Block elimination factors det S into the determinants of the
+    supernodes' pivot blocks after the Schur updates from the supernodes
+    eliminated before them, and getrf's F11 = P L U gives
+    det F11 = (-1)^(number of interchanges) * prod_j u_jj.  The logarithms are
+    summed in FP64 over all pivot blocks.
+    """
+    total = 0.0
+    flips = 0
+    for lu, piv in fa.lu:
+        d = np.diag(lu)
+        total += float(np.sum(np.log(np.abs(d))))
+        flips += int(np.count_nonzero(d < 0.0)) + int(np.count_nonzero(piv != np.arange(piv.size)))
+    return total, (-1 if flips % 2 else 1)
+
+
 def solve(h, sp: Sparsified, fa: Factors, b: np.ndarray) -> np.ndarray:
     """x = V S^{-1} U^T b (Eq. sp0: S y = U^T b, x = V y)."""
     from .sparsify import apply_N, apply_T

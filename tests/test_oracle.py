@@ -14,7 +14,9 @@ at least one of them:
 * the block LU solve agrees with dense LAPACK solves of S and of A;
 * the symbolic elimination agrees with brute-force boolean elimination;
 * the number of nonzeros per row of S stays bounded as N grows (§5.1);
-* IR / GMRES with the factored S reach 1e-10 (§5.5).
+* IR / GMRES with the factored S reach 1e-10 (§5.5);
+* log|det A| from the pivots of S equals LAPACK's slogdet of the dense A and
+  of the dense S, with the sign of det S (§5.3).
 """
 import numpy as np
 import pytest
@@ -290,6 +292,46 @@ def test_singular_pivot_block_is_reported():
 # --------------------------------------------------------------------------
 # iterative solves (§5.5)
 # --------------------------------------------------------------------------
+
+
+# --------------------------------------------------------------------------
+# log-determinant from the block LU (§5.3)
+# --------------------------------------------------------------------------
+
+_LOGDET_CASES = ["log1k", "log4k", "skew1k", "inv3d", "small", "tiny", "gauss1k"]
+
+
+@pytest.mark.parametrize("name", _LOGDET_CASES)
+def test_logdet_matches_dense_slogdet(name):
+    """|det A| = |det S| since U and V are orthogonal; det A = det S when the
+    bases are symmetric (V = U).  Both dense determinants come from LAPACK."""
+    h, b, sp, A = case(name)
+    fa = ofa.factor(h, sp)
+    ld, sign = ofa.logdet(fa)
+    # rounding of the pivots scales with the sum of the magnitudes of the terms
+    terms = sum(float(np.sum(np.abs(np.log(np.abs(np.diag(lu)))))) for lu, _ in fa.lu)
+    tol = 1e-10 * max(1.0, terms)
+    sa, la = np.linalg.slogdet(A)
+    ss, ls = np.linalg.slogdet(osp.dense_S(sp))
+    assert abs(ld - la) <= tol
+    assert abs(ld - ls) <= tol
+    assert sign == int(ss)
+    if h.col_leaf_basis is None:
+        assert sign == int(sa)
+
+
+def test_logdet_cases_exercise_both_sign_terms():
+    """The cases above hold odd and even counts of interchanges and of
+    negative pivots, and both signs of det S, so dropping either sign term of
+    the oracle flips the sign of at least one case."""
+    swaps, negs, signs = set(), set(), set()
+    for name in _LOGDET_CASES:
+        h, b, sp, A = case(name)
+        fa = ofa.factor(h, sp)
+        swaps.add(sum(int(np.count_nonzero(p != np.arange(p.size))) for _, p in fa.lu) % 2)
+        negs.add(sum(int(np.count_nonzero(np.diag(lu) < 0.0)) for lu, _ in fa.lu) % 2)
+        signs.add(ofa.logdet(fa)[1])
+    assert swaps == {0, 1} and negs == {0, 1} and signs == {-1, 1}
 
 
 def test_refinement_and_gmres_reach_1e10():
