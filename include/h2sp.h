@@ -168,6 +168,7 @@ typedef struct {
   int32_t factor_prec;            /* h2sp_prec of the current factors, -1 if none */
   double plan_seconds;            /* host time spent planning in the last h2sp_sparsify */
   int32_t sparsify_prec;          /* h2sp_prec of S (U and V are always FP64); -1 for an analysis-only handle */
+  int32_t nsys;                   /* independent systems (roots at depth 0) */
 } h2sp_stats;
 
 /*
@@ -254,6 +255,24 @@ int h2sp_refactor(h2sp_handle *h, h2sp_stream stream);
  */
 int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *opts, int32_t nrhs, const double *b, int64_t ldb,
                double *x, int64_t ldx, h2sp_solve_info *info, h2sp_stream stream);
+
+/*
+ * h2sp_logdet -- log|det A| of every independent system from the current
+ * factors of S.  §5.3 proposes the factorization of the sparse S as a way to
+ * the determinant of the dense matrix: U and V are orthogonal (Eq. main_uv),
+ * so |det A| = |det S|, and block elimination makes det S the product over
+ * the supernodes of det F11 = (-1)^(row interchanges) * prod_j u_jj of their
+ * pivot blocks.  logabsdet (host, nsys doubles, nsys from h2sp_query) gets
+ * the sums of log|u_jj|, accumulated in FP64 in a fixed order; sign (host,
+ * nsys int32, may be NULL) gets the sign of det S, +1 or -1, which is also
+ * the sign of det A when the column bases are NULL (V = U, so det A =
+ * det(U)^2 det S); with separate column bases det A = det U det V det S and
+ * det U, det V (each +1 or -1) are not computed.  The value is that of the
+ * factored S in the factors' precision: with H2SP_FP32 factors it carries
+ * the FP32 rounding of the pivots.  Needs h2sp_factor (H2SP_ESTATE
+ * otherwise).  Synchronises the stream.
+ */
+int h2sp_logdet(h2sp_handle *h, double *logabsdet, int32_t *sign, h2sp_stream stream);
 
 /*
  * h2sp_apply -- out = op(in) for one of the operators above; device arrays,

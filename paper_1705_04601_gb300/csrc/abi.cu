@@ -190,6 +190,10 @@ struct h2sp_handle {
   std::vector<int> chain_fwd_off, chain_fwd_n, chain_bwd_off, chain_bwd_n;
   int *chain_tickets = nullptr, *chain_flags = nullptr, *serr = nullptr;
   int chain_epoch = 0;
+  // log-determinant: fronts of each independent system (CSR) and per-front / per-system sums
+  int32_t *ld_sys_ptr = nullptr, *ld_sys_front = nullptr, *ld_sign = nullptr;
+  int *ld_flips = nullptr;
+  double *ld_lsum = nullptr, *ld_out = nullptr;
   void release() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
     graph_exec = nullptr;
@@ -1461,6 +1465,54 @@ int h2sp_export_S(h2sp_handle *h, int64_t *node_size, int64_t *brow_ptr, int32_t
   return H2SP_OK;
 }
 
+int h2sp_logdet(h2sp_handle *h, double *logabsdet, int32_t *sign, h2sp_stream stream) {
+  if (!h || !logabsdet) return H2SP_EINVAL;
+  if (!h->device_ready || h->prec < 0) return H2SP_ESTATE;
+  const Plan &p = (*h->plan_ptr);
+  const int nsys = p.level_ptr[1];
+  const int nfront = int(p.fronts.size());
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->prof.stream = h->stream;
+  try {
+    if (h->ld_sys_ptr == nullptr) {
+      // system of a front = root of its supernode's closure cluster
+      std::vector<int32_t> ptr(static_cast<size_t>(nsys) + 1, 0), fronts(static_cast<size_t>(nfront));
+      std::vector<int32_t> sys(static_cast<size_t>(nfront));
+      for (int k = 0; k < nfront; ++k) {
+        sys[size_t(k)] = p.root[p.closure[p.order[p.sn_ptr[k]]]];
+        ptr[size_t(sys[size_t(k)]) + 1]++;
+      }
+      for (int w = 0; w < nsys; ++w) ptr[size_t(w) + 1] += ptr[size_t(w)];
+      std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+      for (int k = 0; k < nfront; ++k) fronts[size_t(fill[size_t(sys[size_t(k)])]++)] = k;
+      h->ld_sys_front = h->upload(fronts);
+      h->ld_lsum = h->alloc<double>(size_t(nfront));
+      h->ld_flips = h->alloc<int>(size_t(nfront));
+      h->ld_out = h->alloc<double>(size_t(nsys));
+      h->ld_sign = h->alloc<int32_t>(size_t(nsys));
+      h->ld_sys_ptr = h->upload(ptr);  // last: marks the buffers above as ready
+    }
+    if (h->prec == H2SP_FP64)
+      ck(launch_logdet<double>(h->fr, nfront, static_cast<const double *>(h->fronts), h->piv, h->ld_sys_ptr,
+                               h->ld_sys_front, nsys, h->ld_lsum, h->ld_flips, h->ld_out, h->ld_sign, h->stream,
+                               &h->prof));
+    else
+      ck(launch_logdet<float>(h->fr, nfront, static_cast<const float *>(h->fronts), h->piv, h->ld_sys_ptr,
+                              h->ld_sys_front, nsys, h->ld_lsum, h->ld_flips, h->ld_out, h->ld_sign, h->stream,
+                              &h->prof));
+    std::vector<double> l(static_cast<size_t>(nsys));
+    std::vector<int32_t> g(static_cast<size_t>(nsys));
+    ck(cudaMemcpyAsync(l.data(), h->ld_out, sizeof(double) * size_t(nsys), cudaMemcpyDeviceToHost, h->stream));
+    ck(cudaMemcpyAsync(g.data(), h->ld_sign, sizeof(int32_t) * size_t(nsys), cudaMemcpyDeviceToHost, h->stream));
+    ck(cudaStreamSynchronize(h->stream));
+    std::copy(l.begin(), l.end(), logabsdet);
+    if (sign) std::copy(g.begin(), g.end(), sign);
+  } catch (const CudaFail &f) {
+    return status_of(f.e);
+  }
+  return H2SP_OK;
+}
+
 int h2sp_export_Q(h2sp_handle *h, int32_t cluster, int32_t col, int64_t *m, double *q, h2sp_stream stream) {
   if (!h || !m) return H2SP_EINVAL;
   const Plan &p = (*h->plan_ptr);
@@ -1518,6 +1570,7 @@ int h2sp_query(const h2sp_handle *h, h2sp_stats *st) {
   st->factor_prec = h->prec;
   st->sparsify_prec = h->device_ready ? h->sp_prec : -1;
   st->plan_seconds = h->plan_seconds;
+  st->nsys = p.level_ptr[1];
   return H2SP_OK;
 }
 

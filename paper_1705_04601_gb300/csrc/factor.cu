@@ -2031,6 +2031,87 @@ cudaError_t launch_invert_diag(const FrontDev *fr, int nfront, int max_s, const 
   return cudaGetLastError();
 }
 
+constexpr int kLogdetThreads = 256;
+
+// One CTA per front: sum of log|u_jj| over the pivot block (the diagonal of
+// U11 left in place by the LU) and the parity of the block's interchanges
+// (piv[j] != j) and negative pivots; det F11 = (-1)^interchanges prod u_jj.
+template <typename T>
+__global__ void __launch_bounds__(kLogdetThreads) k_logdet_front(const FrontDev *__restrict__ fr,
+                                                                 const T *__restrict__ fronts,
+                                                                 const int32_t *__restrict__ piv,
+                                                                 double *__restrict__ lsum, int *__restrict__ flips) {
+  const FrontDev F = fr[blockIdx.x];
+  double acc = 0.0;
+  int odd = 0;
+  for (int j = threadIdx.x; j < F.s; j += kLogdetThreads) {
+    const double u = double(fronts[F.off + int64_t(j) * F.ld + j]);
+    acc += log(fabs(u));
+    odd ^= int(u < 0.0) ^ int(piv[F.piv_off + j] != j);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    odd ^= __shfl_xor_sync(0xffffffffu, odd, o);
+  }
+  __shared__ double sa[kLogdetThreads / 32];
+  __shared__ int so[kLogdetThreads / 32];
+  if ((threadIdx.x & 31) == 0) {
+    sa[threadIdx.x >> 5] = acc;
+    so[threadIdx.x >> 5] = odd;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    int p = 0;
+    for (int w = 0; w < kLogdetThreads / 32; ++w) {
+      t += sa[w];
+      p ^= so[w];
+    }
+    lsum[blockIdx.x] = t;
+    flips[blockIdx.x] = p;
+  }
+}
+
+// One warp per independent system: its fronts' sums, lanes strided, then a
+// butterfly (every lane ends with the same value).
+__global__ void __launch_bounds__(kLogdetThreads) k_logdet_sys(const int32_t *__restrict__ sys_ptr,
+                                                               const int32_t *__restrict__ sys_front,
+                                                               const double *__restrict__ lsum,
+                                                               const int *__restrict__ flips, int nsys,
+                                                               double *__restrict__ out, int32_t *__restrict__ sign) {
+  const int w = blockIdx.x * (kLogdetThreads / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= nsys) return;  // uniform across the warp
+  double acc = 0.0;
+  int odd = 0;
+  for (int i = sys_ptr[w] + lane; i < sys_ptr[w + 1]; i += 32) {
+    const int f = sys_front[i];
+    acc += lsum[f];
+    odd ^= flips[f];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    odd ^= __shfl_xor_sync(0xffffffffu, odd, o);
+  }
+  if (lane == 0) {
+    out[w] = acc;
+    sign[w] = odd ? -1 : 1;
+  }
+}
+
+template <typename T>
+cudaError_t launch_logdet(const FrontDev *fr, int nfront, const T *fronts, const int32_t *piv, const int32_t *sys_ptr,
+                          const int32_t *sys_front, int nsys, double *lsum, int *flips, double *out, int32_t *sign,
+                          cudaStream_t s, Prof *prof) {
+  if (nsys <= 0) return cudaSuccess;
+  const size_t e0 = prof->begin();
+  if (nfront > 0) k_logdet_front<T><<<nfront, kLogdetThreads, 0, s>>>(fr, fronts, piv, lsum, flips);
+  k_logdet_sys<<<cdiv(nsys, kLogdetThreads / 32), kLogdetThreads, 0, s>>>(sys_ptr, sys_front, lsum, flips, nsys, out,
+                                                                          sign);
+  prof->end(P_OTHER, nfront > 0 ? 2 : 1, e0, 0.0);
+  return cudaGetLastError();
+}
+
 template <typename T>
 size_t step_smem() {
   const size_t bytes = sizeof(T) * (kBS * kBS + 2 * kBS * kMaxRhs);
@@ -2113,6 +2194,12 @@ template cudaError_t launch_make_perm<double>(const FrontDev *, int, int, const 
 template cudaError_t launch_extend_add_impl<double>(const FrontDev *, int, int, int, const int32_t *, double *, cudaStream_t,
                                                   Prof *, double);
 template cudaError_t launch_invert_diag<double>(const FrontDev *, int, int, const double *, double *, cudaStream_t, Prof *);
+template cudaError_t launch_logdet<double>(const FrontDev *, int, const double *, const int32_t *, const int32_t *,
+                                           const int32_t *, int, double *, int *, double *, int32_t *, cudaStream_t,
+                                           Prof *);
+template cudaError_t launch_logdet<float>(const FrontDev *, int, const float *, const int32_t *, const int32_t *,
+                                          const int32_t *, int, double *, int *, double *, int32_t *, cudaStream_t,
+                                          Prof *);
 template cudaError_t launch_solve_fwd_level_impl<double>(const FrontDev *, int, int, int, int, const double *, const double *,
                                                        const int32_t *, const int32_t *, double *, int64_t, int, double *,
                                                        double *, const int64_t *, cudaStream_t, Prof *, double,

@@ -84,6 +84,15 @@ cudaError_t launch_make_perm(const FrontDev *fr, int nfront, int max_s, const in
 template <typename T>
 cudaError_t launch_invert_diag(const FrontDev *fr, int nfront, int max_s, const T *fronts, T *dinv, cudaStream_t s,
                                Prof *prof);
+// log|det| of the factored S per independent system (§5.3): per front, the sum
+// of log|u_jj| over its pivot block and the parity of its interchanges and
+// negative pivots (lsum, flips: one entry per front); then per system w the
+// sums over its fronts sys_front[sys_ptr[w] .. sys_ptr[w+1]) into out[w] and
+// sign[w] (+1 / -1).  Both sums in FP64, in a fixed order.
+template <typename T>
+cudaError_t launch_logdet(const FrontDev *fr, int nfront, const T *fronts, const int32_t *piv, const int32_t *sys_ptr,
+                          const int32_t *sys_front, int nsys, double *lsum, int *flips, double *out, int32_t *sign,
+                          cudaStream_t s, Prof *prof);
 // Work lists of the flag-synchronised sweeps (one launch per level and
 // direction): items (front, row block) of level li are items[fwd_off[li] ..
 // fwd_off[li] + fwd_n[li]) in dependency order (a supernode item covers row

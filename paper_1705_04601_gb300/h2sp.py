@@ -62,7 +62,7 @@ class Stats(ctypes.Structure):
         ("nnzb", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nsupernodes", ctypes.c_int32),
         ("nfront_levels", ctypes.c_int32), ("max_front", ctypes.c_int64), ("front_elems", ctypes.c_int64),
         ("factor_flops", ctypes.c_double), ("sparsify_flops", ctypes.c_double), ("factor_prec", ctypes.c_int32),
-        ("plan_seconds", ctypes.c_double), ("sparsify_prec", ctypes.c_int32),
+        ("plan_seconds", ctypes.c_double), ("sparsify_prec", ctypes.c_int32), ("nsys", ctypes.c_int32),
     ]
 
 
@@ -84,6 +84,7 @@ SIGNATURES = {
     "h2sp_refactor": (ctypes.c_int, [_vp, _vp]),
     "h2sp_solve": (ctypes.c_int, [_vp, ctypes.POINTER(SolveOpts), ctypes.c_int32, _vp, ctypes.c_int64, _vp,
                                   ctypes.c_int64, ctypes.POINTER(SolveInfo), _vp]),
+    "h2sp_logdet": (ctypes.c_int, [_vp, _f64p, _i32p, _vp]),
     "h2sp_apply": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int64, _vp, ctypes.c_int64,
                                   _vp]),
     "h2sp_export_S": (ctypes.c_int, [_vp, _i64p, _i64p, _i32p, _i64p, _f64p, _vp]),
@@ -275,6 +276,16 @@ def h2sp_apply(h: Handle, op: int, x, y, stream=None):
     _, ldy = _cols(y, n)
     _check(lib().h2sp_apply(h.ptr, int(op), nrhs, _vp(x.data_ptr()), ldx, _vp(y.data_ptr()), ldy, _stream(stream)),
            "h2sp_apply")
+
+
+def h2sp_logdet(h: Handle, stream=None):
+    """(log|det A|, sign of det S) per independent system: two arrays of length nsys."""
+    nsys = h2sp_query(h)["nsys"]
+    ld = np.zeros(nsys, np.float64)
+    sg = np.zeros(nsys, np.int32)
+    _check(lib().h2sp_logdet(h.ptr, _ptr(ld, ctypes.c_double), _ptr(sg, ctypes.c_int32), _stream(stream)),
+           "h2sp_logdet")
+    return ld, sg
 
 
 def h2sp_query(h: Handle) -> dict:

@@ -239,3 +239,25 @@ def test_refactor_needs_a_factorized_handle():
     an = H.h2sp_analyze(H.H2Input(h, device=None))
     assert H.lib().h2sp_refactor(an.ptr, None) == H.H2SP_ESTATE
     an.close()
+
+
+def test_logdet_needs_factors():
+    """h2sp_logdet: a null handle or output array is EINVAL; an analysis-only
+    handle has no factors (ESTATE), decided on the host before any CUDA call."""
+    d = ctypes.c_double(0.0)
+    assert H.lib().h2sp_logdet(None, ctypes.byref(d), None, None) == H.H2SP_EINVAL
+    h = _make("log1k")
+    an = H.h2sp_analyze(H.H2Input(h, device=None))
+    assert H.lib().h2sp_logdet(an.ptr, None, None, None) == H.H2SP_EINVAL
+    assert H.lib().h2sp_logdet(an.ptr, ctypes.byref(d), None, None) == H.H2SP_ESTATE
+    an.close()
+
+
+def test_query_counts_independent_systems():
+    systems, f, _ = synth.make_batched(4, 400, 1200, leaf=32, tol=1e-8)
+    an = H.h2sp_analyze(H.H2Input(f, device=None))
+    assert H.h2sp_query(an)["nsys"] == 4 == len(systems)
+    an.close()
+    an = H.h2sp_analyze(H.H2Input(_make("tiny"), device=None))
+    assert H.h2sp_query(an)["nsys"] == 1
+    an.close()

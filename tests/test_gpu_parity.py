@@ -495,3 +495,55 @@ def test_refactor_replays_on_new_numbers(name, prec, flags):
         err = np.linalg.norm(host(xt) - xd / 4.0) / np.linalg.norm(xd / 4.0)
         assert err <= 1e-7
     hd.close()
+
+
+# ---------------------------------------------------------------------------
+# log-determinant from the factors (§5.3)
+# ---------------------------------------------------------------------------
+
+
+def _logdet_terms(fa):
+    """Sum of |log|u_jj|| over the oracle's pivots: the scale the rounding of the pivots is relative to."""
+    return sum(float(np.sum(np.abs(np.log(np.abs(np.diag(lu)))))) for lu, _ in fa.lu)
+
+
+@pytest.mark.parametrize("name", ["log1k", "skew1k", "inv3d", "tiny", "ragged"])
+def test_logdet_matches_oracle(name):
+    """log|det A| and sign(det S) from the GPU factors equal the oracle's.
+    Both are invariants of S, so they agree whatever pivots each side chose.
+    FP64 factors: within 1e-10 of the sum of the terms' magnitudes.  FP32
+    factors: within 1e-5 of it; a dense FP32 getrf of the same S (LAPACK)
+    stays within 4e-7 on these cases."""
+    h, b, sp, hd = sparsified(name)
+    fa = ofa.factor(h, sp)
+    lo, so = ofa.logdet(fa)
+    terms = max(1.0, _logdet_terms(fa))
+    H.h2sp_factor(hd, H.H2SP_FP64)
+    ld, sg = H.h2sp_logdet(hd)
+    print("logdet %s: oracle %.12g, fp64 diff %.2e" % (name, lo, ld[0] - lo))
+    assert ld.shape == (1,) and sg.shape == (1,)
+    assert abs(ld[0] - lo) <= 1e-10 * terms
+    assert sg[0] == so
+    H.h2sp_factor(hd, H.H2SP_FP32)
+    ld32, sg32 = H.h2sp_logdet(hd)
+    print("logdet %s: fp32 diff %.2e" % (name, ld32[0] - lo))
+    assert abs(ld32[0] - lo) <= 1e-5 * terms
+    assert sg32[0] == so
+    hd.close()
+
+
+def test_logdet_per_system_of_a_forest():
+    """Batched form: one value per independent system, each equal to the
+    oracle's for that system alone."""
+    systems, f, b = synth.make_batched(5, 500, 2500, leaf=32, tol=1e-8, nrhs=1)
+    hd = H.h2sp_sparsify(H.H2Input(f))
+    H.h2sp_factor(hd, H.H2SP_FP64)
+    ld, sg = H.h2sp_logdet(hd)
+    assert ld.shape == (len(systems),)
+    for w, s in enumerate(systems):
+        sp = osp.sparsify(s)
+        fa = ofa.factor(s, sp)
+        lo, so = ofa.logdet(fa)
+        assert abs(ld[w] - lo) <= 1e-10 * max(1.0, _logdet_terms(fa))
+        assert sg[w] == so
+    hd.close()
