@@ -41,6 +41,9 @@ struct LevelDev {
   CItem *c = nullptr;
   XItem *x = nullptr;
   int nq = 0, nw = 0, nc = 0, nx = 0;
+  int nq_small = 0, nx_small = 0;  // small items (blocks <= kMaxBlock) lead q / qc and x
+  int max_m = 0;                   // largest block of the level (Householder and apply items)
+  int max_xr = 0, max_xc = 0;      // largest rows / cols of the level's large transform items
   void **src_base = nullptr, **dst_base = nullptr;  // device arrays of 4 pointers
   double *W = nullptr, *Wc = nullptr;
   ApItem *ap = nullptr;  // applies of this level's Q blocks
@@ -62,7 +65,7 @@ struct StructureDev {
   int device = -1;
   std::vector<void *> allocs;
   std::vector<LevelDev> lv;  // item arrays only
-  std::vector<double> x_flops;
+  std::vector<double> x_flops, x_flops_large;  // transform flops of each level's small / large items
   int max_rank = 1;
   int64_t max_pack_tiles = 0;  // largest sum over a level's fronts of ceil(f / 128)
   int64_t max_width = 0;
@@ -160,7 +163,7 @@ struct h2sp_handle {
   double plan_seconds = 0.0;
   bool device_ready = false;
   Prof prof;
-  std::vector<double> x_flops;  // algorithmic flops of each level's transform launch
+  std::vector<double> x_flops, x_flops_large;  // algorithmic flops of each level's transform launches
   double near_bytes = 0.0;      // bytes of the close blocks (Definition 4.8)
   double mv_flops_per_rhs = 0.0;  // FP64 flops of one H^2 product per right-hand side
 
@@ -292,7 +295,7 @@ void apply_T_impl(h2sp_handle *h, const T *Qb, const T *in, int64_t ldin, T *out
   T *bufs[2] = {bufA, bufB};
   for (int l = 0; l < p.lstop; ++l) {
     T *xn = bufs[l & 1];
-    ck(launch_apply_qt(h->lv[l].ap, h->lv[l].nap, Qb, x, ldx, out, ldout, xn, ldw, nrhs, s));
+    ck(launch_apply_qt(h->lv[l].ap, h->lv[l].nap, Qb, x, ldx, out, ldout, xn, ldw, nrhs, s, h->lv[l].max_m));
     x = xn;
     ldx = ldw;
   }
@@ -324,7 +327,7 @@ void apply_N_impl(h2sp_handle *h, const T *Qb, const T *in, int64_t ldin, T *out
   for (int l = p.lstop - 1; l >= 0; --l) {
     T *x = (l == 0) ? out : bufs[l & 1];
     const int64_t ldx = (l == 0) ? ldout : ldw;
-    ck(launch_apply_q(h->lv[l].ap, h->lv[l].nap, Qb, xn, ldw, in, ldin, x, ldx, nrhs, s));
+    ck(launch_apply_q(h->lv[l].ap, h->lv[l].nap, Qb, xn, ldw, in, ldin, x, ldx, nrhs, s, h->lv[l].max_m));
     xn = x;
   }
 }
@@ -698,10 +701,24 @@ std::shared_ptr<StructureDev> build_structure(const Plan &p) {
     d.nc = int(w.c.size());
     d.x = sd->upload(w.x);
     d.nx = int(w.x.size());
-    double xf = 0.0;
-    for (const XItem &it : w.x)
-      xf += (it.qR >= 0 ? 2.0 * it.rows * it.cols * it.cols : 0.0) + (it.qL >= 0 ? 2.0 * it.rows * it.rows * it.cols : 0.0);
+    d.nq_small = w.nq_small;
+    d.nx_small = w.nx_small;
+    d.max_m = w.max_m;
+    double xf = 0.0, xfl = 0.0;
+    for (size_t i = 0; i < w.x.size(); ++i) {
+      const XItem &it = w.x[i];
+      const double f =
+          (it.qR >= 0 ? 2.0 * it.rows * it.cols * it.cols : 0.0) + (it.qL >= 0 ? 2.0 * it.rows * it.rows * it.cols : 0.0);
+      if (int(i) < w.nx_small) {
+        xf += f;
+      } else {
+        xfl += f;
+        d.max_xr = std::max(d.max_xr, it.rows);
+        d.max_xc = std::max(d.max_xc, it.cols);
+      }
+    }
     sd->x_flops.push_back(xf);
+    sd->x_flops_large.push_back(xfl);
     if (!p.sym) {
       d.qc = sd->upload(w.qc);
       d.wc = sd->upload(w.wc);
@@ -789,6 +806,10 @@ std::shared_ptr<StructureDev> build_structure(const Plan &p) {
       for (int i = 0; i < p.nleaf; ++i) ol[i] = i;
       for (int i = 0; i < p.ncl; ++i) oc[i] = i;
       std::stable_sort(ol.begin(), ol.end(), [&](int a, int b) { return wl[a] > wl[b]; });
+      // leaves above 64 points last (their own launch)
+      auto large = std::stable_partition(ol.begin(), ol.end(),
+                                         [&](int lf) { return p.h_size[p.level_ptr[p.D] + lf] <= kMaxBlock; });
+      g.nleaf_large = int32_t(ol.end() - large);
       std::stable_sort(oc.begin(), oc.end(), [&](int a, int b) { return wc[a] > wc[b]; });
       g.leaf_order = sd->upload(ol);
       g.couple_order = sd->upload(oc);
@@ -910,17 +931,25 @@ void sparsify_kernels(h2sp_handle *h, const Plan &p, const StructureDev &sd, cud
         ck(launch_stack_w(d.w, d.nw, h->Rr, h->transfer, d.W, s, &h->prof));
         if (!p.sym) ck(launch_stack_w(d.wc, d.nw, h->Rrc, h->col_transfer, d.Wc, s, &h->prof));
       }
-      ck(launch_householder(d.q, d.nq, h->leaf_basis, d.W, h->Q, h->Rr, std::max(w.max_m, 1), std::max(w.max_k, 1),
-                            s, &h->prof));
-      if (!p.sym)
-        ck(launch_householder(d.qc, d.nq, h->col_leaf_basis, d.Wc, h->Qc, h->Rrc, std::max(w.max_m, 1),
-                              std::max(w.max_k, 1), s, &h->prof));
+      // small items (m <= kMaxBlock) first, in shared memory; then the large ones
+      const int ms = std::max(std::min(w.max_m, kMaxBlock), 1), mk = std::max(w.max_k, 1);
+      const int nl = d.nq - d.nq_small;
+      ck(launch_householder(d.q, d.nq_small, h->leaf_basis, d.W, h->Q, h->Rr, ms, mk, s, &h->prof));
+      ck(launch_householder_large(d.q + d.nq_small, nl, h->leaf_basis, d.W, h->Q, h->Rr, w.max_m, mk, s, &h->prof));
+      if (!p.sym) {
+        ck(launch_householder(d.qc, d.nq_small, h->col_leaf_basis, d.Wc, h->Qc, h->Rrc, ms, mk, s, &h->prof));
+        ck(launch_householder_large(d.qc + d.nq_small, nl, h->col_leaf_basis, d.Wc, h->Qc, h->Rrc, w.max_m, mk, s,
+                                    &h->prof));
+      }
       ck(launch_coupling<W>(d.c, d.nc, h->Rr, h->Rrc, h->coupling, reinterpret_cast<W *const *>(d.dst_base),
                             sd.max_rank, s, &h->prof));
     }
-    ck(launch_transform<W>(d.x, d.nx, const_cast<const void *const *>(d.src_base), h->Q, h->Qc,
+    ck(launch_transform<W>(d.x, d.nx_small, const_cast<const void *const *>(d.src_base), h->Q, h->Qc,
                            reinterpret_cast<W *const *>(d.dst_base), s, &h->prof,
                            l < int(h->x_flops.size()) ? h->x_flops[l] : 0.0));
+    ck(launch_transform_large<W>(d.x + d.nx_small, d.nx - d.nx_small, const_cast<const void *const *>(d.src_base),
+                                 h->Q, h->Qc, reinterpret_cast<W *const *>(d.dst_base), d.max_xr, d.max_xc, s,
+                                 &h->prof, l < int(h->x_flops_large.size()) ? h->x_flops_large[l] : 0.0));
   }
 }
 
@@ -992,6 +1021,7 @@ int sparsify_numeric(h2sp_handle *h, const h2sp_h2_desc *desc, int32_t sp_prec, 
     // ---- per-level tables and the sparsification kernels, level by level ----
     h->lv = sd.lv;
     h->x_flops = sd.x_flops;
+    h->x_flops_large = sd.x_flops_large;
     sparsify_setup_levels(h, p);
     sparsify_launch(h);
     // ---- structure views for the applies, products, factor and solves ----

@@ -81,6 +81,78 @@ __global__ void __launch_bounds__(64) k_apply_q(const ApItem *__restrict__ items
   }
 }
 
+// k_apply_qt / k_apply_q for levels whose blocks exceed kMaxBlock rows: the
+// input slab (m x nrhs, leading dimension ms = the level's largest m) sits in
+// dynamic shared memory; each thread computes rows i, i + 128, ...
+template <typename T>
+__global__ void __launch_bounds__(128) k_apply_qt_large(const ApItem *__restrict__ items, const T *__restrict__ Q,
+                                                        const T *__restrict__ x, int64_t ldx, T *__restrict__ ys,
+                                                        int64_t ldys, T *__restrict__ xn, int64_t ldxn, int nrhs,
+                                                        int ms) {
+  const ApItem it = items[blockIdx.x];
+  extern __shared__ __align__(16) unsigned char smraw_a[];
+  T *sx = reinterpret_cast<T *>(smraw_a);
+  const int m = it.m;
+  for (int e = threadIdx.x; e < m * nrhs; e += blockDim.x) {
+    const int j = e % m, r = e / m;
+    sx[j + r * ms] = x[it.xin + j + r * ldx];
+  }
+  __syncthreads();
+  const T *Qt = Q + it.q;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    T acc[kRhs];
+#pragma unroll
+    for (int r = 0; r < kRhs; ++r) acc[r] = T(0);
+    for (int j = 0; j < m; ++j) {
+      const T q = Qt[j + int64_t(i) * m];
+#pragma unroll
+      for (int r = 0; r < kRhs; ++r)
+        if (r < nrhs) acc[r] += q * sx[j + r * ms];
+    }
+    if (i < it.kp) {
+      if (it.xout >= 0)
+        for (int r = 0; r < nrhs; ++r) xn[it.xout + i + r * ldxn] = acc[r];
+    } else {
+      for (int r = 0; r < nrhs; ++r) ys[it.yout + (i - it.kp) + r * ldys] = acc[r];
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_apply_q_large(const ApItem *__restrict__ items, const T *__restrict__ Q,
+                                                       const T *__restrict__ xn, int64_t ldxn,
+                                                       const T *__restrict__ ys, int64_t ldys, T *__restrict__ x,
+                                                       int64_t ldx, int nrhs, int ms) {
+  const ApItem it = items[blockIdx.x];
+  extern __shared__ __align__(16) unsigned char smraw_a[];
+  T *sz = reinterpret_cast<T *>(smraw_a);
+  const int m = it.m;
+  for (int e = threadIdx.x; e < m * nrhs; e += blockDim.x) {
+    const int j = e % m, r = e / m;
+    T v = T(0);
+    if (j < it.kp) {
+      if (it.xout >= 0) v = xn[it.xout + j + r * ldxn];
+    } else {
+      v = ys[it.yout + (j - it.kp) + r * ldys];
+    }
+    sz[j + r * ms] = v;
+  }
+  __syncthreads();
+  const T *Qt = Q + it.q;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    T acc[kRhs];
+#pragma unroll
+    for (int r = 0; r < kRhs; ++r) acc[r] = T(0);
+    for (int j = 0; j < m; ++j) {
+      const T q = Qt[i + int64_t(j) * m];
+#pragma unroll
+      for (int r = 0; r < kRhs; ++r)
+        if (r < nrhs) acc[r] += q * sz[j + r * ms];
+    }
+    for (int r = 0; r < nrhs; ++r) x[it.xin + i + r * ldx] = acc[r];
+  }
+}
+
 template <typename T>
 __global__ void k_copy_rows(const int64_t *__restrict__ src_row, const int64_t *__restrict__ dst_row,
                             const int32_t *__restrict__ len, const T *__restrict__ src, int64_t lds,
@@ -197,6 +269,39 @@ __global__ void __launch_bounds__(kMvThreads, 10) k_h2_leaf_out(H2Dev h, const d
     case 2: leaf_out_body<2>(h, lf, x, ldx, yh, ldh, y, ldy, nrhs); break;
     default: leaf_out_body<1>(h, lf, x, ldx, yh, ldh, y, ldy, nrhs); break;
   }
+}
+
+// leaf_out_body for leaves of more than kMvThreads points: rows r0 + tid, all
+// right-hand sides per thread
+__device__ __forceinline__ void leaf_out_rows(const H2Dev &h, int lf, int r0, const double *__restrict__ x,
+                                              int64_t ldx, const double *__restrict__ yh, int64_t ldh,
+                                              double *__restrict__ y, int64_t ldy, int nrhs) {
+  const int t = h.leaf0 + lf;
+  const int n = int(h.size[t]), k = h.rank[t];
+  const int i = r0 + int(threadIdx.x);
+  if (i >= n) return;
+  double acc[kRhs];
+#pragma unroll
+  for (int q = 0; q < kRhs; ++q) acc[q] = 0.0;
+  mv_accumulate<1>(acc, h.leaf_basis + h.leaf_basis_off[lf], n, i, k, yh + h.xh_off[t], ldh, 0, nrhs);
+  for (int64_t z = h.near_ptr[lf]; z < h.near_ptr[lf + 1]; ++z) {
+    const int s = h.near_col[z];
+    mv_accumulate<1>(acc, h.near_block + h.near_off[z], n, i, int(h.size[s]), x + h.begin[s], ldx, 0, nrhs);
+  }
+  const int64_t b0 = h.begin[t];
+#pragma unroll
+  for (int q = 0; q < kRhs; ++q)
+    if (q < nrhs) y[b0 + i + q * ldy] = acc[q];
+}
+
+// close blocks of the leaves leaf_order[first ..]: more than kMvThreads points each
+__global__ void __launch_bounds__(kMvThreads) k_h2_leaf_out_large(H2Dev h, int first, const double *__restrict__ x,
+                                                                  int64_t ldx, const double *__restrict__ yh,
+                                                                  int64_t ldh, double *__restrict__ y, int64_t ldy,
+                                                                  int nrhs) {
+  const int lf = h.leaf_order[first + int(blockIdx.x)];
+  const int n = int(h.size[h.leaf0 + lf]);
+  for (int r0 = 0; r0 < n; r0 += kMvThreads) leaf_out_rows(h, lf, r0, x, ldx, yh, ldh, y, ldy, nrhs);
 }
 
 // y^_t = sum_{s in Far(t)} D_ts x^_s
@@ -433,8 +538,21 @@ inline unsigned grid_for(int64_t n, int per = 256) {
 
 template <typename T>
 cudaError_t launch_apply_qt(const ApItem *items, int n, const T *Q, const T *x, int64_t ldx, T *ys, int64_t ldys, T *xn,
-                            int64_t ldxn, int nrhs, cudaStream_t s) {
+                            int64_t ldxn, int nrhs, cudaStream_t s, int max_m) {
   if (n == 0) return cudaSuccess;
+  if (max_m > kMaxBlock) {
+    const size_t smem = sizeof(T) * size_t(max_m) * kRhs;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_apply_qt_large<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(sizeof(T) * kMaxLargeBlock * kRhs));
+      attr = true;
+    }
+    for (int r0 = 0; r0 < nrhs; r0 += kRhs)
+      k_apply_qt_large<T><<<n, 128, smem, s>>>(items, Q, x + r0 * ldx, ldx, ys + r0 * ldys, ldys,
+                                               xn ? xn + r0 * ldxn : nullptr, ldxn, std::min(kRhs, nrhs - r0), max_m);
+    return cudaGetLastError();
+  }
   for (int r0 = 0; r0 < nrhs; r0 += kRhs)
     k_apply_qt<T><<<n, 64, 0, s>>>(items, Q, x + r0 * ldx, ldx, ys + r0 * ldys, ldys, xn ? xn + r0 * ldxn : nullptr,
                                    ldxn, std::min(kRhs, nrhs - r0));
@@ -443,8 +561,21 @@ cudaError_t launch_apply_qt(const ApItem *items, int n, const T *Q, const T *x, 
 
 template <typename T>
 cudaError_t launch_apply_q(const ApItem *items, int n, const T *Q, const T *xn, int64_t ldxn, const T *ys, int64_t ldys,
-                           T *x, int64_t ldx, int nrhs, cudaStream_t s) {
+                           T *x, int64_t ldx, int nrhs, cudaStream_t s, int max_m) {
   if (n == 0) return cudaSuccess;
+  if (max_m > kMaxBlock) {
+    const size_t smem = sizeof(T) * size_t(max_m) * kRhs;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_apply_q_large<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(sizeof(T) * kMaxLargeBlock * kRhs));
+      attr = true;
+    }
+    for (int r0 = 0; r0 < nrhs; r0 += kRhs)
+      k_apply_q_large<T><<<n, 128, smem, s>>>(items, Q, xn ? xn + r0 * ldxn : nullptr, ldxn, ys + r0 * ldys, ldys,
+                                              x + r0 * ldx, ldx, std::min(kRhs, nrhs - r0), max_m);
+    return cudaGetLastError();
+  }
   for (int r0 = 0; r0 < nrhs; r0 += kRhs)
     k_apply_q<T><<<n, 64, 0, s>>>(items, Q, xn ? xn + r0 * ldxn : nullptr, ldxn, ys + r0 * ldys, ldys, x + r0 * ldx,
                                   ldx, std::min(kRhs, nrhs - r0));
@@ -461,9 +592,9 @@ cudaError_t launch_copy_rows(const int64_t *src_row, const int64_t *dst_row, con
 
 #define H2SP_APPLY_INSTANTIATE(T)                                                                                      \
   template cudaError_t launch_apply_qt<T>(const ApItem *, int, const T *, const T *, int64_t, T *, int64_t, T *,       \
-                                          int64_t, int, cudaStream_t);                                                 \
+                                          int64_t, int, cudaStream_t, int);                                            \
   template cudaError_t launch_apply_q<T>(const ApItem *, int, const T *, const T *, int64_t, const T *, int64_t, T *,  \
-                                         int64_t, int, cudaStream_t);                                                  \
+                                         int64_t, int, cudaStream_t, int);                                             \
   template cudaError_t launch_copy_rows<T>(const int64_t *, const int64_t *, const int32_t *, int, const T *, int64_t, \
                                            T *, int64_t, int, cudaStream_t);
 H2SP_APPLY_INSTANTIATE(double)
@@ -506,7 +637,9 @@ cudaError_t launch_h2_matvec(const H2Dev &h, const int32_t *level_ptr_host, cons
       const int lo = level_ptr_host[d], hi = level_ptr_host[d + 1];
       k_h2_down<<<hi - lo, kMvThreads, 0, s>>>(h, lo, yh, ldh, nr);
     }
-    k_h2_leaf_out<<<nleaf, kMvThreads, 0, s>>>(h, xr, ldx, yh, ldh, yr, ldy, nr);
+    const int nlarge = h.nleaf_large;
+    if (nleaf > nlarge) k_h2_leaf_out<<<nleaf - nlarge, kMvThreads, 0, s>>>(h, xr, ldx, yh, ldh, yr, ldy, nr);
+    if (nlarge > 0) k_h2_leaf_out_large<<<nlarge, kMvThreads, 0, s>>>(h, nleaf - nlarge, xr, ldx, yh, ldh, yr, ldy, nr);
   }
   return cudaGetLastError();
 }

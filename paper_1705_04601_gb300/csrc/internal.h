@@ -14,10 +14,14 @@
 
 namespace h2sp {
 
-// Largest local block (m_t) the shared-memory transform kernels accept.
+// Largest local block (m_t) of the kernels that stage whole blocks in shared
+// memory; items up to this size take them.
 constexpr int kMaxBlock = 64;
-// Largest block the Householder kernel accepts (rows) and basis rank (columns).
-constexpr int kMaxQrRows = 128;
+// Largest local block (m_t) accepted at all: larger items (3D leaves of up to
+// 128 points, upper-level blocks stacked from up to 8 sons) take the kernels
+// that stream the block from global memory.
+constexpr int kMaxLargeBlock = 384;
+// Largest basis rank (columns of a Householder item).
 constexpr int kMaxRank = 64;
 
 // Buffers a transform item reads from / writes to.
@@ -92,6 +96,9 @@ struct LevelWork {
   std::vector<XItem> x;
   int64_t w_elems = 0, wc_elems = 0;  // W buffer sizes for this level (built from level l-1)
   int max_m = 0, max_k = 0;
+  // q / qc and x are ordered small items first (all sizes <= kMaxBlock), then
+  // the large ones; these count the small ones
+  int nq_small = 0, nx_small = 0;
 };
 
 struct Plan {

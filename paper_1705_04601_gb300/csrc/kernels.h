@@ -12,6 +12,9 @@ namespace h2sp {
 // feed it) use W = double, or float for an FP32 S.
 cudaError_t launch_householder(const QItem *items, int n, const double *w_in, const double *w_buf, double *Q,
                                double *Rr, int max_m, int max_k, cudaStream_t s, Prof *prof);
+// the same for items with m > kMaxBlock (Q formed in its global output)
+cudaError_t launch_householder_large(const QItem *items, int n, const double *w_in, const double *w_buf, double *Q,
+                                     double *Rr, int max_m, int max_k, cudaStream_t s, Prof *prof);
 cudaError_t launch_stack_w(const WItem *items, int n, const double *Rr, const double *T, double *W, cudaStream_t s,
                            Prof *prof);
 template <typename W>
@@ -21,6 +24,11 @@ cudaError_t launch_coupling(const CItem *items, int n, const double *Rr, const d
 template <typename W>
 cudaError_t launch_transform(const XItem *items, int n, const void *const *src_base, const double *Qrow,
                              const double *Qcol, W *const *dst_base, cudaStream_t s, Prof *prof, double flops);
+// the same for items with rows or cols above kMaxBlock (max_rows, max_cols: their largest sizes)
+template <typename W>
+cudaError_t launch_transform_large(const XItem *items, int n, const void *const *src_base, const double *Qrow,
+                                   const double *Qcol, W *const *dst_base, int max_rows, int max_cols, cudaStream_t s,
+                                   Prof *prof, double flops);
 
 // ---- block LU of S (factor.cu), T = double or float ----
 struct FrontDev {
@@ -163,13 +171,15 @@ struct ApItem {
 };
 // out rows: non-basis -> S space (ys), basis -> next level (xn); op = Q^T.
 // T = double (the API's applies) or float (inside the FP32 preconditioner).
+// max_m: the level's largest block; above kMaxBlock the input slab is staged
+// in dynamic shared memory.
 template <typename T>
 cudaError_t launch_apply_qt(const ApItem *items, int n, const T *Q, const T *x, int64_t ldx, T *ys, int64_t ldys, T *xn,
-                            int64_t ldxn, int nrhs, cudaStream_t s);
+                            int64_t ldxn, int nrhs, cudaStream_t s, int max_m);
 // reverse: X_l(t) = Q [xn part; ys part]
 template <typename T>
 cudaError_t launch_apply_q(const ApItem *items, int n, const T *Q, const T *xn, int64_t ldxn, const T *ys, int64_t ldys,
-                           T *x, int64_t ldx, int nrhs, cudaStream_t s);
+                           T *x, int64_t ldx, int nrhs, cudaStream_t s, int max_m);
 // copy rows: dst[dst_row[i] + r] = src[src_row[i] + r] for r < len[i]
 template <typename T>
 cudaError_t launch_copy_rows(const int64_t *src_row, const int64_t *dst_row, const int32_t *len, int n, const T *src,
@@ -194,6 +204,9 @@ struct H2Dev {
   // the last wave is made of the lightest clusters
   const int32_t *leaf_order, *couple_order;
   int32_t leaf0;  // first leaf cluster
+  // leaves with more than 64 points come last in leaf_order and take the
+  // close-block kernel that loops over row groups
+  int32_t nleaf_large;
 };
 // y = A x with A of Definition 4.9 (upward pass, couplings, downward pass, close blocks);
 // xh / yh: coefficient workspaces with leading dimension ldh (>= sum of ranks), 16 columns

@@ -250,7 +250,7 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
     }
     for (int l = 0; l < std::max(lstop, 1); ++l)
       for (int t = lev_begin(l); t < lev_end(l); ++t)
-        if (p.m[t] > kMaxBlock) throw Fail{H2SP_EUNSUPPORTED, "local block above 64 rows (leaf or level size)"};
+        if (p.m[t] > kMaxLargeBlock) throw Fail{H2SP_EUNSUPPORTED, "local block above 384 rows (leaf or level size)"};
     // S nodes: non-basis parts level by level, then the top clusters
     p.node_of.assign(ncl, -1);
     for (int l = 0; l <= lstop; ++l)
@@ -782,6 +782,28 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
         p.front_level_ptr.push_back(k);
     p.front_level_ptr.push_back(nsn);
 
+    // ---------------- small items first ----------------
+    // Items whose blocks fit kMaxBlock go to the shared-memory kernels, the
+    // rest to the streaming ones: each level's list keeps the small items in
+    // front (relative order kept), the row and column completions in step.
+    for (LevelWork &w : p.lw) {
+      std::vector<size_t> qi(w.q.size());
+      for (size_t i = 0; i < qi.size(); ++i) qi[i] = i;
+      auto qsmall = std::stable_partition(qi.begin(), qi.end(), [&](size_t i) { return w.q[i].m <= kMaxBlock; });
+      w.nq_small = int(qsmall - qi.begin());
+      std::vector<QItem> q2, qc2;
+      for (size_t i : qi) {
+        q2.push_back(w.q[i]);
+        if (!w.qc.empty()) qc2.push_back(w.qc[i]);
+      }
+      w.q.swap(q2);
+      w.qc.swap(qc2);
+      auto xsmall = std::stable_partition(w.x.begin(), w.x.end(), [](const XItem &it) {
+        return it.rows <= kMaxBlock && it.cols <= kMaxBlock;
+      });
+      w.nx_small = int(xsmall - w.x.begin());
+    }
+
     // ---------------- bounds audit of every work item ----------------
     // Each item's accessed range must lie inside the internal buffer it names;
     // a failure here is a planning bug and nothing is launched.
@@ -798,8 +820,10 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
         const int64_t dsz[4] = {p.s_elems, cn, rn, pn};
         const int64_t ssz[4] = {std::numeric_limits<int64_t>::max() / 4, l < lstop ? p.c_elems[l] : 0,
                                 l < lstop ? p.rp_elems[l] : 0, l < lstop ? p.cp_elems[l] : 0};
-        for (const XItem &it : w.x) {
-          if (it.rows > kMaxBlock || it.cols > kMaxBlock || it.rows <= 0 || it.cols <= 0)
+        for (size_t i = 0; i < w.x.size(); ++i) {
+          const XItem &it = w.x[i];
+          const int cap = int(i) < w.nx_small ? kMaxBlock : kMaxLargeBlock;
+          if (it.rows > cap || it.cols > cap || it.rows <= 0 || it.cols <= 0)
             throw Fail{H2SP_EINVAL, "internal: transform block size"};
           inside(it.src, it.rows, it.cols, it.ld_src, ssz[it.src_buf], "transform source");
           if (it.qL >= 0) inside(it.qL, it.rows, it.rows, it.rows, p.q_elems, "left Q");
@@ -819,8 +843,10 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
           inside(it.rr_c, it.kp_c, it.k_c, it.kp_c, p.rr_elems, "stack Rr");
           inside(it.w_dst, it.kp_c, it.k_p, it.ld_w, w.w_elems, "stack W");
         }
-        for (const QItem &it : w.q) {
-          if (it.m > kMaxBlock || it.k > kMaxRank) throw Fail{H2SP_EINVAL, "internal: Householder size"};
+        for (size_t i = 0; i < w.q.size(); ++i) {
+          const QItem &it = w.q[i];
+          const int cap = int(i) < w.nq_small ? kMaxBlock : kMaxLargeBlock;
+          if (it.m > cap || it.k > kMaxRank) throw Fail{H2SP_EINVAL, "internal: Householder size"};
           inside(it.q, it.m, it.m, it.m, p.q_elems, "Q");
           inside(it.rr, std::min(it.m, it.k), it.k, std::min(it.m, it.k), p.rr_elems, "Rr");
           if (it.w_buf == 1) inside(it.w, it.m, it.k, it.ld_w, w.w_elems, "W");

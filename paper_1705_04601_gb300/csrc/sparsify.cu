@@ -12,8 +12,13 @@
 //                   cross-level panels, split at the basis / non-basis
 //                   boundary and scattered into S or the next level (§2.2).
 //
-// Every block here is at most 64 x 64, so each CTA stages its operands in
-// shared memory; the level's work is one launch per kernel, one CTA per item.
+// Blocks of at most 64 x 64 are staged whole in shared memory, one CTA per
+// item.  Larger blocks (up to kMaxLargeBlock: 3D leaves, upper levels stacked
+// from up to eight sons) take k_householder_large, which keeps Q in its
+// global output, and k_transform_large, which streams the block and the Q
+// factors from global memory and keeps one 16-column slab of the product in
+// shared memory.  A level's small items come first in its lists; each group
+// is one launch.
 #include <cstdint>
 
 #include "internal.h"
@@ -120,6 +125,85 @@ __global__ void __launch_bounds__(kThreads) k_householder(const QItem *__restric
   }
   double *Qg = Qout + it.q;
   for (int i = tid; i < m * m; i += nt) Qg[i] = Q[i];
+}
+
+// k_householder for m > kMaxBlock: the same reflectors and completion, with W
+// (m x k) in shared memory and Q formed in place in its global output.  Each
+// column of Q is updated by one warp per reflector; the CTA barrier between
+// reflectors orders the global writes.
+__global__ void __launch_bounds__(kThreads) k_householder_large(const QItem *__restrict__ items,
+                                                                const double *__restrict__ w_in,
+                                                                const double *__restrict__ w_buf,
+                                                                double *__restrict__ Qout, double *__restrict__ Rout) {
+  const QItem it = items[blockIdx.x];
+  const int m = it.m, k = it.k, kp = min(m, k);
+  extern __shared__ double sm[];
+  double *A = sm;              // m x k, ld m
+  double *tau = A + m * k;     // kp
+  double *red = tau + kMaxRank + 1;
+  __shared__ double s_bcast;
+  const double *W = (it.w_buf == 0 ? w_in : w_buf) + it.w;
+  double *Q = Qout + it.q;     // m x m, ld m
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int i = tid; i < m * k; i += nt) A[i] = W[(i % m) + int64_t(i / m) * it.ld_w];
+  __syncthreads();
+  for (int j = 0; j < kp; ++j) {
+    double part = 0.0;
+    for (int i = j + 1 + tid; i < m; i += nt) part += A[i + j * m] * A[i + j * m];
+    const double s2 = block_sum(part, red);
+    if (tid == 0) {
+      double t = 0.0;
+      if (s2 != 0.0) {
+        const double alpha = A[j + j * m];
+        const double beta = -copysign(hypot(alpha, sqrt(s2)), alpha);
+        t = (beta - alpha) / beta;
+        s_bcast = 1.0 / (alpha - beta);
+        A[j + j * m] = beta;
+      }
+      tau[j] = t;
+    }
+    __syncthreads();
+    const double tj = tau[j];
+    if (tj != 0.0) {
+      const double scal = s_bcast;
+      for (int i = j + 1 + tid; i < m; i += nt) A[i + j * m] *= scal;
+      __syncthreads();
+      for (int c = j + 1 + wid; c < k; c += nw) {
+        double w = 0.0;
+        for (int i = j + 1 + lane; i < m; i += 32) w += A[i + j * m] * A[i + c * m];
+        w = warp_sum(w) + A[j + c * m];
+        const double tw = tj * w;
+        __syncwarp();
+        if (lane == 0) A[j + c * m] -= tw;
+        for (int i = j + 1 + lane; i < m; i += 32) A[i + c * m] -= tw * A[i + j * m];
+      }
+    }
+    __syncthreads();
+  }
+  double *R = Rout + it.rr;
+  for (int i = tid; i < kp * k; i += nt) {
+    const int r = i % kp, c = i / kp;
+    R[i] = (r <= c) ? A[r + c * m] : 0.0;
+  }
+  for (int64_t i = tid; i < int64_t(m) * m; i += nt) Q[i] = ((i % m) == (i / m)) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int j = kp - 1; j >= 0; --j) {
+    const double tj = tau[j];
+    if (tj != 0.0) {
+      for (int c = j + wid; c < m; c += nw) {
+        double *qc = Q + int64_t(c) * m;
+        double w = 0.0;
+        for (int i = j + 1 + lane; i < m; i += 32) w += A[i + j * m] * qc[i];
+        w = warp_sum(w) + qc[j];
+        const double tw = tj * w;
+        __syncwarp();
+        if (lane == 0) qc[j] -= tw;
+        for (int i = j + 1 + lane; i < m; i += 32) qc[i] -= tw * A[i + j * m];
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // rows [off_c, off_c + kp_c) of W_parent = Rr_c (kp_c x k_c) * T_c (k_c x k_p)
@@ -245,6 +329,84 @@ __global__ void __launch_bounds__(kThreads) k_transform(const XItem *__restrict_
   }
 }
 
+// k_transform for blocks above kMaxBlock rows or columns: Y = QL^T X QR by
+// slabs of kSlab output columns.  Per slab J, T_J = X QR[:, J] (rows x kSlab,
+// X read from global memory, QR[:, J] staged), then Y[:, J] = QL^T T_J (QL
+// read from global memory) and each element goes to its quadrant's
+// destination.  Same association and summation order as k_transform.
+constexpr int kSlab = 16;
+
+template <typename W>
+__global__ void __launch_bounds__(kThreads) k_transform_large(const XItem *__restrict__ items,
+                                                              const void *const *__restrict__ src_base,
+                                                              const double *__restrict__ Qrow,
+                                                              const double *__restrict__ Qcol,
+                                                              W *const *__restrict__ dst_base) {
+  const XItem it = items[blockIdx.x];
+  const int rows = it.rows, cols = it.cols;
+  extern __shared__ __align__(16) unsigned char smraw_l[];
+  W *sQ = reinterpret_cast<W *>(smraw_l);  // cols x kSlab, ld cols
+  W *sT = sQ + cols * kSlab;                // rows x kSlab, ld rows
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const bool near = it.src_buf == SRC_NEAR;
+  const double *srcd = near ? static_cast<const double *>(src_base[SRC_NEAR]) + it.src : nullptr;
+  const W *srcw = near ? nullptr : static_cast<const W *>(src_base[it.src_buf]) + it.src;
+  const int64_t lds = it.ld_src;
+  const double *QR = it.qR >= 0 ? ((it.qside & 2) ? Qcol : Qrow) + it.qR : nullptr;  // cols x cols
+  const double *QL = it.qL >= 0 ? ((it.qside & 1) ? Qcol : Qrow) + it.qL : nullptr;  // rows x rows
+  const int kr = it.kr, kc = it.kc;
+  for (int c0 = 0; c0 < cols; c0 += kSlab) {
+    const int cb = min(kSlab, cols - c0);
+    if (QR) {
+      for (int i = tid; i < cols * cb; i += nt) {
+        const int q = i % cols, c = i / cols;
+        sQ[q + c * cols] = W(QR[q + int64_t(c0 + c) * cols]);
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < rows * cb; i += nt) {
+      const int r = i % rows, c = i / rows;
+      W acc;
+      if (QR) {
+        acc = W(0);
+        const W *qc = sQ + c * cols;
+        if (near) {
+          for (int q = 0; q < cols; ++q) acc += W(srcd[r + q * lds]) * qc[q];
+        } else {
+          for (int q = 0; q < cols; ++q) acc += srcw[r + q * lds] * qc[q];
+        }
+      } else {
+        acc = near ? W(srcd[r + (c0 + c) * lds]) : srcw[r + (c0 + c) * lds];
+      }
+      sT[r + c * rows] = acc;
+    }
+    __syncthreads();
+    for (int i = tid; i < rows * cb; i += nt) {
+      const int r = i % rows, c = i / rows;
+      const W *tc = sT + c * rows;
+      W y;
+      if (QL) {
+        const double *ql = QL + int64_t(r) * rows;  // column r of QL = row r of QL^T
+        y = W(0);
+        for (int q = 0; q < rows; ++q) y += W(ql[q]) * tc[q];
+      } else {
+        y = tc[r];
+      }
+      const int cc = c0 + c;
+      const bool lo_r = r < kr, lo_c = cc < kc;
+      // quadrant of (r, cc): 0 basis x basis, 1 basis x non-basis, 2 non-basis x basis, 3 non-basis x non-basis
+      const int64_t doff = lo_r ? (lo_c ? it.dst[0] : it.dst[1]) : (lo_c ? it.dst[2] : it.dst[3]);
+      if (doff >= 0) {
+        const int dbuf = lo_r ? (lo_c ? it.dst_buf[0] : it.dst_buf[1]) : (lo_c ? it.dst_buf[2] : it.dst_buf[3]);
+        const int ldd = lo_r ? (lo_c ? it.ld[0] : it.ld[1]) : (lo_c ? it.ld[2] : it.ld[3]);
+        const int rr = lo_r ? r : r - kr, ccl = lo_c ? cc : cc - kc;
+        dst_base[dbuf][doff + rr + int64_t(ccl) * ldd] = y;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_householder(const QItem *items, int n, const double *w_in, const double *w_buf, double *Q,
@@ -258,6 +420,21 @@ cudaError_t launch_householder(const QItem *items, int n, const double *w_in, co
   }
   const size_t e0 = prof->begin();
   k_householder<<<n, kThreads, smem, s>>>(items, w_in, w_buf, Q, Rr);
+  prof->end(P_HOUSEHOLDER, 1, e0, 0.0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_householder_large(const QItem *items, int n, const double *w_in, const double *w_buf, double *Q,
+                                     double *Rr, int max_m, int max_k, cudaStream_t s, Prof *prof) {
+  if (n == 0) return cudaSuccess;
+  const size_t smem = sizeof(double) * (size_t(max_m) * max_k + kMaxRank + 1 + 64);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_householder_large, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr_done = true;
+  }
+  const size_t e0 = prof->begin();
+  k_householder_large<<<n, kThreads, smem, s>>>(items, w_in, w_buf, Q, Rr);
   prof->end(P_HOUSEHOLDER, 1, e0, 0.0);
   return cudaGetLastError();
 }
@@ -303,6 +480,24 @@ cudaError_t launch_transform(const XItem *items, int n, const void *const *src_b
   return cudaGetLastError();
 }
 
+template <typename W>
+cudaError_t launch_transform_large(const XItem *items, int n, const void *const *src_base, const double *Qrow,
+                                   const double *Qcol, W *const *dst_base, int max_rows, int max_cols, cudaStream_t s,
+                                   Prof *prof, double flops) {
+  if (n == 0) return cudaSuccess;
+  const size_t smem = sizeof(W) * size_t(kSlab) * size_t(max_rows + max_cols);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_transform_large<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(sizeof(W) * kSlab * 2 * kMaxLargeBlock));
+    attr_done = true;
+  }
+  const size_t e0 = prof->begin();
+  k_transform_large<W><<<n, kThreads, smem, s>>>(items, src_base, Qrow, Qcol, dst_base);
+  prof->end(P_TRANSFORM, 1, e0, flops);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_coupling<double>(const CItem *, int, const double *, const double *, const double *,
                                              double *const *, int, cudaStream_t, Prof *);
 template cudaError_t launch_coupling<float>(const CItem *, int, const double *, const double *, const double *,
@@ -311,5 +506,12 @@ template cudaError_t launch_transform<double>(const XItem *, int, const void *co
                                               double *const *, cudaStream_t, Prof *, double);
 template cudaError_t launch_transform<float>(const XItem *, int, const void *const *, const double *, const double *,
                                              float *const *, cudaStream_t, Prof *, double);
+
+template cudaError_t launch_transform_large<double>(const XItem *, int, const void *const *, const double *,
+                                                    const double *, double *const *, int, int, cudaStream_t, Prof *,
+                                                    double);
+template cudaError_t launch_transform_large<float>(const XItem *, int, const void *const *, const double *,
+                                                   const double *, float *const *, int, int, cudaStream_t, Prof *,
+                                                   double);
 
 }  // namespace h2sp

@@ -46,11 +46,17 @@ _CASES = {
     "tiny": dict(n=48, kernel="log", leaf=64, tol=1e-8, seed=6),
     "inv3d": dict(n=1500, kernel="inv", leaf=40, tol=1e-6, seed=5, dim=3),
     "log16k": dict(n=16384, kernel="log", leaf=64, tol=1e-6, seed=9),
+    # 3D with blocks above 64 rows: 1/r on the jittered Fibonacci sphere (leaf <= 128,
+    # levels up to 91 rows) and Yukawa in the cube (leaves up to 113 points)
+    "sphere8k": dict(workload="inv3d_sphere_n262144", n=8192),
+    "cube6k": dict(workload="yukawa3d_n1048576", n=6000),
 }
 
 
 def _make(name):
     s = _CASES[name]
+    if "workload" in s:
+        return synth.make_workload(s["workload"], n=s["n"])[0]
     h, _ = synth.make_small(s["n"], kernel=s["kernel"], leaf=s["leaf"], tol=s["tol"], seed=s["seed"],
                             dim=s.get("dim", 2))
     return h
@@ -118,8 +124,8 @@ def test_malformed_descriptors_are_rejected():
 
 
 def test_oversized_blocks_are_reported_unsupported():
-    h, _ = synth.make_small(1000, kernel="log", leaf=300, tol=1e-8, seed=3)
-    assert h.size[h.level_ptr[h.depth]:].max() > 64
+    h, _ = synth.make_small(2000, kernel="log", leaf=1000, tol=1e-8, seed=3)
+    assert h.size[h.level_ptr[h.depth]:].max() > 384
     with pytest.raises(H.H2spError) as e:
         H.h2sp_analyze(H.H2Input(h, device=None))
     assert e.value.status == H.H2SP_EUNSUPPORTED
@@ -261,3 +267,16 @@ def test_query_counts_independent_systems():
     an = H.h2sp_analyze(H.H2Input(_make("tiny"), device=None))
     assert H.h2sp_query(an)["nsys"] == 1
     an.close()
+
+
+@pytest.mark.parametrize("name", ["sphere8k", "cube6k"])
+def test_large_blocks_plan_small_items_first(name):
+    """Blocks above 64 rows are planned (up to 384): the structure matches the
+    oracle (test above) and the planner's audit accepts the item lists, whose
+    small items lead each level."""
+    h = _make(name)
+    sp = osp.sparsify(h)
+    assert max(int(sp.sch.m[c]) for c in range(h.ncl) if sp.sch.level[c] < max(sp.sch.lstop, 1)) > 64
+    hd = H.h2sp_analyze(H.H2Input(h, device=None))
+    assert H.h2sp_query(hd)["lstop"] == sp.sch.lstop
+    hd.close()
