@@ -19,8 +19,9 @@ Contents, in the order of the method:
 * ``factor``      -- nested-dissection ordering of S by cluster closure, the
                      symbolic elimination, a right-looking block LU with
                      partial pivoting inside each pivot block, the solve
-                     S y = U^T b, x = V y of §1 (Eq. sp0), and log|det A|
-                     from the pivots (§5.3).
+                     S y = U^T b, x = V y of §1 (Eq. sp0), log|det A|
+                     from the pivots (§5.3), and the block Cholesky of an
+                     SPD S on the same supernodes.
 * ``iterate``     -- iterative refinement and restarted GMRES driven by the
                      H^2 matvec and preconditioned by the factored S (§5.5).
 

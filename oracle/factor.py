@@ -223,6 +223,83 @@ def solve_S(fa: Factors, c: np.ndarray) -> np.ndarray:
     return y.reshape(np.shape(c))
 
 
+@dataclasses.dataclass
+class CholFactors:
+    sym: Symbolic
+    node_off: np.ndarray
+    L11: list      # per supernode: lower Cholesky factor of its pivot block
+    L21: list      # per supernode: boundary rows x supernode columns
+
+
+def cholesky(h, sp: Sparsified, sym: Symbolic | None = None) -> CholFactors:
+    """Block Cholesky S = L L^T for a symmetric positive definite S.
+
+    The sparse package the paper factors S with (§5.3-5.4) is a Cholesky
+    code, and an SPD A gives an SPD S (Proposition 2.1: S = U^T A U with U
+    orthogonal).  Same supernodes, elimination order and boundaries as
+    factor(); per supernode, right-looking:
+        F11 = L11 L11^T          (dense Cholesky of the pivot block, LAPACK potrf)
+        L21 = F21 L11^-T
+        M[w1, w2] -= L21[w1] L21[w2]^T   for all boundary pairs (w1, w2).
+    No pivoting: a pivot block that is not positive definite raises
+    LinAlgError.
+    """
+    if sym is None:
+        sym = symbolic(h, sp)
+    size = sp.sch.node_size
+    M = {k: v.copy() for k, v in sp.blocks.items()}
+    L11s, L21s = [], []
+    for k in range(sym.sn_ptr.size - 1):
+        sn = [int(v) for v in sym.order[sym.sn_ptr[k]:sym.sn_ptr[k + 1]]]
+        bd = [int(w) for w in sym.boundary[k]]
+        F11 = _gather(M, sn, sn, size)
+        F21 = _gather(M, bd, sn, size)
+        L11 = sla.cholesky(F11, lower=True, check_finite=True)
+        L21 = sla.solve_triangular(L11, F21.T, lower=True).T if F21.size else F21
+        L11s.append(L11)
+        L21s.append(L21)
+        if bd:
+            upd = L21 @ L21.T
+            bo = np.concatenate([[0], np.cumsum([size[w] for w in bd])]).astype(np.int64)
+            for a, w1 in enumerate(bd):
+                for b, w2 in enumerate(bd):
+                    blk = upd[bo[a]:bo[a + 1], bo[b]:bo[b + 1]]
+                    if (w1, w2) in M:
+                        M[(w1, w2)] = M[(w1, w2)] - blk
+                    else:
+                        M[(w1, w2)] = -blk
+        for v in sn:
+            for w in list(bd) + sn:
+                M.pop((v, w), None)
+                M.pop((w, v), None)
+    return CholFactors(sym, sp.sch.node_off, L11s, L21s)
+
+
+def solve_S_chol(fa: CholFactors, c: np.ndarray) -> np.ndarray:
+    """y = S^{-1} c = L^-T L^-1 c by the block Cholesky factors."""
+    sym = fa.sym
+    y = np.array(c, dtype=np.float64, copy=True).reshape(c.shape[0], -1)
+    rows = [_rows(fa.node_off, [int(v) for v in sym.order[sym.sn_ptr[k]:sym.sn_ptr[k + 1]]])
+            for k in range(sym.sn_ptr.size - 1)]
+    brows = [_rows(fa.node_off, [int(w) for w in sym.boundary[k]]) for k in range(sym.sn_ptr.size - 1)]
+    for k in range(len(rows)):
+        ys = sla.solve_triangular(fa.L11[k], y[rows[k]], lower=True)
+        y[rows[k]] = ys
+        if brows[k].size:
+            y[brows[k]] -= fa.L21[k] @ ys
+    for k in range(len(rows) - 1, -1, -1):
+        ys = y[rows[k]]
+        if brows[k].size:
+            ys = ys - fa.L21[k].T @ y[brows[k]]
+        y[rows[k]] = sla.solve_triangular(fa.L11[k], ys, lower=True, trans="T")
+    return y.reshape(np.shape(c))
+
+
+def logdet_chol(fa: CholFactors) -> float:
+    """log det S = log det A (> 0 for SPD A, V = U) = 2 sum_j log l_jj (§5.3)."""
+    return 2.0 * sum(float(np.sum(np.log(np.diag(L)))) for L in fa.L11)
+
+
 def logdet(fa: Factors) -> tuple[float, int]:
     """log|det A| and the sign of det S of one system, from the block LU of S.
 

@@ -16,7 +16,10 @@ at least one of them:
 * the number of nonzeros per row of S stays bounded as N grows (§5.1);
 * IR / GMRES with the factored S reach 1e-10 (§5.5);
 * log|det A| from the pivots of S equals LAPACK's slogdet of the dense A and
-  of the dense S, with the sign of det S (§5.3).
+  of the dense S, with the sign of det S (§5.3);
+* the block Cholesky of an SPD S reproduces S, equals LAPACK's dense
+  Cholesky factor of S in elimination order (the factor is unique), solves
+  like a dense solve, and refuses an indefinite S.
 """
 import numpy as np
 import pytest
@@ -44,6 +47,7 @@ def case(name):
         "inv3d": dict(n=1500, kernel="inv", leaf=40, tol=1e-6, seed=5, dim=3),
         "tiny": dict(n=48, kernel="log", leaf=64, tol=1e-8, seed=6),
         "small": dict(n=256, kernel="log", leaf=16, tol=1e-8, seed=7),
+        "gauss3d": dict(n=1500, kernel="gauss", leaf=40, tol=1e-8, seed=10, dim=3),
     }[name]
     h, b = synth.make_small(spec["n"], kernel=spec["kernel"], leaf=spec["leaf"], tol=spec["tol"],
                             seed=spec["seed"], dim=spec.get("dim", 2), nrhs=2)
@@ -353,3 +357,50 @@ def test_refinement_and_gmres_reach_1e10():
     assert hg[-1] <= 1e-10
     assert np.linalg.norm(xg - xd[:, 0]) / np.linalg.norm(xd[:, 0]) < 1e-8
     assert len(hg) > 2
+
+
+# --------------------------------------------------------------------------
+# block Cholesky of an SPD S (§5.3-5.4, Proposition 2.1)
+# --------------------------------------------------------------------------
+
+
+def _dense_chol(fa, n):
+    """The block factors as one dense lower factor in the original row order,
+    and the scalar elimination order."""
+    sym = fa.sym
+    Ld = np.zeros((n, n))
+    perm = []
+    for k in range(sym.sn_ptr.size - 1):
+        rows = ofa._rows(fa.node_off, [int(v) for v in sym.order[sym.sn_ptr[k]:sym.sn_ptr[k + 1]]])
+        brows = ofa._rows(fa.node_off, [int(w) for w in sym.boundary[k]])
+        Ld[np.ix_(rows, rows)] = fa.L11[k]
+        if brows.size:
+            Ld[np.ix_(brows, rows)] = fa.L21[k]
+        perm.extend(rows.tolist())
+    return Ld, np.array(perm)
+
+
+@pytest.mark.parametrize("name", ["gauss1k", "gauss3d"])
+def test_block_cholesky_matches_dense(name):
+    h, b, sp, A = case(name)
+    S = osp.dense_S(sp)
+    fa = ofa.cholesky(h, sp)
+    Ld, perm = _dense_chol(fa, h.n)
+    assert np.linalg.norm(Ld @ Ld.T - S) <= 1e-12 * np.linalg.norm(S)
+    Lp = Ld[np.ix_(perm, perm)]
+    assert np.abs(np.triu(Lp, 1)).max() == 0.0           # lower triangular in elimination order
+    Lref = np.linalg.cholesky(S[np.ix_(perm, perm)])      # unique for an SPD matrix
+    assert np.linalg.norm(Lp - Lref) <= 1e-10 * np.linalg.norm(Lref)
+    c = osp.apply_T(sp, h, b)
+    y = ofa.solve_S_chol(fa, c)
+    yd = np.linalg.solve(S, c)
+    assert np.linalg.norm(y - yd) <= 1e-10 * np.linalg.norm(yd)
+    sgn, ld = np.linalg.slogdet(A)
+    assert sgn > 0 and abs(ofa.logdet_chol(fa) - ld) <= 1e-10 * max(1.0, abs(ld))
+
+
+def test_block_cholesky_refuses_an_indefinite_S():
+    h, b, sp, A = case("log1k")     # -log r on [0,1]^2: S has a negative eigenvalue
+    assert np.linalg.eigvalsh(osp.dense_S(sp)).min() < 0
+    with pytest.raises(np.linalg.LinAlgError):
+        ofa.cholesky(h, sp)
