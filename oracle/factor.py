@@ -156,7 +156,34 @@ def _gather(M: dict, rows: list, cols: list, size) -> np.ndarray:
     return out
 
 
-def factor(h, sp: Sparsified, sym: Symbolic | None = None) -> Factors:
+def getrf_tile(F: np.ndarray, nb: int = 64) -> tuple[np.ndarray, np.ndarray]:
+    """P F = L U with the pivot of column j searched only among rows j .. the
+    end of the nb-row diagonal tile that holds j (LAPACK ipiv convention,
+    L unit lower and U in one array).  A further restriction of the pivoting
+    reading above, for the FP32 preconditioner: a panel's pivots then come
+    from its own diagonal tile, so the rows below need no search.  With
+    nb >= the block size it is getrf's partial pivoting.  Plain unblocked
+    right-looking elimination; a zero pivot raises LinAlgError.
+    """
+    A = np.array(F, dtype=np.float64, copy=True)
+    s = A.shape[0]
+    piv = np.arange(s)
+    for j in range(s):
+        t_end = min((j // nb + 1) * nb, s)
+        p = j + int(np.argmax(np.abs(A[j:t_end, j])))
+        piv[j] = p
+        if p != j:
+            A[[j, p]] = A[[p, j]]
+        if A[j, j] == 0.0:
+            raise np.linalg.LinAlgError("zero pivot in column %d" % j)
+        A[j + 1:, j] /= A[j, j]
+        A[j + 1:, j + 1:] -= np.outer(A[j + 1:, j], A[j, j + 1:])
+    return A, piv
+
+
+def factor(h, sp: Sparsified, sym: Symbolic | None = None, pivot: str = "supernode") -> Factors:
+    """Block LU of S; pivot = "supernode" (getrf on each pivot block) or
+    "tile" (getrf_tile, the pivot of each column from its 64-row diagonal tile)."""
     if sym is None:
         sym = symbolic(h, sp)
     size = sp.sch.node_size
@@ -168,7 +195,7 @@ def factor(h, sp: Sparsified, sym: Symbolic | None = None) -> Factors:
         F11 = _gather(M, sn, sn, size)
         F12 = _gather(M, sn, bd, size)
         F21 = _gather(M, bd, sn, size)
-        lu, piv = sla.lu_factor(F11, check_finite=True)
+        lu, piv = sla.lu_factor(F11, check_finite=True) if pivot == "supernode" else getrf_tile(F11)
         if np.any(np.diag(lu) == 0.0):
             raise np.linalg.LinAlgError("zero pivot in supernode %d" % k)
         F12p = F12.copy()

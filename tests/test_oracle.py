@@ -404,3 +404,49 @@ def test_block_cholesky_refuses_an_indefinite_S():
     assert np.linalg.eigvalsh(osp.dense_S(sp)).min() < 0
     with pytest.raises(np.linalg.LinAlgError):
         ofa.cholesky(h, sp)
+
+
+# --------------------------------------------------------------------------
+# pivot search restricted to the 64-row diagonal tile (FP32 preconditioner)
+# --------------------------------------------------------------------------
+
+
+def test_getrf_tile_with_one_tile_is_lapack_getrf():
+    rng = np.random.default_rng(3)
+    for n in (1, 7, 64, 150):
+        F = rng.standard_normal((n, n))
+        lu, piv = ofa.getrf_tile(F, nb=max(n, 1))
+        lur, pivr = sla.lu_factor(F)
+        assert np.array_equal(piv, pivr)
+        assert np.abs(lu - lur).max() <= 1e-12 * max(1.0, np.abs(lur).max())
+
+
+def test_getrf_tile_reconstructs_and_searches_only_its_tile():
+    rng = np.random.default_rng(4)
+    n = 150
+    F = rng.standard_normal((n, n))
+    F[100, 0] = 1e3          # the column maximum lies outside the first 64-row tile
+    lu, piv = ofa.getrf_tile(F, nb=64)
+    assert piv[0] == int(np.argmax(np.abs(F[:64, 0])))
+    assert np.all(piv >= np.arange(n)) and np.all(piv < np.minimum((np.arange(n) // 64 + 1) * 64, n))
+    P = np.arange(n)
+    for j, p in enumerate(piv):
+        P[[j, p]] = P[[p, j]]
+    L = np.tril(lu, -1) + np.eye(n)
+    U = np.triu(lu)
+    assert np.linalg.norm(L @ U - F[P]) <= 1e-13 * np.linalg.norm(F) * n
+
+
+@pytest.mark.parametrize("name", ["log1k", "log4k", "skew1k"])
+def test_tile_pivoted_block_lu_solves(name):
+    h, b, sp, A = case(name)
+    fa = ofa.factor(h, sp, pivot="tile")
+    c = osp.apply_T(sp, h, b)
+    y = ofa.solve_S(fa, c)
+    yd = np.linalg.solve(osp.dense_S(sp), c)
+    assert np.linalg.norm(y - yd) <= 1e-9 * np.linalg.norm(yd)
+    lo, so = ofa.logdet(fa)
+    sa, la = np.linalg.slogdet(A)
+    assert abs(lo - la) <= 1e-9 * max(1.0, abs(la))
+    if h.col_leaf_basis is None:
+        assert so == int(sa)
