@@ -422,6 +422,158 @@ constexpr int kRegPanelThreads = 384;
 constexpr int kRegPanelRows = 2;  // panel rows per thread, held in registers
 constexpr int kRegPanelMaxRows = kRegPanelThreads * kRegPanelRows;
 
+// Tile-pivoted FP32 panel (the FP32 preconditioner's option): the pivot of
+// column j0 + j is searched only among the rows of the panel's jb x jb
+// diagonal tile, so no search or row exchange reaches below the tile.
+// Step 1, one CTA per front: LU of the tile with partial pivoting among its
+// rows (first maximum on ties), in shared memory; LAPACK ipiv and the step's
+// swap list as k_panel_reg writes them.  Step 2 (k_panel_tile_l21): the rows
+// below, L21 = A21 U11^-1.
+constexpr int kTileThreads = 256;
+
+template <int NB>
+__global__ void __launch_bounds__(kTileThreads) k_panel_tile_diag(const FrontDev *__restrict__ fr, int j0,
+                                                                  float *__restrict__ fronts,
+                                                                  int32_t *__restrict__ piv,
+                                                                  int32_t *__restrict__ swaps, int *__restrict__ err) {
+  const FrontDev F = fr[blockIdx.x];
+  if (j0 >= F.s) return;  // uniform over the CTA
+  const int jb = min(NB, F.s - j0);
+  float *A = fronts + F.off;
+  const int64_t ld = F.ld;
+  __shared__ float T[NB * NB];  // tile, column-major, ld NB
+  __shared__ int perm[NB];      // tile row (relative to j0) now at each position
+  __shared__ int s_p;
+  __shared__ float s_inv;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < jb * jb; e += kTileThreads) {
+    const int r = e % jb, c = e / jb;
+    T[r + c * NB] = A[(j0 + r) + int64_t(j0 + c) * ld];
+  }
+  for (int r = tid; r < jb; r += kTileThreads) perm[r] = r;
+  __syncthreads();
+  for (int j = 0; j < jb; ++j) {
+    if (tid < 32) {
+      // first row of largest modulus among rows j .. jb-1 of column j
+      float best = -1.0f;
+      int bi = jb;
+      for (int r = j + tid; r < jb; r += 32) {
+        const float v = fabsf(T[r + j * NB]);
+        if (v > best) best = v, bi = r;  // rows visited in increasing order per lane
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) best = ob, bi = oi;
+      }
+      if (tid == 0) {
+        if (bi >= jb) bi = j;  // no comparable candidate (NaN column): keep the row
+        s_p = bi;
+        piv[F.piv_off + j0 + j] = j0 + bi;
+        const int t = perm[j];
+        perm[j] = perm[bi];
+        perm[bi] = t;
+      }
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != j)
+      for (int c = tid; c < jb; c += kTileThreads) {
+        const float t = T[j + c * NB];
+        T[j + c * NB] = T[p + c * NB];
+        T[p + c * NB] = t;
+      }
+    __syncthreads();
+    if (tid == 0) {
+      const float pv = T[j + j * NB];
+      if (pv == 0.0f) atomicOr(err, 1);
+      s_inv = pv != 0.0f ? 1.0f / pv : 0.0f;
+    }
+    __syncthreads();
+    const float inv = s_inv;
+    for (int r = j + 1 + tid; r < jb; r += kTileThreads) T[r + j * NB] *= inv;
+    __syncthreads();
+    const int m = jb - j - 1;
+    for (int e = tid; e < m * m; e += kTileThreads) {
+      const int r = j + 1 + e % m, c = j + 1 + e / m;
+      T[r + c * NB] -= T[r + j * NB] * T[j + c * NB];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < jb * jb; e += kTileThreads) {
+    const int r = e % jb, c = e / jb;
+    A[(j0 + r) + int64_t(j0 + c) * ld] = T[r + c * NB];
+  }
+  if (tid == 0) {
+    int32_t *sw = swaps + int64_t(blockIdx.x) * (1 + 2 * kMaxSwapRows);
+    int n = 0;
+    for (int r = 0; r < jb; ++r)
+      if (perm[r] != r) {
+        sw[1 + n] = j0 + r;
+        sw[1 + kMaxSwapRows + n] = j0 + perm[r];
+        ++n;
+      }
+    sw[0] = n;
+  }
+}
+
+// Step 2: rows j0 + jb .. f of the panel columns, L21 = A21 U11^-1.  Each CTA
+// inverts U11 in shared memory (back substitution, one column per thread),
+// then each thread takes one row: the row in registers, one column of
+// U11^-1 per output element.  grid = (row chunks of kL21Rows, fronts).
+constexpr int kL21Rows = 64;
+
+template <int NB>
+__global__ void __launch_bounds__(kL21Rows) k_panel_tile_l21(const FrontDev *__restrict__ fr, int j0,
+                                                             float *__restrict__ fronts) {
+  static_assert(NB == kL21Rows, "one thread per column of U11 while inverting it");
+  const FrontDev F = fr[blockIdx.y];
+  if (j0 >= F.s) return;
+  const int jb = min(NB, F.s - j0);
+  const int row0 = j0 + jb + int(blockIdx.x) * kL21Rows;
+  if (row0 >= F.f) return;  // uniform over the CTA
+  float *A = fronts + F.off;
+  const int64_t ld = F.ld;
+  __shared__ float U[NB * NB];   // U11, column-major, ld NB; zero outside the upper jb x jb tile
+  __shared__ float Ui[NB * NB];  // U11^-1 (upper); zero columns from jb on
+  for (int e = threadIdx.x; e < NB * NB; e += kL21Rows) {
+    const int r = e % NB, c = e / NB;
+    U[e] = (r < jb && c < jb && r <= c) ? A[(j0 + r) + int64_t(j0 + c) * ld] : 0.0f;
+  }
+  __syncthreads();
+  {
+    const int c = int(threadIdx.x);  // U11 x = e_c, rows c down to 0
+    for (int r = NB - 1; r > c; --r) Ui[r + c * NB] = 0.0f;
+    if (c < jb) {
+      const float d = U[c + c * NB];
+      Ui[c + c * NB] = d != 0.0f ? 1.0f / d : 0.0f;
+      for (int r = c - 1; r >= 0; --r) {
+        float acc = 0.0f;
+        for (int k = r + 1; k <= c; ++k) acc += U[r + k * NB] * Ui[k + c * NB];
+        const float dr = U[r + r * NB];
+        Ui[r + c * NB] = dr != 0.0f ? -acc / dr : 0.0f;
+      }
+    } else {
+      for (int r = c; r >= 0; --r) Ui[r + c * NB] = 0.0f;
+    }
+  }
+  __syncthreads();
+  const int row = row0 + int(threadIdx.x);
+  if (row >= F.f) return;
+  float a[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) a[k] = k < jb ? A[row + int64_t(j0 + k) * ld] : 0.0f;
+#pragma unroll 1
+  for (int c = 0; c < jb; ++c) {
+    const float *ui = Ui + c * NB;
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) acc += a[k] * ui[k];
+    A[row + int64_t(j0 + c) * ld] = acc;
+  }
+}
+
 // Panel factorization with the rows in registers, by one thread-block cluster
 // per front.  Thread t of CTA q holds rows r_lo(q) + t and r_lo(q) + t + 384,
 // NB values each, in a shifting frame: at column j, slot 0 holds column j,
@@ -1682,6 +1834,17 @@ inline bool blocked_lu_enabled() {
   return v == 1;
 }
 
+// FP32 panels with the pivot search restricted to the diagonal tile
+// (H2SP_PANEL=tile); partial pivoting over the supernode rows otherwise.
+inline bool tile_panel_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = std::getenv("H2SP_PANEL");
+    v = (e && std::strcmp(e, "tile") == 0) ? 1 : 0;
+  }
+  return v == 1;
+}
+
 // The FP32 trailing update runs on the tensor cores (three-term TF32 split);
 // H2SP_GEMM=simt selects the CUDA-core kernel instead.
 inline bool use_tensor_core_gemm() {
@@ -1736,6 +1899,16 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
       }
     const size_t e0 = prof->begin(st);
     const int R = max_f - j0;
+    if constexpr (std::is_same<T, float>::value) {
+      if (tile_panel_enabled()) {
+        *cl = nfront;
+        k_panel_tile_diag<NB><<<nfront, kTileThreads, 0, st>>>(fr, j0, fronts, piv, swp, err);
+        const int chunks = std::max(1, cdiv(R - 1, kL21Rows));
+        k_panel_tile_l21<NB><<<dim3(unsigned(chunks), unsigned(nfront)), kL21Rows, 0, st>>>(fr, j0, fronts);
+        prof->end(P_PANEL, 2, e0, fpanel, st);
+        return cudaGetLastError();
+      }
+    }
     const int creg = reg_panel_cluster_max<T, NB>();
     const int C = (creg > 0 && R <= kRegPanelMaxRows * creg) ? 0 : panel_cluster_size<T, NB>(R);
     if (creg > 0 && R <= kRegPanelMaxRows * creg) {
