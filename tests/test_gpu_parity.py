@@ -547,3 +547,70 @@ def test_logdet_per_system_of_a_forest():
         assert abs(ld[w] - lo) <= 1e-10 * max(1.0, _logdet_terms(fa))
         assert sg[w] == so
     hd.close()
+
+
+# ---------------------------------------------------------------------------
+# the small configurations of the workloads, as generated for the bench
+# ---------------------------------------------------------------------------
+
+
+def test_config_log2d_n4096_fp64_direct():
+    """2D -log r, N = 4,096 uniform points, leaf <= 64, Chebyshev 4x4
+    recompressed to 1e-8, one right-hand side: the FP64 path end to end (S
+    pattern equal, S and Q blocks within 1e-10, the direct solve within 1e-10
+    of the oracle's)."""
+    h, b = synth.make_workload("log2d_n4096")
+    sp = osp.sparsify(h)
+    hd = H.h2sp_sparsify(H.H2Input(h))
+    S = H.h2sp_export_S(hd)
+    vbr = osp.to_vbr(sp)
+    assert np.array_equal(S["node_size"], vbr.node_size)
+    assert np.array_equal(S["brow_ptr"], vbr.brow_ptr) and np.array_equal(S["bcol_idx"], vbr.bcol_idx)
+    ns = vbr.node_size
+    for i in range(ns.size):
+        lo, hi = int(vbr.brow_ptr[i]), int(vbr.brow_ptr[i + 1])
+        if hi == lo:
+            continue
+        a, e = int(vbr.val_off[lo]), int(vbr.val_off[hi - 1] + ns[i] * ns[vbr.bcol_idx[hi - 1]])
+        assert np.linalg.norm(S["vals"][a:e] - vbr.vals[a:e]) <= TOL * np.linalg.norm(vbr.vals[a:e])
+    for t in sp.Q:
+        assert np.linalg.norm(H.h2sp_export_Q(hd, t) - sp.Q[t]) <= TOL * np.linalg.norm(sp.Q[t]), t
+    H.h2sp_factor(hd, H.H2SP_FP64)
+    bt = dev(b)
+    xt = torch.empty_like(bt)
+    H.h2sp_solve(hd, bt, xt, mode=H.H2SP_DIRECT)
+    torch.cuda.synchronize()
+    xo = ofa.solve(h, sp, ofa.factor(h, sp), b)
+    assert np.linalg.norm(host(xt) - xo) <= TOL * np.linalg.norm(xo)
+    hd.close()
+
+
+def test_batched_ellipses_fp32_refinement_and_graph_replay():
+    """Batched form: 16 systems with N_k uniform in [2048, 8192] on random
+    ellipses, leaf <= 64, tol 1e-6.  FP32 factors + FP64 refinement bring every
+    system to 1e-10 (checked on each system's own oracle H^2 product); after the
+    close blocks and couplings are doubled in place, h2sp_refactor (graph
+    replay) and the same refinement bring the doubled systems to 1e-10."""
+    systems, f, b = synth.make_batched(16, 2048, 8192, leaf=64, tol=1e-6, nrhs=2)
+    inp = H.H2Input(f)
+    hd = H.h2sp_sparsify(inp)
+    H.h2sp_factor(hd, H.H2SP_FP32)
+    bt = dev(b)
+    xt = torch.empty_like(bt)
+    mvs = [oh2.Matvec(s) for s in systems]
+    for scale in (1.0, 2.0):
+        if scale != 1.0:
+            inp.dev["near_block"].mul_(scale)
+            inp.dev["coupling"].mul_(scale)
+            H.h2sp_refactor(hd)
+        info = H.h2sp_solve(hd, bt, xt, mode=H.H2SP_IR, tol=1e-10, maxit=30)
+        assert info.status == H.H2SP_OK and info.rel_residual <= 1e-10
+        torch.cuda.synchronize()
+        xg = host(xt)
+        o = 0
+        for s, mv in zip(systems, mvs):
+            bs = b[o:o + s.n]
+            r = np.linalg.norm(bs - scale * mv(xg[o:o + s.n]), axis=0) / np.linalg.norm(bs, axis=0)
+            assert r.max() <= 2e-10, (scale, o, r.max())
+            o += s.n
+    hd.close()
