@@ -280,3 +280,25 @@ def test_large_blocks_plan_small_items_first(name):
     hd = H.h2sp_analyze(H.H2Input(h, device=None))
     assert H.h2sp_query(hd)["lstop"] == sp.sch.lstop
     hd.close()
+
+
+def test_plain_c_consumer(tmp_path):
+    """The ABI from C: include/h2sp.h compiles as C99 (and as C++), and a C
+    program linked against libh2sp.so analyses a hand-built two-leaf structure
+    and checks the sizes, the S pattern of §3 and the state errors."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    lib_dir = os.path.dirname(H.LIB_PATH)
+    exe = str(tmp_path / "analyze_tiny")
+    src = os.path.join(ROOT, "tests", "c_abi", "analyze_tiny.c")
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), src,
+                        "-L", lib_dir, "-lh2sp", "-Wl,-rpath," + lib_dir, "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
+    if shutil.which("g++") is not None:
+        r = subprocess.run(["g++", "-std=c++17", "-fsyntax-only", "-Wall", "-Werror", "-x", "c++",
+                            os.path.join(ROOT, "include", "h2sp.h")], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
