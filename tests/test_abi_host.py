@@ -302,3 +302,23 @@ def test_plain_c_consumer(tmp_path):
         r = subprocess.run(["g++", "-std=c++17", "-fsyntax-only", "-Wall", "-Werror", "-x", "c++",
                             os.path.join(ROOT, "include", "h2sp.h")], capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def test_sparsification_work_is_linear_in_n():
+    """§5.2: the sparsification costs O(N) for a fixed accuracy.  The
+    planner's algorithmic flop count per point and the nonzeros of S per point
+    stay within a factor 1.5 across N = 4,096 .. 32,768 (2D -log r, leaf <= 64,
+    basis tol 1e-6), while the factorization work per point grows with N."""
+    per_n = []
+    for n in (4096, 16384, 32768):
+        h, _ = synth.make_workload("log2d_n65536", n=n)
+        an = H.h2sp_analyze(H.H2Input(h, device=None))
+        q = H.h2sp_query(an)
+        per_n.append((q["sparsify_flops"] / n, q["nnz"] / n, q["factor_flops"] / n))
+        an.close()
+    sf = [a for a, _, _ in per_n]
+    nz = [b for _, b, _ in per_n]
+    ff = [c for _, _, c in per_n]
+    assert max(sf) / min(sf) <= 1.5
+    assert max(nz) / min(nz) <= 1.5
+    assert ff[0] < ff[1] < ff[2]
