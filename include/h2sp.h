@@ -246,7 +246,8 @@ int h2sp_refactor(h2sp_handle *h, h2sp_stream stream);
  * h2sp_solve -- x = A^{-1} b through S y = U^T b, x = V y (Eq. sp0), either
  * once (DIRECT, needs h2sp_factor) or iterated on the FP64 H^2 residual
  * (IR, or GMRES right-preconditioned by the factored S, §5.5).  b (ldb >= n)
- * and x (ldx >= n) are device arrays of nrhs columns; x may not alias b.
+ * and x (ldx >= n) are device arrays of nrhs columns (1 <= nrhs <= 64, else
+ * H2SP_EINVAL); x may not alias b.
  * `info` (host, may be NULL) receives iterations and the final relative
  * residual.  The triangular sweeps are one cooperative launch per level and
  * direction whose row blocks wait (bounded) for the blocks they depend on;

@@ -322,3 +322,18 @@ def test_sparsification_work_is_linear_in_n():
     assert max(sf) / min(sf) <= 1.5
     assert max(nz) / min(nz) <= 1.5
     assert ff[0] < ff[1] < ff[2]
+
+
+def test_solve_rejects_bad_right_hand_side_counts():
+    """h2sp_solve takes 1 <= nrhs <= 64; other counts, or a null handle, are
+    H2SP_EINVAL before anything is touched."""
+    o = H.SolveOpts(int(H.H2SP_DIRECT), 1e-10, 10, 20)
+    dummy = ctypes.c_void_p(16)
+    for nrhs in (0, -1, 65):
+        assert H.lib().h2sp_solve(None, ctypes.byref(o), nrhs, dummy, 1, dummy, 1, None, None) == H.H2SP_EINVAL
+    h = _make("tiny")
+    an = H.h2sp_analyze(H.H2Input(h, device=None))
+    for nrhs in (0, 65):
+        assert H.lib().h2sp_solve(an.ptr, ctypes.byref(o), nrhs, dummy, h.n, dummy, h.n, None, None) == H.H2SP_EINVAL
+    assert H.lib().h2sp_solve(an.ptr, ctypes.byref(o), 1, dummy, h.n, dummy, h.n, None, None) == H.H2SP_ESTATE
+    an.close()
