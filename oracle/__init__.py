@@ -22,6 +22,8 @@ Contents, in the order of the method:
                      S y = U^T b, x = V y of §1 (Eq. sp0), log|det A|
                      from the pivots (§5.3), and the block Cholesky of an
                      SPD S on the same supernodes.
+* ``ilu``         -- the threshold incomplete LU (ILUt) of S that §5.5 uses
+                     as the preconditioner, on dense arrays for small cases.
 * ``iterate``     -- iterative refinement and restarted GMRES driven by the
                      H^2 matvec and preconditioned by the factored S (§5.5).
 

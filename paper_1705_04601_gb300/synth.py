@@ -104,8 +104,19 @@ def kernel_log_skew(x, y):
     return kernel_log(x, y) + 0.1 * (x[:, None, 0] - y[None, :, 0])
 
 
+def kernel_ifmm(d: float):
+    """The matrix of the preconditioning example of §5.5: |x-y|/d for
+    0 < |x-y| < d, d/|x-y| beyond (1 on the diagonal, from default_diag).
+    Its condition number grows with d."""
+    def k(x, y):
+        r = _pairdist(x, y)
+        with np.errstate(divide="ignore"):
+            return np.where(r < d, r / d, d / r)
+    return k
+
+
 KERNELS = {"log": kernel_log, "inv": kernel_inv, "yukawa": kernel_yukawa, "log_skew": kernel_log_skew,
-           "gauss": kernel_gauss}
+           "gauss": kernel_gauss, "ifmm_d1e-3": kernel_ifmm(1e-3), "ifmm_d1e-2": kernel_ifmm(1e-2)}
 
 
 def default_diag(kernel: str, n: int, dim: int) -> float:
@@ -117,6 +128,8 @@ def default_diag(kernel: str, n: int, dim: int) -> float:
         return 2.0 * n ** (1.0 / 3.0)
     if kernel == "gauss":
         return 3.0
+    if kernel.startswith("ifmm_"):
+        return 1.0
     raise ValueError(kernel)
 
 

@@ -17,6 +17,9 @@ at least one of them:
 * IR / GMRES with the factored S reach 1e-10 (§5.5);
 * log|det A| from the pivots of S equals LAPACK's slogdet of the dense A and
   of the dense S, with the sign of det S (§5.3);
+* the threshold incomplete LU (ILUt) of §5.5 matches a hand-worked example,
+  is the exact LU without dropping, keeps no entry below its row threshold,
+  and preconditions §5.5's example as the paper describes;
 * the block Cholesky of an SPD S reproduces S, equals LAPACK's dense
   Cholesky factor of S in elimination order (the factor is unique), solves
   like a dense solve, and refuses an indefinite S.
@@ -29,6 +32,7 @@ from paper_1705_04601_gb300 import synth
 from oracle import factor as ofa
 from oracle import h2 as oh2
 from oracle import householder as ohh
+from oracle import ilu as oilu
 from oracle import iterate as oit
 from oracle import sparsify as osp
 
@@ -450,3 +454,77 @@ def test_tile_pivoted_block_lu_solves(name):
     assert abs(lo - la) <= 1e-9 * max(1.0, abs(la))
     if h.col_leaf_basis is None:
         assert so == int(sa)
+
+
+# --------------------------------------------------------------------------
+# threshold incomplete LU (ILUt), the preconditioner of §5.5
+# --------------------------------------------------------------------------
+
+
+def test_ilut_hand_example():
+    """A 3 x 3 arrow matrix worked by hand.  Row 1: multiplier 1/4, then
+    u11 = 4 - 1/4 = 3.75 and the fill u12 = -1/4.  With tau = 0.1 the
+    threshold of row 1 is 0.1 * ||(1, 4, 0)|| = 0.412 > 1/4, so the multiplier
+    itself is dropped and row 1 of U stays (0, 4, 0)."""
+    A = np.array([[4.0, 1.0, 1.0], [1.0, 4.0, 0.0], [1.0, 0.0, 4.0]])
+    L, U = oilu.ilut(A, 0.01)
+    assert L[1, 0] == 0.25 and U[1, 1] == 3.75 and U[1, 2] == -0.25
+    assert L[2, 0] == 0.25 and abs(L[2, 1] - (-0.25 / 3.75)) < 1e-15
+    assert abs(U[2, 2] - (4.0 - 0.25 - 0.25 * 0.25 / 3.75)) < 1e-14
+    L, U = oilu.ilut(A, 0.1)
+    assert L[1, 0] == 0.0 and np.array_equal(U[1], [0.0, 4.0, 0.0])
+
+
+def test_ilut_without_dropping_is_the_exact_lu():
+    h, b, sp, A = case("log1k")
+    fa = oilu.factor_ilut(h, sp, 0.0)
+    Ap = osp.dense_S(sp)[np.ix_(fa.perm, fa.perm)]
+    assert np.array_equal(fa.L, np.tril(fa.L)) and np.all(np.diag(fa.L) == 1.0)
+    assert np.array_equal(fa.U, np.triu(fa.U))
+    assert np.linalg.norm(fa.L @ fa.U - Ap) <= 1e-12 * np.linalg.norm(Ap)   # the LU without pivoting is unique
+    c = osp.apply_T(sp, h, b)
+    yd = np.linalg.solve(osp.dense_S(sp), c)
+    assert np.linalg.norm(oilu.solve_S_ilu(fa, c) - yd) <= 1e-9 * np.linalg.norm(yd)
+
+
+def test_ilut_keeps_no_entry_below_the_row_threshold():
+    h, b, sp, A = case("small")
+    tau = 1e-2
+    fa = oilu.factor_ilut(h, sp, tau)
+    Ap = osp.dense_S(sp)[np.ix_(fa.perm, fa.perm)]
+    thr = tau * np.linalg.norm(Ap, axis=1)
+    off_l = np.abs(np.tril(fa.L, -1))
+    off_u = np.abs(np.triu(fa.U, 1))
+    assert np.all((off_l == 0) | (off_l >= thr[:, None]))
+    assert np.all((off_u == 0) | (off_u >= thr[:, None]))
+    full = oilu.factor_ilut(h, sp, 0.0)
+    assert np.count_nonzero(fa.L) + np.count_nonzero(fa.U) < np.count_nonzero(full.L) + np.count_nonzero(full.U)
+
+
+def test_ilut_preconditions_the_example_of_section_5_5():
+    """§5.5's matrix (3D points, 1 on the diagonal, |r|/d inside d, d/|r|
+    beyond): GMRES on the H^2 product preconditioned by the ILUt of S reaches
+    1e-10 at the paper's drop tolerances 1e-2 and 2e-2.  As §5.5 describes,
+    the larger d (worse conditioned) needs more steps, and the larger tau
+    gives sparser factors and more steps."""
+    steps, nnz = {}, {}
+    for kern in ("ifmm_d1e-3", "ifmm_d1e-2"):
+        h, b = synth.make_small(1500, kernel=kern, leaf=40, tol=1e-6, seed=12, dim=3, nrhs=1)
+        sp = osp.sparsify(h)
+        mv = oh2.Matvec(h)
+        for tau in (1e-2, 2e-2):
+            fa = oilu.factor_ilut(h, sp, tau)
+            cnt = [0]
+
+            def pre(v, fa=fa, h=h, sp=sp):
+                cnt[0] += 1
+                return oilu.precondition(h, sp, fa, v)
+
+            x, hist = oit.gmres(mv, pre, b[:, 0], tol=1e-10, restart=30, maxit=300)
+            assert oit.rel_residual(mv, b[:, 0], x) <= 2e-10
+            steps[kern, tau] = cnt[0]
+            nnz[kern, tau] = np.count_nonzero(fa.L) + np.count_nonzero(fa.U)
+    for kern in ("ifmm_d1e-3", "ifmm_d1e-2"):
+        assert nnz[kern, 2e-2] < nnz[kern, 1e-2] and steps[kern, 2e-2] >= steps[kern, 1e-2]
+    for tau in (1e-2, 2e-2):
+        assert steps["ifmm_d1e-2", tau] > steps["ifmm_d1e-3", tau]
