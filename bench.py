@@ -21,8 +21,8 @@ Inputs are resident in HBM when the timed region starts (the close blocks are
 443 MB, larger than the 129 MB L2, so no flush is needed); ``e2e`` repeats the
 mixed step from pinned host buffers with the copies inside the timed region.
 
-``--impl reference`` times the CPU FP64 oracle instead (the reference arm of
-this build): each step runs the oracle's full pipeline on a bounded sample.
+``--impl reference`` times the CPU FP64 oracle instead (the reference arm):
+each step runs the oracle's full pipeline on a bounded sample.
 Under torchrun every rank solves an independent replica; rank 0 prints one
 JSON line.
 """
@@ -44,7 +44,7 @@ sys.path.insert(0, ROOT)
 METRIC = "time-to-solution at rel. residual 1e-10 (s), mixed vs FP64 GPU; factor GFLOP/s"
 CPU_SAMPLE_N = 16384
 
-# Nominal peaks used where the measured file has no entry:
+# Nominal peaks, used where MEASURED_PEAKS.json has no entry:
 #   FP32 SIMT  = 152 SMs x 128 lanes x 2 flop x 2.070 GHz
 #   FP64       = 1.25 TFLOP/s (GB300 nominal)
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12

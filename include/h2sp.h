@@ -52,7 +52,7 @@ typedef enum {
   H2SP_ESTATE = -5,     /* calls in the wrong order (e.g. solve before factor) */
   H2SP_ENOCONV = -6,    /* the iteration did not reach the tolerance in maxit */
   H2SP_ETIMEOUT = -7,   /* a bounded device wait gave up */
-  H2SP_EUNSUPPORTED = -8 /* a valid input outside what this build supports (block too large) */
+  H2SP_EUNSUPPORTED = -8 /* a valid input outside what the library supports (block too large) */
 } h2sp_status;
 
 /* Precision of the factorization of S (h2sp_factor). */

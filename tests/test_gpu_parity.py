@@ -1,6 +1,6 @@
 """GPU parity of the CUDA path against the CPU oracle, through the C ABI.
 
-Bars (spec tolerances):
+Bars:
 * integer structure (S node order, VBR pattern, elimination structure): equal;
 * FP64 values: per block of S, ||S_gpu - S_oracle||_F <= 1e-10 ||row block of S_oracle||_F;
   per cluster, ||Q_gpu - Q_oracle||_F <= 1e-10 ||Q||_F; solutions
