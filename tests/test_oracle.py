@@ -52,6 +52,8 @@ def case(name):
         "tiny": dict(n=48, kernel="log", leaf=64, tol=1e-8, seed=6),
         "small": dict(n=256, kernel="log", leaf=16, tol=1e-8, seed=7),
         "gauss3d": dict(n=1500, kernel="gauss", leaf=40, tol=1e-8, seed=10, dim=3),
+        # 3D leaves above 64 points (octree leaf <= 128), as the streaming kernels take them
+        "yukawa3d": dict(n=3000, kernel="yukawa", leaf=128, tol=1e-6, seed=13, dim=3),
     }[name]
     h, b = synth.make_small(spec["n"], kernel=spec["kernel"], leaf=spec["leaf"], tol=spec["tol"],
                             seed=spec["seed"], dim=spec.get("dim", 2), nrhs=2)
@@ -98,7 +100,7 @@ def test_householder_closed_forms():
 # sparsification A = U S V^T (§2, §4)
 # --------------------------------------------------------------------------
 
-CASES = ["log1k", "log4k", "skew1k", "raw1k", "gauss1k", "inv3d", "small", "tiny"]
+CASES = ["log1k", "log4k", "skew1k", "raw1k", "gauss1k", "inv3d", "small", "tiny", "yukawa3d"]
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -132,7 +134,7 @@ def test_U_is_block_diagonal_times_permutation(name):
         assert np.abs(cols[hi:]).max(initial=0.0) == 0.0
 
 
-@pytest.mark.parametrize("name", ["log1k", "log4k", "skew1k", "inv3d", "small"])
+@pytest.mark.parametrize("name", ["log1k", "log4k", "skew1k", "inv3d", "small", "yukawa3d"])
 def test_pattern_rule(name):
     h, b, sp, A = case(name)
     sch = sp.sch
@@ -230,7 +232,7 @@ def test_h2_approximates_kernel_and_matvec(name):
 # --------------------------------------------------------------------------
 
 
-@pytest.mark.parametrize("name", ["log1k", "log4k", "skew1k", "raw1k", "inv3d", "small", "tiny"])
+@pytest.mark.parametrize("name", ["log1k", "log4k", "skew1k", "raw1k", "inv3d", "small", "tiny", "yukawa3d"])
 def test_block_lu_solve_matches_dense(name):
     h, b, sp, A = case(name)
     fa = ofa.factor(h, sp)
