@@ -424,12 +424,12 @@ def test_fp32_sparsify_products_stay_fp64_vectors():
 
 
 def test_fp32_factor_backward_error():
-    """The FP32 block LU of S is a backward-stable factorization, also where
-    the panels pivot by tournament (supernodes of more than one block of
-    candidate rows, as in the top fronts here): y = S^{-1} c from the FP32
-    factors has a normwise backward error ||c - S y|| / (||S||_F ||y|| + ||c||)
-    of FP32 order (u = 6e-8 times a modest growth), required <= 1e-5; a
-    wrong pivot row, a stale update or a misplaced row gives O(1e-2) or more."""
+    """The FP32 block LU of S is a backward-stable factorization, also on the
+    large top fronts here (panels on thread-block clusters, block-end updates
+    on the tensor cores): y = S^{-1} c from the FP32 factors has a normwise
+    backward error ||c - S y|| / (||S||_F ||y|| + ||c||) of FP32 order
+    (u = 6e-8 times a modest growth), required <= 1e-5; a wrong pivot row, a
+    stale update or a misplaced row gives O(1e-2) or more."""
     n = 16384
     h, _ = synth.make_workload("log2d_n65536", n=n)
     hd = H.h2sp_sparsify(H.H2Input(h))
