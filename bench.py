@@ -192,7 +192,7 @@ def roofline(prof, timed_launches_ok=True, sparsify_fp32=False):
     elif cls in sp_cls or cls == "h2_matvec":
         achieved = p["work"] / (p["ms"] * 1e-3) / 1e12
         out.update(bound="alu", achieved=achieved, peak=FP64_TFLOPS, unit="TFLOP/s",
-                   peak_source="nominal GB300 FP64 (1.25 TFLOP/s); no measured FP64 peak on this pool")
+                   peak_source="nominal GB300 FP64 (1.25 TFLOP/s); no measured FP64 peak available")
     else:
         achieved = p["work"] / (p["ms"] * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)

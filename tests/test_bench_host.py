@@ -67,3 +67,30 @@ def test_reference_arm_json_line(monkeypatch):
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == out["value"] and "N=2048" in cb["sample"]
     e2e = out["e2e"]
     assert e2e["value"] == out["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def _prof(**ms_work):
+    return {c: {"ms": ms, "work": work, "timed": 10, "launches": 10} for c, (ms, work) in ms_work.items()}
+
+
+def test_roofline_picks_the_dominant_class_and_its_bound():
+    sys.path.insert(0, ROOT)
+    import bench
+    # panel dominant: FP32 flops on the CUDA cores
+    r = bench.roofline(_prof(panel=(50.0, 1.5e10), apply=(5.0, 1e9)))
+    assert r["kernel"] == "panel" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["peak"] == pytest.approx(bench.FP32_SIMT_TFLOPS)
+    assert r["achieved"] == pytest.approx(1.5e10 / 50e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["traffic"] is None                       # no capture registered
+    # the FP64 H^2 product: FP64 pipe
+    r = bench.roofline(_prof(h2_matvec=(20.0, 2.3e10), panel=(1.0, 1e9)))
+    assert r["bound"] == "alu" and r["peak"] == bench.FP64_TFLOPS
+    # a byte-counted class: HBM
+    r = bench.roofline(_prof(apply=(30.0, 6e10), panel=(1.0, 1e9)))
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(6e10 / 30e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    # FP32 sparsification kernels are FP32-ALU bound, FP64 ones FP64-bound
+    assert bench.roofline(_prof(transform=(9.0, 1e10)), sparsify_fp32=True)["peak"] == pytest.approx(bench.FP32_SIMT_TFLOPS)
+    assert bench.roofline(_prof(transform=(9.0, 1e10)), sparsify_fp32=False)["peak"] == bench.FP64_TFLOPS
