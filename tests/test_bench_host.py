@@ -94,3 +94,89 @@ def test_roofline_picks_the_dominant_class_and_its_bound():
     # FP32 sparsification kernels are FP32-ALU bound, FP64 ones FP64-bound
     assert bench.roofline(_prof(transform=(9.0, 1e10)), sparsify_fp32=True)["peak"] == pytest.approx(bench.FP32_SIMT_TFLOPS)
     assert bench.roofline(_prof(transform=(9.0, 1e10)), sparsify_fp32=False)["peak"] == bench.FP64_TFLOPS
+
+
+_FAKED_RUN = r'''
+import argparse
+import json
+import sys
+import types
+
+import numpy as np
+import torch
+
+sys.path.insert(0, sys.argv[1])
+import bench  # noqa: E402
+from paper_1705_04601_gb300 import build, synth  # noqa: E402
+from paper_1705_04601_gb300 import h2sp as H  # noqa: E402
+
+build.build = lambda: None
+_real_make = synth.make_workload
+synth.make_workload = lambda name, n=None, **kw: _real_make(name, n=2048)
+
+
+class Ev:
+    def record(self, s=None):
+        pass
+
+    def elapsed_time(self, o):
+        return 10.0
+
+
+torch.cuda.Event = lambda enable_timing=True: Ev()
+torch.cuda.synchronize = lambda *a, **k: None
+torch.cuda.current_stream = lambda *a, **k: object()
+torch.cuda.current_device = lambda: 0
+torch.Tensor.cuda = lambda self, *a, **k: self
+torch.Tensor.pin_memory = lambda self, *a, **k: self
+
+
+class FakeHandle:
+    def close(self):
+        pass
+
+
+class FakeInput:
+    def __init__(self, h, device="cuda", nonblocking_from=None):
+        self.h = h
+
+
+classes = H.KERNEL_CLASSES
+H.H2Input = FakeInput
+H.h2sp_analyze = lambda inp: FakeHandle()
+H.h2sp_sparsify_analyzed = lambda an, inp, stream=None, flags=0: FakeHandle()
+H.h2sp_factor = lambda hd, prec, stream=None: None
+H.h2sp_solve = lambda hd, b, x, mode=0, tol=1e-10, maxit=50, restart=30, stream=None: types.SimpleNamespace(
+    iters=5, rel_residual=5e-11, status=0)
+H.h2sp_profile = lambda hd, timing=-1, reset=False: {
+    c: {"launches": 3, "timed": 3, "ms": (5.0 if c == "panel" else 1.0), "work": 1e9} for c in classes}
+H.h2sp_query = lambda hd: {"factor_flops": 3e12}
+H.h2sp_apply = lambda hd, op, x, y, stream=None: y.copy_(x)
+
+args = argparse.Namespace(gpus=1, steps=2, warmup=1, impl="ours", workload="log2d_n65536", fp64_steps=1,
+                          sparsify_prec="fp32", solver="gmres", no_e2e=False, no_cpu_baseline=True)
+out = bench.run_ours(args, 1, 0, 0)
+print(json.dumps(out))
+'''
+
+
+def test_bench_json_line_with_faked_library(tmp_path):
+    """bench.run_ours end to end on the CPU, with the library calls and the
+    CUDA events faked (a child process, so the fakes stay there): the JSON
+    line carries every field of the measurement contract."""
+    import subprocess
+    src = tmp_path / "faked_run.py"
+    src.write_text(_FAKED_RUN)
+    r = subprocess.run([sys.executable, str(src), ROOT], capture_output=True, text=True, timeout=600,
+                       env=dict(os.environ, PYTHONPATH=ROOT))
+    assert r.returncode == 0, r.stderr[-3000:]
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "clocks", "gpu_launches",
+              "cpu_baseline", "factor_gflops_fp32", "factor_gflops_fp64"):
+        assert k in out, k
+    assert out["higher_is_better"] is False and out["steps"] == 2 and out["warmup"] == 1
+    assert out["config"]["workload"] == "log2d_n65536"
+    assert out["roofline"]["kernel"] == "panel" and out["roofline"]["frac"] > 0
+    assert set(out["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
+    assert out["factor_gflops_fp64"] > 0 and out["gpu_launches"] > 0
