@@ -358,7 +358,9 @@ int h2sp_profile(h2sp_handle *h, int32_t timing, int32_t reset, h2sp_kernel_time
  * so nothing needs clearing), so calls that overlap on the GPU -- on
  * different streams, or from different host threads -- race; serialise them.
  * h is a handle from h2sp_sparsify (its device structure is read, not
- * changed); x (ldx >= n) and y (ldy >= n) are device arrays of nrhs columns.
+ * changed), and the current device must be the one it was built on
+ * (H2SP_EINVAL otherwise, with a message in h2sp_last_cuda_error); x
+ * (ldx >= n) and y (ldy >= n) are device arrays of nrhs columns.
  * Enqueued on `stream`; does not synchronise.
  */
 int h2sp_h2_matvec_static(const h2sp_handle *h, int32_t nrhs, const double *x, int64_t ldx, double *y, int64_t ldy,

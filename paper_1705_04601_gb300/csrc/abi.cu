@@ -138,6 +138,7 @@ struct h2sp_handle {
   // factor
   int prec = -1;
   void *fronts = nullptr;
+  size_t fronts_esz = 0;  // element size the front buffer is sized for (4: FP32 fronts only, 8: either)
   FrontDev *fr = nullptr;
   int32_t *piv = nullptr, *perm = nullptr, *swaps = nullptr, *fidx = nullptr, *fmap = nullptr;
   AItem *asm_items = nullptr;
@@ -181,8 +182,19 @@ struct h2sp_handle {
     if (!v.empty()) ck(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, stream));
     return d;
   }
+  // free one buffer of `allocs` before the handle is released
+  void free_one(void *p) {
+    for (size_t i = 0; i < allocs.size(); ++i)
+      if (allocs[i] == p) {
+        cudaFreeAsync(p, stream);
+        allocs.erase(allocs.begin() + long(i));
+        return;
+      }
+  }
   LuAsync la;  // look-ahead stream and events of the block LU (created on first use)
   uint8_t *tmaps = nullptr;  // TMA descriptors of the FP32 fronts (built on the first FP32 factorization)
+  uint8_t *tmaps_buf = nullptr;     // their device storage
+  const void *tmaps_base = nullptr;  // the front buffer they were encoded for
   float *pack = nullptr;     // packed GEMM operands of the blocked FP32 LU (3 buffers of the largest level)
   int32_t last_prec = -1;    // precision of the last h2sp_factor (h2sp_refactor repeats it)
   cudaGraphExec_t graph_exec = nullptr;  // sparsification + factorization, captured by h2sp_refactor
@@ -246,11 +258,14 @@ bool lookahead_enabled() {
 }
 
 void init_pool_once() {
-  static bool done = false;
-  if (done) return;
-  done = true;
+  // once per device: keep freed memory in that device's default pool
+  static std::mutex mu;
+  static bool done[128] = {};
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return;
+  done[dev] = true;
   cudaMemPool_t pool;
   if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
     uint64_t thr = UINT64_MAX;  // keep freed memory in the pool between calls of this process
@@ -1106,9 +1121,16 @@ void copy_out(h2sp_handle *h, double *dst, const void *src, int64_t n) {
 void factor_prepare(h2sp_handle *h, int32_t prec) {
   const Plan &p = (*h->plan_ptr);
   cudaStream_t s = h->stream;
-  if (h->fronts == nullptr) {
-    // sized for FP64 so that a later factorization in either precision reuses it
-    h->fronts = h->alloc<double>(size_t(std::max<int64_t>(p.front_elems, 1)));
+  // the fronts are sized by the precision of the factorization: FP32 fronts
+  // take half the memory of FP64 ones; a later FP64 factorization of the same
+  // handle replaces the buffer by a wider one (which also holds FP32 fronts)
+  const size_t esz = prec == H2SP_FP64 ? sizeof(double) : sizeof(float);
+  if (h->fronts == nullptr || h->fronts_esz < esz) {
+    if (h->fronts != nullptr) h->free_one(h->fronts);
+    h->fronts = h->alloc<uint8_t>(size_t(std::max<int64_t>(p.front_elems, 1)) * esz);
+    h->fronts_esz = esz;
+  }
+  if (h->piv == nullptr) {
     h->piv = h->alloc<int32_t>(size_t(std::max<int64_t>(p.piv_elems, 1)));
     h->perm = h->alloc<int32_t>(size_t(std::max<int64_t>(p.piv_elems, 1)));
     size_t maxn = 1;
@@ -1126,13 +1148,18 @@ void factor_prepare(h2sp_handle *h, int32_t prec) {
     ck(cudaEventCreateWithFlags(&h->la.panel, cudaEventDisableTiming));
     ck(cudaEventCreateWithFlags(&h->la.done, cudaEventDisableTiming));
   }
-  if (prec == H2SP_FP32 && h->tmaps == nullptr && tma_enabled() && !p.fronts.empty()) {
-    uint8_t *m = h->alloc<uint8_t>(p.fronts.size() * kTmapBytes);
+  if (prec == H2SP_FP32 && tma_enabled() && !p.fronts.empty() && h->tmaps_base != h->fronts) {
+    // (re-)encode the descriptors whenever the front buffer is new
+    h->tmaps = nullptr;
+    if (h->tmaps_buf == nullptr) h->tmaps_buf = h->alloc<uint8_t>(p.fronts.size() * kTmapBytes);
     ck(cudaStreamSynchronize(s));  // the allocation is usable by the synchronous copy
-    if (make_front_tmaps(p.fronts.data(), int(p.fronts.size()), static_cast<float *>(h->fronts), m) == cudaSuccess)
-      h->tmaps = m;
+    if (make_front_tmaps(p.fronts.data(), int(p.fronts.size()), static_cast<float *>(h->fronts), h->tmaps_buf) ==
+        cudaSuccess) {
+      h->tmaps = h->tmaps_buf;
+      h->tmaps_base = h->fronts;
+    }
     cudaGetLastError();
-    if (h->tmaps != nullptr && h->sdev->max_pack_tiles > 0)
+    if (h->tmaps != nullptr && h->pack == nullptr && h->sdev->max_pack_tiles > 0)
       h->pack = h->alloc<float>(size_t(3 * h->sdev->max_pack_tiles * kPackTileFloats));
   }
 }
@@ -1616,6 +1643,14 @@ int h2sp_h2_matvec_static(const h2sp_handle *h, int32_t nrhs, const double *x, i
     g_cuda_err = "h2sp_h2_matvec_static: needs " + std::to_string(need) + " doubles of workspace, the static array has " +
                  std::to_string(kStaticScratchElems);
     return H2SP_EUNSUPPORTED;
+  }
+  // the structure pointers belong to the device the handle was built on; the
+  // static array's address is looked up for the current device
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || !h->sdev || dev != h->sdev->device) {
+    g_cuda_err = "h2sp_h2_matvec_static: the current device (" + std::to_string(dev) +
+                 ") is not the device the handle was built on (" + std::to_string(h->sdev ? h->sdev->device : -1) + ")";
+    return H2SP_EINVAL;
   }
   try {
     double *scratch = nullptr;

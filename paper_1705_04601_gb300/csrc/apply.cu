@@ -531,7 +531,7 @@ __global__ void k_cast(const A *__restrict__ a, int64_t lda, B *__restrict__ b, 
 }
 
 inline unsigned grid_for(int64_t n, int per = 256) {
-  return unsigned(std::max<int64_t>(1, std::min<int64_t>((n + per - 1) / per, 4 * 152)));
+  return unsigned(std::max<int64_t>(1, std::min<int64_t>((n + per - 1) / per, 4 * device_sms())));
 }
 
 }  // namespace
@@ -542,12 +542,7 @@ cudaError_t launch_apply_qt(const ApItem *items, int n, const T *Q, const T *x, 
   if (n == 0) return cudaSuccess;
   if (max_m > kMaxBlock) {
     const size_t smem = sizeof(T) * size_t(max_m) * kRhs;
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_apply_qt_large<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           int(sizeof(T) * kMaxLargeBlock * kRhs));
-      attr = true;
-    }
+    if (cudaError_t ea = smem_attr((const void *)k_apply_qt_large<T>, int(smem)); ea != cudaSuccess) return ea;
     for (int r0 = 0; r0 < nrhs; r0 += kRhs)
       k_apply_qt_large<T><<<n, 128, smem, s>>>(items, Q, x + r0 * ldx, ldx, ys + r0 * ldys, ldys,
                                                xn ? xn + r0 * ldxn : nullptr, ldxn, std::min(kRhs, nrhs - r0), max_m);
@@ -565,12 +560,7 @@ cudaError_t launch_apply_q(const ApItem *items, int n, const T *Q, const T *xn, 
   if (n == 0) return cudaSuccess;
   if (max_m > kMaxBlock) {
     const size_t smem = sizeof(T) * size_t(max_m) * kRhs;
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_apply_q_large<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           int(sizeof(T) * kMaxLargeBlock * kRhs));
-      attr = true;
-    }
+    if (cudaError_t ea = smem_attr((const void *)k_apply_q_large<T>, int(smem)); ea != cudaSuccess) return ea;
     for (int r0 = 0; r0 < nrhs; r0 += kRhs)
       k_apply_q_large<T><<<n, 128, smem, s>>>(items, Q, xn ? xn + r0 * ldxn : nullptr, ldxn, ys + r0 * ldys, ldys,
                                               x + r0 * ldx, ldx, std::min(kRhs, nrhs - r0), max_m);

@@ -1438,16 +1438,7 @@ __global__ void k_bwd_scatter(const FrontDev *__restrict__ fr, const int32_t *__
 
 inline int cdiv(int64_t a, int64_t b) { return int((a + b - 1) / b); }
 
-inline int num_sms() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        n <= 0)
-      n = 152;
-  }
-  return n;
-}
+inline int num_sms() { return device_sms(); }
 
 
 // ---------------- flag-synchronised block sweeps ----------------
@@ -1871,11 +1862,7 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
   using G = GemmCfg<T>;
   auto gemm = k_gemm_update<T, G::BM, G::BN, G::TM, G::TN, NB>;
   const size_t gsmem = sizeof(T) * NB * (G::BM + G::BN + 2 * (16 / sizeof(T)));
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gsmem));
-    attr = true;
-  }
+  if (cudaError_t ea = smem_attr((const void *)gemm, int(gsmem)); ea != cudaSuccess) return ea;
   bool tc = false;
   if constexpr (std::is_same<T, float>::value) tc = use_tensor_core_gemm();
   const int W = tc ? kTcTile : G::BN;  // width of the first column tile (holds the next panel)
@@ -2015,12 +2002,9 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
         if ((e = cudaStreamWaitEvent(ms, la->next, 0)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(rs, la->next, 0)) != cudaSuccess) return e;
       }
-      static bool blk_attr = false;
-      if (!blk_attr) {
-        cudaFuncSetAttribute(k_blk_swap_trsm<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(sizeof(float) * 64 * KB));
-        blk_attr = true;
-      }
+      if (cudaError_t ea = smem_attr((const void *)k_blk_swap_trsm<KB>, int(sizeof(float) * 64 * KB));
+          ea != cudaSuccess)
+        return ea;
       auto fl_trsm = [&](int j0, int lo_col, int hi_col) {  // U12 flops of a panel step over a column range
         double f = 0.0;
         if (prof->timing)
@@ -2183,11 +2167,7 @@ cudaError_t launch_make_perm(const FrontDev *fr, int nfront, int max_s, const in
   if (nfront == 0) return cudaSuccess;
   const int cap = 40 * 1024;  // entries staged in shared memory (160 KB)
   const size_t smem = sizeof(int32_t) * size_t(std::min(max_s, cap));
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_make_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(int32_t) * cap));
-    attr = true;
-  }
+  if (cudaError_t ea = smem_attr((const void *)k_make_perm, int(sizeof(int32_t) * cap)); ea != cudaSuccess) return ea;
   const size_t e0 = prof->begin();
   k_make_perm<<<nfront, 256, smem, s>>>(fr, piv, perm, std::min(max_s, cap));
   prof->end(P_OTHER, 1, e0, 0.0);
@@ -2288,12 +2268,8 @@ cudaError_t launch_logdet(const FrontDev *fr, int nfront, const T *fronts, const
 template <typename T>
 size_t step_smem() {
   const size_t bytes = sizeof(T) * (kBS * kBS + 2 * kBS * kMaxRhs);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_fwd_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-    cudaFuncSetAttribute(k_bwd_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-    attr = true;
-  }
+  smem_attr((const void *)k_fwd_step<T>, int(bytes));
+  smem_attr((const void *)k_bwd_step<T>, int(bytes));
   return bytes;
 }
 

@@ -781,12 +781,8 @@ size_t gemm_tc_smem() { return size_t(24) * kTileFloats + 1024; }
 cudaError_t launch_gemm_tc(const FrontDev *fr, int j0, int nfront, int max_f, float *fronts, int *err,
                            cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps,
                            bool any_full, bool any_partial) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gemm_tc_smem()));
-    cudaFuncSetAttribute(k_gemm_tc_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gemm_tc_smem()));
-    attr = true;
-  }
+  if (cudaError_t ea = smem_attr((const void *)k_gemm_tc, int(gemm_tc_smem())); ea != cudaSuccess) return ea;
+  if (cudaError_t ea = smem_attr((const void *)k_gemm_tc_tma, int(gemm_tc_smem())); ea != cudaSuccess) return ea;
   const int rest = max_f - j0 - 1;
   if (rest <= 0) return cudaSuccess;
   const int rt = (rest + kTcM - 1) / kTcM;
@@ -811,11 +807,7 @@ cudaError_t launch_gemm_tc(const FrontDev *fr, int j0, int nfront, int max_f, fl
 
 cudaError_t launch_gemm_tc_inner(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
                                  cudaStream_t s, int sm_budget) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gemm_tc_smem()));
-    attr = true;
-  }
+  if (cudaError_t ea = smem_attr((const void *)k_gemm_tc, int(gemm_tc_smem())); ea != cudaSuccess) return ea;
   const int rest = max_f - j0 - 1;
   const int cols = (j0 / kb) * kb + kb - (j0 + kTcK);  // columns left in the outer block (at most)
   if (rest <= 0 || cols <= 0) return cudaSuccess;
@@ -850,11 +842,7 @@ size_t gemm_ws_smem() { return size_t(kWsStages) * 4 * kPkTile * sizeof(float) +
 cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
                               cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps,
                               const float *apack, const float *bpack) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gemm_tc_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gemm_ws_smem()));
-    attr = true;
-  }
+  if (cudaError_t ea = smem_attr((const void *)k_gemm_tc_ws, int(gemm_ws_smem())); ea != cudaSuccess) return ea;
   (void)maps;
   if (apack == nullptr || bpack == nullptr) return cudaErrorInvalidValue;
   const int rest = max_f - j0 - 1;

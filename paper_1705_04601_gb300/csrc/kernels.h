@@ -1,11 +1,47 @@
 // Launchers of the h2sp kernels (host side declarations).
 #pragma once
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include <cuda_runtime.h>
 
 #include "internal.h"
 
 namespace h2sp {
+
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current
+// device.  The attribute belongs to one device, so it is remembered per
+// (kernel, device), under a lock shared by every host thread.
+inline cudaError_t smem_attr(const void *fn, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, int> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  int &have = done[{fn, dev}];
+  if (have >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) have = bytes;
+  return e;
+}
+
+// Streaming multiprocessors of the current device (cached per device).
+inline int device_sms() {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 1;
+  cache[dev] = n;
+  return n;
+}
 
 // ---- sparsification (sparsify.cu).  Householder completions and stacked
 // bases are FP64; the products that land in S (and in the level buffers that

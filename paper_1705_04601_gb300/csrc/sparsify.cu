@@ -413,11 +413,7 @@ cudaError_t launch_householder(const QItem *items, int n, const double *w_in, co
                                double *Rr, int max_m, int max_k, cudaStream_t s, Prof *prof) {
   if (n == 0) return cudaSuccess;
   size_t smem = sizeof(double) * (size_t(max_m) * max_k + size_t(max_m) * max_m + kMaxRank + 1 + 64);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(k_householder, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_done = true;
-  }
+  if (cudaError_t ea = smem_attr((const void *)k_householder, int(smem)); ea != cudaSuccess) return ea;
   const size_t e0 = prof->begin();
   k_householder<<<n, kThreads, smem, s>>>(items, w_in, w_buf, Q, Rr);
   prof->end(P_HOUSEHOLDER, 1, e0, 0.0);
@@ -428,11 +424,7 @@ cudaError_t launch_householder_large(const QItem *items, int n, const double *w_
                                      double *Rr, int max_m, int max_k, cudaStream_t s, Prof *prof) {
   if (n == 0) return cudaSuccess;
   const size_t smem = sizeof(double) * (size_t(max_m) * max_k + kMaxRank + 1 + 64);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(k_householder_large, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    attr_done = true;
-  }
+  if (cudaError_t ea = smem_attr((const void *)k_householder_large, int(smem)); ea != cudaSuccess) return ea;
   const size_t e0 = prof->begin();
   k_householder_large<<<n, kThreads, smem, s>>>(items, w_in, w_buf, Q, Rr);
   prof->end(P_HOUSEHOLDER, 1, e0, 0.0);
@@ -453,11 +445,7 @@ cudaError_t launch_coupling(const CItem *items, int n, const double *Rr, const d
                             W *const *dst_base, int max_k, cudaStream_t s, Prof *prof) {
   if (n == 0) return cudaSuccess;
   size_t smem = sizeof(double) * 4 * size_t(max_k) * max_k;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(k_coupling<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_done = true;
-  }
+  if (cudaError_t ea = smem_attr((const void *)k_coupling<W>, int(smem)); ea != cudaSuccess) return ea;
   const size_t e0 = prof->begin();
   k_coupling<W><<<n, 128, smem, s>>>(items, Rr, Rrc, Dc, dst_base);
   prof->end(P_COUPLING, 1, e0, 0.0);
@@ -469,11 +457,7 @@ cudaError_t launch_transform(const XItem *items, int n, const void *const *src_b
                              const double *Qcol, W *const *dst_base, cudaStream_t s, Prof *prof, double flops) {
   if (n == 0) return cudaSuccess;
   size_t smem = sizeof(W) * 3 * size_t(kMaxBlock) * kMaxBlock;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(k_transform<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    attr_done = true;
-  }
+  if (cudaError_t ea = smem_attr((const void *)k_transform<W>, int(smem)); ea != cudaSuccess) return ea;
   const size_t e0 = prof->begin();
   k_transform<W><<<n, kThreads, smem, s>>>(items, src_base, Qrow, Qcol, dst_base);
   prof->end(P_TRANSFORM, 1, e0, flops);
@@ -486,12 +470,7 @@ cudaError_t launch_transform_large(const XItem *items, int n, const void *const 
                                    Prof *prof, double flops) {
   if (n == 0) return cudaSuccess;
   const size_t smem = sizeof(W) * size_t(kSlab) * size_t(max_rows + max_cols);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(k_transform_large<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(sizeof(W) * kSlab * 2 * kMaxLargeBlock));
-    attr_done = true;
-  }
+  if (cudaError_t ea = smem_attr((const void *)k_transform_large<W>, int(smem)); ea != cudaSuccess) return ea;
   const size_t e0 = prof->begin();
   k_transform_large<W><<<n, kThreads, smem, s>>>(items, src_base, Qrow, Qcol, dst_base);
   prof->end(P_TRANSFORM, 1, e0, flops);

