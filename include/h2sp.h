@@ -55,10 +55,13 @@ typedef enum {
   H2SP_EUNSUPPORTED = -8 /* a valid input outside what the library supports (block too large) */
 } h2sp_status;
 
-/* Precision of the factorization of S (h2sp_factor). */
+/* Precision and kind of the factorization of S (h2sp_factor).  Bit 0: FP32
+ * fronts; bit 1: block Cholesky S = L L^T instead of the block LU. */
 typedef enum {
-  H2SP_FP64 = 0, /* FP64 fronts, FP64 arithmetic */
-  H2SP_FP32 = 1  /* FP32 fronts, FP32 arithmetic (a preconditioner for FP64 IR/GMRES) */
+  H2SP_FP64 = 0,      /* block LU, FP64 fronts, FP64 arithmetic */
+  H2SP_FP32 = 1,      /* block LU, FP32 fronts, FP32 arithmetic (a preconditioner for FP64 IR/GMRES) */
+  H2SP_FP64_CHOL = 2, /* block Cholesky of a symmetric positive definite S, FP64 */
+  H2SP_FP32_CHOL = 3  /* block Cholesky of a symmetric positive definite S, FP32 (tensor-core updates) */
 } h2sp_prec;
 
 /* Operators for h2sp_apply. */
@@ -169,6 +172,8 @@ typedef struct {
   double plan_seconds;            /* host time spent planning in the last h2sp_sparsify */
   int32_t sparsify_prec;          /* h2sp_prec of S (U and V are always FP64); -1 for an analysis-only handle */
   int32_t nsys;                   /* independent systems (roots at depth 0) */
+  int32_t factor_chol;            /* 1 if the current factors come from the block Cholesky */
+  double chol_flops;              /* sum over supernodes of s^3/3 + s^2 b + s b^2 (the block Cholesky's work) */
 } h2sp_stats;
 
 /*
@@ -215,7 +220,7 @@ int h2sp_analyze(const h2sp_h2_desc *desc, h2sp_handle **out);
  * method, §5.3-5.4): nested-dissection order along the cluster tree,
  * multifrontal elimination level by level, partial pivoting inside each
  * supernode's diagonal block.  `prec` selects FP64 or FP32 fronts.  FP64
- * fronts take one trailing update per 64-column panel.  FP32 fronts are
+ * fronts take one trailing update per 32-column panel.  FP32 fronts are
  * factored in 256-column outer blocks of four panels: interchanges and
  * updates stay inside the block until its end, then the other columns take
  * the interchanges, the triangular solve for U12 and one rank-256 update on
@@ -223,9 +228,24 @@ int h2sp_analyze(const h2sp_h2_desc *desc, h2sp_handle **out);
  * products); the same factorization up to rounding order.  The panels and
  * the next block's columns run on an internal high-priority stream, the rest
  * of each block end on an internal low-priority one; both are joined back to
- * `stream` before the call returns.  Synchronises the stream; returns
- * H2SP_ESINGULAR on a zero or non-finite pivot and H2SP_ETIMEOUT if a bounded
- * device wait gave up.
+ * `stream` before the call returns.
+ *
+ * H2SP_FP64_CHOL / H2SP_FP32_CHOL select the block Cholesky S = L L^T
+ * instead: the sparse package of §5.3-5.4 is a Cholesky code, and
+ * Proposition 2.1 makes S symmetric positive definite when A is.  Same
+ * supernodes and fronts, no pivoting, half the work (h2sp_stats.chol_flops):
+ * per panel the diagonal tile's Cholesky and L21 = F21 L11^-T, then the lower
+ * triangle of the trailing matrix only, C -= L21 L21^T (FP32: 256-column outer
+ * blocks with rank-256 tensor-core updates of the lower 128 x 128 tiles).
+ * The factors are stored in the LU form (unit L = L_chol D^-1, U = D L_chol^T,
+ * D = diag(L_chol)), so h2sp_solve, H2SP_OP_SINV and h2sp_logdet work as for
+ * the LU.  Needs symmetric bases (no column bases; H2SP_EINVAL otherwise) and
+ * a symmetric S; a pivot that is not positive (S not positive definite in the
+ * factor's precision) returns H2SP_ESINGULAR with a message in
+ * h2sp_last_cuda_error.
+ *
+ * Synchronises the stream; returns H2SP_ESINGULAR on a zero or non-finite
+ * pivot and H2SP_ETIMEOUT if a bounded device wait gave up.
  */
 int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream);
 
@@ -256,6 +276,26 @@ int h2sp_refactor(h2sp_handle *h, h2sp_stream stream);
  */
 int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *opts, int32_t nrhs, const double *b, int64_t ldb,
                double *x, int64_t ldx, h2sp_solve_info *info, h2sp_stream stream);
+
+/*
+ * h2sp_solve_host -- the whole path in one call, from and to HOST memory:
+ * x = A^{-1} b with A = U S V^T built (§2.1-2.3, §4.2-4.3), S factored and
+ * the system solved as h2sp_sparsify_analyzed + h2sp_factor + h2sp_solve do.
+ * Here the numeric arrays of `desc` (leaf_basis, transfer, coupling,
+ * near_block and, if present, the column arrays) and b (ldb >= n, nrhs
+ * columns, 1 <= nrhs <= 64) are HOST arrays (page-locked memory copies
+ * fastest); the call copies them to the device on `stream`, runs the
+ * sparsification (opts), the factorization (prec, an h2sp_prec) and the solve
+ * (sopts), copies the solution to the host array x (ldx >= n) and frees every
+ * device buffer it made before returning.  `an` is an analysis of the same
+ * structure (h2sp_analyze / h2sp_sparsify; checked as h2sp_sparsify_analyzed
+ * checks it) or NULL to plan one inside the call.  info (may be NULL) as for
+ * h2sp_solve.  Returns the first failing status of the three steps; with
+ * H2SP_ENOCONV x still holds the last iterate.  Synchronises the stream.
+ */
+int h2sp_solve_host(const h2sp_handle *an, const h2sp_h2_desc *desc, const h2sp_opts *opts, int32_t prec,
+                    const h2sp_solve_opts *sopts, int32_t nrhs, const double *b, int64_t ldb, double *x, int64_t ldx,
+                    h2sp_solve_info *info, h2sp_stream stream);
 
 /*
  * h2sp_logdet -- log|det A| of every independent system from the current
@@ -312,6 +352,21 @@ int h2sp_export_Q(h2sp_handle *h, int32_t cluster, int32_t col, int64_t *m, doub
  */
 int h2sp_export_structure(h2sp_handle *h, int32_t *node_level, int32_t *node_cluster, int32_t *closure,
                           int32_t *order, int32_t *sn_ptr, int32_t *bnd_ptr, int32_t *bnd, int64_t *nbnd);
+
+/*
+ * h2sp_export_front -- copy the front of supernode k (0 <= k < nsupernodes, in
+ * elimination order; rows and columns = the supernode's S rows, then its
+ * boundary rows, as h2sp_export_structure lists them) to host memory vals
+ * (f x f, column-major, FP64; FP32 factors are widened).  After h2sp_factor its
+ * first s columns hold the factors of the supernode (§5.3): unit lower L
+ * strictly below the diagonal and U on and above it, rows interchanged by the
+ * supernode's pivoting (none for the block Cholesky, whose L_chol is
+ * L D^1/2 with D = diag(U)).  The last f - s columns hold U12 above row s;
+ * the rest is work space.  *f and *s (may be NULL) receive the sizes; vals
+ * may be NULL to query them.  H2SP_ESTATE before h2sp_factor.  Synchronises
+ * the stream.
+ */
+int h2sp_export_front(h2sp_handle *h, int32_t k, int64_t *f, int64_t *s, double *vals, h2sp_stream stream);
 
 /* Per-kernel-class counters of a handle (h2sp_profile).  Classes:
  *  0 trailing GEMM update of the fronts     6 basis completions (Householder)

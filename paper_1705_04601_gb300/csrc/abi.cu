@@ -11,6 +11,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -196,7 +197,9 @@ struct h2sp_handle {
   uint8_t *tmaps_buf = nullptr;     // their device storage
   const void *tmaps_base = nullptr;  // the front buffer they were encoded for
   float *pack = nullptr;     // packed GEMM operands of the blocked FP32 LU (3 buffers of the largest level)
-  int32_t last_prec = -1;    // precision of the last h2sp_factor (h2sp_refactor repeats it)
+  int32_t last_prec = -1;    // h2sp_prec of the last h2sp_factor (h2sp_refactor repeats it)
+  bool chol = false;         // the current factors come from the block Cholesky (stored in the LU form)
+  double *chol_inv = nullptr;  // L11^-1 tiles of the block Cholesky's panels (one per front of a level)
   cudaGraphExec_t graph_exec = nullptr;  // sparsification + factorization, captured by h2sp_refactor
   cudaStream_t graph_stream = nullptr;    // the graph is captured and launched here (the caller's may be legacy)
   cudaEvent_t graph_in = nullptr, graph_out = nullptr;
@@ -1118,13 +1121,17 @@ void copy_out(h2sp_handle *h, double *dst, const void *src, int64_t n) {
 }
 
 // ---- factorization, in three parts: buffers (first call), launches, check ----
+// `prec` is an h2sp_prec: bit 0 selects FP32 fronts, bit 1 the block Cholesky.
+inline bool prec_fp32(int32_t prec) { return (prec & 1) != 0; }
+inline bool prec_chol(int32_t prec) { return (prec & 2) != 0; }
+
 void factor_prepare(h2sp_handle *h, int32_t prec) {
   const Plan &p = (*h->plan_ptr);
   cudaStream_t s = h->stream;
   // the fronts are sized by the precision of the factorization: FP32 fronts
   // take half the memory of FP64 ones; a later FP64 factorization of the same
   // handle replaces the buffer by a wider one (which also holds FP32 fronts)
-  const size_t esz = prec == H2SP_FP64 ? sizeof(double) : sizeof(float);
+  const size_t esz = prec_fp32(prec) ? sizeof(float) : sizeof(double);
   if (h->fronts == nullptr || h->fronts_esz < esz) {
     if (h->fronts != nullptr) h->free_one(h->fronts);
     h->fronts = h->alloc<uint8_t>(size_t(std::max<int64_t>(p.front_elems, 1)) * esz);
@@ -1139,6 +1146,12 @@ void factor_prepare(h2sp_handle *h, int32_t prec) {
     h->err = h->alloc<int>(1);
     h->dinv = h->alloc<double>(size_t(std::max<int64_t>(p.dinv_elems, 1)));
   }
+  if (prec_chol(prec) && h->chol_inv == nullptr) {
+    // the L11^-1 tiles of one level's panels (one per front), sized for FP64
+    size_t maxn = 1;
+    for (const FrontLevel &L : h->flev) maxn = std::max<size_t>(maxn, size_t(L.hi - L.lo));
+    h->chol_inv = h->alloc<double>(maxn * kCholInvElems);
+  }
   if (h->la.side == nullptr && lookahead_enabled()) {
     int lo = 0, hi = 0;
     ck(cudaDeviceGetStreamPriorityRange(&lo, &hi));
@@ -1148,7 +1161,7 @@ void factor_prepare(h2sp_handle *h, int32_t prec) {
     ck(cudaEventCreateWithFlags(&h->la.panel, cudaEventDisableTiming));
     ck(cudaEventCreateWithFlags(&h->la.done, cudaEventDisableTiming));
   }
-  if (prec == H2SP_FP32 && tma_enabled() && !p.fronts.empty() && h->tmaps_base != h->fronts) {
+  if (prec_fp32(prec) && tma_enabled() && !p.fronts.empty() && h->tmaps_base != h->fronts) {
     // (re-)encode the descriptors whenever the front buffer is new
     h->tmaps = nullptr;
     if (h->tmaps_buf == nullptr) h->tmaps_buf = h->alloc<uint8_t>(p.fronts.size() * kTmapBytes);
@@ -1164,48 +1177,50 @@ void factor_prepare(h2sp_handle *h, int32_t prec) {
   }
 }
 
-// every launch of the factorization (no allocation, no host synchronisation)
-void factor_launch(h2sp_handle *h, int32_t prec) {
+template <typename T>
+void factor_launch_t(h2sp_handle *h, bool chol) {
   const Plan &p = (*h->plan_ptr);
   cudaStream_t s = h->stream;
-  const size_t esz = prec == H2SP_FP64 ? sizeof(double) : sizeof(float);
   const LuAsync *la = h->la.side ? &h->la : nullptr;
-  ck(cudaMemsetAsync(h->fronts, 0, size_t(std::max<int64_t>(p.front_elems, 1)) * esz, s));
+  ck(cudaMemsetAsync(h->fronts, 0, size_t(std::max<int64_t>(p.front_elems, 1)) * sizeof(T), s));
   ck(cudaMemsetAsync(h->err, 0, sizeof(int), s));
   const int64_t na = int64_t(p.assemble.size());
-  const double abytes = double(p.s_elems) * double((h->sp_prec == H2SP_FP32 ? sizeof(float) : sizeof(double)) + esz);
-  if (prec == H2SP_FP64) {
-    double *F = static_cast<double *>(h->fronts);
-    if (h->sp_prec == H2SP_FP32)
-      ck(launch_assemble<float, double>(h->asm_items, na, static_cast<const float *>(h->S), F, s, &h->prof, abytes));
-    else
-      ck(launch_assemble<double, double>(h->asm_items, na, static_cast<const double *>(h->S), F, s, &h->prof,
-                                         abytes));
-    for (const FrontLevel &L : h->flev) {
-      ck(launch_lu_level<double>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv,
-                                 h->swaps, h->err, s, la, &h->prof));
-      ck(launch_extend_add_impl<double>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s, &h->prof, L.b2));
+  const double abytes = double(p.s_elems) * double((h->sp_prec == H2SP_FP32 ? sizeof(float) : sizeof(double)) + sizeof(T));
+  T *F = static_cast<T *>(h->fronts);
+  if (h->sp_prec == H2SP_FP32)
+    ck(launch_assemble<float, T>(h->asm_items, na, static_cast<const float *>(h->S), F, s, &h->prof, abytes));
+  else
+    ck(launch_assemble<double, T>(h->asm_items, na, static_cast<const double *>(h->S), F, s, &h->prof, abytes));
+  const bool fp32 = std::is_same<T, float>::value;
+  for (const FrontLevel &L : h->flev) {
+    const uint8_t *maps = (fp32 && h->tmaps) ? h->tmaps + size_t(L.lo) * kTmapBytes : nullptr;
+    if (chol) {
+      ck(launch_chol_level<T>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv, h->err,
+                              s, la, &h->prof, maps, h->pack, reinterpret_cast<T *>(h->chol_inv)));
+    } else {
+      ck(launch_lu_level<T>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv, h->swaps,
+                            h->err, s, la, &h->prof, maps, fp32 ? h->pack : nullptr));
     }
-    ck(launch_make_perm<double>(h->fr, int(p.fronts.size()), h->max_s_all, h->piv, h->perm, s, &h->prof));
-    ck(launch_invert_diag<double>(h->fr, int(p.fronts.size()), h->max_s_all, F, static_cast<double *>(h->dinv), s,
-                                  &h->prof));
-  } else {
-    float *F = static_cast<float *>(h->fronts);
-    if (h->sp_prec == H2SP_FP32)
-      ck(launch_assemble<float, float>(h->asm_items, na, static_cast<const float *>(h->S), F, s, &h->prof, abytes));
-    else
-      ck(launch_assemble<double, float>(h->asm_items, na, static_cast<const double *>(h->S), F, s, &h->prof,
-                                        abytes));
-    for (const FrontLevel &L : h->flev) {
-      ck(launch_lu_level<float>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv,
-                                h->swaps, h->err, s, la, &h->prof,
-                                h->tmaps ? h->tmaps + size_t(L.lo) * kTmapBytes : nullptr, h->pack));
-      ck(launch_extend_add_impl<float>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s, &h->prof, L.b2));
-    }
-    ck(launch_make_perm<float>(h->fr, int(p.fronts.size()), h->max_s_all, h->piv, h->perm, s, &h->prof));
-    ck(launch_invert_diag<float>(h->fr, int(p.fronts.size()), h->max_s_all, F, static_cast<float *>(h->dinv), s,
-                                 &h->prof));
+    ck(launch_extend_add_impl<T>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s, &h->prof, chol ? 0.5 * L.b2 : L.b2,
+                                 chol));
   }
+  const int nf = int(p.fronts.size());
+  if (chol) {
+    // the LU form: unit L and U = D L^T (read + written: sum of s(2f - s) entries)
+    double el = 0.0;
+    for (const Front &Fr : p.fronts) el += double(Fr.s) * (2.0 * Fr.f - Fr.s);
+    ck(launch_chol_to_lu<T>(h->fr, nf, int(p.max_front), F, s, &h->prof, 1.5 * el * sizeof(T)));
+  }
+  ck(launch_make_perm<T>(h->fr, nf, h->max_s_all, h->piv, h->perm, s, &h->prof));
+  ck(launch_invert_diag<T>(h->fr, nf, h->max_s_all, F, static_cast<T *>(h->dinv), s, &h->prof));
+}
+
+// every launch of the factorization (no allocation, no host synchronisation)
+void factor_launch(h2sp_handle *h, int32_t prec) {
+  if (prec_fp32(prec))
+    factor_launch_t<float>(h, prec_chol(prec));
+  else
+    factor_launch_t<double>(h, prec_chol(prec));
 }
 
 // the factorization's error word, after the stream has drained
@@ -1214,9 +1229,62 @@ int factor_finish(h2sp_handle *h, int32_t prec) {
   ck(cudaMemcpyAsync(&herr, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   ck(cudaStreamSynchronize(h->stream));
   if (herr & 4) return H2SP_ETIMEOUT;
+  if (herr & 8) {
+    g_cuda_err = "h2sp_factor: a pivot of the block Cholesky is not positive: S is not positive definite "
+                 "in this precision";
+    return H2SP_ESINGULAR;
+  }
   if (herr != 0) return H2SP_ESINGULAR;
-  h->prec = prec;
+  h->prec = prec_fp32(prec) ? H2SP_FP32 : H2SP_FP64;
+  h->chol = prec_chol(prec);
   return H2SP_OK;
+}
+
+// the descriptor has the analysed structure: sizes first, then a fingerprint
+// of every structure array; the numeric arrays are present as the analysis
+// expects (with or without column bases)
+bool same_structure(const h2sp_handle *an, const h2sp_h2_desc *desc) {
+  const Plan &ap = *an->plan_ptr;
+  if (desc->n != ap.n || desc->depth != ap.D || !desc->level_ptr || !desc->far_ptr || !desc->near_ptr) return false;
+  for (int l = 0; l <= ap.D + 1; ++l)
+    if (desc->level_ptr[l] != ap.level_ptr[l]) return false;
+  if (desc->far_ptr[ap.ncl] != ap.far_ptr[ap.ncl] || desc->near_ptr[ap.nleaf] != ap.near_ptr[ap.nleaf]) return false;
+  if (!desc->leaf_basis || !desc->transfer || !desc->coupling || !desc->near_block) return false;
+  if ((desc->col_leaf_basis == nullptr) != ap.sym || (desc->col_transfer == nullptr) != ap.sym) return false;
+  return structure_hash(desc, ap) == an->structure_hash;
+}
+
+// elements of each numeric array of a descriptor whose structure has been
+// validated (the largest block end of each packed array)
+struct NumericSizes {
+  int64_t leaf = 0, transfer = 0, coupling = 0, near = 0, col_leaf = 0, col_transfer = 0;
+};
+NumericSizes numeric_sizes(const h2sp_h2_desc *d) {
+  NumericSizes z;
+  const int D = d->depth;
+  const int l0 = d->level_ptr[D], ncl = d->level_ptr[D + 1];
+  for (int t = l0; t < ncl; ++t) {
+    const int64_t blk = d->size[t] * int64_t(d->rank[t]);
+    if (blk > 0) z.leaf = std::max(z.leaf, d->leaf_basis_off[t - l0] + blk);
+    if (blk > 0 && d->col_leaf_basis_off) z.col_leaf = std::max(z.col_leaf, d->col_leaf_basis_off[t - l0] + blk);
+  }
+  for (int c = 0; c < ncl; ++c) {
+    if (d->parent[c] < 0) continue;
+    const int64_t blk = int64_t(d->rank[c]) * d->rank[d->parent[c]];
+    if (blk > 0) z.transfer = std::max(z.transfer, d->transfer_off[c] + blk);
+    if (blk > 0 && d->col_transfer_off) z.col_transfer = std::max(z.col_transfer, d->col_transfer_off[c] + blk);
+  }
+  for (int t = 0; t < ncl; ++t)
+    for (int64_t e = d->far_ptr[t]; e < d->far_ptr[t + 1]; ++e) {
+      const int64_t blk = int64_t(d->rank[t]) * d->rank[d->far_col[e]];
+      if (blk > 0) z.coupling = std::max(z.coupling, d->coupling_off[e] + blk);
+    }
+  for (int t = l0; t < ncl; ++t)
+    for (int64_t e = d->near_ptr[t - l0]; e < d->near_ptr[t - l0 + 1]; ++e) {
+      const int64_t blk = d->size[t] * d->size[d->near_col[e]];
+      if (blk > 0) z.near = std::max(z.near, d->near_off[e] + blk);
+    }
+  return z;
 }
 
 }  // namespace
@@ -1270,16 +1338,7 @@ int h2sp_sparsify_analyzed(const h2sp_handle *an, const h2sp_h2_desc *desc, cons
   const int32_t sp_prec = sparsify_prec_of(opts);
   if (sp_prec < 0) return H2SP_EINVAL;
   if (!an || !an->plan_ptr || !an->cell || !desc) return H2SP_EINVAL;
-  const Plan &ap = *an->plan_ptr;
-  // same structure as the analysed descriptor (sizes first, then every structure array)
-  if (desc->n != ap.n || desc->depth != ap.D || !desc->level_ptr || !desc->far_ptr || !desc->near_ptr) return H2SP_EINVAL;
-  for (int l = 0; l <= ap.D + 1; ++l)
-    if (desc->level_ptr[l] != ap.level_ptr[l]) return H2SP_EINVAL;
-  if (desc->far_ptr[ap.ncl] != ap.far_ptr[ap.ncl] || desc->near_ptr[ap.nleaf] != ap.near_ptr[ap.nleaf])
-    return H2SP_EINVAL;
-  if (!desc->leaf_basis || !desc->transfer || !desc->coupling || !desc->near_block) return H2SP_EINVAL;
-  if ((desc->col_leaf_basis == nullptr) != ap.sym || (desc->col_transfer == nullptr) != ap.sym) return H2SP_EINVAL;
-  if (structure_hash(desc, ap) != an->structure_hash) return H2SP_EINVAL;
+  if (!same_structure(an, desc)) return H2SP_EINVAL;
   h2sp_handle *h = new (std::nothrow) h2sp_handle();
   if (!h) return H2SP_ENOMEM;
   h->plan_ptr = an->plan_ptr;
@@ -1315,7 +1374,11 @@ int h2sp_analyze(const h2sp_h2_desc *desc, h2sp_handle **out) {
 int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
   if (!h) return H2SP_EINVAL;
   if (!h->device_ready) return H2SP_ESTATE;
-  if (prec != H2SP_FP64 && prec != H2SP_FP32) return H2SP_EINVAL;
+  if (prec < H2SP_FP64 || prec > H2SP_FP32_CHOL) return H2SP_EINVAL;
+  if (prec_chol(prec) && (h->col_leaf_basis != nullptr || h->col_transfer != nullptr)) {
+    g_cuda_err = "h2sp_factor: the block Cholesky needs symmetric bases (V = U)";
+    return H2SP_EINVAL;
+  }
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   h->prof.stream = h->stream;
   try {
@@ -1503,6 +1566,72 @@ int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *o, int32_t nrhs, const dou
   return H2SP_OK;
 }
 
+int h2sp_solve_host(const h2sp_handle *an, const h2sp_h2_desc *desc, const h2sp_opts *opts, int32_t prec,
+                    const h2sp_solve_opts *sopts, int32_t nrhs, const double *b, int64_t ldb, double *x, int64_t ldx,
+                    h2sp_solve_info *info, h2sp_stream stream) {
+  if (!desc || !sopts || !b || !x || nrhs <= 0 || nrhs > 64) return H2SP_EINVAL;
+  if (ldb < desc->n || ldx < desc->n) return H2SP_EINVAL;
+  h2sp_handle *own = nullptr;
+  if (an == nullptr) {
+    // validates the structure and plans it
+    const int st = h2sp_analyze(desc, &own);
+    if (st != H2SP_OK) return st;
+    an = own;
+  } else if (!an->plan_ptr || !an->cell || !same_structure(an, desc)) {
+    return H2SP_EINVAL;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<void *> bufs;
+  h2sp_handle *h = nullptr;
+  int st = H2SP_OK;
+  try {
+    init_pool_once();
+    const NumericSizes z = numeric_sizes(desc);
+    auto up = [&](const double *src, int64_t n) -> const double * {
+      if (src == nullptr) return nullptr;
+      void *p = nullptr;
+      ck(cudaMallocAsync(&p, size_t(std::max<int64_t>(n, 1)) * sizeof(double), s));
+      bufs.push_back(p);
+      if (n > 0) ck(cudaMemcpyAsync(p, src, size_t(n) * sizeof(double), cudaMemcpyHostToDevice, s));
+      return static_cast<const double *>(p);
+    };
+    h2sp_h2_desc dd = *desc;
+    dd.leaf_basis = up(desc->leaf_basis, z.leaf);
+    dd.transfer = up(desc->transfer, z.transfer);
+    dd.coupling = up(desc->coupling, z.coupling);
+    dd.near_block = up(desc->near_block, z.near);
+    dd.col_leaf_basis = up(desc->col_leaf_basis, z.col_leaf);
+    dd.col_transfer = up(desc->col_transfer, z.col_transfer);
+    const int64_t n = desc->n;
+    void *db = nullptr, *dx = nullptr;
+    ck(cudaMallocAsync(&db, size_t(std::max<int64_t>(n * nrhs, 1)) * sizeof(double), s));
+    bufs.push_back(db);
+    ck(cudaMallocAsync(&dx, size_t(std::max<int64_t>(n * nrhs, 1)) * sizeof(double), s));
+    bufs.push_back(dx);
+    if (n > 0)
+      ck(cudaMemcpy2DAsync(db, size_t(n) * sizeof(double), b, size_t(ldb) * sizeof(double), size_t(n) * sizeof(double),
+                           size_t(nrhs), cudaMemcpyHostToDevice, s));
+    st = h2sp_sparsify_analyzed(an, &dd, opts, stream, &h);
+    if (st == H2SP_OK) st = h2sp_factor(h, prec, stream);
+    if (st == H2SP_OK) {
+      st = h2sp_solve(h, sopts, nrhs, static_cast<const double *>(db), n, static_cast<double *>(dx), n, info, stream);
+      if (st == H2SP_OK || st == H2SP_ENOCONV) {
+        if (n > 0)
+          ck(cudaMemcpy2DAsync(x, size_t(ldx) * sizeof(double), dx, size_t(n) * sizeof(double),
+                               size_t(n) * sizeof(double), size_t(nrhs), cudaMemcpyDeviceToHost, s));
+        ck(cudaStreamSynchronize(s));
+      }
+    }
+  } catch (const CudaFail &f) {
+    st = status_of(f.e);
+  }
+  if (h) h2sp_destroy(h);
+  for (void *p : bufs) cudaFreeAsync(p, s);
+  cudaStreamSynchronize(s);
+  if (own) h2sp_destroy(own);
+  return st;
+}
+
 int h2sp_export_S(h2sp_handle *h, int64_t *node_size, int64_t *brow_ptr, int32_t *bcol_idx, int64_t *val_off,
                   double *vals, h2sp_stream stream) {
   if (!h) return H2SP_EINVAL;
@@ -1608,6 +1737,35 @@ int h2sp_export_structure(h2sp_handle *h, int32_t *node_level, int32_t *node_clu
   return H2SP_OK;
 }
 
+int h2sp_export_front(h2sp_handle *h, int32_t k, int64_t *f, int64_t *sz, double *vals, h2sp_stream stream) {
+  if (!h) return H2SP_EINVAL;
+  const Plan &p = (*h->plan_ptr);
+  if (k < 0 || k >= int32_t(p.fronts.size())) return H2SP_EINVAL;
+  const Front &F = p.fronts[size_t(k)];
+  if (f) *f = F.f;
+  if (sz) *sz = F.s;
+  if (!vals) return H2SP_OK;
+  if (!h->device_ready || h->prec < 0) return H2SP_ESTATE;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  try {
+    const size_t esz = h->prec == H2SP_FP32 ? sizeof(float) : sizeof(double);
+    std::vector<unsigned char> tmp(size_t(F.f) * size_t(F.f) * esz);
+    const unsigned char *src = static_cast<const unsigned char *>(h->fronts) + size_t(F.off) * esz;
+    if (F.f > 0)
+      ck(cudaMemcpy2DAsync(tmp.data(), size_t(F.f) * esz, src, size_t(F.ld) * esz, size_t(F.f) * esz, size_t(F.f),
+                           cudaMemcpyDeviceToHost, h->stream));
+    ck(cudaStreamSynchronize(h->stream));
+    const size_t n = size_t(F.f) * size_t(F.f);
+    if (esz == sizeof(float))
+      for (size_t i = 0; i < n; ++i) vals[i] = double(reinterpret_cast<const float *>(tmp.data())[i]);
+    else
+      std::memcpy(vals, tmp.data(), n * sizeof(double));
+  } catch (const CudaFail &e) {
+    return status_of(e.e);
+  }
+  return H2SP_OK;
+}
+
 int h2sp_query(const h2sp_handle *h, h2sp_stats *st) {
   if (!h || !st) return H2SP_EINVAL;
   const Plan &p = (*h->plan_ptr);
@@ -1625,6 +1783,8 @@ int h2sp_query(const h2sp_handle *h, h2sp_stats *st) {
   st->factor_flops = p.factor_flops;
   st->sparsify_flops = p.sparsify_flops;
   st->factor_prec = h->prec;
+  st->factor_chol = h->prec >= 0 && h->chol ? 1 : 0;
+  st->chol_flops = p.chol_flops;
   st->sparsify_prec = h->device_ready ? h->sp_prec : -1;
   st->plan_seconds = h->plan_seconds;
   st->nsys = p.level_ptr[1];

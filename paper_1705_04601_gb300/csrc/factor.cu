@@ -1002,9 +1002,11 @@ __global__ void __launch_bounds__(256, 3) k_blk_swap_trsm(const FrontDev *__rest
 // stored permuted in shared memory -- row tr + RT*i of the A tile at
 // tr*TM + i -- so each thread reads its TM (TN) values as 16-byte vectors.
 // The C tile is prefetched into the accumulators while the operands are staged.
+// sym = 1 (block Cholesky): only tiles that reach the lower triangle, and the
+// B operand is L21^T, read from the panel columns of the rows [t0, f).
 template <typename T, int BM, int BN, int TM, int TN, int NB>
 __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict__ fr, int j0, T *__restrict__ fronts,
-                                                     int c_lo, int c_hi) {
+                                                     int c_lo, int c_hi, int sym) {
   constexpr int RT = BM / TM, CT = BN / TN;  // thread grid over the tile (rows fastest)
   constexpr int PA = BM + 16 / int(sizeof(T)), PB = BN + 16 / int(sizeof(T));  // padded rows, 16-byte aligned
   constexpr int VA = 16 / int(sizeof(T));    // elements per 16-byte vector
@@ -1016,6 +1018,7 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
   const int ncol = min(nrest, c_hi);  // trailing columns [c_lo, ncol) of this launch
   const int rb = blockIdx.y * BM, cb = c_lo + blockIdx.x * BN;
   if (rb >= nrest || cb >= ncol) return;
+  if (sym && cb >= rb + BM) return;  // strictly above the diagonal
   T *A = fronts + F.off;
   const int64_t ld = F.ld;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -1056,14 +1059,16 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
 #pragma unroll
     for (int it = 0; it < kIB; ++it) {
       const int e = tid + it * 256;
-      const int k = e % NB, j = e / NB;
+      // U12 rows (K contiguous), or L21 rows (columns of the tile contiguous)
+      const int k = sym ? e / BN : e % NB, j = sym ? e % BN : e / NB;
       const int c = cb + j;
-      v[it] = (k < jb && c < ncol) ? A[(j0 + k) + int64_t(t0 + c) * ld] : T(0);
+      v[it] = (k < jb && c < ncol) ? (sym ? A[(t0 + c) + int64_t(j0 + k) * ld] : A[(j0 + k) + int64_t(t0 + c) * ld])
+                                   : T(0);
     }
 #pragma unroll
     for (int it = 0; it < kIB; ++it) {
       const int e = tid + it * 256;
-      const int k = e % NB, j = e / NB;
+      const int k = sym ? e / BN : e % NB, j = sym ? e % BN : e / NB;
       sB[k * PB + (j % CT) * TN + j / CT] = v[it];
     }
   }
@@ -1112,18 +1117,18 @@ __global__ void __launch_bounds__(256) k_gemm_update(const FrontDev *__restrict_
 
 template <typename T>
 __global__ void k_extend_add(const FrontDev *__restrict__ fr_all, int lo, const int32_t *__restrict__ map,
-                             T *__restrict__ fronts) {
+                             T *__restrict__ fronts, int lower) {
   const FrontDev F = fr_all[lo + blockIdx.z];
   if (F.parent < 0 || F.b == 0) return;
   const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
-  if (i0 >= F.b || j0 >= F.b) return;
+  if (i0 >= F.b || j0 >= F.b || (lower && i0 + 31 < j0)) return;
   const FrontDev P = fr_all[F.parent];
   const int32_t *mp = map + F.map_off;
   const T *C = fronts + F.off + int64_t(F.s) * F.ld + F.s;
   T *Pa = fronts + P.off;
   for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
     const int i = i0 + (e & 31), j = j0 + (e >> 5);
-    if (i < F.b && j < F.b) atomicAdd(&Pa[mp[i] + int64_t(mp[j]) * P.ld], C[i + int64_t(j) * F.ld]);
+    if (i < F.b && j < F.b && (!lower || i >= j)) atomicAdd(&Pa[mp[i] + int64_t(mp[j]) * P.ld], C[i + int64_t(j) * F.ld]);
   }
 }
 
@@ -1811,7 +1816,7 @@ cudaError_t launch_assemble(const AItem *items, int64_t n, const TS *S, T *front
 }
 
 // Outer block width of the blocked FP32 LU (four 64-column panels).
-constexpr int kLuOuter = 256;
+constexpr int kLuOuter = kLuOuterBlock;
 
 // The FP32 fronts are factored in outer blocks of kLuOuter columns (with
 // tensor cores and TMA descriptors); H2SP_LU=step keeps one trailing update
@@ -1974,7 +1979,7 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
     } else {
       const int ncol = std::min(rest, c_hi) - c_lo;
       dim3 g(cdiv(ncol, G::BN), cdiv(rest, G::BM), nfront);
-      gemm<<<g, 256, gsmem, us>>>(fr, j0, fronts, c_lo, c_hi);
+      gemm<<<g, 256, gsmem, us>>>(fr, j0, fronts, c_lo, c_hi, 0);
     }
     prof->end(P_GEMM, 1, e0, fgemm, us);
     return cudaSuccess;
@@ -2152,14 +2157,30 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
 
 template <typename T>
 cudaError_t launch_extend_add_impl(const FrontDev *fr_all, int lo, int nfront, int max_b, const int32_t *map,
-                                   T *fronts, cudaStream_t s, Prof *prof, double elems) {
+                                   T *fronts, cudaStream_t s, Prof *prof, double elems, bool lower) {
   if (nfront == 0 || max_b == 0) return cudaSuccess;
   dim3 g(cdiv(max_b, 32), cdiv(max_b, 32), nfront);
   const size_t e0 = prof->begin();
-  k_extend_add<T><<<g, 256, 0, s>>>(fr_all, lo, map, fronts);
+  k_extend_add<T><<<g, 256, 0, s>>>(fr_all, lo, map, fronts, lower ? 1 : 0);
   prof->end(P_EXTEND, 1, e0, elems);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_gemm_update_sym(const FrontDev *fr, int j0, int nfront, int max_f, T *fronts, cudaStream_t s) {
+  constexpr int NB = LuCfg<T>::NB;
+  using G = GemmCfg<T>;
+  auto gemm = k_gemm_update<T, G::BM, G::BN, G::TM, G::TN, NB>;
+  const size_t gsmem = sizeof(T) * NB * (G::BM + G::BN + 2 * (16 / sizeof(T)));
+  if (cudaError_t ea = smem_attr((const void *)gemm, int(gsmem)); ea != cudaSuccess) return ea;
+  const int rest = max_f - j0 - 1;
+  if (rest <= 0 || nfront == 0) return cudaSuccess;
+  dim3 g(cdiv(rest, G::BN), cdiv(rest, G::BM), nfront);
+  gemm<<<g, 256, gsmem, s>>>(fr, j0, fronts, 0, INT_MAX, 1);
+  return cudaGetLastError();
+}
+
+bool use_tensor_core_gemm_host() { return use_tensor_core_gemm(); }
 
 template <typename T>
 cudaError_t launch_make_perm(const FrontDev *fr, int nfront, int max_s, const int32_t *piv, int32_t *perm,
@@ -2341,7 +2362,9 @@ template cudaError_t launch_lu_level<double>(const FrontDev *, const Front *, in
                                            const uint8_t *, float *);
 template cudaError_t launch_make_perm<double>(const FrontDev *, int, int, const int32_t *, int32_t *, cudaStream_t, Prof *);
 template cudaError_t launch_extend_add_impl<double>(const FrontDev *, int, int, int, const int32_t *, double *, cudaStream_t,
-                                                  Prof *, double);
+                                                  Prof *, double, bool);
+template cudaError_t launch_gemm_update_sym<double>(const FrontDev *, int, int, int, double *, cudaStream_t);
+template cudaError_t launch_gemm_update_sym<float>(const FrontDev *, int, int, int, float *, cudaStream_t);
 template cudaError_t launch_invert_diag<double>(const FrontDev *, int, int, const double *, double *, cudaStream_t, Prof *);
 template cudaError_t launch_logdet<double>(const FrontDev *, int, const double *, const int32_t *, const int32_t *,
                                            const int32_t *, int, double *, int *, double *, int32_t *, cudaStream_t,
@@ -2366,7 +2389,7 @@ template cudaError_t launch_lu_level<float>(const FrontDev *, const Front *, int
                                            const uint8_t *, float *);
 template cudaError_t launch_make_perm<float>(const FrontDev *, int, int, const int32_t *, int32_t *, cudaStream_t, Prof *);
 template cudaError_t launch_extend_add_impl<float>(const FrontDev *, int, int, int, const int32_t *, float *, cudaStream_t,
-                                                  Prof *, double);
+                                                  Prof *, double, bool);
 template cudaError_t launch_invert_diag<float>(const FrontDev *, int, int, const float *, float *, cudaStream_t, Prof *);
 template cudaError_t launch_solve_fwd_level_impl<float>(const FrontDev *, int, int, int, int, const float *, const float *,
                                                        const int32_t *, const int32_t *, float *, int64_t, int, float *,

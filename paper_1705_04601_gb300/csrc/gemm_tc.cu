@@ -101,10 +101,12 @@ __device__ __forceinline__ void sync_for_tensor_cores() {
 // With kb > 0 (an inner step of the blocked LU) only the columns left in the
 // step's kb-wide outer block, [t0, min(J + kb, s)) with J = kb floor(j0 / kb),
 // are updated; the columns after the block wait for the block's rank-kb update.
+// With sym (block Cholesky) the B operand is L21^T: column n of the tile is
+// row t0 + n of the panel columns, staged like the A tile.
 __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__restrict__ fr, int j0,
                                                           float *__restrict__ fronts, int *__restrict__ err,
                                                           int splits, int tile_lo, int tile_hi, int partial_only,
-                                                          int kb) {
+                                                          int kb, int sym) {
   const FrontDev F = fr[blockIdx.z];
   if (j0 >= F.s) return;
   const int jb = min(kTcK, F.s - j0);
@@ -159,6 +161,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const FrontDev *__res
   auto stage_b = [&](int ct, int buf) {
     const int cb = ct * kTcN;
     float v[kIters];
+    if (sym) {
+      // same canonical layout as A: element e is (n, k) of the tile, stored at word e
+#pragma unroll
+      for (int it = 0; it < kIters; ++it) {
+        const int e = tid + it * kTcThreads;
+        const int n = (e >> 9) * 8 + ((e & 31) >> 2), k = ((e >> 5) & 15) * 4 + (e & 3);
+        const int c = cb + n;
+        v[it] = (k < jb && c < ncols) ? A[(t0 + c) + int64_t(j0 + k) * ld] : 0.f;
+      }
+      float *bh = reinterpret_cast<float *>(sBh[buf]), *bl = reinterpret_cast<float *>(sBl[buf]);
+#pragma unroll
+      for (int it = 0; it < kIters; ++it) {
+        const int e = tid + it * kTcThreads;
+        float hi, lo;
+        split_tf32(v[it], hi, lo);
+        bh[e] = hi;
+        bl[e] = lo;
+      }
+      return;
+    }
 #pragma unroll
     for (int it = 0; it < kIters; ++it) {
       const int e = tid + it * kTcThreads;
@@ -581,7 +603,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__
                                                              float *__restrict__ fronts, int *__restrict__ err,
                                                              int splits, int tile_lo, int tile_hi,
                                                              const float *__restrict__ apack,
-                                                             const float *__restrict__ bpack) {
+                                                             const float *__restrict__ bpack, int lower) {
   const FrontDev F = fr[blockIdx.z];
   if (j0 >= F.s) return;
   const int jb = min(kb, F.s - j0);
@@ -592,7 +614,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__
   const int ntiles = min((nrest + kTcN - 1) / kTcN, tile_hi) - tile_lo;
   if (ntiles <= 0) return;
   const int per = (ntiles + splits - 1) / splits;
-  const int c_lo = tile_lo + blockIdx.x * per, c_hi = min(tile_lo + ntiles, c_lo + per);
+  // lower (block Cholesky): the column tiles up to the diagonal tile only
+  const int tile_end = lower ? min(tile_lo + ntiles, int(blockIdx.y) + 1) : tile_lo + ntiles;
+  const int c_lo = tile_lo + blockIdx.x * per, c_hi = min(tile_end, c_lo + per);
   if (c_lo >= c_hi) return;
   const int nt = c_hi - c_lo;
   const int nq = (jb + kPkK - 1) / kPkK;
@@ -798,15 +822,15 @@ cudaError_t launch_gemm_tc(const FrontDev *fr, int j0, int nfront, int max_f, fl
     if (any_full)
       k_gemm_tc_tma<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, tile_lo, tile_hi, maps);
     if (any_partial)
-      k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, tile_lo, tile_hi, 1, 0);
+      k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, tile_lo, tile_hi, 1, 0, 0);
   } else {
-    k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, tile_lo, tile_hi, 0, 0);
+    k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, tile_lo, tile_hi, 0, 0, 0);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_tc_inner(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
-                                 cudaStream_t s, int sm_budget) {
+                                 cudaStream_t s, int sm_budget, int sym) {
   if (cudaError_t ea = smem_attr((const void *)k_gemm_tc, int(gemm_tc_smem())); ea != cudaSuccess) return ea;
   const int rest = max_f - j0 - 1;
   const int cols = (j0 / kb) * kb + kb - (j0 + kTcK);  // columns left in the outer block (at most)
@@ -815,7 +839,7 @@ cudaError_t launch_gemm_tc_inner(const FrontDev *fr, int j0, int kb, int nfront,
   const int ct = (cols + kTcN - 1) / kTcN;
   const int splits = wave_splits(rt, ct, nfront, std::max(sm_budget, 1), 0.3);
   dim3 g(splits, rt, nfront);
-  k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, 0, ct, 0, kb);
+  k_gemm_tc<<<g, kTcThreads, gemm_tc_smem(), s>>>(fr, j0, fronts, err, splits, 0, ct, 0, kb, sym);
   return cudaGetLastError();
 }
 
@@ -841,7 +865,7 @@ size_t gemm_ws_smem() { return size_t(kWsStages) * 4 * kPkTile * sizeof(float) +
 
 cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
                               cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps,
-                              const float *apack, const float *bpack) {
+                              const float *apack, const float *bpack, int lower) {
   if (cudaError_t ea = smem_attr((const void *)k_gemm_tc_ws, int(gemm_ws_smem())); ea != cudaSuccess) return ea;
   (void)maps;
   if (apack == nullptr || bpack == nullptr) return cudaErrorInvalidValue;
@@ -854,7 +878,7 @@ cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, in
   const int splits = wave_splits(rt, ct, nfront, std::max(sm_budget, 1), 1.0);
   dim3 g(splits, rt, nfront);
   k_gemm_tc_ws<<<g, kWsThreads, gemm_ws_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi, apack,
-                                                     bpack);
+                                                     bpack, lower);
   return cudaGetLastError();
 }
 

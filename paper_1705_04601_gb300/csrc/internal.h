@@ -130,6 +130,7 @@ struct Plan {
   std::vector<AItem> assemble;
   int64_t front_elems = 0, piv_elems = 0, max_front = 0, dinv_elems = 0;
   double factor_flops = 0.0;
+  double chol_flops = 0.0;  // the block Cholesky's: sum over supernodes of s^3/3 + s^2 b + s b^2
   // H^2 matvec structure (Definition 4.9)
   std::vector<int64_t> h_begin, h_size;
   std::vector<int64_t> leaf_basis_off, transfer_off, coupling_off, near_off;

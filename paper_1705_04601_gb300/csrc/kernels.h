@@ -98,6 +98,12 @@ struct LuCfg<float> {
 // Maximum number of rows a panel swaps (2 per column).
 constexpr int kMaxSwapRows = 2 * 64;
 
+// Outer block width of the blocked FP32 factorizations (four 64-column panels).
+constexpr int kLuOuterBlock = 256;
+
+// FP32 trailing updates on the tensor cores (H2SP_GEMM unset or not "simt").
+bool use_tensor_core_gemm_host();
+
 // S values of type TS (the sparsification's precision) into fronts of type T
 template <typename TS, typename T>
 cudaError_t launch_assemble(const AItem *items, int64_t n, const TS *S, T *fronts, cudaStream_t s, Prof *prof,
@@ -118,9 +124,28 @@ template <typename T>
 cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
                             int32_t *piv, int32_t *swaps, int *err, cudaStream_t s, const LuAsync *la, Prof *prof,
                             const uint8_t *maps = nullptr, float *pack = nullptr);
+// lower: only the lower triangle of each contribution block (block Cholesky;
+// the map is monotone, so it lands in the parent's lower triangle)
 template <typename T>
 cudaError_t launch_extend_add_impl(const FrontDev *fr_all, int lo, int nfront, int max_b, const int32_t *map,
-                                   T *fronts, cudaStream_t s, Prof *prof, double elems);
+                                   T *fronts, cudaStream_t s, Prof *prof, double elems, bool lower = false);
+// Block Cholesky of every front of one level (all fronts in parallel): no
+// pivoting, lower-triangle updates, the B operand read from L21.  A pivot
+// that is not positive sets bit 8 of *err.  FP32 with `maps` and `pack` uses
+// the tensor cores in 256-column outer blocks (la as in launch_lu_level).
+// inv: scratch of nfront x kCholInvElems elements (the panels' L11^-1).
+constexpr int kCholInvElems = 64 * 64;
+template <typename T>
+cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
+                              int32_t *piv, int *err, cudaStream_t s, const LuAsync *la, Prof *prof,
+                              const uint8_t *maps, float *pack, T *inv);
+// Rewrite Cholesky-factored fronts in the LU form: unit L = L_chol D^-1, U = D L_chol^T.
+template <typename T>
+cudaError_t launch_chol_to_lu(const FrontDev *fr, int nfront, int max_f, T *fronts, cudaStream_t s, Prof *prof,
+                              double bytes);
+// One CUDA-core panel update of the lower triangle, the B operand read from L21.
+template <typename T>
+cudaError_t launch_gemm_update_sym(const FrontDev *fr, int j0, int nfront, int max_f, T *fronts, cudaStream_t s);
 template <typename T>
 cudaError_t launch_make_perm(const FrontDev *fr, int nfront, int max_s, const int32_t *piv, int32_t *perm,
                              cudaStream_t s, Prof *prof);
@@ -178,22 +203,24 @@ cudaError_t launch_gemm_tc(const FrontDev *fr, int j0, int nfront, int max_f, fl
                            bool any_full, bool any_partial);
 // Blocked FP32 LU (kb-column outer blocks of 64-column panels):
 // inner step at panel j0: C -= L21 U12 on the columns left in the outer block
-// only, [j0 + 64, min(J + kb, s)) with J = kb floor(j0 / kb);
+// only, [j0 + 64, min(J + kb, s)) with J = kb floor(j0 / kb); sym = 1 (block
+// Cholesky): the B operand is L21^T, read from the panel columns;
 cudaError_t launch_gemm_tc_inner(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
-                                 cudaStream_t s, int sm_budget);
+                                 cudaStream_t s, int sm_budget, int sym = 0);
 // block end at J = j0: C[t0:f, t0:f] -= L21 U12 with K = min(kb, s - j0)
 // (t0 = j0 + K), over the 128-column tiles [tile_lo, tile_hi), from packed
 // operands: k_pack_a writes L21 (the rows after the block, K = the block's
 // columns) into apack, k_pack_b the U12 columns of tiles [ct_lo, ct_hi) of the
 // trailing block into bpack; the warp-specialised GEMM streams both with bulk
-// copies.
+// copies.  lower = 1 (block Cholesky, bpack = apack): only the tiles on and
+// below the diagonal of the trailing block.
 cudaError_t launch_pack_a(const FrontDev *fr, int j0, int kb, int nfront, int max_f, const float *fronts, float *apack,
                           cudaStream_t s);
 cudaError_t launch_pack_b(const FrontDev *fr, int j0, int kb, int nfront, int max_f, const float *fronts, float *bpack,
                           int ct_lo, int ct_hi, cudaStream_t s);
 cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
                               cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps,
-                              const float *apack, const float *bpack);
+                              const float *apack, const float *bpack, int lower = 0);
 cudaError_t make_front_tmaps(const Front *fronts, int n, const float *base, uint8_t *maps_dev);
 constexpr int kTcTile = 128;
 

@@ -704,7 +704,7 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
     p.fronts.resize(nsn);
     std::vector<int64_t> sn_local(nn, 0);  // scalar offset of a node inside its own supernode
     std::vector<std::vector<int64_t>> bpre(nsn);
-    double fl = 0.0;
+    double fl = 0.0, flc = 0.0;
     for (int k = 0; k < nsn; ++k) {
       int64_t s = 0;
       for (int i = p.sn_ptr[k]; i < p.sn_ptr[k + 1]; ++i) {
@@ -742,8 +742,10 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
         for (int64_t r = 0; r < p.node_size[w]; ++r) p.front_idx.push_back(int32_t(p.node_off[w] + r));
       double ds = double(s), db = double(b);
       fl += (2.0 / 3.0) * ds * ds * ds + 2.0 * ds * ds * db + 2.0 * ds * db * db;
+      flc += ds * ds * ds / 3.0 + ds * ds * db + ds * db * db;
     }
     p.factor_flops = fl;
+    p.chol_flops = flc;
     auto pos_in_front = [&](int k, int w) -> int64_t {
       if (sn_of[w] == k) return sn_local[w];
       const auto &B = bnd[k];
@@ -865,7 +867,9 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
           if (F.map_off + F.b > int64_t(p.front_map.size())) throw Fail{H2SP_EINVAL, "internal: front map"};
           const int pf = p.fronts[F.parent].f;
           for (int i = 0; i < F.b; ++i)
-            if (p.front_map[F.map_off + i] < 0 || p.front_map[F.map_off + i] >= pf)
+            if (p.front_map[F.map_off + i] < 0 || p.front_map[F.map_off + i] >= pf ||
+                (i > 0 && p.front_map[F.map_off + i] <= p.front_map[F.map_off + i - 1]))
+              // increasing: the lower triangle of a contribution block lands in the parent's
               throw Fail{H2SP_EINVAL, "internal: extend-add position"};
         }
         for (int i = 0; i < F.f; ++i)

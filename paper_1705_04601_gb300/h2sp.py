@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libh2sp.so")
 
 H2SP_OK, H2SP_EINVAL, H2SP_ENOMEM, H2SP_ECUDA, H2SP_ESINGULAR = 0, -1, -2, -3, -4
 H2SP_ESTATE, H2SP_ENOCONV, H2SP_ETIMEOUT, H2SP_EUNSUPPORTED = -5, -6, -7, -8
-H2SP_FP64, H2SP_FP32 = 0, 1
+H2SP_FP64, H2SP_FP32, H2SP_FP64_CHOL, H2SP_FP32_CHOL = 0, 1, 2, 3
 H2SP_SPARSIFY_FP32 = 1  # h2sp_opts.flags bit
 H2SP_OP_UT, H2SP_OP_V, H2SP_OP_U, H2SP_OP_VT, H2SP_OP_S, H2SP_OP_H2, H2SP_OP_SINV = range(7)
 H2SP_DIRECT, H2SP_IR, H2SP_GMRES = 0, 1, 2
@@ -63,6 +63,7 @@ class Stats(ctypes.Structure):
         ("nfront_levels", ctypes.c_int32), ("max_front", ctypes.c_int64), ("front_elems", ctypes.c_int64),
         ("factor_flops", ctypes.c_double), ("sparsify_flops", ctypes.c_double), ("factor_prec", ctypes.c_int32),
         ("plan_seconds", ctypes.c_double), ("sparsify_prec", ctypes.c_int32), ("nsys", ctypes.c_int32),
+        ("factor_chol", ctypes.c_int32), ("chol_flops", ctypes.c_double),
     ]
 
 
@@ -90,6 +91,10 @@ SIGNATURES = {
     "h2sp_export_S": (ctypes.c_int, [_vp, _i64p, _i64p, _i32p, _i64p, _f64p, _vp]),
     "h2sp_export_Q": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _i64p, _f64p, _vp]),
     "h2sp_export_structure": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i64p]),
+    "h2sp_export_front": (ctypes.c_int, [_vp, ctypes.c_int32, _i64p, _i64p, _f64p, _vp]),
+    "h2sp_solve_host": (ctypes.c_int, [_vp, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_int32, _vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_void_p,
+                                       _vp]),
     "h2sp_query": (ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
     "h2sp_profile": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(KernelTimes)]),
     "h2sp_h2_matvec_static": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int64, _vp, ctypes.c_int64, _vp]),
@@ -147,9 +152,11 @@ def _stream(stream):
 class H2Input:
     """An H^2 matrix marshalled for the ABI: host structure arrays (kept alive
     here) and device copies of the numeric arrays (torch tensors on cuda),
-    or ``device=None`` for h2sp_analyze (no numbers)."""
+    or ``device=None`` for h2sp_analyze (no numbers), or ``device="host"``
+    for h2sp_solve_host: the numeric arrays stay in host memory (``host``:
+    optional dict of page-locked torch tensors holding them)."""
 
-    def __init__(self, h, device="cuda", nonblocking_from=None):
+    def __init__(self, h, device="cuda", nonblocking_from=None, host=None):
         self.h = h
         c = np.ascontiguousarray
         self.arrs = dict(
@@ -163,7 +170,20 @@ class H2Input:
             self.arrs["col_leaf_basis_off"] = c(h.col_leaf_basis_off, np.int64)
             self.arrs["col_transfer_off"] = c(h.col_transfer_off, np.int64)
         self.dev = {}
-        if device is not None:
+        self.host_ptrs = {}
+        if device == "host":
+            names = ["leaf_basis", "transfer", "coupling", "near_block"]
+            if h.col_rank is not None:
+                names += ["col_leaf_basis", "col_transfer"]
+            self._keep = []
+            for nm in names:
+                if host is not None:
+                    self.host_ptrs[nm] = host[nm].data_ptr()
+                else:
+                    a = c(getattr(h, nm), np.float64)
+                    self._keep.append(a)
+                    self.host_ptrs[nm] = a.ctypes.data
+        elif device is not None:
             import torch
             names = ["leaf_basis", "transfer", "coupling", "near_block"]
             if h.col_rank is not None:
@@ -187,7 +207,7 @@ class H2Input:
             setattr(d, nm, _ptr(a.get(nm), ctypes.c_int64))
         for nm in ("leaf_basis", "transfer", "coupling", "near_block", "col_leaf_basis", "col_transfer"):
             t = self.dev.get(nm)
-            setattr(d, nm, t.data_ptr() if t is not None else None)
+            setattr(d, nm, t.data_ptr() if t is not None else self.host_ptrs.get(nm))
         return d
 
 
@@ -278,6 +298,24 @@ def h2sp_apply(h: Handle, op: int, x, y, stream=None):
            "h2sp_apply")
 
 
+def h2sp_solve_host(an, inp: H2Input, b_ptr: int, ldb: int, x_ptr: int, ldx: int, nrhs: int, flags: int = 0,
+                    prec: int = H2SP_FP32, mode: int = H2SP_GMRES, tol: float = 1e-10, maxit: int = 60,
+                    restart: int = 20, stream=None) -> SolveInfo:
+    """The whole path from host memory (inp built with device="host"; b and x
+    host arrays given by address and leading dimension, column-major)."""
+    o = Opts(int(flags))
+    so = SolveOpts(int(mode), float(tol), int(maxit), int(restart))
+    info = SolveInfo()
+    d = inp.desc()
+    st = lib().h2sp_solve_host(an.ptr if an is not None else None, ctypes.byref(d), ctypes.byref(o), int(prec),
+                               ctypes.byref(so), int(nrhs), _vp(b_ptr), int(ldb), _vp(x_ptr), int(ldx),
+                               ctypes.byref(info), _stream(stream))
+    if st not in (H2SP_OK, H2SP_ENOCONV):
+        _check(st, "h2sp_solve_host")
+    info.status = st
+    return info
+
+
 def h2sp_logdet(h: Handle, stream=None):
     """(log|det A|, sign of det S) per independent system: two arrays of length nsys."""
     nsys = h2sp_query(h)["nsys"]
@@ -318,6 +356,17 @@ def h2sp_export_Q(h: Handle, cluster: int, col: bool = False, stream=None):
     _check(lib().h2sp_export_Q(h.ptr, int(cluster), int(col), ctypes.byref(m), _ptr(q, ctypes.c_double),
                                _stream(stream)), "h2sp_export_Q")
     return q.reshape(m.value, m.value).T
+
+
+def h2sp_export_front(h: Handle, k: int, stream=None):
+    """(F, s): the factored front of supernode k as an f x f FP64 array and its supernode size."""
+    f, sz = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().h2sp_export_front(h.ptr, int(k), ctypes.byref(f), ctypes.byref(sz), None, _vp(None)),
+           "h2sp_export_front")
+    v = np.zeros(max(f.value * f.value, 1), np.float64)
+    _check(lib().h2sp_export_front(h.ptr, int(k), ctypes.byref(f), ctypes.byref(sz), _ptr(v, ctypes.c_double),
+                                   _stream(stream)), "h2sp_export_front")
+    return v[:f.value * f.value].reshape(f.value, f.value).T, int(sz.value)
 
 
 def h2sp_export_structure(h: Handle) -> dict:

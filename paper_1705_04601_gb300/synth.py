@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import os
 from typing import Callable, Optional
 
 import numpy as np
@@ -71,8 +72,12 @@ def points_ellipse(n: int, rng: np.random.Generator) -> np.ndarray:
 
 
 def _pairdist(x: np.ndarray, y: np.ndarray) -> np.ndarray:
-    d = x[:, None, :] - y[None, :, :]
-    return np.sqrt(np.einsum("ijk,ijk->ij", d, d))
+    d = np.subtract.outer(x[:, 0], y[:, 0])
+    r2 = d * d
+    for k in range(1, x.shape[1]):
+        d = np.subtract.outer(x[:, k], y[:, k])
+        r2 += d * d
+    return np.sqrt(r2)
 
 
 def kernel_log(x, y):
@@ -91,6 +96,52 @@ def kernel_yukawa(x, y):
     r = _pairdist(x, y)
     with np.errstate(divide="ignore", invalid="ignore"):
         return np.exp(-r) / r
+
+
+def _pool():
+    import concurrent.futures as cf
+    return cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1))
+
+
+def _sandwich_pairs(Lm, M, Rm, pairs, transpose_left):
+    """[Lm[t] @ M[i] @ Rm[s].T] (or Lm[t].T @ M[i] @ Rm[s] with
+    transpose_left) for pairs i = (t, s), batched by block shape."""
+    out = [None] * len(pairs)
+    groups = {}
+    for i, (t, s) in enumerate(pairs):
+        groups.setdefault((Lm[t].shape, M[i].shape, Rm[s].shape), []).append(i)
+    for idx in groups.values():
+        L = np.stack([Lm[pairs[i][0]] for i in idx])
+        X = np.stack([M[i] for i in idx])
+        Rr = np.stack([Rm[pairs[i][1]] for i in idx])
+        if transpose_left:
+            Y = np.matmul(np.matmul(L.transpose(0, 2, 1), X), Rr)
+        else:
+            Y = np.matmul(np.matmul(L, X), Rr.transpose(0, 2, 1))
+        for z, i in enumerate(idx):
+            out[i] = Y[z]
+    return out
+
+
+def _blocks_by_row(kf, rows_pts, cols_pts, pairs):
+    """Kernel blocks K(rows_pts[t], cols_pts[s]) for a list of (t, s) pairs
+    sorted by t: one kernel evaluation per row t over all its columns (the
+    values are those of evaluating each block alone), split back per pair."""
+    out = [None] * len(pairs)
+    i = 0
+    while i < len(pairs):
+        t = int(pairs[i][0])
+        j = i
+        while j < len(pairs) and int(pairs[j][0]) == t:
+            j += 1
+        cols = [cols_pts(int(pairs[z][1])) for z in range(i, j)]
+        K = kf(rows_pts(t), np.concatenate(cols, axis=0))
+        o = 0
+        for z, c in zip(range(i, j), cols):
+            out[z] = K[:, o:o + c.shape[0]]
+            o += c.shape[0]
+        i = j
+    return out
 
 
 def kernel_gauss(x, y):
@@ -480,27 +531,31 @@ def _truncation(tree, Tq, Z, far_pairs, Dorth, tol, col: bool):
     G = [None] * ncl
     B = [None] * ncl
     R = [0] * ncl
-    for d in range(D + 1):
-        for t in range(lp[d], lp[d + 1]):
-            p = tree.parent[t]
-            kt = Z[t].shape[0]
-            blocks = list(rows_of[t])
-            if p >= 0 and G[p].shape[1] > 0:
-                blocks.append(Tq[t] @ G[p])
-            if not blocks or kt == 0:
-                G[t] = np.zeros((kt, 0))
-                B[t] = np.zeros((kt, 0))
-                continue
-            Y = np.hstack(blocks)
-            G[t] = np.linalg.qr(Y.T, mode="r").T
-            u, sig, _ = np.linalg.svd(G[t], full_matrices=True)
-            if sig.size == 0 or sig[0] == 0.0:
-                G[t] = np.zeros((kt, 0))
-                B[t] = np.zeros((kt, 0))
-                continue
-            r = int(np.sum(sig > tol * sig[0]))
-            B[t] = u
-            R[t] = r
+
+    def one(t):
+        p = tree.parent[t]
+        kt = Z[t].shape[0]
+        blocks = list(rows_of[t])
+        if p >= 0 and G[p].shape[1] > 0:
+            blocks.append(Tq[t] @ G[p])
+        if not blocks or kt == 0:
+            G[t] = np.zeros((kt, 0))
+            B[t] = np.zeros((kt, 0))
+            return
+        Y = np.hstack(blocks)
+        G[t] = np.linalg.qr(Y.T, mode="r").T
+        u, sig, _ = np.linalg.svd(G[t], full_matrices=True)
+        if sig.size == 0 or sig[0] == 0.0:
+            G[t] = np.zeros((kt, 0))
+            B[t] = np.zeros((kt, 0))
+            return
+        B[t] = u
+        R[t] = int(np.sum(sig > tol * sig[0]))
+
+    # the clusters of one depth are independent (each needs only its parent's G)
+    with _pool() as ex:
+        for d in range(D + 1):
+            list(ex.map(one, range(lp[d], lp[d + 1])))
     return B, R
 
 
@@ -533,13 +588,13 @@ def build_h2(points: np.ndarray, kernel: str, leaf_size: int, p: int = 4, tol: O
     for c in range(1, ncl):
         par = tree.parent[c]
         T[c] = _tensor_lagrange(tree.box_lo[par], tree.box_hi[par], p, nodes[c])
-    Dfar = [kf(nodes[t], nodes[s]) for (t, s) in far]
+    Dfar = _blocks_by_row(kf, lambda t: nodes[t], lambda s: nodes[s], far)
     symmetric = kernel != "log_skew"
     col = None
     if tol is not None:
         Ql_r, Tq_r, Z_r = _orthogonalise(tree, kids, Rleaf, T)
         Ql_c, Tq_c, Z_c = (Ql_r, Tq_r, Z_r) if symmetric else _orthogonalise(tree, kids, Rleaf, T)
-        Dorth = [Z_r[t] @ Dfar[i] @ Z_c[s].T for i, (t, s) in enumerate(far)]
+        Dorth = _sandwich_pairs(Z_r, Dfar, Z_c, far, transpose_left=False)
         U_r, r_r = _truncation(tree, Tq_r, Z_r, far, Dorth, tol, col=False)
         if symmetric:
             U_c, r_c = U_r, r_r
@@ -549,7 +604,7 @@ def build_h2(points: np.ndarray, kernel: str, leaf_size: int, p: int = 4, tol: O
         rk = [max(a, b) for a, b in zip(r_r, r_c)]
         B_r = [U_r[t][:, :rk[t]] for t in range(ncl)]
         B_c = B_r if symmetric else [U_c[t][:, :rk[t]] for t in range(ncl)]
-        Dfar = [B_r[t].T @ Dorth[i] @ B_c[s] for i, (t, s) in enumerate(far)]
+        Dfar = _sandwich_pairs(B_r, Dorth, B_c, far, transpose_left=True)
         Rleaf = {t: Ql_r[t] @ B_r[t] for t in Ql_r}
         T = [None] + [B_r[c].T @ Tq_r[c] @ B_r[tree.parent[c]] for c in range(1, ncl)]
         rank = np.array([B_r[t].shape[1] for t in range(ncl)], dtype=np.int32)
@@ -574,14 +629,14 @@ def build_h2(points: np.ndarray, kernel: str, leaf_size: int, p: int = 4, tol: O
     near_ptr = np.zeros(nleaf + 1, dtype=np.int64)
     np.add.at(near_ptr, near[:, 0] - lp[D] + 1, 1)
     near_ptr = np.cumsum(near_ptr)
-    blocks = []
-    for (t, s) in near:
-        bt, st = int(tree.begin[t]), int(tree.size[t])
-        bs, ss = int(tree.begin[s]), int(tree.size[s])
-        blk = kf(pts[bt:bt + st], pts[bs:bs + ss])
+    def leaf_pts(t):
+        return pts[int(tree.begin[t]):int(tree.begin[t]) + int(tree.size[t])]
+
+    blocks = _blocks_by_row(kf, leaf_pts, leaf_pts, near)
+    for z, (t, s) in enumerate(near):
         if t == s:
-            np.fill_diagonal(blk, diag)
-        blocks.append(blk)
+            blocks[z] = np.array(blocks[z])
+            np.fill_diagonal(blocks[z], diag)
     near_block, near_off = _pack_colmajor(blocks)
     h = H2Matrix(
         n=n, dim=dim, depth=D, level_ptr=lp.astype(np.int32), parent=tree.parent.astype(np.int32),
