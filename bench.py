@@ -1,30 +1,41 @@
 #!/usr/bin/env python
 """Time to solution of A x = b at relative residual 1e-10 on one GB300.
 
-One step = the whole hot path on the 2D log-kernel H^2 matrix with 65,536
-points (leaf <= 64, basis tolerance 1e-6, 16 right-hand sides): the numeric
-sparsification h2sp_sparsify_analyzed (A = U S V^T), h2sp_factor (block LU
-of S) and h2sp_solve.  The host analysis of the structure (h2sp_analyze:
-level schedule, block pattern of S, symbolic factorization) runs once per
-structure, before the timed steps, and is reported as ``analysis_ms``.  Two
-paths:
+One step = the whole hot path on one H^2 matrix with inputs resident in HBM:
+the numeric sparsification h2sp_sparsify_analyzed (A = U S V^T), the
+factorization of S (h2sp_factor) and the solve (h2sp_solve).  The host
+analysis of the structure (h2sp_analyze: level schedule, block pattern of S,
+symbolic factorization) runs once per structure, before the timed steps, and
+is reported as ``analysis_ms``.
 
-* mixed (the headline): S from FP32 sandwich products (the Householder
-  completions stay FP64; --sparsify-prec fp64 keeps them all FP64), FP32
-  factorization of S, then restarted GMRES (or iterative refinement,
-  --solver ir) on the FP64 H^2 product, preconditioned by FP32 U^T, S^-1 and
-  V, until max_k ||b_k - A x_k|| / ||b_k|| <= 1e-10;
-* fp64: FP64 sparsification and factorization of S, refinement on the FP64
-  H^2 residual to 1e-10 (reported beside it).
+Default workload (the configuration the metric is stated on): 1/r on the
+jittered Fibonacci sphere, N = 262,144, octree leaf <= 128, Chebyshev 4^3
+bases recompressed to 1e-6, A_ii = 2 sqrt(N), one right-hand side.  S is
+symmetric positive definite there, so S is factored by the block Cholesky
+(--factor lu selects the block LU; the 2D -log r workloads need it).  Two
+paths on the same inputs:
 
-Inputs are resident in HBM when the timed region starts (the close blocks are
-443 MB, larger than the 129 MB L2, so no flush is needed); ``e2e`` repeats the
-mixed step from pinned host buffers with the copies inside the timed region.
+* mixed (the headline ``value``): S from FP32 sandwich products (the
+  Householder completions stay FP64), FP32 factorization of S with FP32
+  (three-term TF32) tensor-core updates, then restarted GMRES on the FP64 H^2
+  product, right-preconditioned by V S^-1 U^T, until
+  max_k ||b_k - A x_k|| / ||b_k|| <= 1e-10;
+* fp64 (``fp64_direct_s``): FP64 sparsification and factorization, the
+  direct solve refined on the FP64 H^2 residual to 1e-10.
 
-``--impl reference`` times the CPU FP64 oracle instead (the reference arm):
-each step runs the oracle's full pipeline on a bounded sample.
-Under torchrun every rank solves an independent replica; rank 0 prints one
-JSON line.
+``value`` comes from unprofiled steps; the per-kernel-class times and the
+roofline come from one extra step with CUDA events around every launch.
+``e2e`` repeats the mixed step through h2sp_solve_host from pinned host
+buffers (all numeric H^2 arrays and b copied in, x copied out, inside the
+timed region).  The close blocks (GBs) are larger than the 129 MB L2, so no
+flush is needed between steps.
+
+``--impl reference`` times the CPU FP64 oracle instead (the reference arm);
+``cpu_baseline`` times it once.  Both run the oracle as it stands on the
+N = 16,384 instance of the same workload (a bounded sample) and scale each
+phase to the benched N by its algorithmic work (sparsification flops, factor
+flops, factor entries for the solve).  Under torchrun every rank solves an
+independent replica; rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -42,39 +53,45 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time-to-solution at rel. residual 1e-10 (s), mixed vs FP64 GPU; factor GFLOP/s"
+DEFAULT_WORKLOAD = "inv3d_sphere_n262144"
 CPU_SAMPLE_N = 16384
+# workloads whose S is symmetric positive definite (1/r on the sphere with
+# A_ii = 2 sqrt(N)): the block Cholesky applies
+SPD_WORKLOADS = {"inv3d_sphere_n262144"}
 
-# Nominal peaks, used where MEASURED_PEAKS.json has no entry:
-#   FP32 SIMT  = 152 SMs x 128 lanes x 2 flop x 2.070 GHz
-#   FP64       = 1.25 TFLOP/s (GB300 nominal)
-FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-FP64_TFLOPS = 1.25
-
-# DRAM traffic of the dominant kernel from an ncu capture: per kernel class,
-# dram bytes read + written over the class's algorithmic work in the captured
-# run, valid while the kernel's source file is unchanged (sha256 prefix of
-# "src").  The bench's traffic figure is this ratio times the class's average
-# work per launch.  Empty: the current captures (profiles/) are single
-# small-case launches whose algorithmic work is not known per launch, so the
-# traffic field is null.
+# DRAM traffic of the dominant kernel from an ncu capture, per kernel class:
+# dram bytes read + written of the captured launch divided by that launch's
+# algorithmic work, valid while the kernel's source file is unchanged (sha256
+# prefix of "src").  The bench's traffic figure is this ratio times the
+# class's average work per launch.
 TRAFFIC = {}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="log2d_n65536")
-    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--n", type=int, default=None, help="points (default: the workload's own N)")
+    ap.add_argument("--factor", default="auto", choices=["auto", "chol", "lu"],
+                    help="block Cholesky (SPD S) or block LU; auto: Cholesky on the SPD workloads")
+    ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 path steps timed (0: skip)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--sparsify-prec", default="fp32", choices=["fp32", "fp64"],
-                    help="precision of U, S, V on the mixed path (the FP64 path always sparsifies in FP64)")
+                    help="precision of the products into S on the mixed path (the FP64 path is FP64 throughout)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--solver", default="gmres", choices=["gmres", "ir"],
                     help="outer iteration of the mixed path on the FP64 H^2 residual")
-    return ap.parse_args()
+    return ap.parse_args(argv)
+
+
+def factor_kind(args):
+    if args.factor != "auto":
+        return args.factor
+    return "chol" if args.workload in SPD_WORKLOADS else "lu"
 
 
 def dist_setup(n):
@@ -165,17 +182,21 @@ def kernel_source_hash(fname):
     return hashlib.sha256(src).hexdigest()[:16]
 
 
-def roofline(prof, timed_launches_ok=True, sparsify_fp32=False):
+def roofline(prof, fma_peaks, fp32_gemm_tc=True, sparsify_fp32=False):
     """Dominant kernel class by event time -> achieved vs its peak.
 
     The library's profiler records per class the algorithmic work of its
-    launches: bytes for HBM-bound classes, flops for ALU-bound ones.
-      gemm_update   tensor-core rank-64 update: HBM-bound, bytes (C read + written, L21, U12)
-                    (H2SP_GEMM=simt: FP32 CUDA-core flops)
+    launches (h2sp_kernel_times):
+      gemm_update   the trailing update of the fronts, flops.  FP32 on the
+                    tensor cores (three-term TF32 split, three MMAs per FP32
+                    product): bound "tensor" against the three-pass ceiling
+                    = measured BF16 dense rate x 0.5 (TF32 : BF16 nominal) / 3;
+                    FP64 (or H2SP_GEMM=simt FP32): CUDA-core FMA pipe
       panel, swap_trsm   FP32 flops (CUDA cores)
-      transform, householder, coupling   FP64 flops (FP64 pipe), FP32 flops with an FP32 sparsification
-      h2_matvec     FP64 flops (FP64 pipe)
-      solve, apply, assemble, extend_add, vector    bytes
+      transform     FP64 flops (FP32 with an FP32 sparsification)
+      h2_matvec     FP64 flops
+      the others    bytes (HBM)
+    fma_peaks: {"fp64": TFLOP/s, "fp32": TFLOP/s} measured by h2sp_measure_peak.
     """
     cls = max(prof, key=lambda c: prof[c]["ms"])
     p = prof[cls]
@@ -183,29 +204,46 @@ def roofline(prof, timed_launches_ok=True, sparsify_fp32=False):
     work_per_launch = p["work"] / max(p["timed"], 1)
     peaks = measured_peaks()
     out = {"kernel": cls, "launches_timed": p["timed"], "avg_launch_ms": per_launch_ms}
-    simt_gemm = os.environ.get("H2SP_GEMM", "") == "simt"
-    sp_cls = ("transform", "householder", "coupling")
-    if cls in ("panel", "swap_trsm") or (cls == "gemm_update" and simt_gemm) or (cls in sp_cls and sparsify_fp32):
-        achieved = p["work"] / (p["ms"] * 1e-3) / 1e12
-        out.update(bound="alu", achieved=achieved, peak=FP32_SIMT_TFLOPS, unit="TFLOP/s",
-                   peak_source="derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal max clock)")
-    elif cls in sp_cls or cls == "h2_matvec":
-        achieved = p["work"] / (p["ms"] * 1e-3) / 1e12
-        out.update(bound="alu", achieved=achieved, peak=FP64_TFLOPS, unit="TFLOP/s",
-                   peak_source="nominal GB300 FP64 (1.25 TFLOP/s); no measured FP64 peak available")
+    achieved_t = p["work"] / max(p["ms"] * 1e-3, 1e-30) / 1e12
+    if cls == "gemm_update" and fp32_gemm_tc:
+        bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+        src = "measured (MEASURED_PEAKS.json bf16_tflops_sustained)" if bf16 else "fallback 1700 TFLOP/s bf16"
+        bf16 = bf16 or 1700.0
+        tf32 = 0.5 * bf16
+        out.update(bound="tensor", achieved=achieved_t, peak=tf32 / 3.0, unit="TFLOP/s",
+                   peak_source=src + " x 0.5 (TF32:BF16 nominal) / 3 (three TF32 MMAs per FP32 product)",
+                   tf32_pipe_frac=3.0 * achieved_t / tf32)
+    elif cls in ("gemm_update", "panel", "swap_trsm", "transform", "h2_matvec"):
+        # the profiled step is the mixed one: its gemm_update here is the FP32 CUDA-core update
+        fp64 = cls == "h2_matvec" or (cls == "transform" and not sparsify_fp32)
+        key = "fp64" if fp64 else "fp32"
+        out.update(bound="alu", achieved=achieved_t, peak=fma_peaks[key], unit="TFLOP/s",
+                   peak_source="measured: h2sp_measure_peak %s FMA chains on every SM, CUDA events" % key.upper())
     else:
-        achieved = p["work"] / (p["ms"] * 1e-3) / 1e9
+        achieved = p["work"] / max(p["ms"] * 1e-3, 1e-30) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         out.update(bound="hbm", achieved=achieved, peak=peak, unit="GB/s",
                    peak_source="measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback")
     out["frac"] = out["achieved"] / out["peak"]
     out["work_per_launch"] = work_per_launch
     tr = TRAFFIC.get(cls)
-    valid = tr is not None and not simt_gemm and tr["src_hash"] == kernel_source_hash(tr["src"])
+    valid = tr is not None and tr["src_hash"] == kernel_source_hash(tr["src"])
     out["traffic"] = tr["dram_over_algorithmic"] * work_per_launch if valid else None
     if valid:
         out["traffic_source"] = tr["capture"]
     return out
+
+
+def workload_config(name, n, nrhs, kind, sparsify_prec):
+    from paper_1705_04601_gb300 import synth
+    w = synth.WORKLOADS[name]
+    kern = {"inv": "1/r", "log": "-log r", "yukawa": "exp(-r)/r"}[w["kernel"]]
+    pts = {"sphere": "jittered Fibonacci sphere (seeded)"}.get(w.get("points", ""),
+                                                                "uniform [0,1]^%d (seeded)" % w["dim"])
+    return {"workload": name, "n": int(n), "leaf": w["leaf"], "basis_tol": w["tol"], "nrhs": int(nrhs),
+            "kernel": kern, "points": pts, "factor": "block Cholesky" if kind == "chol" else "block LU",
+            "sparsify_prec": sparsify_prec, "factor_prec": "fp32",
+            "l2": "inputs larger than L2 (close blocks of several GB resident in HBM); no flush"}
 
 
 def run_ours(args, ws, rank, local):
@@ -217,212 +255,249 @@ def run_ours(args, ws, rank, local):
     from paper_1705_04601_gb300 import synth
 
     build.build()
+    kind = factor_kind(args)
+    prec32 = H.H2SP_FP32_CHOL if kind == "chol" else H.H2SP_FP32
+    prec64 = H.H2SP_FP64_CHOL if kind == "chol" else H.H2SP_FP64
     t0 = time.time()
-    h, b = synth.make_workload(args.workload)
+    h, b = synth.make_workload(args.workload, n=getattr(args, "n", None))
     gen_s = time.time() - t0
     inp = H.H2Input(h)
     # symbolic analysis: once per structure, outside the timed steps
     ta = time.perf_counter()
     an = H.h2sp_analyze(H.H2Input(h, device=None))
     analysis_ms = (time.perf_counter() - ta) * 1e3
+    stats = H.h2sp_query(an)
+    fl32 = stats["chol_flops"] if kind == "chol" else stats["factor_flops"]
     bt = torch.from_numpy(np.ascontiguousarray(b.T)).cuda()
     xt = torch.empty_like(bt)
     stream = torch.cuda.current_stream()
+    fma = {"fp64": H.h2sp_measure_peak(0), "fp32": H.h2sp_measure_peak(1)}
 
     def ev():
         return torch.cuda.Event(enable_timing=True)
 
     mode = H.H2SP_GMRES if args.solver == "gmres" else H.H2SP_IR
-
     sp_flags = H.H2SP_SPARSIFY_FP32 if args.sparsify_prec == "fp32" else 0
 
-    def mixed_step(profile=False):
+    def mixed_step(profile=False, marks=None):
+        if marks:
+            marks[0].record(stream)
         hd = H.h2sp_sparsify_analyzed(an, inp, flags=sp_flags)
         if profile:
-            H.h2sp_profile(hd, timing=1, reset=True)
-        H.h2sp_factor(hd, H.H2SP_FP32)
+            H.h2sp_profile(hd, timing=1)
+        if marks:
+            marks[1].record(stream)
+        H.h2sp_factor(hd, prec32)
+        if marks:
+            marks[2].record(stream)
         info = H.h2sp_solve(hd, bt, xt, mode=mode, tol=1e-10, maxit=60, restart=20)
+        if marks:
+            marks[3].record(stream)
         return hd, info
-
-    def fp64_step():
-        # FP64 factorization; refinement on the FP64 H^2 residual stops as soon as 1e-10 holds
-        hd = H.h2sp_sparsify_analyzed(an, inp)
-        H.h2sp_factor(hd, H.H2SP_FP64)
-        info64 = H.h2sp_solve(hd, bt, xt, mode=H.H2SP_IR, tol=1e-10, maxit=10)
-        return hd, info64
 
     for _ in range(args.warmup):
         hd, info = mixed_step()
         hd.close()
     torch.cuda.synchronize()
 
-    # ---- timed mixed steps (per-kernel events on the library's launch stream) ----
+    # ---- timed mixed steps, unprofiled ----
     clocks = Clocks(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
     barrier(ws)
     torch.cuda.synchronize()
     evs = [ev() for _ in range(args.steps + 1)]
     evs[0].record(stream)
-    prof_sum, launches, infos, stats = None, 0, [], None
-    # each step builds, factors and solves with its own handle; the handles
-    # are read (per-kernel events) and released after the timed region, so
-    # the host work of freeing them does not sit between two steps
-    handles = []
+    infos = []
+    launches = 0
+    # each step builds, factors and solves with its own handle and releases it
+    # (its fronts alone can be ~100 GB); the memory goes back to the
+    # stream-ordered pool, which keeps it for the next step
     for k in range(args.steps):
-        hd, info = mixed_step(profile=True)
+        hd, info = mixed_step()
         evs[k + 1].record(stream)
-        handles.append(hd)
-        infos.append((info.iters, info.rel_residual, info.status))
+        infos.append((int(info.iters), float(info.rel_residual), int(info.status)))
+        launches += sum(v["launches"] for v in H.h2sp_profile(hd, timing=-1).values())
+        hd.close()
     torch.cuda.synchronize()
     barrier(ws)
     clk = clocks.stop()
-    for hd in handles:
-        pr = H.h2sp_profile(hd, timing=0)
-        launches += sum(v["launches"] for v in pr.values())
-        if prof_sum is None:
-            prof_sum = {c: dict(v) for c, v in pr.items()}
-            stats = H.h2sp_query(hd)
-        else:
-            for c, v in pr.items():
-                for f in v:
-                    prof_sum[c][f] += v[f]
-        hd.close()
-    del handles
     step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     mixed_s = max_over_ranks(sum(step_ms) / 1e3, ws) / args.steps
+    res_mixed = max(r for (_, r, _) in infos)
+    converged = all(st == H.H2SP_OK for (_, _, st) in infos) and res_mixed <= 1e-10
     x_mixed = xt.clone()
 
-    # ---- FP64 direct path ----
-    hd, _ = fp64_step()
-    hd.close()
+    # ---- one profiled mixed step: per-class event times, phases ----
+    marks = [ev() for _ in range(4)]
+    hd, _ = mixed_step(profile=True, marks=marks)
     torch.cuda.synchronize()
-    e0, e1 = ev(), ev()
-    e0.record(stream)
-    for _ in range(args.fp64_steps):
-        hd, info64 = fp64_step()
-        if _ < args.fp64_steps - 1:
+    prof = H.h2sp_profile(hd, timing=0)
+    hd.close()
+    phase = {"sparsify_ms": marks[0].elapsed_time(marks[1]), "factor_fp32_ms": marks[1].elapsed_time(marks[2]),
+             "solve_ms": marks[2].elapsed_time(marks[3]), "analysis_ms": analysis_ms}
+
+    # ---- FP64 path on the same inputs (phases timed inside the step) ----
+    fp64_s, res64, info64, diff = None, None, None, None
+    if args.fp64_steps > 0:
+        tot = 0.0
+        for _ in range(args.fp64_steps):
+            m = [ev() for _ in range(4)]
+            m[0].record(stream)
+            hd = H.h2sp_sparsify_analyzed(an, inp)
+            m[1].record(stream)
+            H.h2sp_factor(hd, prec64)
+            m[2].record(stream)
+            info64 = H.h2sp_solve(hd, bt, xt, mode=H.H2SP_IR, tol=1e-10, maxit=10)
+            m[3].record(stream)
+            torch.cuda.synchronize()
+            tot += m[0].elapsed_time(m[3]) / 1e3
+            phase.update(sparsify_fp64_ms=m[0].elapsed_time(m[1]), factor_fp64_ms=m[1].elapsed_time(m[2]),
+                         solve_fp64_ms=m[2].elapsed_time(m[3]))
+            yt = torch.empty_like(xt)
+            H.h2sp_apply(hd, H.H2SP_OP_H2, xt, yt)
+            res64 = float(((bt - yt).norm(dim=1) / bt.norm(dim=1)).max())
             hd.close()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    fp64_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, ws) / args.fp64_steps
-    # residual of the FP64 direct solution with the library's FP64 H^2 product
-    yt = torch.empty_like(xt)
-    H.h2sp_apply(hd, H.H2SP_OP_H2, xt, yt)
-    res64 = float(((bt - yt).norm(dim=1) / bt.norm(dim=1)).max())
-    diff = float((x_mixed - xt).norm() / xt.norm())
-    hd.close()
+        fp64_s = max_over_ranks(tot, ws) / args.fp64_steps
+        if info64.status != H.H2SP_OK or not (res64 <= 1e-10):
+            fp64_s = None
+        diff = float((x_mixed - xt).norm() / xt.norm())
 
-    # ---- separate phase timing of one mixed step (outside the timed region) ----
-    phase = {}
-    e = [ev() for _ in range(4)]
-    e[0].record(stream)
-    hd = H.h2sp_sparsify_analyzed(an, inp, flags=sp_flags)
-    e[1].record(stream)
-    H.h2sp_factor(hd, H.H2SP_FP32)
-    e[2].record(stream)
-    H.h2sp_solve(hd, bt, xt, mode=mode, tol=1e-10, maxit=60, restart=20)
-    e[3].record(stream)
-    torch.cuda.synchronize()
-    phase = {"sparsify_ms": e[0].elapsed_time(e[1]), "factor_fp32_ms": e[1].elapsed_time(e[2]),
-             "refine_ms": e[2].elapsed_time(e[3]), "analysis_ms": analysis_ms}
-    hd.close()
-    # the FP64 factorization alone, for its GFLOP/s (also outside the timed region)
-    e = [ev() for _ in range(3)]
-    e[0].record(stream)
-    hd = H.h2sp_sparsify_analyzed(an, inp)
-    e[1].record(stream)
-    H.h2sp_factor(hd, H.H2SP_FP64)
-    e[2].record(stream)
-    torch.cuda.synchronize()
-    phase["sparsify_fp64_ms"] = e[0].elapsed_time(e[1])
-    phase["factor_fp64_ms"] = e[1].elapsed_time(e[2])
-    hd.close()
-
-    # ---- e2e: host (pinned) buffers, copies inside the timed region ----
+    # ---- e2e: the whole path from pinned host buffers through h2sp_solve_host ----
     e2e = None
     if not args.no_e2e:
         names = ["leaf_basis", "transfer", "coupling", "near_block"]
         pinned = {nm: torch.from_numpy(np.ascontiguousarray(getattr(h, nm))).pin_memory() for nm in names}
+        hinp = H.H2Input(h, device="host", host=pinned)
         b_pin = torch.from_numpy(np.ascontiguousarray(b.T)).pin_memory()
         x_pin = torch.empty_like(b_pin).pin_memory()
         h2d = sum(t.numel() * 8 for t in pinned.values()) + b_pin.numel() * 8
         d2h = x_pin.numel() * 8
+        nr = int(b.shape[1])
+        sh = torch.cuda.current_stream().cuda_stream
 
         def e2e_step():
-            inp2 = H.H2Input(h, nonblocking_from=pinned)
-            b2 = b_pin.cuda(non_blocking=True)
-            x2 = torch.empty_like(b2)
-            hd2 = H.h2sp_sparsify_analyzed(an, inp2, flags=sp_flags)
-            H.h2sp_factor(hd2, H.H2SP_FP32)
-            H.h2sp_solve(hd2, b2, x2, mode=mode, tol=1e-10, maxit=60, restart=20)
-            x_pin.copy_(x2, non_blocking=True)
-            return hd2, inp2
+            return H.h2sp_solve_host(an, hinp, b_pin.data_ptr(), h.n, x_pin.data_ptr(), h.n, nr, flags=sp_flags,
+                                     prec=prec32, mode=mode, tol=1e-10, stream=sh)
 
-        hd2, _ = e2e_step()
+        e2e_step()
         torch.cuda.synchronize()
-        hd2.close()
         barrier(ws)
+        ks = max(1, min(args.steps, args.e2e_steps))
         a0, a1 = ev(), ev()
         a0.record(stream)
-        keep = []
-        for _ in range(args.steps):
-            hd2, inp2 = e2e_step()
-            keep.append((hd2, inp2))
+        e2e_infos = [e2e_step() for _ in range(ks)]
         a1.record(stream)
         torch.cuda.synchronize()
-        for hd2, _ in keep:
-            hd2.close()
-        e2e_s = max_over_ranks(a0.elapsed_time(a1) / 1e3, ws) / args.steps
-        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        e2e_s = max_over_ranks(a0.elapsed_time(a1) / 1e3, ws) / ks
+        ok = all(i.status == H.H2SP_OK and i.rel_residual <= 1e-10 for i in e2e_infos)
+        e2e = {"value": e2e_s if ok else None, "unit": "s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": ks, "entry": "h2sp_solve_host"}
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(args.workload)
+        cpu = cpu_oracle_sample(args.workload, kind, h)
 
-    roof = roofline(prof_sum, sparsify_fp32=(args.sparsify_prec == "fp32"))
-    fl = stats["factor_flops"]
-    res_mixed = max(r for (_, r, _) in infos)
+    roof = roofline(prof, fma, fp32_gemm_tc=os.environ.get("H2SP_GEMM", "") != "simt",
+                    sparsify_fp32=(args.sparsify_prec == "fp32"))
     out = {
-        "metric": METRIC, "value": mixed_s, "unit": "s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": mixed_s * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64+f32", "data": "synthetic",
-        "config": {"workload": args.workload, "n": int(h.n), "leaf": 64, "basis_tol": 1e-6, "nrhs": int(b.shape[1]),
-                   "kernel": "-log r", "points": "uniform [0,1]^2 (seeded)",
-                   "l2": "inputs larger than L2 (443 MB of close blocks resident in HBM)",
-                   "parallelism": "replicas" if ws > 1 else "single GPU",
-                   "sparsify_prec": args.sparsify_prec, "factor_prec": "fp32"},
-        "mixed_s": mixed_s, "fp64_direct_s": fp64_s, "speedup_mixed_vs_fp64": fp64_s / mixed_s,
-        "factor_flops": fl, "factor_gflops_fp32": None, "factor_gflops_fp64": None,
-        "solver": args.solver, "refine_iters": [i for (i, _, _) in infos], "rel_residual_mixed": res_mixed, "rel_residual_fp64": res64,
-        "fp64_refine_iters": info64.iters,
+        "metric": METRIC, "value": mixed_s if converged else None, "unit": "s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mixed_s * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": dict(workload_config(args.workload, h.n, b.shape[1], kind, args.sparsify_prec),
+                       parallelism="replicas" if ws > 1 else "single GPU"),
+        "mixed_s": mixed_s, "converged": converged, "fp64_direct_s": fp64_s,
+        "speedup_mixed_vs_fp64": (fp64_s / mixed_s) if (fp64_s and converged) else None,
+        "factor_flops": fl32, "factor_gflops_fp32": fl32 / (phase["factor_fp32_ms"] * 1e-3) / 1e9,
+        "factor_gflops_fp64": (fl32 / (phase["factor_fp64_ms"] * 1e-3) / 1e9) if "factor_fp64_ms" in phase else None,
+        "solver": args.solver, "iters": [i for (i, _, _) in infos], "rel_residual_mixed": res_mixed,
+        "rel_residual_fp64": res64, "fp64_refine_iters": info64.iters if info64 is not None else None,
         "mixed_vs_fp64_rel_diff": diff, "phase_ms": phase, "input_gen_s": gen_s,
-        "roofline": roof, "e2e": e2e, "gpu_launches": int(launches),
-        "gpu_launches_per_step": int(launches / max(args.steps, 1)),
-        "kernel_ms_per_step": {c: v["ms"] / args.steps for c, v in prof_sum.items() if v["ms"] > 0},
+        "structure": {"max_front": stats["max_front"], "nsupernodes": stats["nsupernodes"],
+                      "nnz_S": stats["nnz"], "front_elems": stats["front_elems"]},
+        "fma_peaks_tflops": fma, "roofline": roof, "e2e": e2e,
+        "gpu_launches": int(launches), "gpu_launches_per_step": int(launches / max(args.steps, 1)),
+        "kernel_ms_per_step": {c: v["ms"] for c, v in prof.items() if v["ms"] > 0},
         "clocks": clk, "cpu_baseline": cpu,
     }
-    out["factor_gflops_fp32"] = fl / (phase["factor_fp32_ms"] * 1e-3) / 1e9
-    out["factor_gflops_fp64"] = fl / (phase["factor_fp64_ms"] * 1e-3) / 1e9
     return out
 
 
-def cpu_oracle_sample(workload, n=CPU_SAMPLE_N):
-    """The oracle, as it stands, on the N=16384 instance of the same workload family."""
+def _oracle_step(h, b, kind):
+    """The oracle's pipeline, phase by phase: sparsify, factor, solve (FP64)."""
+    from oracle import factor as ofa
+    from oracle import sparsify as osp
+    t0 = time.perf_counter()
+    sp = osp.sparsify(h)
+    t1 = time.perf_counter()
+    fa = ofa.cholesky(h, sp) if kind == "chol" else ofa.factor(h, sp)
+    t2 = time.perf_counter()
+    if kind == "chol":
+        c = osp.apply_T(sp, h, b, col=False)
+        x = osp.apply_N(sp, h, ofa.solve_S_chol(fa, c), col=True)
+    else:
+        x = ofa.solve(h, sp, fa, b)
+    t3 = time.perf_counter()
+    return x, (t1 - t0, t2 - t1, t3 - t2)
+
+
+def _oracle_work(h, kind):
+    """Algorithmic work of the oracle's three phases on an H^2 matrix, from
+    the oracle's own structure (no numerical work): the level schedule, the
+    block pattern of S predicted from the close lists, and the symbolic
+    factorization on it.  (sparsification: sum over each level's close pairs
+    of m_t m_s (m_t + m_s); factor: flops of the block Cholesky / LU; solve:
+    entries of the factors.)"""
+    import types
+
     import numpy as np
 
     from oracle import factor as ofa
     from oracle import sparsify as osp
+    sch = osp.schedule(h)
+    sym = ofa.symbolic(h, types.SimpleNamespace(sch=sch, blocks=dict.fromkeys(osp.pattern_rule(h, sch))))
+    m = sch.m
+    wsp = 0.0
+    for lev in range(sch.lstop):
+        pr = sch.near[lev]
+        if len(pr):
+            mt, ms = m[pr[:, 0]].astype(float), m[pr[:, 1]].astype(float)
+            wsp += float(np.sum(mt * ms * (mt + ms)))
+    size = sch.node_size
+    fl, ent = 0.0, 0.0
+    for k in range(sym.sn_ptr.size - 1):
+        sv = float(sum(size[int(v)] for v in sym.order[sym.sn_ptr[k]:sym.sn_ptr[k + 1]]))
+        bv = float(sum(size[int(w)] for w in sym.boundary[k]))
+        fl += (sv ** 3 / 3.0 + sv * sv * bv + sv * bv * bv) if kind == "chol" else \
+            (2.0 / 3.0 * sv ** 3 + 2.0 * sv * sv * bv + 2.0 * sv * bv * bv)
+        ent += sv * sv + 2.0 * sv * bv
+    return wsp, fl, ent
+
+
+def _work_ratios(h_full, h_sample, kind):
+    wf, ws_ = _oracle_work(h_full, kind), _oracle_work(h_sample, kind)
+    return tuple(a / b for a, b in zip(wf, ws_))
+
+
+def cpu_oracle_sample(workload, kind, h_full, n=CPU_SAMPLE_N):
+    """The oracle, as it stands, on the N = 16,384 instance of the same
+    workload, each phase scaled to the benched N by its algorithmic work."""
+    import numpy as np
+
     from paper_1705_04601_gb300 import synth
-    h, b = synth.make_workload(workload, n=n)
-    t0 = time.time()
-    sp = osp.sparsify(h)
-    fa = ofa.factor(h, sp)
-    x = ofa.solve(h, sp, fa, b)
-    dt = time.time() - t0
+    hs, bs = synth.make_workload(workload, n=n)
+    x, ph = _oracle_step(hs, bs, kind)
     assert np.all(np.isfinite(x))
-    return {"value": dt, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "oracle sparsify + FP64 block LU + direct solve (16 RHS) on the N=%d instance of the same "
-                      "2D -log r workload (leaf<=64, basis tol 1e-6); not scaled to N=65536" % n}
+    ratios = _work_ratios(h_full, hs, kind)
+    nfull, nsamp = int(h_full.n), int(hs.n)
+    scaled = sum(t * r for t, r in zip(ph, ratios))
+    return {"value": scaled, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": ("oracle (FP64 sparsify + block %s + direct solve) on the N=%d instance of the same workload, "
+                       "phases %.2f / %.2f / %.2f s, scaled to N=%d by algorithmic work x %.1f / %.1f / %.1f "
+                       "(sparsification work, factor flops, factor entries, counted on the oracle's own schedule, block pattern "
+                       "and symbolic factorization)"
+                       % ("Cholesky" if kind == "chol" else "LU", nsamp, ph[0], ph[1], ph[2], nfull,
+                          ratios[0], ratios[1], ratios[2])),
+            "sample_phases_s": list(ph), "scale": list(ratios), "sample_n": nsamp}
 
 
 def run_reference(args, ws, rank):
@@ -430,30 +505,32 @@ def run_reference(args, ws, rank):
         return None
     import numpy as np
 
-    from oracle import factor as ofa
-    from oracle import sparsify as osp
     from paper_1705_04601_gb300 import synth
+    kind = factor_kind(args)
     h, b = synth.make_workload(args.workload, n=CPU_SAMPLE_N)
-
-    def step():
-        sp = osp.sparsify(h)
-        fa = ofa.factor(h, sp)
-        return ofa.solve(h, sp, fa, b)
-
+    h_full, _ = synth.make_workload(args.workload, n=getattr(args, "n", None))  # its structure only enters the scaling
+    ratios = _work_ratios(h_full, h, kind)
+    nfull, nsamp = int(h_full.n), int(h.n)
+    del h_full
     for _ in range(args.warmup):
-        step()
-    t0 = time.time()
+        _oracle_step(h, b, kind)
+    tot, ph_sum = 0.0, [0.0, 0.0, 0.0]
     for _ in range(args.steps):
-        x = step()
-    dt = (time.time() - t0) / args.steps
+        x, ph = _oracle_step(h, b, kind)
+        tot += sum(t * r for t, r in zip(ph, ratios))
+        ph_sum = [a + c for a, c in zip(ph_sum, ph)]
+    dt = tot / args.steps
     assert np.all(np.isfinite(x))
-    sample = ("oracle sparsify + FP64 block LU + direct solve (16 RHS) on the N=%d instance of the same 2D -log r "
-              "workload (leaf<=64, basis tol 1e-6)" % CPU_SAMPLE_N)
+    sample = ("oracle (FP64 sparsify + block %s + direct solve) on the N=%d instance of the same workload per step, "
+              "phases scaled to N=%d by algorithmic work x %.1f / %.1f / %.1f"
+              % ("Cholesky" if kind == "chol" else "LU", nsamp, nfull, ratios[0], ratios[1], ratios[2]))
     return {"impl": "reference", "metric": METRIC, "value": dt, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n": CPU_SAMPLE_N, "sample_of_n": 65536},
-            "cpu_baseline": {"value": dt, "unit": "s", "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
+            "config": {"workload": args.workload, "n": nfull, "sample_n": nsamp,
+                       "factor": "block Cholesky" if kind == "chol" else "block LU"},
+            "cpu_baseline": {"value": dt, "unit": "s", "cores": os.cpu_count(), "kind": "oracle", "sample": sample,
+                             "sample_phases_s": [p / args.steps for p in ph_sum]},
             "e2e": {"value": dt, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

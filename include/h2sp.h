@@ -375,8 +375,11 @@ int h2sp_export_front(h2sp_handle *h, int32_t k, int64_t *f, int64_t *s, double 
  *  3 extend-add into parent fronts          9 FP64 H^2 product
  *  4 S blocks into fronts                  10 U^T / V applies
  *  5 close-block / panel transforms        11 vector kernels, casts, permutations
- * work[] is the algorithmic flop count (classes 0, 1, 2, 5), bytes (4, 8, 9)
- * or elements (3) of the timed launches; 0 where not defined. */
+ * 12 FP32 blocked factorizations: in-block rank-64 tensor-core updates and
+ *    operand packing
+ * work[] is the algorithmic flop count (classes 0, 1, 2, 5, 9), bytes (4, 8,
+ * 11, 12) or elements (3) of the timed launches; 0 where not defined (6, 7,
+ * 10). */
 typedef struct {
   int64_t launches[16];   /* kernel launches since the last reset (always counted) */
   int64_t timed[16];      /* launches or launch groups bracketed by CUDA events */
@@ -420,6 +423,16 @@ int h2sp_profile(h2sp_handle *h, int32_t timing, int32_t reset, h2sp_kernel_time
  */
 int h2sp_h2_matvec_static(const h2sp_handle *h, int32_t nrhs, const double *x, int64_t ldx, double *y, int64_t ldy,
                           h2sp_stream stream);
+
+/*
+ * h2sp_measure_peak -- the fused multiply-add rate of the current device in
+ * TFLOP/s into *tflops: kind 0 for FP64, 1 for FP32 on the CUDA cores.  One
+ * warm-up and one timed launch (CUDA events on `stream`, about 50 ms) of
+ * independent FMA chains on every multiprocessor.  A measurement aid for the
+ * roofline fractions of the FP64 / FP32 CUDA-core kernels; the paper has no
+ * counterpart.  Synchronises the stream.
+ */
+int h2sp_measure_peak(int32_t kind, double *tflops, h2sp_stream stream);
 
 /* h2sp_query -- fill *st with the handle's sizes and counters. */
 int h2sp_query(const h2sp_handle *h, h2sp_stats *st);

@@ -27,6 +27,23 @@ struct CudaFail {
   cudaError_t e;
 };
 
+// cudaMallocAsync that, when the device is out of memory, returns the memory
+// the current device's pool keeps from freed buffers (the pool is set to
+// keep it between calls) and tries once more.
+cudaError_t malloc_async(void **p, size_t bytes, cudaStream_t s) {
+  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e != cudaErrorMemoryAllocation) return e;
+  cudaGetLastError();
+  int dev = 0;
+  cudaMemPool_t pool;
+  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess || cudaMemPoolTrimTo(pool, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocAsync(p, bytes, s);
+}
+
 inline void ck(cudaError_t e) {
   if (e != cudaSuccess) {
     g_cuda_err = cudaGetErrorString(e);
@@ -173,7 +190,7 @@ struct h2sp_handle {
   T *alloc(size_t n) {
     if (n == 0) n = 1;
     void *p = nullptr;
-    ck(cudaMallocAsync(&p, n * sizeof(T), stream));
+    ck(malloc_async(&p, n * sizeof(T), stream));
     allocs.push_back(p);
     return static_cast<T *>(p);
   }
@@ -1590,7 +1607,7 @@ int h2sp_solve_host(const h2sp_handle *an, const h2sp_h2_desc *desc, const h2sp_
     auto up = [&](const double *src, int64_t n) -> const double * {
       if (src == nullptr) return nullptr;
       void *p = nullptr;
-      ck(cudaMallocAsync(&p, size_t(std::max<int64_t>(n, 1)) * sizeof(double), s));
+      ck(malloc_async(&p, size_t(std::max<int64_t>(n, 1)) * sizeof(double), s));
       bufs.push_back(p);
       if (n > 0) ck(cudaMemcpyAsync(p, src, size_t(n) * sizeof(double), cudaMemcpyHostToDevice, s));
       return static_cast<const double *>(p);
@@ -1604,9 +1621,9 @@ int h2sp_solve_host(const h2sp_handle *an, const h2sp_h2_desc *desc, const h2sp_
     dd.col_transfer = up(desc->col_transfer, z.col_transfer);
     const int64_t n = desc->n;
     void *db = nullptr, *dx = nullptr;
-    ck(cudaMallocAsync(&db, size_t(std::max<int64_t>(n * nrhs, 1)) * sizeof(double), s));
+    ck(malloc_async(&db, size_t(std::max<int64_t>(n * nrhs, 1)) * sizeof(double), s));
     bufs.push_back(db);
-    ck(cudaMallocAsync(&dx, size_t(std::max<int64_t>(n * nrhs, 1)) * sizeof(double), s));
+    ck(malloc_async(&dx, size_t(std::max<int64_t>(n * nrhs, 1)) * sizeof(double), s));
     bufs.push_back(dx);
     if (n > 0)
       ck(cudaMemcpy2DAsync(db, size_t(n) * sizeof(double), b, size_t(ldb) * sizeof(double), size_t(n) * sizeof(double),
@@ -1762,6 +1779,17 @@ int h2sp_export_front(h2sp_handle *h, int32_t k, int64_t *f, int64_t *sz, double
       std::memcpy(vals, tmp.data(), n * sizeof(double));
   } catch (const CudaFail &e) {
     return status_of(e.e);
+  }
+  return H2SP_OK;
+}
+
+int h2sp_measure_peak(int32_t kind, double *tflops, h2sp_stream stream) {
+  if (!tflops || (kind != 0 && kind != 1)) return H2SP_EINVAL;
+  *tflops = 0.0;
+  try {
+    ck(measure_fma_peak(kind, tflops, reinterpret_cast<cudaStream_t>(stream)));
+  } catch (const CudaFail &f) {
+    return status_of(f.e);
   }
   return H2SP_OK;
 }

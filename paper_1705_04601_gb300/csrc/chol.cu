@@ -256,9 +256,9 @@ cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfro
           const int jbo = std::min(KB, F.s - J), nrest = F.f - J - jbo;
           const double c0 = std::min(nrest, lo), c1 = std::min(nrest, hi);
           if (c1 <= c0) continue;
-          // algorithmic bytes: the lower part of C in and out, L21 read for rows and columns
-          const double lower = (c1 - c0) * (double(nrest) - 0.5 * (c0 + c1));
-          fg += double(sizeof(float)) * (2.0 * lower + double(jbo) * (double(nrest - c0) + (c1 - c0)));
+          // algorithmic flops: 2 jbo per entry of the lower triangle in the columns
+          const double lower = (c1 - c0) * (double(nrest) - 0.5 * (c0 + c1 - 1.0));
+          fg += 2.0 * double(jbo) * lower;
         }
         if (fg <= 0.0) return cudaSuccess;
         const int tlo = lo / kTcTile, thi = hi >= (INT_MAX - kTcTile) ? INT_MAX : hi / kTcTile;
@@ -289,7 +289,7 @@ cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfro
             const size_t e0 = prof->begin(ms);
             if ((e = launch_gemm_tc_inner(fr, jp, KB, nfront, max_f, fronts, err, ms, nsm, /*sym=*/1)) != cudaSuccess)
               return e;
-            prof->end(P_GEMM, 1, e0, fgemm, ms);
+            prof->end(P_GEMM_INNER, 1, e0, fgemm, ms);
           }
         }
         const bool more = J + KB < max_s;

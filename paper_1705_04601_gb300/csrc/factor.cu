@@ -1958,9 +1958,7 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
         const double jb = std::min(NB, F.s - j0);
         const int nrest = F.f - j0 - int(jb);
         const double cols = std::max(0, std::min(nrest, c_hi) - c_lo);
-        // tensor cores: HBM-bound rank-jb update, work = algorithmic bytes
-        // (C read and written, L21 and U12 read); CUDA cores: flops
-        fgemm += tc ? double(sizeof(T)) * (2.0 * nrest * cols + jb * (nrest + cols)) : 2.0 * nrest * cols * jb;
+        fgemm += 2.0 * nrest * cols * jb;  // algorithmic flops
       }
     const size_t e0 = prof->begin(us);
     if (tc) {
@@ -2026,7 +2024,7 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
       float *apack[2] = {pack, pack + pack_stride};
       float *bpack = pack + 2 * pack_stride;
       auto block_end = [&](int J, int lo, int hi, bool left, int budget, cudaStream_t st) -> cudaError_t {
-        double ft = 0.0, fg = 0.0;
+        double ft = 0.0, fg = 0.0, fp = 0.0;
         int wcols = 0;
         for (int k = 0; k < nfront; ++k) {
           const Front &F = host_fr[k];
@@ -2035,8 +2033,8 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
           const int cols = std::max(0, std::min(nrest, hi) - lo);
           wcols = std::max(wcols, cols);
           ft += 0.5 * double(jbo) * jbo * cols;
-          // algorithmic bytes of the rank-jbo update: C in and out, L21 and U12 read
-          fg += double(sizeof(float)) * (2.0 * nrest * cols + double(jbo) * (nrest + cols));
+          fg += 2.0 * double(jbo) * nrest * cols;  // algorithmic flops of the rank-jbo update
+          fp += 12.0 * double(jbo) * cols;         // the U12 pack: 4 bytes read, 8 written per element
         }
         size_t e0 = prof->begin(st);
         if (left && J > 0)
@@ -2050,6 +2048,8 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
         const int tlo = lo / kTcTile, thi = hi >= (INT_MAX - kTcTile) ? INT_MAX : hi / kTcTile;
         e0 = prof->begin(st);
         cudaError_t ge = launch_pack_b(fr, J, KB, nfront, max_f, fronts, bpack, tlo, thi, st);
+        prof->end(P_GEMM_INNER, 1, e0, fp, st);
+        e0 = prof->begin(st);
         if (ge == cudaSuccess)
           ge = launch_gemm_tc_ws(fr, J, KB, nfront, max_f, fronts, err, st, tlo, thi, budget, maps,
                                  apack[(J / KB) & 1], bpack);
@@ -2082,7 +2082,7 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
               }
             const size_t e0 = prof->begin(ms);
             if ((e = launch_gemm_tc_inner(fr, jp, KB, nfront, max_f, fronts, err, ms, nsm)) != cudaSuccess) return e;
-            prof->end(P_GEMM, 1, e0, fgemm, ms);
+            prof->end(P_GEMM_INNER, 1, e0, fgemm, ms);
           }
         }
         const bool more = J + KB < max_s;

@@ -156,7 +156,8 @@ enum ProfClass : int {
   P_MATVEC = 9,      // FP64 H^2 product
   P_APPLY = 10,      // U^T / V applies
   P_OTHER = 11,      // vector kernels, casts, permutations
-  P_NCLASS = 12
+  P_GEMM_INNER = 12, // FP32 blocked factorizations: in-block rank-64 updates and operand packing
+  P_NCLASS = 13
 };
 
 // Counts every launch; when `timing` is on, brackets launches with CUDA events

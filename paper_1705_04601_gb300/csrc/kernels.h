@@ -28,6 +28,9 @@ inline cudaError_t smem_attr(const void *fn, int bytes) {
   return e;
 }
 
+// FMA rate of the current device in TFLOP/s (kind 0: FP64, 1: FP32), peak.cu.
+cudaError_t measure_fma_peak(int kind, double *tflops, cudaStream_t s);
+
 // Streaming multiprocessors of the current device (cached per device).
 inline int device_sms() {
   static std::mutex mu;

@@ -73,7 +73,7 @@ class KernelTimes(ctypes.Structure):
 
 
 KERNEL_CLASSES = ["gemm_update", "panel", "swap_trsm", "extend_add", "assemble", "transform", "householder",
-                  "coupling", "solve", "h2_matvec", "apply", "vector"]
+                  "coupling", "solve", "h2_matvec", "apply", "vector", "gemm_inner"]
 
 # name -> (restype, argtypes); every symbol of include/h2sp.h
 SIGNATURES = {
@@ -92,6 +92,7 @@ SIGNATURES = {
     "h2sp_export_Q": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _i64p, _f64p, _vp]),
     "h2sp_export_structure": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i64p]),
     "h2sp_export_front": (ctypes.c_int, [_vp, ctypes.c_int32, _i64p, _i64p, _f64p, _vp]),
+    "h2sp_measure_peak": (ctypes.c_int, [ctypes.c_int32, _f64p, _vp]),
     "h2sp_solve_host": (ctypes.c_int, [_vp, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_int32, _vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_void_p,
                                        _vp]),
@@ -314,6 +315,13 @@ def h2sp_solve_host(an, inp: H2Input, b_ptr: int, ldb: int, x_ptr: int, ldx: int
         _check(st, "h2sp_solve_host")
     info.status = st
     return info
+
+
+def h2sp_measure_peak(kind: int, stream=None) -> float:
+    """Measured FMA rate of the current device in TFLOP/s (kind 0: FP64, 1: FP32)."""
+    v = ctypes.c_double(0.0)
+    _check(lib().h2sp_measure_peak(int(kind), ctypes.byref(v), _stream(stream)), "h2sp_measure_peak")
+    return float(v.value)
 
 
 def h2sp_logdet(h: Handle, stream=None):
