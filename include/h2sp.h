@@ -424,6 +424,27 @@ int h2sp_profile(h2sp_handle *h, int32_t timing, int32_t reset, h2sp_kernel_time
 int h2sp_h2_matvec_static(const h2sp_handle *h, int32_t nrhs, const double *x, int64_t ldx, double *y, int64_t ldy,
                           h2sp_stream stream);
 
+/* Options of h2sp_set_option. */
+enum {
+  /* Polls of one flag wait of the triangular sweeps before it gives up (the
+   * solve then returns H2SP_ETIMEOUT); 1 .. 2^31, default 2^22 (on the order
+   * of a second: each poll is an acquire load and a 32 ns back-off). */
+  H2SP_OPTION_WAIT_POLLS = 1,
+  /* Test of the bounded waits: value != 0 makes the forward sweeps of the
+   * next solve of this handle await an epoch that no solved block publishes,
+   * so every wait of a block on another runs out; that solve returns
+   * H2SP_ETIMEOUT and the option clears itself.  The handle, its factors and
+   * the device stay usable (a wait that runs out raises an error word and
+   * leaves; nothing faults or traps). */
+  H2SP_OPTION_TEST_STALE_EPOCH = 2
+};
+
+/*
+ * h2sp_set_option -- set a runtime option of handle h (the enum above).
+ * H2SP_EINVAL for an unknown option or a value out of range.
+ */
+int h2sp_set_option(h2sp_handle *h, int32_t option, int64_t value);
+
 /*
  * h2sp_measure_peak -- the fused multiply-add rate of the current device in
  * TFLOP/s into *tflops: kind 0 for FP64, 1 for FP32 on the CUDA cores.  One

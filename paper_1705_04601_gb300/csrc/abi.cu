@@ -225,6 +225,8 @@ struct h2sp_handle {
   std::vector<int> chain_fwd_off, chain_fwd_n, chain_bwd_off, chain_bwd_n;
   int *chain_tickets = nullptr, *chain_flags = nullptr, *serr = nullptr;
   int chain_epoch = 0;
+  uint32_t chain_spin_cap = 1u << 22;  // H2SP_OPTION_WAIT_POLLS
+  bool test_stale_epoch = false;       // H2SP_OPTION_TEST_STALE_EPOCH: the next solve's forward waits never end
   // log-determinant: fronts of each independent system (CSR) and per-front / per-system sums
   int32_t *ld_sys_ptr = nullptr, *ld_sys_front = nullptr, *ld_sign = nullptr;
   int *ld_flips = nullptr;
@@ -437,6 +439,10 @@ void solve_S_T(h2sp_handle *h, T *y, int nrhs) {
   ca.tickets = h->chain_tickets;
   ca.flags = h->chain_flags;
   ca.err = h->serr;
+  ca.spin_cap = h->chain_spin_cap;
+  // the wait test: the forward sweeps await an epoch that no block publishes
+  const int stale = h->test_stale_epoch ? (1 << 29) : 0;
+  h->test_stale_epoch = false;
   for (int r0 = 0; r0 < nrhs; r0 += kSolveRhs) {
     const int nr = std::min(kSolveRhs, nrhs - r0);
     T *yr = y + int64_t(r0) * p.n;
@@ -447,6 +453,7 @@ void solve_S_T(h2sp_handle *h, T *y, int nrhs) {
     for (size_t li = 0; li < h->flev.size(); ++li) {
       const FrontLevel &L = h->flev[li];
       ca.epoch = ++h->chain_epoch;
+      ca.wait_epoch = ca.epoch + stale;
       ck(launch_solve_fwd_level_impl<T>(h->fr, L.lo, L.hi - L.lo, L.max_s, L.max_f, fronts, dinv, h->perm, h->fidx,
                                         yr, p.n, nr, work, zbuf, h->work_off, h->stream, &h->prof,
                                         L.lu_elems * sizeof(T), chain ? &ca : nullptr, int(li)));
@@ -454,6 +461,7 @@ void solve_S_T(h2sp_handle *h, T *y, int nrhs) {
     for (int i = int(h->flev.size()) - 1; i >= 0; --i) {
       const FrontLevel &L = h->flev[i];
       ca.epoch = ++h->chain_epoch;
+      ca.wait_epoch = ca.epoch;
       ck(launch_solve_bwd_level_impl<T>(h->fr, L.lo, L.hi - L.lo, L.max_s, L.max_f, fronts, dinv, h->fidx, yr, p.n,
                                         nr, work, zbuf, h->work_off, h->stream, &h->prof, L.lu_elems * sizeof(T),
                                         chain ? &ca : nullptr, i));
@@ -1781,6 +1789,21 @@ int h2sp_export_front(h2sp_handle *h, int32_t k, int64_t *f, int64_t *sz, double
     return status_of(e.e);
   }
   return H2SP_OK;
+}
+
+int h2sp_set_option(h2sp_handle *h, int32_t option, int64_t value) {
+  if (!h) return H2SP_EINVAL;
+  switch (option) {
+    case H2SP_OPTION_WAIT_POLLS:
+      if (value < 1 || value > (int64_t(1) << 31)) return H2SP_EINVAL;
+      h->chain_spin_cap = uint32_t(value);
+      return H2SP_OK;
+    case H2SP_OPTION_TEST_STALE_EPOCH:
+      h->test_stale_epoch = value != 0;
+      return H2SP_OK;
+    default:
+      return H2SP_EINVAL;
+  }
 }
 
 int h2sp_measure_peak(int32_t kind, double *tflops, h2sp_stream stream) {

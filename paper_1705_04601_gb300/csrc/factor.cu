@@ -1463,10 +1463,10 @@ inline int num_sms() { return device_sms(); }
 // is published as soon as it is solved (release store of the launch's
 // epoch).  An item depends only on items with smaller tickets, which are held
 // by running or finished CTAs of the same cooperative launch, so every wait
-// ends; each wait is still bounded (kChainSpinCap polls), after which the CTA
-// raises an error flag and leaves.
+// ends; each wait is still bounded (ChainArgs::spin_cap polls, 2^22 unless
+// the handle sets another), after which the CTA raises an error flag and
+// leaves.
 constexpr int kChainThreads = 256;
-constexpr uint32_t kChainSpinCap = 1u << 22;
 constexpr int kChainSub = 2;                          // row blocks per supernode item
 constexpr int kChainPre = kBS * kBS / kChainThreads;  // values of one 64 x 64 block per thread
 
@@ -1479,13 +1479,14 @@ __device__ __forceinline__ void st_release_gpu(int *p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// bounded wait of thread 0 for flag == epoch; the verdict is shared through *s_ok
-__device__ __forceinline__ bool chain_wait(const int *flag, int epoch, int *err, int *s_ok) {
+// bounded wait of thread 0 for flag == epoch (at most spin_cap polls); the
+// verdict is shared through *s_ok
+__device__ __forceinline__ bool chain_wait(const int *flag, int epoch, uint32_t spin_cap, int *err, int *s_ok) {
   if (threadIdx.x == 0) {
     int okv = 1;
     uint32_t n = 0;
     while (ld_acquire_gpu(flag) != epoch) {
-      if (++n > kChainSpinCap) {
+      if (++n > spin_cap) {
         okv = 0;
         atomicOr(err, 4);
         break;
@@ -1504,7 +1505,8 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrontDev *__restr
                                                          const T *__restrict__ fronts, const T *__restrict__ dinv,
                                                          int nrhs, T *__restrict__ work, T *__restrict__ zbuf,
                                                          const int64_t *__restrict__ work_off, int *__restrict__ flags,
-                                                         int epoch, int *__restrict__ err) {
+                                                         int epoch, int *__restrict__ err, int wait_epoch,
+                                                         uint32_t spin_cap) {
   __shared__ __align__(16) T sL[kChainSub * kBS * kBS];  // blocks of L / U for both sub-blocks, column-major
   __shared__ __align__(16) T sZ[kBS * kMaxRhs];           // a solution block, sZ[k * kMaxRhs + c]
   __shared__ int s_item, s_ok;
@@ -1595,7 +1597,7 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrontDev *__restr
 #pragma unroll
         for (int e = 0; e < kChainPre; ++e) sL[u * kBS * kBS + tid + e * kChainThreads] = pre[u][e];
       if (s + 1 < nblk) load_block(Fwd ? bp + 1 : bp - 1);  // in flight during the wait
-      if (!chain_wait(&flags[fbase + bp], epoch, err, &s_ok)) {
+      if (!chain_wait(&flags[fbase + bp], wait_epoch, spin_cap, err, &s_ok)) {
         ok = false;
         break;
       }
@@ -1696,10 +1698,11 @@ cudaError_t launch_chain(const FrontDev *fr, const ChainArgs &ca, int li, const 
   if (n == 0) return cudaSuccess;
   const int2 *items = ca.items + off;
   int *ticket = ca.tickets + 2 * li + (Fwd ? 0 : 1);
-  int epoch = ca.epoch;
+  int epoch = ca.epoch, wait_epoch = ca.wait_epoch;
+  uint32_t spin_cap = ca.spin_cap;
   void *args[] = {(void *)&fr, (void *)&items, (void *)&n, (void *)&ticket, (void *)&fronts, (void *)&dinv,
                   (void *)&nrhs, (void *)&work, (void *)&zbuf, (void *)&work_off, (void *)&ca.flags, (void *)&epoch,
-                  (void *)&ca.err};
+                  (void *)&ca.err, (void *)&wait_epoch, (void *)&spin_cap};
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_chain<T, Fwd>), dim3(chain_grid<T, Fwd>(n)),
                                      dim3(kChainThreads), args, 0, s);
 }

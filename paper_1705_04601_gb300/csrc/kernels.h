@@ -177,7 +177,9 @@ struct ChainArgs {
   const int2 *items = nullptr;
   const int *fwd_off = nullptr, *fwd_n = nullptr, *bwd_off = nullptr, *bwd_n = nullptr;  // host arrays
   int *tickets = nullptr, *flags = nullptr, *err = nullptr;
-  int epoch = 0;
+  int epoch = 0;       // published by every solved block of the launch
+  int wait_epoch = 0;  // awaited on the blocks a block depends on (= epoch, except in the wait test)
+  uint32_t spin_cap = 1u << 22;  // polls of one wait before it gives up
 };
 // Forward sweep for one level (fronts [lo, lo+nfront) of fr): gathers P^T y into
 // the fronts' work vectors, z = L11^-1 (.) block by block into zbuf, adds

@@ -93,6 +93,7 @@ SIGNATURES = {
     "h2sp_export_structure": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i64p]),
     "h2sp_export_front": (ctypes.c_int, [_vp, ctypes.c_int32, _i64p, _i64p, _f64p, _vp]),
     "h2sp_measure_peak": (ctypes.c_int, [ctypes.c_int32, _f64p, _vp]),
+    "h2sp_set_option": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int64]),
     "h2sp_solve_host": (ctypes.c_int, [_vp, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_int32, _vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_void_p,
                                        _vp]),
@@ -315,6 +316,13 @@ def h2sp_solve_host(an, inp: H2Input, b_ptr: int, ldb: int, x_ptr: int, ldx: int
         _check(st, "h2sp_solve_host")
     info.status = st
     return info
+
+
+H2SP_OPTION_WAIT_POLLS, H2SP_OPTION_TEST_STALE_EPOCH = 1, 2
+
+
+def h2sp_set_option(h: Handle, option: int, value: int):
+    _check(lib().h2sp_set_option(h.ptr, int(option), int(value)), "h2sp_set_option")
 
 
 def h2sp_measure_peak(kind: int, stream=None) -> float:
