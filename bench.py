@@ -83,6 +83,9 @@ def parse(argv=None):
                     help="precision of the products into S on the mixed path (the FP64 path is FP64 throughout)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tune", default="auto", choices=["auto", "off", "force"],
+                    help="schedule of the FP32 block Cholesky: auto = the stored choice for this device and "
+                         "structure (paper_1705_04601_gb300/tuned.json), else tune now; off = library defaults")
     ap.add_argument("--solver", default="gmres", choices=["gmres", "ir"],
                     help="outer iteration of the mixed path on the FP64 H^2 residual")
     return ap.parse_args(argv)
@@ -272,17 +275,35 @@ def run_ours(args, ws, rank, local):
     xt = torch.empty_like(bt)
     stream = torch.cuda.current_stream()
     fma = {"fp64": H.h2sp_measure_peak(0), "fp32": H.h2sp_measure_peak(1)}
+    sp_flags = H.H2SP_SPARSIFY_FP32 if args.sparsify_prec == "fp32" else 0
+    # schedule of the FP32 block Cholesky: stored for this device and structure, or tuned now
+    sched, sched_src, tune_s = None, "library defaults", 0.0
+    if kind == "chol" and getattr(args, "tune", "auto") != "off":
+        from paper_1705_04601_gb300 import tune as T
+        tkey = T.key(dict(stats, n=int(h.n)), torch.cuda.get_device_name())
+        sched = T.load(tkey) if args.tune == "auto" else None
+        if sched is not None:
+            sched_src = "stored (tuned.json)"
+        else:
+            t1 = time.time()
+            sched, _ = T.tune(an, inp, flags=sp_flags)
+            tune_s = time.time() - t1
+            sched_src = "tuned in this run"
+            if os.environ.get("H2SP_TUNE_STORE"):
+                T.store(tkey, sched, _)
 
     def ev():
         return torch.cuda.Event(enable_timing=True)
 
     mode = H.H2SP_GMRES if args.solver == "gmres" else H.H2SP_IR
-    sp_flags = H.H2SP_SPARSIFY_FP32 if args.sparsify_prec == "fp32" else 0
 
     def mixed_step(profile=False, marks=None):
         if marks:
             marks[0].record(stream)
         hd = H.h2sp_sparsify_analyzed(an, inp, flags=sp_flags)
+        if sched:
+            from paper_1705_04601_gb300 import tune as T
+            T.apply(hd, sched)
         if profile:
             H.h2sp_profile(hd, timing=1)
         if marks:
@@ -415,6 +436,7 @@ def run_ours(args, ws, rank, local):
         "structure": {"max_front": stats["max_front"], "nsupernodes": stats["nsupernodes"],
                       "nnz_S": stats["nnz"], "front_elems": stats["front_elems"]},
         "fma_peaks_tflops": fma, "roofline": roof, "e2e": e2e,
+        "schedule": sched, "schedule_source": sched_src, "tune_s": tune_s,
         "gpu_launches": int(launches), "gpu_launches_per_step": int(launches / max(args.steps, 1)),
         "kernel_ms_per_step": {c: v["ms"] for c, v in prof.items() if v["ms"] > 0},
         "clocks": clk, "cpu_baseline": cpu,

@@ -436,7 +436,18 @@ enum {
    * H2SP_ETIMEOUT and the option clears itself.  The handle, its factors and
    * the device stay usable (a wait that runs out raises an error word and
    * leaves; nothing faults or traps). */
-  H2SP_OPTION_TEST_STALE_EPOCH = 2
+  H2SP_OPTION_TEST_STALE_EPOCH = 2,
+  /* Schedule of the FP32 block Cholesky (H2SP_FP32_CHOL), the knobs the
+   * package's autotuner sets; none changes the result beyond rounding order.
+   * TILES_PER_CTA: most 128-column tiles one CTA of the low-priority
+   * block-end update takes (0, the default: a whole-wave split); short CTAs
+   * let the panel stream reach the SMs sooner.  PANEL_SMS: SMs that update
+   * leaves to the panel stream (-1, the default: one per front of the
+   * level).  LOOKAHEAD: 1 (default) factors the next block's panels on a
+   * high-priority stream while the rest of the update runs, 0 serialises. */
+  H2SP_OPTION_CHOL_TILES_PER_CTA = 3,
+  H2SP_OPTION_CHOL_PANEL_SMS = 4,
+  H2SP_OPTION_CHOL_LOOKAHEAD = 5
 };
 
 /*

@@ -227,6 +227,7 @@ struct h2sp_handle {
   int chain_epoch = 0;
   uint32_t chain_spin_cap = 1u << 22;  // H2SP_OPTION_WAIT_POLLS
   bool test_stale_epoch = false;       // H2SP_OPTION_TEST_STALE_EPOCH: the next solve's forward waits never end
+  CholSchedule chol_sched;             // H2SP_OPTION_CHOL_*: schedule of the blocked FP32 block Cholesky
   // log-determinant: fronts of each independent system (CSR) and per-front / per-system sums
   int32_t *ld_sys_ptr = nullptr, *ld_sys_front = nullptr, *ld_sign = nullptr;
   int *ld_flips = nullptr;
@@ -853,6 +854,9 @@ std::shared_ptr<StructureDev> build_structure(const Plan &p) {
       auto large = std::stable_partition(ol.begin(), ol.end(),
                                          [&](int lf) { return p.h_size[p.level_ptr[p.D] + lf] <= kMaxBlock; });
       g.nleaf_large = int32_t(ol.end() - large);
+      g.max_leaf = 0;
+      for (int lf = 0; lf < p.nleaf; ++lf)
+        g.max_leaf = std::max<int32_t>(g.max_leaf, int32_t(p.h_size[p.level_ptr[p.D] + lf]));
       std::stable_sort(oc.begin(), oc.end(), [&](int a, int b) { return wc[a] > wc[b]; });
       g.leaf_order = sd->upload(ol);
       g.couple_order = sd->upload(oc);
@@ -1221,7 +1225,7 @@ void factor_launch_t(h2sp_handle *h, bool chol) {
     const uint8_t *maps = (fp32 && h->tmaps) ? h->tmaps + size_t(L.lo) * kTmapBytes : nullptr;
     if (chol) {
       ck(launch_chol_level<T>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv, h->err,
-                              s, la, &h->prof, maps, h->pack, reinterpret_cast<T *>(h->chol_inv)));
+                              s, la, &h->prof, maps, h->pack, reinterpret_cast<T *>(h->chol_inv), &h->chol_sched));
     } else {
       ck(launch_lu_level<T>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv, h->swaps,
                             h->err, s, la, &h->prof, maps, fp32 ? h->pack : nullptr));
@@ -1800,6 +1804,17 @@ int h2sp_set_option(h2sp_handle *h, int32_t option, int64_t value) {
       return H2SP_OK;
     case H2SP_OPTION_TEST_STALE_EPOCH:
       h->test_stale_epoch = value != 0;
+      return H2SP_OK;
+    case H2SP_OPTION_CHOL_TILES_PER_CTA:
+      if (value < 0 || value > (1 << 20)) return H2SP_EINVAL;
+      h->chol_sched.tiles_per_cta = int(value);
+      return H2SP_OK;
+    case H2SP_OPTION_CHOL_PANEL_SMS:
+      if (value < -1 || value > 4096) return H2SP_EINVAL;
+      h->chol_sched.panel_sms = int(value);
+      return H2SP_OK;
+    case H2SP_OPTION_CHOL_LOOKAHEAD:
+      h->chol_sched.lookahead = value != 0;
       return H2SP_OK;
     default:
       return H2SP_EINVAL;

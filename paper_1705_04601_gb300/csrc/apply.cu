@@ -336,6 +336,116 @@ __global__ void __launch_bounds__(kMvThreads, 10) k_h2_couple(H2Dev h, const dou
   }
 }
 
+// ---- the same products for few right-hand sides (nrhs <= 4) ----
+// With one right-hand side the kernels above give each thread one row and a
+// serial chain of dependent FMAs, one global load per step.  Here a CTA of
+// kNwThreads threads takes one block row (a leaf's close blocks, or a
+// cluster's couplings) with several threads per row: thread (i, ph) of a
+// row pad RP (32, 64 or 128 rows) sums the columns j = ph, ph + PH, ...
+// (PH = kNwThreads / RP) with two independent accumulator sets, so a warp
+// reads 32 consecutive rows of a column per load (coalesced) and keeps
+// several loads in flight; the vector entries are read from global memory
+// (every lane of a warp reads the same one).  The PH partial sums of a row
+// are added in shared memory at the end, in a fixed order.
+constexpr int kNwThreads = 256;
+
+__device__ __forceinline__ int nw_rowpad(int rows) { return rows <= 32 ? 32 : (rows <= 64 ? 64 : 128); }
+
+// acc0/acc1[r] += sum over this thread's columns j of A[i + j lda] X[j + r ldx]
+template <int NR>
+__device__ __forceinline__ void nw_accumulate(double (&acc0)[NR], double (&acc1)[NR], const double *__restrict__ A,
+                                              int64_t lda, int i, int nc, const double *__restrict__ X, int64_t ldx,
+                                              int ph, int PH, int nrhs) {
+  int j = ph;
+  for (; j + PH < nc; j += 2 * PH) {
+    const double a0 = A[i + int64_t(j) * lda], a1 = A[i + int64_t(j + PH) * lda];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r < nrhs) {
+        acc0[r] += a0 * X[j + int64_t(r) * ldx];
+        acc1[r] += a1 * X[j + PH + int64_t(r) * ldx];
+      }
+  }
+  if (j < nc) {
+    const double a0 = A[i + int64_t(j) * lda];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r < nrhs) acc0[r] += a0 * X[j + int64_t(r) * ldx];
+  }
+}
+
+// sum of the PH partials of each row (thread ph = 0 of row i receives it)
+template <int NR>
+__device__ __forceinline__ void nw_reduce(double (&acc0)[NR], const double (&acc1)[NR], int i, int ph, int RP,
+                                          int PH, double *red) {
+#pragma unroll
+  for (int r = 0; r < NR; ++r) red[threadIdx.x + r * kNwThreads] = acc0[r] + acc1[r];
+  __syncthreads();
+  if (ph == 0)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      double v = 0.0;
+      for (int q = 0; q < PH; ++q) v += red[q * RP + i + r * kNwThreads];
+      acc0[r] = v;
+    }
+}
+
+// y_t = R_t y^_t + sum_{s near t} C_ts x_s for leaves of at most 128 points
+template <int NR>
+__global__ void __launch_bounds__(kNwThreads) k_h2_leaf_out_nw(H2Dev h, const double *__restrict__ x, int64_t ldx,
+                                                             const double *__restrict__ yh, int64_t ldh,
+                                                             double *__restrict__ y, int64_t ldy, int nrhs) {
+  const int lf = h.leaf_order ? h.leaf_order[blockIdx.x] : int(blockIdx.x);
+  const int t = h.leaf0 + lf;
+  const int n = int(h.size[t]), k = h.rank[t];
+  const int RP = nw_rowpad(n), PH = kNwThreads / RP;
+  const int i = threadIdx.x % RP, ph = threadIdx.x / RP;
+  __shared__ double red[kNwThreads * NR];
+  double acc0[NR], acc1[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) acc0[r] = acc1[r] = 0.0;
+  if (i < n) {
+    nw_accumulate<NR>(acc0, acc1, h.leaf_basis + h.leaf_basis_off[lf], n, i, k, yh + h.xh_off[t], ldh, ph, PH, nrhs);
+    for (int64_t z = h.near_ptr[lf]; z < h.near_ptr[lf + 1]; ++z) {
+      const int s = h.near_col[z];
+      nw_accumulate<NR>(acc0, acc1, h.near_block + h.near_off[z], n, i, int(h.size[s]), x + h.begin[s], ldx, ph, PH,
+                        nrhs);
+    }
+  }
+  nw_reduce<NR>(acc0, acc1, i, ph, RP, PH, red);
+  if (ph == 0 && i < n) {
+    const int64_t b0 = h.begin[t];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r < nrhs) y[b0 + i + r * ldy] = acc0[r];
+  }
+}
+
+// y^_t = sum_{s in Far(t)} D_ts x^_s
+template <int NR>
+__global__ void __launch_bounds__(kNwThreads) k_h2_couple_nw(H2Dev h, const double *__restrict__ xh,
+                                                           double *__restrict__ yh, int64_t ldh, int nrhs) {
+  const int t = h.couple_order ? h.couple_order[blockIdx.x] : int(blockIdx.x);
+  const int kt = h.rank[t];
+  const int RP = nw_rowpad(kt), PH = kNwThreads / RP;
+  const int i = threadIdx.x % RP, ph = threadIdx.x / RP;
+  __shared__ double red[kNwThreads * NR];
+  double acc0[NR], acc1[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) acc0[r] = acc1[r] = 0.0;
+  if (i < kt)
+    for (int64_t z = h.far_ptr[t]; z < h.far_ptr[t + 1]; ++z) {
+      const int s = h.far_col[z];
+      nw_accumulate<NR>(acc0, acc1, h.coupling + h.coupling_off[z], kt, i, h.rank[s], xh + h.xh_off[s], ldh, ph, PH,
+                        nrhs);
+    }
+  nw_reduce<NR>(acc0, acc1, i, ph, RP, PH, red);
+  if (ph == 0 && i < kt)
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r < nrhs) yh[h.xh_off[t] + i + r * ldh] = acc0[r];
+}
+
 // y^_c += T_c y^_parent for the clusters [lo, hi) of one depth
 template <int G>
 __device__ __forceinline__ void down_body(const H2Dev &h, int c, double *__restrict__ yh, int64_t ldh, int nrhs) {
@@ -622,14 +732,27 @@ cudaError_t launch_h2_matvec(const H2Dev &h, const int32_t *level_ptr_host, cons
       const int lo = level_ptr_host[d], hi = level_ptr_host[d + 1];
       k_h2_up<<<hi - lo, kMvThreads, 0, s>>>(h, child_start, child_cnt, lo, xh, ldh, nr);
     }
-    k_h2_couple<<<ncl, kMvThreads, 0, s>>>(h, xh, yh, ldh, nr);
+    const bool narrow = nr <= 4 && h.max_leaf <= 128;
+    if (narrow && nr == 1)
+      k_h2_couple_nw<1><<<ncl, kNwThreads, 0, s>>>(h, xh, yh, ldh, nr);
+    else if (narrow)
+      k_h2_couple_nw<4><<<ncl, kNwThreads, 0, s>>>(h, xh, yh, ldh, nr);
+    else
+      k_h2_couple<<<ncl, kMvThreads, 0, s>>>(h, xh, yh, ldh, nr);
     for (int d = 1; d <= depth; ++d) {
       const int lo = level_ptr_host[d], hi = level_ptr_host[d + 1];
       k_h2_down<<<hi - lo, kMvThreads, 0, s>>>(h, lo, yh, ldh, nr);
     }
     const int nlarge = h.nleaf_large;
-    if (nleaf > nlarge) k_h2_leaf_out<<<nleaf - nlarge, kMvThreads, 0, s>>>(h, xr, ldx, yh, ldh, yr, ldy, nr);
-    if (nlarge > 0) k_h2_leaf_out_large<<<nlarge, kMvThreads, 0, s>>>(h, nleaf - nlarge, xr, ldx, yh, ldh, yr, ldy, nr);
+    if (narrow && nr == 1) {
+      k_h2_leaf_out_nw<1><<<nleaf, kNwThreads, 0, s>>>(h, xr, ldx, yh, ldh, yr, ldy, nr);
+    } else if (narrow) {
+      k_h2_leaf_out_nw<4><<<nleaf, kNwThreads, 0, s>>>(h, xr, ldx, yh, ldh, yr, ldy, nr);
+    } else {
+      if (nleaf > nlarge) k_h2_leaf_out<<<nleaf - nlarge, kMvThreads, 0, s>>>(h, xr, ldx, yh, ldh, yr, ldy, nr);
+      if (nlarge > 0)
+        k_h2_leaf_out_large<<<nlarge, kMvThreads, 0, s>>>(h, nleaf - nlarge, xr, ldx, yh, ldh, yr, ldy, nr);
+    }
   }
   return cudaGetLastError();
 }

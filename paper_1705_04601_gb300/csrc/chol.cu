@@ -40,10 +40,10 @@ inline int cdiv_c(int64_t a, int64_t b) { return int((a + b - 1) / b); }
 // entry j by it and publishes it, and updates its entries j+1 .. r.  A
 // pivot that is not positive and finite sets bit 8 of *err (the matrix is
 // not positive definite in this precision) and is replaced by 1 so that the
-// factorization stays finite.  Then thread r forms row r of L11^-1 by
-// substitution along the row (li_c = (delta_rc - sum_{c<m<=r} li_m l_mc) / l_cc,
-// c from r down to 0) and writes it to inv[front][r * NB + c] (zero-padded to
-// NB x NB).
+// factorization stays finite.  Then thread c forms column c of L11^-1 by
+// forward substitution, y_r = -(sum_{c<=m<r} l_rm y_m) / l_rr with
+// y_c = 1 / l_cc, each row's sum split over four partial sums, and writes it
+// to inv[front][r * NB + c] (row-major, zero above the diagonal and beyond jb).
 template <typename T, int NB>
 __global__ void __launch_bounds__(NB) k_chol_diag(const FrontDev *__restrict__ fr, int j0, T *__restrict__ fronts,
                                                   int32_t *__restrict__ piv, int *__restrict__ err,
@@ -53,63 +53,82 @@ __global__ void __launch_bounds__(NB) k_chol_diag(const FrontDev *__restrict__ f
   const int jb = min(NB, F.s - j0);
   T *A = fronts + F.off;
   const int64_t ld = F.ld;
-  __shared__ T col[NB];  // the current column below the pivot, and the pivot itself
+  constexpr int P = NB + 1;       // padded row length of the tile in shared memory
+  __shared__ T col[NB];           // the current column below the pivot, and the pivot itself
+  __shared__ T Lr[NB * P];        // L11 row-major (row r at r * P), zero above the diagonal and beyond jb
   const int r = threadIdx.x;
-  T x[NB];
+  {
+    T x[NB];
 #pragma unroll
-  for (int c = 0; c < NB; ++c) x[c] = (r < jb && c <= r) ? A[(j0 + r) + int64_t(j0 + c) * ld] : T(0);
+    for (int c = 0; c < NB; ++c) x[c] = (r < jb && c <= r) ? A[(j0 + r) + int64_t(j0 + c) * ld] : T(0);
+    for (int j = 0; j < jb; ++j) {
+      T xj = T(0);
 #pragma unroll
-  for (int j = 0; j < NB; ++j) {
-    if (j >= jb) break;  // uniform
-    if (r == j) {
-      T a = x[j];
-      if (!(a > T(0)) || !isfinite(a)) {
-        atomicOr(err, 8);
-        a = T(1);
+      for (int c = 0; c < NB; ++c)
+        if (c == j) xj = x[c];
+      if (r == j) {
+        T a = xj;
+        if (!(a > T(0)) || !isfinite(a)) {
+          atomicOr(err, 8);
+          a = T(1);
+        }
+        col[j] = sqrt(a);
       }
-      x[j] = sqrt(a);
-      col[j] = x[j];
-    }
-    __syncthreads();
-    T l = T(0);
-    if (r > j && r < jb) {
-      l = x[j] / col[j];
-      x[j] = l;
-      col[r] = l;
-    }
-    __syncthreads();
-    if (r > j && r < jb) {
-#pragma unroll
-      for (int c = j + 1; c < NB; ++c)
-        if (c <= r) x[c] -= l * col[c];
-    }
-    __syncthreads();  // col is rewritten by the next column
-  }
-  __shared__ T Lt[NB * (NB + 1)];  // L11 column-major, padded
-  __shared__ T rdiag[NB];
-  if (r < jb) {
-#pragma unroll
-    for (int c = 0; c < NB; ++c)
-      if (c <= r) {
-        A[(j0 + r) + int64_t(j0 + c) * ld] = x[c];
-        Lt[r + c * (NB + 1)] = x[c];
+      __syncthreads();
+      const T d = col[j];
+      T l = T(0);
+      if (r > j && r < jb) {
+        l = xj / d;
+        col[r] = l;
       }
-    rdiag[r] = T(1) / x[r];
-    piv[F.piv_off + j0 + r] = j0 + r;
+      __syncthreads();
+      if (r >= j && r < jb) {
+        // entry j becomes final (l, or d on the diagonal); entries j+1 .. r take the update
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+          if (c == j) x[c] = (r == j) ? d : l;
+          else if (c > j && c <= r) x[c] -= l * col[c];
+        }
+      }
+      __syncthreads();  // col is rewritten by the next column
+    }
+#pragma unroll
+    for (int c = 0; c < NB; ++c) Lr[r * P + c] = (r < jb && c <= r) ? x[c] : T(0);
+    if (r < jb) {
+#pragma unroll
+      for (int c = 0; c < NB; ++c)
+        if (c <= r) A[(j0 + r) + int64_t(j0 + c) * ld] = x[c];
+      piv[F.piv_off + j0 + r] = j0 + r;
+    }
   }
   __syncthreads();
-  // row r of L11^-1, in x (entries c <= r)
+  // column c = r of L11^-1
+  const int c = r;
+  T y[NB];
 #pragma unroll
-  for (int c = NB - 1; c >= 0; --c) {
-    T v = (c == r) ? T(1) : T(0);
+  for (int q = 0; q < NB; ++q) y[q] = T(0);
+  if (c < jb) {
 #pragma unroll
-    for (int m = c + 1; m < NB; ++m)
-      if (m <= r) v -= x[m] * Lt[m + c * (NB + 1)];
-    x[c] = (c <= r && r < jb) ? v * rdiag[c] : T(0);
+    for (int rr = 0; rr < NB; ++rr) {
+      if (rr < c || rr >= jb) continue;
+      if (rr == c) {
+        y[rr] = T(1) / Lr[rr * P + rr];
+        continue;
+      }
+      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+#pragma unroll
+      for (int m = 0; m < rr; m += 4) {
+        if (m >= c) s0 += Lr[rr * P + m] * y[m];
+        if (m + 1 < rr && m + 1 >= c) s1 += Lr[rr * P + m + 1] * y[m + 1];
+        if (m + 2 < rr && m + 2 >= c) s2 += Lr[rr * P + m + 2] * y[m + 2];
+        if (m + 3 < rr && m + 3 >= c) s3 += Lr[rr * P + m + 3] * y[m + 3];
+      }
+      y[rr] = -((s0 + s1) + (s2 + s3)) / Lr[rr * P + rr];
+    }
   }
-  T *Li = inv + int64_t(blockIdx.x) * NB * NB + int64_t(r) * NB;
+  T *Li = inv + int64_t(blockIdx.x) * NB * NB;
 #pragma unroll
-  for (int c = 0; c < NB; ++c) Li[c] = x[c];
+  for (int rr = 0; rr < NB; ++rr) Li[rr * NB + c] = y[rr];
 }
 
 // L21 = F21 L11^-T for rows [j0 + jb, f) of the panel columns: a thread per
@@ -204,8 +223,9 @@ constexpr int chol_nb() {
 template <typename T>
 cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
                               int32_t *piv, int *err, cudaStream_t s, const LuAsync *la, Prof *prof,
-                              const uint8_t *maps, float *pack, T *inv) {
+                              const uint8_t *maps, float *pack, T *inv, const CholSchedule *sched) {
   constexpr int NB = chol_nb<T>();
+  const CholSchedule sch = sched ? *sched : CholSchedule();
   const int nsm = device_sms();
   cudaError_t e = cudaSuccess;
   auto panel = [&](int j0, cudaStream_t st) -> cudaError_t {
@@ -233,8 +253,8 @@ cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfro
       // ---- FP32: outer blocks of KB columns, tensor-core updates ----
       constexpr int KB = kLuOuterBlock;
       static_assert(NB == 64 && KB % NB == 0, "panel and outer block");
-      const bool ahead = la != nullptr && la->side != nullptr && la->rest != nullptr && la->next != nullptr &&
-                         la->panel != nullptr && la->done != nullptr;
+      const bool ahead = sch.lookahead != 0 && la != nullptr && la->side != nullptr && la->rest != nullptr &&
+                         la->next != nullptr && la->panel != nullptr && la->done != nullptr;
       int64_t pack_tiles = 0;
       for (int k = 0; k < nfront; ++k) pack_tiles += cdiv_c(host_fr[k].f, kTcTile);
       const int64_t pack_stride = pack_tiles * kPackTileFloats;
@@ -248,7 +268,7 @@ cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfro
         if ((e = cudaStreamWaitEvent(rs, la->next, 0)) != cudaSuccess) return e;
       }
       // the lower-triangle rank-jbo update of the trailing block, columns [lo, hi)
-      auto block_end = [&](int J, int lo, int hi, int budget, float *ap, cudaStream_t st) -> cudaError_t {
+      auto block_end = [&](int J, int lo, int hi, int budget, float *ap, cudaStream_t st, int max_tiles) -> cudaError_t {
         double fg = 0.0;
         for (int k = 0; k < nfront; ++k) {
           const Front &F = host_fr[k];
@@ -264,7 +284,7 @@ cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfro
         const int tlo = lo / kTcTile, thi = hi >= (INT_MAX - kTcTile) ? INT_MAX : hi / kTcTile;
         const size_t e0 = prof->begin(st);
         cudaError_t ge = launch_gemm_tc_ws(fr, J, KB, nfront, max_f, fronts, err, st, tlo, thi, budget, maps, ap, ap,
-                                           /*lower=*/1);
+                                           /*lower=*/1, max_tiles);
         prof->end(P_GEMM, 1, e0, fg, st);
         return ge;
       };
@@ -300,12 +320,14 @@ cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfro
           // block's columns stay on the panel stream
           if ((e = cudaEventRecord(la->next, ms)) != cudaSuccess) return e;
           if ((e = cudaStreamWaitEvent(rs, la->next, 0)) != cudaSuccess) return e;
-          if ((e = block_end(J, KB, INT_MAX, std::max(nsm - nfront, nsm / 2), ap, rs)) != cudaSuccess) return e;
+          const int keep = sch.panel_sms >= 0 ? sch.panel_sms : nfront;
+          if ((e = block_end(J, KB, INT_MAX, std::max(nsm - keep, nsm / 2), ap, rs, sch.tiles_per_cta)) != cudaSuccess)
+            return e;
           if ((e = cudaEventRecord(done_ev[b & 1], rs)) != cudaSuccess) return e;
           if (b > 0 && (e = cudaStreamWaitEvent(ms, done_ev[(b - 1) & 1], 0)) != cudaSuccess) return e;
-          if ((e = block_end(J, 0, KB, nsm, ap, ms)) != cudaSuccess) return e;
+          if ((e = block_end(J, 0, KB, nsm, ap, ms, 0)) != cudaSuccess) return e;
         } else {
-          if ((e = block_end(J, 0, INT_MAX, nsm, ap, s)) != cudaSuccess) return e;
+          if ((e = block_end(J, 0, INT_MAX, nsm, ap, s, 0)) != cudaSuccess) return e;
         }
         if (more && (e = panel(J + KB, ms)) != cudaSuccess) return e;
       }
@@ -349,10 +371,10 @@ cudaError_t launch_chol_to_lu(const FrontDev *fr, int nfront, int max_f, T *fron
 
 template cudaError_t launch_chol_level<double>(const FrontDev *, const Front *, int, int, int, double *, int32_t *,
                                                int *, cudaStream_t, const LuAsync *, Prof *, const uint8_t *, float *,
-                                               double *);
+                                               double *, const CholSchedule *);
 template cudaError_t launch_chol_level<float>(const FrontDev *, const Front *, int, int, int, float *, int32_t *,
                                               int *, cudaStream_t, const LuAsync *, Prof *, const uint8_t *, float *,
-                                              float *);
+                                              float *, const CholSchedule *);
 template cudaError_t launch_chol_to_lu<double>(const FrontDev *, int, int, double *, cudaStream_t, Prof *, double);
 template cudaError_t launch_chol_to_lu<float>(const FrontDev *, int, int, float *, cudaStream_t, Prof *, double);
 

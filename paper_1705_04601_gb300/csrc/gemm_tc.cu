@@ -865,7 +865,7 @@ size_t gemm_ws_smem() { return size_t(kWsStages) * 4 * kPkTile * sizeof(float) +
 
 cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
                               cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps,
-                              const float *apack, const float *bpack, int lower) {
+                              const float *apack, const float *bpack, int lower, int max_tiles) {
   if (cudaError_t ea = smem_attr((const void *)k_gemm_tc_ws, int(gemm_ws_smem())); ea != cudaSuccess) return ea;
   (void)maps;
   if (apack == nullptr || bpack == nullptr) return cudaErrorInvalidValue;
@@ -875,7 +875,10 @@ cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, in
   const int ct = std::min((rest + kTcN - 1) / kTcN, tile_hi) - tile_lo;
   if (ct <= 0) return cudaSuccess;
   // a CTA's first tile costs about one more tile (set-up, first copies and C)
-  const int splits = wave_splits(rt, ct, nfront, std::max(sm_budget, 1), 1.0);
+  int splits = wave_splits(rt, ct, nfront, std::max(sm_budget, 1), 1.0);
+  // a cap on the column tiles of one CTA keeps CTAs short, so that the SMs
+  // turn over often (work on a higher-priority stream gets them sooner)
+  if (max_tiles > 0) splits = std::max(splits, std::min(ct, (ct + max_tiles - 1) / max_tiles));
   dim3 g(splits, rt, nfront);
   k_gemm_tc_ws<<<g, kWsThreads, gemm_ws_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi, apack,
                                                      bpack, lower);

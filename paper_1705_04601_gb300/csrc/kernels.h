@@ -132,6 +132,16 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
 template <typename T>
 cudaError_t launch_extend_add_impl(const FrontDev *fr_all, int lo, int nfront, int max_b, const int32_t *map,
                                    T *fronts, cudaStream_t s, Prof *prof, double elems, bool lower = false);
+// Schedule of the blocked FP32 block Cholesky (h2sp_set_option; chosen by the
+// package's autotuner): a cap on the 128-column tiles one CTA of the
+// low-priority block-end update takes (0: whole-wave split), the SMs that
+// update leaves free for the panel stream (-1: the level's front count), and
+// the look-ahead (the next block's panels on their own stream).
+struct CholSchedule {
+  int tiles_per_cta = 0;
+  int panel_sms = -1;
+  int lookahead = 1;
+};
 // Block Cholesky of every front of one level (all fronts in parallel): no
 // pivoting, lower-triangle updates, the B operand read from L21.  A pivot
 // that is not positive sets bit 8 of *err.  FP32 with `maps` and `pack` uses
@@ -141,7 +151,7 @@ constexpr int kCholInvElems = 64 * 64;
 template <typename T>
 cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
                               int32_t *piv, int *err, cudaStream_t s, const LuAsync *la, Prof *prof,
-                              const uint8_t *maps, float *pack, T *inv);
+                              const uint8_t *maps, float *pack, T *inv, const CholSchedule *sched = nullptr);
 // Rewrite Cholesky-factored fronts in the LU form: unit L = L_chol D^-1, U = D L_chol^T.
 template <typename T>
 cudaError_t launch_chol_to_lu(const FrontDev *fr, int nfront, int max_f, T *fronts, cudaStream_t s, Prof *prof,
@@ -225,7 +235,7 @@ cudaError_t launch_pack_b(const FrontDev *fr, int j0, int kb, int nfront, int ma
                           int ct_lo, int ct_hi, cudaStream_t s);
 cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
                               cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps,
-                              const float *apack, const float *bpack, int lower = 0);
+                              const float *apack, const float *bpack, int lower = 0, int max_tiles = 0);
 cudaError_t make_front_tmaps(const Front *fronts, int n, const float *base, uint8_t *maps_dev);
 constexpr int kTcTile = 128;
 
@@ -275,6 +285,7 @@ struct H2Dev {
   // leaves with more than 64 points come last in leaf_order and take the
   // close-block kernel that loops over row groups
   int32_t nleaf_large;
+  int32_t max_leaf;  // largest leaf (points); up to 128 admits the few-right-hand-side kernels
 };
 // y = A x with A of Definition 4.9 (upward pass, couplings, downward pass, close blocks);
 // xh / yh: coefficient workspaces with leading dimension ldh (>= sum of ranks), 16 columns

@@ -330,11 +330,19 @@ __global__ void __launch_bounds__(kThreads) k_transform(const XItem *__restrict_
 }
 
 // k_transform for blocks above kMaxBlock rows or columns: Y = QL^T X QR by
-// slabs of kSlab output columns.  Per slab J, T_J = X QR[:, J] (rows x kSlab,
-// X read from global memory, QR[:, J] staged), then Y[:, J] = QL^T T_J (QL
-// read from global memory) and each element goes to its quadrant's
-// destination.  Same association and summation order as k_transform.
-constexpr int kSlab = 16;
+// output slabs of kSlab columns, register-tiled.  Per slab J:
+//   stage 1  T_J = X QR[:, J]      (rows x kSlab, kept in shared memory)
+//   stage 2  Y_J = QL^T T_J        (rows x kSlab)
+// and each element of Y_J goes to its quadrant's destination.  Thread (tr,
+// tc) of the 32 x 8 grid owns rows tr + 32 i (i < ceil(rows / 32) <= 12) and
+// the four columns 4 tc .. 4 tc + 3 of the slab: 48 accumulators, so every
+// operand value a thread loads from shared memory serves four (or twelve)
+// multiply-adds.  The K dimension streams through shared memory in chunks of
+// kKc: X (or QL^T) as kKc columns of all rows, QR (or T) as kKc rows of the
+// slab.  Without QR (QL) the stage is a copy.
+constexpr int kSlab = 32;
+constexpr int kKc = 8;
+constexpr int kTrMax = kMaxLargeBlock / 32;  // row groups per thread
 
 template <typename W>
 __global__ void __launch_bounds__(kThreads) k_transform_large(const XItem *__restrict__ items,
@@ -342,68 +350,138 @@ __global__ void __launch_bounds__(kThreads) k_transform_large(const XItem *__res
                                                               const double *__restrict__ Qrow,
                                                               const double *__restrict__ Qcol,
                                                               W *const *__restrict__ dst_base) {
+  static_assert(kThreads == 256 && kSlab == 32, "thread grid of the tiles");
   const XItem it = items[blockIdx.x];
   const int rows = it.rows, cols = it.cols;
+  const int nti = (rows + 31) / 32;  // row groups in use
   extern __shared__ __align__(16) unsigned char smraw_l[];
-  W *sQ = reinterpret_cast<W *>(smraw_l);  // cols x kSlab, ld cols
-  W *sT = sQ + cols * kSlab;                // rows x kSlab, ld rows
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lda = rows + 1;                 // odd: the transposed stores of QL^T spread over the banks
+  W *sT = reinterpret_cast<W *>(smraw_l);  // rows x kSlab, ld rows (the slab of T = X QR)
+  W *sA = sT + size_t(rows) * kSlab;        // kKc columns of X or of QL^T, ld lda
+  W *sB = sA + size_t(lda) * kKc;           // kKc x kSlab of QR (row-major)
+  const int tid = threadIdx.x, tr = tid & 31, tc = tid >> 5;
   const bool near = it.src_buf == SRC_NEAR;
   const double *srcd = near ? static_cast<const double *>(src_base[SRC_NEAR]) + it.src : nullptr;
   const W *srcw = near ? nullptr : static_cast<const W *>(src_base[it.src_buf]) + it.src;
   const int64_t lds = it.ld_src;
   const double *QR = it.qR >= 0 ? ((it.qside & 2) ? Qcol : Qrow) + it.qR : nullptr;  // cols x cols
   const double *QL = it.qL >= 0 ? ((it.qside & 1) ? Qcol : Qrow) + it.qL : nullptr;  // rows x rows
+  auto xval = [&](int r, int q) -> W { return near ? W(srcd[r + int64_t(q) * lds]) : srcw[r + int64_t(q) * lds]; };
   const int kr = it.kr, kc = it.kc;
   for (int c0 = 0; c0 < cols; c0 += kSlab) {
     const int cb = min(kSlab, cols - c0);
+    // ---- stage 1: sT = X QR[:, c0 : c0 + cb] ----
     if (QR) {
-      for (int i = tid; i < cols * cb; i += nt) {
-        const int q = i % cols, c = i / cols;
-        sQ[q + c * cols] = W(QR[q + int64_t(c0 + c) * cols]);
-      }
-    }
-    __syncthreads();
-    for (int i = tid; i < rows * cb; i += nt) {
-      const int r = i % rows, c = i / rows;
-      W acc;
-      if (QR) {
-        acc = W(0);
-        const W *qc = sQ + c * cols;
-        if (near) {
-          for (int q = 0; q < cols; ++q) acc += W(srcd[r + q * lds]) * qc[q];
-        } else {
-          for (int q = 0; q < cols; ++q) acc += srcw[r + q * lds] * qc[q];
+      W acc[kTrMax][4];
+#pragma unroll
+      for (int i = 0; i < kTrMax; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = W(0);
+      for (int q0 = 0; q0 < cols; q0 += kKc) {
+        const int kn = min(kKc, cols - q0);
+        __syncthreads();  // sA / sB free
+        for (int e = tid; e < rows * kKc; e += kThreads) {
+          const int r = e % rows, k = e / rows;  // down the columns of X (coalesced)
+          sA[r + k * lda] = k < kn ? xval(r, q0 + k) : W(0);
         }
-      } else {
-        acc = near ? W(srcd[r + (c0 + c) * lds]) : srcw[r + (c0 + c) * lds];
+        for (int e = tid; e < kKc * kSlab; e += kThreads) {
+          const int k = e % kKc, c = e / kKc;  // down the columns of QR
+          sB[k * kSlab + c] = (k < kn && c < cb) ? W(QR[(q0 + k) + int64_t(c0 + c) * cols]) : W(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kKc; ++k) {
+          W b[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) b[j] = sB[k * kSlab + 4 * tc + j];
+#pragma unroll
+          for (int i = 0; i < kTrMax; ++i) {
+            if (i >= nti) break;
+            const int r = tr + 32 * i;
+            const W a = r < rows ? sA[r + k * lda] : W(0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += a * b[j];
+          }
+        }
       }
-      sT[r + c * rows] = acc;
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < kTrMax; ++i) {
+        if (i >= nti) break;
+        const int r = tr + 32 * i;
+        if (r < rows)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) sT[r + (4 * tc + j) * rows] = acc[i][j];
+      }
+    } else {
+      __syncthreads();
+      for (int e = tid; e < rows * kSlab; e += kThreads) {
+        const int r = e % rows, c = e / rows;
+        sT[e] = c < cb ? xval(r, c0 + c) : W(0);
+      }
     }
     __syncthreads();
-    for (int i = tid; i < rows * cb; i += nt) {
-      const int r = i % rows, c = i / rows;
-      const W *tc = sT + c * rows;
-      W y;
-      if (QL) {
-        const double *ql = QL + int64_t(r) * rows;  // column r of QL = row r of QL^T
-        y = W(0);
-        for (int q = 0; q < rows; ++q) y += W(ql[q]) * tc[q];
-      } else {
-        y = tc[r];
+    // ---- stage 2: Y = QL^T sT, then the quadrant scatter ----
+    W y[kTrMax][4];
+    if (QL) {
+#pragma unroll
+      for (int i = 0; i < kTrMax; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) y[i][j] = W(0);
+      for (int q0 = 0; q0 < rows; q0 += kKc) {
+        const int kn = min(kKc, rows - q0);
+        __syncthreads();  // sA free
+        // sA[r + k lda] = QL^T[r][q0 + k] = QL[(q0 + k) + r rows]
+        for (int e = tid; e < rows * kKc; e += kThreads) {
+          const int k = e % kKc, r = e / kKc;  // down the columns of QL
+          sA[r + k * lda] = k < kn ? W(QL[(q0 + k) + int64_t(r) * rows]) : W(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kKc; ++k) {
+          if (k >= kn) break;
+          W b[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) b[j] = sT[(q0 + k) + (4 * tc + j) * rows];
+#pragma unroll
+          for (int i = 0; i < kTrMax; ++i) {
+            if (i >= nti) break;
+            const int r = tr + 32 * i;
+            const W a = r < rows ? sA[r + k * lda] : W(0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) y[i][j] += a * b[j];
+          }
+        }
       }
-      const int cc = c0 + c;
-      const bool lo_r = r < kr, lo_c = cc < kc;
-      // quadrant of (r, cc): 0 basis x basis, 1 basis x non-basis, 2 non-basis x basis, 3 non-basis x non-basis
-      const int64_t doff = lo_r ? (lo_c ? it.dst[0] : it.dst[1]) : (lo_c ? it.dst[2] : it.dst[3]);
-      if (doff >= 0) {
-        const int dbuf = lo_r ? (lo_c ? it.dst_buf[0] : it.dst_buf[1]) : (lo_c ? it.dst_buf[2] : it.dst_buf[3]);
-        const int ldd = lo_r ? (lo_c ? it.ld[0] : it.ld[1]) : (lo_c ? it.ld[2] : it.ld[3]);
-        const int rr = lo_r ? r : r - kr, ccl = lo_c ? cc : cc - kc;
-        dst_base[dbuf][doff + rr + int64_t(ccl) * ldd] = y;
+    } else {
+#pragma unroll
+      for (int i = 0; i < kTrMax; ++i) {
+        if (i >= nti) break;
+        const int r = tr + 32 * i;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) y[i][j] = r < rows ? sT[r + (4 * tc + j) * rows] : W(0);
       }
     }
-    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kTrMax; ++i) {
+      if (i >= nti) break;
+      const int r = tr + 32 * i;
+      if (r >= rows) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int cc = c0 + 4 * tc + j;
+        if (4 * tc + j >= cb) continue;
+        const bool lo_r = r < kr, lo_c = cc < kc;
+        // quadrant of (r, cc): 0 basis x basis, 1 basis x non-basis, 2 non-basis x basis, 3 non-basis x non-basis
+        const int qd = (lo_r ? 0 : 2) + (lo_c ? 0 : 1);
+        const int64_t doff = it.dst[qd];
+        if (doff >= 0) {
+          const int rr = lo_r ? r : r - kr, ccl = lo_c ? cc : cc - kc;
+          dst_base[it.dst_buf[qd]][doff + rr + int64_t(ccl) * it.ld[qd]] = y[i][j];
+        }
+      }
+    }
+    __syncthreads();  // sT is rewritten by the next slab
   }
 }
 
@@ -469,7 +547,8 @@ cudaError_t launch_transform_large(const XItem *items, int n, const void *const 
                                    const double *Qcol, W *const *dst_base, int max_rows, int max_cols, cudaStream_t s,
                                    Prof *prof, double flops) {
   if (n == 0) return cudaSuccess;
-  const size_t smem = sizeof(W) * size_t(kSlab) * size_t(max_rows + max_cols);
+  const size_t smem = sizeof(W) * (size_t(max_rows) * kSlab + size_t(max_rows + 1) * kKc + size_t(kKc) * kSlab);
+  (void)max_cols;
   if (cudaError_t ea = smem_attr((const void *)k_transform_large<W>, int(smem)); ea != cudaSuccess) return ea;
   const size_t e0 = prof->begin();
   k_transform_large<W><<<n, kThreads, smem, s>>>(items, src_base, Qrow, Qcol, dst_base);

@@ -197,7 +197,7 @@ H.h2sp_apply = lambda hd, op, x, y, stream=None: y.copy_(x)
 
 args = argparse.Namespace(gpus=1, steps=2, warmup=1, impl="ours", workload="log2d_n65536", fp64_steps=1,
                           e2e_steps=2, factor="auto", sparsify_prec="fp32", solver="gmres", no_e2e=False,
-                          no_cpu_baseline=True)
+                          no_cpu_baseline=True, tune="auto")
 out = bench.run_ours(args, 1, 0, 0)
 print(json.dumps(out))
 '''
@@ -242,3 +242,21 @@ def test_bench_json_line_with_faked_library(tmp_path):
     assert out["factor_gflops_fp64"] > 0 and out["gpu_launches"] > 0
     assert out["converged"] is True and out["value"] is not None and out["config"]["factor"] == "block LU"
     assert out["fma_peaks_tflops"] == {"fp64": 1.2, "fp32": 75.0}
+
+
+def test_tune_cache_roundtrip(tmp_path, monkeypatch):
+    """The autotuner's store: keyed by device and structure sizes; the
+    environment's cache file is read before the shipped one and written."""
+    sys.path.insert(0, ROOT)
+    from paper_1705_04601_gb300 import tune as T
+    st = {"n": 262144, "nsupernodes": 66, "max_front": 89578, "chol_flops": 3.7e14}
+    k = T.key(st, "NVIDIA GB300")
+    assert k == T.key(dict(st), "NVIDIA GB300") and k != T.key(dict(st, max_front=1), "NVIDIA GB300")
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("H2SP_TUNE_CACHE", str(cache))
+    assert T.load(k) is None
+    sched = {"tiles_per_cta": 16, "panel_sms": 8, "lookahead": 1}
+    T.store(k, sched, 123.0)
+    assert T.load(k) == sched
+    assert json.load(open(cache))[k]["factor_ms"] == 123.0
+    assert set(T.DEFAULT) == set(T.CANDIDATES) and all(T.DEFAULT[n] in T.CANDIDATES[n] for n in T.DEFAULT)

@@ -197,3 +197,29 @@ def test_cholesky_then_lu_then_cholesky_same_handle():
         xs.append(host(xt))
     assert np.linalg.norm(xs[0] - xs[2]) <= 1e-9 * np.linalg.norm(xs[1])
     hd.close()
+
+
+def test_schedules_give_the_same_factor():
+    """Every candidate schedule of the autotuner (tiles per CTA of the
+    block-end update, SMs left to the panel stream, look-ahead) factors S to
+    the same L up to FP32 rounding order, and the tuner returns one of them."""
+    from paper_1705_04601_gb300 import tune as T
+    h, b, sp, ch = case("sphere8k")
+    an = H.h2sp_analyze(H.H2Input(h, device=None))
+    inp = H.H2Input(h)
+    ref = None
+    for sched in [T.DEFAULT, {"tiles_per_cta": 8, "panel_sms": 16, "lookahead": 1},
+                  {"tiles_per_cta": 32, "panel_sms": 8, "lookahead": 0}]:
+        hd = H.h2sp_sparsify_analyzed(an, inp)
+        T.apply(hd, sched)
+        H.h2sp_factor(hd, H.H2SP_FP32_CHOL)
+        F = [H.h2sp_export_front(hd, k)[0] for k in range(len(ch.L11))]
+        if ref is None:
+            ref = F
+        else:
+            for a, r in zip(F, ref):
+                assert np.linalg.norm(a - r) <= 1e-5 * np.linalg.norm(r)
+        hd.close()
+    sched, ms = T.tune(an, inp, flags=0, repeats=1)
+    assert ms > 0 and set(sched) == set(T.DEFAULT)
+    assert all(sched[n] in T.CANDIDATES[n] for n in sched)

@@ -44,11 +44,14 @@ def test_sweep_wait_runs_out_and_the_handle_recovers(prec):
         H.h2sp_solve(hd, bt, x1, mode=H.H2SP_DIRECT)
     assert e.value.status == H.H2SP_ETIMEOUT
     # the option cleared itself: the same handle solves again, to the same x
+    # up to the order of the atomic additions of the boundary rows (FP32
+    # factors: to the FP32 direct solve's accuracy)
     x2 = torch.empty_like(bt)
     info = H.h2sp_solve(hd, bt, x2, mode=H.H2SP_DIRECT)
     assert info.status == H.H2SP_OK
     torch.cuda.synchronize()
-    assert torch.equal(x0, x2) or float((x0 - x2).norm() / x0.norm()) <= 1e-6
+    tol = 1e-10 if prec == H.H2SP_FP64 else 1e-3
+    assert float((x0 - x2).norm() / x0.norm()) <= tol
     # and GMRES to 1e-10 still works on it
     info = H.h2sp_solve(hd, bt, x2, mode=H.H2SP_GMRES, tol=1e-10, maxit=60, restart=20)
     assert info.status == H.H2SP_OK and info.rel_residual <= 1e-10
