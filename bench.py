@@ -439,6 +439,8 @@ def run_ours(args, ws, rank, local):
         "schedule": sched, "schedule_source": sched_src, "tune_s": tune_s,
         "gpu_launches": int(launches), "gpu_launches_per_step": int(launches / max(args.steps, 1)),
         "kernel_ms_per_step": {c: v["ms"] for c, v in prof.items() if v["ms"] > 0},
+        "kernel_work_per_step": {c: v["work"] for c, v in prof.items() if v["ms"] > 0},
+        "kernel_launches_per_step": {c: v["timed"] for c, v in prof.items() if v["ms"] > 0},
         "clocks": clk, "cpu_baseline": cpu,
     }
     return out

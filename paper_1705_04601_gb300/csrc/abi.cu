@@ -212,6 +212,7 @@ struct h2sp_handle {
   LuAsync la;  // look-ahead stream and events of the block LU (created on first use)
   uint8_t *tmaps = nullptr;  // TMA descriptors of the FP32 fronts (built on the first FP32 factorization)
   uint8_t *tmaps_buf = nullptr;     // their device storage
+  uint8_t *tmaps64 = nullptr;       // the same fronts with 128 x 64 boxes (the block-end update's C halves)
   const void *tmaps_base = nullptr;  // the front buffer they were encoded for
   float *pack = nullptr;     // packed GEMM operands of the blocked FP32 LU (3 buffers of the largest level)
   int32_t last_prec = -1;    // h2sp_prec of the last h2sp_factor (h2sp_refactor repeats it)
@@ -1193,11 +1194,15 @@ void factor_prepare(h2sp_handle *h, int32_t prec) {
   if (prec_fp32(prec) && tma_enabled() && !p.fronts.empty() && h->tmaps_base != h->fronts) {
     // (re-)encode the descriptors whenever the front buffer is new
     h->tmaps = nullptr;
-    if (h->tmaps_buf == nullptr) h->tmaps_buf = h->alloc<uint8_t>(p.fronts.size() * kTmapBytes);
+    if (h->tmaps_buf == nullptr) h->tmaps_buf = h->alloc<uint8_t>(2 * p.fronts.size() * kTmapBytes);
     ck(cudaStreamSynchronize(s));  // the allocation is usable by the synchronous copy
+    uint8_t *m64 = h->tmaps_buf + p.fronts.size() * kTmapBytes;
     if (make_front_tmaps(p.fronts.data(), int(p.fronts.size()), static_cast<float *>(h->fronts), h->tmaps_buf) ==
-        cudaSuccess) {
+            cudaSuccess &&
+        make_front_tmaps(p.fronts.data(), int(p.fronts.size()), static_cast<float *>(h->fronts), m64, 64) ==
+            cudaSuccess) {
       h->tmaps = h->tmaps_buf;
+      h->tmaps64 = m64;
       h->tmaps_base = h->fronts;
     }
     cudaGetLastError();
@@ -1223,12 +1228,14 @@ void factor_launch_t(h2sp_handle *h, bool chol) {
   const bool fp32 = std::is_same<T, float>::value;
   for (const FrontLevel &L : h->flev) {
     const uint8_t *maps = (fp32 && h->tmaps) ? h->tmaps + size_t(L.lo) * kTmapBytes : nullptr;
+    const uint8_t *maps64 = (fp32 && h->tmaps64) ? h->tmaps64 + size_t(L.lo) * kTmapBytes : nullptr;
     if (chol) {
       ck(launch_chol_level<T>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv, h->err,
-                              s, la, &h->prof, maps, h->pack, reinterpret_cast<T *>(h->chol_inv), &h->chol_sched));
+                              s, la, &h->prof, maps, h->pack, reinterpret_cast<T *>(h->chol_inv), &h->chol_sched,
+                              maps64));
     } else {
       ck(launch_lu_level<T>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv, h->swaps,
-                            h->err, s, la, &h->prof, maps, fp32 ? h->pack : nullptr));
+                            h->err, s, la, &h->prof, maps, fp32 ? h->pack : nullptr, maps64));
     }
     ck(launch_extend_add_impl<T>(h->fr, L.lo, L.hi - L.lo, L.max_b, h->fmap, F, s, &h->prof, chol ? 0.5 * L.b2 : L.b2,
                                  chol));

@@ -34,101 +34,85 @@ namespace {
 
 inline int cdiv_c(int64_t a, int64_t b) { return int((a + b - 1) / b); }
 
-// Cholesky of the diagonal tile [j0, j0 + jb) of every front.  Thread r holds
-// row r of the tile (its lower part) in registers.  Per column j: thread j
-// takes the square root of its diagonal entry, every row below scales its
-// entry j by it and publishes it, and updates its entries j+1 .. r.  A
-// pivot that is not positive and finite sets bit 8 of *err (the matrix is
-// not positive definite in this precision) and is replaced by 1 so that the
-// factorization stays finite.  Then thread c forms column c of L11^-1 by
-// forward substitution, y_r = -(sum_{c<=m<r} l_rm y_m) / l_rr with
-// y_c = 1 / l_cc, each row's sum split over four partial sums, and writes it
-// to inv[front][r * NB + c] (row-major, zero above the diagonal and beyond jb).
+// Cholesky of the diagonal tile [j0, j0 + jb) of every front, and its inverse.
+// The tile sits in shared memory; the loops stay compact (this kernel runs
+// once per panel, so instruction fetch, not arithmetic, would bound a fully
+// unrolled form).  kDiagThreads threads: four per row.
+//   Cholesky, left-looking by columns: for column j, the four threads of row
+//   r >= j each take a quarter of l_rj's dot product sum_{m<j} l_rm l_jm
+//   (lanes of one warp, added by shuffles); l_jj = sqrt(a_jj - ...) and
+//   l_rj = (a_rj - ...) / l_jj.  A pivot that is not positive and finite sets
+//   bit 8 of *err (S is not positive definite in this precision) and is
+//   replaced by 1 so that the factorization stays finite.
+//   Inverse, forward substitution by columns: the four threads of column c
+//   (lanes of one warp) split y_r = -(sum_{c<=m<r} l_rm y_m) / l_rr, with
+//   y_c = 1 / l_cc, row by row; it goes to inv[front][r * NB + c]
+//   (row-major, zero above the diagonal and beyond jb).
+constexpr int kDiagThreads = 256;
 template <typename T, int NB>
-__global__ void __launch_bounds__(NB) k_chol_diag(const FrontDev *__restrict__ fr, int j0, T *__restrict__ fronts,
-                                                  int32_t *__restrict__ piv, int *__restrict__ err,
-                                                  T *__restrict__ inv) {
+__global__ void __launch_bounds__(kDiagThreads) k_chol_diag(const FrontDev *__restrict__ fr, int j0,
+                                                            T *__restrict__ fronts, int32_t *__restrict__ piv,
+                                                            int *__restrict__ err, T *__restrict__ inv) {
+  static_assert(NB * 4 <= kDiagThreads, "four threads per row");
   const FrontDev F = fr[blockIdx.x];
   if (j0 >= F.s) return;  // uniform over the CTA
   const int jb = min(NB, F.s - j0);
   T *A = fronts + F.off;
   const int64_t ld = F.ld;
-  constexpr int P = NB + 1;       // padded row length of the tile in shared memory
-  __shared__ T col[NB];           // the current column below the pivot, and the pivot itself
-  __shared__ T Lr[NB * P];        // L11 row-major (row r at r * P), zero above the diagonal and beyond jb
-  const int r = threadIdx.x;
-  {
-    T x[NB];
-#pragma unroll
-    for (int c = 0; c < NB; ++c) x[c] = (r < jb && c <= r) ? A[(j0 + r) + int64_t(j0 + c) * ld] : T(0);
-    for (int j = 0; j < jb; ++j) {
-      T xj = T(0);
-#pragma unroll
-      for (int c = 0; c < NB; ++c)
-        if (c == j) xj = x[c];
-      if (r == j) {
-        T a = xj;
-        if (!(a > T(0)) || !isfinite(a)) {
-          atomicOr(err, 8);
-          a = T(1);
-        }
-        col[j] = sqrt(a);
-      }
-      __syncthreads();
-      const T d = col[j];
-      T l = T(0);
-      if (r > j && r < jb) {
-        l = xj / d;
-        col[r] = l;
-      }
-      __syncthreads();
-      if (r >= j && r < jb) {
-        // entry j becomes final (l, or d on the diagonal); entries j+1 .. r take the update
-#pragma unroll
-        for (int c = 0; c < NB; ++c) {
-          if (c == j) x[c] = (r == j) ? d : l;
-          else if (c > j && c <= r) x[c] -= l * col[c];
-        }
-      }
-      __syncthreads();  // col is rewritten by the next column
-    }
-#pragma unroll
-    for (int c = 0; c < NB; ++c) Lr[r * P + c] = (r < jb && c <= r) ? x[c] : T(0);
-    if (r < jb) {
-#pragma unroll
-      for (int c = 0; c < NB; ++c)
-        if (c <= r) A[(j0 + r) + int64_t(j0 + c) * ld] = x[c];
-      piv[F.piv_off + j0 + r] = j0 + r;
-    }
+  constexpr int P = NB + 1;  // padded row length
+  __shared__ T L[NB * P];    // row-major: L[r * P + c]
+  __shared__ T Y[NB * P];    // L11^-1, row-major
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NB * NB; e += kDiagThreads) {
+    const int r = e % NB, c = e / NB;  // down the columns of the front
+    L[r * P + c] = (r < jb && c <= r) ? A[(j0 + r) + int64_t(j0 + c) * ld] : T(0);
   }
   __syncthreads();
-  // column c = r of L11^-1
-  const int c = r;
-  T y[NB];
-#pragma unroll
-  for (int q = 0; q < NB; ++q) y[q] = T(0);
-  if (c < jb) {
-#pragma unroll
-    for (int rr = 0; rr < NB; ++rr) {
-      if (rr < c || rr >= jb) continue;
-      if (rr == c) {
-        y[rr] = T(1) / Lr[rr * P + rr];
-        continue;
+  const int r = tid >> 2, sub = tid & 3;  // row (or column, below) and quarter
+  for (int j = 0; j < jb; ++j) {
+    T part = T(0);
+    if (r >= j && r < jb)
+      for (int m = sub; m < j; m += 4) part += L[r * P + m] * L[j * P + m];
+    part += __shfl_xor_sync(0xffffffffu, part, 1);
+    part += __shfl_xor_sync(0xffffffffu, part, 2);
+    if (sub == 0 && r == j) {
+      T a = L[j * P + j] - part;
+      if (!(a > T(0)) || !isfinite(a)) {
+        atomicOr(err, 8);
+        a = T(1);
       }
-      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-#pragma unroll
-      for (int m = 0; m < rr; m += 4) {
-        if (m >= c) s0 += Lr[rr * P + m] * y[m];
-        if (m + 1 < rr && m + 1 >= c) s1 += Lr[rr * P + m + 1] * y[m + 1];
-        if (m + 2 < rr && m + 2 >= c) s2 += Lr[rr * P + m + 2] * y[m + 2];
-        if (m + 3 < rr && m + 3 >= c) s3 += Lr[rr * P + m + 3] * y[m + 3];
-      }
-      y[rr] = -((s0 + s1) + (s2 + s3)) / Lr[rr * P + rr];
+      L[j * P + j] = sqrt(a);
     }
+    __syncthreads();
+    if (sub == 0 && r > j && r < jb) L[r * P + j] = (L[r * P + j] - part) / L[j * P + j];
+    __syncthreads();
+  }
+  // inverse: the four lanes of column c = r walk the rows together
+  const int c = r;
+  for (int rr = 0; rr < NB; ++rr) {
+    T part = T(0);
+    if (c < jb && rr > c && rr < jb)
+      for (int m = c + sub; m < rr; m += 4) part += L[rr * P + m] * Y[m * P + c];
+    part += __shfl_xor_sync(0xffffffffu, part, 1);
+    part += __shfl_xor_sync(0xffffffffu, part, 2);
+    if (sub == 0 && c < NB) {  // (threads of columns c >= NB only join the shuffles)
+      T y = T(0);
+      if (c < jb && rr < jb) {
+        if (rr == c) y = T(1) / L[rr * P + rr];
+        else if (rr > c) y = -part / L[rr * P + rr];
+      }
+      Y[rr * P + c] = y;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int e = tid; e < NB * NB; e += kDiagThreads) {
+    const int rr = e % NB, cc = e / NB;
+    if (rr < jb && cc <= rr) A[(j0 + rr) + int64_t(j0 + cc) * ld] = L[rr * P + cc];
   }
   T *Li = inv + int64_t(blockIdx.x) * NB * NB;
-#pragma unroll
-  for (int rr = 0; rr < NB; ++rr) Li[rr * NB + c] = y[rr];
+  for (int e = tid; e < NB * NB; e += kDiagThreads) Li[e] = Y[(e / NB) * P + e % NB];
+  for (int j = tid; j < jb; j += kDiagThreads) piv[F.piv_off + j0 + j] = j0 + j;
 }
 
 // L21 = F21 L11^-T for rows [j0 + jb, f) of the panel columns: a thread per
@@ -223,7 +207,8 @@ constexpr int chol_nb() {
 template <typename T>
 cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
                               int32_t *piv, int *err, cudaStream_t s, const LuAsync *la, Prof *prof,
-                              const uint8_t *maps, float *pack, T *inv, const CholSchedule *sched) {
+                              const uint8_t *maps, float *pack, T *inv, const CholSchedule *sched,
+                              const uint8_t *maps64) {
   constexpr int NB = chol_nb<T>();
   const CholSchedule sch = sched ? *sched : CholSchedule();
   const int nsm = device_sms();
@@ -238,7 +223,7 @@ cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfro
         fpanel += jb * jb * jb / 3.0 + rows * jb * jb;  // tile Cholesky + triangular solve of the rows below
       }
     const size_t e0 = prof->begin(st);
-    k_chol_diag<T, NB><<<nfront, NB, 0, st>>>(fr, j0, fronts, piv, err, inv);
+    k_chol_diag<T, NB><<<nfront, kDiagThreads, 0, st>>>(fr, j0, fronts, piv, err, inv);
     const int below = max_f - j0 - 1;
     if (below > 0)
       k_chol_l21<T, NB><<<dim3(unsigned(cdiv_c(below, kL21Threads)), unsigned(nfront)), kL21Threads, 0, st>>>(
@@ -284,7 +269,7 @@ cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfro
         const int tlo = lo / kTcTile, thi = hi >= (INT_MAX - kTcTile) ? INT_MAX : hi / kTcTile;
         const size_t e0 = prof->begin(st);
         cudaError_t ge = launch_gemm_tc_ws(fr, J, KB, nfront, max_f, fronts, err, st, tlo, thi, budget, maps, ap, ap,
-                                           /*lower=*/1, max_tiles);
+                                           /*lower=*/1, max_tiles, maps64);
         prof->end(P_GEMM, 1, e0, fg, st);
         return ge;
       };
@@ -371,10 +356,10 @@ cudaError_t launch_chol_to_lu(const FrontDev *fr, int nfront, int max_f, T *fron
 
 template cudaError_t launch_chol_level<double>(const FrontDev *, const Front *, int, int, int, double *, int32_t *,
                                                int *, cudaStream_t, const LuAsync *, Prof *, const uint8_t *, float *,
-                                               double *, const CholSchedule *);
+                                               double *, const CholSchedule *, const uint8_t *);
 template cudaError_t launch_chol_level<float>(const FrontDev *, const Front *, int, int, int, float *, int32_t *,
                                               int *, cudaStream_t, const LuAsync *, Prof *, const uint8_t *, float *,
-                                              float *, const CholSchedule *);
+                                              float *, const CholSchedule *, const uint8_t *);
 template cudaError_t launch_chol_to_lu<double>(const FrontDev *, int, int, double *, cudaStream_t, Prof *, double);
 template cudaError_t launch_chol_to_lu<float>(const FrontDev *, int, int, float *, cudaStream_t, Prof *, double);
 

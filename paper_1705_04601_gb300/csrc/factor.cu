@@ -1865,7 +1865,7 @@ inline bool use_tensor_core_gemm() {
 template <typename T>
 cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
                             int32_t *piv, int32_t *swaps, int *err, cudaStream_t s, const LuAsync *la, Prof *prof,
-                            const uint8_t *maps, float *pack) {
+                            const uint8_t *maps, float *pack, const uint8_t *maps64) {
   constexpr int NB = LuCfg<T>::NB;
   using G = GemmCfg<T>;
   auto gemm = k_gemm_update<T, G::BM, G::BN, G::TM, G::TN, NB>;
@@ -2055,7 +2055,7 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
         e0 = prof->begin(st);
         if (ge == cudaSuccess)
           ge = launch_gemm_tc_ws(fr, J, KB, nfront, max_f, fronts, err, st, tlo, thi, budget, maps,
-                                 apack[(J / KB) & 1], bpack);
+                                 apack[(J / KB) & 1], bpack, 0, 0, maps64);
         prof->end(P_GEMM, 1, e0, fg, st);
         return ge != cudaSuccess ? ge : cudaGetLastError();
       };
@@ -2362,7 +2362,7 @@ template cudaError_t launch_assemble<float, double>(const AItem *, int64_t, cons
                                                     Prof *, double);
 template cudaError_t launch_lu_level<double>(const FrontDev *, const Front *, int, int, int, double *, int32_t *, int32_t *,
                                            int *, cudaStream_t, const LuAsync *, Prof *,
-                                           const uint8_t *, float *);
+                                           const uint8_t *, float *, const uint8_t *);
 template cudaError_t launch_make_perm<double>(const FrontDev *, int, int, const int32_t *, int32_t *, cudaStream_t, Prof *);
 template cudaError_t launch_extend_add_impl<double>(const FrontDev *, int, int, int, const int32_t *, double *, cudaStream_t,
                                                   Prof *, double, bool);
@@ -2389,7 +2389,7 @@ template cudaError_t launch_assemble<float, float>(const AItem *, int64_t, const
                                                    double);
 template cudaError_t launch_lu_level<float>(const FrontDev *, const Front *, int, int, int, float *, int32_t *, int32_t *,
                                            int *, cudaStream_t, const LuAsync *, Prof *,
-                                           const uint8_t *, float *);
+                                           const uint8_t *, float *, const uint8_t *);
 template cudaError_t launch_make_perm<float>(const FrontDev *, int, int, const int32_t *, int32_t *, cudaStream_t, Prof *);
 template cudaError_t launch_extend_add_impl<float>(const FrontDev *, int, int, int, const int32_t *, float *, cudaStream_t,
                                                   Prof *, double, bool);

@@ -476,7 +476,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc_tma(const FrontDev *_
 constexpr int kPkK = 16;                          // K values per packed chunk
 constexpr int kPkTile = kTcM * kPkK;              // floats per hi (or lo) array: 2048 = 8 KB
 constexpr uint32_t kPkSbo = (kPkK / 4) * 128;     // 8-row groups of a packed array (512 bytes)
-constexpr int kWsStages = 6;                      // chunks in flight (32 KB each)
+constexpr int kWsStages = 5;                      // chunks in flight (32 KB each)
+constexpr int kWsHalf = 64;                       // columns of one C half-tile moved by TMA
+constexpr int kWsCFloats = kTcM * kWsHalf;        // one C half-tile in shared memory: 32 KB
 static_assert(kPackTileFloats == int64_t(kPackChunks) * 2 * kPkTile, "packed tile size");
 
 __device__ __forceinline__ uint64_t smem_desc_pk(uint32_t saddr) {
@@ -603,7 +605,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__
                                                              float *__restrict__ fronts, int *__restrict__ err,
                                                              int splits, int tile_lo, int tile_hi,
                                                              const float *__restrict__ apack,
-                                                             const float *__restrict__ bpack, int lower) {
+                                                             const float *__restrict__ bpack, int lower,
+                                                             const uint8_t *__restrict__ maps64) {
   const FrontDev F = fr[blockIdx.z];
   if (j0 >= F.s) return;
   const int jb = min(kb, F.s - j0);
@@ -625,7 +628,13 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__
   const int64_t ld = F.ld;
   extern __shared__ __align__(1024) unsigned char smraw[];
   float *stage0 = reinterpret_cast<float *>(smraw);  // kWsStages x (Ah, Al, Bh, Bl)
-  __shared__ __align__(8) uint64_t full[kWsStages], empty[kWsStages], accf[2], acce[2];
+  float *sC = stage0 + kWsStages * 4 * kPkTile;      // two C half-tiles (TMA epilogue)
+  __shared__ __align__(8) uint64_t full[kWsStages], empty[kWsStages], accf[2], acce[2], cfull[2];
+  // The C tiles move by TMA when the tile origin's row t0 + rb sits on a
+  // 16-byte boundary (the tensor maps' rule for the innermost coordinate);
+  // otherwise the epilogue threads load and store C themselves.
+  const bool use_tma = maps64 != nullptr && (t0 & 3) == 0;
+  const void *tmap = use_tma ? static_cast<const void *>(maps64 + size_t(blockIdx.z) * kTmapBytes) : nullptr;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -642,6 +651,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__
     for (int i = 0; i < 2; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&accf[i])), "r"(1));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acce[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&cfull[i])), "r"(1));
     }
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
@@ -730,8 +740,81 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__
           wait_phase(smem_u32(&empty[last_mma % kWsStages]), uint32_t((last_mma / kWsStages) & 1));
       }
     }
+  } else if (use_tma) {
+    // ---- epilogue warps with TMA: per tile two 128 x 64 halves of C pass
+    // through sC[h]; thread (q4, qc) owns row q4 * 32 + lane and columns
+    // qc * 16 .. + 15 of each half.  Thread 0 issues every TMA operation: the
+    // load of half h of the next tile goes out as soon as the store of half h
+    // of this tile has read sC[h], so it runs under the next tile's MMAs.
+    const int q4 = warp & 3, qc = warp >> 2;
+    const int row = q4 * 32 + lane;
+    const int x = t0 + rb;
+    auto load_half = [&](int ct, int h) {
+      const uint32_t mb = smem_u32(&cfull[h]);
+      mbar_expect_tx(mb, uint32_t(kWsCFloats * 4));
+      tma_load_2d(smem_u32(sC + h * kWsCFloats), tmap, x, t0 + ct * kTcN + h * kWsHalf, mb);
+    };
+    if (tid == 0) {
+      load_half(c_lo, 0);
+      load_half(c_lo, 1);
+    }
+    int loads_issued = 2, loads_done = 0;  // thread 0's count of C halves requested / consumed
+    for (int i = 0; i < nt; ++i) {
+      const int a = i & 1, ct = c_lo + i;
+      const bool w = !abort_flag && wait_phase(smem_u32(&accf[a]), uint32_t((i >> 1) & 1));
+      if (!epi_bar_and(w)) {
+        if (tid == 0) abort_flag = 1, atomicOr(err, 4);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      bool ok = true;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const bool wc = !abort_flag && wait_phase(smem_u32(&cfull[h]), uint32_t(i & 1));
+        if (!epi_bar_and(wc)) {
+          ok = false;
+          break;
+        }
+        if (tid == 0) ++loads_done;
+        uint32_t v[16];
+        const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(a * kTcN + h * kWsHalf + qc * 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        float *col = sC + h * kWsCFloats + (qc * 16) * kTcM + row;  // box order: rows fastest
+#pragma unroll
+        for (int j = 0; j < 16; ++j) col[j * kTcM] -= __uint_as_float(v[j]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        epi_bar();
+        if (tid == 0) {
+          tma_store_2d(tmap, x, t0 + ct * kTcN + h * kWsHalf, smem_u32(sC + h * kWsCFloats));
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          if (i + 1 < nt) {
+            // sC[h] is read by the store before it is refilled
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            load_half(ct + 1, h);
+            ++loads_issued;
+          }
+        }
+      }
+      if (!ok) {
+        if (tid == 0) abort_flag = 1, atomicOr(err, 4);
+        break;
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      if (tid == 0) mbar_arrive(smem_u32(&acce[a]));  // the accumulator is free again
+    }
+    if (tid == 0) {
+      // bounded waits for the C loads still writing sC, then for the stores
+      for (int g = loads_done; g < loads_issued; ++g) wait_phase(smem_u32(&cfull[g & 1]), uint32_t((g >> 1) & 1));
+      asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    }
   } else {
-    // ---- epilogue warps: thread (q4, qc) owns row q4 * 32 + lane, columns qc * 32 .. + 31 ----
+    // ---- epilogue warps without TMA: thread (q4, qc) owns row q4 * 32 + lane, columns qc * 32 .. + 31 ----
     const int q4 = warp & 3, qc = warp >> 2;
     const int row = rb + q4 * 32 + lane;
     for (int i = 0; i < nt; ++i) {
@@ -861,11 +944,12 @@ cudaError_t launch_pack_b(const FrontDev *fr, int j0, int kb, int nfront, int ma
   return cudaGetLastError();
 }
 
-size_t gemm_ws_smem() { return size_t(kWsStages) * 4 * kPkTile * sizeof(float) + 1024; }
+size_t gemm_ws_smem() { return (size_t(kWsStages) * 4 * kPkTile + 2 * size_t(kWsCFloats)) * sizeof(float) + 1024; }
 
 cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
                               cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps,
-                              const float *apack, const float *bpack, int lower, int max_tiles) {
+                              const float *apack, const float *bpack, int lower, int max_tiles,
+                              const uint8_t *maps64) {
   if (cudaError_t ea = smem_attr((const void *)k_gemm_tc_ws, int(gemm_ws_smem())); ea != cudaSuccess) return ea;
   (void)maps;
   if (apack == nullptr || bpack == nullptr) return cudaErrorInvalidValue;
@@ -881,13 +965,13 @@ cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, in
   if (max_tiles > 0) splits = std::max(splits, std::min(ct, (ct + max_tiles - 1) / max_tiles));
   dim3 g(splits, rt, nfront);
   k_gemm_tc_ws<<<g, kWsThreads, gemm_ws_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi, apack,
-                                                     bpack, lower);
+                                                     bpack, lower, maps64);
   return cudaGetLastError();
 }
 
 // One TMA descriptor per FP32 front: 2D, rows x columns, leading dimension
 // ld (16-byte multiple), 128 x 128 boxes, zero fill outside the front.
-cudaError_t make_front_tmaps(const Front *fronts, int n, const float *base, uint8_t *maps_dev) {
+cudaError_t make_front_tmaps(const Front *fronts, int n, const float *base, uint8_t *maps_dev, int box_cols) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (encode == nullptr) {
     void *fn = nullptr;
@@ -902,7 +986,7 @@ cudaError_t make_front_tmaps(const Front *fronts, int n, const float *base, uint
     const Front &F = fronts[k];
     const cuuint64_t dims[2] = {cuuint64_t(std::max(F.f, 1)), cuuint64_t(std::max(F.f, 1))};
     const cuuint64_t strides[1] = {cuuint64_t(F.ld) * sizeof(float)};
-    const cuuint32_t box[2] = {cuuint32_t(kTcM), cuuint32_t(kTcN)};
+    const cuuint32_t box[2] = {cuuint32_t(kTcM), cuuint32_t(box_cols)};
     const cuuint32_t es[2] = {1, 1};
     CUresult r = encode(&maps[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base + F.off), dims, strides,
                         box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

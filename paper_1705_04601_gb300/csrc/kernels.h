@@ -126,7 +126,7 @@ struct LuAsync {
 template <typename T>
 cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
                             int32_t *piv, int32_t *swaps, int *err, cudaStream_t s, const LuAsync *la, Prof *prof,
-                            const uint8_t *maps = nullptr, float *pack = nullptr);
+                            const uint8_t *maps = nullptr, float *pack = nullptr, const uint8_t *maps64 = nullptr);
 // lower: only the lower triangle of each contribution block (block Cholesky;
 // the map is monotone, so it lands in the parent's lower triangle)
 template <typename T>
@@ -151,7 +151,8 @@ constexpr int kCholInvElems = 64 * 64;
 template <typename T>
 cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
                               int32_t *piv, int *err, cudaStream_t s, const LuAsync *la, Prof *prof,
-                              const uint8_t *maps, float *pack, T *inv, const CholSchedule *sched = nullptr);
+                              const uint8_t *maps, float *pack, T *inv, const CholSchedule *sched = nullptr,
+                              const uint8_t *maps64 = nullptr);
 // Rewrite Cholesky-factored fronts in the LU form: unit L = L_chol D^-1, U = D L_chol^T.
 template <typename T>
 cudaError_t launch_chol_to_lu(const FrontDev *fr, int nfront, int max_f, T *fronts, cudaStream_t s, Prof *prof,
@@ -235,8 +236,10 @@ cudaError_t launch_pack_b(const FrontDev *fr, int j0, int kb, int nfront, int ma
                           int ct_lo, int ct_hi, cudaStream_t s);
 cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
                               cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps,
-                              const float *apack, const float *bpack, int lower = 0, int max_tiles = 0);
-cudaError_t make_front_tmaps(const Front *fronts, int n, const float *base, uint8_t *maps_dev);
+                              const float *apack, const float *bpack, int lower = 0, int max_tiles = 0,
+                              const uint8_t *maps64 = nullptr);
+// one descriptor per front: 2D (rows, columns), boxes of 128 rows x box_cols columns
+cudaError_t make_front_tmaps(const Front *fronts, int n, const float *base, uint8_t *maps_dev, int box_cols = 128);
 constexpr int kTcTile = 128;
 
 // ---- applies, H^2 product, vector kernels (apply.cu) ----

@@ -669,6 +669,10 @@ WORKLOADS = {
                                  points="sphere"),
     # 3D Yukawa, N=1048576 uniform in the cube, leaf<=128, tol 1e-4
     "yukawa3d_n1048576": dict(kernel="yukawa", n=1048576, dim=3, leaf=128, tol=1e-4, nrhs=1, index=5),
+    # batched form: 256 independent 2D -log r systems on random ellipses, N_k ~ U[2048, 32768], leaf<=64,
+    # tol 1e-6, one forest (n = the systems' total; "n" overrides the count of systems)
+    "batched_ellipse_256": dict(kernel="log", n=256, dim=2, leaf=64, tol=1e-6, nrhs=1, index=4,
+                                batched=(2048, 32768), points="ellipses"),
 }
 
 
@@ -678,6 +682,13 @@ def make_workload(name: str, n: Optional[int] = None, seed: Optional[int] = None
     cfg = dict(WORKLOADS[name])
     if n is not None:
         cfg["n"] = n
+    if "batched" in cfg:
+        # n counts systems; the size range may be narrowed through leaf/tol-free overrides of the caller
+        lo, hi = cfg["batched"]
+        _, forest, b = make_batched(cfg["n"], lo, hi, seed=SEED_BASE + cfg["index"] if seed is None else seed,
+                                    leaf=cfg["leaf"] if leaf is None else leaf,
+                                    tol=cfg["tol"] if tol == "cfg" else tol, nrhs=cfg["nrhs"])
+        return forest, b
     if leaf is not None:
         cfg["leaf"] = leaf
     if tol != "cfg":
@@ -853,11 +864,24 @@ def make_batched(nsys: int, n_lo: int, n_hi: int, seed: int = SEED_BASE + 4, lea
     N_k ~ U[n_lo, n_hi]; ellipse centre (0.5, 0.5), full axes ~ U[0.2, 1],
     random rotation; diagonal -log(0.5/sqrt(N_k)).  Returns (systems, forest, b)."""
     rng = np.random.default_rng(seed)
-    systems = []
-    for k in range(nsys):
-        nk = int(rng.integers(n_lo, n_hi + 1))
-        pts = points_ellipse(nk, np.random.default_rng(seed + 1000 * (k + 1)))
-        systems.append(build_h2(pts, "log", leaf, tol=tol))
+    sizes = [int(rng.integers(n_lo, n_hi + 1)) for _ in range(nsys)]
+    jobs = [(nk, seed + 1000 * (k + 1), leaf, tol) for k, nk in enumerate(sizes)]
+    workers = min(len(jobs), os.cpu_count() or 1, int(os.environ.get("H2SP_GEN_WORKERS", "16")))
+    if workers > 1 and sum(sizes) > 200000:
+        # the systems are independent: build them in worker processes (spawned,
+        # so that no CUDA state is inherited), each from its own seed as below
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            systems = list(ex.map(_ellipse_system, jobs, chunksize=max(1, len(jobs) // (4 * workers))))
+    else:
+        systems = [_ellipse_system(j) for j in jobs]
     forest = make_forest(systems)
     b = rng.standard_normal((forest.n, nrhs))
     return systems, forest, b
+
+
+def _ellipse_system(job):
+    nk, sd, leaf, tol = job
+    pts = points_ellipse(nk, np.random.default_rng(sd))
+    return build_h2(pts, "log", leaf, tol=tol)
