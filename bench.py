@@ -64,7 +64,14 @@ SPD_WORKLOADS = {"inv3d_sphere_n262144"}
 # algorithmic work, valid while the kernel's source file is unchanged (sha256
 # prefix of "src").  The bench's traffic figure is this ratio times the
 # class's average work per launch.
-TRAFFIC = {}
+TRAFFIC = {
+    "gemm_update": {
+        "src": "gemm_tc.cu", "src_hash": "6c2ff605cd11920b", "dram_over_algorithmic": 0.016543,
+        "capture": "profiles/gemm_tc_ws_inv3d_sphere_n32768.md: dram__bytes_read.sum + dram__bytes_write.sum over "
+                   "every k_gemm_tc_ws launch of two factorizations at N = 32,768 (70.52 GB per factorization) "
+                   "divided by their algorithmic flops (4.263e12)",
+    },
+}
 
 
 def parse(argv=None):
@@ -446,6 +453,165 @@ def run_ours(args, ws, rank, local):
     return out
 
 
+def run_batched(args, ws, rank, local):
+    """The batched form: many independent systems in one forest (one analysis,
+    one handle).  A step is the persistent graph form: h2sp_refactor (graph
+    replay of the numeric sparsification and the FP32 block LU of every
+    system) + iterative refinement on the FP64 H^2 residual until every
+    system's relative residual is <= 1e-10."""
+    import numpy as np
+    import torch
+
+    from paper_1705_04601_gb300 import build
+    from paper_1705_04601_gb300 import h2sp as H
+    from paper_1705_04601_gb300 import synth
+
+    build.build()
+    w = synth.WORKLOADS[args.workload]
+    nsys = getattr(args, "n", None) or w["n"]
+    lo, hi = w["batched"]
+    t0 = time.time()
+    systems, forest, b = synth.make_batched(nsys, lo, hi, seed=synth.SEED_BASE + w["index"], leaf=w["leaf"],
+                                            tol=w["tol"], nrhs=w["nrhs"])
+    gen_s = time.time() - t0
+    ta = time.perf_counter()
+    an = H.h2sp_analyze(H.H2Input(forest, device=None))
+    analysis_ms = (time.perf_counter() - ta) * 1e3
+    stats = H.h2sp_query(an)
+    inp = H.H2Input(forest)
+    bt = torch.from_numpy(np.ascontiguousarray(b.T)).cuda()
+    xt = torch.empty_like(bt)
+    stream = torch.cuda.current_stream()
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    # the persistent handle: built once, then every step replays its graph
+    hd = H.h2sp_sparsify_analyzed(an, inp, flags=H.H2SP_SPARSIFY_FP32)
+    H.h2sp_factor(hd, H.H2SP_FP32)
+
+    def step():
+        H.h2sp_refactor(hd)
+        return H.h2sp_solve(hd, bt, xt, mode=H.H2SP_IR, tol=1e-10, maxit=30)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    before = sum(v["launches"] for v in H.h2sp_profile(hd, timing=-1, reset=True).values())
+    e0.record(stream)
+    infos = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    launches = sum(v["launches"] for v in H.h2sp_profile(hd, timing=-1).values())
+    del before
+    t_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, ws) / args.steps
+    res = max(float(i.rel_residual) for i in infos)
+    converged = all(i.status == H.H2SP_OK for i in infos) and res <= 1e-10
+    # phases of one step (outside the timed region)
+    m = [ev() for _ in range(3)]
+    m[0].record(stream)
+    H.h2sp_refactor(hd)
+    m[1].record(stream)
+    info = H.h2sp_solve(hd, bt, xt, mode=H.H2SP_IR, tol=1e-10, maxit=30)
+    m[2].record(stream)
+    torch.cuda.synchronize()
+    phase = {"refactor_graph_ms": m[0].elapsed_time(m[1]), "refine_ms": m[1].elapsed_time(m[2]),
+             "analysis_ms": analysis_ms, "refine_iters": int(info.iters)}
+    # every system on its own: residual with its own H^2 product (the library's FP64 product on the forest)
+    yt = torch.empty_like(xt)
+    H.h2sp_apply(hd, H.H2SP_OP_H2, xt, yt)
+    r = (bt - yt).cpu().numpy().T
+    bb = b
+    off = np.cumsum([0] + [s_.n for s_ in systems])
+    per_sys = [float(np.linalg.norm(r[off[k]:off[k + 1]]) / np.linalg.norm(bb[off[k]:off[k + 1]]))
+               for k in range(len(systems))]
+    hd.close()
+    # FP64 path: FP64 sparsification and block LU, refinement to 1e-10
+    fp64_s = None
+    if args.fp64_steps > 0:
+        f0, f1 = ev(), ev()
+        f0.record(stream)
+        hd64 = H.h2sp_sparsify_analyzed(an, inp)
+        H.h2sp_factor(hd64, H.H2SP_FP64)
+        i64 = H.h2sp_solve(hd64, bt, xt, mode=H.H2SP_IR, tol=1e-10, maxit=10)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fp64_s = f0.elapsed_time(f1) / 1e3 if (i64.status == H.H2SP_OK and i64.rel_residual <= 1e-10) else None
+        hd64.close()
+    # e2e: the whole path from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        names = ["leaf_basis", "transfer", "coupling", "near_block"]
+        pinned = {nm: torch.from_numpy(np.ascontiguousarray(getattr(forest, nm))).pin_memory() for nm in names}
+        hinp = H.H2Input(forest, device="host", host=pinned)
+        b_pin = torch.from_numpy(np.ascontiguousarray(b.T)).pin_memory()
+        x_pin = torch.empty_like(b_pin).pin_memory()
+        sh = torch.cuda.current_stream().cuda_stream
+
+        def e2e_step():
+            return H.h2sp_solve_host(an, hinp, b_pin.data_ptr(), forest.n, x_pin.data_ptr(), forest.n,
+                                     int(b.shape[1]), flags=H.H2SP_SPARSIFY_FP32, prec=H.H2SP_FP32, mode=H.H2SP_IR,
+                                     tol=1e-10, stream=sh)
+
+        e2e_step()
+        ks = max(1, min(args.steps, args.e2e_steps))
+        a0, a1 = ev(), ev()
+        a0.record(stream)
+        oks = [e2e_step() for _ in range(ks)]
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ok = all(i.status == H.H2SP_OK and i.rel_residual <= 1e-10 for i in oks)
+        e2e = {"value": (a0.elapsed_time(a1) / 1e3 / ks) if ok else None, "unit": "s",
+               "h2d_bytes_per_step": int(sum(t.numel() * 8 for t in pinned.values()) + b_pin.numel() * 8),
+               "d2h_bytes_per_step": int(x_pin.numel() * 8), "steps": ks, "entry": "h2sp_solve_host"}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_batched(systems, b)
+    return {
+        "metric": METRIC, "value": t_s if converged else None, "unit": "s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_s * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n": int(forest.n), "nsys": len(systems), "n_k_range": [lo, hi],
+                   "leaf": w["leaf"], "basis_tol": w["tol"], "kernel": "-log r", "points": "random ellipses (seeded)",
+                   "factor": "block LU", "form": "persistent: h2sp_refactor graph replay + refinement",
+                   "parallelism": "single GPU", "l2": "inputs larger than L2; no flush"},
+        "converged": converged, "rel_residual_max": res, "rel_residual_per_system_max": max(per_sys),
+        "iters": [int(i.iters) for i in infos], "fp64_direct_s": fp64_s,
+        "speedup_mixed_vs_fp64": (fp64_s / t_s) if (fp64_s and converged) else None,
+        "factor_flops": stats["factor_flops"], "phase_ms": phase, "input_gen_s": gen_s,
+        "structure": {"max_front": stats["max_front"], "nsupernodes": stats["nsupernodes"],
+                      "nfront_levels": stats["nfront_levels"]},
+        "e2e": e2e, "gpu_launches": int(launches), "gpu_launches_per_step": int(launches / max(args.steps, 1)),
+        "clocks": clk, "cpu_baseline": cpu, "roofline": None,
+    }
+
+
+def cpu_oracle_batched(systems, b, nsample=8):
+    """The oracle on every (nsys / nsample)-th system, scaled to all systems
+    by the oracle's own work counts (summed per phase)."""
+    import numpy as np
+    step = max(1, len(systems) // nsample)
+    idx = list(range(0, len(systems), step))[:nsample]
+    off = np.cumsum([0] + [s.n for s in systems])
+    ph = [0.0, 0.0, 0.0]
+    for k in idx:
+        _, p = _oracle_step(systems[k], b[off[k]:off[k + 1]], "lu")
+        ph = [a + c for a, c in zip(ph, p)]
+    wall = [_oracle_work(s, "lu") for s in systems]
+    ws_ = [wall[k] for k in idx]
+    ratios = [sum(w[i] for w in wall) / max(sum(w[i] for w in ws_), 1e-300) for i in range(3)]
+    return {"value": sum(t * r for t, r in zip(ph, ratios)), "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "oracle (FP64 sparsify + block LU + direct solve) on %d of the %d systems, phases %.2f / %.2f / "
+                      "%.2f s, scaled to all systems by the oracle's work counts x %.1f / %.1f / %.1f"
+                      % (len(idx), len(systems), ph[0], ph[1], ph[2], ratios[0], ratios[1], ratios[2])}
+
+
 def _oracle_step(h, b, kind):
     """The oracle's pipeline, phase by phase: sparsify, factor, solve (FP64)."""
     from oracle import factor as ofa
@@ -531,6 +697,23 @@ def run_reference(args, ws, rank):
 
     from paper_1705_04601_gb300 import synth
     kind = factor_kind(args)
+    w = synth.WORKLOADS[args.workload]
+    if "batched" in w:
+        # the sampled systems of the batched workload, each step scaled to all of them
+        nsys = getattr(args, "n", None) or w["n"]
+        lo_, hi_ = w["batched"]
+        systems, forest, b = synth.make_batched(nsys, lo_, hi_, seed=synth.SEED_BASE + w["index"], leaf=w["leaf"],
+                                                tol=w["tol"], nrhs=w["nrhs"])
+        for _ in range(args.warmup):
+            cpu_oracle_batched(systems, b)
+        vals = [cpu_oracle_batched(systems, b) for _ in range(args.steps)]
+        dt = sum(v["value"] for v in vals) / args.steps
+        return {"impl": "reference", "metric": METRIC, "value": dt, "unit": "s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "n": int(forest.n), "nsys": len(systems)},
+                "cpu_baseline": dict(vals[-1], value=dt),
+                "e2e": {"value": dt, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     h, b = synth.make_workload(args.workload, n=CPU_SAMPLE_N)
     h_full, _ = synth.make_workload(args.workload, n=getattr(args, "n", None))  # its structure only enters the scaling
     ratios = _work_ratios(h_full, h, kind)
@@ -568,7 +751,11 @@ def main():
             print(json.dumps(out))
         return
     ws, rank, local = dist_setup(args.gpus)
-    out = run_ours(args, ws, rank, local)
+    from paper_1705_04601_gb300 import synth
+    if "batched" in synth.WORKLOADS.get(args.workload, {}):
+        out = run_batched(args, ws, rank, local)
+    else:
+        out = run_ours(args, ws, rank, local)
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:

@@ -278,6 +278,25 @@ int h2sp_solve(h2sp_handle *h, const h2sp_solve_opts *opts, int32_t nrhs, const 
                double *x, int64_t ldx, h2sp_solve_info *info, h2sp_stream stream);
 
 /*
+ * h2sp_solve_captured -- iterative refinement with a fixed number of steps,
+ * captured in a CUDA graph: x_0 = M^-1 b, then `steps` times
+ * x += M^-1 (b - A x) with M^-1 = V S^-1 U^T from the current factors and A
+ * the FP64 H^2 product (§5.5), then the final residual; no host decision
+ * between the launches.  The first call for given (b, ldb, x, ldx, nrhs,
+ * steps) and factor precision captures every launch into a graph the handle
+ * owns; later calls with the same arguments replay it with one graph launch
+ * (new values in b, or new factors from h2sp_refactor, are picked up).  The
+ * sweeps' flags are zeroed at the start of every replay, so the epochs fixed
+ * at capture are new each time.  Needs h2sp_factor; device arrays as for
+ * h2sp_solve, 1 <= nrhs <= 64, 0 <= steps <= 100.  info (may be NULL) gets
+ * steps and the final max relative residual over systems and columns;
+ * returns H2SP_ENOCONV if that is above tol (x is still the last iterate),
+ * H2SP_ETIMEOUT if a sweep's wait gave up.  Synchronises the stream.
+ */
+int h2sp_solve_captured(h2sp_handle *h, int32_t steps, double tol, int32_t nrhs, const double *b, int64_t ldb,
+                        double *x, int64_t ldx, h2sp_solve_info *info, h2sp_stream stream);
+
+/*
  * h2sp_solve_host -- the whole path in one call, from and to HOST memory:
  * x = A^{-1} b with A = U S V^T built (§2.1-2.3, §4.2-4.3), S factored and
  * the system solved as h2sp_sparsify_analyzed + h2sp_factor + h2sp_solve do.

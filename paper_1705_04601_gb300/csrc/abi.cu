@@ -221,6 +221,13 @@ struct h2sp_handle {
   cudaGraphExec_t graph_exec = nullptr;  // sparsification + factorization, captured by h2sp_refactor
   cudaStream_t graph_stream = nullptr;    // the graph is captured and launched here (the caller's may be legacy)
   cudaEvent_t graph_in = nullptr, graph_out = nullptr;
+  // h2sp_solve_captured: its graph and the arguments it was captured for
+  cudaGraphExec_t solve_exec = nullptr;
+  const double *cap_b = nullptr;
+  double *cap_x = nullptr;
+  int64_t cap_ldb = 0, cap_ldx = 0;
+  int cap_nrhs = 0, cap_steps = -1, cap_prec = -1;
+  double *cap_norms = nullptr;  // ||b||^2 and ||b - A x||^2 per (system, right-hand side)
   // flag-synchronised triangular sweeps
   int2 *chain_items = nullptr;
   std::vector<int> chain_fwd_off, chain_fwd_n, chain_bwd_off, chain_bwd_n;
@@ -236,6 +243,8 @@ struct h2sp_handle {
   void release() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
     graph_exec = nullptr;
+    if (solve_exec) cudaGraphExecDestroy(solve_exec);
+    solve_exec = nullptr;
     if (graph_stream) cudaStreamSynchronize(graph_stream);
     if (graph_in) cudaEventDestroy(graph_in);
     if (graph_out) cudaEventDestroy(graph_out);
@@ -1666,6 +1675,101 @@ int h2sp_solve_host(const h2sp_handle *an, const h2sp_h2_desc *desc, const h2sp_
   cudaStreamSynchronize(s);
   if (own) h2sp_destroy(own);
   return st;
+}
+
+int h2sp_solve_captured(h2sp_handle *h, int32_t steps, double tol, int32_t nrhs, const double *b, int64_t ldb,
+                        double *x, int64_t ldx, h2sp_solve_info *info, h2sp_stream stream) {
+  if (!h || !b || !x || nrhs <= 0 || nrhs > 64 || steps < 0 || steps > 100) return H2SP_EINVAL;
+  if (!h->device_ready) return H2SP_ESTATE;
+  const Plan &p = (*h->plan_ptr);
+  if (ldb < p.n || ldx < p.n) return H2SP_EINVAL;
+  if (h->prec < 0) return H2SP_ESTATE;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->prof.stream = h->stream;
+  cudaStream_t s = h->stream;
+  const int64_t n = p.n;
+  const int ns = h->nseg;
+  bool capturing = false;
+  try {
+    // every buffer the captured launches use exists before the capture
+    ensure_vectors(h, nrhs);
+    ensure_work(h, nrhs);
+    if (h->prec == H2SP_FP32 && fp32_applies_enabled()) ensure_vectors_f32(h, nrhs);
+    if (h->cap_norms == nullptr) h->cap_norms = h->alloc<double>(size_t(2) * ns * 64);
+    if (h->graph_stream == nullptr) {
+      ck(cudaStreamCreateWithFlags(&h->graph_stream, cudaStreamNonBlocking));
+      ck(cudaEventCreateWithFlags(&h->graph_in, cudaEventDisableTiming));
+      ck(cudaEventCreateWithFlags(&h->graph_out, cudaEventDisableTiming));
+    }
+    const bool same = h->solve_exec && h->cap_b == b && h->cap_x == x && h->cap_ldb == ldb && h->cap_ldx == ldx &&
+                      h->cap_nrhs == nrhs && h->cap_steps == steps && h->cap_prec == h->prec;
+    if (!same && h->solve_exec) {
+      ck(cudaGraphExecDestroy(h->solve_exec));
+      h->solve_exec = nullptr;
+    }
+    cudaStream_t gs = h->graph_stream;
+    if (h->solve_exec == nullptr) {
+      ck(cudaStreamSynchronize(s));
+      const int timing = h->prof.timing;
+      h->prof.timing = 0;
+      h->stream = gs;
+      ck(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+      capturing = true;
+      // the sweeps' flags start from zero in every replay, so the epochs
+      // captured with the launches are new each time
+      if (h->chain_flags) ck(cudaMemsetAsync(h->chain_flags, 0, sizeof(int) * size_t(h->sdev->nflags), gs));
+      double *bn2 = h->cap_norms, *rn2 = h->cap_norms + size_t(ns) * 64;
+      ck(launch_colnorm2(b, ldb, h->seg_ptr, ns, n, nrhs, bn2, gs));
+      precond(h, b, ldb, x, ldx, nrhs);  // x_0 = M^-1 b
+      for (int k = 0; k < steps; ++k) {
+        h2_matvec(h, x, ldx, h->vecT, n, nrhs);
+        ck(launch_residual(b, ldb, h->vecT, n, h->vecR, n, h->seg_ptr, ns, n, nrhs, rn2, gs));
+        precond(h, h->vecR, n, h->vecT, n, nrhs);
+        ck(launch_axpy(h->vecT, n, x, ldx, n, nrhs, gs));
+      }
+      h2_matvec(h, x, ldx, h->vecT, n, nrhs);
+      ck(launch_residual(b, ldb, h->vecT, n, h->vecR, n, h->seg_ptr, ns, n, nrhs, rn2, gs));
+      cudaGraph_t g = nullptr;
+      capturing = false;
+      const cudaError_t ee = cudaStreamEndCapture(gs, &g);
+      h->stream = s;
+      h->prof.timing = timing;
+      ck(ee);
+      const cudaError_t ie = cudaGraphInstantiate(&h->solve_exec, g, 0);
+      cudaGraphDestroy(g);
+      ck(ie);
+      h->cap_b = b, h->cap_x = x, h->cap_ldb = ldb, h->cap_ldx = ldx;
+      h->cap_nrhs = nrhs, h->cap_steps = steps, h->cap_prec = h->prec;
+    }
+    ck(cudaEventRecord(h->graph_in, s));
+    ck(cudaStreamWaitEvent(gs, h->graph_in, 0));
+    ck(cudaGraphLaunch(h->solve_exec, gs));
+    ck(cudaEventRecord(h->graph_out, gs));
+    ck(cudaStreamWaitEvent(s, h->graph_out, 0));
+    std::vector<double> nb(size_t(ns) * nrhs), nr(size_t(ns) * nrhs);
+    ck(cudaMemcpyAsync(nb.data(), h->cap_norms, sizeof(double) * nb.size(), cudaMemcpyDeviceToHost, s));
+    ck(cudaMemcpyAsync(nr.data(), h->cap_norms + size_t(ns) * 64, sizeof(double) * nr.size(), cudaMemcpyDeviceToHost,
+                       s));
+    ck(cudaStreamSynchronize(s));
+    double res = 0.0;  // worst system, worst column
+    for (size_t q = 0; q < nr.size(); ++q) res = std::max(res, std::sqrt(nr[q] / std::max(nb[q], 1e-300)));
+    const int ss = sweep_status(h);
+    const int st = ss != H2SP_OK ? ss : (res <= tol ? H2SP_OK : H2SP_ENOCONV);
+    if (info) {
+      info->iters = steps;
+      info->rel_residual = res;
+      info->status = st;
+    }
+    return st;
+  } catch (const CudaFail &f) {
+    if (capturing) {
+      cudaGraph_t g = nullptr;
+      if (cudaStreamEndCapture(h->graph_stream, &g) == cudaSuccess && g) cudaGraphDestroy(g);
+      cudaGetLastError();
+    }
+    h->stream = s;
+    return status_of(f.e);
+  }
 }
 
 int h2sp_export_S(h2sp_handle *h, int64_t *node_size, int64_t *brow_ptr, int32_t *bcol_idx, int64_t *val_off,

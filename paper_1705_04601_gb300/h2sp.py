@@ -94,6 +94,8 @@ SIGNATURES = {
     "h2sp_export_front": (ctypes.c_int, [_vp, ctypes.c_int32, _i64p, _i64p, _f64p, _vp]),
     "h2sp_measure_peak": (ctypes.c_int, [ctypes.c_int32, _f64p, _vp]),
     "h2sp_set_option": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int64]),
+    "h2sp_solve_captured": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _vp, ctypes.c_int64,
+                                           _vp, ctypes.c_int64, ctypes.c_void_p, _vp]),
     "h2sp_solve_host": (ctypes.c_int, [_vp, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_int32, _vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_void_p,
                                        _vp]),
@@ -331,6 +333,20 @@ def h2sp_measure_peak(kind: int, stream=None) -> float:
     v = ctypes.c_double(0.0)
     _check(lib().h2sp_measure_peak(int(kind), ctypes.byref(v), _stream(stream)), "h2sp_measure_peak")
     return float(v.value)
+
+
+def h2sp_solve_captured(h: Handle, b, x, steps: int, tol: float = 1e-10, stream=None) -> SolveInfo:
+    """Fixed-step refinement replayed from a CUDA graph (captured on the first call)."""
+    n = int(h.inp.h.n)
+    nrhs, ldb = _cols(b, n)
+    _, ldx = _cols(x, n)
+    info = SolveInfo()
+    st = lib().h2sp_solve_captured(h.ptr, int(steps), float(tol), nrhs, _vp(b.data_ptr()), ldb, _vp(x.data_ptr()), ldx,
+                                   ctypes.byref(info), _stream(stream))
+    if st not in (H2SP_OK, H2SP_ENOCONV):
+        _check(st, "h2sp_solve_captured")
+    info.status = st
+    return info
 
 
 def h2sp_logdet(h: Handle, stream=None):

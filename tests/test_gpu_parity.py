@@ -614,3 +614,93 @@ def test_batched_ellipses_fp32_refinement_and_graph_replay():
             assert r.max() <= 2e-10, (scale, o, r.max())
             o += s.n
     hd.close()
+
+
+def test_batched_256_systems_persistent_form():
+    """256 independent ellipse systems (N_k in [256, 1024]) in one forest: the
+    persistent form (h2sp_refactor graph replay + FP64 refinement) brings every
+    system to 1e-10 on its own oracle H^2 product, and the FP64 direct solve of
+    sampled systems equals their oracle's."""
+    systems, f, b = synth.make_batched(256, 256, 1024, leaf=64, tol=1e-6, nrhs=1)
+    inp = H.H2Input(f)
+    an = H.h2sp_analyze(H.H2Input(f, device=None))
+    assert H.h2sp_query(an)["nsys"] == 256
+    hd = H.h2sp_sparsify_analyzed(an, inp, flags=H.H2SP_SPARSIFY_FP32)
+    H.h2sp_factor(hd, H.H2SP_FP32)
+    bt = dev(b)
+    xt = torch.empty_like(bt)
+    for rep in range(2):
+        if rep:
+            H.h2sp_refactor(hd)
+        info = H.h2sp_solve(hd, bt, xt, mode=H.H2SP_IR, tol=1e-10, maxit=30)
+        assert info.status == H.H2SP_OK and info.rel_residual <= 1e-10
+    torch.cuda.synchronize()
+    xg = host(xt)
+    o = 0
+    for s in systems:
+        bs = b[o:o + s.n]
+        r = np.linalg.norm(bs - oh2.Matvec(s)(xg[o:o + s.n])) / np.linalg.norm(bs)
+        assert r <= 2e-10, (o, r)
+        o += s.n
+    # the captured refinement (one graph launch per call) after another refactorization
+    H.h2sp_refactor(hd)
+    xc = torch.empty_like(bt)
+    for _ in range(2):
+        info = H.h2sp_solve_captured(hd, bt, xc, steps=8)
+        assert info.status == H.H2SP_OK and info.rel_residual <= 1e-10
+    torch.cuda.synchronize()
+    xg = host(xc)
+    o = 0
+    for s in systems:
+        bs = b[o:o + s.n]
+        assert np.linalg.norm(bs - oh2.Matvec(s)(xg[o:o + s.n])) <= 2e-10 * np.linalg.norm(bs)
+        o += s.n
+    hd.close()
+    hd64 = H.h2sp_sparsify_analyzed(an, inp)
+    H.h2sp_factor(hd64, H.H2SP_FP64)
+    H.h2sp_solve(hd64, bt, xt, mode=H.H2SP_DIRECT)
+    torch.cuda.synchronize()
+    xg = host(xt)
+    offs = np.cumsum([0] + [s.n for s in systems])
+    for k in (0, 77, 255):
+        s = systems[k]
+        sp = osp.sparsify(s)
+        xo = ofa.solve(s, sp, ofa.factor(s, sp), b[offs[k]:offs[k + 1]])
+        assert np.linalg.norm(xg[offs[k]:offs[k + 1]] - xo) <= TOL * np.linalg.norm(xo)
+    hd64.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_captured_refinement_replays_with_new_right_hand_sides(prec):
+    """h2sp_solve_captured: the fixed-step refinement captured once and
+    replayed; a new b written into the same buffer is solved by the replay
+    (the sweeps' flags are reset inside the graph), and after a refactor with
+    doubled numbers the replay uses the new factors."""
+    h, b, sp, hd = sparsified("log4k")
+    H.h2sp_factor(hd, H.H2SP_FP64 if prec == "fp64" else H.H2SP_FP32)
+    A = oh2.dense(h)
+    bt = dev(b)
+    xt = torch.empty_like(bt)
+    steps = 1 if prec == "fp64" else 8
+    for rep in range(3):
+        if rep:
+            bt.copy_(dev(np.random.default_rng(50 + rep).standard_normal(b.shape)))
+        info = H.h2sp_solve_captured(hd, bt, xt, steps=steps)
+        assert info.status == H.H2SP_OK and info.rel_residual <= 1e-10, (rep, info.rel_residual)
+        torch.cuda.synchronize()
+        bh = host(bt)
+        r = np.linalg.norm(bh - A @ host(xt), axis=0) / np.linalg.norm(bh, axis=0)
+        assert r.max() <= 2e-10
+    # the same numbers doubled, refactored: the replay solves 2A x = b
+    inp = hd.inp
+    inp.dev["near_block"].mul_(2.0)
+    inp.dev["coupling"].mul_(2.0)
+    H.h2sp_refactor(hd)
+    info = H.h2sp_solve_captured(hd, bt, xt, steps=steps)
+    assert info.status == H.H2SP_OK and info.rel_residual <= 1e-10
+    torch.cuda.synchronize()
+    bh = host(bt)
+    assert np.linalg.norm(bh - 2.0 * A @ host(xt)) <= 2e-10 * np.linalg.norm(bh) * np.sqrt(b.shape[1])
+    inp.dev["near_block"].mul_(0.5)
+    inp.dev["coupling"].mul_(0.5)
+    hd.close()
