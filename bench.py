@@ -86,6 +86,8 @@ def parse(argv=None):
                     help="block Cholesky (SPD S) or block LU; auto: Cholesky on the SPD workloads")
     ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 path steps timed (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--bf16-steps", type=int, default=2,
+                    help="steps of the mixed path with BF16 block-end updates (reported beside the headline; 0: skip)")
     ap.add_argument("--sparsify-prec", default="fp32", choices=["fp32", "fp64"],
                     help="precision of the products into S on the mixed path (the FP64 path is FP64 throughout)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -354,6 +356,44 @@ def run_ours(args, ws, rank, local):
     converged = all(st == H.H2SP_OK for (_, _, st) in infos) and res_mixed <= 1e-10
     x_mixed = xt.clone()
 
+    # ---- the same mixed step with the block-end updates on BF16 tensor cores
+    # (per-tile power-of-two scaling, FP32 accumulation; one BF16 term, or a
+    # hi + lo split with three products): reported variants ----
+    bf16_variants = {}
+    bf16_kinds = [("mixed_bf16", "H2SP_BF16_CHOL", "one BF16 term"),
+                  ("mixed_bf16x3", "H2SP_BF16X3_CHOL", "BF16 hi + lo split, three BF16 products")]
+    for key, precname, what in bf16_kinds:
+        if kind != "chol" or getattr(args, "bf16_steps", 2) <= 0:
+            bf16_variants[key] = None
+            continue
+        try:
+            def bf16_step(prec=getattr(H, precname)):
+                hd = H.h2sp_sparsify_analyzed(an, inp, flags=sp_flags)
+                if sched:
+                    from paper_1705_04601_gb300 import tune as T
+                    T.apply(hd, sched)
+                H.h2sp_factor(hd, prec)
+                info = H.h2sp_solve(hd, bt, xt, mode=mode, tol=1e-10, maxit=100, restart=30)
+                info.compensated = int(H.h2sp_query(hd)["compensated_pivots"])
+                hd.close()
+                return info
+            bf16_step()
+            torch.cuda.synchronize()
+            b0, b1 = ev(), ev()
+            b0.record(stream)
+            binfos = [bf16_step() for _ in range(args.bf16_steps)]
+            b1.record(stream)
+            torch.cuda.synchronize()
+            ok = all(i.status == H.H2SP_OK and i.rel_residual <= 1e-10 for i in binfos)
+            bf16_variants[key] = {
+                "value": (b0.elapsed_time(b1) / 1e3 / args.bf16_steps) if ok else None, "unit": "s",
+                "iters": [int(i.iters) for i in binfos], "rel_residual": max(float(i.rel_residual) for i in binfos),
+                "compensated_pivots": max(i.compensated for i in binfos),
+                "factor": "block Cholesky, block-end updates on BF16 tensor cores (%s) with a power-of-two scale "
+                          "per 128-row tile of L21, FP32 accumulation" % what}
+        except H.H2spError as e:
+            bf16_variants[key] = {"value": None, "error": str(e)}
+
     # ---- one profiled mixed step: per-class event times, phases ----
     marks = [ev() for _ in range(4)]
     hd, _ = mixed_step(profile=True, marks=marks)
@@ -443,7 +483,7 @@ def run_ours(args, ws, rank, local):
         "structure": {"max_front": stats["max_front"], "nsupernodes": stats["nsupernodes"],
                       "nnz_S": stats["nnz"], "front_elems": stats["front_elems"]},
         "fma_peaks_tflops": fma, "roofline": roof, "e2e": e2e,
-        "schedule": sched, "schedule_source": sched_src, "tune_s": tune_s,
+        "schedule": sched, "schedule_source": sched_src, "tune_s": tune_s, "mixed_bf16": bf16_variants["mixed_bf16"], "mixed_bf16x3": bf16_variants["mixed_bf16x3"],
         "gpu_launches": int(launches), "gpu_launches_per_step": int(launches / max(args.steps, 1)),
         "kernel_ms_per_step": {c: v["ms"] for c, v in prof.items() if v["ms"] > 0},
         "kernel_work_per_step": {c: v["work"] for c, v in prof.items() if v["ms"] > 0},

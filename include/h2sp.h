@@ -56,12 +56,19 @@ typedef enum {
 } h2sp_status;
 
 /* Precision and kind of the factorization of S (h2sp_factor).  Bit 0: FP32
- * fronts; bit 1: block Cholesky S = L L^T instead of the block LU. */
+ * fronts; bit 1: block Cholesky S = L L^T instead of the block LU; bit 2: BF16
+ * block-end updates; bit 3: their two-term split. */
 typedef enum {
   H2SP_FP64 = 0,      /* block LU, FP64 fronts, FP64 arithmetic */
   H2SP_FP32 = 1,      /* block LU, FP32 fronts, FP32 arithmetic (a preconditioner for FP64 IR/GMRES) */
   H2SP_FP64_CHOL = 2, /* block Cholesky of a symmetric positive definite S, FP64 */
-  H2SP_FP32_CHOL = 3  /* block Cholesky of a symmetric positive definite S, FP32 (tensor-core updates) */
+  H2SP_FP32_CHOL = 3, /* block Cholesky of a symmetric positive definite S, FP32 (tensor-core updates) */
+  H2SP_BF16_CHOL = 7, /* H2SP_FP32_CHOL with the block-end updates in BF16: each 128-row tile of L21 scaled by
+                         a power of two (its largest entry's exponent) and rounded to BF16, products accumulated
+                         in FP32 and rescaled; a preconditioner for FP64 GMRES / refinement */
+  H2SP_BF16X3_CHOL = 15 /* as H2SP_BF16_CHOL, with each scaled entry split into two BF16 values, x = hi + lo
+                           (lo = the rounding error of hi, rounded), and three BF16 products per update:
+                           hi*hi + hi*lo + lo*hi (about 16 significant bits) */
 } h2sp_prec;
 
 /* Operators for h2sp_apply. */
@@ -174,6 +181,8 @@ typedef struct {
   int32_t nsys;                   /* independent systems (roots at depth 0) */
   int32_t factor_chol;            /* 1 if the current factors come from the block Cholesky */
   double chol_flops;              /* sum over supernodes of s^3/3 + s^2 b + s b^2 (the block Cholesky's work) */
+  int32_t compensated_pivots;     /* pivots of the last BF16-mode block Cholesky that were not positive and were
+                                     replaced by their diagonal entry before the panel (0 otherwise) */
 } h2sp_stats;
 
 /*
@@ -242,7 +251,15 @@ int h2sp_analyze(const h2sp_h2_desc *desc, h2sp_handle **out);
  * the LU.  Needs symmetric bases (no column bases; H2SP_EINVAL otherwise) and
  * a symmetric S; a pivot that is not positive (S not positive definite in the
  * factor's precision) returns H2SP_ESINGULAR with a message in
- * h2sp_last_cuda_error.
+ * h2sp_last_cuda_error.  H2SP_BF16_CHOL / H2SP_BF16X3_CHOL are H2SP_FP32_CHOL
+ * with the rank-256 block-end updates on BF16 tensor cores (one power-of-two
+ * scale per 128-row tile of L21); they need the tensor-core path
+ * (H2SP_EUNSUPPORTED otherwise).  One BF16 term keeps 8 significant bits; the
+ * two-term split about 16, at half the tensor work of the TF32 split.  Their
+ * factors are a preconditioner only: a pivot that comes out not positive is
+ * replaced by the diagonal entry as the panel found it (the pivot before the
+ * panel's own sums: diagonal compensation) and counted in
+ * h2sp_stats.compensated_pivots, instead of failing the call.
  *
  * Synchronises the stream; returns H2SP_ESINGULAR on a zero or non-finite
  * pivot and H2SP_ETIMEOUT if a bounded device wait gave up.
@@ -371,6 +388,36 @@ int h2sp_export_Q(h2sp_handle *h, int32_t cluster, int32_t col, int64_t *m, doub
  */
 int h2sp_export_structure(h2sp_handle *h, int32_t *node_level, int32_t *node_cluster, int32_t *closure,
                           int32_t *order, int32_t *sn_ptr, int32_t *bnd_ptr, int32_t *bnd, int64_t *nbnd);
+
+/*
+ * h2sp_export_schedule -- the level schedule of §2.2-2.3 as the device
+ * kernels build it: runs them now, on the current device, for the structure
+ * of h (an analysis or a numeric handle), and copies the result to host
+ * arrays (any pointer may be NULL).  Per cluster (ncl = level_ptr[depth + 1]
+ * entries): m (local block size m_t: |t| at the leaves, the sum of the
+ * children's k' above), kp (basis part k'_t = min(k_t, m_t) below l_stop, 0 at
+ * l_stop; d_t = m_t - k'_t rows of t enter S), off (row of t's basis part in
+ * its parent's block), xoff (offset of X_l(t) in the level-l vector; 0 above
+ * l_stop).  Per S node (nnodes + 1 entries, h2sp_query): node_off (first row
+ * of the node in S, node_off[nnodes] = n); node_cluster (nnodes entries).
+ * *lstop: l_stop, the level whose clusters are kept whole (one above the
+ * highest level with an admissible pair).  Synchronous.  The same kernels
+ * build the plan of h2sp_sparsify and the level maps of every numeric
+ * handle; this entry exposes them for verification.
+ */
+int h2sp_export_schedule(h2sp_handle *h, int32_t *lstop, int64_t *m, int64_t *kp, int64_t *off, int64_t *xoff,
+                         int64_t *node_off, int32_t *node_cluster);
+
+/*
+ * h2sp_export_near -- the close list Near_level (1 <= level <= l_stop) of the
+ * device level schedule: Near_{l+1} = {(par a, par b) : (a, b) in Near_l or
+ * Far_l}, each pair once (§2.3: the admissible pairs of level l join their
+ * parents' close blocks).  CSR over the clusters of the level in tree order:
+ * ptr (clusters of the level + 1 entries), col (*nnz cluster indices,
+ * ascending within a row).  Query *nnz first with col == NULL.  H2SP_EINVAL
+ * for a level outside [1, l_stop].  Synchronous.
+ */
+int h2sp_export_near(h2sp_handle *h, int32_t level, int64_t *ptr, int32_t *col, int64_t *nnz);
 
 /*
  * h2sp_export_front -- copy the front of supernode k (0 <= k < nsupernodes, in

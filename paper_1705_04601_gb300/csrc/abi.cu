@@ -161,6 +161,7 @@ struct h2sp_handle {
   int32_t *piv = nullptr, *perm = nullptr, *swaps = nullptr, *fidx = nullptr, *fmap = nullptr;
   AItem *asm_items = nullptr;
   int *err = nullptr;
+  int compensated = 0;  // pivots the last factorization compensated (BF16 block-end modes)
   std::vector<FrontLevel> flev;
   int max_s_all = 0;
   int64_t *work_off = nullptr;
@@ -787,8 +788,23 @@ std::shared_ptr<StructureDev> build_structure(const Plan &p) {
       width = std::max(width, wl);
     }
     sd->max_width = width;
-    for (int l = 0; l < L; ++l) {
-      std::vector<ApItem> ap;
+    // the level maps come from the device level schedule, which must agree
+    // with the plan (the host's, or the same device schedule's) to the integer
+    DeviceMaps maps;
+    A1Result a1;
+    std::string err;
+    const int st = device_schedule(p, &a1, &maps, err);
+    for (void *q : maps.allocs) sd->allocs.push_back(q);
+    if (st != H2SP_OK) {
+      g_cuda_err = err;
+      throw CudaFail{st == H2SP_ENOMEM ? cudaErrorMemoryAllocation : cudaErrorUnknown};
+    }
+    bool same = a1.lstop == L && a1.m == p.m && a1.kp == p.kp && a1.d == p.d && a1.off == p.off &&
+                a1.xoff == p.xoff && a1.node_of == p.node_of && a1.node_off == p.node_off &&
+                a1.node_cluster == p.node_cluster && a1.node_level == p.node_level && int(maps.nap.size()) == L;
+    for (int l = 0; same && l < L; ++l) {
+      // the apply items the plan implies, against the device's
+      std::vector<ApItem> want, got(size_t(maps.nap[l]));
       for (int t = p.level_ptr[p.D - l]; t < p.level_ptr[p.D - l + 1]; ++t) {
         if (p.m[t] == 0) continue;
         ApItem a{};
@@ -798,29 +814,51 @@ std::shared_ptr<StructureDev> build_structure(const Plan &p) {
         a.xin = p.xoff[t];
         a.yout = p.d[t] > 0 ? p.node_off[p.node_of[t]] : -1;
         a.xout = p.kp[t] > 0 ? p.xoff[p.parent[t]] + p.off[t] : -1;
-        ap.push_back(a);
+        want.push_back(a);
       }
-      sd->lv[l].ap = sd->upload(ap);
-      sd->lv[l].nap = int(ap.size());
+      same = want.size() == got.size();
+      if (same && !got.empty())
+        ck(cudaMemcpy(got.data(), maps.ap + maps.ap_base[l], got.size() * sizeof(ApItem), cudaMemcpyDeviceToHost));
+      for (size_t i = 0; same && i < got.size(); ++i)
+        same = got[i].q == want[i].q && got[i].m == want[i].m && got[i].kp == want[i].kp &&
+               got[i].xin == want[i].xin && got[i].yout == want[i].yout && got[i].xout == want[i].xout;
+      sd->lv[l].ap = maps.ap + maps.ap_base[l];
+      sd->lv[l].nap = maps.nap[l];
     }
-    std::vector<int64_t> ts, td;
-    std::vector<int32_t> tl;
-    for (int t = p.level_ptr[p.D - L]; t < p.level_ptr[p.D - L + 1]; ++t)
-      if (p.m[t] > 0) {
-        ts.push_back(L == 0 ? p.h_begin[t] : p.xoff[t]);
-        td.push_back(p.node_off[p.node_of[t]]);
-        tl.push_back(int32_t(p.m[t]));
+    if (same) {
+      // the top clusters' copies
+      std::vector<int64_t> ts, td;
+      std::vector<int32_t> tl;
+      for (int t = p.level_ptr[p.D - L]; t < p.level_ptr[p.D - L + 1]; ++t)
+        if (p.m[t] > 0) {
+          ts.push_back(L == 0 ? p.h_begin[t] : p.xoff[t]);
+          td.push_back(p.node_off[p.node_of[t]]);
+          tl.push_back(int32_t(p.m[t]));
+        }
+      same = int(ts.size()) == maps.ntop;
+      if (same && !ts.empty()) {
+        std::vector<int64_t> gs(ts.size()), gd(ts.size());
+        std::vector<int32_t> gl(ts.size());
+        ck(cudaMemcpy(gs.data(), maps.top_src, gs.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        ck(cudaMemcpy(gd.data(), maps.top_dst, gd.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        ck(cudaMemcpy(gl.data(), maps.top_len, gl.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        same = gs == ts && gd == td && gl == tl;
       }
-    sd->top_src = sd->upload(ts);
-    sd->top_dst = sd->upload(td);
-    sd->top_len = sd->upload(tl);
-    sd->ntop = int(ts.size());
+    }
+    if (!same) {
+      g_cuda_err = "internal: the device level schedule differs from the plan";
+      throw CudaFail{cudaErrorUnknown};
+    }
+    sd->top_src = maps.top_src;
+    sd->top_dst = maps.top_dst;
+    sd->top_len = maps.top_len;
+    sd->ntop = maps.ntop;
+    sd->node_off = maps.node_off;
   }
   // S structure, H^2 structure
   sd->brow_ptr = sd->upload(p.brow_ptr);
   sd->bcol = sd->upload(p.bcol);
   sd->val_off = sd->upload(p.val_off);
-  sd->node_off = sd->upload(p.node_off);
   {
     H2Dev &g = sd->h2;
     g.begin = sd->upload(p.h_begin);
@@ -1160,9 +1198,15 @@ void copy_out(h2sp_handle *h, double *dst, const void *src, int64_t n) {
 }
 
 // ---- factorization, in three parts: buffers (first call), launches, check ----
-// `prec` is an h2sp_prec: bit 0 selects FP32 fronts, bit 1 the block Cholesky.
+// `prec` is an h2sp_prec: bit 0 selects FP32 fronts, bit 1 the block Cholesky,
+// bit 2 BF16 block-end updates, bit 3 their two-term (hi + lo) split.
 inline bool prec_fp32(int32_t prec) { return (prec & 1) != 0; }
 inline bool prec_chol(int32_t prec) { return (prec & 2) != 0; }
+// the BF16 mode of the block-end updates: 0 none, 1 BF16, 2 BF16 hi + lo
+inline int prec_bf16(int32_t prec) { return (prec & 4) ? ((prec & 8) ? 2 : 1) : 0; }
+inline bool prec_valid(int32_t prec) {
+  return (prec >= H2SP_FP64 && prec <= H2SP_FP32_CHOL) || prec == H2SP_BF16_CHOL || prec == H2SP_BF16X3_CHOL;
+}
 
 void factor_prepare(h2sp_handle *h, int32_t prec) {
   const Plan &p = (*h->plan_ptr);
@@ -1182,7 +1226,7 @@ void factor_prepare(h2sp_handle *h, int32_t prec) {
     size_t maxn = 1;
     for (const FrontLevel &L : h->flev) maxn = std::max<size_t>(maxn, size_t(L.hi - L.lo));
     h->swaps = h->alloc<int32_t>(8 * maxn * (1 + 2 * kMaxSwapRows));  // two outer blocks of panels in flight
-    h->err = h->alloc<int>(1);
+    h->err = h->alloc<int>(2);  // error bits, pivots compensated
     h->dinv = h->alloc<double>(size_t(std::max<int64_t>(p.dinv_elems, 1)));
   }
   if (prec_chol(prec) && h->chol_inv == nullptr) {
@@ -1221,12 +1265,12 @@ void factor_prepare(h2sp_handle *h, int32_t prec) {
 }
 
 template <typename T>
-void factor_launch_t(h2sp_handle *h, bool chol) {
+void factor_launch_t(h2sp_handle *h, bool chol, int bf16) {
   const Plan &p = (*h->plan_ptr);
   cudaStream_t s = h->stream;
   const LuAsync *la = h->la.side ? &h->la : nullptr;
   ck(cudaMemsetAsync(h->fronts, 0, size_t(std::max<int64_t>(p.front_elems, 1)) * sizeof(T), s));
-  ck(cudaMemsetAsync(h->err, 0, sizeof(int), s));
+  ck(cudaMemsetAsync(h->err, 0, 2 * sizeof(int), s));
   const int64_t na = int64_t(p.assemble.size());
   const double abytes = double(p.s_elems) * double((h->sp_prec == H2SP_FP32 ? sizeof(float) : sizeof(double)) + sizeof(T));
   T *F = static_cast<T *>(h->fronts);
@@ -1241,7 +1285,7 @@ void factor_launch_t(h2sp_handle *h, bool chol) {
     if (chol) {
       ck(launch_chol_level<T>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv, h->err,
                               s, la, &h->prof, maps, h->pack, reinterpret_cast<T *>(h->chol_inv), &h->chol_sched,
-                              maps64));
+                              maps64, bf16));
     } else {
       ck(launch_lu_level<T>(h->fr + L.lo, p.fronts.data() + L.lo, L.hi - L.lo, L.max_s, L.max_f, F, h->piv, h->swaps,
                             h->err, s, la, &h->prof, maps, fp32 ? h->pack : nullptr, maps64));
@@ -1263,16 +1307,18 @@ void factor_launch_t(h2sp_handle *h, bool chol) {
 // every launch of the factorization (no allocation, no host synchronisation)
 void factor_launch(h2sp_handle *h, int32_t prec) {
   if (prec_fp32(prec))
-    factor_launch_t<float>(h, prec_chol(prec));
+    factor_launch_t<float>(h, prec_chol(prec), prec_bf16(prec));
   else
-    factor_launch_t<double>(h, prec_chol(prec));
+    factor_launch_t<double>(h, prec_chol(prec), 0);
 }
 
 // the factorization's error word, after the stream has drained
 int factor_finish(h2sp_handle *h, int32_t prec) {
-  int herr = 0;
-  ck(cudaMemcpyAsync(&herr, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  int herr2[2] = {0, 0};
+  ck(cudaMemcpyAsync(herr2, h->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   ck(cudaStreamSynchronize(h->stream));
+  const int herr = herr2[0] & ~16;
+  h->compensated = (herr2[0] & 16) ? herr2[1] : 0;
   if (herr & 4) return H2SP_ETIMEOUT;
   if (herr & 8) {
     g_cuda_err = "h2sp_factor: a pivot of the block Cholesky is not positive: S is not positive definite "
@@ -1363,7 +1409,9 @@ int h2sp_sparsify(const h2sp_h2_desc *desc, const h2sp_opts *opts, h2sp_stream s
   std::string err;
   auto t0 = std::chrono::steady_clock::now();
   auto plan = std::make_shared<Plan>();
-  int st = build_plan(desc, *plan, err);
+  // the level schedule on the device, from the validated structure
+  const A1Source dev_a1 = [](const Plan &p, A1Result &r, std::string &e) { return device_schedule(p, &r, nullptr, e); };
+  int st = build_plan(desc, *plan, err, true, &dev_a1);
   h->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (st != H2SP_OK) {
     g_cuda_err = err;
@@ -1419,7 +1467,11 @@ int h2sp_analyze(const h2sp_h2_desc *desc, h2sp_handle **out) {
 int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
   if (!h) return H2SP_EINVAL;
   if (!h->device_ready) return H2SP_ESTATE;
-  if (prec < H2SP_FP64 || prec > H2SP_FP32_CHOL) return H2SP_EINVAL;
+  if (!prec_valid(prec)) return H2SP_EINVAL;
+  if (prec_bf16(prec) && (!tma_enabled() || !use_tensor_core_gemm_host())) {
+    g_cuda_err = "h2sp_factor: the BF16 block-end updates need the tensor-core path";
+    return H2SP_EUNSUPPORTED;
+  }
   if (prec_chol(prec) && (h->col_leaf_basis != nullptr || h->col_transfer != nullptr)) {
     g_cuda_err = "h2sp_factor: the block Cholesky needs symmetric bases (V = U)";
     return H2SP_EINVAL;
@@ -1877,6 +1929,46 @@ int h2sp_export_structure(h2sp_handle *h, int32_t *node_level, int32_t *node_clu
   return H2SP_OK;
 }
 
+int h2sp_export_schedule(h2sp_handle *h, int32_t *lstop, int64_t *m, int64_t *kp, int64_t *off, int64_t *xoff,
+                         int64_t *node_off, int32_t *node_cluster) {
+  if (!h || !h->plan_ptr) return H2SP_EINVAL;
+  const Plan &p = (*h->plan_ptr);
+  A1Result r;
+  std::string err;
+  const int st = device_schedule(p, &r, nullptr, err);
+  if (st != H2SP_OK) {
+    g_cuda_err = err;
+    return st;
+  }
+  if (lstop) *lstop = r.lstop;
+  if (m) std::copy(r.m.begin(), r.m.end(), m);
+  if (kp) std::copy(r.kp.begin(), r.kp.end(), kp);
+  if (off) std::copy(r.off.begin(), r.off.end(), off);
+  if (xoff) std::copy(r.xoff.begin(), r.xoff.end(), xoff);
+  if (node_off) std::copy(r.node_off.begin(), r.node_off.end(), node_off);
+  if (node_cluster) std::copy(r.node_cluster.begin(), r.node_cluster.end(), node_cluster);
+  return H2SP_OK;
+}
+
+int h2sp_export_near(h2sp_handle *h, int32_t level, int64_t *ptr, int32_t *col, int64_t *nnz) {
+  if (!h || !h->plan_ptr) return H2SP_EINVAL;
+  const Plan &p = (*h->plan_ptr);
+  A1Result r;
+  std::string err;
+  const int st = device_schedule(p, &r, nullptr, err);
+  if (st != H2SP_OK) {
+    g_cuda_err = err;
+    return st;
+  }
+  if (level < 1 || level > r.lstop) return H2SP_EINVAL;
+  const auto &P = r.near_ptr[size_t(level)];
+  const auto &C = r.near_col[size_t(level)];
+  if (nnz) *nnz = int64_t(C.size());
+  if (ptr) std::copy(P.begin(), P.end(), ptr);
+  if (col) std::copy(C.begin(), C.end(), col);
+  return H2SP_OK;
+}
+
 int h2sp_export_front(h2sp_handle *h, int32_t k, int64_t *f, int64_t *sz, double *vals, h2sp_stream stream) {
   if (!h) return H2SP_EINVAL;
   const Plan &p = (*h->plan_ptr);
@@ -1962,6 +2054,7 @@ int h2sp_query(const h2sp_handle *h, h2sp_stats *st) {
   st->factor_prec = h->prec;
   st->factor_chol = h->prec >= 0 && h->chol ? 1 : 0;
   st->chol_flops = p.chol_flops;
+  st->compensated_pivots = h->prec >= 0 ? h->compensated : 0;
   st->sparsify_prec = h->device_ready ? h->sp_prec : -1;
   st->plan_seconds = h->plan_seconds;
   st->nsys = p.level_ptr[1];

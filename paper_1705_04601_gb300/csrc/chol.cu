@@ -43,7 +43,11 @@ inline int cdiv_c(int64_t a, int64_t b) { return int((a + b - 1) / b); }
 //   (lanes of one warp, added by shuffles); l_jj = sqrt(a_jj - ...) and
 //   l_rj = (a_rj - ...) / l_jj.  A pivot that is not positive and finite sets
 //   bit 8 of *err (S is not positive definite in this precision) and is
-//   replaced by 1 so that the factorization stays finite.
+//   replaced by 1 so that the factorization stays finite.  With `compensate`
+//   (the BF16 block-end modes, whose factors serve as a preconditioner only)
+//   it is replaced by a_jj as the tile holds it before this panel's sums
+//   (diagonal compensation: the pivot of the updates received so far, which
+//   an SPD S keeps positive), and counted in err[1] under bit 16.
 //   Inverse, forward substitution by columns: the four threads of column c
 //   (lanes of one warp) split y_r = -(sum_{c<=m<r} l_rm y_m) / l_rr, with
 //   y_c = 1 / l_cc, row by row; it goes to inv[front][r * NB + c]
@@ -52,7 +56,8 @@ constexpr int kDiagThreads = 256;
 template <typename T, int NB>
 __global__ void __launch_bounds__(kDiagThreads) k_chol_diag(const FrontDev *__restrict__ fr, int j0,
                                                             T *__restrict__ fronts, int32_t *__restrict__ piv,
-                                                            int *__restrict__ err, T *__restrict__ inv) {
+                                                            int *__restrict__ err, T *__restrict__ inv,
+                                                            int compensate) {
   static_assert(NB * 4 <= kDiagThreads, "four threads per row");
   const FrontDev F = fr[blockIdx.x];
   if (j0 >= F.s) return;  // uniform over the CTA
@@ -76,10 +81,17 @@ __global__ void __launch_bounds__(kDiagThreads) k_chol_diag(const FrontDev *__re
     part += __shfl_xor_sync(0xffffffffu, part, 1);
     part += __shfl_xor_sync(0xffffffffu, part, 2);
     if (sub == 0 && r == j) {
-      T a = L[j * P + j] - part;
+      const T a0 = L[j * P + j];
+      T a = a0 - part;
       if (!(a > T(0)) || !isfinite(a)) {
-        atomicOr(err, 8);
-        a = T(1);
+        if (compensate && a0 > T(0) && isfinite(a0)) {
+          atomicOr(err, 16);
+          atomicAdd(err + 1, 1);
+          a = a0;
+        } else {
+          atomicOr(err, 8);
+          a = T(1);
+        }
       }
       L[j * P + j] = sqrt(a);
     }
@@ -208,7 +220,7 @@ template <typename T>
 cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
                               int32_t *piv, int *err, cudaStream_t s, const LuAsync *la, Prof *prof,
                               const uint8_t *maps, float *pack, T *inv, const CholSchedule *sched,
-                              const uint8_t *maps64) {
+                              const uint8_t *maps64, int bf16) {
   constexpr int NB = chol_nb<T>();
   const CholSchedule sch = sched ? *sched : CholSchedule();
   const int nsm = device_sms();
@@ -223,7 +235,7 @@ cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfro
         fpanel += jb * jb * jb / 3.0 + rows * jb * jb;  // tile Cholesky + triangular solve of the rows below
       }
     const size_t e0 = prof->begin(st);
-    k_chol_diag<T, NB><<<nfront, kDiagThreads, 0, st>>>(fr, j0, fronts, piv, err, inv);
+    k_chol_diag<T, NB><<<nfront, kDiagThreads, 0, st>>>(fr, j0, fronts, piv, err, inv, bf16 != 0 ? 1 : 0);
     const int below = max_f - j0 - 1;
     if (below > 0)
       k_chol_l21<T, NB><<<dim3(unsigned(cdiv_c(below, kL21Threads)), unsigned(nfront)), kL21Threads, 0, st>>>(
@@ -233,6 +245,7 @@ cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfro
   };
   bool tc = false;
   if constexpr (std::is_same<T, float>::value) tc = use_tensor_core_gemm_host() && maps != nullptr && pack != nullptr;
+  if (bf16 && !tc) return cudaErrorNotSupported;  // BF16 block ends need the tensor-core path
   if constexpr (std::is_same<T, float>::value) {
     if (tc) {
       // ---- FP32: outer blocks of KB columns, tensor-core updates ----
@@ -269,7 +282,7 @@ cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfro
         const int tlo = lo / kTcTile, thi = hi >= (INT_MAX - kTcTile) ? INT_MAX : hi / kTcTile;
         const size_t e0 = prof->begin(st);
         cudaError_t ge = launch_gemm_tc_ws(fr, J, KB, nfront, max_f, fronts, err, st, tlo, thi, budget, maps, ap, ap,
-                                           /*lower=*/1, max_tiles, maps64);
+                                           /*lower=*/1, max_tiles, maps64, bf16);
         prof->end(P_GEMM, 1, e0, fg, st);
         return ge;
       };
@@ -299,7 +312,9 @@ cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfro
         }
         const bool more = J + KB < max_s;
         float *ap = apack[b & 1];
-        if ((e = launch_pack_a(fr, J, KB, nfront, max_f, fronts, ap, ms)) != cudaSuccess) return e;
+        if ((e = bf16 ? launch_pack_bf16(fr, J, KB, nfront, max_f, fronts, ap, ms, bf16)
+                      : launch_pack_a(fr, J, KB, nfront, max_f, fronts, ap, ms)) != cudaSuccess)
+          return e;
         if (ahead) {
           // the rest of the block end on the low-priority stream; the next
           // block's columns stay on the panel stream
@@ -356,10 +371,10 @@ cudaError_t launch_chol_to_lu(const FrontDev *fr, int nfront, int max_f, T *fron
 
 template cudaError_t launch_chol_level<double>(const FrontDev *, const Front *, int, int, int, double *, int32_t *,
                                                int *, cudaStream_t, const LuAsync *, Prof *, const uint8_t *, float *,
-                                               double *, const CholSchedule *, const uint8_t *);
+                                               double *, const CholSchedule *, const uint8_t *, int);
 template cudaError_t launch_chol_level<float>(const FrontDev *, const Front *, int, int, int, float *, int32_t *,
                                               int *, cudaStream_t, const LuAsync *, Prof *, const uint8_t *, float *,
-                                              float *, const CholSchedule *, const uint8_t *);
+                                              float *, const CholSchedule *, const uint8_t *, int);
 template cudaError_t launch_chol_to_lu<double>(const FrontDev *, int, int, double *, cudaStream_t, Prof *, double);
 template cudaError_t launch_chol_to_lu<float>(const FrontDev *, int, int, float *, cudaStream_t, Prof *, double);
 

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include "kernels.h"
@@ -562,6 +563,148 @@ __global__ void __launch_bounds__(256) k_pack_b(const FrontDev *__restrict__ fr,
   }
 }
 
+// ---- the BF16 block-end operands (block Cholesky, H2SP_BF16_CHOL) ----
+// A 128-row tile of L21 (K = the block's columns, <= 256) scaled by 2^-e,
+// e = the exponent of the tile's largest |entry| (frexp), and rounded to BF16,
+// in the canonical K-major layout of kind::f16: per 64-deep K chunk, 8-row
+// groups 1024 bytes apart, K-adjacent 8 x 8 core matrices 128 bytes apart
+// (chunk q at byte 16384 q).  The exponent (an int) follows at byte 65536 of
+// the tile's slot.  One CTA per tile and front.
+constexpr int kBfK = 64;                            // K per chunk
+constexpr uint32_t kBfSbo = (kBfK / 8) * 128;       // 8-row groups: 1024 bytes
+constexpr int kBfChunkBytes = kTcM * kBfK * 2;      // 16 KB
+constexpr int kBfExpFloat = 4 * kBfChunkBytes / 4;  // float index of the exponent (byte 65536)
+static_assert(kBfChunkBytes == 2 * kPkTile * 4, "a BF16 chunk has the bytes of a TF32 hi/lo chunk pair");
+
+__device__ __forceinline__ uint64_t smem_desc_bf(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr >> 4) & 0x3FFFu);
+  d |= uint64_t((kLbo >> 4) & 0x3FFFu) << 16;
+  d |= uint64_t((kBfSbo >> 4) & 0x3FFFu) << 32;
+  d |= uint64_t(1) << 46;
+  return d;
+}
+
+// kind::f16, D = F32, A = B = BF16, both K-major, M = 128, N = 128
+constexpr uint32_t kIdescBf = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kTcN >> 3) << 17) |
+                              (uint32_t(kTcM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(kIdescBf), "r"(accumulate));
+}
+
+// The exponent e (frexp) of the largest |entry| of rows [r0, r0 + rows) x
+// columns [j0, j0 + jb) of a column-major array (0 for an all-zero tile), on
+// every thread of a 256-thread CTA; thread 0 also stores it at *out.
+__device__ int tile_exponent(const float *__restrict__ A, int64_t ld, int r0, int rows, int j0, int jb, int *out) {
+  __shared__ float red[8];
+  __shared__ int s_e;
+  const int tid = threadIdx.x;
+  float mx = 0.f;
+  for (int e = tid; e < kTcM * jb; e += 256) {
+    const int m = e % kTcM, k = e / kTcM;
+    if (m < rows) mx = fmaxf(mx, fabsf(A[(r0 + m) + int64_t(j0 + k) * ld]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((tid & 31) == 0) red[tid >> 5] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.f;
+    for (int i = 0; i < 8; ++i) t = fmaxf(t, red[i]);
+    int ex = 0;
+    if (t > 0.f && isfinite(t)) frexpf(t, &ex);
+    s_e = ex;
+    *out = ex;
+  }
+  __syncthreads();
+  return s_e;
+}
+
+__global__ void __launch_bounds__(256) k_pack_bf16(const FrontDev *__restrict__ fr, int j0, int kb,
+                                                   const float *__restrict__ fronts, float *__restrict__ pack) {
+  const FrontDev F = fr[blockIdx.y];
+  if (j0 >= F.s) return;
+  const int jb = min(kb, F.s - j0), t0 = j0 + jb, nrest = F.f - t0;
+  const int rt = blockIdx.x;
+  if (rt * kTcM >= nrest) return;  // uniform over the CTA
+  const float *A = fronts + F.off;
+  const int64_t ld = F.ld;
+  float *slot = pack + (int64_t(F.pack_off) + rt) * kPackTileFloats;
+  const int tid = threadIdx.x;
+  const int r0 = t0 + rt * kTcM;
+  const int s_e = tile_exponent(A, ld, r0, nrest - rt * kTcM, j0, jb, reinterpret_cast<int *>(slot) + kBfExpFloat);
+  const float sc = ldexpf(1.f, -s_e);
+  // units of 8 consecutive K values of one row: one 16-byte store each
+  unsigned char *dst = reinterpret_cast<unsigned char *>(slot);
+  const int nunit = kTcM * (kLuOuterBlock / 8);
+  for (int u = tid; u < nunit; u += 256) {
+    const int m = u % kTcM, kcg = u / kTcM;  // row, global K core (8 values)
+    const int q = kcg / (kBfK / 8), kc = kcg % (kBfK / 8);
+    const bool row_ok = rt * kTcM + m < nrest;
+    uint32_t w[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      float v[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int k = kcg * 8 + 2 * h + t;
+        v[t] = (row_ok && k < jb) ? A[(r0 + m) + int64_t(j0 + k) * ld] * sc : 0.f;
+      }
+      const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[0], v[1]);
+      w[h] = *reinterpret_cast<const uint32_t *>(&b2);
+    }
+    const int g = m / 8, r = m % 8;
+    const size_t off = size_t(q) * kBfChunkBytes + size_t((g * (kBfK / 8) + kc) * 8 + r) * 16;
+    *reinterpret_cast<uint4 *>(dst + off) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// The two-term split (H2SP_BF16X3_CHOL): with the tile's scale 2^-e as above,
+// x 2^-e = hi + lo + O(2^-17 |x 2^-e|), hi = bf16(x 2^-e), lo = bf16(x 2^-e - hi).
+// Layout of the TF32 operands: per 32-deep K chunk q a hi and a lo 128 x 32
+// array (8 KB each, chunk q at float 4096 q); word w of an array holds the
+// BF16 pair of K values 2k, 2k + 1 of element (m, k) = pk_coords(w).  The
+// exponent follows the eight chunks at float kBf2ExpFloat.
+constexpr int kBf2K = 32;
+constexpr int kBf2ExpFloat = (kLuOuterBlock / kBf2K) * 2 * kPkTile;
+static_assert(kBf2ExpFloat < kPackTileFloats, "exponent inside the tile slot");
+
+__global__ void __launch_bounds__(256) k_pack_bf16x2(const FrontDev *__restrict__ fr, int j0, int kb,
+                                                     const float *__restrict__ fronts, float *__restrict__ pack) {
+  const FrontDev F = fr[blockIdx.y];
+  if (j0 >= F.s) return;
+  const int jb = min(kb, F.s - j0), t0 = j0 + jb, nrest = F.f - t0;
+  const int rt = blockIdx.x;
+  if (rt * kTcM >= nrest) return;  // uniform over the CTA
+  const float *A = fronts + F.off;
+  const int64_t ld = F.ld;
+  float *slot = pack + (int64_t(F.pack_off) + rt) * kPackTileFloats;
+  const int r0 = t0 + rt * kTcM, rows = nrest - rt * kTcM;
+  const int ex = tile_exponent(A, ld, r0, rows, j0, jb, reinterpret_cast<int *>(slot) + kBf2ExpFloat);
+  const float sc = ldexpf(1.f, -ex);
+  uint32_t *dst = reinterpret_cast<uint32_t *>(slot);
+  const int nq = (jb + kBf2K - 1) / kBf2K;
+  for (int u = threadIdx.x; u < nq * kPkTile; u += 256) {
+    const int q = u / kPkTile, w = u % kPkTile;
+    int m, kw;
+    pk_coords(w, m, kw);
+    const int k = q * kBf2K + 2 * kw;
+    float v[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) v[t] = (m < rows && k + t < jb) ? A[(r0 + m) + int64_t(j0 + k + t) * ld] * sc : 0.f;
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[0], v[1]);
+    const __nv_bfloat162 l2 =
+        __floats2bfloat162_rn(v[0] - __bfloat162float(h2.x), v[1] - __bfloat162float(h2.y));
+    dst[q * 2 * kPkTile + w] = *reinterpret_cast<const uint32_t *>(&h2);
+    dst[q * 2 * kPkTile + kPkTile + w] = *reinterpret_cast<const uint32_t *>(&l2);
+  }
+}
+
 __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(mbar)
@@ -601,6 +744,10 @@ constexpr int kWsThreads = (kWsEpiWarps + 2) * 32;  // sixteen epilogue warps, a
 // accumulator back.  Every wait is bounded; on
 // timeout the kernel raises the error flag, waits (bounded) for its copies and
 // MMAs in flight, releases TMEM and returns.
+// MODE 0: FP32 operands as TF32 hi/lo pairs, three kind::tf32 MMAs per K step;
+// MODE 1: BF16 operands (k_pack_bf16), one kind::f16 MMA per K step;
+// MODE 2: BF16 hi/lo pairs (k_pack_bf16x2), three kind::f16 MMAs per K step.
+template <int MODE>
 __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__restrict__ fr, int j0, int kb,
                                                              float *__restrict__ fronts, int *__restrict__ err,
                                                              int splits, int tile_lo, int tile_hi,
@@ -622,7 +769,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__
   const int c_lo = tile_lo + blockIdx.x * per, c_hi = min(tile_end, c_lo + per);
   if (c_lo >= c_hi) return;
   const int nt = c_hi - c_lo;
-  const int nq = (jb + kPkK - 1) / kPkK;
+  // K chunks: 16 TF32 values (hi and lo arrays), 64 BF16 values or 32 BF16
+  // values (hi and lo arrays), 16 KB per operand in each case
+  const int nq = MODE == 1 ? (jb + kBfK - 1) / kBfK : MODE == 2 ? (jb + kBf2K - 1) / kBf2K : (jb + kPkK - 1) / kPkK;
   const int G = nt * nq;  // chunk steps of this CTA
   float *A = fronts + F.off;
   const int64_t ld = F.ld;
@@ -661,7 +810,20 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__
   const uint32_t tmem = tmem_base;
   const float *Ab = apack + (int64_t(F.pack_off) + blockIdx.y) * kPackTileFloats;
   const float *Bb = bpack + int64_t(F.pack_off) * kPackTileFloats;
-  constexpr uint32_t kHalfBytes = 2 * kPkTile * 4;  // a hi and a lo array: 16 KB
+  constexpr uint32_t kHalfBytes = 2 * kPkTile * 4;  // a hi and a lo array (or a BF16 chunk): 16 KB
+  // BF16 operands carry one power-of-two scale per tile: the product of the
+  // row tile's and the column tile's goes back on in the epilogue
+  auto tile_scale = [&](int ct) -> float {
+    if constexpr (MODE != 0) {
+      constexpr int xf = MODE == 1 ? kBfExpFloat : kBf2ExpFloat;
+      const int ea = reinterpret_cast<const int *>(Ab)[xf];
+      const int eb = reinterpret_cast<const int *>(Bb + int64_t(ct) * kPackTileFloats)[xf];
+      return ldexpf(1.f, ea + eb);
+    } else {
+      (void)ct;
+      return 1.f;
+    }
+  };
   constexpr int kStageFloats = 4 * kPkTile;
 
   __shared__ volatile int s_consumed;  // chunks whose copies the MMA warp has waited for
@@ -717,14 +879,36 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__
         const uint32_t base = smem_u32(stage0 + st * kStageFloats);
         const uint32_t ah0 = base, al0 = base + kPkTile * 4, bh0 = base + 2 * kPkTile * 4, bl0 = base + 3 * kPkTile * 4;
         const uint32_t acc = tmem + uint32_t(a * kTcN);
+        if constexpr (MODE == 2) {
+          // the TF32 pairs' layout, K = 16 BF16 values per MMA (32 bytes: the same cores)
 #pragma unroll
-        for (int kk = 0; kk < kPkK / 8; ++kk) {
-          const uint32_t koff = uint32_t(kk) * 2 * kLbo;
-          const uint64_t ah = smem_desc_pk(ah0 + koff), al = smem_desc_pk(al0 + koff);
-          const uint64_t bh = smem_desc_pk(bh0 + koff), bl = smem_desc_pk(bl0 + koff);
-          mma_tf32(acc, ah, bh, (q > 0 || kk > 0) ? 1u : 0u);
-          mma_tf32(acc, ah, bl, 1u);
-          mma_tf32(acc, al, bh, 1u);
+          for (int kk = 0; kk < kBf2K / 16; ++kk) {
+            const uint32_t koff = uint32_t(kk) * 2 * kLbo;
+            const uint64_t ah = smem_desc_pk(ah0 + koff), al = smem_desc_pk(al0 + koff);
+            const uint64_t bh = smem_desc_pk(bh0 + koff), bl = smem_desc_pk(bl0 + koff);
+            mma_bf16(acc, ah, bh, (q > 0 || kk > 0) ? 1u : 0u);
+            mma_bf16(acc, ah, bl, 1u);
+            mma_bf16(acc, al, bh, 1u);
+          }
+        } else if constexpr (MODE == 1) {
+          // A at the stage's first 16 KB, B at the second; K = 16 per MMA
+          const uint32_t b0 = base + uint32_t(kBfChunkBytes);
+          (void)al0, (void)bh0, (void)bl0;
+#pragma unroll
+          for (int kk = 0; kk < kBfK / 16; ++kk) {
+            const uint32_t koff = uint32_t(kk) * 2 * kLbo;
+            mma_bf16(acc, smem_desc_bf(ah0 + koff), smem_desc_bf(b0 + koff), (q > 0 || kk > 0) ? 1u : 0u);
+          }
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < kPkK / 8; ++kk) {
+            const uint32_t koff = uint32_t(kk) * 2 * kLbo;
+            const uint64_t ah = smem_desc_pk(ah0 + koff), al = smem_desc_pk(al0 + koff);
+            const uint64_t bh = smem_desc_pk(bh0 + koff), bl = smem_desc_pk(bl0 + koff);
+            mma_tf32(acc, ah, bh, (q > 0 || kk > 0) ? 1u : 0u);
+            mma_tf32(acc, ah, bl, 1u);
+            mma_tf32(acc, al, bh, 1u);
+          }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(&empty[st])));
@@ -786,8 +970,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;");
         float *col = sC + h * kWsCFloats + (qc * 16) * kTcM + row;  // box order: rows fastest
+        const float scl = tile_scale(ct);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) col[j * kTcM] -= __uint_as_float(v[j]);
+        for (int j = 0; j < 16; ++j) col[j * kTcM] -= scl * __uint_as_float(v[j]);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         epi_bar();
         if (tid == 0) {
@@ -845,8 +1030,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__
               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;");
+        const float scl = tile_scale(ct);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) cv[c0 + j] -= __uint_as_float(v[j]);
+        for (int j = 0; j < 16; ++j) cv[c0 + j] -= scl * __uint_as_float(v[j]);
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       epi_bar();
@@ -934,6 +1120,18 @@ cudaError_t launch_pack_a(const FrontDev *fr, int j0, int kb, int nfront, int ma
   return cudaGetLastError();
 }
 
+cudaError_t launch_pack_bf16(const FrontDev *fr, int j0, int kb, int nfront, int max_f, const float *fronts,
+                             float *pack, cudaStream_t s, int mode) {
+  const int rest = max_f - j0 - 1;
+  if (rest <= 0 || nfront == 0) return cudaSuccess;
+  const dim3 g((rest + kTcM - 1) / kTcM, nfront);
+  if (mode == 2)
+    k_pack_bf16x2<<<g, 256, 0, s>>>(fr, j0, kb, fronts, pack);
+  else
+    k_pack_bf16<<<g, 256, 0, s>>>(fr, j0, kb, fronts, pack);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pack_b(const FrontDev *fr, int j0, int kb, int nfront, int max_f, const float *fronts, float *bpack,
                           int ct_lo, int ct_hi, cudaStream_t s) {
   const int rest = max_f - j0 - 1;
@@ -949,8 +1147,11 @@ size_t gemm_ws_smem() { return (size_t(kWsStages) * 4 * kPkTile + 2 * size_t(kWs
 cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
                               cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps,
                               const float *apack, const float *bpack, int lower, int max_tiles,
-                              const uint8_t *maps64) {
-  if (cudaError_t ea = smem_attr((const void *)k_gemm_tc_ws, int(gemm_ws_smem())); ea != cudaSuccess) return ea;
+                              const uint8_t *maps64, int bf16) {
+  const void *kern = bf16 == 2 ? (const void *)k_gemm_tc_ws<2>
+                     : bf16 == 1 ? (const void *)k_gemm_tc_ws<1>
+                                 : (const void *)k_gemm_tc_ws<0>;
+  if (cudaError_t ea = smem_attr(kern, int(gemm_ws_smem())); ea != cudaSuccess) return ea;
   (void)maps;
   if (apack == nullptr || bpack == nullptr) return cudaErrorInvalidValue;
   const int rest = max_f - j0 - 1;
@@ -964,8 +1165,15 @@ cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, in
   // turn over often (work on a higher-priority stream gets them sooner)
   if (max_tiles > 0) splits = std::max(splits, std::min(ct, (ct + max_tiles - 1) / max_tiles));
   dim3 g(splits, rt, nfront);
-  k_gemm_tc_ws<<<g, kWsThreads, gemm_ws_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi, apack,
-                                                     bpack, lower, maps64);
+  if (bf16 == 2)
+    k_gemm_tc_ws<2><<<g, kWsThreads, gemm_ws_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi, apack,
+                                                          bpack, lower, maps64);
+  else if (bf16 == 1)
+    k_gemm_tc_ws<1><<<g, kWsThreads, gemm_ws_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi, apack,
+                                                          bpack, lower, maps64);
+  else
+    k_gemm_tc_ws<0><<<g, kWsThreads, gemm_ws_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi, apack,
+                                                          bpack, lower, maps64);
   return cudaGetLastError();
 }
 

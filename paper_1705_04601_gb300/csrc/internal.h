@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -221,7 +222,24 @@ struct Prof {
   }
 };
 
-// Validate the descriptor and build the plan.  Returns an h2sp_status.
-int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbers = true);
+// The level schedule of §2.2-2.3 as the device kernels give it (host copies):
+// l_stop, per cluster m, k', d, off, xoff, q_off and its S node (-1: none),
+// per node its cluster, level and first row (node_off[nn] = n), and Near_l
+// for 1 <= l <= l_stop as CSR over the clusters of level l.
+struct A1Result {
+  int lstop = 0, nn = 0;
+  std::vector<int64_t> m, kp, d, off, xoff, q_off, node_off;
+  std::vector<int32_t> node_of, node_cluster, node_level;
+  std::vector<std::vector<int64_t>> near_ptr;
+  std::vector<std::vector<int32_t>> near_col;
+};
+// Called by build_plan once the descriptor is validated (the plan's copies of
+// the structure arrays are set): fills the level schedule.  Returns an h2sp_status.
+using A1Source = std::function<int(const Plan &, A1Result &, std::string &)>;
+
+// Validate the descriptor and build the plan.  Returns an h2sp_status.  With
+// `a1`, the level schedule comes from it; otherwise the host derives it.
+int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbers = true,
+               const A1Source *a1 = nullptr);
 
 }  // namespace h2sp

@@ -152,7 +152,7 @@ template <typename T>
 cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfront, int max_s, int max_f, T *fronts,
                               int32_t *piv, int *err, cudaStream_t s, const LuAsync *la, Prof *prof,
                               const uint8_t *maps, float *pack, T *inv, const CholSchedule *sched = nullptr,
-                              const uint8_t *maps64 = nullptr);
+                              const uint8_t *maps64 = nullptr, int bf16 = 0);
 // Rewrite Cholesky-factored fronts in the LU form: unit L = L_chol D^-1, U = D L_chol^T.
 template <typename T>
 cudaError_t launch_chol_to_lu(const FrontDev *fr, int nfront, int max_f, T *fronts, cudaStream_t s, Prof *prof,
@@ -237,7 +237,13 @@ cudaError_t launch_pack_b(const FrontDev *fr, int j0, int kb, int nfront, int ma
 cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
                               cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps,
                               const float *apack, const float *bpack, int lower = 0, int max_tiles = 0,
-                              const uint8_t *maps64 = nullptr);
+                              const uint8_t *maps64 = nullptr, int bf16 = 0);
+// BF16 operands of the block-end update (block Cholesky): each 128-row tile of
+// L21 scaled by a power of two and rounded to BF16 (mode 1), or split into a
+// BF16 hi and lo part (mode 2); the exponent rides in the tile's slot of the
+// pack buffer.  bf16 of launch_gemm_tc_ws takes the same mode.
+cudaError_t launch_pack_bf16(const FrontDev *fr, int j0, int kb, int nfront, int max_f, const float *fronts,
+                             float *pack, cudaStream_t s, int mode);
 // one descriptor per front: 2D (rows, columns), boxes of 128 rows x box_cols columns
 cudaError_t make_front_tmaps(const Front *fronts, int n, const float *base, uint8_t *maps_dev, int box_cols = 128);
 constexpr int kTcTile = 128;
@@ -250,6 +256,24 @@ struct ApItem {
   int64_t xout;   // row in the level-(l+1) vector of the basis part, -1 if none
   int32_t m, kp;
 };
+// The level maps of the applies and the S node offsets built by the device
+// level schedule (sched.cu): apply items of level l at ap + ap_base[l]
+// (nap[l] of them), the top clusters' copies into S, node_off.  The buffers
+// in `allocs` pass to the caller.
+struct DeviceMaps {
+  std::vector<void *> allocs;
+  ApItem *ap = nullptr;
+  std::vector<int32_t> ap_base, nap;
+  int64_t *top_src = nullptr, *top_dst = nullptr;
+  int32_t *top_len = nullptr;
+  int ntop = 0;
+  int64_t *node_off = nullptr;
+};
+// Runs the level schedule on the current device from the plan's (validated)
+// structure arrays; host copies into *out, device level maps into *maps
+// (either may be null).  Synchronous; returns an h2sp_status.
+int device_schedule(const Plan &p, A1Result *out, DeviceMaps *maps, std::string &err);
+
 // out rows: non-basis -> S space (ys), basis -> next level (xn); op = Q^T.
 // T = double (the API's applies) or float (inside the FP32 preconditioner).
 // max_m: the level's largest block; above kMaxBlock the input slab is staged

@@ -94,7 +94,7 @@ struct Fail {
 
 }  // namespace
 
-int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbers) {
+int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbers, const A1Source *a1) {
   try {
     REQUIRE(d != nullptr, "null descriptor");
     REQUIRE(d->n > 0 && d->n < (int64_t(1) << 31), "n out of range");
@@ -209,62 +209,95 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
     int lstop = 0;
     for (int l = 0; l <= D; ++l)
       if (!far[l].empty()) lstop = l + 1;
+    A1Result dev;
+    if (a1) {
+      const int st = (*a1)(p, dev, err);
+      if (st != H2SP_OK) throw Fail{st, err};
+      if (dev.lstop != lstop || int64_t(dev.m.size()) != ncl || int64_t(dev.near_ptr.size()) != lstop + 1)
+        throw Fail{H2SP_EINVAL, "internal: device level schedule of another shape"};
+    }
     p.lstop = lstop;
     std::vector<std::vector<u64>> near(lstop + 1);
     for (int lf = 0; lf < nleaf; ++lf)
       for (int64_t i = p.near_ptr[lf]; i < p.near_ptr[lf + 1]; ++i) near[0].push_back(key(lp[D] + lf, p.near_col[i]));
     // near[0] is sorted by construction (rows ascending, columns ascending)
-    for (int l = 0; l < lstop; ++l) {
-      auto &nx = near[l + 1];
-      nx.reserve(near[l].size() / 2 + far[l].size() / 4 + 1);
-      for (u64 k : near[l]) nx.push_back(key(p.parent[kfirst(k)], p.parent[ksecond(k)]));
-      for (auto &f : far[l]) nx.push_back(key(p.parent[f[0]], p.parent[f[1]]));
-      sort_unique(nx);
-    }
-    // local sizes
-    p.m.assign(ncl, 0);
-    p.kp.assign(ncl, 0);
-    p.d.assign(ncl, 0);
-    p.off.assign(ncl, 0);
-    p.xoff.assign(ncl, 0);
-    for (int t = lev_begin(0); t < lev_end(0); ++t) p.m[t] = p.h_size[t];
-    for (int l = 0; l <= lstop; ++l) {
-      int64_t a = 0;
-      for (int t = lev_begin(l); t < lev_end(l); ++t) {
-        p.xoff[t] = a;
-        a += p.m[t];
-        if (l < lstop) {
-          p.kp[t] = std::min<int64_t>(p.rank[t], p.m[t]);
-          p.d[t] = p.m[t] - p.kp[t];
-        } else {
-          p.kp[t] = 0;
-          p.d[t] = p.m[t];
-        }
+    if (a1) {
+      // the device's Near_l: CSR over the level's clusters, rows and columns ascending
+      for (int l = 1; l <= lstop; ++l) {
+        const auto &ptr = dev.near_ptr[l];
+        const auto &col = dev.near_col[l];
+        near[l].reserve(col.size());
+        for (int r = 0; r + 1 < int(ptr.size()); ++r)
+          for (int64_t i = ptr[r]; i < ptr[r + 1]; ++i) near[l].push_back(key(lev_begin(l) + r, col[i]));
       }
-      if (l < lstop)
+      p.m = std::move(dev.m);
+      p.kp = std::move(dev.kp);
+      p.d = std::move(dev.d);
+      p.off = std::move(dev.off);
+      p.xoff = std::move(dev.xoff);
+    } else {
+      for (int l = 0; l < lstop; ++l) {
+        auto &nx = near[l + 1];
+        nx.reserve(near[l].size() / 2 + far[l].size() / 4 + 1);
+        for (u64 k : near[l]) nx.push_back(key(p.parent[kfirst(k)], p.parent[ksecond(k)]));
+        for (auto &f : far[l]) nx.push_back(key(p.parent[f[0]], p.parent[f[1]]));
+        sort_unique(nx);
+      }
+      // local sizes
+      p.m.assign(ncl, 0);
+      p.kp.assign(ncl, 0);
+      p.d.assign(ncl, 0);
+      p.off.assign(ncl, 0);
+      p.xoff.assign(ncl, 0);
+      for (int t = lev_begin(0); t < lev_end(0); ++t) p.m[t] = p.h_size[t];
+      for (int l = 0; l <= lstop; ++l) {
+        int64_t a = 0;
         for (int t = lev_begin(l); t < lev_end(l); ++t) {
-          int pa = p.parent[t];
-          p.off[t] = p.m[pa];
-          p.m[pa] += p.kp[t];
+          p.xoff[t] = a;
+          a += p.m[t];
+          if (l < lstop) {
+            p.kp[t] = std::min<int64_t>(p.rank[t], p.m[t]);
+            p.d[t] = p.m[t] - p.kp[t];
+          } else {
+            p.kp[t] = 0;
+            p.d[t] = p.m[t];
+          }
         }
+        if (l < lstop)
+          for (int t = lev_begin(l); t < lev_end(l); ++t) {
+            int pa = p.parent[t];
+            p.off[t] = p.m[pa];
+            p.m[pa] += p.kp[t];
+          }
+      }
     }
     for (int l = 0; l < std::max(lstop, 1); ++l)
       for (int t = lev_begin(l); t < lev_end(l); ++t)
         if (p.m[t] > kMaxLargeBlock) throw Fail{H2SP_EUNSUPPORTED, "local block above 384 rows (leaf or level size)"};
     // S nodes: non-basis parts level by level, then the top clusters
-    p.node_of.assign(ncl, -1);
-    for (int l = 0; l <= lstop; ++l)
-      for (int t = lev_begin(l); t < lev_end(l); ++t)
-        if (p.d[t] > 0) {
-          p.node_of[t] = int32_t(p.node_size.size());
-          p.node_level.push_back(l);
-          p.node_cluster.push_back(t);
-          p.node_size.push_back(p.d[t]);
-        }
+    if (a1) {
+      p.node_of = std::move(dev.node_of);
+      p.node_level = std::move(dev.node_level);
+      p.node_cluster = std::move(dev.node_cluster);
+      p.node_off = std::move(dev.node_off);
+      p.node_size.resize(p.node_cluster.size());
+      for (size_t v = 0; v < p.node_cluster.size(); ++v) p.node_size[v] = p.d[p.node_cluster[v]];
+    } else {
+      p.node_of.assign(ncl, -1);
+      for (int l = 0; l <= lstop; ++l)
+        for (int t = lev_begin(l); t < lev_end(l); ++t)
+          if (p.d[t] > 0) {
+            p.node_of[t] = int32_t(p.node_size.size());
+            p.node_level.push_back(l);
+            p.node_cluster.push_back(t);
+            p.node_size.push_back(p.d[t]);
+          }
+      const int nn0 = int(p.node_size.size());
+      p.node_off.assign(nn0 + 1, 0);
+      for (int v = 0; v < nn0; ++v) p.node_off[v + 1] = p.node_off[v] + p.node_size[v];
+    }
     const int nn = int(p.node_size.size());
-    p.node_off.assign(nn + 1, 0);
-    for (int v = 0; v < nn; ++v) p.node_off[v + 1] = p.node_off[v] + p.node_size[v];
-    REQUIRE(p.node_off[nn] == p.n, "internal: S nodes do not cover n");
+    REQUIRE(int64_t(p.node_off.size()) == nn + 1 && p.node_off[nn] == p.n, "internal: S nodes do not cover n");
     // Q / Rr storage for the compressed levels
     p.q_off.assign(ncl, -1);
     p.rr_off.assign(ncl, -1);

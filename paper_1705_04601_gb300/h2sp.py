@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libh2sp.so")
 
 H2SP_OK, H2SP_EINVAL, H2SP_ENOMEM, H2SP_ECUDA, H2SP_ESINGULAR = 0, -1, -2, -3, -4
 H2SP_ESTATE, H2SP_ENOCONV, H2SP_ETIMEOUT, H2SP_EUNSUPPORTED = -5, -6, -7, -8
-H2SP_FP64, H2SP_FP32, H2SP_FP64_CHOL, H2SP_FP32_CHOL = 0, 1, 2, 3
+H2SP_FP64, H2SP_FP32, H2SP_FP64_CHOL, H2SP_FP32_CHOL, H2SP_BF16_CHOL, H2SP_BF16X3_CHOL = 0, 1, 2, 3, 7, 15
 H2SP_SPARSIFY_FP32 = 1  # h2sp_opts.flags bit
 H2SP_OP_UT, H2SP_OP_V, H2SP_OP_U, H2SP_OP_VT, H2SP_OP_S, H2SP_OP_H2, H2SP_OP_SINV = range(7)
 H2SP_DIRECT, H2SP_IR, H2SP_GMRES = 0, 1, 2
@@ -63,7 +63,7 @@ class Stats(ctypes.Structure):
         ("nfront_levels", ctypes.c_int32), ("max_front", ctypes.c_int64), ("front_elems", ctypes.c_int64),
         ("factor_flops", ctypes.c_double), ("sparsify_flops", ctypes.c_double), ("factor_prec", ctypes.c_int32),
         ("plan_seconds", ctypes.c_double), ("sparsify_prec", ctypes.c_int32), ("nsys", ctypes.c_int32),
-        ("factor_chol", ctypes.c_int32), ("chol_flops", ctypes.c_double),
+        ("factor_chol", ctypes.c_int32), ("chol_flops", ctypes.c_double), ("compensated_pivots", ctypes.c_int32),
     ]
 
 
@@ -91,6 +91,8 @@ SIGNATURES = {
     "h2sp_export_S": (ctypes.c_int, [_vp, _i64p, _i64p, _i32p, _i64p, _f64p, _vp]),
     "h2sp_export_Q": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _i64p, _f64p, _vp]),
     "h2sp_export_structure": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i64p]),
+    "h2sp_export_schedule": (ctypes.c_int, [_vp, _i32p, _i64p, _i64p, _i64p, _i64p, _i64p, _i32p]),
+    "h2sp_export_near": (ctypes.c_int, [_vp, ctypes.c_int32, _i64p, _i32p, _i64p]),
     "h2sp_export_front": (ctypes.c_int, [_vp, ctypes.c_int32, _i64p, _i64p, _f64p, _vp]),
     "h2sp_measure_peak": (ctypes.c_int, [ctypes.c_int32, _f64p, _vp]),
     "h2sp_set_option": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int64]),
@@ -416,6 +418,32 @@ def h2sp_export_structure(h: Handle) -> dict:
                                                  "bnd_ptr", "bnd")], ctypes.byref(nb)), "h2sp_export_structure")
     out["bnd"] = out["bnd"][:nb.value]
     return out
+
+
+def h2sp_export_schedule(h: Handle, ncl: int) -> dict:
+    """The device level schedule of h's structure: lstop, per cluster m, kp,
+    off, xoff, per S node node_off (nnodes + 1) and node_cluster."""
+    nn = h2sp_query(h)["nnodes"]
+    out = dict(m=np.zeros(ncl, np.int64), kp=np.zeros(ncl, np.int64), off=np.zeros(ncl, np.int64),
+               xoff=np.zeros(ncl, np.int64), node_off=np.zeros(nn + 1, np.int64), node_cluster=np.zeros(nn, np.int32))
+    ls = ctypes.c_int32(0)
+    _check(lib().h2sp_export_schedule(h.ptr, ctypes.byref(ls), *[_ptr(out[k], ctypes.c_int64) for k in
+                                                                 ("m", "kp", "off", "xoff", "node_off")],
+                                      _ptr(out["node_cluster"], ctypes.c_int32)), "h2sp_export_schedule")
+    out["lstop"] = int(ls.value)
+    return out
+
+
+def h2sp_export_near(h: Handle, level: int, nrows: int) -> tuple:
+    """(ptr, col): Near_level of the device level schedule as CSR over the
+    level's nrows clusters."""
+    nnz = ctypes.c_int64(0)
+    _check(lib().h2sp_export_near(h.ptr, int(level), None, None, ctypes.byref(nnz)), "h2sp_export_near")
+    ptr = np.zeros(nrows + 1, np.int64)
+    col = np.zeros(max(nnz.value, 1), np.int32)
+    _check(lib().h2sp_export_near(h.ptr, int(level), _ptr(ptr, ctypes.c_int64), _ptr(col, ctypes.c_int32),
+                                  ctypes.byref(nnz)), "h2sp_export_near")
+    return ptr, col[:nnz.value]
 
 
 def h2sp_profile(h: Handle, timing: int = -1, reset: bool = False) -> dict:

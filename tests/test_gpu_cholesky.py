@@ -223,3 +223,36 @@ def test_schedules_give_the_same_factor():
     sched, ms = T.tune(an, inp, flags=0, repeats=1)
     assert ms > 0 and set(sched) == set(T.DEFAULT)
     assert all(sched[n] in T.CANDIDATES[n] for n in sched)
+
+
+@pytest.mark.parametrize("name", ["gauss3d", "sphere8k"])
+@pytest.mark.parametrize("prec,bound", [("H2SP_BF16_CHOL", 1e-2), ("H2SP_BF16X3_CHOL", 2e-4)])
+def test_bf16_cholesky_preconditions_gmres_to_1e10(name, prec, bound):
+    """H2SP_BF16_CHOL: the block-end updates in BF16 with a power-of-two scale
+    per 128-row tile of L21 (FP32 accumulation); H2SP_BF16X3_CHOL: the same
+    with each scaled entry split into a BF16 hi and lo part and three BF16
+    products.  The factor is an approximation of the FP64 one -- its error
+    against the oracle's factor is printed and bounded (8 significant bits:
+    1e-2; about 16: 2e-4) -- and it preconditions FP64 GMRES to 1e-10."""
+    h, b, sp, ch = case(name)
+    hd = H.h2sp_sparsify(H.H2Input(h), flags=H.H2SP_SPARSIFY_FP32)
+    H.h2sp_factor(hd, getattr(H, prec))
+    q = H.h2sp_query(hd)
+    num = den = 0.0
+    for k in range(q["nsupernodes"]):
+        F, s = H.h2sp_export_front(hd, k)
+        ref = np.vstack([ch.L11[k], ch.L21[k]]) if ch.L21[k].size else ch.L11[k]
+        num += np.linalg.norm(chol_of_front(F, s) - ref) ** 2
+        den += np.linalg.norm(ref) ** 2
+    rel = np.sqrt(num / den)
+    print("%s: %s factor vs the FP64 oracle: %.2e" % (name, prec, rel))
+    assert rel <= bound
+    bt = dev(b)
+    xt = torch.empty_like(bt)
+    info = H.h2sp_solve(hd, bt, xt, mode=H.H2SP_GMRES, tol=1e-10, maxit=100, restart=30)
+    print("%s: GMRES steps %d" % (name, info.iters))
+    assert info.status == H.H2SP_OK and info.rel_residual <= 1e-10
+    torch.cuda.synchronize()
+    r = np.linalg.norm(b - oh2.Matvec(h)(host(xt)), axis=0) / np.linalg.norm(b, axis=0)
+    assert r.max() <= 2e-10
+    hd.close()
