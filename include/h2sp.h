@@ -135,6 +135,75 @@ typedef struct {
   const double *col_transfer;        /* column transfer matrices; NULL iff col_leaf_basis is NULL */
 } h2sp_h2_desc;
 
+/*
+ * ---- GPU construction of an H^2 matrix (the parameters of Definition 4.9) ----
+ *
+ * h2sp_construct builds, for a kernel function a(x, y) and points in a
+ * cluster tree, the H^2 matrix the sparsification takes: cluster bases by
+ * tensor Chebyshev interpolation on each cluster's box (order p per axis,
+ * rank p^dim <= 64; the leaf basis R_t[i, alpha] = L_alpha(x_i), the transfer
+ * T_c[alpha, beta] = L^{parent}_beta(y_alpha) at the Chebyshev points y of
+ * c), the coupling blocks D_ts = a(y_t, y_s) at the Chebyshev points, and
+ * the close blocks a(x_i, x_j) with `diag` on the diagonal.  With tol > 0
+ * the bases are then recompressed on the GPU:
+ *   orthogonalised bottom-up by Householder QR (R_t = Q_t Z_t, and
+ *   [Z_c T_c]_c = Q_t Z_t above the leaves, whose row blocks give the
+ *   transfers Tq_c of the orthonormal basis); every cluster weighted by the
+ *   far field its basis carries, top-down, M_t = sum_s Do_ts Do_ts^T +
+ *   Tq_t M_parent Tq_t^T with Do_ts = Z_t D_ts Z_s^T; the eigenvectors B_t
+ *   of M_t (Jacobi) with sqrt(lambda_i) > tol sqrt(lambda_0) kept; and the
+ *   parameters rewritten as Q_t B_t, B_c^T Tq_c B_parent and B_t^T Do_ts B_s.
+ * The weights are Gram matrices, so tol must be 0 or >= 1e-7 (H2SP_EINVAL).
+ * Symmetric kernels only: column bases equal row bases.
+ */
+typedef enum {
+  H2SP_KERNEL_LOG = 0,    /* -log r */
+  H2SP_KERNEL_INV = 1,    /* 1 / r */
+  H2SP_KERNEL_YUKAWA = 2, /* e^{-r} / r */
+  H2SP_KERNEL_GAUSS = 3   /* e^{-r^2} */
+} h2sp_kernel;
+
+typedef struct {
+  int64_t n;                     /* points */
+  int32_t dim;                   /* 2 or 3 */
+  int32_t depth;                 /* leaf depth D of the level-uniform tree */
+  /* tree and lists: HOST arrays, with the rules of h2sp_h2_desc */
+  const int32_t *level_ptr;      /* [D+2] */
+  const int32_t *parent;         /* [ncl] */
+  const int64_t *begin, *size;   /* [ncl]; every leaf non-empty */
+  const double *box_lo, *box_hi; /* [ncl * dim], row-major: the box of each cluster (its Chebyshev grid) */
+  const int64_t *far_ptr;        /* [ncl+1] */
+  const int32_t *far_col;        /* [nfar] */
+  const int64_t *near_ptr;       /* [nleaf+1] */
+  const int32_t *near_col;       /* [nnear] */
+  const double *points;          /* DEVICE [n * dim], row-major, in tree order */
+  int32_t kernel;                /* h2sp_kernel */
+  double diag;                   /* a_ii */
+  int32_t order;                 /* Chebyshev points per axis p; p^dim <= 64 */
+  double tol;                    /* 0: no recompression (rank p^dim); else >= 1e-7 */
+} h2sp_construct_desc;
+
+typedef struct h2sp_h2 h2sp_h2;  /* a constructed H^2 matrix: owns its arrays */
+
+/* Builds the matrix on the current device, enqueued on `stream` and
+ * synchronised before the call returns.  H2SP_EINVAL for a malformed tree or
+ * argument (message in h2sp_last_cuda_error), H2SP_ENOMEM / H2SP_ECUDA on
+ * device failures; *out is NULL then. */
+int h2sp_construct(const h2sp_construct_desc *c, h2sp_stream stream, h2sp_h2 **out);
+
+/* Fills *desc with m's structure (host arrays owned by m) and numbers
+ * (device arrays owned by m; symmetric bases), valid until h2sp_h2_destroy:
+ * the descriptor h2sp_analyze / h2sp_sparsify take. */
+int h2sp_h2_describe(const h2sp_h2 *m, h2sp_h2_desc *desc);
+
+/* Copies numeric array `which` (0 leaf_basis, 1 transfer, 2 coupling,
+ * 3 near_block) of m to dst (host or device memory) and gives its element
+ * count in *count; dst may be NULL to query the count.  Synchronous. */
+int h2sp_h2_copy(const h2sp_h2 *m, int32_t which, double *dst, int64_t *count, h2sp_stream stream);
+
+/* Frees m (NULL is allowed). */
+void h2sp_h2_destroy(h2sp_h2 *m);
+
 /* Bits of h2sp_opts.flags. */
 enum {
   /* Sparsify with FP32 products: the sandwich products of the close blocks
@@ -265,6 +334,36 @@ int h2sp_analyze(const h2sp_h2_desc *desc, h2sp_handle **out);
  * pivot and H2SP_ETIMEOUT if a bounded device wait gave up.
  */
 int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream);
+
+/*
+ * h2sp_factor_ilut -- threshold incomplete LU of S, the preconditioner of
+ * §5.5 (ILUt with a drop tolerance tau; the paper takes 1e-2 and 2e-2):
+ * the rows of S in the elimination order of the block LU (supernodes in
+ * order, each node's rows together), no pivoting; for each row i, with
+ * tau_i = tau ||S_i||_2, the multipliers w_k (k < i in increasing order)
+ * below tau_i are dropped before their update, and at the end every entry
+ * below tau_i except the diagonal.  tau = 0 gives the exact LU without
+ * pivoting of that matrix.  Computed in FP64 on the GPU from S (either
+ * sparsification precision); the supernodes of each elimination level in
+ * parallel, the rows of a supernode in order.  Afterwards h2sp_solve,
+ * H2SP_OP_SINV and the preconditioner of IR / GMRES use (L U)^{-1}
+ * (h2sp_stats.factor_prec = H2SP_FP64); h2sp_logdet, h2sp_refactor,
+ * h2sp_solve_captured and h2sp_export_front return H2SP_ESTATE until the next
+ * h2sp_factor.  H2SP_EINVAL for tau < 0 or not finite; H2SP_ESINGULAR on a
+ * zero pivot; H2SP_ENOMEM if the factors outgrow the memory.  Synchronous.
+ */
+int h2sp_factor_ilut(h2sp_handle *h, double tau, h2sp_stream stream);
+
+/*
+ * h2sp_export_ilut -- the incomplete factors, host arrays in elimination
+ * order (row e is row perm[e] of S): L strictly lower (unit diagonal not
+ * stored) as CSR l_ptr[n+1], l_col, l_val; U upper, diagonal first in each
+ * row, as u_ptr[n+1], u_col, u_val; columns ascending, in elimination order.
+ * Any pointer may be NULL (query *nnz_l and *nnz_u first).  H2SP_ESTATE
+ * unless the current factors come from h2sp_factor_ilut.
+ */
+int h2sp_export_ilut(h2sp_handle *h, int32_t *perm, int64_t *l_ptr, int32_t *l_col, double *l_val, int64_t *u_ptr,
+                     int32_t *u_col, double *u_val, int64_t *nnz_l, int64_t *nnz_u);
 
 /*
  * h2sp_refactor -- repeat the numeric sparsification and the factorization of

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libh2sp.so")
-SOURCES = ["plan.cpp", "sparsify.cu", "factor.cu", "chol.cu", "gemm_tc.cu", "apply.cu", "peak.cu", "sched.cu", "abi.cu"]
+SOURCES = ["plan.cpp", "sparsify.cu", "factor.cu", "chol.cu", "gemm_tc.cu", "apply.cu", "peak.cu", "sched.cu", "construct.cu", "ilut.cu", "abi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

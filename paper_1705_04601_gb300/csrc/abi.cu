@@ -218,6 +218,10 @@ struct h2sp_handle {
   float *pack = nullptr;     // packed GEMM operands of the blocked FP32 LU (3 buffers of the largest level)
   int32_t last_prec = -1;    // h2sp_prec of the last h2sp_factor (h2sp_refactor repeats it)
   bool chol = false;         // the current factors come from the block Cholesky (stored in the LU form)
+  bool ilut = false;         // the current factors are the threshold incomplete LU (ilu)
+  IlutState ilu;
+  double *ilu_z = nullptr;   // n x ilu_z_rhs work of the incomplete factors' solves
+  int ilu_z_rhs = 0;
   double *chol_inv = nullptr;  // L11^-1 tiles of the block Cholesky's panels (one per front of a level)
   cudaGraphExec_t graph_exec = nullptr;  // sparsification + factorization, captured by h2sp_refactor
   cudaStream_t graph_stream = nullptr;    // the graph is captured and launched here (the caller's may be legacy)
@@ -495,8 +499,17 @@ int sweep_status(h2sp_handle *h) {
 
 // in-place S^{-1} on an FP64 S-space vector (ld n)
 void solve_S(h2sp_handle *h, double *y, int nrhs) {
-  ensure_work(h, nrhs);
   const int64_t n = (*h->plan_ptr).n;
+  if (h->ilut) {
+    // the incomplete factors: (L U)^{-1}
+    if (h->ilu_z_rhs < nrhs) {
+      h->ilu_z = h->alloc<double>(size_t(n) * size_t(nrhs));
+      h->ilu_z_rhs = nrhs;
+    }
+    ilut_solve(h->ilu, y, nrhs, h->ilu_z, h->stream, &h->prof);
+    return;
+  }
+  ensure_work(h, nrhs);
   if (h->prec == H2SP_FP64) {
     solve_S_T<double>(h, y, nrhs);
   } else {
@@ -1328,6 +1341,7 @@ int factor_finish(h2sp_handle *h, int32_t prec) {
   if (herr != 0) return H2SP_ESINGULAR;
   h->prec = prec_fp32(prec) ? H2SP_FP32 : H2SP_FP64;
   h->chol = prec_chol(prec);
+  h->ilut = false;
   return H2SP_OK;
 }
 
@@ -1379,6 +1393,10 @@ NumericSizes numeric_sizes(const h2sp_h2_desc *d) {
 }
 
 }  // namespace
+
+namespace h2sp {
+void set_last_error(const std::string &msg) { g_cuda_err = msg; }
+}  // namespace h2sp
 
 extern "C" {
 
@@ -1494,9 +1512,75 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream) {
   }
 }
 
+int h2sp_factor_ilut(h2sp_handle *h, double tau, h2sp_stream stream) {
+  if (!h || !(tau >= 0.0) || !std::isfinite(tau)) return H2SP_EINVAL;
+  if (!h->device_ready) return H2SP_ESTATE;
+  const Plan &p = (*h->plan_ptr);
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->prof.stream = h->stream;
+  const StructureDev &sd = *h->sdev;
+  h->prec = -1;
+  h->ilut = false;
+  try {
+    ilut_factor(h->ilu, p, sd.brow_ptr, sd.bcol, sd.val_off, sd.node_off, h->S, h->sp_prec == H2SP_FP32, tau,
+                h->stream, &h->prof);
+  } catch (const IlutFail &f) {
+    g_cuda_err = "h2sp_factor_ilut: " + f.msg;
+    h->ilu.release();
+    return f.st;
+  }
+  h->prec = H2SP_FP64;
+  h->chol = false;
+  h->ilut = true;
+  return H2SP_OK;
+}
+
+int h2sp_export_ilut(h2sp_handle *h, int32_t *perm, int64_t *l_ptr, int32_t *l_col, double *l_val, int64_t *u_ptr,
+                     int32_t *u_col, double *u_val, int64_t *nnz_l, int64_t *nnz_u) {
+  if (!h) return H2SP_EINVAL;
+  if (!h->ilut || !h->ilu.ready) return H2SP_ESTATE;
+  IlutState &st = h->ilu;
+  const int64_t n = st.n;
+  std::vector<int64_t> off(static_cast<size_t>(n));
+  std::vector<int32_t> nl(static_cast<size_t>(n)), nu(static_cast<size_t>(n)), pc(static_cast<size_t>(st.nnz));
+  std::vector<double> pv(static_cast<size_t>(st.nnz));
+  cudaError_t e = cudaMemcpy(off.data(), st.row_off, sizeof(int64_t) * size_t(n), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(nl.data(), st.nl, sizeof(int32_t) * size_t(n), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(nu.data(), st.nu, sizeof(int32_t) * size_t(n), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && st.nnz)
+    e = cudaMemcpy(pc.data(), st.pool_col, sizeof(int32_t) * size_t(st.nnz), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && st.nnz)
+    e = cudaMemcpy(pv.data(), st.pool_val, sizeof(double) * size_t(st.nnz), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && perm) e = cudaMemcpy(perm, st.perm, sizeof(int32_t) * size_t(n), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    g_cuda_err = cudaGetErrorString(e);
+    cudaGetLastError();
+    return H2SP_ECUDA;
+  }
+  int64_t tl = 0, tu = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t o = off[size_t(i)];
+    if (l_ptr) l_ptr[i] = tl;
+    if (u_ptr) u_ptr[i] = tu;
+    for (int q = 0; q < nl[size_t(i)]; ++q, ++tl) {
+      if (l_col) l_col[tl] = pc[size_t(o + q)];
+      if (l_val) l_val[tl] = pv[size_t(o + q)];
+    }
+    for (int q = 0; q < nu[size_t(i)]; ++q, ++tu) {
+      if (u_col) u_col[tu] = pc[size_t(o + nl[size_t(i)] + q)];
+      if (u_val) u_val[tu] = pv[size_t(o + nl[size_t(i)] + q)];
+    }
+  }
+  if (l_ptr) l_ptr[n] = tl;
+  if (u_ptr) u_ptr[n] = tu;
+  if (nnz_l) *nnz_l = tl;
+  if (nnz_u) *nnz_u = tu;
+  return H2SP_OK;
+}
+
 int h2sp_refactor(h2sp_handle *h, h2sp_stream stream) {
   if (!h) return H2SP_EINVAL;
-  if (!h->device_ready || h->last_prec < 0) return H2SP_ESTATE;
+  if (!h->device_ready || h->last_prec < 0 || h->ilut) return H2SP_ESTATE;
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   h->prof.stream = h->stream;
   cudaStream_t s = h->stream;
@@ -1735,7 +1819,7 @@ int h2sp_solve_captured(h2sp_handle *h, int32_t steps, double tol, int32_t nrhs,
   if (!h->device_ready) return H2SP_ESTATE;
   const Plan &p = (*h->plan_ptr);
   if (ldb < p.n || ldx < p.n) return H2SP_EINVAL;
-  if (h->prec < 0) return H2SP_ESTATE;
+  if (h->prec < 0 || h->ilut) return H2SP_ESTATE;
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   h->prof.stream = h->stream;
   cudaStream_t s = h->stream;
@@ -1845,7 +1929,7 @@ int h2sp_export_S(h2sp_handle *h, int64_t *node_size, int64_t *brow_ptr, int32_t
 
 int h2sp_logdet(h2sp_handle *h, double *logabsdet, int32_t *sign, h2sp_stream stream) {
   if (!h || !logabsdet) return H2SP_EINVAL;
-  if (!h->device_ready || h->prec < 0) return H2SP_ESTATE;
+  if (!h->device_ready || h->prec < 0 || h->ilut) return H2SP_ESTATE;
   const Plan &p = (*h->plan_ptr);
   const int nsys = p.level_ptr[1];
   const int nfront = int(p.fronts.size());
@@ -1977,7 +2061,7 @@ int h2sp_export_front(h2sp_handle *h, int32_t k, int64_t *f, int64_t *sz, double
   if (f) *f = F.f;
   if (sz) *sz = F.s;
   if (!vals) return H2SP_OK;
-  if (!h->device_ready || h->prec < 0) return H2SP_ESTATE;
+  if (!h->device_ready || h->prec < 0 || h->ilut) return H2SP_ESTATE;
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   try {
     const size_t esz = h->prec == H2SP_FP32 ? sizeof(float) : sizeof(double);

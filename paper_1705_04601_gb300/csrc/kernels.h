@@ -46,6 +46,35 @@ inline int device_sms() {
   return n;
 }
 
+// Grid of a persistent launch over n work items: the CTAs of `fn` (threads,
+// dynamic shared memory) that are resident at once on the current device
+// (occupancy x SMs, cached per kernel, device and launch shape), at most n.
+inline unsigned persistent_grid(const void *fn, int threads, size_t smem, int n) {
+  static std::mutex mu;
+  static std::map<std::pair<std::pair<const void *, int>, std::pair<int, size_t>>, int> cache;
+  int dev = 0;
+  if (n <= 0) return 1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return unsigned(n);
+  int per = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_pair(std::make_pair(fn, dev), std::make_pair(threads, smem));
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      per = it->second;
+    } else {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        per = 1;
+      }
+      per = per > 0 ? per : 1;
+      cache[key] = per;
+    }
+  }
+  const long long g = (long long)per * device_sms();
+  return unsigned(g < n ? g : n);
+}
+
 // ---- sparsification (sparsify.cu).  Householder completions and stacked
 // bases are FP64; the products that land in S (and in the level buffers that
 // feed it) use W = double, or float for an FP32 S.
@@ -273,6 +302,40 @@ struct DeviceMaps {
 // structure arrays; host copies into *out, device level maps into *maps
 // (either may be null).  Synchronous; returns an h2sp_status.
 int device_schedule(const Plan &p, A1Result *out, DeviceMaps *maps, std::string &err);
+// the message h2sp_last_cuda_error returns (this thread)
+void set_last_error(const std::string &msg);
+
+// ---- threshold incomplete LU of S (ilut.cu) ----
+struct IlutFail {
+  int st;
+  std::string msg;
+};
+// The factors: rows in elimination order (row e is row perm[e] of S), each
+// row's kept entries at pool offset row_off: nl L entries (columns below the
+// row), then nu U entries starting with the diagonal, columns ascending.
+struct IlutState {
+  std::vector<void *> bufs;
+  bool ready = false;
+  int64_t n = 0, nnz = 0;
+  double tau = 0.0;
+  int32_t *perm = nullptr;
+  int64_t *sn_row = nullptr, *row_off = nullptr;
+  int32_t *nl = nullptr, *nu = nullptr;
+  int32_t *pool_col = nullptr;
+  double *pool_val = nullptr;
+  unsigned long long *cursor = nullptr;
+  int *err = nullptr;
+  std::vector<std::pair<int, int>> levels;  // supernodes of each elimination level
+  int grid = 1;
+  void release();
+  ~IlutState() { release(); }
+};
+// ILUt of the VBR S (values FP64, or FP32 when s_fp32) in the plan's
+// elimination order; throws IlutFail.  Synchronous.
+void ilut_factor(IlutState &st, const Plan &p, const int64_t *brow_ptr, const int32_t *bcol, const int64_t *val_off,
+                 const int64_t *node_off, const void *S, bool s_fp32, double tau, cudaStream_t s, Prof *prof);
+// y <- (L U)^-1 y in S order (ld n, nrhs columns); z: n x nrhs work
+void ilut_solve(IlutState &st, double *y, int nrhs, double *z, cudaStream_t s, Prof *prof);
 
 // out rows: non-basis -> S space (ys), basis -> next level (xn); op = Q^T.
 // T = double (the API's applies) or float (inside the FP32 preconditioner).

@@ -817,15 +817,23 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
         p.front_level_ptr.push_back(k);
     p.front_level_ptr.push_back(nsn);
 
-    // ---------------- small items first ----------------
+    // ---------------- work lists: small items first, grouped by size ----------------
     // Items whose blocks fit kMaxBlock go to the shared-memory kernels, the
     // rest to the streaming ones: each level's list keeps the small items in
-    // front (relative order kept), the row and column completions in step.
+    // front, the row and column completions in step.  Inside each part the
+    // items are grouped by (block size, rank), largest first, so that the
+    // persistent kernels walking a list with the grid's stride see items of
+    // like cost side by side and finish together.
     for (LevelWork &w : p.lw) {
       std::vector<size_t> qi(w.q.size());
       for (size_t i = 0; i < qi.size(); ++i) qi[i] = i;
       auto qsmall = std::stable_partition(qi.begin(), qi.end(), [&](size_t i) { return w.q[i].m <= kMaxBlock; });
       w.nq_small = int(qsmall - qi.begin());
+      auto by_size_q = [&](size_t a, size_t b) {
+        return w.q[a].m != w.q[b].m ? w.q[a].m > w.q[b].m : w.q[a].k > w.q[b].k;
+      };
+      std::stable_sort(qi.begin(), qsmall, by_size_q);
+      std::stable_sort(qsmall, qi.end(), by_size_q);
       std::vector<QItem> q2, qc2;
       for (size_t i : qi) {
         q2.push_back(w.q[i]);
@@ -837,6 +845,16 @@ int build_plan(const h2sp_h2_desc *d, Plan &p, std::string &err, bool need_numbe
         return it.rows <= kMaxBlock && it.cols <= kMaxBlock;
       });
       w.nx_small = int(xsmall - w.x.begin());
+      auto by_size_x = [](const XItem &a, const XItem &b) {
+        const int64_t ca = int64_t(a.rows) * a.cols, cb = int64_t(b.rows) * b.cols;
+        return ca != cb ? ca > cb : a.rows > b.rows;
+      };
+      std::stable_sort(w.x.begin(), xsmall, by_size_x);
+      std::stable_sort(xsmall, w.x.end(), by_size_x);
+      std::stable_sort(w.c.begin(), w.c.end(), [](const CItem &a, const CItem &b) {
+        const int64_t ca = int64_t(a.kp_p) * a.kp_q, cb = int64_t(b.kp_p) * b.kp_q;
+        return ca != cb ? ca > cb : a.k_p > b.k_p;
+      });
     }
 
     // ---------------- bounds audit of every work item ----------------

@@ -50,11 +50,13 @@ __device__ double block_sum(double v, double *red) {
 
 // Householder QR of W (m x k) with LAPACK's conventions and the square
 // completion Q = H_0 H_1 ... H_{k'-1} I_m.
-__global__ void __launch_bounds__(kThreads) k_householder(const QItem *__restrict__ items,
+__global__ void __launch_bounds__(kThreads) k_householder(const QItem *__restrict__ items, int n_items,
                                                           const double *__restrict__ w_in,
                                                           const double *__restrict__ w_buf,
                                                           double *__restrict__ Qout, double *__restrict__ Rout) {
-  const QItem it = items[blockIdx.x];
+  // persistent: each CTA walks the work list with a stride of the grid
+  for (int ib = blockIdx.x; ib < n_items; ib += gridDim.x) {
+  const QItem it = items[ib];
   const int m = it.m, k = it.k, kp = min(m, k);
   extern __shared__ double sm[];
   double *A = sm;              // m x k, ld m
@@ -125,17 +127,21 @@ __global__ void __launch_bounds__(kThreads) k_householder(const QItem *__restric
   }
   double *Qg = Qout + it.q;
   for (int i = tid; i < m * m; i += nt) Qg[i] = Q[i];
+  __syncthreads();  // shared memory is reused by the next item
+  }
 }
 
 // k_householder for m > kMaxBlock: the same reflectors and completion, with W
 // (m x k) in shared memory and Q formed in place in its global output.  Each
 // column of Q is updated by one warp per reflector; the CTA barrier between
 // reflectors orders the global writes.
-__global__ void __launch_bounds__(kThreads) k_householder_large(const QItem *__restrict__ items,
+__global__ void __launch_bounds__(kThreads) k_householder_large(const QItem *__restrict__ items, int n_items,
                                                                 const double *__restrict__ w_in,
                                                                 const double *__restrict__ w_buf,
                                                                 double *__restrict__ Qout, double *__restrict__ Rout) {
-  const QItem it = items[blockIdx.x];
+  // persistent: each CTA walks the work list with a stride of the grid
+  for (int ib = blockIdx.x; ib < n_items; ib += gridDim.x) {
+  const QItem it = items[ib];
   const int m = it.m, k = it.k, kp = min(m, k);
   extern __shared__ double sm[];
   double *A = sm;              // m x k, ld m
@@ -204,12 +210,16 @@ __global__ void __launch_bounds__(kThreads) k_householder_large(const QItem *__r
     }
     __syncthreads();
   }
+  __syncthreads();  // shared memory is reused by the next item
+  }
 }
 
 // rows [off_c, off_c + kp_c) of W_parent = Rr_c (kp_c x k_c) * T_c (k_c x k_p)
-__global__ void __launch_bounds__(kThreads) k_stack_w(const WItem *__restrict__ items, const double *__restrict__ Rr,
+__global__ void __launch_bounds__(kThreads) k_stack_w(const WItem *__restrict__ items, int n_items, const double *__restrict__ Rr,
                                                       const double *__restrict__ Tr, double *__restrict__ W) {
-  const WItem it = items[blockIdx.x];
+  // persistent: each CTA walks the work list with a stride of the grid
+  for (int ib = blockIdx.x; ib < n_items; ib += gridDim.x) {
+  const WItem it = items[ib];
   const double *R = Rr + it.rr_c;
   const double *T = Tr + it.t_c;
   double *out = W + it.w_dst;
@@ -219,14 +229,18 @@ __global__ void __launch_bounds__(kThreads) k_stack_w(const WItem *__restrict__ 
     for (int q = 0; q < it.k_c; ++q) acc += R[r + q * it.kp_c] * T[q + c * it.k_c];
     out[r + int64_t(c) * it.ld_w] = acc;
   }
+  __syncthreads();  // shared memory is reused by the next item
+  }
 }
 
 // F = Rr_p (kp_p x k_p) * D (k_p x k_q) * Rrc_q^T (k_q x kp_q)
 template <typename W>
-__global__ void __launch_bounds__(kThreads) k_coupling(const CItem *__restrict__ items, const double *__restrict__ Rr,
+__global__ void __launch_bounds__(kThreads) k_coupling(const CItem *__restrict__ items, int n_items, const double *__restrict__ Rr,
                                                        const double *__restrict__ Rrc, const double *__restrict__ Dc,
                                                        W *const *__restrict__ dst_base) {
-  const CItem it = items[blockIdx.x];
+  // persistent: each CTA walks the work list with a stride of the grid
+  for (int ib = blockIdx.x; ib < n_items; ib += gridDim.x) {
+  const CItem it = items[ib];
   extern __shared__ double sm[];
   const int kpp = it.kp_p, kpn = it.k_p, kqq = it.kp_q, kqn = it.k_q;
   double *sD = sm;                  // kpn x kqn
@@ -255,6 +269,8 @@ __global__ void __launch_bounds__(kThreads) k_coupling(const CItem *__restrict__
     for (int q = 0; q < kpn; ++q) acc += sRp[r + q * kpp] * sT[q + c * kpn];
     out[r + int64_t(c) * it.ld] = W(acc);
   }
+  __syncthreads();  // shared memory is reused by the next item
+  }
 }
 
 // W is the arithmetic and storage type of the close blocks and cross-level
@@ -262,11 +278,13 @@ __global__ void __launch_bounds__(kThreads) k_coupling(const CItem *__restrict__
 // mixed-precision path.  src_base[0] is the FP64 close-block input and
 // src_base[1..3] level buffers of type W; Q is FP64 and rounded to W on load.
 template <typename W>
-__global__ void __launch_bounds__(kThreads) k_transform(const XItem *__restrict__ items,
+__global__ void __launch_bounds__(kThreads) k_transform(const XItem *__restrict__ items, int n_items,
                                                         const void *const *__restrict__ src_base,
                                                         const double *__restrict__ Qrow, const double *__restrict__ Qcol,
                                                         W *const *__restrict__ dst_base) {
-  const XItem it = items[blockIdx.x];
+  // persistent: each CTA walks the work list with a stride of the grid
+  for (int ib = blockIdx.x; ib < n_items; ib += gridDim.x) {
+  const XItem it = items[ib];
   const int rows = it.rows, cols = it.cols;
   extern __shared__ __align__(16) unsigned char smraw_t[];
   W *X = reinterpret_cast<W *>(smraw_t);  // rows x cols, ld rows
@@ -327,6 +345,8 @@ __global__ void __launch_bounds__(kThreads) k_transform(const XItem *__restrict_
       out[r + int64_t(c) * ld] = cur[(r0 + r) + (c0 + c) * rows];
     }
   }
+  __syncthreads();  // shared memory is reused by the next item
+  }
 }
 
 // k_transform for blocks above kMaxBlock rows or columns: Y = QL^T X QR by
@@ -345,13 +365,15 @@ constexpr int kKc = 8;
 constexpr int kTrMax = kMaxLargeBlock / 32;  // row groups per thread
 
 template <typename W>
-__global__ void __launch_bounds__(kThreads) k_transform_large(const XItem *__restrict__ items,
+__global__ void __launch_bounds__(kThreads) k_transform_large(const XItem *__restrict__ items, int n_items,
                                                               const void *const *__restrict__ src_base,
                                                               const double *__restrict__ Qrow,
                                                               const double *__restrict__ Qcol,
                                                               W *const *__restrict__ dst_base) {
   static_assert(kThreads == 256 && kSlab == 32, "thread grid of the tiles");
-  const XItem it = items[blockIdx.x];
+  // persistent: each CTA walks the work list with a stride of the grid
+  for (int ib = blockIdx.x; ib < n_items; ib += gridDim.x) {
+  const XItem it = items[ib];
   const int rows = it.rows, cols = it.cols;
   const int nti = (rows + 31) / 32;  // row groups in use
   extern __shared__ __align__(16) unsigned char smraw_l[];
@@ -483,6 +505,8 @@ __global__ void __launch_bounds__(kThreads) k_transform_large(const XItem *__res
     }
     __syncthreads();  // sT is rewritten by the next slab
   }
+  __syncthreads();  // shared memory is reused by the next item
+  }
 }
 
 }  // namespace
@@ -493,7 +517,7 @@ cudaError_t launch_householder(const QItem *items, int n, const double *w_in, co
   size_t smem = sizeof(double) * (size_t(max_m) * max_k + size_t(max_m) * max_m + kMaxRank + 1 + 64);
   if (cudaError_t ea = smem_attr((const void *)k_householder, int(smem)); ea != cudaSuccess) return ea;
   const size_t e0 = prof->begin();
-  k_householder<<<n, kThreads, smem, s>>>(items, w_in, w_buf, Q, Rr);
+  k_householder<<<persistent_grid((const void *)k_householder, kThreads, smem, n), kThreads, smem, s>>>(items, n, w_in, w_buf, Q, Rr);
   prof->end(P_HOUSEHOLDER, 1, e0, 0.0);
   return cudaGetLastError();
 }
@@ -504,7 +528,7 @@ cudaError_t launch_householder_large(const QItem *items, int n, const double *w_
   const size_t smem = sizeof(double) * (size_t(max_m) * max_k + kMaxRank + 1 + 64);
   if (cudaError_t ea = smem_attr((const void *)k_householder_large, int(smem)); ea != cudaSuccess) return ea;
   const size_t e0 = prof->begin();
-  k_householder_large<<<n, kThreads, smem, s>>>(items, w_in, w_buf, Q, Rr);
+  k_householder_large<<<persistent_grid((const void *)k_householder_large, kThreads, smem, n), kThreads, smem, s>>>(items, n, w_in, w_buf, Q, Rr);
   prof->end(P_HOUSEHOLDER, 1, e0, 0.0);
   return cudaGetLastError();
 }
@@ -513,7 +537,7 @@ cudaError_t launch_stack_w(const WItem *items, int n, const double *Rr, const do
                            Prof *prof) {
   if (n == 0) return cudaSuccess;
   const size_t e0 = prof->begin();
-  k_stack_w<<<n, 64, 0, s>>>(items, Rr, T, W);
+  k_stack_w<<<persistent_grid((const void *)k_stack_w, 64, 0, n), 64, 0, s>>>(items, n, Rr, T, W);
   prof->end(P_COUPLING, 1, e0, 0.0);
   return cudaGetLastError();
 }
@@ -525,7 +549,7 @@ cudaError_t launch_coupling(const CItem *items, int n, const double *Rr, const d
   size_t smem = sizeof(double) * 4 * size_t(max_k) * max_k;
   if (cudaError_t ea = smem_attr((const void *)k_coupling<W>, int(smem)); ea != cudaSuccess) return ea;
   const size_t e0 = prof->begin();
-  k_coupling<W><<<n, 128, smem, s>>>(items, Rr, Rrc, Dc, dst_base);
+  k_coupling<W><<<persistent_grid((const void *)k_coupling<W>, 128, smem, n), 128, smem, s>>>(items, n, Rr, Rrc, Dc, dst_base);
   prof->end(P_COUPLING, 1, e0, 0.0);
   return cudaGetLastError();
 }
@@ -537,7 +561,7 @@ cudaError_t launch_transform(const XItem *items, int n, const void *const *src_b
   size_t smem = sizeof(W) * 3 * size_t(kMaxBlock) * kMaxBlock;
   if (cudaError_t ea = smem_attr((const void *)k_transform<W>, int(smem)); ea != cudaSuccess) return ea;
   const size_t e0 = prof->begin();
-  k_transform<W><<<n, kThreads, smem, s>>>(items, src_base, Qrow, Qcol, dst_base);
+  k_transform<W><<<persistent_grid((const void *)k_transform<W>, kThreads, smem, n), kThreads, smem, s>>>(items, n, src_base, Qrow, Qcol, dst_base);
   prof->end(P_TRANSFORM, 1, e0, flops);
   return cudaGetLastError();
 }
@@ -551,7 +575,7 @@ cudaError_t launch_transform_large(const XItem *items, int n, const void *const 
   (void)max_cols;
   if (cudaError_t ea = smem_attr((const void *)k_transform_large<W>, int(smem)); ea != cudaSuccess) return ea;
   const size_t e0 = prof->begin();
-  k_transform_large<W><<<n, kThreads, smem, s>>>(items, src_base, Qrow, Qcol, dst_base);
+  k_transform_large<W><<<persistent_grid((const void *)k_transform_large<W>, kThreads, smem, n), kThreads, smem, s>>>(items, n, src_base, Qrow, Qcol, dst_base);
   prof->end(P_TRANSFORM, 1, e0, flops);
   return cudaGetLastError();
 }

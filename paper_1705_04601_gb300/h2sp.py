@@ -93,6 +93,12 @@ SIGNATURES = {
     "h2sp_export_structure": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i64p]),
     "h2sp_export_schedule": (ctypes.c_int, [_vp, _i32p, _i64p, _i64p, _i64p, _i64p, _i64p, _i32p]),
     "h2sp_export_near": (ctypes.c_int, [_vp, ctypes.c_int32, _i64p, _i32p, _i64p]),
+    "h2sp_construct": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp)]),
+    "h2sp_factor_ilut": (ctypes.c_int, [_vp, ctypes.c_double, _vp]),
+    "h2sp_export_ilut": (ctypes.c_int, [_vp, _i32p, _i64p, _i32p, _f64p, _i64p, _i32p, _f64p, _i64p, _i64p]),
+    "h2sp_h2_describe": (ctypes.c_int, [_vp, _vp]),
+    "h2sp_h2_copy": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _i64p, _vp]),
+    "h2sp_h2_destroy": (None, [_vp]),
     "h2sp_export_front": (ctypes.c_int, [_vp, ctypes.c_int32, _i64p, _i64p, _f64p, _vp]),
     "h2sp_measure_peak": (ctypes.c_int, [ctypes.c_int32, _f64p, _vp]),
     "h2sp_set_option": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int64]),
@@ -215,6 +221,85 @@ class H2Input:
             t = self.dev.get(nm)
             setattr(d, nm, t.data_ptr() if t is not None else self.host_ptrs.get(nm))
         return d
+
+
+class ConstructDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("dim", ctypes.c_int32), ("depth", ctypes.c_int32),
+                ("level_ptr", _i32p), ("parent", _i32p), ("begin", _i64p), ("size", _i64p),
+                ("box_lo", _f64p), ("box_hi", _f64p), ("far_ptr", _i64p), ("far_col", _i32p),
+                ("near_ptr", _i64p), ("near_col", _i32p), ("points", _vp), ("kernel", ctypes.c_int32),
+                ("diag", ctypes.c_double), ("order", ctypes.c_int32), ("tol", ctypes.c_double)]
+
+
+KERNEL_IDS = {"log": 0, "inv": 1, "yukawa": 2, "gauss": 3}
+
+
+class Constructed:
+    """An H^2 matrix built on the GPU by h2sp_construct; owns its arrays.
+    Serves as the input of h2sp_analyze / h2sp_sparsify (``desc()``)."""
+
+    def __init__(self, ptr: _vp, n: int, depth: int, ncl: int):
+        self.ptr = ptr
+        self.n, self.depth, self.ncl = n, depth, ncl
+        self.h = self  # the entry points read .h.n
+
+    def desc(self) -> "Desc":
+        d = Desc()
+        _check(lib().h2sp_h2_describe(self.ptr, ctypes.byref(d)), "h2sp_h2_describe")
+        return d
+
+    def copy(self, which: int) -> np.ndarray:
+        """Host copy of numeric array `which` (0 leaf_basis, 1 transfer, 2 coupling, 3 near_block)."""
+        cnt = ctypes.c_int64(0)
+        _check(lib().h2sp_h2_copy(self.ptr, int(which), None, ctypes.byref(cnt), _vp(None)), "h2sp_h2_copy")
+        out = np.zeros(max(cnt.value, 1), np.float64)
+        _check(lib().h2sp_h2_copy(self.ptr, int(which), _vp(out.ctypes.data), ctypes.byref(cnt), _vp(None)),
+               "h2sp_h2_copy")
+        return out[:cnt.value]
+
+    def close(self):
+        if self.ptr is not None and self.ptr.value:
+            lib().h2sp_h2_destroy(self.ptr)
+        self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def h2sp_construct(tree: dict, points, kernel: str, diag: float, order: int = 4, tol: float = 0.0,
+                   stream=None) -> Constructed:
+    """Build the H^2 matrix of `kernel` on the GPU.  `tree`: host arrays
+    level_ptr, parent, begin, size, box_lo, box_hi (ncl x dim), far_ptr,
+    far_col, near_ptr, near_col and the depth; `points`: a CUDA float64 tensor
+    (n x dim) in tree order."""
+    c = np.ascontiguousarray
+    keep = dict(level_ptr=c(tree["level_ptr"], np.int32), parent=c(tree["parent"], np.int32),
+                begin=c(tree["begin"], np.int64), size=c(tree["size"], np.int64),
+                box_lo=c(tree["box_lo"], np.float64), box_hi=c(tree["box_hi"], np.float64),
+                far_ptr=c(tree["far_ptr"], np.int64), far_col=c(tree["far_col"], np.int32),
+                near_ptr=c(tree["near_ptr"], np.int64), near_col=c(tree["near_col"], np.int32))
+    d = ConstructDesc()
+    d.n = int(points.shape[0])
+    d.dim = int(points.shape[1])
+    d.depth = int(tree["depth"])
+    for nm in ("level_ptr", "parent", "far_col", "near_col"):
+        setattr(d, nm, _ptr(keep[nm], ctypes.c_int32))
+    for nm in ("begin", "size", "far_ptr", "near_ptr"):
+        setattr(d, nm, _ptr(keep[nm], ctypes.c_int64))
+    for nm in ("box_lo", "box_hi"):
+        setattr(d, nm, _ptr(keep[nm], ctypes.c_double))
+    pts = points.contiguous()
+    d.points = _vp(pts.data_ptr())
+    d.kernel = KERNEL_IDS[kernel]
+    d.diag = float(diag)
+    d.order = int(order)
+    d.tol = float(tol)
+    out = _vp()
+    _check(lib().h2sp_construct(ctypes.byref(d), _stream(stream), ctypes.byref(out)), "h2sp_construct")
+    return Constructed(out, d.n, d.depth, int(keep["parent"].size))
 
 
 class Handle:
@@ -444,6 +529,30 @@ def h2sp_export_near(h: Handle, level: int, nrows: int) -> tuple:
     _check(lib().h2sp_export_near(h.ptr, int(level), _ptr(ptr, ctypes.c_int64), _ptr(col, ctypes.c_int32),
                                   ctypes.byref(nnz)), "h2sp_export_near")
     return ptr, col[:nnz.value]
+
+
+def h2sp_factor_ilut(h: Handle, tau: float, stream=None):
+    """Threshold incomplete LU of S (ILUt, drop tolerance tau)."""
+    _check(lib().h2sp_factor_ilut(h.ptr, float(tau), _stream(stream)), "h2sp_factor_ilut")
+
+
+def h2sp_export_ilut(h: Handle) -> dict:
+    """The incomplete factors: perm, and L / U as CSR in elimination order."""
+    n = int(h.inp.h.n)
+    nl, nu = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().h2sp_export_ilut(h.ptr, None, None, None, None, None, None, None, ctypes.byref(nl),
+                                  ctypes.byref(nu)), "h2sp_export_ilut")
+    out = dict(perm=np.zeros(n, np.int32), l_ptr=np.zeros(n + 1, np.int64), l_col=np.zeros(max(nl.value, 1), np.int32),
+               l_val=np.zeros(max(nl.value, 1)), u_ptr=np.zeros(n + 1, np.int64),
+               u_col=np.zeros(max(nu.value, 1), np.int32), u_val=np.zeros(max(nu.value, 1)))
+    _check(lib().h2sp_export_ilut(h.ptr, _ptr(out["perm"], ctypes.c_int32), _ptr(out["l_ptr"], ctypes.c_int64),
+                                  _ptr(out["l_col"], ctypes.c_int32), _ptr(out["l_val"], ctypes.c_double),
+                                  _ptr(out["u_ptr"], ctypes.c_int64), _ptr(out["u_col"], ctypes.c_int32),
+                                  _ptr(out["u_val"], ctypes.c_double), ctypes.byref(nl), ctypes.byref(nu)),
+           "h2sp_export_ilut")
+    for k, m in (("l_col", nl.value), ("l_val", nl.value), ("u_col", nu.value), ("u_val", nu.value)):
+        out[k] = out[k][:m]
+    return out
 
 
 def h2sp_profile(h: Handle, timing: int = -1, reset: bool = False) -> dict:

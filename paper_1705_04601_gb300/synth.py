@@ -655,6 +655,47 @@ def build_h2(points: np.ndarray, kernel: str, leaf_size: int, p: int = 4, tol: O
     return h
 
 
+def tree_arrays(points: np.ndarray, leaf_size: int, lo=None, hi=None) -> tuple[dict, np.ndarray]:
+    """The cluster tree and the close / admissible lists build_h2 uses, as the
+    host arrays of a GPU construction (boxes, CSR lists), and the points in
+    tree order."""
+    n, dim = points.shape
+    lo = np.zeros(dim) if lo is None else np.asarray(lo, float)
+    hi = np.ones(dim) if hi is None else np.asarray(hi, float)
+    tree = build_tree(points, leaf_size, lo, hi)
+    D = tree.depth
+    lp = tree.level_ptr
+    ncl = tree.parent.shape[0]
+    near, far = block_lists(tree)
+    far_ptr = np.zeros(ncl + 1, dtype=np.int64)
+    np.add.at(far_ptr, far[:, 0] + 1, 1)
+    nleaf = int(lp[D + 1] - lp[D])
+    near_ptr = np.zeros(nleaf + 1, dtype=np.int64)
+    np.add.at(near_ptr, near[:, 0] - lp[D] + 1, 1)
+    t = dict(depth=D, level_ptr=lp.astype(np.int32), parent=tree.parent.astype(np.int32),
+             begin=tree.begin.astype(np.int64), size=tree.size.astype(np.int64),
+             box_lo=np.ascontiguousarray(tree.box_lo, np.float64), box_hi=np.ascontiguousarray(tree.box_hi, np.float64),
+             far_ptr=np.cumsum(far_ptr).astype(np.int64), far_col=far[:, 1].astype(np.int32),
+             near_ptr=np.cumsum(near_ptr).astype(np.int64), near_col=near[:, 1].astype(np.int32))
+    return t, np.ascontiguousarray(points[tree.perm])
+
+
+def workload_points(name: str, n: Optional[int] = None, seed: Optional[int] = None):
+    """(points, lo, hi, config) of a named single-system workload: the same
+    seeded points make_workload builds its H^2 matrix from."""
+    cfg = dict(WORKLOADS[name])
+    if n is not None:
+        cfg["n"] = n
+    rng = np.random.default_rng(SEED_BASE + cfg["index"] if seed is None else seed)
+    if cfg.get("points", "uniform") == "sphere":
+        pts = points_sphere_fibonacci(cfg["n"], rng)
+        lo, hi = np.full(3, -1.01), np.full(3, 1.01)
+    else:
+        pts = points_uniform(cfg["n"], cfg["dim"], rng)
+        lo, hi = np.zeros(cfg["dim"]), np.ones(cfg["dim"])
+    return pts, lo, hi, cfg
+
+
 # --------------------------------------------------------------------------
 # named workloads
 # --------------------------------------------------------------------------

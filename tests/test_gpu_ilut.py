@@ -1,0 +1,137 @@
+"""GPU threshold incomplete LU of S (h2sp_factor_ilut) against the oracle's
+ILUt (§5.5) with the same drop rule and elimination order: the factors
+entry by entry, the exact LU at tau = 0, and GMRES on the H^2 product
+preconditioned by the incomplete factors on the paper's example."""
+import numpy as np
+import pytest
+
+from paper_1705_04601_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1705_04601_gb300 import h2sp as H  # noqa: E402
+from oracle import h2 as oh2  # noqa: E402
+from oracle import ilu as oilu  # noqa: E402
+from oracle import iterate as oit  # noqa: E402
+from oracle import sparsify as osp  # noqa: E402
+
+_CASES = {
+    "log1k": dict(n=1024, kernel="log", leaf=32, tol=1e-8, seed=1),
+    "gauss1k": dict(n=1024, kernel="gauss", leaf=32, tol=1e-8, seed=4),
+    "ifmm_d1e-3": dict(n=1500, kernel="ifmm_d1e-3", leaf=40, tol=1e-6, seed=12, dim=3),
+    "ifmm_d1e-2": dict(n=1500, kernel="ifmm_d1e-2", leaf=40, tol=1e-6, seed=12, dim=3),
+}
+_cache = {}
+
+
+def case(name):
+    if name not in _cache:
+        c = _CASES[name]
+        h, b = synth.make_small(c["n"], kernel=c["kernel"], leaf=c["leaf"], tol=c["tol"], seed=c["seed"],
+                                dim=c.get("dim", 2), nrhs=1)
+        _cache[name] = (h, b, osp.sparsify(h))
+    return _cache[name]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1705_04601_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA is required for the gpu tests")
+
+
+def dense_factors(ex, n):
+    L = np.eye(n)
+    U = np.zeros((n, n))
+    for i in range(n):
+        a, b = ex["l_ptr"][i], ex["l_ptr"][i + 1]
+        L[i, ex["l_col"][a:b]] = ex["l_val"][a:b]
+        a, b = ex["u_ptr"][i], ex["u_ptr"][i + 1]
+        U[i, ex["u_col"][a:b]] = ex["u_val"][a:b]
+        assert ex["u_col"][a] == i  # the diagonal leads its row
+        assert np.all(np.diff(ex["u_col"][a:b]) > 0) and np.all(ex["l_col"][ex["l_ptr"][i]:ex["l_ptr"][i + 1]] < i)
+    return L, U
+
+
+@pytest.mark.parametrize("name,tau", [("log1k", 0.0), ("log1k", 1e-3), ("gauss1k", 1e-2), ("ifmm_d1e-3", 1e-2),
+                                      ("ifmm_d1e-2", 2e-2)])
+def test_ilut_factors_match_oracle(name, tau):
+    h, b, sp = case(name)
+    fa = oilu.factor_ilut(h, sp, tau)
+    hd = H.h2sp_sparsify(H.H2Input(h))
+    H.h2sp_factor_ilut(hd, tau)
+    ex = H.h2sp_export_ilut(hd)
+    assert np.array_equal(ex["perm"], fa.perm)
+    L, U = dense_factors(ex, h.n)
+    # the same kept entries (the drop decisions are taken in FP64 on both sides)
+    assert np.array_equal(L != 0, fa.L != 0) or tau == 0.0
+    assert np.array_equal(U != 0, fa.U != 0) or tau == 0.0
+    assert np.linalg.norm(L - fa.L) <= 1e-10 * np.linalg.norm(fa.L)
+    assert np.linalg.norm(U - fa.U) <= 1e-10 * np.linalg.norm(fa.U)
+    q = H.h2sp_query(hd)
+    assert q["factor_prec"] == H.H2SP_FP64
+    hd.close()
+
+
+def test_ilut_at_tau0_is_the_exact_lu_and_solves():
+    h, b, sp = case("log1k")
+    hd = H.h2sp_sparsify(H.H2Input(h))
+    H.h2sp_factor_ilut(hd, 0.0)
+    bt = torch.from_numpy(np.ascontiguousarray(b.T)).cuda()
+    xt = torch.empty_like(bt)
+    H.h2sp_solve(hd, bt, xt, mode=H.H2SP_DIRECT)
+    torch.cuda.synchronize()
+    xd = np.linalg.solve(oh2.dense(h), b)
+    assert np.linalg.norm(xt.cpu().numpy().T - xd) <= 1e-9 * np.linalg.norm(xd)
+    # the other factor-bound calls wait for a block factorization
+    with pytest.raises(H.H2spError) as e:
+        H.h2sp_logdet(hd)
+    assert e.value.status == H.H2SP_ESTATE
+    H.h2sp_factor(hd, H.H2SP_FP64)
+    H.h2sp_logdet(hd)
+    with pytest.raises(H.H2spError) as e:
+        H.h2sp_export_ilut(hd)
+    assert e.value.status == H.H2SP_ESTATE
+    hd.close()
+
+
+@pytest.mark.parametrize("name", ["ifmm_d1e-3", "ifmm_d1e-2"])
+@pytest.mark.parametrize("tau", [1e-2, 2e-2])
+def test_ilut_preconditions_gmres_like_the_oracle(name, tau):
+    """§5.5's example: GMRES on the FP64 H^2 product, right-preconditioned by
+    V (L U)^{-1} U^T, reaches 1e-10; the step count is the oracle's (the same
+    preconditioner up to rounding) within a step or two."""
+    h, b, sp = case(name)
+    fa = oilu.factor_ilut(h, sp, tau)
+    mv = oh2.Matvec(h)
+    cnt = [0]
+
+    def pre(v):
+        cnt[0] += 1
+        return oilu.precondition(h, sp, fa, v)
+
+    xo, _ = oit.gmres(mv, pre, b[:, 0], tol=1e-10, restart=30, maxit=300)
+    hd = H.h2sp_sparsify(H.H2Input(h))
+    H.h2sp_factor_ilut(hd, tau)
+    bt = torch.from_numpy(np.ascontiguousarray(b.T)).cuda()
+    xt = torch.zeros_like(bt)
+    info = H.h2sp_solve(hd, bt, xt, mode=H.H2SP_GMRES, tol=1e-10, maxit=300, restart=30)
+    torch.cuda.synchronize()
+    print("%s tau %.0e: GMRES steps GPU %d, oracle %d" % (name, tau, info.iters, cnt[0]))
+    assert info.status == H.H2SP_OK and info.rel_residual <= 1e-10
+    x = xt.cpu().numpy().T
+    assert np.linalg.norm(b - mv(x)) / np.linalg.norm(b) <= 2e-10
+    assert abs(info.iters - cnt[0]) <= max(2, cnt[0] // 5)
+    hd.close()
+
+
+def test_ilut_rejects_bad_tau():
+    h, b, sp = case("log1k")
+    hd = H.h2sp_sparsify(H.H2Input(h))
+    for bad in (-1.0, float("nan"), float("inf")):
+        with pytest.raises(H.H2spError) as e:
+            H.h2sp_factor_ilut(hd, bad)
+        assert e.value.status == H.H2SP_EINVAL
+    hd.close()
