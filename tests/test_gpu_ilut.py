@@ -55,11 +55,14 @@ def dense_factors(ex, n):
     return L, U
 
 
-# (case, tau, elementwise bar).  The -log r case has an indefinite S: its LU
-# without pivoting has |L| ~ 2e3 and |U| ~ 1e4 and amplifies the rounding-order
-# differences between the two sides (fused multiply-adds on the GPU) to about
-# 1e-9 of |L|, so its bar is 1e-8 with the backward error |L U - A| checked at
-# FP64 level; the SPD and the §5.5 cases keep 1e-10.
+# (case, tau, elementwise bar).  The -log r case has an indefinite S: its
+# elimination without pivoting amplifies rounding-order differences (fused
+# multiply-adds on the GPU).  Its bar is the larger of 1e-8 and four times the
+# oracle's own change when S is perturbed by one rounding (1e-16 relative):
+# at tau = 1e-3 the incomplete factors have pivots down to 1.3e-6 of the
+# largest, and that change is 2e-5.  The exact LU (tau = 0) also has its
+# backward error |L U - A| checked at FP64 level; the SPD and the §5.5 cases
+# keep 1e-10.
 @pytest.mark.parametrize("name,tau,bar", [("log1k", 0.0, 1e-8), ("log1k", 1e-3, 1e-8), ("gauss1k", 1e-2, 1e-10),
                                           ("ifmm_d1e-3", 1e-2, 1e-10), ("ifmm_d1e-2", 2e-2, 1e-10)])
 def test_ilut_factors_match_oracle(name, tau, bar):
@@ -76,7 +79,13 @@ def test_ilut_factors_match_oracle(name, tau, bar):
         assert np.array_equal(U != 0, fa.U != 0)
     dl = np.linalg.norm(L - fa.L) / np.linalg.norm(fa.L)
     du = np.linalg.norm(U - fa.U) / np.linalg.norm(fa.U)
-    print("%s tau %.0e: L %.1e, U %.1e from the oracle" % (name, tau, dl, du))
+    if name == "log1k":
+        # the oracle's sensitivity to one rounding of S
+        Ap = osp.dense_S(sp)[np.ix_(fa.perm, fa.perm)]
+        Lq, Uq = oilu.ilut(Ap * (1.0 + 1e-16 * np.random.default_rng(0).standard_normal(Ap.shape)), tau)
+        sens = max(np.linalg.norm(Lq - fa.L) / np.linalg.norm(fa.L), np.linalg.norm(Uq - fa.U) / np.linalg.norm(fa.U))
+        bar = max(bar, 4.0 * sens)
+    print("%s tau %.0e: L %.1e, U %.1e from the oracle (bar %.1e)" % (name, tau, dl, du, bar))
     assert dl <= bar and du <= bar
     if tau == 0.0:
         Ap = osp.dense_S(sp)[np.ix_(fa.perm, fa.perm)]
