@@ -609,10 +609,14 @@ enum {
    * let the panel stream reach the SMs sooner.  PANEL_SMS: SMs that update
    * leaves to the panel stream (-1, the default: one per front of the
    * level).  LOOKAHEAD: 1 (default) factors the next block's panels on a
-   * high-priority stream while the rest of the update runs, 0 serialises. */
+   * high-priority stream while the rest of the update runs, 0 serialises.
+   * WIDE: 1 (default) takes the TF32 block-end update in 128 x 256 output
+   * tiles (one N = 256 MMA over two packed column tiles: a quarter fewer
+   * operand bytes per product), 0 in 128 x 128 tiles. */
   H2SP_OPTION_CHOL_TILES_PER_CTA = 3,
   H2SP_OPTION_CHOL_PANEL_SMS = 4,
-  H2SP_OPTION_CHOL_LOOKAHEAD = 5
+  H2SP_OPTION_CHOL_LOOKAHEAD = 5,
+  H2SP_OPTION_CHOL_WIDE = 6
 };
 
 /*

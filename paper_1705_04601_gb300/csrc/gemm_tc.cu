@@ -1051,6 +1051,295 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(2 * kTcN)));
 }
 
+// ---- the block-end update of the block Cholesky with 128 x 256 output tiles ----
+// The same lower-triangle update C -= L21 L21^T (three-term TF32 products) as
+// k_gemm_tc_ws, with the column tiles taken in pairs: one kind::tf32 MMA of
+// N = 256 per K step reads two packed 128-row tiles of L21 laid one after the
+// other in shared memory (their 8-row groups continue at the same stride), so
+// each staged byte of A serves twice the products.  A pair past the diagonal
+// tile (the last one, when the CTA's tiles are odd in number) is a single
+// tile with the N = 128 MMA.  Three 48 KB operand stages, two 256-column TMEM
+// accumulators (all 512 columns), and the C tile through TMA in 64-column
+// quarters alternating between two shared-memory buffers: quarter s + 2 is
+// requested as soon as the store of quarter s has read its buffer.  Every
+// wait is bounded, as in k_gemm_tc_ws.
+constexpr int kWdStages = 3;
+constexpr int kWdStageFloats = 6 * kPkTile;  // A hi, A lo, B hi x 2 tiles, B lo x 2 tiles: 48 KB
+constexpr uint32_t kIdescWide = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(256 >> 3) << 17) |
+                                (uint32_t(kTcM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32_i(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                           uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+}
+
+__global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_wide(const FrontDev *__restrict__ fr, int j0, int kb,
+                                                               float *__restrict__ fronts, int *__restrict__ err,
+                                                               int splits, int tile_lo, int tile_hi,
+                                                               const float *__restrict__ apack,
+                                                               const uint8_t *__restrict__ maps64) {
+  const FrontDev F = fr[blockIdx.z];
+  if (j0 >= F.s) return;
+  const int jb = min(kb, F.s - j0);
+  const int t0 = j0 + jb;
+  const int nrest = F.f - t0;
+  const int rb = blockIdx.y * kTcM;
+  if (rb >= nrest) return;
+  // column tiles [tile_lo, tend): up to the diagonal tile, taken in pairs
+  const int tend = min(min((nrest + kTcN - 1) / kTcN, tile_hi), int(blockIdx.y) + 1);
+  if (tend <= tile_lo) return;
+  const int npair = (tend - tile_lo + 1) / 2;
+  const int per = (npair + splits - 1) / splits;
+  const int p_lo = blockIdx.x * per, p_hi = min(npair, p_lo + per);
+  if (p_lo >= p_hi) return;
+  const int np = p_hi - p_lo;
+  const int nq = (jb + kPkK - 1) / kPkK;
+  const int G = np * nq;
+  auto pair_tile = [&](int i) { return tile_lo + 2 * (p_lo + i); };
+  auto pair_wide = [&](int i) { return pair_tile(i) + 1 < tend; };
+  float *A = fronts + F.off;
+  const int64_t ld = F.ld;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  float *stage0 = reinterpret_cast<float *>(smraw);
+  float *sC = stage0 + kWdStages * kWdStageFloats;  // two 128 x 64 C quarters
+  __shared__ __align__(8) uint64_t full[kWdStages], empty[kWdStages], accf[2], acce[2], cfull[2];
+  const bool use_tma = maps64 != nullptr && (t0 & 3) == 0;
+  const void *tmap = use_tma ? static_cast<const void *>(maps64 + size_t(blockIdx.z) * kTmapBytes) : nullptr;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  __shared__ volatile int s_consumed;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(uint32_t(4 * kTcN)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < kWdStages; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(1));
+    }
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&accf[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acce[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&cfull[i])), "r"(1));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+    s_consumed = 0;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const float *Ab = apack + (int64_t(F.pack_off) + blockIdx.y) * kPackTileFloats;
+  const float *Bb = apack + int64_t(F.pack_off) * kPackTileFloats;
+  constexpr uint32_t kArr = kPkTile * 4;  // one 128 x 16 hi (or lo) array: 8 KB
+
+  if (warp == kWsEpiWarps) {
+    // ---- copy producer ----
+    if (lane == 0) {
+      int issued = 0;
+      for (int g = 0; g < G; ++g) {
+        const int st = g % kWdStages, i = g / nq, q = g % nq;
+        if (g >= kWdStages) {
+          const bool w = !abort_flag && wait_phase(smem_u32(&empty[st]), uint32_t(((g - kWdStages) / kWdStages) & 1));
+          if (!w) {
+            abort_flag = 1;
+            break;
+          }
+        }
+        const int c0 = pair_tile(i);
+        const bool wide = pair_wide(i);
+        const float *a = Ab + int64_t(q) * 2 * kPkTile;
+        const float *b0 = Bb + int64_t(c0) * kPackTileFloats + int64_t(q) * 2 * kPkTile;
+        const float *b1 = b0 + kPackTileFloats;
+        const uint32_t dst = smem_u32(stage0 + st * kWdStageFloats);
+        const uint32_t mb = smem_u32(&full[st]);
+        mbar_expect_tx(mb, 2 * kArr + (wide ? 4 : 2) * kArr);
+        bulk_copy_g2s(dst, a, 2 * kArr, mb);                       // A hi, A lo
+        bulk_copy_g2s(dst + 2 * kArr, b0, kArr, mb);               // B hi, tile c0
+        if (wide) bulk_copy_g2s(dst + 3 * kArr, b1, kArr, mb);     // B hi, tile c0 + 1
+        bulk_copy_g2s(dst + 4 * kArr, b0 + kPkTile, kArr, mb);     // B lo, tile c0
+        if (wide) bulk_copy_g2s(dst + 5 * kArr, b1 + kPkTile, kArr, mb);  // B lo, tile c0 + 1
+        ++issued;
+      }
+      if (abort_flag) {
+        atomicOr(err, 4);
+        for (int g = s_consumed; g < issued; ++g)
+          wait_phase(smem_u32(&full[g % kWdStages]), uint32_t((g / kWdStages) & 1));
+      }
+    }
+  } else if (warp == kWsEpiWarps + 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      int last_mma = -1;
+      bool ok = true;
+      for (int g = 0; g < G && ok; ++g) {
+        const int st = g % kWdStages, i = g / nq, q = g % nq, a = i & 1;
+        if (abort_flag || !wait_phase(smem_u32(&full[st]), uint32_t((g / kWdStages) & 1))) {
+          ok = false;
+          break;
+        }
+        s_consumed = g + 1;
+        if (q == 0 && i >= 2 && !wait_phase(smem_u32(&acce[a]), uint32_t(((i - 2) >> 1) & 1))) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t base = smem_u32(stage0 + st * kWdStageFloats);
+        const uint32_t ah0 = base, al0 = base + kArr, bh0 = base + 2 * kArr, bl0 = base + 4 * kArr;
+        const uint32_t acc = tmem + uint32_t(a * 2 * kTcN);
+        const uint32_t idesc = pair_wide(i) ? kIdescWide : kIdesc;
+#pragma unroll
+        for (int kk = 0; kk < kPkK / 8; ++kk) {
+          const uint32_t koff = uint32_t(kk) * 2 * kLbo;
+          const uint64_t ah = smem_desc_pk(ah0 + koff), al = smem_desc_pk(al0 + koff);
+          const uint64_t bh = smem_desc_pk(bh0 + koff), bl = smem_desc_pk(bl0 + koff);
+          mma_tf32_i(acc, ah, bh, idesc, (q > 0 || kk > 0) ? 1u : 0u);
+          mma_tf32_i(acc, ah, bl, idesc, 1u);
+          mma_tf32_i(acc, al, bh, idesc, 1u);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&empty[st])));
+        last_mma = g;
+        if (q == nq - 1)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&accf[a])));
+      }
+      if (!ok) {
+        abort_flag = 1;
+        atomicOr(err, 4);
+        if (last_mma >= 0)
+          wait_phase(smem_u32(&empty[last_mma % kWdStages]), uint32_t((last_mma / kWdStages) & 1));
+      }
+    }
+  } else if (use_tma) {
+    // ---- epilogue with TMA: slot s = quarter (s & 3) of pair (s >> 2), 64 columns, buffer s & 1 ----
+    const int q4 = warp & 3, qc = warp >> 2;
+    const int row = q4 * 32 + lane;
+    const int x = t0 + rb;
+    const int nslot = 4 * (np - 1) + (pair_wide(np - 1) ? 4 : 2);
+    auto slot_col = [&](int sl) { return t0 + pair_tile(sl >> 2) * kTcN + (sl & 3) * kWsHalf; };
+    auto load_slot = [&](int sl) {
+      const uint32_t mb = smem_u32(&cfull[sl & 1]);
+      mbar_expect_tx(mb, uint32_t(kWsCFloats * 4));
+      tma_load_2d(smem_u32(sC + (sl & 1) * kWsCFloats), tmap, x, slot_col(sl), mb);
+    };
+    if (tid == 0) {
+      load_slot(0);
+      if (nslot > 1) load_slot(1);
+    }
+    int loads_issued = min(2, nslot), loads_done = 0;
+    bool ok = true;
+    for (int i = 0; i < np && ok; ++i) {
+      const int a = i & 1;
+      const bool w = !abort_flag && wait_phase(smem_u32(&accf[a]), uint32_t((i >> 1) & 1));
+      if (!epi_bar_and(w)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int nqq = pair_wide(i) ? 4 : 2;
+      for (int qq = 0; qq < nqq; ++qq) {
+        const int sl = 4 * i + qq, buf = sl & 1;
+        const bool wc = !abort_flag && wait_phase(smem_u32(&cfull[buf]), uint32_t((sl >> 1) & 1));
+        if (!epi_bar_and(wc)) {
+          ok = false;
+          break;
+        }
+        if (tid == 0) ++loads_done;
+        uint32_t v[16];
+        const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(a * 2 * kTcN + qq * kWsHalf + qc * 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        float *col = sC + buf * kWsCFloats + (qc * 16) * kTcM + row;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) col[j * kTcM] -= __uint_as_float(v[j]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        epi_bar();
+        if (tid == 0) {
+          tma_store_2d(tmap, x, slot_col(sl), smem_u32(sC + buf * kWsCFloats));
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          if (sl + 2 < nslot) {
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            load_slot(sl + 2);
+            ++loads_issued;
+          }
+        }
+      }
+      if (!ok) break;
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      if (tid == 0) mbar_arrive(smem_u32(&acce[a]));
+    }
+    if (!ok && tid == 0) abort_flag = 1, atomicOr(err, 4);
+    if (tid == 0) {
+      for (int g = loads_done; g < loads_issued; ++g) wait_phase(smem_u32(&cfull[g & 1]), uint32_t((g >> 1) & 1));
+      asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    }
+  } else {
+    // ---- epilogue without TMA: thread (q4, qc) owns row q4 * 32 + lane, columns qc * 32 .. + 31 of each tile ----
+    const int q4 = warp & 3, qc = warp >> 2;
+    const int row = rb + q4 * 32 + lane;
+    for (int i = 0; i < np; ++i) {
+      const int a = i & 1;
+      const bool w = !abort_flag && wait_phase(smem_u32(&accf[a]), uint32_t((i >> 1) & 1));
+      if (!epi_bar_and(w)) {
+        if (tid == 0) abort_flag = 1, atomicOr(err, 4);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int nh = pair_wide(i) ? 2 : 1;
+      for (int hh = 0; hh < nh; ++hh) {
+        const int ct = pair_tile(i) + hh;
+        const int cb = ct * kTcN + qc * 32;
+        float *Crow = A + (t0 + row) + int64_t(t0 + cb) * ld;
+        const int ncol = row < nrest ? min(32, nrest - cb) : 0;
+        float cv[32];
+        {
+          const float *pp = Crow;
+#pragma unroll
+          for (int j = 0; j < 32; ++j, pp += ld) cv[j] = j < ncol ? *pp : 0.f;
+        }
+#pragma unroll
+        for (int c0 = 0; c0 < 32; c0 += 16) {
+          uint32_t v[16];
+          const uint32_t taddr =
+              tmem + (uint32_t(q4 * 32) << 16) + uint32_t(a * 2 * kTcN + hh * kTcN + qc * 32 + c0);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+              "%14, %15}, [%16];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+          for (int j = 0; j < 16; ++j) cv[c0 + j] -= __uint_as_float(v[j]);
+        }
+        float *pp = Crow;
+#pragma unroll
+        for (int j = 0; j < 32; ++j, pp += ld)
+          if (j < ncol) *pp = cv[j];
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      epi_bar();
+      if (tid == 0) mbar_arrive(smem_u32(&acce[a]));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(4 * kTcN)));
+}
+
 // Whole-wave split count: each CTA takes ceil(ct / splits) column tiles of one
 // row tile; the launch lasts about ceil(CTAs / slots) such ranges (plus the
 // A staging, `lead` tiles), minimised over whole waves.
@@ -1174,6 +1463,32 @@ cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, in
   else
     k_gemm_tc_ws<0><<<g, kWsThreads, gemm_ws_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi, apack,
                                                           bpack, lower, maps64);
+  return cudaGetLastError();
+}
+
+size_t gemm_wide_smem() {
+  return (size_t(kWdStages) * kWdStageFloats + 2 * size_t(kWsCFloats)) * sizeof(float) + 1024;
+}
+
+cudaError_t launch_gemm_tc_wide(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
+                                cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const float *apack,
+                                int max_tiles, const uint8_t *maps64) {
+  if (cudaError_t ea = smem_attr((const void *)k_gemm_tc_wide, int(gemm_wide_smem())); ea != cudaSuccess) return ea;
+  if (apack == nullptr) return cudaErrorInvalidValue;
+  const int rest = max_f - j0 - 1;
+  if (rest <= 0) return cudaSuccess;
+  const int rt = (rest + kTcM - 1) / kTcM;
+  const int ct = std::min((rest + kTcN - 1) / kTcN, tile_hi) - tile_lo;
+  if (ct <= 0) return cudaSuccess;
+  const int npair = (ct + 1) / 2;
+  int splits = wave_splits(rt, npair, nfront, std::max(sm_budget, 1), 1.0);
+  if (max_tiles > 0) {
+    const int max_pairs = std::max(1, max_tiles / 2);
+    splits = std::max(splits, std::min(npair, (npair + max_pairs - 1) / max_pairs));
+  }
+  dim3 g(splits, rt, nfront);
+  k_gemm_tc_wide<<<g, kWsThreads, gemm_wide_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi, apack,
+                                                         maps64);
   return cudaGetLastError();
 }
 

@@ -409,6 +409,7 @@ def h2sp_solve_host(an, inp: H2Input, b_ptr: int, ldb: int, x_ptr: int, ldx: int
 
 H2SP_OPTION_WAIT_POLLS, H2SP_OPTION_TEST_STALE_EPOCH = 1, 2
 H2SP_OPTION_CHOL_TILES_PER_CTA, H2SP_OPTION_CHOL_PANEL_SMS, H2SP_OPTION_CHOL_LOOKAHEAD = 3, 4, 5
+H2SP_OPTION_CHOL_WIDE = 6
 
 
 def h2sp_set_option(h: Handle, option: int, value: int):

@@ -4,9 +4,10 @@ The factorization's dense work is the block-end tensor-core update of every
 front; how it shares the GPU with the panel stream depends on the front
 sizes of the structure.  For one structure (an analysis handle) and one
 device, ``tune`` times h2sp_factor(H2SP_FP32_CHOL) under candidate schedules
--- the h2sp_set_option knobs: the most 128-column tiles one CTA of the
-block-end update takes, the SMs that update leaves to the panel stream, and
-the look-ahead -- by coordinate descent from the library's defaults, and
+-- the h2sp_set_option knobs: the output tile of the block-end update (128 x
+128, or 128 x 256 over pairs of column tiles), the most 128-column tiles one
+CTA of it takes, the SMs that update leaves to the panel stream, and the
+look-ahead -- by coordinate descent from the library's defaults, and
 keeps the fastest.  A schedule changes the order of work, not the factors
 beyond rounding order.
 
@@ -24,14 +25,15 @@ from . import h2sp as H
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SHIPPED = os.path.join(HERE, "tuned.json")
-DEFAULT = {"tiles_per_cta": 0, "panel_sms": -1, "lookahead": 1}
+DEFAULT = {"tiles_per_cta": 0, "panel_sms": -1, "lookahead": 1, "wide": 1}
 CANDIDATES = {
+    "wide": [1, 0],
     "tiles_per_cta": [0, 8, 16, 32, 64],
     "panel_sms": [-1, 8, 16, 32],
     "lookahead": [1, 0],
 }
 _OPT = {"tiles_per_cta": H.H2SP_OPTION_CHOL_TILES_PER_CTA, "panel_sms": H.H2SP_OPTION_CHOL_PANEL_SMS,
-        "lookahead": H.H2SP_OPTION_CHOL_LOOKAHEAD}
+        "lookahead": H.H2SP_OPTION_CHOL_LOOKAHEAD, "wide": H.H2SP_OPTION_CHOL_WIDE}
 
 
 def key(stats: dict, device: str) -> str:

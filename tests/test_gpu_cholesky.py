@@ -200,8 +200,9 @@ def test_cholesky_then_lu_then_cholesky_same_handle():
 
 
 def test_schedules_give_the_same_factor():
-    """Every candidate schedule of the autotuner (tiles per CTA of the
-    block-end update, SMs left to the panel stream, look-ahead) factors S to
+    """Every candidate schedule of the autotuner (128 x 128 or 128 x 256
+    tiles and tiles per CTA of the block-end update, SMs left to the panel
+    stream, look-ahead) factors S to
     the same L up to FP32 rounding order, and the tuner returns one of them."""
     from paper_1705_04601_gb300 import tune as T
     h, b, sp, ch = case("sphere8k")
@@ -209,7 +210,8 @@ def test_schedules_give_the_same_factor():
     inp = H.H2Input(h)
     ref = None
     for sched in [T.DEFAULT, {"tiles_per_cta": 8, "panel_sms": 16, "lookahead": 1},
-                  {"tiles_per_cta": 32, "panel_sms": 8, "lookahead": 0}]:
+                  {"tiles_per_cta": 32, "panel_sms": 8, "lookahead": 0}, dict(T.DEFAULT, wide=1),
+                  {"tiles_per_cta": 3, "panel_sms": 8, "lookahead": 1, "wide": 1}]:
         hd = H.h2sp_sparsify_analyzed(an, inp)
         T.apply(hd, sched)
         H.h2sp_factor(hd, H.H2SP_FP32_CHOL)
