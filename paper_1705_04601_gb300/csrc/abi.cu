@@ -2104,7 +2104,8 @@ int h2sp_set_option(h2sp_handle *h, int32_t option, int64_t value) {
       h->chol_sched.lookahead = value != 0;
       return H2SP_OK;
     case H2SP_OPTION_CHOL_WIDE:
-      h->chol_sched.wide = value != 0;
+      if (value < 0 || value > 2) return H2SP_EINVAL;
+      h->chol_sched.wide = int(value);
       return H2SP_OK;
     default:
       return H2SP_EINVAL;

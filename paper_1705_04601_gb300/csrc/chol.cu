@@ -283,7 +283,8 @@ cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfro
         const size_t e0 = prof->begin(st);
         cudaError_t ge =
             (sch.wide && bf16 == 0)
-                ? launch_gemm_tc_wide(fr, J, KB, nfront, max_f, fronts, err, st, tlo, thi, budget, ap, max_tiles, maps64)
+                ? launch_gemm_tc_wide(fr, J, KB, nfront, max_f, fronts, err, st, tlo, thi, budget, ap, ap, /*lower=*/1,
+                                      max_tiles, maps64, sch.wide == 2 ? 1 : 0)
                 : launch_gemm_tc_ws(fr, J, KB, nfront, max_f, fronts, err, st, tlo, thi, budget, maps, ap, ap,
                                     /*lower=*/1, max_tiles, maps64, bf16);
         prof->end(P_GEMM, 1, e0, fg, st);

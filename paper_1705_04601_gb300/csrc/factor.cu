@@ -1855,6 +1855,17 @@ inline bool use_tensor_core_gemm() {
   return v == 1;
 }
 
+// The FP32 block LU's block-end update in 128 x 256 tiles (k_gemm_tc_wide);
+// H2SP_GEMM_WIDE=0 keeps the 128 x 128 tiles.
+inline bool wide_lu_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = std::getenv("H2SP_GEMM_WIDE");
+    v = (e && std::strcmp(e, "0") == 0) ? 0 : 1;
+  }
+  return v == 1;
+}
+
 
 // Step j0 of the blocked LU of every front of a level: panel (columns
 // [j0, j0 + NB), partial pivoting over the supernode rows), row interchanges
@@ -2054,8 +2065,11 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
         prof->end(P_GEMM_INNER, 1, e0, fp, st);
         e0 = prof->begin(st);
         if (ge == cudaSuccess)
-          ge = launch_gemm_tc_ws(fr, J, KB, nfront, max_f, fronts, err, st, tlo, thi, budget, maps,
-                                 apack[(J / KB) & 1], bpack, 0, 0, maps64);
+          ge = wide_lu_enabled()
+                   ? launch_gemm_tc_wide(fr, J, KB, nfront, max_f, fronts, err, st, tlo, thi, budget,
+                                         apack[(J / KB) & 1], bpack, /*lower=*/0, 0, maps64)
+                   : launch_gemm_tc_ws(fr, J, KB, nfront, max_f, fronts, err, st, tlo, thi, budget, maps,
+                                       apack[(J / KB) & 1], bpack, 0, 0, maps64);
         prof->end(P_GEMM, 1, e0, fg, st);
         return ge != cudaSuccess ? ge : cudaGetLastError();
       };

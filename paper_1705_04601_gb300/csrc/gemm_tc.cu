@@ -302,6 +302,13 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int 
       "l"(tmap), "r"(x), "r"(y), "r"(mbar)
       : "memory");
 }
+// C += box (FP32 add in L2), same completion as a store
+__device__ __forceinline__ void tma_reduce_add_2d(const void *tmap, int x, int y, uint32_t src) {
+  asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   tmap),
+               "r"(x), "r"(y), "r"(src)
+               : "memory");
+}
 __device__ __forceinline__ void tma_store_2d(const void *tmap, int x, int y, uint32_t src) {
   asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(tmap), "r"(x),
                "r"(y), "r"(src)
@@ -1051,18 +1058,23 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(2 * kTcN)));
 }
 
-// ---- the block-end update of the block Cholesky with 128 x 256 output tiles ----
-// The same lower-triangle update C -= L21 L21^T (three-term TF32 products) as
-// k_gemm_tc_ws, with the column tiles taken in pairs: one kind::tf32 MMA of
-// N = 256 per K step reads two packed 128-row tiles of L21 laid one after the
-// other in shared memory (their 8-row groups continue at the same stride), so
-// each staged byte of A serves twice the products.  A pair past the diagonal
-// tile (the last one, when the CTA's tiles are odd in number) is a single
-// tile with the N = 128 MMA.  Three 48 KB operand stages, two 256-column TMEM
-// accumulators (all 512 columns), and the C tile through TMA in 64-column
-// quarters alternating between two shared-memory buffers: quarter s + 2 is
-// requested as soon as the store of quarter s has read its buffer.  Every
-// wait is bounded, as in k_gemm_tc_ws.
+// ---- the block-end update with 128 x 256 output tiles ----
+// The same update as k_gemm_tc_ws (three-term TF32 products; C -= L21 U12
+// from the packed A and B, or with `lower` the block Cholesky's lower
+// triangle C -= L21 L21^T with B = A's pack), with the column tiles taken in
+// pairs: one kind::tf32 MMA of N = 256 per K step reads two packed 128-row
+// B tiles laid one after the other in shared memory (their 8-row groups
+// continue at the same stride), so each staged byte of A serves twice the
+// products.  A pair whose second tile lies past the last column tile (or,
+// with `lower`, past the diagonal tile) is a single tile with the N = 128 MMA.
+// Three 48 KB operand stages, two 256-column TMEM accumulators (all 512
+// columns), and the C tile through TMA in 64-column quarters alternating
+// between two shared-memory buffers.  RED = false: C is loaded, the product
+// subtracted and C stored back, quarter s + 2 requested as soon as the store
+// of quarter s has read its buffer.  RED = true: the negated product goes out
+// as a TMA reduce-add into C (one FP32 addition in L2, the rounding of
+// C - product), so the epilogue never waits for C.  Every wait is bounded, as
+// in k_gemm_tc_ws.
 constexpr int kWdStages = 3;
 constexpr int kWdStageFloats = 6 * kPkTile;  // A hi, A lo, B hi x 2 tiles, B lo x 2 tiles: 48 KB
 constexpr uint32_t kIdescWide = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(256 >> 3) << 17) |
@@ -1077,10 +1089,12 @@ __device__ __forceinline__ void mma_tf32_i(uint32_t tmem_d, uint64_t da, uint64_
       "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
 }
 
+template <bool RED>
 __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_wide(const FrontDev *__restrict__ fr, int j0, int kb,
                                                                float *__restrict__ fronts, int *__restrict__ err,
                                                                int splits, int tile_lo, int tile_hi,
                                                                const float *__restrict__ apack,
+                                                               const float *__restrict__ bpack, int lower,
                                                                const uint8_t *__restrict__ maps64) {
   const FrontDev F = fr[blockIdx.z];
   if (j0 >= F.s) return;
@@ -1089,8 +1103,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_wide(const FrontDev *
   const int nrest = F.f - t0;
   const int rb = blockIdx.y * kTcM;
   if (rb >= nrest) return;
-  // column tiles [tile_lo, tend): up to the diagonal tile, taken in pairs
-  const int tend = min(min((nrest + kTcN - 1) / kTcN, tile_hi), int(blockIdx.y) + 1);
+  // column tiles [tile_lo, tend) (with `lower`, up to the diagonal tile), taken in pairs
+  const int tend_all = min((nrest + kTcN - 1) / kTcN, tile_hi);
+  const int tend = lower ? min(tend_all, int(blockIdx.y) + 1) : tend_all;
   if (tend <= tile_lo) return;
   const int npair = (tend - tile_lo + 1) / 2;
   const int per = (npair + splits - 1) / splits;
@@ -1136,7 +1151,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_wide(const FrontDev *
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   const float *Ab = apack + (int64_t(F.pack_off) + blockIdx.y) * kPackTileFloats;
-  const float *Bb = apack + int64_t(F.pack_off) * kPackTileFloats;
+  const float *Bb = bpack + int64_t(F.pack_off) * kPackTileFloats;
   constexpr uint32_t kArr = kPkTile * 4;  // one 128 x 16 hi (or lo) array: 8 KB
 
   if (warp == kWsEpiWarps) {
@@ -1217,6 +1232,52 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_wide(const FrontDev *
           wait_phase(smem_u32(&empty[last_mma % kWdStages]), uint32_t((last_mma / kWdStages) & 1));
       }
     }
+  } else if (use_tma && RED) {
+    // ---- epilogue by TMA reduce-add: slot s = quarter (s & 3) of pair (s >> 2), buffer s & 1 ----
+    const int q4 = warp & 3, qc = warp >> 2;
+    const int row = q4 * 32 + lane;
+    const int x = t0 + rb;
+    bool ok = true;
+    for (int i = 0; i < np && ok; ++i) {
+      const int a = i & 1;
+      const bool w = !abort_flag && wait_phase(smem_u32(&accf[a]), uint32_t((i >> 1) & 1));
+      if (!epi_bar_and(w)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int nqq = pair_wide(i) ? 4 : 2;
+      for (int qq = 0; qq < nqq; ++qq) {
+        const int sl = 4 * i + qq, buf = sl & 1;
+        uint32_t v[16];
+        const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(a * 2 * kTcN + qq * kWsHalf + qc * 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (sl >= 2) {
+          // the reduce of quarter s - 2 has read buffer `buf`
+          if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          epi_bar();
+        }
+        float *col = sC + buf * kWsCFloats + (qc * 16) * kTcM + row;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) col[j * kTcM] = -__uint_as_float(v[j]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        epi_bar();
+        if (tid == 0) {
+          tma_reduce_add_2d(tmap, x, t0 + pair_tile(i) * kTcN + qq * kWsHalf, smem_u32(sC + buf * kWsCFloats));
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      if (tid == 0) mbar_arrive(smem_u32(&acce[a]));
+    }
+    if (!ok && tid == 0) abort_flag = 1, atomicOr(err, 4);
+    if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   } else if (use_tma) {
     // ---- epilogue with TMA: slot s = quarter (s & 3) of pair (s >> 2), 64 columns, buffer s & 1 ----
     const int q4 = warp & 3, qc = warp >> 2;
@@ -1472,9 +1533,10 @@ size_t gemm_wide_smem() {
 
 cudaError_t launch_gemm_tc_wide(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
                                 cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const float *apack,
-                                int max_tiles, const uint8_t *maps64) {
-  if (cudaError_t ea = smem_attr((const void *)k_gemm_tc_wide, int(gemm_wide_smem())); ea != cudaSuccess) return ea;
-  if (apack == nullptr) return cudaErrorInvalidValue;
+                                const float *bpack, int lower, int max_tiles, const uint8_t *maps64, int reduce) {
+  const void *kern = reduce ? (const void *)k_gemm_tc_wide<true> : (const void *)k_gemm_tc_wide<false>;
+  if (cudaError_t ea = smem_attr(kern, int(gemm_wide_smem())); ea != cudaSuccess) return ea;
+  if (apack == nullptr || bpack == nullptr) return cudaErrorInvalidValue;
   const int rest = max_f - j0 - 1;
   if (rest <= 0) return cudaSuccess;
   const int rt = (rest + kTcM - 1) / kTcM;
@@ -1487,8 +1549,12 @@ cudaError_t launch_gemm_tc_wide(const FrontDev *fr, int j0, int kb, int nfront, 
     splits = std::max(splits, std::min(npair, (npair + max_pairs - 1) / max_pairs));
   }
   dim3 g(splits, rt, nfront);
-  k_gemm_tc_wide<<<g, kWsThreads, gemm_wide_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi, apack,
-                                                         maps64);
+  if (reduce)
+    k_gemm_tc_wide<true><<<g, kWsThreads, gemm_wide_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi,
+                                                                 apack, bpack, lower, maps64);
+  else
+    k_gemm_tc_wide<false><<<g, kWsThreads, gemm_wide_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi,
+                                                                  apack, bpack, lower, maps64);
   return cudaGetLastError();
 }
 

@@ -170,7 +170,8 @@ struct CholSchedule {
   int tiles_per_cta = 0;
   int panel_sms = -1;
   int lookahead = 1;
-  int wide = 1;  // TF32 block-end update in 128 x 256 tiles (launch_gemm_tc_wide); 0: 128 x 128
+  int wide = 1;  // TF32 block-end update in 128 x 256 tiles (launch_gemm_tc_wide); 0: 128 x 128; 2: 128 x 256
+                 // with the C update by TMA reduce-add
 };
 // Block Cholesky of every front of one level (all fronts in parallel): no
 // pivoting, lower-triangle updates, the B operand read from L21.  A pivot
@@ -268,11 +269,12 @@ cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, in
                               cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const uint8_t *maps,
                               const float *apack, const float *bpack, int lower = 0, int max_tiles = 0,
                               const uint8_t *maps64 = nullptr, int bf16 = 0);
-// The block Cholesky's TF32 block-end update in 128 x 256 output tiles (pairs
-// of column tiles of the packed L21 `apack`, lower triangle): k_gemm_tc_wide.
+// The TF32 block-end update in 128 x 256 output tiles (pairs of packed
+// column tiles of `bpack`; with `lower`, the block Cholesky's lower triangle
+// with bpack = apack): k_gemm_tc_wide.
 cudaError_t launch_gemm_tc_wide(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
                                 cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const float *apack,
-                                int max_tiles, const uint8_t *maps64);
+                                const float *bpack, int lower, int max_tiles, const uint8_t *maps64, int reduce = 0);
 // BF16 operands of the block-end update (block Cholesky): each 128-row tile of
 // L21 scaled by a power of two and rounded to BF16 (mode 1), or split into a
 // BF16 hi and lo part (mode 2); the exponent rides in the tile's slot of the

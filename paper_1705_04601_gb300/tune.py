@@ -27,7 +27,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SHIPPED = os.path.join(HERE, "tuned.json")
 DEFAULT = {"tiles_per_cta": 0, "panel_sms": -1, "lookahead": 1, "wide": 1}
 CANDIDATES = {
-    "wide": [1, 0],
+    "wide": [1, 2, 0],
     "tiles_per_cta": [0, 8, 16, 32, 64],
     "panel_sms": [-1, 8, 16, 32],
     "lookahead": [1, 0],

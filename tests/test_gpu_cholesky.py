@@ -210,8 +210,9 @@ def test_schedules_give_the_same_factor():
     inp = H.H2Input(h)
     ref = None
     for sched in [T.DEFAULT, {"tiles_per_cta": 8, "panel_sms": 16, "lookahead": 1},
-                  {"tiles_per_cta": 32, "panel_sms": 8, "lookahead": 0}, dict(T.DEFAULT, wide=1),
-                  {"tiles_per_cta": 3, "panel_sms": 8, "lookahead": 1, "wide": 1}]:
+                  {"tiles_per_cta": 32, "panel_sms": 8, "lookahead": 0}, dict(T.DEFAULT, wide=0),
+                  dict(T.DEFAULT, wide=2), {"tiles_per_cta": 3, "panel_sms": 8, "lookahead": 1, "wide": 1},
+                  {"tiles_per_cta": 5, "panel_sms": 16, "lookahead": 1, "wide": 2}]:
         hd = H.h2sp_sparsify_analyzed(an, inp)
         T.apply(hd, sched)
         H.h2sp_factor(hd, H.H2SP_FP32_CHOL)
