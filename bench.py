@@ -66,9 +66,9 @@ SPD_WORKLOADS = {"inv3d_sphere_n262144"}
 # class's average work per launch.
 TRAFFIC = {
     "gemm_update": {
-        "src": "gemm_tc.cu", "src_hash": "6c2ff605cd11920b", "dram_over_algorithmic": 0.016543,
-        "capture": "profiles/gemm_tc_ws_inv3d_sphere_n32768.md: dram__bytes_read.sum + dram__bytes_write.sum over "
-                   "every k_gemm_tc_ws launch of two factorizations at N = 32,768 (70.52 GB per factorization) "
+        "src": "gemm_tc.cu", "src_hash": "ce4a225b676a05e3", "dram_over_algorithmic": 0.016660,
+        "capture": "profiles/gemm_tc_wide_inv3d_sphere_n32768.md: dram__bytes_read.sum + dram__bytes_write.sum over "
+                   "every k_gemm_tc_wide launch of two factorizations at N = 32,768 (71.02 GB per factorization) "
                    "divided by their algorithmic flops (4.263e12)",
     },
 }
