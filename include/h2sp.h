@@ -610,9 +610,11 @@ enum {
    * leaves to the panel stream (-1, the default: one per front of the
    * level).  LOOKAHEAD: 1 (default) factors the next block's panels on a
    * high-priority stream while the rest of the update runs, 0 serialises.
-   * WIDE: 1 (default) takes the TF32 block-end update in 128 x 256 output
+   * WIDE: the TF32 block-end update's tiles: 2 (default) 128 x 256 output
    * tiles (one N = 256 MMA over two packed column tiles: a quarter fewer
-   * operand bytes per product), 0 in 128 x 128 tiles. */
+   * operand bytes per product) with the product subtracted from C by a TMA
+   * reduce-add, which frees a shared-memory buffer for a fourth operand
+   * stage; 1 the same tiles with C loaded and stored; 0 128 x 128 tiles. */
   H2SP_OPTION_CHOL_TILES_PER_CTA = 3,
   H2SP_OPTION_CHOL_PANEL_SMS = 4,
   H2SP_OPTION_CHOL_LOOKAHEAD = 5,

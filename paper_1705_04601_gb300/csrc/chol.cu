@@ -25,6 +25,8 @@
 // the LU path serve unchanged (u_jj = d_j^2 > 0).
 #include <climits>
 #include <cstdint>
+#include <cstdlib>
+#include <cstring>
 #include <type_traits>
 
 #include "kernels.h"
@@ -125,6 +127,186 @@ __global__ void __launch_bounds__(kDiagThreads) k_chol_diag(const FrontDev *__re
   T *Li = inv + int64_t(blockIdx.x) * NB * NB;
   for (int e = tid; e < NB * NB; e += kDiagThreads) Li[e] = Y[(e / NB) * P + e % NB];
   for (int j = tid; j < jb; j += kDiagThreads) piv[F.piv_off + j0 + j] = j0 + j;
+}
+
+// The same tile Cholesky and inverse as k_chol_diag, blocked by 8 columns
+// so that the CTA synchronises 3 times per 8 columns instead of twice per
+// column, with short dependent chains:
+//   factorization, for each 8-column step c0 (right-looking):
+//     (a) warp 0, lane i < 8 holding row c0 + i of the 8 x 8 diagonal block:
+//         for j < 8, l_jj = sqrt(a_jj) (shuffled from lane j), l_ij = a_ij / l_jj,
+//         then a_ik -= l_ij l_kj for j < k <= i (l_kj shuffled from lane k);
+//     (b) a thread per row r below: x_j = (a_rj - sum_{m<j} x_m l_jm) / l_jj;
+//     (c) the lower triangle below: a_rc -= sum_{m<8} l_rm l_cm (rank 8);
+//   a pivot that is not positive is handled as in k_chol_diag (its "diagonal
+//   as the panel found it" is the tile's entry before this kernel).
+//   inverse Y = L^-1 by 8 x 8 blocks: each warp inverts one diagonal block
+//   (lane c forms column c by forward substitution); then for d = 1, 2, ...
+//   the blocks (i, j = i - d) at once: S = sum_{m = 8j}^{8i - 1} L[8i + r][m]
+//   Y[m][8j + c], and Y_ij = -Y_ii S.
+// Rows and columns beyond jb hold the identity, so they factor trivially and
+// leave the result unchanged; only rows and columns below jb are written.
+template <typename T, int NB>
+__global__ void __launch_bounds__(kDiagThreads) k_chol_diag_blk(const FrontDev *__restrict__ fr, int j0,
+                                                                T *__restrict__ fronts, int32_t *__restrict__ piv,
+                                                                int *__restrict__ err, T *__restrict__ inv,
+                                                                int compensate) {
+  static_assert(NB % 8 == 0 && NB / 8 <= kDiagThreads / 32, "8-column blocks, a warp per diagonal block");
+  const FrontDev F = fr[blockIdx.x];
+  if (j0 >= F.s) return;  // uniform over the CTA
+  const int jb = min(NB, F.s - j0);
+  T *A = fronts + F.off;
+  const int64_t ld = F.ld;
+  constexpr int P = NB + 1;
+  constexpr int NBK = NB / 8;
+  __shared__ T L[NB * P];  // row-major
+  __shared__ T Y[NB * P];
+  __shared__ T S[(NBK - 1) * 64 + 1];
+  __shared__ T d0[NB];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < NB * NB; e += kDiagThreads) {
+    const int r = e % NB, c = e / NB;  // down the columns of the front
+    T v = T(0);
+    if (r < jb && c <= r) v = A[(j0 + r) + int64_t(j0 + c) * ld];
+    else if (r == c) v = T(1);
+    L[r * P + c] = v;
+    Y[r * P + c] = T(0);
+    if (r == c) d0[r] = v;
+  }
+  __syncthreads();
+  for (int c0 = 0; c0 < NB; c0 += 8) {
+    // (a) the 8 x 8 diagonal block
+    if (warp == 0) {
+      T rv[8];
+      const bool own = lane < 8;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) rv[m] = (own && m <= lane) ? L[(c0 + lane) * P + c0 + m] : T(0);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        T a = __shfl_sync(0xffffffffu, rv[j], j);
+        if (!(a > T(0)) || !isfinite(a)) {
+          const T a0 = d0[c0 + j];
+          const bool comp = compensate && a0 > T(0) && isfinite(a0);
+          if (lane == 0) {
+            if (comp) {
+              atomicOr(err, 16);
+              atomicAdd(err + 1, 1);
+            } else {
+              atomicOr(err, 8);
+            }
+          }
+          a = comp ? a0 : T(1);
+        }
+        const T djj = sqrt(a);
+        if (lane == j) rv[j] = djj;
+        if (lane > j) rv[j] = rv[j] / djj;
+#pragma unroll
+        for (int k = j + 1; k < 8; ++k) {
+          const T lkj = __shfl_sync(0xffffffffu, rv[j], k);
+          if (lane > j && k <= lane) rv[k] -= rv[j] * lkj;
+        }
+      }
+      if (own)
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+          if (m <= lane) L[(c0 + lane) * P + c0 + m] = rv[m];
+    }
+    __syncthreads();
+    // (b) the rows below against the diagonal block
+    const int nbelow = NB - c0 - 8;
+    if (tid < nbelow) {
+      const int r = c0 + 8 + tid;
+      T x[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) x[m] = L[r * P + c0 + m];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        T v = x[j];
+#pragma unroll
+        for (int m = 0; m < j; ++m) v -= x[m] * L[(c0 + j) * P + c0 + m];
+        x[j] = v / L[(c0 + j) * P + c0 + j];
+      }
+#pragma unroll
+      for (int m = 0; m < 8; ++m) L[r * P + c0 + m] = x[m];
+    }
+    __syncthreads();
+    // (c) the rank-8 update of the lower triangle below
+    if (nbelow > 0) {
+      const int tr = tid >> 4, tc = tid & 15;
+      for (int r = c0 + 8 + tr; r < NB; r += 16) {
+        T xr[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) xr[m] = L[r * P + c0 + m];
+        for (int c = c0 + 8 + tc; c <= r; c += 16) {
+          T acc = L[r * P + c];
+#pragma unroll
+          for (int m = 0; m < 8; ++m) acc -= xr[m] * L[c * P + c0 + m];
+          L[r * P + c] = acc;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // inverse: the diagonal blocks, a warp each (lane c: column c of the block)
+  if (warp < NBK && lane < 8) {
+    const int b = warp * 8, c = lane;
+    T y[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      T v = T(0);
+      if (r == c) {
+        v = T(1) / L[(b + r) * P + b + r];
+      } else if (r > c) {
+#pragma unroll
+        for (int m = 0; m < r; ++m)
+          if (m >= c) v -= L[(b + r) * P + b + m] * y[m];
+        v /= L[(b + r) * P + b + r];
+      }
+      y[r] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) Y[(b + r) * P + b + c] = y[r];
+  }
+  __syncthreads();
+  for (int d = 1; d < NBK; ++d) {
+    const int nblk = NBK - d;
+    for (int e = tid; e < nblk * 64; e += kDiagThreads) {
+      const int j = e >> 6, i = j + d, r = (e >> 3) & 7, c = e & 7;
+      T acc = T(0);
+      for (int m = 8 * j; m < 8 * i; ++m) acc += L[(8 * i + r) * P + m] * Y[m * P + 8 * j + c];
+      S[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < nblk * 64; e += kDiagThreads) {
+      const int j = e >> 6, i = j + d, r = (e >> 3) & 7, c = e & 7;
+      T acc = T(0);
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (t <= r) acc += Y[(8 * i + r) * P + 8 * i + t] * S[(j << 6) + t * 8 + c];
+      Y[(8 * i + r) * P + 8 * j + c] = -acc;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < NB * NB; e += kDiagThreads) {
+    const int rr = e % NB, cc = e / NB;
+    if (rr < jb && cc <= rr) A[(j0 + rr) + int64_t(j0 + cc) * ld] = L[rr * P + cc];
+  }
+  T *Li = inv + int64_t(blockIdx.x) * NB * NB;
+  for (int e = tid; e < NB * NB; e += kDiagThreads) {
+    const int rr = e / NB, cc = e % NB;
+    Li[e] = (rr < jb && cc < jb) ? Y[rr * P + cc] : T(0);
+  }
+  for (int j = tid; j < jb; j += kDiagThreads) piv[F.piv_off + j0 + j] = j0 + j;
+}
+
+// Tile kernel of the panel: the blocked form unless H2SP_CHOL_DIAG=columns
+inline bool chol_diag_blocked() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = std::getenv("H2SP_CHOL_DIAG");
+    v = (e && std::strcmp(e, "columns") == 0) ? 0 : 1;
+  }
+  return v == 1;
 }
 
 // L21 = F21 L11^-T for rows [j0 + jb, f) of the panel columns: a thread per
@@ -235,7 +417,10 @@ cudaError_t launch_chol_level(const FrontDev *fr, const Front *host_fr, int nfro
         fpanel += jb * jb * jb / 3.0 + rows * jb * jb;  // tile Cholesky + triangular solve of the rows below
       }
     const size_t e0 = prof->begin(st);
-    k_chol_diag<T, NB><<<nfront, kDiagThreads, 0, st>>>(fr, j0, fronts, piv, err, inv, bf16 != 0 ? 1 : 0);
+    if (chol_diag_blocked())
+      k_chol_diag_blk<T, NB><<<nfront, kDiagThreads, 0, st>>>(fr, j0, fronts, piv, err, inv, bf16 != 0 ? 1 : 0);
+    else
+      k_chol_diag<T, NB><<<nfront, kDiagThreads, 0, st>>>(fr, j0, fronts, piv, err, inv, bf16 != 0 ? 1 : 0);
     const int below = max_f - j0 - 1;
     if (below > 0)
       k_chol_l21<T, NB><<<dim3(unsigned(cdiv_c(below, kL21Threads)), unsigned(nfront)), kL21Threads, 0, st>>>(

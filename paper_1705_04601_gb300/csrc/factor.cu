@@ -1855,15 +1855,16 @@ inline bool use_tensor_core_gemm() {
   return v == 1;
 }
 
-// The FP32 block LU's block-end update in 128 x 256 tiles (k_gemm_tc_wide);
-// H2SP_GEMM_WIDE=0 keeps the 128 x 128 tiles.
-inline bool wide_lu_enabled() {
+// The FP32 block LU's block-end update: 128 x 256 tiles with the C update by
+// TMA reduce-add (k_gemm_tc_wide, four operand stages); H2SP_GEMM_WIDE=load
+// loads and stores C instead, H2SP_GEMM_WIDE=0 keeps the 128 x 128 tiles.
+inline int wide_lu_mode() {
   static int v = -1;
   if (v < 0) {
     const char *e = std::getenv("H2SP_GEMM_WIDE");
-    v = (e && std::strcmp(e, "0") == 0) ? 0 : 1;
+    v = (e && std::strcmp(e, "0") == 0) ? 0 : (e && std::strcmp(e, "load") == 0) ? 1 : 2;
   }
-  return v == 1;
+  return v;
 }
 
 
@@ -2065,9 +2066,9 @@ cudaError_t launch_lu_level(const FrontDev *fr, const Front *host_fr, int nfront
         prof->end(P_GEMM_INNER, 1, e0, fp, st);
         e0 = prof->begin(st);
         if (ge == cudaSuccess)
-          ge = wide_lu_enabled()
+          ge = wide_lu_mode() != 0
                    ? launch_gemm_tc_wide(fr, J, KB, nfront, max_f, fronts, err, st, tlo, thi, budget,
-                                         apack[(J / KB) & 1], bpack, /*lower=*/0, 0, maps64)
+                                         apack[(J / KB) & 1], bpack, /*lower=*/0, 0, maps64, wide_lu_mode() == 2)
                    : launch_gemm_tc_ws(fr, J, KB, nfront, max_f, fronts, err, st, tlo, thi, budget, maps,
                                        apack[(J / KB) & 1], bpack, 0, 0, maps64);
         prof->end(P_GEMM, 1, e0, fg, st);

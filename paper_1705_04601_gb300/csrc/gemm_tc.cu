@@ -1067,15 +1067,17 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_ws(const FrontDev *__
 // continue at the same stride), so each staged byte of A serves twice the
 // products.  A pair whose second tile lies past the last column tile (or,
 // with `lower`, past the diagonal tile) is a single tile with the N = 128 MMA.
-// Three 48 KB operand stages, two 256-column TMEM accumulators (all 512
-// columns), and the C tile through TMA in 64-column quarters alternating
-// between two shared-memory buffers.  RED = false: C is loaded, the product
-// subtracted and C stored back, quarter s + 2 requested as soon as the store
-// of quarter s has read its buffer.  RED = true: the negated product goes out
-// as a TMA reduce-add into C (one FP32 addition in L2, the rounding of
-// C - product), so the epilogue never waits for C.  Every wait is bounded, as
-// in k_gemm_tc_ws.
-constexpr int kWdStages = 3;
+// S 48 KB operand stages, two 256-column TMEM accumulators (all 512
+// columns), and the C tile through TMA in 64-column quarters.  RED = false
+// (three stages): C is loaded, the product subtracted and C stored back
+// through two alternating buffers, quarter s + 2 requested as soon as the
+// store of quarter s has read its buffer.  RED = true (four stages): the
+// negated product goes out as a TMA reduce-add into C (one FP32 addition in
+// L2, the rounding of C - product) through one buffer, so the epilogue never
+// waits for C and the freed buffer buys a fourth operand stage.  Every wait
+// is bounded, as in k_gemm_tc_ws.
+constexpr int kWdStages = 3;     // with the load / store epilogue
+constexpr int kWdStagesRed = 4;  // with the reduce-add epilogue (one C buffer)
 constexpr int kWdStageFloats = 6 * kPkTile;  // A hi, A lo, B hi x 2 tiles, B lo x 2 tiles: 48 KB
 constexpr uint32_t kIdescWide = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(256 >> 3) << 17) |
                                 (uint32_t(kTcM >> 4) << 24);
@@ -1089,7 +1091,7 @@ __device__ __forceinline__ void mma_tf32_i(uint32_t tmem_d, uint64_t da, uint64_
       "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
 }
 
-template <bool RED>
+template <bool RED, int S>
 __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_wide(const FrontDev *__restrict__ fr, int j0, int kb,
                                                                float *__restrict__ fronts, int *__restrict__ err,
                                                                int splits, int tile_lo, int tile_hi,
@@ -1120,8 +1122,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_wide(const FrontDev *
   const int64_t ld = F.ld;
   extern __shared__ __align__(1024) unsigned char smraw[];
   float *stage0 = reinterpret_cast<float *>(smraw);
-  float *sC = stage0 + kWdStages * kWdStageFloats;  // two 128 x 64 C quarters
-  __shared__ __align__(8) uint64_t full[kWdStages], empty[kWdStages], accf[2], acce[2], cfull[2];
+  float *sC = stage0 + S * kWdStageFloats;  // 128 x 64 C quarters: two (RED: one)
+  __shared__ __align__(8) uint64_t full[S], empty[S], accf[2], acce[2], cfull[2];
   const bool use_tma = maps64 != nullptr && (t0 & 3) == 0;
   const void *tmap = use_tma ? static_cast<const void *>(maps64 + size_t(blockIdx.z) * kTmapBytes) : nullptr;
   __shared__ uint32_t tmem_base;
@@ -1134,7 +1136,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_wide(const FrontDev *
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int i = 0; i < kWdStages; ++i) {
+    for (int i = 0; i < S; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(1));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(1));
     }
@@ -1159,9 +1161,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_wide(const FrontDev *
     if (lane == 0) {
       int issued = 0;
       for (int g = 0; g < G; ++g) {
-        const int st = g % kWdStages, i = g / nq, q = g % nq;
-        if (g >= kWdStages) {
-          const bool w = !abort_flag && wait_phase(smem_u32(&empty[st]), uint32_t(((g - kWdStages) / kWdStages) & 1));
+        const int st = g % S, i = g / nq, q = g % nq;
+        if (g >= S) {
+          const bool w = !abort_flag && wait_phase(smem_u32(&empty[st]), uint32_t(((g - S) / S) & 1));
           if (!w) {
             abort_flag = 1;
             break;
@@ -1185,7 +1187,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_wide(const FrontDev *
       if (abort_flag) {
         atomicOr(err, 4);
         for (int g = s_consumed; g < issued; ++g)
-          wait_phase(smem_u32(&full[g % kWdStages]), uint32_t((g / kWdStages) & 1));
+          wait_phase(smem_u32(&full[g % S]), uint32_t((g / S) & 1));
       }
     }
   } else if (warp == kWsEpiWarps + 1) {
@@ -1194,8 +1196,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_wide(const FrontDev *
       int last_mma = -1;
       bool ok = true;
       for (int g = 0; g < G && ok; ++g) {
-        const int st = g % kWdStages, i = g / nq, q = g % nq, a = i & 1;
-        if (abort_flag || !wait_phase(smem_u32(&full[st]), uint32_t((g / kWdStages) & 1))) {
+        const int st = g % S, i = g / nq, q = g % nq, a = i & 1;
+        if (abort_flag || !wait_phase(smem_u32(&full[st]), uint32_t((g / S) & 1))) {
           ok = false;
           break;
         }
@@ -1229,7 +1231,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_wide(const FrontDev *
         abort_flag = 1;
         atomicOr(err, 4);
         if (last_mma >= 0)
-          wait_phase(smem_u32(&empty[last_mma % kWdStages]), uint32_t((last_mma / kWdStages) & 1));
+          wait_phase(smem_u32(&empty[last_mma % S]), uint32_t((last_mma / S) & 1));
       }
     }
   } else if (use_tma && RED) {
@@ -1248,7 +1250,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_wide(const FrontDev *
       asm volatile("tcgen05.fence::after_thread_sync;");
       const int nqq = pair_wide(i) ? 4 : 2;
       for (int qq = 0; qq < nqq; ++qq) {
-        const int sl = 4 * i + qq, buf = sl & 1;
+        const int sl = 4 * i + qq, buf = 0;
         uint32_t v[16];
         const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(a * 2 * kTcN + qq * kWsHalf + qc * 16);
         asm volatile(
@@ -1258,9 +1260,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_tc_wide(const FrontDev *
               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;");
-        if (sl >= 2) {
-          // the reduce of quarter s - 2 has read buffer `buf`
-          if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        if (sl >= 1) {
+          // the reduce of the previous quarter has read the (single) buffer
+          if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
           epi_bar();
         }
         float *col = sC + buf * kWsCFloats + (qc * 16) * kTcM + row;
@@ -1527,15 +1529,17 @@ cudaError_t launch_gemm_tc_ws(const FrontDev *fr, int j0, int kb, int nfront, in
   return cudaGetLastError();
 }
 
-size_t gemm_wide_smem() {
-  return (size_t(kWdStages) * kWdStageFloats + 2 * size_t(kWsCFloats)) * sizeof(float) + 1024;
+size_t gemm_wide_smem(bool reduce) {
+  return reduce ? (size_t(kWdStagesRed) * kWdStageFloats + size_t(kWsCFloats)) * sizeof(float) + 1024
+                : (size_t(kWdStages) * kWdStageFloats + 2 * size_t(kWsCFloats)) * sizeof(float) + 1024;
 }
 
 cudaError_t launch_gemm_tc_wide(const FrontDev *fr, int j0, int kb, int nfront, int max_f, float *fronts, int *err,
                                 cudaStream_t s, int tile_lo, int tile_hi, int sm_budget, const float *apack,
                                 const float *bpack, int lower, int max_tiles, const uint8_t *maps64, int reduce) {
-  const void *kern = reduce ? (const void *)k_gemm_tc_wide<true> : (const void *)k_gemm_tc_wide<false>;
-  if (cudaError_t ea = smem_attr(kern, int(gemm_wide_smem())); ea != cudaSuccess) return ea;
+  const void *kern = reduce ? (const void *)k_gemm_tc_wide<true, kWdStagesRed>
+                            : (const void *)k_gemm_tc_wide<false, kWdStages>;
+  if (cudaError_t ea = smem_attr(kern, int(gemm_wide_smem(reduce != 0))); ea != cudaSuccess) return ea;
   if (apack == nullptr || bpack == nullptr) return cudaErrorInvalidValue;
   const int rest = max_f - j0 - 1;
   if (rest <= 0) return cudaSuccess;
@@ -1550,11 +1554,11 @@ cudaError_t launch_gemm_tc_wide(const FrontDev *fr, int j0, int kb, int nfront, 
   }
   dim3 g(splits, rt, nfront);
   if (reduce)
-    k_gemm_tc_wide<true><<<g, kWsThreads, gemm_wide_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi,
-                                                                 apack, bpack, lower, maps64);
+    k_gemm_tc_wide<true, kWdStagesRed><<<g, kWsThreads, gemm_wide_smem(true), s>>>(
+        fr, j0, kb, fronts, err, splits, tile_lo, tile_hi, apack, bpack, lower, maps64);
   else
-    k_gemm_tc_wide<false><<<g, kWsThreads, gemm_wide_smem(), s>>>(fr, j0, kb, fronts, err, splits, tile_lo, tile_hi,
-                                                                  apack, bpack, lower, maps64);
+    k_gemm_tc_wide<false, kWdStages><<<g, kWsThreads, gemm_wide_smem(false), s>>>(
+        fr, j0, kb, fronts, err, splits, tile_lo, tile_hi, apack, bpack, lower, maps64);
   return cudaGetLastError();
 }
 

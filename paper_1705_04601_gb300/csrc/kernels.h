@@ -170,8 +170,8 @@ struct CholSchedule {
   int tiles_per_cta = 0;
   int panel_sms = -1;
   int lookahead = 1;
-  int wide = 1;  // TF32 block-end update in 128 x 256 tiles (launch_gemm_tc_wide); 0: 128 x 128; 2: 128 x 256
-                 // with the C update by TMA reduce-add
+  int wide = 2;  // TF32 block-end update: 2 = 128 x 256 tiles, C by TMA reduce-add, four operand stages
+                 // (launch_gemm_tc_wide, reduce); 1 = 128 x 256 tiles, C loaded and stored; 0 = 128 x 128
 };
 // Block Cholesky of every front of one level (all fronts in parallel): no
 // pivoting, lower-triangle updates, the B operand read from L21.  A pivot

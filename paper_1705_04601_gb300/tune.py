@@ -25,9 +25,9 @@ from . import h2sp as H
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SHIPPED = os.path.join(HERE, "tuned.json")
-DEFAULT = {"tiles_per_cta": 0, "panel_sms": -1, "lookahead": 1, "wide": 1}
+DEFAULT = {"tiles_per_cta": 0, "panel_sms": -1, "lookahead": 1, "wide": 2}
 CANDIDATES = {
-    "wide": [1, 2, 0],
+    "wide": [2, 1, 0],
     "tiles_per_cta": [0, 8, 16, 32, 64],
     "panel_sms": [-1, 8, 16, 32],
     "lookahead": [1, 0],
