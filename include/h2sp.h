@@ -351,6 +351,10 @@ int h2sp_factor(h2sp_handle *h, int32_t prec, h2sp_stream stream);
  * h2sp_solve_captured and h2sp_export_front return H2SP_ESTATE until the next
  * h2sp_factor.  H2SP_EINVAL for tau < 0 or not finite; H2SP_ESINGULAR on a
  * zero pivot; H2SP_ENOMEM if the factors outgrow the memory.  Synchronous.
+ * Work space: a dense row and a bitmap of n entries for each CTA of the
+ * widest elimination level (at most two per SM), about 8.1 n bytes each,
+ * and a pool for the factors that starts at max(4 nnz(S), 64 n) entries and
+ * grows fourfold (recomputing the factorization) while it overflows.
  */
 int h2sp_factor_ilut(h2sp_handle *h, double tau, h2sp_stream stream);
 
