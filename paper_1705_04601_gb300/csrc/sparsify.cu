@@ -359,17 +359,18 @@ __global__ void __launch_bounds__(kThreads) k_transform(const XItem *__restrict_
 // operand value a thread loads from shared memory serves four (or twelve)
 // multiply-adds.  The K dimension streams through shared memory in chunks of
 // kKc: X (or QL^T) as kKc columns of all rows, QR (or T) as kKc rows of the
-// slab.  Without QR (QL) the stage is a copy.
+// slab.  Without QR (QL) the stage is a copy.  The FP32 form is held to 128
+// registers (two CTAs per SM): with one CTA of 8 warps per SM nothing covers
+// the latency of each chunk's global loads, and the FMA pipe idled (9 %).
 constexpr int kSlab = 32;
 constexpr int kKc = 8;
 constexpr int kTrMax = kMaxLargeBlock / 32;  // row groups per thread
 
 template <typename W>
-__global__ void __launch_bounds__(kThreads) k_transform_large(const XItem *__restrict__ items, int n_items,
-                                                              const void *const *__restrict__ src_base,
-                                                              const double *__restrict__ Qrow,
-                                                              const double *__restrict__ Qcol,
-                                                              W *const *__restrict__ dst_base) {
+__global__ void __launch_bounds__(kThreads, sizeof(W) == 4 ? 2 : 1)
+    k_transform_large(const XItem *__restrict__ items, int n_items, const void *const *__restrict__ src_base,
+                      const double *__restrict__ Qrow, const double *__restrict__ Qcol,
+                      W *const *__restrict__ dst_base) {
   static_assert(kThreads == 256 && kSlab == 32, "thread grid of the tiles");
   // persistent: each CTA walks the work list with a stride of the grid
   for (int ib = blockIdx.x; ib < n_items; ib += gridDim.x) {
