@@ -108,15 +108,26 @@ def tune(an: H.Handle, inp: H.H2Input, flags: int = H.H2SP_SPARSIFY_FP32, repeat
         return best
 
     H.h2sp_factor(hd, H.H2SP_FP32_CHOL)  # warm-up: buffers, descriptors
-    cur = dict(DEFAULT)
-    cur_ms = run(cur)
-    for name, values in CANDIDATES.items():
+    try:
+        return descend(run)
+    finally:
+        hd.close()
+
+
+def descend(cost, default: dict | None = None, candidates: dict | None = None, margin: float = 0.99):
+    """Coordinate descent: from ``default``, try each knob's candidate values
+    in turn with the other knobs at the best schedule so far, and move only
+    when the time ``cost(schedule)`` falls below ``margin`` times the best
+    (run-to-run noise does not move it).  Returns (schedule, time)."""
+    cur = dict(DEFAULT if default is None else default)
+    cands = CANDIDATES if candidates is None else candidates
+    cur_ms = cost(cur)
+    for name, values in cands.items():
         for v in values:
             if v == cur[name]:
                 continue
             cand = dict(cur, **{name: v})
-            ms = run(cand)
-            if ms < cur_ms * 0.99:
+            ms = cost(cand)
+            if ms < cur_ms * margin:
                 cur, cur_ms = cand, ms
-    hd.close()
     return cur, cur_ms

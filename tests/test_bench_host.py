@@ -260,3 +260,28 @@ def test_tune_cache_roundtrip(tmp_path, monkeypatch):
     assert T.load(k) == sched
     assert json.load(open(cache))[k]["factor_ms"] == 123.0
     assert set(T.DEFAULT) == set(T.CANDIDATES) and all(T.DEFAULT[n] in T.CANDIDATES[n] for n in T.DEFAULT)
+
+
+def test_tune_descent_finds_the_coordinate_optimum():
+    """The tuner's search on a fake timer: with a separable cost it reaches
+    the best value of every knob, trying each other value once per knob; a
+    gain inside the noise margin does not move it off the defaults."""
+    sys.path.insert(0, ROOT)
+    from paper_1705_04601_gb300 import tune as T
+    cands = {"a": [0, 1, 2], "b": [5, 6], "c": [1, 0]}
+    best = {"a": 2, "b": 6, "c": 0}
+    calls = []
+
+    def cost(s):
+        calls.append(dict(s))
+        return 100.0 + sum(10.0 * abs(s[k] - best[k]) for k in s)
+
+    sched, ms = T.descend(cost, {"a": 0, "b": 5, "c": 1}, cands)
+    assert sched == best and ms == 100.0
+    assert len(calls) == 1 + sum(len(v) - 1 for v in cands.values())
+    # every candidate changes one knob of a schedule timed before it
+    assert all(any(sum(c[k] != d[k] for k in c) == 1 for d in calls[:i]) for i, c in enumerate(calls) if i)
+    flat = lambda s: 100.0 - (0.5 if s["a"] == 1 else 0.0)  # 0.5 % better: inside the 1 % margin
+    assert T.descend(flat, {"a": 0, "b": 5, "c": 1}, cands)[0] == {"a": 0, "b": 5, "c": 1}
+    assert T.descend(lambda s: 100.0 - (5.0 if s["a"] == 1 else 0.0), {"a": 0, "b": 5, "c": 1},
+                     cands)[0] == {"a": 1, "b": 5, "c": 1}
