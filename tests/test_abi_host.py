@@ -337,3 +337,26 @@ def test_solve_rejects_bad_right_hand_side_counts():
         assert H.lib().h2sp_solve(an.ptr, ctypes.byref(o), nrhs, dummy, h.n, dummy, h.n, None, None) == H.H2SP_EINVAL
     assert H.lib().h2sp_solve(an.ptr, ctypes.byref(o), 1, dummy, h.n, dummy, h.n, None, None) == H.H2SP_ESTATE
     an.close()
+
+
+def test_empty_and_null_descriptors_are_rejected():
+    """An empty matrix (N = 0), a descriptor without levels, a NULL
+    descriptor or a NULL output handle are EINVAL, and no handle comes back."""
+    h = _make("tiny")
+    inp = H.H2Input(h, device=None)
+    out = ctypes.c_void_p()
+    d = inp.desc()
+    d.n = 0
+    assert H.lib().h2sp_analyze(ctypes.byref(d), ctypes.byref(out)) == H.H2SP_EINVAL and not out.value
+    d = inp.desc()
+    d.depth = -1
+    assert H.lib().h2sp_analyze(ctypes.byref(d), ctypes.byref(out)) == H.H2SP_EINVAL and not out.value
+    d = inp.desc()
+    d.level_ptr = None
+    assert H.lib().h2sp_analyze(ctypes.byref(d), ctypes.byref(out)) == H.H2SP_EINVAL and not out.value
+    assert H.lib().h2sp_analyze(None, ctypes.byref(out)) == H.H2SP_EINVAL and not out.value
+    assert H.lib().h2sp_analyze(ctypes.byref(inp.desc()), None) == H.H2SP_EINVAL
+    # the same descriptor, intact, is accepted: a single leaf, no far field (S = A)
+    an = H.h2sp_analyze(inp)
+    assert H.h2sp_query(an)["n"] == h.n
+    an.close()
