@@ -285,3 +285,18 @@ def test_tune_descent_finds_the_coordinate_optimum():
     assert T.descend(flat, {"a": 0, "b": 5, "c": 1}, cands)[0] == {"a": 0, "b": 5, "c": 1}
     assert T.descend(lambda s: 100.0 - (5.0 if s["a"] == 1 else 0.0), {"a": 0, "b": 5, "c": 1},
                      cands)[0] == {"a": 1, "b": 5, "c": 1}
+
+
+def test_shipped_schedules_are_candidates():
+    """Every schedule stored in the shipped tuned.json sets each knob of the
+    tuner, to one of its candidate values, under a well-formed key."""
+    sys.path.insert(0, ROOT)
+    from paper_1705_04601_gb300 import tune as T
+    d = json.load(open(T.SHIPPED))
+    assert d
+    for k, v in d.items():
+        dev, *sizes = k.split("|")
+        assert dev and [s.split("=")[0] for s in sizes] == ["n", "sn", "front", "chol"]
+        assert set(v["schedule"]) == set(T.CANDIDATES)
+        assert all(v["schedule"][name] in T.CANDIDATES[name] for name in T.CANDIDATES)
+        assert v["factor_ms"] > 0
